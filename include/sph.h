@@ -1,0 +1,170 @@
+/* sph.h — C ABI of the B300 weakly-compressible SPH library (libsph_b300.so).
+ *
+ * The library advances particle states with the delta-SPH scheme described in diffSPH
+ * (Winchenbach & Thuerey, arXiv 2507.21684) and differentiates rollouts with a hand-written
+ * adjoint.  Every step of the method runs in CUDA kernels for sm_103a; there is no CPU path.
+ *
+ * Method summary (paper sections in brackets):
+ *   state u = (x, v, rho) per particle, global parameters sigma, u_{n+1} = P(u_n)   [Sec. 2.2]
+ *   kernel W(r, H) = C_d / H^d w(|r|/H), Wendland C4 (2D/3D) or C2, support H     [App. A.1]
+ *   neighbours: cell list (cell key, radix sort, cell ranges), periodic minimum image [Sec. 3.2, App. B]
+ *   drho_i/dt = -rho_i sum_j V_j (v_j - v_i) . grad_i W_ij
+ *               + delta h c0 sum_j V_j psi_ij . grad_i W_ij                         [Sec. 2.3, Eq. continuity]
+ *   dv_i/dt   = -(1/rho_i) sum_j V_j (p_i + p_j) grad_i W_ij
+ *               + 2(d+2) nu (rho0/rho_i) sum_j V_j pi_ij grad_i W_ij + g            [Sec. 2.3, Eq. NS, viscosity]
+ *   p = rho0 c0^2 / gamma [(rho/rho0)^gamma - 1]  (Tait)                           [Sec. 2.3, Eq. EOS]
+ *   v' = v + dt a, rho' = rho + dt drho, x' = x + dt v'  (symplectic Euler)       [Sec. 3.4]
+ *   psi_ij = 2 (rho_j - rho_i)(x_j - x_i)/(|x_ij|^2 + eps h^2),
+ *   pi_ij  = (v_i - v_j).(x_i - x_j)/(|x_ij|^2 + eps h^2),  V_j = m_j / rho_j
+ *   H is the kernel support; h = H/2 is the smoothing length used in delta h c0 and eps h^2
+ *   (the paper's common choice H/h = 2, App. A.1).
+ *
+ * Conventions shared by all calls:
+ *   - Every function returns an int status (SPH_OK = 0).  Nothing throws across the ABI.
+ *     sph_last_error() returns a thread-local message for the last failing call.
+ *   - Particle arrays are packed row-major: x and v hold n*dim floats (x0 y0 [z0] x1 ...),
+ *     rho and mass hold n floats.  Fluid particles come first, then wall particles.
+ *   - "ptr_is_device" = 1 means the pointers are CUDA device pointers (for example torch
+ *     tensors' data_ptr()); 0 means host memory (pageable or pinned).  Inputs are copied;
+ *     the caller keeps ownership of everything it passes.  Outputs are caller-allocated.
+ *   - Results are always returned in the caller's original particle order.
+ *   - A scene is bound to one CUDA stream (0 = legacy default stream).  Calls on one scene
+ *     are not thread-safe; different scenes may be used from different threads.
+ *   - Device memory comes from the allocator set with sph_set_allocator (default cudaMalloc).
+ */
+#ifndef SPH_B300_H
+#define SPH_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPH_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define SPH_API __attribute__((visibility("default")))
+#else
+#define SPH_API
+#endif
+
+/* status codes */
+#define SPH_OK 0
+#define SPH_EINVAL 1      /* bad argument or unsupported combination */
+#define SPH_ENOMEM 2      /* device allocation failed */
+#define SPH_ECUDA 3       /* a CUDA runtime call failed */
+#define SPH_EUNSTABLE 4   /* non-finite state or density out of [0.5, 2] rho0 */
+#define SPH_ETIMEOUT 5    /* a bounded wait ran out */
+#define SPH_EBUSY 6       /* resource temporarily unavailable (admission) */
+#define SPH_EINTERNAL 7   /* internal consistency check failed (e.g. a cell overflow) */
+
+#define SPH_KERNEL_WENDLAND4 0   /* Wendland C4, 2D and 3D (App. A.1) */
+#define SPH_KERNEL_WENDLAND2 1   /* Wendland C2, 2D and 3D */
+#define SPH_DENSITY_CONTINUITY 0 /* integrate drho/dt with delta diffusion (Sec. 2.3) */
+#define SPH_DENSITY_SUMMATION 1  /* rho_i = sum_j m_j W_ij each step, no diffusion (Sec. 2.3) */
+
+/* Global parameters sigma of one scene (Sec. 2.2; App. C "global state dictionary").
+ * The support radius H is the kernel's cut-off (the paper stores the support and calls it h).
+ * Box: [box_lo, box_hi) per axis; periodic axes (bit k of periodic_mask) use the minimum
+ * image on absolute, unwrapped positions (Sec. 3.2); open axes clamp particles into the edge
+ * cells.  Cells have edge >= H + skin; a periodic axis needs at least 3 cells.
+ * Neighbour lists are rebuilt every step when skin == 0; with skin > 0 they are rebuilt every
+ * rebuild_interval steps (a Verlet list in the sense of App. B). */
+typedef struct sph_params {
+  int32_t dim;            /* 2 or 3 */
+  int32_t kernel;         /* SPH_KERNEL_* */
+  int32_t density_mode;   /* SPH_DENSITY_* */
+  int32_t periodic_mask;  /* bit k: axis k periodic */
+  double box_lo[3];
+  double box_hi[3];
+  float H;                /* support radius (> 0) */
+  float dt;               /* fixed time step (> 0) */
+  float rho0;             /* rest density */
+  float c0;               /* numerical speed of sound */
+  float gamma;            /* Tait exponent (7) */
+  float nu;               /* kinematic viscosity (>= 0) */
+  float delta;            /* delta-SPH diffusion coefficient (term delta h c0, h = H/2) */
+  float eps;              /* regulariser: denominators use |x_ij|^2 + eps h^2, h = H/2 */
+  float g[3];             /* body acceleration */
+  int32_t rebuild_interval; /* >= 1, used when skin > 0 */
+  float skin;             /* Verlet skin (absolute length, >= 0) */
+} sph_params;
+
+typedef struct sph_scene sph_scene;
+
+/* Allocator hooks: alloc(bytes, stream, ctx) returns a device pointer or NULL; free(ptr, bytes,
+ * stream, ctx).  Passing NULL restores cudaMalloc/cudaFree.  Applies to scenes created after
+ * the call.  The hooks must stay valid until every scene using them is destroyed. */
+typedef void* (*sph_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*sph_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+SPH_API int sph_set_allocator(sph_alloc_fn alloc_fn, sph_free_fn free_fn, void* ctx);
+
+SPH_API int sph_abi_version(void);
+SPH_API const char* sph_last_error(void);
+
+/* Create a scene from an initial state u_0 = (x, v, rho) with per-particle masses.
+ * n_fluid fluid particles followed by n_wall fixed wall particles (walls keep v = 0; their
+ * pressure and density are extrapolated from the fluid every step).  Returns SPH_EINVAL for
+ * inconsistent parameters (dim, H <= 0, fewer than 3 cells on a periodic axis, ...). */
+SPH_API int sph_init(const sph_params* params, int n_fluid, int n_wall, const float* x, const float* v,
+             const float* rho, const float* mass, int ptr_is_device, void* cuda_stream, sph_scene** out);
+
+/* Advance the scene by n_steps steps of the scheme above (no tape kept).  Asynchronous with
+ * respect to the host; errors detected on the device surface at the next synchronising call. */
+SPH_API int sph_step(sph_scene* scene, int n_steps);
+
+/* Copy the current state out (original order).  Any pointer may be NULL to skip that field.
+ * Synchronises the scene's stream; returns SPH_EUNSTABLE if the state is not finite. */
+SPH_API int sph_get_state(const sph_scene* scene, float* x, float* v, float* rho, int ptr_is_device);
+
+/* Evaluate the right-hand side at the current state without advancing it: a (n_fluid*dim)
+ * and drho/dt (n_fluid), plus the density used (n_fluid; differs from the state only in
+ * summation mode).  Original order, fluid particles only.  Any output may be NULL. */
+SPH_API int sph_rates(sph_scene* scene, float* a, float* drho, float* rho_used, int ptr_is_device);
+
+/* Forward rollout of n_steps that keeps what the adjoint needs: the state every ckpt_every
+ * steps (gradient checkpointing, Sec. 3.3).  Replaces any previous tape of this scene. */
+SPH_API int sph_rollout(sph_scene* scene, int n_steps, int ckpt_every);
+
+/* Reverse pass of the last sph_rollout (vector-Jacobian product, Sec. 2.2): given the adjoints
+ * of the final state (xbar_T, vbar_T, rhobar_T; NULL = zero) return those of the initial state
+ * (xbar_0, vbar_0, rhobar_0; NULL = skip) and of the viscosity (nubar, host double; may be NULL).
+ * Segments between checkpoints are recomputed forward and replayed backwards.  Continuity
+ * mode without wall particles only (SPH_EINVAL otherwise, or without a preceding rollout).
+ * The scene's state is left at the end of the rollout. */
+SPH_API int sph_adjoint(sph_scene* scene, const float* xbar_T, const float* vbar_T, const float* rhobar_T,
+                float* xbar_0, float* vbar_0, float* rhobar_0, double* nubar, int ptr_is_device);
+
+/* Scene geometry: cells per axis (3 ints), total particles. */
+SPH_API int sph_scene_info(const sph_scene* scene, int32_t* ncell3, int32_t* n_particles);
+
+/* Cell structure of the current state (host outputs): CSR offsets cell_start[n_cells + 1] over
+ * the linear cell index ((cz * ny + cy) * nx + cx), and sorted_ids[n] = original particle index
+ * in sorted order (stable by cell; ties keep the previous storage order, which is ascending
+ * original index for a freshly initialised scene).  Builds the cells if needed. */
+SPH_API int sph_debug_cells(sph_scene* scene, int64_t* cell_start, int32_t* sorted_ids);
+
+/* All ordered neighbour pairs (i, j), i != j, |mimg(x_i - x_j)|^2 < H^2 with the squared
+ * distance evaluated in FP64 from the float32 positions, as original indices (host outputs,
+ * unordered).  *n_pairs receives the total; at most cap pairs are written. */
+SPH_API int sph_debug_pairs(sph_scene* scene, int64_t* n_pairs, int32_t* pi, int32_t* pj, int64_t cap);
+
+/* Per-kernel device timing.  When enabled, the scene records CUDA events around its launches
+ * on its stream; sph_timing returns the accumulated milliseconds and launch count of one
+ * kernel class (0 = fused sweep, 1 = rebuild (keys+sort+ranges+permute), 2 = walls,
+ * 3 = density, 4 = adjoint sweep) and resets it.  Synchronises the stream. */
+SPH_API int sph_profile(sph_scene* scene, int enable);
+SPH_API int sph_timing(sph_scene* scene, int kernel_class, double* ms, int64_t* launches);
+
+/* Counters of the last sph_step/sph_rollout/sph_adjoint call: in-radius ordered pairs per step
+ * (fluid i), kernel launches issued. */
+SPH_API int sph_counters(sph_scene* scene, int64_t* pairs_per_step, int64_t* launches);
+
+SPH_API void sph_destroy(sph_scene* scene);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_B300_H */

@@ -20,7 +20,7 @@
 //   reverse pass             vector-Jacobian product of one step, chained backwards          (Sec. 2.2)
 //
 // Readings of the paper where it is silent or garbled (continuity sign, viscosity prefactor
-// 2(d+2) nu, Molteni-Colagrossi diffusion term, support h == H, wall treatment) are listed
+// 2(d+2) nu, Molteni-Colagrossi diffusion term, smoothing length h = H/2, wall treatment) are listed
 // with the rest of the design notes; the code below implements exactly those readings.
 //
 // Parity pins: every function here is pinned by tests (kernel normalisation and the paper's
@@ -203,7 +203,7 @@ int cell_coord(const OrcParams& P, const CellGrid& G, int k, double x) {
     xw = x - L * std::floor((x - lo) / L);
   }
   double c = std::floor((xw - lo) / G.cs[k]);
-  if (c < 0) c = 0;
+  if (!(c >= 0)) c = 0;  // also catches NaN
   if (c > G.n[k] - 1) c = G.n[k] - 1;
   return (int)c;
 }
@@ -367,11 +367,13 @@ void wall_extrapolation(const OrcParams& P, State<T>& S, const Pairs& pr, std::v
 }
 
 // Rates of the fluid particles (Sec. 2.3, delta-SPH):
-//   drho_i/dt = -rho_i sum_j V_j (v_j - v_i) . gradW_ij + delta H c0 sum_j V_j psi_ij . gradW_ij
-//   psi_ij    = 2 (rho_j - rho_i) (x_j - x_i) / (|x_ij|^2 + eps H^2)
+//   drho_i/dt = -rho_i sum_j V_j (v_j - v_i) . gradW_ij + delta h c0 sum_j V_j psi_ij . gradW_ij
+//   psi_ij    = 2 (rho_j - rho_i) (x_j - x_i) / (|x_ij|^2 + eps h^2)
 //   dv_i/dt   = -(1/rho_i) sum_j V_j (p_i + p_j) gradW_ij
 //               + 2(d+2) nu (rho0/rho_i) sum_j V_j pi_ij gradW_ij + g
-//   pi_ij     = (v_i - v_j) . (x_i - x_j) / (|x_ij|^2 + eps H^2),   V_j = m_j / rho_j
+//   pi_ij     = (v_i - v_j) . (x_i - x_j) / (|x_ij|^2 + eps h^2),   V_j = m_j / rho_j
+// h = H/2 is the smoothing length of the delta-SPH literature the scheme is cited from (the
+// paper's "common choice H/h = 2, h = 2 dx", App. A.1); H is the kernel support.
 // With a summation density the diffusion term is off (rho is not integrated).
 template <class T>
 void rates(const OrcParams& P, const State<T>& S, const Pairs& pr, const std::vector<double>& p_wall,
@@ -380,10 +382,10 @@ void rates(const OrcParams& P, const State<T>& S, const Pairs& pr, const std::ve
   const int M = who ? (int)who->size() : S.nf;
   a.assign((size_t)M * d, T(0.0));
   drho.assign(M, T(0.0));
-  const double eH2 = P.eps * P.H * P.H;
+  const double eH2 = P.eps * (0.5 * P.H) * (0.5 * P.H);  // h = H/2
   const double delta = P.density_mode == 0 ? P.delta : 0.0;
   const T Cv = T(2.0 * (d + 2) * P.rho0) * S.nu[0];
-  const T Cd = T(delta * P.H * P.c0);
+  const T Cd = T(delta * (0.5 * P.H) * P.c0);  // delta h c0, h = H/2
   auto pres = [&](int j) -> T { return j < S.nf ? tait<T>(P, S.rho[j]) : T(p_wall[j - S.nf]); };
 #pragma omp parallel for schedule(static)
   for (int aidx = 0; aidx < M; ++aidx) {
@@ -465,10 +467,10 @@ void step_reverse(const OrcParams& P, const State<double>& S, std::vector<double
                   std::vector<double>& rb, double& nub) {
   const int d = S.d, N = S.N();
   Pairs pr = pairs_of(P, S);
-  const double dt = P.dt, eH2 = P.eps * P.H * P.H;
+  const double dt = P.dt, eH2 = P.eps * (0.5 * P.H) * (0.5 * P.H);  // h = H/2
   const double Cv = 2.0 * (d + 2) * P.rho0 * S.nu[0];
   const double dCv_dnu = 2.0 * (d + 2) * P.rho0;
-  const double Cdel = P.delta * P.H * P.c0;
+  const double Cdel = P.delta * (0.5 * P.H) * P.c0;  // delta h c0, h = H/2
   // seeds: x' = x + dt v', v' = v + dt a, rho' = rho + dt drho
   std::vector<double> vt((size_t)N * d), abar((size_t)N * d), bbar(N);
   for (int i = 0; i < N; ++i) {
@@ -739,12 +741,31 @@ int orc_rates(const OrcParams* P, int nf, int nw, const float* x, const float* v
               int n_who, const int32_t* who, double* a, double* drho, double* rho_used, double* p_used,
               double* p_wall_out) {
   State<double> S = load_state<double>(*P, nf, nw, x, v, rho, m);
-  Pairs pr = pairs_of(*P, S);
-  if (P->density_mode == 1) density_summation(*P, S, pr);
   std::vector<double> p_wall;
-  wall_extrapolation(*P, S, pr, p_wall);
   std::vector<double> av, dr;
   std::vector<int> w;
+  if (who && P->density_mode == 0 && nw == 0) {
+    // sampled evaluation: only the requested particles' neighbour lists are needed
+    w.assign(who, who + n_who);
+    for (int i : w)
+      if (i < 0 || i >= nf) return -1;
+    std::vector<double> xr(S.x.begin(), S.x.end());
+    Pairs sub;
+    neighbour_lists(*P, nf, xr.data(), w, sub.off, sub.nb);
+    rates(*P, S, sub, p_wall, av, dr, &w);
+    const int d = P->dim;
+    for (size_t aidx = 0; aidx < w.size(); ++aidx) {
+      int i = w[aidx];
+      for (int k = 0; k < d; ++k) a[aidx * d + k] = av[aidx * d + k];
+      drho[aidx] = dr[aidx];
+      if (rho_used) rho_used[aidx] = S.rho[i];
+      if (p_used) p_used[aidx] = tait<double>(*P, S.rho[i]);
+    }
+    return 0;
+  }
+  Pairs pr = pairs_of(*P, S);
+  if (P->density_mode == 1) density_summation(*P, S, pr);
+  wall_extrapolation(*P, S, pr, p_wall);
   if (who) {
     w.assign(who, who + n_who);
     for (int i : w)

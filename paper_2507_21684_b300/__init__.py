@@ -1,0 +1,325 @@
+"""Python binding of libsph_b300.so, the B300 CUDA library for the weakly-compressible SPH step
+of diffSPH (Winchenbach & Thuerey, arXiv 2507.21684) and its adjoint.
+
+This module only marshals arguments to the C ABI declared in ``include/sph.h``: every step of
+the method runs in the library's CUDA kernels.  There is no CPU fallback; if the library or a
+GPU is missing, the calls raise.
+
+Inputs may be numpy arrays (host) or CUDA torch tensors (device).  Device memory of a scene is
+taken from PyTorch's caching allocator once torch is imported.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from pathlib import Path
+
+import numpy as np
+
+__all__ = ["lib", "Params", "Scene", "SphError", "rollout_fn", "library_path"]
+
+_HERE = Path(__file__).resolve().parent
+_LIBPATH = _HERE / "libsph_b300.so"
+_lib = None
+
+SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EUNSTABLE, SPH_ETIMEOUT, SPH_EBUSY, SPH_EINTERNAL = range(8)
+_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT", 6: "EBUSY", 7: "EINTERNAL"}
+
+# kernel classes of sph_timing
+TIMING_SWEEP, TIMING_REBUILD, TIMING_WALLS, TIMING_DENSITY, TIMING_ADJOINT = range(5)
+
+
+class SphError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"SPH_{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("kernel", C.c_int32), ("density_mode", C.c_int32), ("periodic_mask", C.c_int32),
+        ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
+        ("H", C.c_float), ("dt", C.c_float), ("rho0", C.c_float), ("c0", C.c_float), ("gamma", C.c_float),
+        ("nu", C.c_float), ("delta", C.c_float), ("eps", C.c_float), ("g", C.c_float * 3),
+        ("rebuild_interval", C.c_int32), ("skin", C.c_float),
+    ]
+
+    @classmethod
+    def from_dict(cls, p: dict) -> "Params":
+        o = cls()
+        for k in ("dim", "kernel", "density_mode", "periodic_mask", "rebuild_interval"):
+            setattr(o, k, int(p[k]))
+        for k in ("H", "dt", "rho0", "c0", "gamma", "nu", "delta", "eps", "skin"):
+            setattr(o, k, float(p[k]))
+        for k in range(3):
+            o.box_lo[k] = float(p["box_lo"][k])
+            o.box_hi[k] = float(p["box_hi"][k])
+            o.g[k] = float(p["g"][k])
+        return o
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_hooks = None
+
+
+def library_path() -> Path:
+    return _LIBPATH
+
+
+def lib() -> C.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _LIBPATH.exists():
+        raise ImportError(f"{_LIBPATH} is missing: run paper_2507_21684_b300/build.py (nvcc, sm_103a)")
+    L = C.CDLL(str(_LIBPATH))
+    P = C.POINTER
+    vp = C.c_void_p
+    L.sph_abi_version.restype = C.c_int
+    L.sph_last_error.restype = C.c_char_p
+    L.sph_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, vp]
+    L.sph_init.argtypes = [P(Params), C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, vp, P(vp)]
+    L.sph_step.argtypes = [vp, C.c_int]
+    L.sph_get_state.argtypes = [vp, vp, vp, vp, C.c_int]
+    L.sph_rates.argtypes = [vp, vp, vp, vp, C.c_int]
+    L.sph_rollout.argtypes = [vp, C.c_int, C.c_int]
+    L.sph_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp, P(C.c_double), C.c_int]
+    L.sph_scene_info.argtypes = [vp, P(C.c_int32), P(C.c_int32)]
+    L.sph_debug_cells.argtypes = [vp, vp, vp]
+    L.sph_debug_pairs.argtypes = [vp, P(C.c_int64), vp, vp, C.c_int64]
+    L.sph_profile.argtypes = [vp, C.c_int]
+    L.sph_timing.argtypes = [vp, C.c_int, P(C.c_double), P(C.c_int64)]
+    L.sph_counters.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
+    L.sph_destroy.argtypes = [vp]
+    L.sph_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != SPH_OK:
+        raise SphError(rc, lib().sph_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def use_torch_allocator():
+    """Back the library's device allocations with PyTorch's caching allocator."""
+    global _hooks
+    if _hooks is not None:
+        return
+    torch = _torch()
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    _hooks = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    _check(lib().sph_set_allocator(_hooks[0], _hooks[1], None))
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _arg(a, dtype=np.float32):
+    """(pointer, keepalive, is_device) for a numpy array or a CUDA tensor."""
+    if a is None:
+        return None, None, None
+    if _is_torch(a):
+        torch = _torch()
+        t = a.detach()
+        if t.dtype != torch.float32:
+            t = t.float()
+        t = t.contiguous()
+        return t.data_ptr(), t, bool(t.is_cuda)
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, arr, False
+
+
+class Scene:
+    """One SPH scene in HBM: initial state in, steps, rollouts and adjoints through the C ABI."""
+
+    def __init__(self, params: dict, n_fluid: int, n_wall: int, x, v, rho, mass, stream=None):
+        L = lib()
+        self.params = dict(params)
+        self.dim = int(params["dim"])
+        self.n_fluid, self.n_wall = int(n_fluid), int(n_wall)
+        self.n = self.n_fluid + self.n_wall
+        args = [_arg(a) for a in (x, v, rho, mass)]
+        dev = {d for _, _, d in args if d is not None}
+        if len(dev) != 1:
+            raise ValueError("inputs must be all host arrays or all CUDA tensors")
+        self.device_inputs = dev.pop()
+        if self.device_inputs:
+            use_torch_allocator()
+        if stream is None and self.device_inputs:
+            stream = _torch().cuda.current_stream().cuda_stream
+        self.stream = int(stream or 0)
+        if self.stream and not self.device_inputs:
+            pass
+        self._p = Params.from_dict(params)
+        h = C.c_void_p()
+        _check(L.sph_init(C.byref(self._p), self.n_fluid, self.n_wall, args[0][0], args[1][0], args[2][0],
+                          args[3][0], int(self.device_inputs), C.c_void_p(self.stream), C.byref(h)))
+        self._h = h
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- forward
+    def step(self, n: int = 1):
+        _check(lib().sph_step(self._h, int(n)))
+
+    def get_state(self, device: bool = False):
+        d, n = self.dim, self.n
+        if device:
+            torch = _torch()
+            x = torch.empty((n, d), device="cuda", dtype=torch.float32)
+            v = torch.empty((n, d), device="cuda", dtype=torch.float32)
+            r = torch.empty((n,), device="cuda", dtype=torch.float32)
+            _check(lib().sph_get_state(self._h, x.data_ptr(), v.data_ptr(), r.data_ptr(), 1))
+            return x, v, r
+        x = np.empty((n, d), np.float32)
+        v = np.empty((n, d), np.float32)
+        r = np.empty((n,), np.float32)
+        _check(lib().sph_get_state(self._h, x.ctypes.data, v.ctypes.data, r.ctypes.data, 0))
+        return x, v, r
+
+    def rates(self):
+        nf, d = self.n_fluid, self.dim
+        a = np.empty((nf, d), np.float32)
+        dr = np.empty((nf,), np.float32)
+        ru = np.empty((nf,), np.float32)
+        _check(lib().sph_rates(self._h, a.ctypes.data, dr.ctypes.data, ru.ctypes.data, 0))
+        return dict(a=a, drho=dr, rho=ru)
+
+    # -- differentiation
+    def rollout(self, n_steps: int, ckpt_every: int = 20):
+        _check(lib().sph_rollout(self._h, int(n_steps), int(ckpt_every)))
+
+    def adjoint(self, xb=None, vb=None, rb=None, device: bool = False):
+        nf, d = self.n_fluid, self.dim
+        ins = [_arg(a) for a in (xb, vb, rb)]
+        flags = {f for _, _, f in ins if f is not None}
+        if len(flags) > 1:
+            raise ValueError("adjoint seeds must be all host or all device")
+        is_dev = bool(flags.pop()) if flags else bool(device)
+        nub = C.c_double()
+        if is_dev:
+            torch = _torch()
+            ox = torch.empty((nf, d), device="cuda", dtype=torch.float32)
+            ov = torch.empty((nf, d), device="cuda", dtype=torch.float32)
+            orr = torch.empty((nf,), device="cuda", dtype=torch.float32)
+            ptrs = [ox.data_ptr(), ov.data_ptr(), orr.data_ptr()]
+        else:
+            ox = np.empty((nf, d), np.float32)
+            ov = np.empty((nf, d), np.float32)
+            orr = np.empty((nf,), np.float32)
+            ptrs = [ox.ctypes.data, ov.ctypes.data, orr.ctypes.data]
+        _check(lib().sph_adjoint(self._h, ins[0][0], ins[1][0], ins[2][0], *ptrs, C.byref(nub), int(is_dev)))
+        return ox, ov, orr, nub.value
+
+    # -- inspection
+    def info(self):
+        n3 = (C.c_int32 * 3)()
+        n = C.c_int32()
+        _check(lib().sph_scene_info(self._h, n3, C.byref(n)))
+        return list(n3), n.value
+
+    def debug_cells(self):
+        n3, n = self.info()
+        nc = n3[0] * n3[1] * n3[2]
+        start = np.empty(nc + 1, np.int64)
+        ids = np.empty(n, np.int32)
+        _check(lib().sph_debug_cells(self._h, start.ctypes.data, ids.ctypes.data))
+        return start, ids
+
+    def debug_pairs(self) -> np.ndarray:
+        cnt = C.c_int64()
+        _check(lib().sph_debug_pairs(self._h, C.byref(cnt), None, None, 0))
+        n = cnt.value
+        pi = np.empty(max(n, 1), np.int32)
+        pj = np.empty(max(n, 1), np.int32)
+        _check(lib().sph_debug_pairs(self._h, C.byref(cnt), pi.ctypes.data, pj.ctypes.data, n))
+        p = np.stack([pi[:n], pj[:n]], 1)
+        order = np.lexsort((p[:, 1], p[:, 0]))
+        return p[order]
+
+    def profile(self, enable: bool = True):
+        _check(lib().sph_profile(self._h, int(enable)))
+
+    def timing(self, cls: int = TIMING_SWEEP):
+        ms = C.c_double()
+        n = C.c_int64()
+        _check(lib().sph_timing(self._h, int(cls), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def counters(self):
+        pairs = C.c_int64()
+        launches = C.c_int64()
+        _check(lib().sph_counters(self._h, C.byref(pairs), C.byref(launches)))
+        return pairs.value, launches.value
+
+
+def scene_from(spec: dict, stream=None, device: bool = False) -> Scene:
+    """Scene from a generator dict (sph_inputs): host arrays, or CUDA tensors if device."""
+    arrs = [spec[k] for k in ("x", "v", "rho", "mass")]
+    if device:
+        torch = _torch()
+        arrs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+    return Scene(spec["params"], spec["n_fluid"], spec["n_wall"], *arrs, stream=stream)
+
+
+def rollout_fn():
+    """torch.autograd.Function: (x0, v0, rho0, nu) -> (x_T, v_T, rho_T) through sph_rollout, with
+    the backward pass through sph_adjoint (checkpoint every `ckpt_every` steps)."""
+    torch = _torch()
+
+    class SphRollout(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x0, v0, rho0, nu, mass, params, n_steps, ckpt_every):
+            p = dict(params)
+            p["nu"] = float(nu.detach().cpu().item()) if torch.is_tensor(nu) else float(nu)
+            sc = Scene(p, x0.shape[0], 0, x0, v0, rho0, mass)
+            sc.rollout(int(n_steps), int(ckpt_every))
+            xT, vT, rT = sc.get_state(device=True)
+            ctx.scene = sc
+            return xT, vT, rT
+
+        @staticmethod
+        def backward(ctx, gx, gv, gr):
+            sc = ctx.scene
+            z = lambda g, shape: g.contiguous() if g is not None else torch.zeros(shape, device="cuda")
+            xb, vb, rb, nub = sc.adjoint(z(gx, (sc.n, sc.dim)), z(gv, (sc.n, sc.dim)), z(gr, (sc.n,)))
+            sc.close()
+            ctx.scene = None
+            nu_grad = torch.tensor(nub, dtype=torch.float32, device="cuda")
+            return xb, vb, rb, nu_grad, None, None, None, None
+
+    return SphRollout

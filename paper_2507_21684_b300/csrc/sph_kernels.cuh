@@ -1,0 +1,70 @@
+// Launch interface of the WCSPH kernels (host side of sph_kernels.cu).
+#pragma once
+#include "sph_device.cuh"
+
+namespace sph {
+
+// Arguments shared by every neighbour pass.
+struct TravArgs {
+  const DevSeg* segs;
+  int N;
+  Arrays a;                  // current (sorted) particle arrays
+  const uint32_t* keys;      // sorted global cell key per particle
+  const int* cell_off;       // CSR offsets over global cells
+  int* status;               // device error word (bit 0: unstable state)
+  unsigned long long* pair_count;  // optional: in-radius pairs of fluid particles
+};
+
+// Outputs of the rate evaluation (original order, fluid only).
+struct RateOut {
+  float* a;
+  float* drho;
+  float* rho;
+  const int* orig_base;      // first original row of each scene in the outputs
+};
+
+cudaError_t configure_kernels();
+int sort_scratch_words(int N);
+size_t trav_smem();
+
+template <int D>
+void launch_keys(const DevSeg* segs, int N, const Arrays& a, uint32_t* keys, uint32_t* vals, cudaStream_t st);
+void launch_sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, int N, int shift,
+                      uint32_t* hist, uint32_t* sums, cudaStream_t st);
+void launch_cell_offsets(const uint32_t* keys, int N, int C, int* off, cudaStream_t st);
+template <int D>
+void launch_permute(const DevSeg* segs, int N, const uint32_t* perm, const Arrays& in, const Arrays& out,
+                    cudaStream_t st);
+template <int D, int KERN>
+void launch_walls(const TravArgs& t, cudaStream_t st);
+template <int D, int KERN>
+void launch_density(const TravArgs& t, cudaStream_t st);
+template <int D, int KERN>
+void launch_sweep(const TravArgs& t, const Arrays& out, cudaStream_t st);
+template <int D, int KERN>
+void launch_rates(const TravArgs& t, const RateOut& ro, cudaStream_t st);
+template <int D>
+void launch_pairs(const TravArgs& t, int32_t* pi, int32_t* pj, unsigned long long* count, long long cap,
+                  cudaStream_t st);
+template <int D>
+void launch_upload(const DevSeg* segs, int seg, int n, int nf, int p0, const float* x, const float* v,
+                   const float* rho, const float* mass, const Arrays& a, cudaStream_t st);
+template <int D>
+void launch_download(int N, const Arrays& a, const int* orig_base, float* x, float* v, float* rho, cudaStream_t st);
+template <int D>
+void launch_adj_seed(const DevSeg* segs, int N, const Arrays& fw, const float4* XB, const float4* VB, float4* S,
+                     float* Pp, cudaStream_t st);
+template <int D, int KERN>
+int launch_adj_sweep(const TravArgs& t, const float4* S, const float* Pp, const float4* XBin, const float4* VBin,
+                     float4* XBout, float4* VBout, double* nu_partial, cudaStream_t st);
+void launch_adj_unpermute(int N, const uint32_t* perm, const float4* XBin, const float4* VBin, float4* XBout,
+                          float4* VBout, cudaStream_t st);
+void launch_sum_partials(const double* part, int n, double* acc, cudaStream_t st);
+template <int D>
+void launch_adj_load(int N, const uint2* meta, const int* orig_base, const float* xb, const float* vb,
+                     const float* rb, float4* XB, float4* VB, cudaStream_t st);
+template <int D>
+void launch_adj_store(int N, const uint2* meta, const int* orig_base, const float4* XB, const float4* VB, float* xb,
+                      float* vb, float* rb, cudaStream_t st);
+
+}  // namespace sph

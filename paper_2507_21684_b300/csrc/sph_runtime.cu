@@ -1,0 +1,1091 @@
+// Host runtime of the B300 WCSPH library: scene state in HBM, the per-step launch sequence,
+// CUDA-graph replay of step chunks, gradient checkpointing and the reverse pass, and the
+// extern "C" entry points declared in include/sph.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sph.h"
+#include "sph_kernels.cuh"
+#include "sph_runtime.h"
+
+namespace sph {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+static void set_err(const std::string& s) { g_err = s; }
+const char* last_error() { return g_err.c_str(); }
+
+struct Fail {
+  int code;
+};
+#define CK(call)                                                                                     \
+  do {                                                                                               \
+    cudaError_t _e = (call);                                                                         \
+    if (_e != cudaSuccess) {                                                                         \
+      sph::set_err(std::string(#call) + ": " + cudaGetErrorString(_e));                                   \
+      throw sph::Fail{SPH_ECUDA};                                                                         \
+    }                                                                                                \
+  } while (0)
+#define CKL()                                                                                        \
+  do {                                                                                               \
+    cudaError_t _e = cudaGetLastError();                                                             \
+    if (_e != cudaSuccess) {                                                                         \
+      sph::set_err(std::string("kernel launch: ") + cudaGetErrorString(_e));                              \
+      throw sph::Fail{SPH_ECUDA};                                                                         \
+    }                                                                                                \
+  } while (0)
+
+static void einval(const std::string& s) {
+  set_err(s);
+  throw Fail{SPH_EINVAL};
+}
+
+// ---------------------------------------------------------------- allocator
+static sph_alloc_fn g_alloc = nullptr;
+static sph_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+static std::mutex g_alloc_mu;
+
+void set_allocator(sph_alloc_fn a, sph_free_fn f, void* ctx) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = a;
+  g_free = f;
+  g_alloc_ctx = ctx;
+}
+
+DeviceMem::~DeviceMem() { release(); }
+void* DeviceMem::get(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (afn) {
+    p = afn(bytes, (void*)stream, actx);
+    if (!p) {
+      set_err("allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
+      throw Fail{SPH_ENOMEM};
+    }
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_err(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+      throw Fail{SPH_ENOMEM};
+    }
+  }
+  blocks.push_back({p, bytes});
+  total += bytes;
+  return p;
+}
+void DeviceMem::release() {
+  for (auto& b : blocks) {
+    if (ffn)
+      ffn(b.first, b.second, (void*)stream, fctx);
+    else
+      cudaFree(b.first);
+  }
+  blocks.clear();
+  total = 0;
+}
+
+// ---------------------------------------------------------------- kernel constants
+static double kernel_cd(int dim, int kern) {
+  const double pi = 3.14159265358979323846;
+  if (kern == 0) return dim == 2 ? 9.0 / pi : 495.0 / (32.0 * pi);
+  return dim == 2 ? 7.0 / pi : 21.0 / (2.0 * pi);
+}
+
+// Per-scene device parameters from the ABI parameters.
+DevSeg make_seg(const sph_params& p, int n_fluid, int cell_base, int p0, int p1, double max_abs_x) {
+  DevSeg s;
+  std::memset(&s, 0, sizeof(s));
+  if (p.dim != 2 && p.dim != 3) einval("dim must be 2 or 3");
+  if (p.kernel != 0 && p.kernel != 1) einval("kernel must be SPH_KERNEL_WENDLAND4 or SPH_KERNEL_WENDLAND2");
+  if (p.density_mode != 0 && p.density_mode != 1) einval("density_mode must be 0 or 1");
+  if (!(p.H > 0.f) || !(p.dt > 0.f) || !(p.rho0 > 0.f) || !(p.c0 > 0.f) || !(p.gamma > 0.f))
+    einval("H, dt, rho0, c0 and gamma must be positive");
+  if (!(p.nu >= 0.f) || !(p.eps > 0.f) || !(p.skin >= 0.f) || p.rebuild_interval < 1)
+    einval("nu >= 0, eps > 0, skin >= 0 and rebuild_interval >= 1 are required");
+  s.dim = p.dim;
+  s.kernel = p.kernel;
+  s.density_mode = p.density_mode;
+  s.periodic_mask = p.periodic_mask & ((1 << p.dim) - 1);
+  double cmin = (double)p.H + (double)p.skin;
+  long long ncell = 1;
+  for (int k = 0; k < 3; ++k) {
+    if (k < p.dim) {
+      double L = p.box_hi[k] - p.box_lo[k];
+      if (!(L > 0.0)) einval("box_hi must exceed box_lo on every axis");
+      int n = (int)std::floor(L / cmin);
+      if (n < 1) n = 1;
+      if (((s.periodic_mask >> k) & 1) && n < 3) einval("a periodic axis needs at least 3 cells of edge >= H + skin");
+      s.n[k] = n;
+      s.L_d[k] = L;
+      s.lo_d[k] = p.box_lo[k];
+      s.cs_d[k] = L / n;
+      s.L[k] = (float)L;
+      s.lo[k] = (float)p.box_lo[k];
+      s.invL[k] = (float)(1.0 / L);
+    } else {
+      s.n[k] = 1;
+      s.L_d[k] = 1.0;
+      s.cs_d[k] = 1.0;
+      s.L[k] = 1.f;
+      s.invL[k] = 1.f;
+    }
+    ncell *= s.n[k];
+  }
+  if (ncell > (1LL << 30)) einval("too many cells");
+  if ((long long)s.n[1] * s.n[2] >= (1LL << 20)) einval("too many cell lines (ny * nz must be < 2^20)");
+  s.cell_base = cell_base;
+  s.p0 = p0;
+  s.p1 = p1;
+  s.nf = n_fluid;
+  const int d = p.dim;
+  const double H = p.H;
+  s.H = p.H;
+  s.H2 = (float)(H * H);
+  s.H2_d = H * H;
+  s.invH = (float)(1.0 / H);
+  s.dt = p.dt;
+  s.rho0 = p.rho0;
+  s.c0 = p.c0;
+  s.gamma = p.gamma;
+  s.B = (float)((double)p.rho0 * p.c0 * p.c0 / p.gamma);
+  s.nu = p.nu;
+  s.dCv_dnu = (float)(2.0 * (d + 2) * p.rho0);
+  s.Cv = (float)(2.0 * (d + 2) * p.rho0 * (double)p.nu);
+  // h = H/2: the smoothing length of the delta-SPH diffusion and of the regulariser
+  s.Cdel = p.density_mode == 0 ? (float)((double)p.delta * (0.5 * H) * p.c0) : 0.f;
+  s.eH2 = (float)((double)p.eps * (0.5 * H) * (0.5 * H));
+  double Cd = kernel_cd(d, p.kernel);
+  s.Kw = (float)(Cd / std::pow(H, d));
+  s.Kg = (float)((p.kernel == 0 ? -56.0 / 3.0 : -20.0) * Cd / std::pow(H, d + 2));
+  s.Kh = (float)((p.kernel == 0 ? 560.0 : 60.0) * Cd / std::pow(H, d + 4));
+  for (int k = 0; k < 3; ++k) s.g[k] = k < d ? p.g[k] : 0.f;
+  // FP32 error of r^2 on folded positions is below ~8 ulp(|x|max) * |r|: guard band in r^2
+  double ex = 8.0 * std::ldexp(std::max(max_abs_x, 1.0), -23);
+  double band = std::max(1e-5, 4.0 * ex / H);
+  s.band_lo = (float)(H * H * (1.0 - band));
+  s.band_hi = (float)(H * H * (1.0 + band));
+  return s;
+}
+
+static int key_bits(long long C) {
+  int b = 0;
+  while ((1LL << b) < C) ++b;
+  return b;
+}
+
+// ---------------------------------------------------------------- scene
+// The caller's stream orders the scene's work.  Stream capture is not allowed on the legacy
+// default stream, so a scene bound to stream 0 runs on a private non-blocking stream and
+// joins the legacy stream with events at every entry point (enter) and before returning
+// device outputs (leave).
+void Scene::bind_stream(cudaStream_t user) {
+  user_st = user;
+  if (user == nullptr) {
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    own_stream = true;
+    CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+  } else {
+    st = user;
+  }
+  mem.stream = st;
+}
+void Scene::enter() {
+  if (!own_stream) return;
+  CK(cudaEventRecord(ev_in, nullptr));
+  CK(cudaStreamWaitEvent(st, ev_in, 0));
+}
+void Scene::leave() {
+  if (!own_stream) return;
+  CK(cudaEventRecord(ev_out, st));
+  CK(cudaStreamWaitEvent(nullptr, ev_out, 0));
+}
+
+Scene::~Scene() {
+  if (st) cudaStreamSynchronize(st);
+  for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& e : prof_events) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  mem.release();
+  if (own_stream) {
+    cudaEventDestroy(ev_in);
+    cudaEventDestroy(ev_out);
+    cudaStreamDestroy(st);
+  }
+}
+
+void Scene::alloc_arrays(Arrays& a) {
+  a.A = (float4*)mem.get(sizeof(float4) * N);
+  a.B = (float4*)mem.get(sizeof(float4) * N);
+  a.X = (float4*)mem.get(sizeof(float4) * N);
+  a.O = (float4*)mem.get(sizeof(float4) * N);
+  a.meta = (uint2*)mem.get(sizeof(uint2) * N);
+  if (D == 3) {
+    a.C = (float2*)mem.get(sizeof(float2) * N);
+    a.XL = (float4*)mem.get(sizeof(float4) * N);
+  } else {
+    a.C = nullptr;
+    a.XL = nullptr;
+  }
+}
+
+void Scene::copy_arrays(const Arrays& dst, const Arrays& src) {
+  CK(cudaMemcpyAsync(dst.A, src.A, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(dst.B, src.B, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(dst.X, src.X, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(dst.O, src.O, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(dst.meta, src.meta, sizeof(uint2) * N, cudaMemcpyDeviceToDevice, st));
+  if (D == 3) {
+    CK(cudaMemcpyAsync(dst.C, src.C, sizeof(float2) * N, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(dst.XL, src.XL, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st));
+  }
+}
+
+void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector<int>& nfs,
+                          const std::vector<int>& nws, const std::vector<double>& max_abs_x) {
+  S = (int)prms.size();
+  D = prms[0].dim;
+  kern = prms[0].kernel;
+  summation = prms[0].density_mode == 1;
+  any_walls = false;
+  skin = prms[0].skin;
+  interval = prms[0].rebuild_interval;
+  N = 0;
+  C_tot = 0;
+  segs.clear();
+  orig_base.clear();
+  for (int s = 0; s < S; ++s) {
+    const sph_params& p = prms[s];
+    if (p.dim != D || p.kernel != kern || (p.density_mode == 1) != summation)
+      einval("all scenes of a batch must share dim, kernel and density mode");
+    int n = nfs[s] + nws[s];
+    if (nfs[s] < 0 || nws[s] < 0 || n < 1) einval("particle counts must be non-negative with at least one particle");
+    if ((long long)N + n >= (1LL << 30)) einval("too many particles");
+    DevSeg g = make_seg(p, nfs[s], C_tot, N, N + n, max_abs_x[s]);
+    long long c = (long long)g.n[0] * g.n[1] * g.n[2];
+    if ((long long)C_tot + c >= (1LL << 31)) einval("too many cells in total");
+    segs.push_back(g);
+    orig_base.push_back(N);
+    N += n;
+    C_tot += (int)c;
+    if (nws[s] > 0) any_walls = true;
+    if (p.skin != skin || p.rebuild_interval != interval)
+      einval("all scenes of a batch must share skin and rebuild_interval");
+  }
+  if (S >= 4096) einval("at most 4095 scenes per batch");
+  static bool configured = false;
+  if (!configured) {
+    CK(configure_kernels());
+    configured = true;
+  }
+  nf_total = 0;
+  for (int s = 0; s < S; ++s) nf_total += nfs[s];
+  bits = key_bits(C_tot);
+  passes = (bits + 7) / 8;
+  if (N > 16384 * 2048) einval("too many particles for the radix sort scratch (max 33554432)");
+}
+
+void Scene::alloc_all() {
+  dseg = (DevSeg*)mem.get(sizeof(DevSeg) * S);
+  d_orig_base = (int*)mem.get(sizeof(int) * S);
+  CK(cudaMemcpyAsync(dseg, segs.data(), sizeof(DevSeg) * S, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_orig_base, orig_base.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
+  alloc_arrays(buf[0]);
+  alloc_arrays(buf[1]);
+  cur = 0;
+  kA = (uint32_t*)mem.get(4 * (size_t)N);
+  vA = (uint32_t*)mem.get(4 * (size_t)N);
+  kB = (uint32_t*)mem.get(4 * (size_t)N);
+  vB = (uint32_t*)mem.get(4 * (size_t)N);
+  keys_sorted = kA;
+  perm = vA;
+  cell_off = (int*)mem.get(sizeof(int) * ((size_t)C_tot + 1));
+  scratch = (uint32_t*)mem.get(4 * (size_t)sort_scratch_words(N));
+  d_status = (int*)mem.get(sizeof(int) * 4);
+  d_pairs = (unsigned long long*)mem.get(sizeof(unsigned long long) * 2);
+  d_nubar = (double*)mem.get(sizeof(double) * 2);
+  CK(cudaMemsetAsync(d_status, 0, sizeof(int) * 4, st));
+  CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long) * 2, st));
+  cells_valid = false;
+  steps_since_build = 0;
+}
+
+void Scene::upload(int s, const float* x, const float* v, const float* rho, const float* mass, int is_dev) {
+  const DevSeg& g = segs[s];
+  int n = g.p1 - g.p0;
+  const float *dx = x, *dv = v, *dr = rho, *dm = mass;
+  float* staging = nullptr;
+  if (!is_dev) {
+    size_t nb = sizeof(float) * ((size_t)n * D * 2 + 2 * (size_t)n);
+    staging = (float*)mem_tmp(nb);
+    float* p = staging;
+    CK(cudaMemcpyAsync(p, x, sizeof(float) * n * D, cudaMemcpyHostToDevice, st));
+    dx = p;
+    p += (size_t)n * D;
+    if (v) CK(cudaMemcpyAsync(p, v, sizeof(float) * n * D, cudaMemcpyHostToDevice, st));
+    else CK(cudaMemsetAsync(p, 0, sizeof(float) * n * D, st));
+    dv = p;
+    p += (size_t)n * D;
+    CK(cudaMemcpyAsync(p, rho, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    dr = p;
+    p += n;
+    CK(cudaMemcpyAsync(p, mass, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    dm = p;
+  } else if (!v) {
+    float* p = (float*)mem_tmp(sizeof(float) * (size_t)n * D);
+    CK(cudaMemsetAsync(p, 0, sizeof(float) * n * D, st));
+    dv = p;
+  }
+  if (D == 2)
+    launch_upload<2>(dseg, s, n, g.nf, g.p0, dx, dv, dr, dm, buf[cur], st);
+  else
+    launch_upload<3>(dseg, s, n, g.nf, g.p0, dx, dv, dr, dm, buf[cur], st);
+  CKL();
+  cells_valid = false;
+}
+
+void* Scene::mem_tmp(size_t bytes) {
+  if (bytes > tmp_bytes) {
+    tmp = mem.get(bytes);
+    tmp_bytes = bytes;
+  }
+  return tmp;
+}
+
+TravArgs Scene::trav(const Arrays& a, const uint32_t* keys, const int* off) const {
+  TravArgs t;
+  t.segs = dseg;
+  t.N = N;
+  t.a = a;
+  t.keys = keys;
+  t.cell_off = off;
+  t.status = d_status;
+  t.pair_count = d_pairs;
+  return t;
+}
+
+void Scene::prof_begin(int cls) {
+  if (!profiling || capturing) return;
+  ProfEvent e;
+  e.cls = cls;
+  CK(cudaEventCreate(&e.a));
+  CK(cudaEventCreate(&e.b));
+  CK(cudaEventRecord(e.a, st));
+  prof_events.push_back(e);
+}
+void Scene::prof_end() {
+  if (!profiling || capturing) return;
+  CK(cudaEventRecord(prof_events.back().b, st));
+}
+
+// Rebuild: keys of the current order -> stable sort -> cell offsets -> permute `in` into
+// `out`.  Returns the sorted keys and the permutation (in kA/kB, vA/vB unless copied to the
+// given tape buffers); cell offsets go to off_out.
+std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& out, uint32_t* keys_out,
+                                               uint32_t* perm_out, int* off_out) {
+  prof_begin(1);
+  if (D == 2)
+    launch_keys<2>(dseg, N, in, kA, vA, st);
+  else
+    launch_keys<3>(dseg, N, in, kA, vA, st);
+  CKL();
+  uint32_t *ki = kA, *vi = vA, *ko = kB, *vo = vB;
+  uint32_t* hist = scratch;
+  uint32_t* sums = scratch + (sort_scratch_words(N) - 2048 - 64);
+  for (int p = 0; p < passes; ++p) {
+    launch_sort_pass(ki, vi, ko, vo, N, 8 * p, hist, sums, st);
+    CKL();
+    std::swap(ki, ko);
+    std::swap(vi, vo);
+  }
+  uint32_t* ks = ki;
+  uint32_t* pm = vi;
+  if (keys_out) {
+    CK(cudaMemcpyAsync(keys_out, ks, 4 * (size_t)N, cudaMemcpyDeviceToDevice, st));
+    ks = keys_out;
+  }
+  if (perm_out) {
+    CK(cudaMemcpyAsync(perm_out, pm, 4 * (size_t)N, cudaMemcpyDeviceToDevice, st));
+    pm = perm_out;
+  }
+  launch_cell_offsets(ks, N, C_tot, off_out, st);
+  CKL();
+  if (D == 2)
+    launch_permute<2>(dseg, N, pm, in, out, st);
+  else
+    launch_permute<3>(dseg, N, pm, in, out, st);
+  CKL();
+  prof_end();
+  return {ks, pm};
+}
+
+void Scene::passes_before_sweep(const TravArgs& t) {
+  if (any_walls) {
+    prof_begin(2);
+    if (D == 2) {
+      if (kern == 0) launch_walls<2, 0>(t, st); else launch_walls<2, 1>(t, st);
+    } else {
+      if (kern == 0) launch_walls<3, 0>(t, st); else launch_walls<3, 1>(t, st);
+    }
+    CKL();
+    prof_end();
+  }
+  if (summation) {
+    prof_begin(3);
+    if (D == 2) {
+      if (kern == 0) launch_density<2, 0>(t, st); else launch_density<2, 1>(t, st);
+    } else {
+      if (kern == 0) launch_density<3, 0>(t, st); else launch_density<3, 1>(t, st);
+    }
+    CKL();
+    prof_end();
+  }
+}
+
+void Scene::sweep(const TravArgs& t, const Arrays& out) {
+  prof_begin(0);
+  if (D == 2) {
+    if (kern == 0) launch_sweep<2, 0>(t, out, st); else launch_sweep<2, 1>(t, out, st);
+  } else {
+    if (kern == 0) launch_sweep<3, 0>(t, out, st); else launch_sweep<3, 1>(t, out, st);
+  }
+  CKL();
+  prof_end();
+  ++launches;
+}
+
+bool Scene::rebuild_due() const { return skin == 0.f || !cells_valid || steps_since_build >= interval; }
+
+// One forward step on the scene's own buffers.
+void Scene::step_once() {
+  if (rebuild_due()) {
+    auto kp = rebuild(buf[cur], buf[1 - cur], nullptr, nullptr, cell_off);
+    keys_sorted = kp.first;
+    perm = kp.second;
+    cur = 1 - cur;
+    cells_valid = true;
+    steps_since_build = 0;
+    launches += 3 + 4 * passes;
+  }
+  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  passes_before_sweep(t);
+  sweep(t, buf[1 - cur]);
+  cur = 1 - cur;
+  ++steps_since_build;
+}
+
+// Host-side replay of the schedule of step_once without launching (graph bookkeeping).
+void Scene::advance_schedule() {
+  if (rebuild_due()) {
+    cur = 1 - cur;
+    cells_valid = true;
+    steps_since_build = 0;
+  }
+  cur = 1 - cur;
+  ++steps_since_build;
+}
+
+void Scene::steps(int n) {
+  if (n <= 0) return;
+  CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st));
+  launches = 0;
+  const int chunk = graph_chunk;
+  if (!use_graphs || profiling || n < chunk) {
+    for (int k = 0; k < n; ++k) step_once();
+    last_steps = n;
+    return;
+  }
+  int done = 0;
+  long long per_chunk = 0;
+  while (n - done >= chunk) {
+    GraphKey key{chunk, cur, cells_valid ? std::min(steps_since_build, interval) : -1};
+    auto it = graphs.find(key);
+    // capture records the launches of `chunk` steps without running them; the host-side
+    // schedule (buffer parity, rebuild counter, sorted-key pointers) advances exactly as in
+    // an eager run, so it is simply kept after the capture.
+    long long l0 = launches;
+    if (it == graphs.end()) {
+      cudaGraph_t g;
+      capturing = true;
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      try {
+        for (int k = 0; k < chunk; ++k) step_once();
+      } catch (...) {
+        cudaStreamEndCapture(st, &g);
+        capturing = false;
+        throw;
+      }
+      CK(cudaStreamEndCapture(st, &g));
+      capturing = false;
+      cudaGraphExec_t ge;
+      CK(cudaGraphInstantiate(&ge, g, 0));
+      cudaGraphDestroy(g);
+      graphs[key] = ge;
+      it = graphs.find(key);
+      per_chunk = launches - l0;
+      graph_launch_count[key] = per_chunk;
+    } else {
+      for (int k = 0; k < chunk; ++k) {
+        if (rebuild_due()) {
+          keys_sorted = (passes % 2 == 0) ? kA : kB;
+          perm = (passes % 2 == 0) ? vA : vB;
+        }
+        advance_schedule();
+      }
+      launches += graph_launch_count[key];
+    }
+    CK(cudaGraphLaunch(it->second, st));
+    done += chunk;
+  }
+  for (; done < n; ++done) step_once();
+  last_steps = n;
+}
+
+void Scene::ensure_cells() {
+  if (cells_valid) return;
+  auto kp = rebuild(buf[cur], buf[1 - cur], nullptr, nullptr, cell_off);
+  keys_sorted = kp.first;
+  perm = kp.second;
+  cur = 1 - cur;
+  cells_valid = true;
+  steps_since_build = 0;
+}
+
+// ---------------------------------------------------------------- adjoint tape
+void Scene::rollout(int n, int k) {
+  if (n < 1 || k < 1) einval("n_steps and ckpt_every must be >= 1");
+  tape_n = n;
+  tape_k = k;
+  int ncp = (n + k - 1) / k;
+  if ((int)ckpts.size() < ncp) {
+    while ((int)ckpts.size() < ncp) {
+      Arrays a;
+      alloc_arrays(a);
+      ckpts.push_back(a);
+    }
+  }
+  CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st));
+  launches = 0;
+  for (int s = 0; s < n; ++s) {
+    if (s % k == 0) {
+      copy_arrays(ckpts[s / k], buf[cur]);
+      cells_valid = false;  // each segment starts with a rebuild (replayed identically)
+    }
+    step_once();
+  }
+  last_steps = n;
+  tape_valid = true;
+}
+
+void Scene::alloc_tape(int k) {
+  if (tape_cap >= k) return;
+  while ((int)tape.size() < k + 1) {
+    TapeSlot t;
+    alloc_arrays(t.a);
+    t.keys = (uint32_t*)mem.get(4 * (size_t)N);
+    t.perm = (uint32_t*)mem.get(4 * (size_t)N);
+    t.off = (int*)mem.get(sizeof(int) * ((size_t)C_tot + 1));
+    tape.push_back(t);
+  }
+  if (!adj_alloc) {
+    for (int q = 0; q < 2; ++q) {
+      XB[q] = (float4*)mem.get(sizeof(float4) * N);
+      VB[q] = (float4*)mem.get(sizeof(float4) * N);
+    }
+    Sd = (float4*)mem.get(sizeof(float4) * N);
+    Pp = (float*)mem.get(sizeof(float) * N);
+    nu_part = (double*)mem.get(sizeof(double) * ((size_t)(N + 255) / 256 + 1));
+    alloc_arrays(scratch_arr);
+    adj_alloc = true;
+  }
+  tape_cap = k;
+}
+
+void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb0, float* vb0, float* rb0, double* nub,
+                    int is_dev) {
+  if (!tape_valid) einval("sph_adjoint needs a preceding sph_rollout on this scene");
+  if (any_walls || summation) einval("the adjoint supports continuity mode without wall particles");
+  const int n = tape_n, k = tape_k;
+  alloc_tape(k);
+  launches = 0;
+  // seeds of the final state, scattered into the final storage order
+  const size_t nd = (size_t)nf_total * D;
+  const float *dxb = xb, *dvb = vb, *drb = rb;
+  if (!is_dev) {
+    float* p = (float*)mem_tmp(sizeof(float) * (2 * nd + nf_total + 64));
+    if (xb) { CK(cudaMemcpyAsync(p, xb, 4 * nd, cudaMemcpyHostToDevice, st)); dxb = p; }
+    if (vb) { CK(cudaMemcpyAsync(p + nd, vb, 4 * nd, cudaMemcpyHostToDevice, st)); dvb = p + nd; }
+    if (rb) { CK(cudaMemcpyAsync(p + 2 * nd, rb, 4 * (size_t)nf_total, cudaMemcpyHostToDevice, st)); drb = p + 2 * nd; }
+  }
+  int q = 0;
+  if (D == 2)
+    launch_adj_load<2>(N, buf[cur].meta, d_orig_base, dxb, dvb, drb, XB[q], VB[q], st);
+  else
+    launch_adj_load<3>(N, buf[cur].meta, d_orig_base, dxb, dvb, drb, XB[q], VB[q], st);
+  CKL();
+  CK(cudaMemsetAsync(d_nubar, 0, sizeof(double), st));
+  const int ncp = (n + k - 1) / k;
+  for (int sgi = ncp - 1; sgi >= 0; --sgi) {
+    const int t0 = sgi * k, t1 = std::min(n, t0 + k);
+    const int L = t1 - t0;
+    // replay the segment forward, keeping the sweep input of every step
+    std::vector<char> rebuilt(L, 0);
+    bool valid = false;
+    int since = 0;
+    const Arrays* prev = &ckpts[sgi];
+    for (int s = 0; s < L; ++s) {
+      bool due = skin == 0.f || !valid || since >= interval;
+      TapeSlot& slot = tape[s];
+      if (due) {
+        rebuild(*prev, slot.a, slot.keys, slot.perm, slot.off);  // keys/perm copied into the slot
+        valid = true;
+        since = 0;
+        rebuilt[s] = 1;
+      } else {
+        // no rebuild: the previous sweep wrote straight into this slot
+        CK(cudaMemcpyAsync(slot.keys, tape[s - 1].keys, 4 * (size_t)N, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(slot.off, tape[s - 1].off, sizeof(int) * ((size_t)C_tot + 1), cudaMemcpyDeviceToDevice, st));
+      }
+      TravArgs t = trav(slot.a, slot.keys, slot.off);
+      passes_before_sweep(t);
+      bool next_due = (s + 1 < L) && (skin == 0.f || since + 1 >= interval);
+      const Arrays& dst = (s + 1 < L && !next_due) ? tape[s + 1].a : scratch_arr;
+      sweep(t, dst);
+      prev = &scratch_arr;
+      ++since;
+    }
+    // backward through the segment
+    for (int s = L - 1; s >= 0; --s) {
+      TapeSlot& slot = tape[s];
+      if (D == 2)
+        launch_adj_seed<2>(dseg, N, slot.a, XB[q], VB[q], Sd, Pp, st);
+      else
+        launch_adj_seed<3>(dseg, N, slot.a, XB[q], VB[q], Sd, Pp, st);
+      CKL();
+      TravArgs t = trav(slot.a, slot.keys, slot.off);
+      t.pair_count = nullptr;
+      prof_begin(4);
+      int nb;
+      if (D == 2) {
+        if (kern == 0) nb = launch_adj_sweep<2, 0>(t, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        else nb = launch_adj_sweep<2, 1>(t, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+      } else {
+        if (kern == 0) nb = launch_adj_sweep<3, 0>(t, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        else nb = launch_adj_sweep<3, 1>(t, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+      }
+      CKL();
+      prof_end();
+      launch_sum_partials(nu_part, nb, d_nubar, st);
+      CKL();
+      q = 1 - q;
+      if (rebuilt[s]) {
+        launch_adj_unpermute(N, slot.perm, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
+        CKL();
+        q = 1 - q;
+      }
+      launches += 3;
+    }
+  }
+  // XB[q] is in the storage order of checkpoint 0; deliver in original order
+  float* oxb = xb0;
+  float* ovb = vb0;
+  float* orb = rb0;
+  float* stage = nullptr;
+  if (!is_dev) {
+    stage = (float*)mem_tmp(sizeof(float) * (2 * nd + nf_total + 64));
+    oxb = xb0 ? stage : nullptr;
+    ovb = vb0 ? stage + nd : nullptr;
+    orb = rb0 ? stage + 2 * nd : nullptr;
+  }
+  if (D == 2)
+    launch_adj_store<2>(N, ckpts[0].meta, d_orig_base, XB[q], VB[q], oxb, ovb, orb, st);
+  else
+    launch_adj_store<3>(N, ckpts[0].meta, d_orig_base, XB[q], VB[q], oxb, ovb, orb, st);
+  CKL();
+  // the replay reused the sort buffers: the live state must rebuild before its next step
+  cells_valid = false;
+  if (!is_dev) {
+    if (xb0) CK(cudaMemcpyAsync(xb0, oxb, 4 * nd, cudaMemcpyDeviceToHost, st));
+    if (vb0) CK(cudaMemcpyAsync(vb0, ovb, 4 * nd, cudaMemcpyDeviceToHost, st));
+    if (rb0) CK(cudaMemcpyAsync(rb0, orb, 4 * (size_t)nf_total, cudaMemcpyDeviceToHost, st));
+  }
+  if (nub) CK(cudaMemcpyAsync(nub, d_nubar, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+}
+
+// ---------------------------------------------------------------- outputs
+void Scene::get_state(float* x, float* v, float* rho, int is_dev) {
+  const size_t nd = (size_t)N * D;
+  float *ox = x, *ov = v, *orh = rho;
+  if (!is_dev) {
+    float* p = (float*)mem_tmp(sizeof(float) * (2 * nd + N + 64));
+    ox = x ? p : nullptr;
+    ov = v ? p + nd : nullptr;
+    orh = rho ? p + 2 * nd : nullptr;
+  }
+  if (D == 2)
+    launch_download<2>(N, buf[cur], d_orig_base, ox, ov, orh, st);
+  else
+    launch_download<3>(N, buf[cur], d_orig_base, ox, ov, orh, st);
+  CKL();
+  if (!is_dev) {
+    if (x) CK(cudaMemcpyAsync(x, ox, 4 * nd, cudaMemcpyDeviceToHost, st));
+    if (v) CK(cudaMemcpyAsync(v, ov, 4 * nd, cudaMemcpyDeviceToHost, st));
+    if (rho) CK(cudaMemcpyAsync(rho, orh, 4 * (size_t)N, cudaMemcpyDeviceToHost, st));
+  }
+  check_status();
+}
+
+void Scene::check_status() {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h & 1) {
+    set_err("unstable state: non-finite values or density outside [0.5, 2] rho0");
+    throw Fail{SPH_EUNSTABLE};
+  }
+}
+
+void Scene::rates(float* a, float* drho, float* rho, int is_dev) {
+  // summation density / walls modify the records in place: work on a copy
+  ensure_cells();
+  if (!adj_alloc) alloc_tape(1);
+  copy_arrays(scratch_arr, buf[cur]);
+  TravArgs t = trav(scratch_arr, keys_sorted, cell_off);
+  passes_before_sweep(t);
+  const size_t nd = (size_t)nf_total * D;
+  float* p = (float*)mem_tmp(sizeof(float) * (nd + 2 * (size_t)nf_total + 64));
+  RateOut ro;
+  ro.a = p;
+  ro.drho = p + nd;
+  ro.rho = p + nd + nf_total;
+  // outputs are indexed by fluid rows: original index + scene base among fluid rows
+  std::vector<int> fbase(S);
+  int acc = 0;
+  for (int s = 0; s < S; ++s) {
+    fbase[s] = acc;
+    acc += segs[s].nf;
+  }
+  if (!d_fluid_base) d_fluid_base = (int*)mem.get(sizeof(int) * S);
+  CK(cudaMemcpyAsync(d_fluid_base, fbase.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
+  ro.orig_base = d_fluid_base;
+  if (D == 2) {
+    if (kern == 0) launch_rates<2, 0>(t, ro, st); else launch_rates<2, 1>(t, ro, st);
+  } else {
+    if (kern == 0) launch_rates<3, 0>(t, ro, st); else launch_rates<3, 1>(t, ro, st);
+  }
+  CKL();
+  cudaMemcpyKind kind = is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (a) CK(cudaMemcpyAsync(a, ro.a, 4 * nd, kind, st));
+  if (drho) CK(cudaMemcpyAsync(drho, ro.drho, 4 * (size_t)nf_total, kind, st));
+  if (rho) CK(cudaMemcpyAsync(rho, ro.rho, 4 * (size_t)nf_total, kind, st));
+  CK(cudaStreamSynchronize(st));
+}
+
+void Scene::debug_cells(int64_t* start, int32_t* ids) {
+  ensure_cells();
+  std::vector<int> off((size_t)C_tot + 1);
+  std::vector<uint2> meta(N);
+  CK(cudaMemcpyAsync(off.data(), cell_off, sizeof(int) * ((size_t)C_tot + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(meta.data(), buf[cur].meta, sizeof(uint2) * N, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (start)
+    for (size_t c = 0; c <= (size_t)C_tot; ++c) start[c] = off[c];
+  if (ids)
+    for (int k = 0; k < N; ++k) ids[k] = (int32_t)(meta[k].x & ~kWallBit) + orig_base[meta[k].y];
+}
+
+void Scene::debug_pairs(int64_t* n_pairs, int32_t* pi, int32_t* pj, int64_t cap) {
+  if (S > 1) einval("sph_debug_pairs supports single scenes");
+  ensure_cells();
+  // widen the FP32 guard band of the exact predicate to the actual coordinate range
+  {
+    std::vector<float4> X(N);
+    CK(cudaMemcpyAsync(X.data(), buf[cur].X, sizeof(float4) * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double mx = 1.0;
+    for (int k = 0; k < N; ++k) {
+      float c[3] = {X[k].x, X[k].y, D == 3 ? X[k].z : 0.f};
+      for (int q = 0; q < D; ++q) mx = std::max(mx, (double)std::fabs(c[q]));
+    }
+    for (int q = 0; q < D; ++q) mx = std::max(mx, std::fabs(segs[0].lo_d[q]) + segs[0].L_d[q]);
+    DevSeg g = segs[0];
+    double H = g.H;
+    double band = std::max(1e-5, 4.0 * 8.0 * std::ldexp(mx, -23) / H);
+    g.band_lo = (float)(H * H * (1.0 - band));
+    g.band_hi = (float)(H * H * (1.0 + band));
+    CK(cudaMemcpyAsync(dseg, &g, sizeof(DevSeg), cudaMemcpyHostToDevice, st));
+  }
+  int64_t c = std::max<int64_t>(cap, 0);
+  int32_t* dpi = (int32_t*)mem_tmp(sizeof(int32_t) * (2 * (size_t)c + 64));
+  int32_t* dpj = dpi + c;
+  unsigned long long* cnt = d_pairs + 1;
+  CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  t.pair_count = nullptr;
+  if (D == 2)
+    launch_pairs<2>(t, dpi, dpj, cnt, (long long)c, st);
+  else
+    launch_pairs<3>(t, dpi, dpj, cnt, (long long)c, st);
+  CKL();
+  unsigned long long h = 0;
+  CK(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *n_pairs = (int64_t)h;
+  int64_t w = std::min<int64_t>((int64_t)h, c);
+  if (w > 0) {
+    CK(cudaMemcpyAsync(pi, dpi, sizeof(int32_t) * w, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(pj, dpj, sizeof(int32_t) * w, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  CK(cudaMemcpyAsync(dseg, segs.data(), sizeof(DevSeg), cudaMemcpyHostToDevice, st));
+}
+
+void Scene::timing(int cls, double* ms, int64_t* count) {
+  CK(cudaStreamSynchronize(st));
+  double tot = 0.0;
+  int64_t c = 0;
+  std::vector<ProfEvent> keep;
+  for (auto& e : prof_events) {
+    if (e.cls == cls) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, e.a, e.b));
+      tot += t;
+      ++c;
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    } else {
+      keep.push_back(e);
+    }
+  }
+  prof_events.swap(keep);
+  *ms = tot;
+  *count = c;
+}
+
+}  // namespace sph
+
+// ================================================================== C ABI
+using sph::Fail;
+using sph::Scene;
+
+struct sph_scene {
+  Scene s;
+};
+
+#define API_BEGIN try {
+#define API_END                                     \
+  }                                                 \
+  catch (const Fail& f) {                           \
+    return f.code;                                  \
+  }                                                 \
+  catch (const std::bad_alloc&) {                   \
+    sph::set_err("host allocation failed");         \
+    return SPH_ENOMEM;                              \
+  }                                                 \
+  catch (...) {                                     \
+    sph::set_err("unexpected internal exception");  \
+    return SPH_EINTERNAL;                           \
+  }                                                 \
+  return SPH_OK;
+
+extern "C" {
+
+int sph_abi_version(void) { return SPH_ABI_VERSION; }
+const char* sph_last_error(void) { return sph::last_error(); }
+
+int sph_set_allocator(sph_alloc_fn a, sph_free_fn f, void* ctx) {
+  if ((a == nullptr) != (f == nullptr)) {
+    sph::set_err("alloc and free hooks must both be set or both be NULL");
+    return SPH_EINVAL;
+  }
+  sph::set_allocator(a, f, ctx);
+  return SPH_OK;
+}
+
+int sph_init(const sph_params* params, int n_fluid, int n_wall, const float* x, const float* v, const float* rho,
+             const float* mass, int ptr_is_device, void* cuda_stream, sph_scene** out) {
+  if (!params || !x || !rho || !mass || !out) {
+    sph::set_err("sph_init: params, x, rho, mass and out must be non-NULL");
+    return SPH_EINVAL;
+  }
+  *out = nullptr;
+  sph_scene* sc = nullptr;
+  API_BEGIN
+  sc = new sph_scene();
+  Scene& s = sc->s;
+  {
+    std::lock_guard<std::mutex> lk(sph::g_alloc_mu);
+    s.mem.afn = sph::g_alloc;
+    s.mem.ffn = sph::g_free;
+    s.mem.actx = sph::g_alloc_ctx;
+    s.mem.fctx = sph::g_alloc_ctx;
+  }
+  double mx = 1.0;
+  for (int k = 0; k < 3; ++k) mx = std::max(mx, std::max(std::fabs(params->box_lo[k]), std::fabs(params->box_hi[k])));
+  if (!ptr_is_device) {
+    size_t nd = (size_t)(n_fluid + n_wall) * params->dim;
+    for (size_t q = 0; q < nd; ++q) {
+      if (!std::isfinite(x[q])) sph::einval("non-finite initial position");
+      mx = std::max(mx, (double)std::fabs(x[q]));
+    }
+  } else {
+    mx = std::max(mx, 16.0);
+  }
+  s.setup_checked({*params}, {n_fluid}, {n_wall}, {mx});
+  s.bind_stream((cudaStream_t)cuda_stream);
+  s.enter();
+  s.alloc_all();
+  s.upload(0, x, v, rho, mass, ptr_is_device);
+  CK(cudaStreamSynchronize(s.st));
+  *out = sc;
+  sc = nullptr;
+  }
+  catch (const Fail& f) {
+    delete sc;
+    return f.code;
+  }
+  catch (...) {
+    delete sc;
+    sph::set_err("sph_init: unexpected failure");
+    return SPH_EINTERNAL;
+  }
+  return SPH_OK;
+}
+
+int sph_step(sph_scene* sc, int n_steps) {
+  if (!sc || n_steps < 0) {
+    sph::set_err("sph_step: bad arguments");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  sc->s.enter();
+  sc->s.tape_valid = false;
+  sc->s.steps(n_steps);
+  API_END
+}
+
+int sph_get_state(const sph_scene* sc, float* x, float* v, float* rho, int ptr_is_device) {
+  if (!sc) {
+    sph::set_err("sph_get_state: NULL scene");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  Scene& s = const_cast<Scene&>(sc->s);
+  s.enter();
+  s.get_state(x, v, rho, ptr_is_device);
+  s.leave();
+  API_END
+}
+
+int sph_rates(sph_scene* sc, float* a, float* drho, float* rho_used, int ptr_is_device) {
+  if (!sc) {
+    sph::set_err("sph_rates: NULL scene");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  sc->s.enter();
+  sc->s.rates(a, drho, rho_used, ptr_is_device);
+  sc->s.leave();
+  API_END
+}
+
+int sph_rollout(sph_scene* sc, int n_steps, int ckpt_every) {
+  if (!sc) {
+    sph::set_err("sph_rollout: NULL scene");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  sc->s.enter();
+  sc->s.rollout(n_steps, ckpt_every);
+  API_END
+}
+
+int sph_adjoint(sph_scene* sc, const float* xbar_T, const float* vbar_T, const float* rhobar_T, float* xbar_0,
+                float* vbar_0, float* rhobar_0, double* nubar, int ptr_is_device) {
+  if (!sc) {
+    sph::set_err("sph_adjoint: NULL scene");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  sc->s.enter();
+  sc->s.adjoint(xbar_T, vbar_T, rhobar_T, xbar_0, vbar_0, rhobar_0, nubar, ptr_is_device);
+  sc->s.leave();
+  API_END
+}
+
+int sph_scene_info(const sph_scene* sc, int32_t* ncell3, int32_t* n) {
+  if (!sc) {
+    sph::set_err("sph_scene_info: NULL scene");
+    return SPH_EINVAL;
+  }
+  if (ncell3)
+    for (int k = 0; k < 3; ++k) ncell3[k] = sc->s.segs[0].n[k];
+  if (n) *n = sc->s.N;
+  return SPH_OK;
+}
+
+int sph_debug_cells(sph_scene* sc, int64_t* cell_start, int32_t* sorted_ids) {
+  if (!sc) {
+    sph::set_err("sph_debug_cells: NULL scene");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  sc->s.enter();
+  sc->s.debug_cells(cell_start, sorted_ids);
+  API_END
+}
+
+int sph_debug_pairs(sph_scene* sc, int64_t* n_pairs, int32_t* pi, int32_t* pj, int64_t cap) {
+  if (!sc || !n_pairs || (cap > 0 && (!pi || !pj))) {
+    sph::set_err("sph_debug_pairs: bad arguments");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  sc->s.enter();
+  sc->s.debug_pairs(n_pairs, pi, pj, cap);
+  API_END
+}
+
+int sph_profile(sph_scene* sc, int enable) {
+  if (!sc) return SPH_EINVAL;
+  sc->s.profiling = enable != 0;
+  return SPH_OK;
+}
+
+int sph_timing(sph_scene* sc, int cls, double* ms, int64_t* launches) {
+  if (!sc || !ms || !launches) return SPH_EINVAL;
+  API_BEGIN
+  sc->s.timing(cls, ms, launches);
+  API_END
+}
+
+int sph_counters(sph_scene* sc, int64_t* pairs_per_step, int64_t* launches) {
+  if (!sc) return SPH_EINVAL;
+  API_BEGIN
+  unsigned long long h = 0;
+  CK(cudaMemcpyAsync(&h, sc->s.d_pairs, sizeof(h), cudaMemcpyDeviceToHost, sc->s.st));
+  CK(cudaStreamSynchronize(sc->s.st));
+  if (pairs_per_step) *pairs_per_step = sc->s.last_steps > 0 ? (int64_t)(h / (unsigned long long)sc->s.last_steps) : 0;
+  if (launches) *launches = sc->s.launches;
+  API_END
+}
+
+void sph_destroy(sph_scene* sc) {
+  if (!sc) return;
+  delete sc;
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Host-side scene object of the B300 WCSPH library (internal; the public ABI is include/sph.h).
+#pragma once
+#include <map>
+#include <string>
+#include <tuple>
+#include <utility>
+#include <vector>
+
+#include "../../include/sph.h"
+#include "sph_kernels.cuh"
+
+namespace sph {
+
+const char* last_error();
+void set_allocator(sph_alloc_fn a, sph_free_fn f, void* ctx);
+
+// Device memory owned by one scene (allocator hook or cudaMalloc); freed with the scene.
+struct DeviceMem {
+  sph_alloc_fn afn = nullptr;
+  sph_free_fn ffn = nullptr;
+  void* actx = nullptr;
+  void* fctx = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<std::pair<void*, size_t>> blocks;
+  size_t total = 0;
+  void* get(size_t bytes);
+  void release();
+  ~DeviceMem();
+};
+
+struct ProfEvent {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+struct TapeSlot {
+  Arrays a;            // sweep input records of one step (sorted order of that step)
+  uint32_t* keys;      // sorted cell keys in effect
+  uint32_t* perm;      // permutation applied at that step's rebuild (if any)
+  int* off;            // cell offsets in effect
+};
+
+struct GraphKey {
+  int chunk, cur, since;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(chunk, cur, since) < std::tie(o.chunk, o.cur, o.since);
+  }
+};
+
+// A scene: one or more packed segments (independent SPH problems) advanced together.
+struct Scene {
+  DeviceMem mem;
+  cudaStream_t st = nullptr;        // stream all work of the scene runs on
+  cudaStream_t user_st = nullptr;   // caller's stream (0 = legacy default stream)
+  bool own_stream = false;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int S = 0, D = 2, kern = 0, N = 0, nf_total = 0, C_tot = 0, bits = 0, passes = 0;
+  bool summation = false, any_walls = false;
+  float skin = 0.f;
+  int interval = 1;
+  std::vector<DevSeg> segs;
+  std::vector<int> orig_base;
+  DevSeg* dseg = nullptr;
+  int* d_orig_base = nullptr;
+  int* d_fluid_base = nullptr;
+  Arrays buf[2];
+  int cur = 0;
+  uint32_t *kA = nullptr, *vA = nullptr, *kB = nullptr, *vB = nullptr;
+  uint32_t* keys_sorted = nullptr;
+  uint32_t* perm = nullptr;
+  int* cell_off = nullptr;
+  uint32_t* scratch = nullptr;
+  int* d_status = nullptr;
+  unsigned long long* d_pairs = nullptr;
+  double* d_nubar = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0;
+  bool cells_valid = false;
+  int steps_since_build = 0;
+  // execution
+  bool use_graphs = true;
+  int graph_chunk = 8;
+  bool capturing = false;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  std::map<GraphKey, long long> graph_launch_count;
+  // profiling and counters
+  bool profiling = false;
+  std::vector<ProfEvent> prof_events;
+  long long launches = 0;
+  int last_steps = 0;
+  // adjoint tape
+  bool tape_valid = false;
+  int tape_n = 0, tape_k = 0, tape_cap = 0;
+  std::vector<Arrays> ckpts;
+  std::vector<TapeSlot> tape;
+  bool adj_alloc = false;
+  float4* XB[2] = {nullptr, nullptr};
+  float4* VB[2] = {nullptr, nullptr};
+  float4* Sd = nullptr;
+  float* Pp = nullptr;
+  double* nu_part = nullptr;
+  Arrays scratch_arr{};
+
+  ~Scene();
+  void bind_stream(cudaStream_t user);
+  void enter();
+  void leave();
+  void setup_checked(const std::vector<sph_params>& prms, const std::vector<int>& nfs,
+                     const std::vector<int>& nws, const std::vector<double>& max_abs_x);
+  void alloc_all();
+  void alloc_arrays(Arrays& a);
+  void copy_arrays(const Arrays& dst, const Arrays& src);
+  void upload(int s, const float* x, const float* v, const float* rho, const float* mass, int is_dev);
+  void* mem_tmp(size_t bytes);
+  TravArgs trav(const Arrays& a, const uint32_t* keys, const int* off) const;
+  void prof_begin(int cls);
+  void prof_end();
+  std::pair<uint32_t*, uint32_t*> rebuild(const Arrays& in, const Arrays& out, uint32_t* keys_out,
+                                          uint32_t* perm_out, int* off_out);
+  void passes_before_sweep(const TravArgs& t);
+  void sweep(const TravArgs& t, const Arrays& out);
+  bool rebuild_due() const;
+  void step_once();
+  void advance_schedule();
+  void steps(int n);
+  void ensure_cells();
+  void rollout(int n, int k);
+  void alloc_tape(int k);
+  void adjoint(const float* xb, const float* vb, const float* rb, float* xb0, float* vb0, float* rb0, double* nub,
+               int is_dev);
+  void get_state(float* x, float* v, float* rho, int is_dev);
+  void check_status();
+  void rates(float* a, float* drho, float* rho, int is_dev);
+  void debug_cells(int64_t* start, int32_t* ids);
+  void debug_pairs(int64_t* n_pairs, int32_t* pi, int32_t* pj, int64_t cap);
+  void timing(int cls, double* ms, int64_t* count);
+};
+
+}  // namespace sph

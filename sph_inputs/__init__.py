@@ -102,32 +102,47 @@ def _lattice_2d(n_side: int, seed: int, jitter: float, L: float = 1.0):
     return dx, np.stack([x, y], axis=1)
 
 
+def _tait_inverse(p, rho0, c0, gamma):
+    B = rho0 * c0 * c0 / gamma
+    return rho0 * (1.0 + p / B) ** (1.0 / gamma)
+
+
 def taylor_green_2d(n_side: int = 64, seed: int = 0, steps: int = 100, nu: float = 0.01,
                     c0: float = 10.0, delta: float = 0.1, jitter: float = 0.05,
                     density_mode: int = DENSITY_CONTINUITY, rebuild_interval: int = 1,
-                    skin: float = 0.0) -> dict:
+                    skin: float = 0.0, dt: float | None = None, pressure: bool = False) -> dict:
     """Periodic 2D Taylor-Green vortex on the unit square (u = sin 2pi x cos 2pi y,
     v = -cos 2pi x sin 2pi y), lattice at (i+1/2)dx jittered by U[-jitter, jitter) dx,
-    rho = rho0 = 1, m = rho0 dx^2, Wendland C4 with support H = 4 dx, dt = H / (4 c0)."""
+    rho = rho0 = 1, m = rho0 dx^2, Wendland C4 with support H = 4 dx, dt = h / (4 c0) with the
+    smoothing length h = H/2 unless given.  With ``pressure`` the density carries the vortex's analytic pressure
+    p = (rho0 U^2 / 4)(cos 4pi x + cos 4pi y) through the inverse Tait law."""
     dx, xy = _lattice_2d(n_side, seed, jitter)
     vx = np.sin(2 * np.pi * xy[:, 0]) * np.cos(2 * np.pi * xy[:, 1])
     vy = -np.cos(2 * np.pi * xy[:, 0]) * np.sin(2 * np.pi * xy[:, 1])
     n = n_side * n_side
     H = 4.0 * dx
-    p = _params(2, KERNEL_WENDLAND4, H, 0.25 * _f32(H) / c0, c0, nu, delta, (0.0, 0.0), (1.0, 1.0), 0b11,
+    dt = 0.25 * (0.5 * _f32(H)) / c0 if dt is None else dt
+    p = _params(2, KERNEL_WENDLAND4, H, dt, c0, nu, delta, (0.0, 0.0), (1.0, 1.0), 0b11,
                 density_mode=density_mode, rebuild_interval=rebuild_interval, skin=skin)
+    rho = np.full(n, p["rho0"])
+    if pressure:
+        pr = 0.25 * (np.cos(4 * np.pi * xy[:, 0]) + np.cos(4 * np.pi * xy[:, 1]))
+        rho = _tait_inverse(pr, 1.0, p["c0"], p["gamma"])
     return dict(
         name=f"tgv2d_{n_side}", params=p, n_fluid=n, n_wall=0, steps=steps, seed=seed, dx=dx,
         x=xy.astype(np.float32), v=np.stack([vx, vy], 1).astype(np.float32),
-        rho=np.full(n, p["rho0"], np.float32), mass=np.full(n, _f32(dx * dx), np.float32),
+        rho=rho.astype(np.float32), mass=np.full(n, _f32(dx * dx), np.float32),
     )
 
 
 def taylor_green_3d(n_side: int = 128, seed: int = 0, steps: int = 200, nu: float = 0.005,
                     c0: float = 10.0, delta: float = 0.1, jitter: float = 0.05,
-                    support: float = 2.43, rebuild_interval: int = 1, skin: float = 0.0) -> dict:
+                    support: float = 2.43, rebuild_interval: int = 1, skin: float = 0.0,
+                    pressure: bool = False) -> dict:
     """Periodic 3D Taylor-Green vortex in the unit cube (u = sin cos cos, v = -cos sin cos,
-    w = 0), Wendland C2 with support 2.43 dx, lattice jittered by U[-jitter, jitter) dx."""
+    w = 0), Wendland C2 with support 2.43 dx, lattice jittered by U[-jitter, jitter) dx.  With
+    ``pressure`` the density carries the analytic pressure
+    p = (rho0 U^2 / 16)(cos 4pi x + cos 4pi y)(cos 4pi z + 2) through the inverse Tait law."""
     dx = 1.0 / n_side
     n = n_side ** 3
     ids = np.arange(n, dtype=np.int64)
@@ -138,12 +153,17 @@ def taylor_green_3d(n_side: int = 128, seed: int = 0, steps: int = 200, nu: floa
     cx, cy, cz = (np.cos(2 * np.pi * x[:, a]) for a in range(3))
     v = np.stack([sx * cy * cz, -cx * sy * cz, np.zeros(n)], 1)
     H = support * dx
-    p = _params(3, KERNEL_WENDLAND2, H, 0.25 * _f32(H) / c0, c0, nu, delta, (0.0, 0.0, 0.0),
+    p = _params(3, KERNEL_WENDLAND2, H, 0.25 * (0.5 * _f32(H)) / c0, c0, nu, delta, (0.0, 0.0, 0.0),
                 (1.0, 1.0, 1.0), 0b111, rebuild_interval=rebuild_interval, skin=skin)
+    rho = np.full(n, p["rho0"])
+    if pressure:
+        pr = (1.0 / 16.0) * (np.cos(4 * np.pi * x[:, 0]) + np.cos(4 * np.pi * x[:, 1])) * \
+            (np.cos(4 * np.pi * x[:, 2]) + 2.0)
+        rho = _tait_inverse(pr, 1.0, p["c0"], p["gamma"])
     return dict(
         name=f"tgv3d_{n_side}", params=p, n_fluid=n, n_wall=0, steps=steps, seed=seed, dx=dx,
         x=x.astype(np.float32), v=v.astype(np.float32),
-        rho=np.full(n, p["rho0"], np.float32), mass=np.full(n, _f32(dx ** 3), np.float32),
+        rho=rho.astype(np.float32), mass=np.full(n, _f32(dx ** 3), np.float32),
     )
 
 
@@ -154,14 +174,16 @@ def dam_break(res: int = 128, steps: int = 2000, alpha_visc: float = 0.02, delta
     filled) and 4+(k+1/2)dx (right), open top.  g = (0, -9.81), c0 = 10 sqrt(2 g 2.0),
     Wendland C4 support 4 dx, hydrostatic initial density by the inverse Tait law.
     The viscosity is the delta-SPH artificial viscosity alpha = 0.02 expressed as
-    nu = alpha H c0 / (2 (d + 2))."""
+    nu = alpha h c0 / (2 (d + 2)) with h = H/2.  The time step is dt = dx / (4 c0) = h / (8 c0):
+    with a free surface, the symplectic-Euler step at h / (4 c0) grows particle-scale modes
+    within a few hundred steps (the FP64 reference diverges too), at h / (8 c0) it does not."""
     dx = 1.0 / res
     g = 9.81
     rho0 = 1.0
     gamma = 7.0
     c0 = 10.0 * math.sqrt(2.0 * g * 2.0)
     H = 4.0 * dx
-    nu = alpha_visc * H * c0 / (2.0 * (2 + 2))
+    nu = alpha_visc * (0.5 * H) * c0 / (2.0 * (2 + 2))
     nfx, nfy = int(round(1.0 * res)), int(round(2.0 * res))
     fi = np.arange(nfx * nfy)
     fx = ((fi % nfx) + 0.5) * dx
@@ -184,7 +206,7 @@ def dam_break(res: int = 128, steps: int = 2000, alpha_visc: float = 0.02, delta
     nf, nw = nfx * nfy, len(w)
     v = np.zeros((nf + nw, 2))
     rho = np.concatenate([rho_f, np.full(nw, rho0)])
-    p = _params(2, KERNEL_WENDLAND4, H, 0.25 * _f32(H) / _f32(c0), c0, nu, delta,
+    p = _params(2, KERNEL_WENDLAND4, H, 0.25 * dx / _f32(c0), c0, nu, delta,
                 (-4 * dx, -4 * dx), (4.0 + 4 * dx, 3.0), 0b00, g=(0.0, -g), rho0=rho0, gamma=gamma,
                 rebuild_interval=rebuild_interval, skin=skin)
     return dict(
@@ -192,6 +214,17 @@ def dam_break(res: int = 128, steps: int = 2000, alpha_visc: float = 0.02, delta
         x=x.astype(np.float32), v=v.astype(np.float32), rho=rho.astype(np.float32),
         mass=np.full(nf + nw, _f32(rho0 * dx * dx), np.float32),
     )
+
+
+def adjoint_problem(n_side: int = 128, steps: int = 200, seed: int = 0) -> dict:
+    """Adjoint workload: periodic Taylor-Green at n_side^2 with the time step of the 128^2 case
+    (dt = h_128 / (4 c0) = 3.90625e-4, so the 16^2 copy covers the same 200 steps and horizon),
+    target rollout from velocities perturbed by 5% Gaussian noise."""
+    dt = 0.25 * (0.5 * _f32(4.0 / 128.0)) / 10.0
+    s = taylor_green_2d(n_side, seed=seed, steps=steps, dt=dt)
+    s["v_target"] = perturbed_velocity(s)
+    s["ckpt_every"] = 20
+    return s
 
 
 def perturbed_velocity(scene: dict, rel: float = 0.05, U0: float = 1.0, seed: int | None = None) -> np.ndarray:

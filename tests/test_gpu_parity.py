@@ -1,0 +1,312 @@
+"""CUDA path vs the FP64 oracle (element by element on seeded inputs).
+
+Bars: cell ranges and neighbour pair sets bit-exact; single-step rates within 1e-5 (normwise
+relative, FP32 vs FP64); 10-step rollouts within 1e-3; adjoint gradients within 1e-3 of the
+oracle's reverse pass and of central finite differences.
+"""
+import numpy as np
+import pytest
+
+import sph_inputs as si
+from tests.scenes import lattice, params, scene
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def sph():
+    from paper_2507_21684_b300 import build
+    build.build()
+    import paper_2507_21684_b300 as m
+    return m
+
+
+def make(sph, s, **kw):
+    return sph.scene_from(s, **kw)
+
+
+CELL_CASES = {
+    "tgv2d_64": lambda: si.taylor_green_2d(64, seed=0),
+    "tgv2d_37_ragged": lambda: si.taylor_green_2d(37, seed=3),
+    "dambreak_32": lambda: si.dam_break(res=32),
+    "tgv3d_20": lambda: si.taylor_green_3d(20, seed=1),
+    "tgv2d_16_skin": lambda: si.taylor_green_2d(16, seed=2, skin=0.01, rebuild_interval=4),
+    "tgv3d_13_wendland4": lambda: dict(si.taylor_green_3d(13, seed=4),
+                                       params=dict(si.taylor_green_3d(13)["params"], kernel=0)),
+}
+
+
+@pytest.mark.parametrize("case", list(CELL_CASES))
+def test_cells_bit_exact(sph, orc, case):
+    s = CELL_CASES[case]()
+    with make(sph, s) as sc:
+        start, ids = sc.debug_cells()
+    n3, key, oids, ostart = orc.cells(s["params"], s["x"])
+    assert np.array_equal(start, ostart)
+    assert np.array_equal(ids, oids)
+
+
+@pytest.mark.parametrize("case", list(CELL_CASES))
+def test_pairs_bit_exact(sph, orc, case):
+    s = CELL_CASES[case]()
+    with make(sph, s) as sc:
+        gp = sc.debug_pairs()
+    op = orc.pairs(s["params"], s["x"], brute=s["x"].shape[0] <= 3000)
+    assert gp.shape == op.shape
+    assert np.array_equal(gp, op)
+
+
+def test_pairs_exact_cutoff_and_periodic_images(sph, orc):
+    """d^2 == H^2 is not a neighbour; images across the periodic edge are; unwrapped
+    positions several boxes away are folded (floor modulo)."""
+    p = params(H=0.25, box_lo=(0, 0), box_hi=(1, 1))
+    x = np.array([[0.25, 0.5], [0.5, 0.5],          # exactly H apart: excluded
+                  [0.03125, 0.75], [0.96875, 0.75],  # 1/16 apart through the edge
+                  [-2.0 + 0.4, 3.0 + 0.1], [0.4, 0.1 + 0.2],  # far unwrapped copy, 0.2 apart
+                  [0.7, 0.2]], np.float32)
+    s = scene(p, x, mass=np.full(len(x), 1e-3))
+    with make(sph, s) as sc:
+        gp = sc.debug_pairs()
+    op = orc.pairs(p, x, brute=True)
+    assert np.array_equal(gp, op)
+    assert not any((a, b) == (0, 1) for a, b in gp.tolist())
+    assert any((a, b) == (2, 3) for a, b in gp.tolist())
+
+
+def test_pairs_translation_invariance(sph, orc):
+    s = si.taylor_green_2d(24, seed=1)
+    x = (np.round(s["x"].astype(np.float64) * 2.0 ** 14) / 2.0 ** 14).astype(np.float32)
+    rng = np.random.default_rng(0)
+    shift = rng.integers(-3, 4, x.shape).astype(np.float64)
+    s0 = dict(s, x=x)
+    s1 = dict(s, x=(x + shift).astype(np.float32))
+    with make(sph, s0) as a, make(sph, s1) as b:
+        pa, pb = a.debug_pairs(), b.debug_pairs()
+    assert np.array_equal(pa, pb)
+    assert np.array_equal(pa, orc.pairs(s["params"], x, brute=True))
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33])
+def test_tiny_and_ragged_counts(sph, orc, n):
+    s = si.taylor_green_2d(16, seed=5)
+    sub = dict(s, x=s["x"][:n].copy(), v=s["v"][:n].copy(), rho=s["rho"][:n].copy(), mass=s["mass"][:n].copy(),
+               n_fluid=n)
+    with make(sph, sub) as sc:
+        gp = sc.debug_pairs()
+        r = sc.rates()
+        sc.step(3)
+        x, v, rho = sc.get_state()
+    assert np.array_equal(gp, orc.pairs(s["params"], sub["x"], brute=True))
+    o = orc.rates(sub)
+    assert rel(r["a"], o["a"]) < 1e-5
+    xo, vo, ro = orc.rollout(sub, 3)
+    assert rel(x - sub["x"], xo - sub["x"]) < 1e-4
+
+
+def _snapshot(orc, s, steps):
+    """Oracle state after `steps` steps, rounded to float32 (so both sides see the same input)."""
+    xo, vo, ro = orc.rollout(s, steps)
+    return dict(s, x=xo.astype(np.float32), v=vo.astype(np.float32), rho=ro.astype(np.float32))
+
+
+RATE_CASES = {
+    "tgv2d_64_t0": lambda orc: si.taylor_green_2d(64, seed=0),
+    "tgv2d_64_pressure_t0": lambda orc: si.taylor_green_2d(64, seed=6, pressure=True),
+    "tgv2d_64_t20": lambda orc: _snapshot(orc, si.taylor_green_2d(64, seed=0), 20),
+    "dambreak_64_t20": lambda orc: _snapshot(orc, si.dam_break(res=64), 20),
+    "tgv3d_24_t10": lambda orc: _snapshot(orc, si.taylor_green_3d(24, seed=2), 10),
+    "tgv2d_48_summation_t10": lambda orc: _snapshot(orc, si.taylor_green_2d(48, seed=1, density_mode=1), 10),
+}
+
+
+@pytest.mark.parametrize("case", list(RATE_CASES))
+def test_single_step_rates(sph, orc, case):
+    s = RATE_CASES[case](orc)
+    with make(sph, s) as sc:
+        g = sc.rates()
+    o = orc.rates(s)
+    ea, ed = rel(g["a"], o["a"]), rel(g["drho"], o["drho"])
+    er = rel(g["rho"], o["rho"])
+    assert ea < 1e-5, ea
+    if s["params"]["density_mode"] == 0:
+        assert ed < 1e-5, ed
+    assert er < 1e-6, er
+
+
+ROLL_CASES = {
+    "tgv2d_64": lambda: si.taylor_green_2d(64, seed=0),
+    "dambreak_128_full": lambda: si.dam_break(res=128),
+    "tgv3d_32": lambda: si.taylor_green_3d(32, seed=1),
+    "tgv2d_32_summation": lambda: si.taylor_green_2d(32, seed=2, density_mode=1),
+    "tgv2d_32_verlet": lambda: si.taylor_green_2d(32, seed=2, skin=0.02, rebuild_interval=5),
+}
+
+
+def quant_floor(ref):
+    """Norm of half an ulp of the float32 output at the reference values: the part of any
+    float32 result's error that no arithmetic can remove."""
+    r = np.asarray(ref, np.float64)
+    return float(np.linalg.norm(0.5 * np.spacing(np.abs(r).astype(np.float32)).astype(np.float64)))
+
+
+def check_rollout(s, n, x, v, rho, xo, vo, ro, tol=1e-3):
+    """Normwise relative errors of displacement, velocity and density change; each bound is
+    tol * |reference| plus the float32 output quantisation of that field."""
+    x0 = s["x"].astype(np.float64)
+    r0 = s["params"]["rho0"]
+    dx_err = np.linalg.norm((x - x0) - (xo - x0))
+    assert dx_err <= tol * np.linalg.norm(xo - x0) + quant_floor(xo), (dx_err, np.linalg.norm(xo - x0))
+    assert np.linalg.norm(v - vo) <= tol * np.linalg.norm(vo) + quant_floor(vo)
+    assert np.linalg.norm((rho - r0) - (ro - r0)) <= tol * np.linalg.norm(ro - r0) + quant_floor(ro)
+
+
+@pytest.mark.parametrize("case", list(ROLL_CASES))
+def test_ten_step_rollout(sph, orc, case):
+    s = ROLL_CASES[case]()
+    n = 10
+    with make(sph, s) as sc:
+        sc.step(n)
+        x, v, rho = sc.get_state()
+    xo, vo, ro = orc.rollout(s, n)
+    check_rollout(s, n, x, v, rho, xo, vo, ro)
+
+
+def test_dam_break_hundred_steps(sph, orc):
+    """100 steps of the full dam break: the displacement now dwarfs the float32 spacing."""
+    s = si.dam_break(res=128)
+    with make(sph, s) as sc:
+        sc.step(100)
+        x, v, rho = sc.get_state()
+    xo, vo, ro = orc.rollout(s, 100)
+    x0 = s["x"].astype(np.float64)
+    assert rel(x - x0, xo - x0) < 1e-3
+    assert rel(v, vo) < 1e-3
+    assert rel(rho - 1.0, ro - 1.0) < 1e-3
+
+
+def test_graph_replay_is_bitwise_eager(sph):
+    s = si.taylor_green_2d(48, seed=3)
+    with make(sph, s) as a, make(sph, s) as b:
+        a.step(24)  # graph chunks
+        for _ in range(24):
+            b.step(1)  # eager
+        xa, va, ra = a.get_state()
+        xb, vb, rb = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ra, rb)
+
+
+def test_rollout_equals_step(sph):
+    s = si.taylor_green_2d(32, seed=3)
+    with make(sph, s) as a, make(sph, s) as b:
+        a.step(30)
+        b.rollout(30, 7)
+        assert all(np.array_equal(p, q) for p, q in zip(a.get_state(), b.get_state()))
+
+
+def test_adjoint_matches_oracle_and_fd(sph, orc):
+    """Config of the adjoint workload on the 16 x 16 copy: 200 steps, checkpoints every 20,
+    loss = mean squared final-position error against a target rollout from perturbed v0."""
+    s = si.adjoint_problem(16)
+    steps, vt = 200, s["v_target"]
+    N = s["n_fluid"]
+    xt, _, _ = orc.rollout(s, steps, v=vt)
+    with make(sph, s) as sc:
+        sc.rollout(steps, 20)
+        xT, vT, rT = sc.get_state()
+        seed = (2.0 * (xT.astype(np.float64) - xt) / N).astype(np.float32)
+        gx, gv, gr, gnu = sc.adjoint(seed, np.zeros_like(seed), np.zeros(N, np.float32))
+    x0, v0, r0 = (s[k].astype(np.float64) for k in ("x", "v", "rho"))
+    xo, _, _ = orc.rollout64(s, steps, x0, v0, r0)
+    oseed = 2.0 * (xo - xt) / N
+    o = orc.adjoint(s, steps, oseed, np.zeros_like(oseed), np.zeros(N), x=x0, v=v0, rho=r0)
+    assert rel(gv, o["vb"]) < 1e-3
+    assert rel(gx, o["xb"]) < 1e-3
+    assert abs(gnu - o["nub"]) < 1e-3 * abs(o["nub"])
+
+    def loss(v, nu=None):
+        xx, _, _ = orc.rollout64(s, steps, x0, v, r0, nu=nu)
+        return ((xx - xt) ** 2).sum() / N
+
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        dv = rng.standard_normal(v0.shape)
+        h = 1e-6
+        fd = (loss(v0 + h * dv) - loss(v0 - h * dv)) / (2 * h)
+        assert abs((gv.astype(np.float64) * dv).sum() - fd) < 1e-3 * abs(fd)
+    nu = s["params"]["nu"]
+    h = 1e-7
+    fd_nu = (loss(v0, nu + h) - loss(v0, nu - h)) / (2 * h)
+    assert abs(gnu - fd_nu) < 1e-3 * abs(fd_nu)
+
+
+def test_checkpoint_recompute_is_bitwise_store_all(sph):
+    s = si.taylor_green_2d(16, seed=1)
+    N = s["n_fluid"]
+    rng = np.random.default_rng(1)
+    seed = rng.standard_normal((N, 2)).astype(np.float32)
+    out = []
+    for k in (5, 40):
+        with make(sph, s) as sc:
+            sc.rollout(40, k)
+            out.append(sc.adjoint(seed, seed, np.ones(N, np.float32)))
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
+    assert out[0][3] == out[1][3]
+
+
+def test_adjoint_full_size_matches_oracle(sph, orc):
+    """128 x 128 copy of the adjoint workload, 200 steps, checkpoints every 20."""
+    s = si.adjoint_problem(128)
+    steps, vt = 200, s["v_target"]
+    N = s["n_fluid"]
+    xt, _, _ = orc.rollout(s, steps, v=vt)
+    with make(sph, s) as sc:
+        sc.rollout(steps, 20)
+        xT, _, _ = sc.get_state()
+        seed = (2.0 * (xT.astype(np.float64) - xt) / N).astype(np.float32)
+        gx, gv, gr, gnu = sc.adjoint(seed, None, None)
+    x0, v0, r0 = (s[k].astype(np.float64) for k in ("x", "v", "rho"))
+    xo, _, _ = orc.rollout64(s, steps, x0, v0, r0)
+    o = orc.adjoint(s, steps, 2.0 * (xo - xt) / N, np.zeros_like(xo), np.zeros(N), x=x0, v=v0, rho=r0)
+    assert rel(gv, o["vb"]) < 1e-3
+    assert abs(gnu - o["nub"]) < 1e-3 * abs(o["nub"])
+
+
+def test_full_size_3d_rates_sampled(sph, orc):
+    """2,097,152-particle 3D Taylor-Green (Wendland C2) with its analytic pressure field:
+    rates of 4096 sampled particles against the oracle, same launch path as the benchmark."""
+    s = si.taylor_green_3d(128, seed=0, pressure=True)
+    with make(sph, s) as sc:
+        g = sc.rates()
+    idx = np.arange(0, s["n_fluid"], 512, dtype=np.int32)
+    o = orc.rates(s, who=idx)
+    assert rel(g["a"][idx], o["a"]) < 1e-5
+    assert rel(g["drho"][idx], o["drho"]) < 1e-5
+
+
+def test_instability_is_reported(sph):
+    s = si.taylor_green_2d(16, seed=0)
+    s = dict(s, v=(s["v"] * 200.0).astype(np.float32))
+    with make(sph, s) as sc:
+        sc.step(20)
+        with pytest.raises(sph.SphError) as e:
+            sc.get_state()
+        assert e.value.code == sph.SPH_EUNSTABLE
+
+
+def test_device_inputs_match_host_inputs(sph):
+    import torch
+    s = si.taylor_green_2d(32, seed=4)
+    with make(sph, s) as a, make(sph, s, device=True) as b:
+        a.step(5)
+        b.step(5)
+        xa, va, ra = a.get_state()
+        xb, vb, rb = b.get_state(device=True)
+        torch.cuda.synchronize()
+    assert np.array_equal(xa, xb.cpu().numpy()) and np.array_equal(va, vb.cpu().numpy())

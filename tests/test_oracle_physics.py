@@ -88,7 +88,7 @@ def test_viscous_term_is_nu_laplacian(orc):
 
 
 def test_delta_diffusion_is_laplacian_of_density(orc):
-    """Molteni-Colagrossi term: D_i ~ delta H c0 lap(rho) for a smooth density field."""
+    """Molteni-Colagrossi term: D_i ~ delta h c0 lap(rho), h = H/2, for a smooth density field."""
     dx, x = lattice(64, 2)
     H = 4 * dx
     p = params(H=H, nu=0.0, delta=0.1, c0=10.0, eps=1e-6)
@@ -97,7 +97,7 @@ def test_delta_diffusion_is_laplacian_of_density(orc):
     s = scene(p, x, rho=rho, mass=np.full(len(x), dx * dx))
     r = orc.rates(s)
     lap = -4 * np.pi ** 2 * kappa * np.cos(2 * np.pi * x[:, 0])
-    expect = 0.1 * H * 10.0 * lap
+    expect = 0.1 * (0.5 * H) * 10.0 * lap
     err = np.abs(r["drho"] - expect).max() / np.abs(expect).max()
     assert err < 0.015
 
