@@ -24,7 +24,6 @@ namespace sph {
 
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint32_t kWallBit = 0x80000000u;
-constexpr int kListCap = 48;  // neighbour-list entries per lane between drains
 
 // Per-scene parameters as the kernels read them (one entry per packed scene).
 struct DevSeg {
@@ -189,6 +188,62 @@ __device__ bool exact_pair(const DevSeg& s, const Arrays& arr, int i, int j) {
   return d2 < s.H2_d;
 }
 
+// ---------------------------------------------------------------- particle records
+template <int D>
+struct PD {
+  float x[D], v[D], rho, p, V, m;
+};
+
+template <int D>
+__device__ __forceinline__ PD<D> load_pd(const Arrays& a, int j) {
+  PD<D> r;
+  float4 A = __ldg(a.A + j), B = __ldg(a.B + j);
+  if (D == 2) {
+    r.x[0] = A.x; r.x[1] = A.y; r.v[0] = A.z; r.v[1] = A.w;
+    r.rho = B.x; r.p = B.y; r.V = B.z; r.m = B.w;
+  } else {
+    float2 C = __ldg(a.C + j);
+    r.x[0] = A.x; r.x[1] = A.y; r.x[2] = A.z; r.V = A.w;
+    r.v[0] = B.x; r.v[1] = B.y; r.v[2] = B.z; r.p = B.w;
+    r.rho = C.x; r.m = C.y;
+  }
+  return r;
+}
+
+template <int D>
+__device__ __forceinline__ void store_pd(const Arrays& a, int j, const PD<D>& r) {
+  if (D == 2) {
+    a.A[j] = make_float4(r.x[0], r.x[1], r.v[0], r.v[1]);
+    a.B[j] = make_float4(r.rho, r.p, r.V, r.m);
+  } else {
+    a.A[j] = make_float4(r.x[0], r.x[1], r.x[2], r.V);
+    a.B[j] = make_float4(r.v[0], r.v[1], r.v[2], r.p);
+    a.C[j] = make_float2(r.rho, r.m);
+  }
+}
+
+// separation r = mimg(x_i - x_j) on folded positions.  Across a periodic edge the box length
+// is taken off the coordinate near the upper edge first (x - L is exact there), so the image
+// separation carries one rounding, as an interior one does.
+template <int D>
+__device__ __forceinline__ float separation(const DevSeg& s, const float* xi, const float* xj, float* r) {
+  float r2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    float d = xi[k] - xj[k];
+    if ((s.periodic_mask >> k) & 1) {
+      const float hL = 0.5f * s.L[k];
+      if (d > hL) d = (xi[k] - s.L[k]) - xj[k];
+      else if (d < -hL) d = xi[k] - (xj[k] - s.L[k]);
+    }
+    r[k] = d;
+    r2 = fmaf(d, d, r2);
+  }
+  return r2;
+}
+
+__device__ __forceinline__ float safe_q(float r2, float invH) { return r2 * rsqrtf(fmaxf(r2, 1e-30f)) * invH; }
+
 // ---------------------------------------------------------------- traversal
 // Cell coordinates of a global key inside its scene.
 __device__ __forceinline__ void key_coords(const DevSeg& s, uint32_t key, int* c) {
@@ -197,118 +252,6 @@ __device__ __forceinline__ void key_coords(const DevSeg& s, uint32_t key, int* c
   int rest = local / s.n[0];
   c[1] = rest % s.n[1];
   c[2] = rest / s.n[1];
-}
-
-// Warp-cooperative traversal.  A warp owns 32 consecutive sorted particles.  Lanes that sit
-// in the same cell line (same scene, same y[,z] cell row) form a group; for each group the
-// warp walks the union of the neighbouring lines' column ranges [cx_min-1, cx_max+1] once,
-// every lane testing the same candidate (broadcast loads).  In-radius candidates go to a
-// per-lane list in shared memory; when any list fills up, each lane evaluates its own list
-// (Body::pair).  Candidates outside a lane's own 3^d cells fail the cut-off test, so the
-// union is exact.  With EXACT the FP32 test is confirmed in FP64 inside a guard band
-// (bit-exact pair sets); otherwise r^2 < H^2 in FP32 decides (pairs that differ lie within
-// a relative 1e-4 of the cut-off, where W and its derivatives vanish to O(1e-13) or less).
-template <int D, bool EXACT, class Body>
-__device__ __forceinline__ void traverse(const DevSeg* __restrict__ segs, const float4* __restrict__ A,
-                                         const Arrays& arr, const uint32_t* __restrict__ keys,
-                                         const int* __restrict__ cell_off, int i, bool active, int seg,
-                                         uint32_t* __restrict__ list, Body& body) {
-  const int lane = threadIdx.x & 31;
-  float xi[3] = {0.f, 0.f, 0.f};
-  int ci[3] = {0, 0, 0};
-  uint32_t line_id = 0xffffffffu;
-  if (active) {
-    load_pos<D>(A, i, xi);
-    key_coords(segs[seg], keys[i], ci);
-    line_id = ((uint32_t)seg << 20) | (uint32_t)(ci[1] + ci[2] * segs[seg].n[1]);
-  }
-  uint32_t pending = __ballot_sync(kFull, active);
-  int cnt = 0;
-  auto drain = [&]() {
-    for (int t = 0; t < cnt; ++t) body.pair(list[t * 32]);
-    cnt = 0;
-  };
-  while (pending) {
-    const int leader = __ffs(pending) - 1;
-    const uint32_t gl = __shfl_sync(kFull, line_id, leader);
-    const bool mine = active && line_id == gl;
-    pending &= ~__ballot_sync(kFull, mine);
-    const int gseg = __shfl_sync(kFull, seg, leader);
-    const DevSeg& s = segs[gseg];
-    const int cxmin = __reduce_min_sync(kFull, mine ? ci[0] : 0x7fffffff);
-    const int cxmax = __reduce_max_sync(kFull, mine ? ci[0] : -1);
-    const int gy = __shfl_sync(kFull, ci[1], leader);
-    const int gz = __shfl_sync(kFull, ci[2], leader);
-    const float H2 = s.H2;
-    const int nx = s.n[0], ny = s.n[1], nz = s.n[2];
-    const bool perx = s.periodic_mask & 1, pery = (s.periodic_mask >> 1) & 1, perz = (s.periodic_mask >> 2) & 1;
-    const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
-    for (int dz = zlo; dz <= zhi; ++dz) {
-      int cz = gz + dz;
-      float sz = 0.f;
-      if (D == 3) {
-        if (cz < 0) { if (!perz) continue; cz += nz; sz = -s.L[2]; }
-        else if (cz >= nz) { if (!perz) continue; cz -= nz; sz = s.L[2]; }
-      }
-      for (int dy = -1; dy <= 1; ++dy) {
-        int cy = gy + dy;
-        float sy = 0.f;
-        if (cy < 0) { if (!pery) continue; cy += ny; sy = -s.L[1]; }
-        else if (cy >= ny) { if (!pery) continue; cy -= ny; sy = s.L[1]; }
-        const int row = s.cell_base + (cz * ny + cy) * nx;
-        // up to three column ranges: left wrap, main, right wrap
-        for (int part = 0; part < 3; ++part) {
-          int c0, c1;
-          float sx = 0.f;
-          if (part == 0) {
-            if (!(perx && cxmin - 1 < 0)) continue;
-            c0 = c1 = nx - 1;
-            sx = -s.L[0];
-          } else if (part == 1) {
-            c0 = max(cxmin - 1, 0);
-            c1 = min(cxmax + 1, nx - 1);
-          } else {
-            if (!(perx && cxmax + 1 > nx - 1)) continue;
-            c0 = c1 = 0;
-            sx = s.L[0];
-          }
-          // cell offsets are monotone by construction; the clamp keeps every read in bounds
-          const int jb = max(cell_off[row + c0], s.p0), je = min(cell_off[row + c1 + 1], s.p1);
-          const float px = xi[0] - sx, py = xi[1] - sy, pz = xi[2] - sz;
-          for (int j0 = jb; j0 < je; j0 += 8) {
-            if (__any_sync(kFull, cnt > kListCap - 8)) drain();
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int j = j0 + u;
-              if (j < je) {
-                float pj[3];
-                load_pos<D>(A, j, pj);
-                float dx = px - pj[0], dy2 = py - pj[1];
-                float r2 = fmaf(dy2, dy2, dx * dx);
-                if (D == 3) {
-                  float dz2 = pz - pj[2];
-                  r2 = fmaf(dz2, dz2, r2);
-                }
-                bool in;
-                if (EXACT) {
-                  in = mine && j != i && r2 < s.band_hi;
-                  if (in && r2 >= s.band_lo) in = exact_pair<D>(s, arr, i, j);
-                } else {
-                  in = mine && j != i && r2 < H2;
-                }
-                if (in) {
-                  list[cnt * 32] = (uint32_t)j;
-                  ++cnt;
-                }
-              }
-            }
-          }
-        }
-      }
-    }
-  }
-  drain();
-  (void)lane;
 }
 
 // Deterministic block reduction of a double (fixed shuffle tree, then warps in order).

@@ -1,4 +1,4 @@
-// Launch interface of the WCSPH kernels (host side of sph_kernels.cu).
+// Launch interface of the element-wise and sorting kernels (host side of sph_kernels.cu).
 #pragma once
 #include "sph_device.cuh"
 
@@ -20,13 +20,11 @@ struct RateOut {
   float* a;
   float* drho;
   float* rho;
-  const int* orig_base;      // first original row of each scene in the outputs
+  const int* orig_base;      // first fluid row of each scene in the outputs
 };
 
-cudaError_t configure_kernels();
 int sort_scratch_words(int N);
-size_t trav_smem();
-
+void launch_exclusive_scan(uint32_t* a, int n, uint32_t* sums, cudaStream_t st);
 template <int D>
 void launch_keys(const DevSeg* segs, int N, const Arrays& a, uint32_t* keys, uint32_t* vals, cudaStream_t st);
 void launch_sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, int N, int shift,
@@ -35,17 +33,6 @@ void launch_cell_offsets(const uint32_t* keys, int N, int C, int* off, cudaStrea
 template <int D>
 void launch_permute(const DevSeg* segs, int N, const uint32_t* perm, const Arrays& in, const Arrays& out,
                     cudaStream_t st);
-template <int D, int KERN>
-void launch_walls(const TravArgs& t, cudaStream_t st);
-template <int D, int KERN>
-void launch_density(const TravArgs& t, cudaStream_t st);
-template <int D, int KERN>
-void launch_sweep(const TravArgs& t, const Arrays& out, cudaStream_t st);
-template <int D, int KERN>
-void launch_rates(const TravArgs& t, const RateOut& ro, cudaStream_t st);
-template <int D>
-void launch_pairs(const TravArgs& t, int32_t* pi, int32_t* pj, unsigned long long* count, long long cap,
-                  cudaStream_t st);
 template <int D>
 void launch_upload(const DevSeg* segs, int seg, int n, int nf, int p0, const float* x, const float* v,
                    const float* rho, const float* mass, const Arrays& a, cudaStream_t st);
@@ -54,12 +41,8 @@ void launch_download(int N, const Arrays& a, const int* orig_base, float* x, flo
 template <int D>
 void launch_adj_seed(const DevSeg* segs, int N, const Arrays& fw, const float4* XB, const float4* VB, float4* S,
                      float* Pp, cudaStream_t st);
-template <int D, int KERN>
-int launch_adj_sweep(const TravArgs& t, const float4* S, const float* Pp, const float4* XBin, const float4* VBin,
-                     float4* XBout, float4* VBout, double* nu_partial, cudaStream_t st);
 void launch_adj_unpermute(int N, const uint32_t* perm, const float4* XBin, const float4* VBin, float4* XBout,
                           float4* VBout, cudaStream_t st);
-void launch_sum_partials(const double* part, int n, double* acc, cudaStream_t st);
 template <int D>
 void launch_adj_load(int N, const uint2* meta, const int* orig_base, const float* xb, const float* vb,
                      const float* rb, float4* XB, float4* VB, cudaStream_t st);

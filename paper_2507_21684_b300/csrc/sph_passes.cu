@@ -1,0 +1,767 @@
+// Neighbour passes of the WCSPH step on the cell-block tiles (sph_tiles.cuh):
+//   tile table      (built after every rebuild from the cell offsets)
+//   walls           Shepard extrapolation of the fluid pressure onto wall particles
+//   density         summation density rho_i = sum_j m_j W_ij            (Sec. 2.3)
+//   sweep           continuity + delta diffusion, Tait pressure, viscosity, gravity, and the
+//                   kick-drift epilogue (Sec. 2.3, Sec. 3.4); also the rate-only evaluation
+//   pairs           exact pair export (FP64 predicate in a guard band)
+//   adjoint sweep   vector-Jacobian product of one step, gathered per particle (Sec. 2.2)
+#include "sph_passes.cuh"
+
+namespace sph {
+
+// ================================================================== tile table
+// Tiles per cell line: ceil(count / TP); exclusive scan over lines; emit (p0, p1, line, seg).
+template <int D>
+__global__ void k_tile_count(const DevSeg* __restrict__ segs, int S, const int* __restrict__ line_base, int n_lines,
+                             const int* __restrict__ cell_off, uint32_t* __restrict__ counts) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n_lines) return;
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (line_base[mid] <= l) lo = mid; else hi = mid - 1;
+  }
+  const DevSeg& s = segs[lo];
+  const int first = s.cell_base + (l - line_base[lo]) * s.n[0];
+  const int cnt = cell_off[first + s.n[0]] - cell_off[first];
+  counts[l] = (uint32_t)((cnt + TileCfg<D>::TP - 1) / TileCfg<D>::TP);
+}
+
+template <int D>
+__global__ void k_tile_emit(const DevSeg* __restrict__ segs, int S, const int* __restrict__ line_base, int n_lines,
+                            const int* __restrict__ cell_off, const uint32_t* __restrict__ base,
+                            const uint32_t* __restrict__ counts_copy, Tile* __restrict__ tiles, int* __restrict__ ntiles) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n_lines) return;
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (line_base[mid] <= l) lo = mid; else hi = mid - 1;
+  }
+  const DevSeg& s = segs[lo];
+  const int first = s.cell_base + (l - line_base[lo]) * s.n[0];
+  const int p0 = cell_off[first], p1 = cell_off[first + s.n[0]];
+  const int b = (int)base[l];
+  const int nt = (int)counts_copy[l];
+  for (int k = 0; k < nt; ++k) {
+    Tile t;
+    t.p0 = p0 + k * TileCfg<D>::TP;
+    t.p1 = min(p1, t.p0 + TileCfg<D>::TP);
+    t.line = l;
+    t.seg = lo;
+    tiles[b + k] = t;
+  }
+  if (l == n_lines - 1) *ntiles = b + nt;
+}
+
+// ================================================================== staged particle data
+template <int D, int E>
+__device__ __forceinline__ PD<D> smem_pd(const TileSmem<D, E>& sm, int k) {
+  PD<D> r;
+  const float4 A = sm.A[k], B = sm.B[k];
+  if (D == 2) {
+    r.x[0] = A.x; r.x[1] = A.y; r.v[0] = A.z; r.v[1] = A.w;
+    r.rho = B.x; r.p = B.y; r.V = B.z; r.m = B.w;
+  } else {
+    const float2 C = sm.C[k];
+    r.x[0] = A.x; r.x[1] = A.y; r.x[2] = A.z; r.V = A.w;
+    r.v[0] = B.x; r.v[1] = B.y; r.v[2] = B.z; r.p = B.w;
+    r.rho = C.x; r.m = C.y;
+  }
+  return r;
+}
+
+// Candidate gathering of one target (this thread = one of LANES for the target): its own 3^d
+// cells in shared memory, split across the LANES threads, hits collected in a per-thread list and
+// evaluated by body.pair(pj, extra, pp, j_global).  Returns the number of pairs evaluated.
+// SELF: 0 = exclude r^2 == 0 (gradient terms vanish there anyway), 1 = exclude by index,
+// 2 = exact FP64 predicate in the guard band (pair export).
+template <int D, int E, int SELF, class Body>
+__device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s, const Arrays& a, int i, int ccol,
+                                             const float* xt0, Body& body) {
+  using Cfg = TileCfg<D>;
+  constexpr int CAP = Cfg::CAP;
+  const int lane = threadIdx.x % Cfg::LANES;
+  unsigned short* list = sm.list + threadIdx.x;
+  int cnt = 0, npair = 0;
+  const float H2 = s.H2;
+  auto drain = [&]() {
+    for (int e = 0; e < cnt; ++e) {
+      const int k = list[e * Cfg::THREADS];
+      const PD<D> pj = smem_pd<D, E>(sm, k);
+      float4 ex = make_float4(0.f, 0.f, 0.f, 0.f);
+      float pp = 0.f;
+      if (E > 0) ex = sm.E[k];
+      if (E > 1) pp = sm.E[CAP + k].x;
+      body.pair(pj, ex, pp, sm.gidx[k]);
+    }
+    npair += cnt;
+    cnt = 0;
+  };
+#pragma unroll 1
+  for (int l = 0; l < Cfg::NL; ++l) {
+    if (sm.linecell[l] < 0) continue;
+    int lo, mid, hi;
+    target_runs<D, E>(sm, l, ccol, s.n[0], lo, mid, hi);
+    float tx = xt0[0];
+    const float ty = xt0[1] - sm.tshift[l][1];
+    const float tz = (D == 3) ? xt0[2] - sm.tshift[l][2] : 0.f;
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      const int b = part == 0 ? lo : mid, en = part == 0 ? mid : hi;
+      if (part == 1) {
+        if (b >= en) break;
+        tx -= s.L[0];
+      }
+      for (int k = b + lane; k < en; k += Cfg::LANES) {
+        const float4 P = sm.A[k];
+        const float dx = tx - P.x, dy = ty - P.y;
+        float r2 = fmaf(dy, dy, dx * dx);
+        if (D == 3) {
+          const float dz = tz - P.z;
+          r2 = fmaf(dz, dz, r2);
+        }
+        bool in;
+        if (SELF == 2) {
+          in = r2 < s.band_hi && sm.gidx[k] != i;
+          if (in && r2 >= s.band_lo) in = exact_pair<D>(s, a, i, sm.gidx[k]);
+        } else if (SELF == 1) {
+          in = r2 < H2 && sm.gidx[k] != i;
+        } else {
+          in = r2 < H2 && r2 > 0.f;
+        }
+        if (in) {
+          list[cnt * Cfg::THREADS] = (unsigned short)k;
+          if (++cnt == Cfg::LIST) drain();
+        }
+      }
+    }
+  }
+  drain();
+  return npair;
+}
+
+// Fallback for tiles whose staged region does not fit: the target's own 3^d cells straight from
+// global memory, one thread per target (the caller lets only lane 0 of the group do this).
+template <int D, int SELF, class Body>
+__device__ int gather_global(const DevSeg& s, const Arrays& a, const uint32_t* __restrict__ keys,
+                             const int* __restrict__ cell_off, const float4* __restrict__ extra0,
+                             const float* __restrict__ extra1, int i, const float* xi, Body& body) {
+  int c[3];
+  key_coords(s, keys[i], c);
+  int npair = 0;
+  const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
+  for (int oz = zlo; oz <= zhi; ++oz)
+    for (int oy = -1; oy <= 1; ++oy)
+      for (int ox = -1; ox <= 1; ++ox) {
+        int cc[3] = {c[0] + ox, c[1] + oy, c[2] + oz};
+        bool skip = false;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          if (cc[k] < 0 || cc[k] >= s.n[k]) {
+            if (!((s.periodic_mask >> k) & 1)) skip = true;
+            cc[k] = (cc[k] + s.n[k]) % s.n[k];
+          }
+        }
+        if (skip) continue;
+        const int cell = s.cell_base + (cc[2] * s.n[1] + cc[1]) * s.n[0] + cc[0];
+        for (int j = cell_off[cell]; j < cell_off[cell + 1]; ++j) {
+          const PD<D> pj = load_pd<D>(a, j);
+          float r[D];
+          const float r2 = separation<D>(s, xi, pj.x, r);
+          bool in;
+          if (SELF == 2) {
+            in = j != i && r2 < s.band_hi;
+            if (in && r2 >= s.band_lo) in = exact_pair<D>(s, a, i, j);
+          } else if (SELF == 1) {
+            in = j != i && r2 < s.H2;
+          } else {
+            in = r2 < s.H2 && r2 > 0.f;
+          }
+          if (in) {
+            float4 ex = extra0 ? __ldg(extra0 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float pp = extra1 ? __ldg(extra1 + j) : 0.f;
+            body.pair(pj, ex, pp, j);
+            ++npair;
+          }
+        }
+      }
+  return npair;
+}
+
+// sum over the LANES threads of one target (all threads of the warp call this)
+template <int LANES>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+template <int LANES>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Common skeleton of a tiled pass: for each tile, stage, gather per target, reduce, epilogue.
+// Body must provide: init(s, me, i), pair(...), reduce<LANES>(), finish(...) via the Pass.
+template <int D, int E, int SELF, class Pass>
+__device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restrict__ tiles, const int* __restrict__ ntiles,
+                                          const float4* __restrict__ extra0, const float* __restrict__ extra1,
+                                          Pass& pass) {
+  using Cfg = TileCfg<D>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TileSmem<D, E>& sm = *reinterpret_cast<TileSmem<D, E>*>(smraw);
+  const int nt = *ntiles;
+  const int tgt = threadIdx.x / Cfg::LANES;
+  const int lane = threadIdx.x % Cfg::LANES;
+  long long pairs_cta = 0;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const Tile T = tiles[ti];
+    const DevSeg& s = t.segs[T.seg];
+    const bool staged = stage_tile<D, E>(sm, s, T, t.a, t.keys, t.cell_off, extra0, extra1);
+    const int i = T.p0 + tgt;
+    const bool valid = i < T.p1;
+    typename Pass::Body body;
+    bool active = false;
+    int ccol = 0;
+    float xi[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+      active = pass.init(body, s, i);
+      const float4 A = __ldg(t.a.A + i);
+      xi[0] = A.x; xi[1] = A.y; xi[2] = A.z;
+      int c[3];
+      key_coords(s, t.keys[i], c);
+      ccol = c[0] - (staged ? sm.colbase : 0);
+    }
+    int np = 0;
+    if (active) {
+      if (staged)
+        np = gather_staged<D, E, SELF>(sm, s, t.a, i, ccol, xi, body);
+      else if (lane == 0)
+        np = gather_global<D, SELF>(s, t.a, t.keys, t.cell_off, extra0, extra1, i, xi, body);
+    }
+    __syncwarp();
+    body.template reduce<Cfg::LANES>();
+    if (valid && lane == 0) pass.finish(body, s, i);
+    pairs_cta += np;
+    __syncthreads();  // shared memory is restaged for the next tile
+  }
+  if (t.pair_count) {
+    long long v = pairs_cta;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(t.pair_count, (unsigned long long)v);
+  }
+}
+
+// ================================================================== walls
+template <int D, int KERN>
+struct WallPass {
+  struct Body {
+    const DevSeg* s;
+    float xi[D];
+    float sW, sp, sh;
+    __device__ __forceinline__ void pair(const PD<D>& pj, float4, float, int) {
+      if (pj.m < 0.f) return;  // wall neighbour
+      float r[D];
+      const float r2 = separation<D>(*s, xi, pj.x, r);
+      const float W = s->Kw * kern_w<KERN>(safe_q(r2, s->invH));
+      float gr = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) gr = fmaf(s->g[k], r[k], gr);
+      sW += W;
+      sp = fmaf(pj.p, W, sp);
+      sh = fmaf(pj.rho * gr, W, sh);
+    }
+    template <int L>
+    __device__ __forceinline__ void reduce() {
+      sW = group_sum<L>(sW);
+      sp = group_sum<L>(sp);
+      sh = group_sum<L>(sh);
+    }
+  };
+  Arrays a;
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
+    b.s = &s;
+    b.sW = b.sp = b.sh = 0.f;
+    const uint2 m = a.meta[i];
+    const float4 A = __ldg(a.A + i);
+    b.xi[0] = A.x; b.xi[1] = A.y;
+    if (D == 3) b.xi[2] = A.z;
+    return (m.x & kWallBit) != 0;
+  }
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i) {
+    if (!(a.meta[i].x & kWallBit)) return;
+    const float pw = b.sW > 0.f ? (b.sp + b.sh) / b.sW : 0.f;
+    const float rw = tait_rho(s, pw);
+    PD<D> me = load_pd<D>(a, i);
+    me.rho = rw;
+    me.p = pw;
+    me.V = fabsf(me.m) / rw;
+    store_pd<D>(a, i, me);
+  }
+};
+
+// ================================================================== density
+template <int D, int KERN>
+struct DensityPass {
+  struct Body {
+    const DevSeg* s;
+    float xi[D];
+    double rho;
+    __device__ __forceinline__ void pair(const PD<D>& pj, float4, float, int) {
+      float r[D];
+      const float r2 = separation<D>(*s, xi, pj.x, r);
+      rho += (double)(fabsf(pj.m) * (s->Kw * kern_w<KERN>(safe_q(r2, s->invH))));
+    }
+    template <int L>
+    __device__ __forceinline__ void reduce() { rho = group_sum<L>(rho); }
+  };
+  Arrays a;
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
+    b.s = &s;
+    b.rho = 0.0;
+    const float4 A = __ldg(a.A + i);
+    b.xi[0] = A.x; b.xi[1] = A.y;
+    if (D == 3) b.xi[2] = A.z;
+    return !(a.meta[i].x & kWallBit);
+  }
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i) {
+    if (a.meta[i].x & kWallBit) return;
+    PD<D> me = load_pd<D>(a, i);
+    const double rho = b.rho + (double)(me.m * s.Kw);  // self term, w(0) = 1
+    const float e = (float)((rho - (double)s.rho0) / (double)s.rho0);
+    me.rho = (float)rho;
+    me.p = s.B * expm1f(s.gamma * log1pf(e));
+    me.V = me.m / me.rho;
+    store_pd<D>(a, i, me);
+    Cold c = load_cold<D>(a, i);
+    c.rlo = (float)(rho - (double)me.rho);
+    store_cold<D>(a, i, c);
+  }
+};
+
+// ================================================================== fused sweep
+// a_i    = (1/rho_i) sum_j V_j gK (Cv w s - (p_i + p_j)) r + g
+// drho_i = rho_i sum_j V_j gK w - 2 Cdel sum_j V_j gK (rho_j - rho_i) r^2 s
+// (r = x_i - x_j, grad_i W_ij = gK r, w = (v_i - v_j).r, s = 1/(r^2 + eps h^2),
+//  Cv = 2(d+2) nu rho0, Cdel = delta h c0): the paper's terms regrouped per pair.
+template <int D, int KERN, bool INTEGRATE>
+struct SweepPass {
+  struct Body {
+    const DevSeg* s;
+    float xi[D], vi[D], rho_i, p_i;
+    float acc[D], c1, c2;
+    __device__ __forceinline__ void pair(const PD<D>& pj, float4, float, int) {
+      const DevSeg& c = *s;
+      float r[D];
+      const float r2 = separation<D>(c, xi, pj.x, r);
+      const float q = safe_q(r2, c.invH);
+      const float gK = c.Kg * kern_gt<KERN>(q);
+      float w = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) w = fmaf(vi[k] - pj.v[k], r[k], w);
+      const float sd = __frcp_rn(r2 + c.eH2);
+      const float VgK = pj.V * gK;
+      const float tt = VgK * fmaf(c.Cv * w, sd, -(p_i + pj.p));
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] = fmaf(tt, r[k], acc[k]);
+      c1 = fmaf(VgK, w, c1);
+      c2 = fmaf(VgK * (pj.rho - rho_i), r2 * sd, c2);
+    }
+    template <int L>
+    __device__ __forceinline__ void reduce() {
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] = group_sum<L>(acc[k]);
+      c1 = group_sum<L>(c1);
+      c2 = group_sum<L>(c2);
+    }
+  };
+  Arrays a, out;
+  RateOut ro;
+  int* status;
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
+    b.s = &s;
+    const PD<D> me = load_pd<D>(a, i);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      b.xi[k] = me.x[k];
+      b.vi[k] = me.v[k];
+      b.acc[k] = 0.f;
+    }
+    b.rho_i = me.rho;
+    b.p_i = me.p;
+    b.c1 = b.c2 = 0.f;
+    return me.m > 0.f;  // fluid
+  }
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i) {
+    PD<D> me = load_pd<D>(a, i);
+    const uint2 m = a.meta[i];
+    const bool fluid = me.m > 0.f;
+    float acc_a[D];
+    const float inv_rho = 1.f / me.rho;
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc_a[k] = fmaf(b.acc[k], inv_rho, s.g[k]);
+    const float drho = fmaf(me.rho, b.c1, -2.f * s.Cdel * b.c2);
+    if (!INTEGRATE) {
+      if (fluid) {
+        const int o = (int)(m.x & ~kWallBit) + ro.orig_base[m.y];
+#pragma unroll
+        for (int k = 0; k < D; ++k) ro.a[(size_t)o * D + k] = acc_a[k];
+        ro.drho[o] = drho;
+        ro.rho[o] = me.rho;
+      }
+      return;
+    }
+    Cold c = load_cold<D>(a, i);
+    if (fluid) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        me.v[k] = fmaf(s.dt, acc_a[k], me.v[k]);
+        ds_add(c.hi[k], c.lo[k], __fmul_rn(s.dt, me.v[k]));
+        me.x[k] = __fadd_rn(__fsub_rn(c.hi[k], c.off[k]), c.lo[k]);
+      }
+      if (s.density_mode == 0) {
+        float rh = me.rho;
+        ds_add(rh, c.rlo, __fmul_rn(s.dt, drho));
+        me.rho = rh;
+        const float e = __fadd_rn(__fsub_rn(rh, s.rho0), c.rlo) / s.rho0;
+        me.p = s.B * expm1f(s.gamma * log1pf(e));
+        me.V = me.m / me.rho;
+      }
+      bool bad = !(me.rho > 0.5f * s.rho0 && me.rho < 2.f * s.rho0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) bad |= !isfinite(c.hi[k]) || !isfinite(me.v[k]);
+      if (bad) atomicOr(status, 1);
+    }
+    store_pd<D>(out, i, me);
+    store_cold<D>(out, i, c);
+    out.meta[i] = m;
+  }
+};
+
+// ================================================================== pair export
+template <int D>
+struct PairPass {
+  struct Body {
+    uint32_t id_i;
+    const uint2* meta;
+    int32_t *pi, *pj;
+    unsigned long long* count;
+    long long cap;
+    __device__ __forceinline__ void pair(const PD<D>&, float4, float, int j) {
+      const unsigned long long k = atomicAdd(count, 1ull);
+      if ((long long)k < cap) {
+        pi[k] = (int32_t)id_i;
+        pj[k] = (int32_t)(meta[j].x & ~kWallBit);
+      }
+    }
+    template <int L>
+    __device__ __forceinline__ void reduce() {}
+  };
+  Arrays a;
+  int32_t *pi, *pj;
+  unsigned long long* count;
+  long long cap;
+  __device__ __forceinline__ bool init(Body& b, const DevSeg&, int i) {
+    b.id_i = a.meta[i].x & ~kWallBit;
+    b.meta = a.meta;
+    b.pi = pi;
+    b.pj = pj;
+    b.count = count;
+    b.cap = cap;
+    return true;
+  }
+  __device__ __forceinline__ void finish(Body&, const DevSeg&, int) {}
+};
+
+// ================================================================== adjoint sweep (Sec. 2.2)
+// For pair (i, j) the step's pair terms add alpha_ab r_ab to a_a and beta_ab to drho_a
+// (a = self, b = other).  With seeds abar = dt vtilde, bbar = dt rhobar' of the self particle,
+// Phi_ab = alpha_ab (abar_a . r_ab) + bbar_a beta_ab; the gather at i adds the derivatives of
+// its own Phi_ij and of the neighbours' Phi_ji with respect to x_i, v_i, rho_i (atomic-free).
+template <int D, int KERN>
+struct AdjPass {
+  struct Body {
+    const DevSeg* s;
+    float xi[D], vi[D], rho_i, p_i, V_i, P_i;
+    float ab_i[D], bb_i;
+    float gx[D], gv[D], grho, gnu;
+    __device__ __forceinline__ void pair(const PD<D>& pj, float4 Sj, float ppj, int) {
+      const DevSeg& c = *s;
+      float ab_j[3], bb_j, P_j;
+      if (D == 2) {
+        ab_j[0] = Sj.x; ab_j[1] = Sj.y; ab_j[2] = 0.f; bb_j = Sj.z; P_j = Sj.w;
+      } else {
+        ab_j[0] = Sj.x; ab_j[1] = Sj.y; ab_j[2] = Sj.z; bb_j = Sj.w; P_j = ppj;
+      }
+      (void)P_j;
+      float r[D], u[D];
+      const float r2 = separation<D>(c, xi, pj.x, r);
+      const float q = safe_q(r2, c.invH);
+      const float gK = c.Kg * kern_gt<KERN>(q);
+      const float hK = c.Kh * kern_ht<KERN>(q);
+      const float sd = __frcp_rn(r2 + c.eH2);
+      float w = 0.f, e_i = 0.f, e_j = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        u[k] = vi[k] - pj.v[k];
+        w = fmaf(u[k], r[k], w);
+        e_i = fmaf(ab_i[k], r[k], e_i);
+        e_j = fmaf(ab_j[k], r[k], e_j);
+      }
+      e_j = -e_j;
+      const float ws = w * sd;
+      const float X = fmaf(c.Cv, ws, -(p_i + pj.p));
+      const float r2s = r2 * sd;
+      const float S1 = hK * r2s + 2.f * gK * sd * (c.eH2 * sd);
+      const float CvsgK = c.Cv * sd * gK;
+      const float XhR = fmaf(X, hK, -2.f * gK * c.Cv * w * sd * sd);
+      float cR, cU, alpha;
+      {  // own term: a = i, b = j
+        const float Vb_ra = pj.V / rho_i;
+        alpha = Vb_ra * gK * X;
+        const float cRb = rho_i * pj.V * hK * w - 2.f * c.Cdel * pj.V * (pj.rho - rho_i) * S1;
+        const float cUb = rho_i * pj.V * gK;
+        cR = e_i * (Vb_ra * XhR) + bb_i * cRb;
+        cU = e_i * (Vb_ra * CvsgK) + bb_i * cUb;
+        grho += e_i * (-pj.V * gK * P_i / rho_i - alpha / rho_i) +
+                bb_i * (pj.V * gK * w + 2.f * c.Cdel * pj.V * gK * r2s);
+        gnu += e_i * Vb_ra * gK * c.dCv_dnu * ws;
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        gx[k] += alpha * ab_i[k] + cR * r[k] + cU * u[k];
+        gv[k] += cU * r[k];
+      }
+      {  // transposed term: a = j, b = i
+        const float Va_rb = V_i / pj.rho;
+        alpha = Va_rb * gK * X;
+        const float beta = pj.rho * V_i * gK * w - 2.f * c.Cdel * V_i * (rho_i - pj.rho) * gK * r2s;
+        const float cRb = pj.rho * V_i * hK * w - 2.f * c.Cdel * V_i * (rho_i - pj.rho) * S1;
+        const float cUb = pj.rho * V_i * gK;
+        cR = e_j * (Va_rb * XhR) + bb_j * cRb;
+        cU = e_j * (Va_rb * CvsgK) + bb_j * cUb;
+        grho += e_j * (-alpha / rho_i - V_i * gK * P_i / pj.rho) + bb_j * (-beta / rho_i - 2.f * c.Cdel * V_i * gK * r2s);
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        gx[k] += -alpha * ab_j[k] + cR * r[k] + cU * u[k];
+        gv[k] += cU * r[k];
+      }
+    }
+    template <int L>
+    __device__ __forceinline__ void reduce() {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        gx[k] = group_sum<L>(gx[k]);
+        gv[k] = group_sum<L>(gv[k]);
+      }
+      grho = group_sum<L>(grho);
+      gnu = group_sum<L>(gnu);
+    }
+  };
+  Arrays a;
+  const float4 *S, *XBin, *VBin;
+  const float* Pp;
+  float4 *XBout, *VBout;
+  float* nu_part;  // per particle viscosity partials (summed deterministically afterwards)
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
+    b.s = &s;
+    const PD<D> me = load_pd<D>(a, i);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      b.xi[k] = me.x[k];
+      b.vi[k] = me.v[k];
+      b.gx[k] = b.gv[k] = 0.f;
+    }
+    b.rho_i = me.rho;
+    b.p_i = me.p;
+    b.V_i = me.V;
+    const float4 Si = S[i];
+    if (D == 2) {
+      b.ab_i[0] = Si.x; b.ab_i[1] = Si.y; b.bb_i = Si.z; b.P_i = Si.w;
+    } else {
+      b.ab_i[0] = Si.x; b.ab_i[1] = Si.y; b.ab_i[2] = Si.z; b.bb_i = Si.w; b.P_i = Pp[i];
+    }
+    b.grho = b.gnu = 0.f;
+    return me.m > 0.f;
+  }
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i) {
+    const float4 xb = XBin[i], vb = VBin[i];
+    const float xbs[3] = {xb.x, xb.y, xb.z}, vbs[3] = {vb.x, vb.y, vb.z};
+    float ox[3] = {0.f, 0.f, 0.f}, ov[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float vt = fmaf(s.dt, xbs[k], vbs[k]);
+      ox[k] = xbs[k] + b.gx[k];
+      ov[k] = vt + b.gv[k];
+    }
+    XBout[i] = make_float4(ox[0], ox[1], ox[2], xb.w + b.grho);
+    VBout[i] = make_float4(ov[0], ov[1], ov[2], 0.f);
+    nu_part[i] = b.gnu;
+  }
+};
+
+// ================================================================== kernels
+template <int D, int KERN>
+__global__ void __launch_bounds__(256) k_walls_t(TravArgs t, const Tile* tiles, const int* ntiles) {
+  WallPass<D, KERN> pass;
+  pass.a = t.a;
+  run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
+}
+template <int D, int KERN>
+__global__ void __launch_bounds__(256) k_density_t(TravArgs t, const Tile* tiles, const int* ntiles) {
+  DensityPass<D, KERN> pass;
+  pass.a = t.a;
+  run_tiles<D, 0, 1>(t, tiles, ntiles, nullptr, nullptr, pass);
+}
+template <int D, int KERN, bool INTEGRATE>
+__global__ void __launch_bounds__(256) k_sweep_t(TravArgs t, const Tile* tiles, const int* ntiles, Arrays out,
+                                                 RateOut ro) {
+  SweepPass<D, KERN, INTEGRATE> pass;
+  pass.a = t.a;
+  pass.out = out;
+  pass.ro = ro;
+  pass.status = t.status;
+  run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
+}
+template <int D>
+__global__ void __launch_bounds__(256) k_pairs_t(TravArgs t, const Tile* tiles, const int* ntiles, int32_t* pi,
+                                                 int32_t* pj, unsigned long long* count, long long cap) {
+  PairPass<D> pass;
+  pass.a = t.a;
+  pass.pi = pi;
+  pass.pj = pj;
+  pass.count = count;
+  pass.cap = cap;
+  run_tiles<D, 0, 2>(t, tiles, ntiles, nullptr, nullptr, pass);
+}
+template <int D, int KERN>
+__global__ void __launch_bounds__(256) k_adj_t(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S,
+                                               const float* Pp, const float4* XBin, const float4* VBin, float4* XBout,
+                                               float4* VBout, float* nu_part) {
+  AdjPass<D, KERN> pass;
+  pass.a = t.a;
+  pass.S = S;
+  pass.Pp = Pp;
+  pass.XBin = XBin;
+  pass.VBin = VBin;
+  pass.XBout = XBout;
+  pass.VBout = VBout;
+  pass.nu_part = nu_part;
+  run_tiles<D, (D == 2 ? 1 : 2), 0>(t, tiles, ntiles, S, D == 2 ? nullptr : Pp, pass);
+}
+
+// Deterministic sum of per-particle float partials into an FP64 accumulator (fixed order).
+__global__ void k_sum_float_partials(const float* __restrict__ part, int n, double* __restrict__ acc) {
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) v += (double)part[k];
+  double tot = block_sum(v, sh);
+  if (threadIdx.x == 0) *acc += tot;
+}
+
+// ================================================================== launchers
+template <int D>
+size_t pass_smem(int extra) {
+  if (extra == 0) return tile_smem_bytes<D, 0>();
+  if (extra == 1) return tile_smem_bytes<D, 1>();
+  return tile_smem_bytes<D, 2>();
+}
+
+static int g_num_sms = 148;
+static int pass_grid(int tiles_upper, int ctas_per_sm) {
+  long long g = (long long)g_num_sms * ctas_per_sm;
+  return (int)std::max<long long>(1, std::min<long long>(g, tiles_upper));
+}
+
+template <int D>
+void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, const int* cell_off, uint32_t* counts,
+                  uint32_t* counts_copy, uint32_t* sums, Tile* tiles, int* ntiles, cudaStream_t st) {
+  const int nb = (n_lines + 255) / 256;
+  k_tile_count<D><<<nb, 256, 0, st>>>(segs, S, line_base, n_lines, cell_off, counts);
+  cudaMemcpyAsync(counts_copy, counts, sizeof(uint32_t) * n_lines, cudaMemcpyDeviceToDevice, st);
+  const int sb = (n_lines + 2047) / 2048;
+  launch_exclusive_scan(counts, n_lines, sums, st);
+  (void)sb;
+  k_tile_emit<D><<<nb, 256, 0, st>>>(segs, S, line_base, n_lines, cell_off, counts, counts_copy, tiles, ntiles);
+}
+
+template <int D, int KERN>
+void launch_walls_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st) {
+  k_walls_t<D, KERN><<<pass_grid(tiles_upper, 4), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles);
+}
+template <int D, int KERN>
+void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st) {
+  k_density_t<D, KERN><<<pass_grid(tiles_upper, 4), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles);
+}
+template <int D, int KERN>
+void launch_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
+                    cudaStream_t st) {
+  k_sweep_t<D, KERN, true><<<pass_grid(tiles_upper, 4), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, out, RateOut{});
+}
+template <int D, int KERN>
+void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const RateOut& ro,
+                    cudaStream_t st) {
+  k_sweep_t<D, KERN, false><<<pass_grid(tiles_upper, 4), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, Arrays{}, ro);
+}
+template <int D>
+void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
+                    unsigned long long* count, long long cap, cudaStream_t st) {
+  k_pairs_t<D><<<pass_grid(tiles_upper, 4), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, pi, pj, count, cap);
+}
+template <int D, int KERN>
+void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* S,
+                  const float* Pp, const float4* XBin, const float4* VBin, float4* XBout, float4* VBout,
+                  float* nu_part, cudaStream_t st) {
+  k_adj_t<D, KERN><<<pass_grid(tiles_upper, 4), 256, pass_smem<D>(D == 2 ? 1 : 2), st>>>(
+      t, tiles, ntiles, S, Pp, XBin, VBin, XBout, VBout, nu_part);
+}
+void launch_sum_float_partials(const float* part, int n, double* acc, cudaStream_t st) {
+  k_sum_float_partials<<<1, 1024, 0, st>>>(part, n, acc);
+}
+
+cudaError_t configure_passes() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+#define SPH_ATTR(fn, bytes)                                                                                    \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes));
+  SPH_ATTR((k_walls_t<2, 0>), pass_smem<2>(0)) SPH_ATTR((k_walls_t<2, 1>), pass_smem<2>(0))
+  SPH_ATTR((k_walls_t<3, 0>), pass_smem<3>(0)) SPH_ATTR((k_walls_t<3, 1>), pass_smem<3>(0))
+  SPH_ATTR((k_density_t<2, 0>), pass_smem<2>(0)) SPH_ATTR((k_density_t<2, 1>), pass_smem<2>(0))
+  SPH_ATTR((k_density_t<3, 0>), pass_smem<3>(0)) SPH_ATTR((k_density_t<3, 1>), pass_smem<3>(0))
+  SPH_ATTR((k_sweep_t<2, 0, true>), pass_smem<2>(0)) SPH_ATTR((k_sweep_t<2, 1, true>), pass_smem<2>(0))
+  SPH_ATTR((k_sweep_t<3, 0, true>), pass_smem<3>(0)) SPH_ATTR((k_sweep_t<3, 1, true>), pass_smem<3>(0))
+  SPH_ATTR((k_sweep_t<2, 0, false>), pass_smem<2>(0)) SPH_ATTR((k_sweep_t<2, 1, false>), pass_smem<2>(0))
+  SPH_ATTR((k_sweep_t<3, 0, false>), pass_smem<3>(0)) SPH_ATTR((k_sweep_t<3, 1, false>), pass_smem<3>(0))
+  SPH_ATTR((k_pairs_t<2>), pass_smem<2>(0)) SPH_ATTR((k_pairs_t<3>), pass_smem<3>(0))
+  SPH_ATTR((k_adj_t<2, 0>), pass_smem<2>(1)) SPH_ATTR((k_adj_t<2, 1>), pass_smem<2>(1))
+  SPH_ATTR((k_adj_t<3, 0>), pass_smem<3>(2)) SPH_ATTR((k_adj_t<3, 1>), pass_smem<3>(2))
+#undef SPH_ATTR
+  return e;
+}
+
+#define SPH_INST_PD(D)                                                                                       \
+  template void launch_tiles<D>(const DevSeg*, int, const int*, int, const int*, uint32_t*, uint32_t*, uint32_t*, \
+                                Tile*, int*, cudaStream_t);                                                   \
+  template void launch_pairs_t<D>(const TravArgs&, const Tile*, const int*, int, int32_t*, int32_t*,          \
+                                  unsigned long long*, long long, cudaStream_t);
+SPH_INST_PD(2)
+SPH_INST_PD(3)
+#define SPH_INST_PDK(D, K)                                                                                   \
+  template void launch_walls_t<D, K>(const TravArgs&, const Tile*, const int*, int, cudaStream_t);          \
+  template void launch_density_t<D, K>(const TravArgs&, const Tile*, const int*, int, cudaStream_t);        \
+  template void launch_sweep_t<D, K>(const TravArgs&, const Tile*, const int*, int, const Arrays&, cudaStream_t); \
+  template void launch_rates_t<D, K>(const TravArgs&, const Tile*, const int*, int, const RateOut&, cudaStream_t); \
+  template void launch_adj_t<D, K>(const TravArgs&, const Tile*, const int*, int, const float4*, const float*,  \
+                                   const float4*, const float4*, float4*, float4*, float*, cudaStream_t);
+SPH_INST_PDK(2, 0)
+SPH_INST_PDK(2, 1)
+SPH_INST_PDK(3, 0)
+SPH_INST_PDK(3, 1)
+
+}  // namespace sph

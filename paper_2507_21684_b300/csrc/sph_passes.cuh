@@ -1,0 +1,31 @@
+// Launch interface of the tiled neighbour passes (host side of sph_passes.cu).
+#pragma once
+#include "sph_kernels.cuh"
+#include "sph_tiles.cuh"
+
+namespace sph {
+
+cudaError_t configure_passes();
+template <int D>
+void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, const int* cell_off, uint32_t* counts,
+                  uint32_t* counts_copy, uint32_t* sums, Tile* tiles, int* ntiles, cudaStream_t st);
+template <int D, int KERN>
+void launch_walls_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st);
+template <int D, int KERN>
+void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st);
+template <int D, int KERN>
+void launch_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
+                    cudaStream_t st);
+template <int D, int KERN>
+void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const RateOut& ro,
+                    cudaStream_t st);
+template <int D>
+void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
+                    unsigned long long* count, long long cap, cudaStream_t st);
+template <int D, int KERN>
+void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* S,
+                  const float* Pp, const float4* XBin, const float4* VBin, float4* XBout, float4* VBout,
+                  float* nu_part, cudaStream_t st);
+void launch_sum_float_partials(const float* part, int n, double* acc, cudaStream_t st);
+
+}  // namespace sph

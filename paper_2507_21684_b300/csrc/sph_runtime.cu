@@ -12,7 +12,6 @@
 #include <vector>
 
 #include "../../include/sph.h"
-#include "sph_kernels.cuh"
 #include "sph_runtime.h"
 
 namespace sph {
@@ -214,6 +213,8 @@ void Scene::leave() {
 Scene::~Scene() {
   if (st) cudaStreamSynchronize(st);
   for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  for (auto g : graph_templates) cudaGraphDestroy(g);
+  for (auto e : event_pool) cudaEventDestroy(e);
   for (auto& e : prof_events) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -287,11 +288,18 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
   if (S >= 4096) einval("at most 4095 scenes per batch");
   static bool configured = false;
   if (!configured) {
-    CK(configure_kernels());
+    CK(configure_passes());
     configured = true;
   }
   nf_total = 0;
   for (int s = 0; s < S; ++s) nf_total += nfs[s];
+  line_base_h.assign(S, 0);
+  n_lines = 0;
+  for (int s = 0; s < S; ++s) {
+    line_base_h[s] = n_lines;
+    n_lines += segs[s].n[1] * segs[s].n[2];
+  }
+  tiles_upper = (D == 2 ? (N + TileCfg<2>::TP - 1) / TileCfg<2>::TP : (N + TileCfg<3>::TP - 1) / TileCfg<3>::TP) + n_lines;
   bits = key_bits(C_tot);
   passes = (bits + 7) / 8;
   if (N > 16384 * 2048) einval("too many particles for the radix sort scratch (max 33554432)");
@@ -312,7 +320,13 @@ void Scene::alloc_all() {
   keys_sorted = kA;
   perm = vA;
   cell_off = (int*)mem.get(sizeof(int) * ((size_t)C_tot + 1));
-  scratch = (uint32_t*)mem.get(4 * (size_t)sort_scratch_words(N));
+  scratch = (uint32_t*)mem.get(4 * (size_t)std::max(sort_scratch_words(N), n_lines + 2048 + 64));
+  line_base = (int*)mem.get(sizeof(int) * S);
+  CK(cudaMemcpyAsync(line_base, line_base_h.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
+  tile_counts = (uint32_t*)mem.get(sizeof(uint32_t) * (size_t)n_lines);
+  tile_counts_copy = (uint32_t*)mem.get(sizeof(uint32_t) * (size_t)n_lines);
+  tiles = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
+  d_ntiles = (int*)mem.get(sizeof(int) * 2);
   d_status = (int*)mem.get(sizeof(int) * 4);
   d_pairs = (unsigned long long*)mem.get(sizeof(unsigned long long) * 2);
   d_nubar = (double*)mem.get(sizeof(double) * 2);
@@ -376,18 +390,40 @@ TravArgs Scene::trav(const Arrays& a, const uint32_t* keys, const int* off) cons
   return t;
 }
 
+cudaEvent_t Scene::take_event() {
+  if (!event_pool.empty()) {
+    cudaEvent_t e = event_pool.back();
+    event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CK(cudaEventCreate(&e));
+  return e;
+}
+
+// Kernel timing: CUDA events on the scene's stream around each timed launch.  Under stream
+// capture the records become event-record nodes of the graph; every replay re-points them
+// at fresh events (cudaGraphExecEventRecordNodeSetEvent), so each launch is timed.
 void Scene::prof_begin(int cls) {
-  if (!profiling || capturing) return;
+  if (!profiling) return;
   ProfEvent e;
   e.cls = cls;
-  CK(cudaEventCreate(&e.a));
-  CK(cudaEventCreate(&e.b));
-  CK(cudaEventRecord(e.a, st));
-  prof_events.push_back(e);
+  e.a = take_event();
+  e.b = take_event();
+  if (capturing) {
+    CK(cudaEventRecordWithFlags(e.a, st, cudaEventRecordExternal));
+    capture_events.push_back(e);
+  } else {
+    CK(cudaEventRecord(e.a, st));
+    prof_events.push_back(e);
+  }
 }
 void Scene::prof_end() {
-  if (!profiling || capturing) return;
-  CK(cudaEventRecord(prof_events.back().b, st));
+  if (!profiling) return;
+  if (capturing)
+    CK(cudaEventRecordWithFlags(capture_events.back().b, st, cudaEventRecordExternal));
+  else
+    CK(cudaEventRecord(prof_events.back().b, st));
 }
 
 // Rebuild: keys of the current order -> stable sort -> cell offsets -> permute `in` into
@@ -422,6 +458,7 @@ std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& o
   }
   launch_cell_offsets(ks, N, C_tot, off_out, st);
   CKL();
+  build_tiles(off_out);
   if (D == 2)
     launch_permute<2>(dseg, N, pm, in, out, st);
   else
@@ -431,13 +468,25 @@ std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& o
   return {ks, pm};
 }
 
+// Tile table of a cell structure (CSR offsets `off`).
+void Scene::build_tiles(const int* off) {
+  uint32_t* sums = scratch + n_lines + 64;
+  if (D == 2)
+    launch_tiles<2>(dseg, S, line_base, n_lines, off, tile_counts, tile_counts_copy, sums, tiles, d_ntiles, st);
+  else
+    launch_tiles<3>(dseg, S, line_base, n_lines, off, tile_counts, tile_counts_copy, sums, tiles, d_ntiles, st);
+  CKL();
+}
+
 void Scene::passes_before_sweep(const TravArgs& t) {
   if (any_walls) {
     prof_begin(2);
     if (D == 2) {
-      if (kern == 0) launch_walls<2, 0>(t, st); else launch_walls<2, 1>(t, st);
+      if (kern == 0) launch_walls_t<2, 0>(t, tiles, d_ntiles, tiles_upper, st);
+      else launch_walls_t<2, 1>(t, tiles, d_ntiles, tiles_upper, st);
     } else {
-      if (kern == 0) launch_walls<3, 0>(t, st); else launch_walls<3, 1>(t, st);
+      if (kern == 0) launch_walls_t<3, 0>(t, tiles, d_ntiles, tiles_upper, st);
+      else launch_walls_t<3, 1>(t, tiles, d_ntiles, tiles_upper, st);
     }
     CKL();
     prof_end();
@@ -445,9 +494,11 @@ void Scene::passes_before_sweep(const TravArgs& t) {
   if (summation) {
     prof_begin(3);
     if (D == 2) {
-      if (kern == 0) launch_density<2, 0>(t, st); else launch_density<2, 1>(t, st);
+      if (kern == 0) launch_density_t<2, 0>(t, tiles, d_ntiles, tiles_upper, st);
+      else launch_density_t<2, 1>(t, tiles, d_ntiles, tiles_upper, st);
     } else {
-      if (kern == 0) launch_density<3, 0>(t, st); else launch_density<3, 1>(t, st);
+      if (kern == 0) launch_density_t<3, 0>(t, tiles, d_ntiles, tiles_upper, st);
+      else launch_density_t<3, 1>(t, tiles, d_ntiles, tiles_upper, st);
     }
     CKL();
     prof_end();
@@ -457,9 +508,11 @@ void Scene::passes_before_sweep(const TravArgs& t) {
 void Scene::sweep(const TravArgs& t, const Arrays& out) {
   prof_begin(0);
   if (D == 2) {
-    if (kern == 0) launch_sweep<2, 0>(t, out, st); else launch_sweep<2, 1>(t, out, st);
+    if (kern == 0) launch_sweep_t<2, 0>(t, tiles, d_ntiles, tiles_upper, out, st);
+    else launch_sweep_t<2, 1>(t, tiles, d_ntiles, tiles_upper, out, st);
   } else {
-    if (kern == 0) launch_sweep<3, 0>(t, out, st); else launch_sweep<3, 1>(t, out, st);
+    if (kern == 0) launch_sweep_t<3, 0>(t, tiles, d_ntiles, tiles_upper, out, st);
+    else launch_sweep_t<3, 1>(t, tiles, d_ntiles, tiles_upper, out, st);
   }
   CKL();
   prof_end();
@@ -501,8 +554,8 @@ void Scene::steps(int n) {
   if (n <= 0) return;
   CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st));
   launches = 0;
-  const int chunk = graph_chunk;
-  if (!use_graphs || profiling || n < chunk) {
+  const int chunk = std::min(graph_chunk, n);
+  if (!use_graphs) {
     for (int k = 0; k < n; ++k) step_once();
     last_steps = n;
     return;
@@ -510,7 +563,7 @@ void Scene::steps(int n) {
   int done = 0;
   long long per_chunk = 0;
   while (n - done >= chunk) {
-    GraphKey key{chunk, cur, cells_valid ? std::min(steps_since_build, interval) : -1};
+    GraphKey key{chunk, cur, cells_valid ? std::min(steps_since_build, interval) : -1, profiling ? 1 : 0};
     auto it = graphs.find(key);
     // capture records the launches of `chunk` steps without running them; the host-side
     // schedule (buffer parity, rebuild counter, sorted-key pointers) advances exactly as in
@@ -529,10 +582,38 @@ void Scene::steps(int n) {
       }
       CK(cudaStreamEndCapture(st, &g));
       capturing = false;
+      // locate the event-record nodes of the timed launches
+      std::vector<GraphProfNode> pn;
+      if (!capture_events.empty()) {
+        size_t nn = 0;
+        CK(cudaGraphGetNodes(g, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+        for (auto& ce : capture_events) {
+          GraphProfNode gn{ce.cls, nullptr, nullptr};
+          for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            CK(cudaGraphNodeGetType(nd, &t));
+            if (t != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev;
+            CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+            if (ev == ce.a) gn.a = nd;
+            if (ev == ce.b) gn.b = nd;
+          }
+          if (gn.a && gn.b) pn.push_back(gn);
+          event_pool.push_back(ce.a);
+          event_pool.push_back(ce.b);
+        }
+        capture_events.clear();
+      }
       cudaGraphExec_t ge;
       CK(cudaGraphInstantiate(&ge, g, 0));
-      cudaGraphDestroy(g);
+      if (pn.empty())
+        cudaGraphDestroy(g);
+      else
+        graph_templates.push_back(g);
       graphs[key] = ge;
+      graph_prof[key] = pn;
       it = graphs.find(key);
       per_chunk = launches - l0;
       graph_launch_count[key] = per_chunk;
@@ -545,6 +626,15 @@ void Scene::steps(int n) {
         advance_schedule();
       }
       launches += graph_launch_count[key];
+    }
+    for (auto& gn : graph_prof[key]) {
+      ProfEvent e;
+      e.cls = gn.cls;
+      e.a = take_event();
+      e.b = take_event();
+      CK(cudaGraphExecEventRecordNodeSetEvent(it->second, gn.a, e.a));
+      CK(cudaGraphExecEventRecordNodeSetEvent(it->second, gn.b, e.b));
+      prof_events.push_back(e);
     }
     CK(cudaGraphLaunch(it->second, st));
     done += chunk;
@@ -606,7 +696,7 @@ void Scene::alloc_tape(int k) {
     }
     Sd = (float4*)mem.get(sizeof(float4) * N);
     Pp = (float*)mem.get(sizeof(float) * N);
-    nu_part = (double*)mem.get(sizeof(double) * ((size_t)(N + 255) / 256 + 1));
+    nu_part = (float*)mem.get(sizeof(float) * (size_t)N);
     alloc_arrays(scratch_arr);
     adj_alloc = true;
   }
@@ -676,18 +766,22 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
       CKL();
       TravArgs t = trav(slot.a, slot.keys, slot.off);
       t.pair_count = nullptr;
+      build_tiles(slot.off);
       prof_begin(4);
-      int nb;
       if (D == 2) {
-        if (kern == 0) nb = launch_adj_sweep<2, 0>(t, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
-        else nb = launch_adj_sweep<2, 1>(t, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        if (kern == 0)
+          launch_adj_t<2, 0>(t, tiles, d_ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        else
+          launch_adj_t<2, 1>(t, tiles, d_ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
       } else {
-        if (kern == 0) nb = launch_adj_sweep<3, 0>(t, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
-        else nb = launch_adj_sweep<3, 1>(t, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        if (kern == 0)
+          launch_adj_t<3, 0>(t, tiles, d_ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        else
+          launch_adj_t<3, 1>(t, tiles, d_ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
       }
       CKL();
       prof_end();
-      launch_sum_partials(nu_part, nb, d_nubar, st);
+      launch_sum_float_partials(nu_part, N, d_nubar, st);
       CKL();
       q = 1 - q;
       if (rebuilt[s]) {
@@ -782,9 +876,11 @@ void Scene::rates(float* a, float* drho, float* rho, int is_dev) {
   CK(cudaMemcpyAsync(d_fluid_base, fbase.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
   ro.orig_base = d_fluid_base;
   if (D == 2) {
-    if (kern == 0) launch_rates<2, 0>(t, ro, st); else launch_rates<2, 1>(t, ro, st);
+    if (kern == 0) launch_rates_t<2, 0>(t, tiles, d_ntiles, tiles_upper, ro, st);
+    else launch_rates_t<2, 1>(t, tiles, d_ntiles, tiles_upper, ro, st);
   } else {
-    if (kern == 0) launch_rates<3, 0>(t, ro, st); else launch_rates<3, 1>(t, ro, st);
+    if (kern == 0) launch_rates_t<3, 0>(t, tiles, d_ntiles, tiles_upper, ro, st);
+    else launch_rates_t<3, 1>(t, tiles, d_ntiles, tiles_upper, ro, st);
   }
   CKL();
   cudaMemcpyKind kind = is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -836,9 +932,9 @@ void Scene::debug_pairs(int64_t* n_pairs, int32_t* pi, int32_t* pj, int64_t cap)
   TravArgs t = trav(buf[cur], keys_sorted, cell_off);
   t.pair_count = nullptr;
   if (D == 2)
-    launch_pairs<2>(t, dpi, dpj, cnt, (long long)c, st);
+    launch_pairs_t<2>(t, tiles, d_ntiles, tiles_upper, dpi, dpj, cnt, (long long)c, st);
   else
-    launch_pairs<3>(t, dpi, dpj, cnt, (long long)c, st);
+    launch_pairs_t<3>(t, tiles, d_ntiles, tiles_upper, dpi, dpj, cnt, (long long)c, st);
   CKL();
   unsigned long long h = 0;
   CK(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -864,8 +960,8 @@ void Scene::timing(int cls, double* ms, int64_t* count) {
       CK(cudaEventElapsedTime(&t, e.a, e.b));
       tot += t;
       ++c;
-      cudaEventDestroy(e.a);
-      cudaEventDestroy(e.b);
+      event_pool.push_back(e.a);
+      event_pool.push_back(e.b);
     } else {
       keep.push_back(e);
     }

@@ -7,7 +7,7 @@
 #include <vector>
 
 #include "../../include/sph.h"
-#include "sph_kernels.cuh"
+#include "sph_passes.cuh"
 
 namespace sph {
 
@@ -41,10 +41,16 @@ struct TapeSlot {
 };
 
 struct GraphKey {
-  int chunk, cur, since;
+  int chunk, cur, since, prof;
   bool operator<(const GraphKey& o) const {
-    return std::tie(chunk, cur, since) < std::tie(o.chunk, o.cur, o.since);
+    return std::tie(chunk, cur, since, prof) < std::tie(o.chunk, o.cur, o.since, o.prof);
   }
+};
+
+// Event-record nodes of a profiled graph: begin/end of one timed launch.
+struct GraphProfNode {
+  int cls;
+  cudaGraphNode_t a, b;
 };
 
 // A scene: one or more packed segments (independent SPH problems) advanced together.
@@ -70,6 +76,13 @@ struct Scene {
   uint32_t* perm = nullptr;
   int* cell_off = nullptr;
   uint32_t* scratch = nullptr;
+  // cell-block tiles of the current cell structure
+  std::vector<int> line_base_h;
+  int* line_base = nullptr;
+  int n_lines = 0, tiles_upper = 0;
+  uint32_t *tile_counts = nullptr, *tile_counts_copy = nullptr;
+  Tile* tiles = nullptr;
+  int* d_ntiles = nullptr;
   int* d_status = nullptr;
   unsigned long long* d_pairs = nullptr;
   double* d_nubar = nullptr;
@@ -83,6 +96,11 @@ struct Scene {
   bool capturing = false;
   std::map<GraphKey, cudaGraphExec_t> graphs;
   std::map<GraphKey, long long> graph_launch_count;
+  std::map<GraphKey, std::vector<GraphProfNode>> graph_prof;
+  std::vector<cudaGraph_t> graph_templates;  // kept alive: profiled graphs address their nodes
+  std::vector<ProfEvent> capture_events;   // events recorded while capturing (profiling)
+  std::vector<cudaEvent_t> event_pool;
+  cudaEvent_t take_event();
   // profiling and counters
   bool profiling = false;
   std::vector<ProfEvent> prof_events;
@@ -98,7 +116,7 @@ struct Scene {
   float4* VB[2] = {nullptr, nullptr};
   float4* Sd = nullptr;
   float* Pp = nullptr;
-  double* nu_part = nullptr;
+  float* nu_part = nullptr;
   Arrays scratch_arr{};
 
   ~Scene();
@@ -117,6 +135,7 @@ struct Scene {
   void prof_end();
   std::pair<uint32_t*, uint32_t*> rebuild(const Arrays& in, const Arrays& out, uint32_t* keys_out,
                                           uint32_t* perm_out, int* off_out);
+  void build_tiles(const int* off);
   void passes_before_sweep(const TravArgs& t);
   void sweep(const TravArgs& t, const Arrays& out);
   bool rebuild_due() const;
