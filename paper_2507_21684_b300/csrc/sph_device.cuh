@@ -44,6 +44,8 @@ struct DevSeg {
   float band_lo, band_hi;  // FP32 r^2 guard band for the exact pair predicate
   double H2_d;
   float nu, pad1;
+  float cs[3];             // cell edge (FP32) of the folded frame
+  float trimR2;            // squared reach used to skip neighbour cells (H + skin/2 + margins)
 };
 
 // ---------------------------------------------------------------- Wendland kernels
@@ -238,6 +240,18 @@ __device__ __forceinline__ float separation(const DevSeg& s, const float* xi, co
     }
     r[k] = d;
     r2 = fmaf(d, d, r2);
+  }
+  return r2;
+}
+
+// r = x_i - x_j for positions already in the same periodic image
+template <int D>
+__device__ __forceinline__ float diff(const float* xi, const float* xj, float* r) {
+  float r2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    r[k] = xi[k] - xj[k];
+    r2 = fmaf(r[k], r[k], r2);
   }
   return r2;
 }

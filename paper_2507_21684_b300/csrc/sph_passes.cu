@@ -6,53 +6,107 @@
 //                   kick-drift epilogue (Sec. 2.3, Sec. 3.4); also the rate-only evaluation
 //   pairs           exact pair export (FP64 predicate in a guard band)
 //   adjoint sweep   vector-Jacobian product of one step, gathered per particle (Sec. 2.2)
+#include <algorithm>
+#include <map>
+
 #include "sph_passes.cuh"
 
 namespace sph {
 
 // ================================================================== tile table
-// Tiles per cell line: ceil(count / TP); exclusive scan over lines; emit (p0, p1, line, seg).
+// Tiles of one cell line are cut at cell boundaries: a tile holds at most TP particles and spans
+// at most TP cells (so its column table fits); a cell with more than TP particles is split into
+// tiles of its own.  One thread per line walks the line's cells twice (count, then emit).
+template <int D, bool EMIT>
+__device__ __forceinline__ int line_tiles(const DevSeg& s, int first, int ll, const int* __restrict__ cell_off,
+                                          Tile* __restrict__ out, int seg, int line) {
+  constexpr int TP = TileCfg<D>::TP;
+  const int nx = s.n[0];
+  int nt = 0;
+  int t_start = -1, t_c0 = 0, t_c1 = 0, t_cnt = 0;
+  auto close = [&]() {
+    if (t_start >= 0) {
+      if (EMIT) {
+        Tile t;
+        t.p0 = t_start;
+        t.p1 = t_start + t_cnt;
+        t.seg = seg;
+        t.line = line;
+        t.cx0 = t_c0;
+        t.cx1 = t_c1;
+        t.cy = ll % s.n[1];
+        t.cz = ll / s.n[1];
+        out[nt] = t;
+      }
+      ++nt;
+      t_start = -1;
+      t_cnt = 0;
+    }
+  };
+  int o0 = cell_off[first];
+  for (int c = 0; c < nx; ++c) {
+    const int o1 = cell_off[first + c + 1];
+    const int n = o1 - o0;
+    if (n > 0) {
+      if (t_start >= 0 && (t_cnt + n > TP || c - t_c0 > TP - 1)) close();
+      if (n > TP) {
+        for (int k = 0; k < n; k += TP) {  // an over-full cell: tiles of its own
+          t_start = o0 + k;
+          t_cnt = min(TP, n - k);
+          t_c0 = t_c1 = c;
+          close();
+        }
+      } else {
+        if (t_start < 0) {
+          t_start = o0;
+          t_c0 = c;
+        }
+        t_cnt += n;
+        t_c1 = c;
+      }
+    }
+    o0 = o1;
+  }
+  close();
+  return nt;
+}
+
+__device__ __forceinline__ int seg_of_line(const int* __restrict__ line_base, int S, int l) {
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (line_base[mid] <= l) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <int D>
 __global__ void k_tile_count(const DevSeg* __restrict__ segs, int S, const int* __restrict__ line_base, int n_lines,
                              const int* __restrict__ cell_off, uint32_t* __restrict__ counts) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n_lines) return;
-  int lo = 0, hi = S - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (line_base[mid] <= l) lo = mid; else hi = mid - 1;
-  }
-  const DevSeg& s = segs[lo];
-  const int first = s.cell_base + (l - line_base[lo]) * s.n[0];
-  const int cnt = cell_off[first + s.n[0]] - cell_off[first];
-  counts[l] = (uint32_t)((cnt + TileCfg<D>::TP - 1) / TileCfg<D>::TP);
+  const int sg = seg_of_line(line_base, S, l);
+  const DevSeg& s = segs[sg];
+  const int ll = l - line_base[sg];
+  const int first = s.cell_base + ll * s.n[0];
+  counts[l] = (uint32_t)line_tiles<D, false>(s, first, ll, cell_off, nullptr, sg, l);
 }
 
 template <int D>
 __global__ void k_tile_emit(const DevSeg* __restrict__ segs, int S, const int* __restrict__ line_base, int n_lines,
-                            const int* __restrict__ cell_off, const uint32_t* __restrict__ base,
-                            const uint32_t* __restrict__ counts_copy, Tile* __restrict__ tiles, int* __restrict__ ntiles) {
+                            const int* __restrict__ cell_off, const uint32_t* __restrict__ keys,
+                            const uint32_t* __restrict__ base, const uint32_t* __restrict__ counts_copy,
+                            Tile* __restrict__ tiles, int* __restrict__ ntiles) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n_lines) return;
-  int lo = 0, hi = S - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (line_base[mid] <= l) lo = mid; else hi = mid - 1;
-  }
-  const DevSeg& s = segs[lo];
-  const int first = s.cell_base + (l - line_base[lo]) * s.n[0];
-  const int p0 = cell_off[first], p1 = cell_off[first + s.n[0]];
+  const int sg = seg_of_line(line_base, S, l);
+  const DevSeg& s = segs[sg];
+  const int ll = l - line_base[sg];
+  const int first = s.cell_base + ll * s.n[0];
   const int b = (int)base[l];
-  const int nt = (int)counts_copy[l];
-  for (int k = 0; k < nt; ++k) {
-    Tile t;
-    t.p0 = p0 + k * TileCfg<D>::TP;
-    t.p1 = min(p1, t.p0 + TileCfg<D>::TP);
-    t.line = l;
-    t.seg = lo;
-    tiles[b + k] = t;
-  }
-  if (l == n_lines - 1) *ntiles = b + nt;
+  line_tiles<D, true>(s, first, ll, cell_off, tiles + b, sg, l);
+  if (l == n_lines - 1) *ntiles = b + (int)counts_copy[l];
+  (void)keys;
 }
 
 // ================================================================== staged particle data
@@ -75,65 +129,109 @@ __device__ __forceinline__ PD<D> smem_pd(const TileSmem<D, E>& sm, int k) {
 // Candidate gathering of one target (this thread = one of LANES for the target): its own 3^d
 // cells in shared memory, split across the LANES threads, hits collected in a per-thread list and
 // evaluated by body.pair(pj, extra, pp, j_global).  Returns the number of pairs evaluated.
+// Neighbour lines and side cells that lie farther than the reach from the target (distance to
+// the cell faces) are skipped.  List entries carry the staged index and, in bits 13..15, which
+// axes take the box length off the target (periodic images on the upper side).
 // SELF: 0 = exclude r^2 == 0 (gradient terms vanish there anyway), 1 = exclude by index,
 // 2 = exact FP64 predicate in the guard band (pair export).
 template <int D, int E, int SELF, class Body>
 __device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s, const Arrays& a, int i, int ccol,
-                                             const float* xt0, Body& body) {
+                                             const float* xt0, const float* face_lo, const float* face_hi,
+                                             Body& body) {
   using Cfg = TileCfg<D>;
   constexpr int CAP = Cfg::CAP;
   const int lane = threadIdx.x % Cfg::LANES;
   unsigned short* list = sm.list + threadIdx.x;
   int cnt = 0, npair = 0;
   const float H2 = s.H2;
+  const float R2 = s.trimR2;
   auto drain = [&]() {
     for (int e = 0; e < cnt; ++e) {
-      const int k = list[e * Cfg::THREADS];
-      const PD<D> pj = smem_pd<D, E>(sm, k);
+      const unsigned code = list[e * Cfg::THREADS];
+      const int k = (int)(code & 0x3ffu);
+      PD<D> pj = smem_pd<D, E>(sm, k);
+      // periodic image of the entry: the target takes off the box length on the flagged axes
+      float xs[D];
+#pragma unroll
+      for (int q = 0; q < D; ++q) xs[q] = xt0[q] - ((code >> (13 + q)) & 1u ? s.L[q] : 0.f);
       float4 ex = make_float4(0.f, 0.f, 0.f, 0.f);
       float pp = 0.f;
       if (E > 0) ex = sm.E[k];
       if (E > 1) pp = sm.E[CAP + k].x;
-      body.pair(pj, ex, pp, sm.gidx[k]);
+      body.pair_at(xs, pj, ex, pp, SELF == 2 ? staged_gidx<D, E>(sm, k) : 0);
     }
     npair += cnt;
     cnt = 0;
   };
+  // squared distances of the target to its own cell's faces (0 if it has drifted past one)
+  float fl[3], fh[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float a0 = q < D ? fmaxf(xt0[q] - face_lo[q], 0.f) : 0.f;
+    const float a1 = q < D ? fmaxf(face_hi[q] - xt0[q], 0.f) : 0.f;
+    fl[q] = a0 * a0;
+    fh[q] = a1 * a1;
+  }
 #pragma unroll 1
   for (int l = 0; l < Cfg::NL; ++l) {
     if (sm.linecell[l] < 0) continue;
-    int lo, mid, hi;
-    target_runs<D, E>(sm, l, ccol, s.n[0], lo, mid, hi);
+    const int dy = (D == 2) ? l - 1 : l % 3 - 1;
+    const int dz = (D == 2) ? 0 : l / 3 - 1;
+    const float dyz = (dy < 0 ? fl[1] : dy > 0 ? fh[1] : 0.f) + (dz < 0 ? fl[2] : dz > 0 ? fh[2] : 0.f);
+    if (dyz >= R2) continue;
+    const bool need_left = fl[0] + dyz < R2, need_right = fh[0] + dyz < R2;
+    constexpr int NCOL = TileSmem<D, E>::NCOL;
+    const int ncols = sm.ncols;
+    const int lo = sm.colstart[l * NCOL + (need_left ? ccol - 1 : ccol)];
+    const int endc = need_right ? ccol + 2 : ccol + 1;
+    const int hi = sm.colstart[l * NCOL + endc];
+    (void)ncols;
+    const bool wrap_right = need_right && (sm.colbase + ccol + 1 >= s.n[0]);
+    const int mid = wrap_right ? sm.colstart[l * NCOL + ccol + 1] : hi;
+    const unsigned lshift = (sm.tshift[l][1] != 0.f ? (1u << 14) : 0u) | (D == 3 && sm.tshift[l][2] != 0.f ? (1u << 15) : 0u);
     float tx = xt0[0];
     const float ty = xt0[1] - sm.tshift[l][1];
     const float tz = (D == 3) ? xt0[2] - sm.tshift[l][2] : 0.f;
 #pragma unroll 1
     for (int part = 0; part < 2; ++part) {
       const int b = part == 0 ? lo : mid, en = part == 0 ? mid : hi;
+      unsigned shift_bits = lshift;
       if (part == 1) {
         if (b >= en) break;
         tx -= s.L[0];
+        shift_bits |= 1u << 13;
       }
-      for (int k = b + lane; k < en; k += Cfg::LANES) {
-        const float4 P = sm.A[k];
-        const float dx = tx - P.x, dy = ty - P.y;
-        float r2 = fmaf(dy, dy, dx * dx);
-        if (D == 3) {
-          const float dz = tz - P.z;
-          r2 = fmaf(dz, dz, r2);
-        }
-        bool in;
-        if (SELF == 2) {
-          in = r2 < s.band_hi && sm.gidx[k] != i;
-          if (in && r2 >= s.band_lo) in = exact_pair<D>(s, a, i, sm.gidx[k]);
-        } else if (SELF == 1) {
-          in = r2 < H2 && sm.gidx[k] != i;
-        } else {
-          in = r2 < H2 && r2 > 0.f;
-        }
-        if (in) {
-          list[cnt * Cfg::THREADS] = (unsigned short)k;
-          if (++cnt == Cfg::LIST) drain();
+      for (int k0 = b + lane; k0 < en; k0 += 4 * Cfg::LANES) {
+        if (cnt > Cfg::LIST - 4) drain();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = k0 + u * Cfg::LANES;
+          if (k < en) {
+            const float4 P = sm.A[k];
+            const float dx = tx - P.x, dy2 = ty - P.y;
+            float r2 = fmaf(dy2, dy2, dx * dx);
+            if (D == 3) {
+              const float dz2 = tz - P.z;
+              r2 = fmaf(dz2, dz2, r2);
+            }
+            bool in;
+            if (SELF == 2) {
+              in = r2 < s.band_hi;
+              if (in) {
+                const int gj = staged_gidx<D, E>(sm, k);
+                in = gj != i;
+                if (in && r2 >= s.band_lo) in = exact_pair<D>(s, a, i, gj);
+              }
+            } else if (SELF == 1) {
+              in = r2 < H2 && (r2 > 0.f || staged_gidx<D, E>(sm, k) != i);
+            } else {
+              in = r2 < H2 && r2 > 0.f;
+            }
+            if (in) {
+              list[cnt * Cfg::THREADS] = (unsigned short)(k | shift_bits);
+              ++cnt;
+            }
+          }
         }
       }
     }
@@ -182,7 +280,11 @@ __device__ int gather_global(const DevSeg& s, const Arrays& a, const uint32_t* _
           if (in) {
             float4 ex = extra0 ? __ldg(extra0 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
             float pp = extra1 ? __ldg(extra1 + j) : 0.f;
-            body.pair(pj, ex, pp, j);
+            // place the neighbour at its nearest image relative to the target
+            PD<D> pm = pj;
+#pragma unroll
+            for (int q = 0; q < D; ++q) pm.x[q] = xi[q] - r[q];
+            body.pair_at(xi, pm, ex, pp, j);
             ++npair;
           }
         }
@@ -213,32 +315,41 @@ __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restr
   using Cfg = TileCfg<D>;
   extern __shared__ __align__(16) unsigned char smraw[];
   TileSmem<D, E>& sm = *reinterpret_cast<TileSmem<D, E>*>(smraw);
+  __shared__ int s_tile;
   const int nt = *ntiles;
   const int tgt = threadIdx.x / Cfg::LANES;
   const int lane = threadIdx.x % Cfg::LANES;
   long long pairs_cta = 0;
-  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+  // tiles are handed out dynamically (one atomic per CTA and tile): load balance whatever the
+  // occupancy and the tile sizes
+  if (threadIdx.x == 0) s_tile = atomicAdd(t.tile_ctr, 1);
+  __syncthreads();
+  for (int ti = s_tile; ti < nt; ti = s_tile) {
     const Tile T = tiles[ti];
     const DevSeg& s = t.segs[T.seg];
-    const bool staged = stage_tile<D, E>(sm, s, T, t.a, t.keys, t.cell_off, extra0, extra1);
+    const bool staged = stage_tile<D, E>(sm, s, T, t.a, t.cell_off, extra0, extra1);
     const int i = T.p0 + tgt;
     const bool valid = i < T.p1;
     typename Pass::Body body;
     bool active = false;
     int ccol = 0;
-    float xi[3] = {0.f, 0.f, 0.f};
+    float xi[3] = {0.f, 0.f, 0.f}, flo[3] = {0.f, 0.f, 0.f}, fhi[3] = {0.f, 0.f, 0.f};
     if (valid) {
       active = pass.init(body, s, i);
       const float4 A = __ldg(t.a.A + i);
       xi[0] = A.x; xi[1] = A.y; xi[2] = A.z;
-      int c[3];
-      key_coords(s, t.keys[i], c);
+      int c[3] = {(int)t.keys[i] - (s.cell_base + (T.cz * s.n[1] + T.cy) * s.n[0]), T.cy, T.cz};
       ccol = c[0] - (staged ? sm.colbase : 0);
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        flo[q] = s.lo[q] + s.cs[q] * (float)c[q];
+        fhi[q] = flo[q] + s.cs[q];
+      }
     }
     int np = 0;
     if (active) {
       if (staged)
-        np = gather_staged<D, E, SELF>(sm, s, t.a, i, ccol, xi, body);
+        np = gather_staged<D, E, SELF>(sm, s, t.a, i, ccol, xi, flo, fhi, body);
       else if (lane == 0)
         np = gather_global<D, SELF>(s, t.a, t.keys, t.cell_off, extra0, extra1, i, xi, body);
     }
@@ -247,6 +358,8 @@ __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restr
     if (valid && lane == 0) pass.finish(body, s, i);
     pairs_cta += np;
     __syncthreads();  // shared memory is restaged for the next tile
+    if (threadIdx.x == 0) s_tile = atomicAdd(t.tile_ctr, 1);
+    __syncthreads();
   }
   if (t.pair_count) {
     long long v = pairs_cta;
@@ -263,10 +376,10 @@ struct WallPass {
     const DevSeg* s;
     float xi[D];
     float sW, sp, sh;
-    __device__ __forceinline__ void pair(const PD<D>& pj, float4, float, int) {
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4, float, int) {
       if (pj.m < 0.f) return;  // wall neighbour
       float r[D];
-      const float r2 = separation<D>(*s, xi, pj.x, r);
+      const float r2 = diff<D>(xs, pj.x, r);
       const float W = s->Kw * kern_w<KERN>(safe_q(r2, s->invH));
       float gr = 0.f;
 #pragma unroll
@@ -311,9 +424,9 @@ struct DensityPass {
     const DevSeg* s;
     float xi[D];
     double rho;
-    __device__ __forceinline__ void pair(const PD<D>& pj, float4, float, int) {
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4, float, int) {
       float r[D];
-      const float r2 = separation<D>(*s, xi, pj.x, r);
+      const float r2 = diff<D>(xs, pj.x, r);
       rho += (double)(fabsf(pj.m) * (s->Kw * kern_w<KERN>(safe_q(r2, s->invH))));
     }
     template <int L>
@@ -354,16 +467,16 @@ struct SweepPass {
     const DevSeg* s;
     float xi[D], vi[D], rho_i, p_i;
     float acc[D], c1, c2;
-    __device__ __forceinline__ void pair(const PD<D>& pj, float4, float, int) {
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4, float, int) {
       const DevSeg& c = *s;
       float r[D];
-      const float r2 = separation<D>(c, xi, pj.x, r);
+      const float r2 = diff<D>(xs, pj.x, r);
       const float q = safe_q(r2, c.invH);
       const float gK = c.Kg * kern_gt<KERN>(q);
       float w = 0.f;
 #pragma unroll
       for (int k = 0; k < D; ++k) w = fmaf(vi[k] - pj.v[k], r[k], w);
-      const float sd = __frcp_rn(r2 + c.eH2);
+      const float sd = __fdividef(1.f, r2 + c.eH2);
       const float VgK = pj.V * gK;
       const float tt = VgK * fmaf(c.Cv * w, sd, -(p_i + pj.p));
 #pragma unroll
@@ -451,7 +564,7 @@ struct PairPass {
     int32_t *pi, *pj;
     unsigned long long* count;
     long long cap;
-    __device__ __forceinline__ void pair(const PD<D>&, float4, float, int j) {
+    __device__ __forceinline__ void pair_at(const float*, const PD<D>&, float4, float, int j) {
       const unsigned long long k = atomicAdd(count, 1ull);
       if ((long long)k < cap) {
         pi[k] = (int32_t)id_i;
@@ -489,7 +602,7 @@ struct AdjPass {
     float xi[D], vi[D], rho_i, p_i, V_i, P_i;
     float ab_i[D], bb_i;
     float gx[D], gv[D], grho, gnu;
-    __device__ __forceinline__ void pair(const PD<D>& pj, float4 Sj, float ppj, int) {
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4 Sj, float ppj, int) {
       const DevSeg& c = *s;
       float ab_j[3], bb_j, P_j;
       if (D == 2) {
@@ -499,11 +612,11 @@ struct AdjPass {
       }
       (void)P_j;
       float r[D], u[D];
-      const float r2 = separation<D>(c, xi, pj.x, r);
+      const float r2 = diff<D>(xs, pj.x, r);
       const float q = safe_q(r2, c.invH);
       const float gK = c.Kg * kern_gt<KERN>(q);
       const float hK = c.Kh * kern_ht<KERN>(q);
-      const float sd = __frcp_rn(r2 + c.eH2);
+      const float sd = __fdividef(1.f, r2 + c.eH2);
       float w = 0.f, e_i = 0.f, e_j = 0.f;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -607,19 +720,19 @@ struct AdjPass {
 
 // ================================================================== kernels
 template <int D, int KERN>
-__global__ void __launch_bounds__(256) k_walls_t(TravArgs t, const Tile* tiles, const int* ntiles) {
+__global__ void __launch_bounds__(256, 4) k_walls_t(TravArgs t, const Tile* tiles, const int* ntiles) {
   WallPass<D, KERN> pass;
   pass.a = t.a;
   run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
 template <int D, int KERN>
-__global__ void __launch_bounds__(256) k_density_t(TravArgs t, const Tile* tiles, const int* ntiles) {
+__global__ void __launch_bounds__(256, 4) k_density_t(TravArgs t, const Tile* tiles, const int* ntiles) {
   DensityPass<D, KERN> pass;
   pass.a = t.a;
   run_tiles<D, 0, 1>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
 template <int D, int KERN, bool INTEGRATE>
-__global__ void __launch_bounds__(256) k_sweep_t(TravArgs t, const Tile* tiles, const int* ntiles, Arrays out,
+__global__ void __launch_bounds__(256, 4) k_sweep_t(TravArgs t, const Tile* tiles, const int* ntiles, Arrays out,
                                                  RateOut ro) {
   SweepPass<D, KERN, INTEGRATE> pass;
   pass.a = t.a;
@@ -629,7 +742,7 @@ __global__ void __launch_bounds__(256) k_sweep_t(TravArgs t, const Tile* tiles, 
   run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
 template <int D>
-__global__ void __launch_bounds__(256) k_pairs_t(TravArgs t, const Tile* tiles, const int* ntiles, int32_t* pi,
+__global__ void __launch_bounds__(256, 4) k_pairs_t(TravArgs t, const Tile* tiles, const int* ntiles, int32_t* pi,
                                                  int32_t* pj, unsigned long long* count, long long cap) {
   PairPass<D> pass;
   pass.a = t.a;
@@ -640,7 +753,7 @@ __global__ void __launch_bounds__(256) k_pairs_t(TravArgs t, const Tile* tiles, 
   run_tiles<D, 0, 2>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
 template <int D, int KERN>
-__global__ void __launch_bounds__(256) k_adj_t(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S,
+__global__ void __launch_bounds__(256, 2) k_adj_t(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S,
                                                const float* Pp, const float4* XBin, const float4* VBin, float4* XBout,
                                                float4* VBout, float* nu_part) {
   AdjPass<D, KERN> pass;
@@ -673,51 +786,66 @@ size_t pass_smem(int extra) {
 }
 
 static int g_num_sms = 148;
-static int pass_grid(int tiles_upper, int ctas_per_sm) {
-  long long g = (long long)g_num_sms * ctas_per_sm;
+// Resident CTAs per SM of each pass kernel (queried once), so the grid is exactly one wave.
+static std::map<const void*, int> g_occ;
+static int pass_grid(const void* fn, int tiles_upper) {
+  auto it = g_occ.find(fn);
+  const int occ = it == g_occ.end() ? 1 : std::max(1, it->second);
+  long long g = (long long)g_num_sms * occ;
   return (int)std::max<long long>(1, std::min<long long>(g, tiles_upper));
+}
+static void set_occ(const void* fn, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 256, smem) == cudaSuccess) g_occ[fn] = n;
 }
 
 template <int D>
-void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, const int* cell_off, uint32_t* counts,
-                  uint32_t* counts_copy, uint32_t* sums, Tile* tiles, int* ntiles, cudaStream_t st) {
+void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, const int* cell_off,
+                  const uint32_t* keys, uint32_t* counts, uint32_t* counts_copy, uint32_t* sums, Tile* tiles,
+                  int* ntiles, cudaStream_t st) {
   const int nb = (n_lines + 255) / 256;
   k_tile_count<D><<<nb, 256, 0, st>>>(segs, S, line_base, n_lines, cell_off, counts);
   cudaMemcpyAsync(counts_copy, counts, sizeof(uint32_t) * n_lines, cudaMemcpyDeviceToDevice, st);
   const int sb = (n_lines + 2047) / 2048;
   launch_exclusive_scan(counts, n_lines, sums, st);
   (void)sb;
-  k_tile_emit<D><<<nb, 256, 0, st>>>(segs, S, line_base, n_lines, cell_off, counts, counts_copy, tiles, ntiles);
+  k_tile_emit<D><<<nb, 256, 0, st>>>(segs, S, line_base, n_lines, cell_off, keys, counts, counts_copy, tiles, ntiles);
 }
 
 template <int D, int KERN>
 void launch_walls_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st) {
-  k_walls_t<D, KERN><<<pass_grid(tiles_upper, 4), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles);
+  cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
+  k_walls_t<D, KERN><<<pass_grid((const void*)k_walls_t<D, KERN>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles);
 }
 template <int D, int KERN>
 void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st) {
-  k_density_t<D, KERN><<<pass_grid(tiles_upper, 4), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles);
+  cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
+  k_density_t<D, KERN><<<pass_grid((const void*)k_density_t<D, KERN>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles);
 }
 template <int D, int KERN>
 void launch_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
                     cudaStream_t st) {
-  k_sweep_t<D, KERN, true><<<pass_grid(tiles_upper, 4), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, out, RateOut{});
+  cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
+  k_sweep_t<D, KERN, true><<<pass_grid((const void*)k_sweep_t<D, KERN, true>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, out, RateOut{});
 }
 template <int D, int KERN>
 void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const RateOut& ro,
                     cudaStream_t st) {
-  k_sweep_t<D, KERN, false><<<pass_grid(tiles_upper, 4), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, Arrays{}, ro);
+  cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
+  k_sweep_t<D, KERN, false><<<pass_grid((const void*)k_sweep_t<D, KERN, false>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, Arrays{}, ro);
 }
 template <int D>
 void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
                     unsigned long long* count, long long cap, cudaStream_t st) {
-  k_pairs_t<D><<<pass_grid(tiles_upper, 4), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, pi, pj, count, cap);
+  cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
+  k_pairs_t<D><<<pass_grid((const void*)k_pairs_t<D>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, pi, pj, count, cap);
 }
 template <int D, int KERN>
 void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* S,
                   const float* Pp, const float4* XBin, const float4* VBin, float4* XBout, float4* VBout,
                   float* nu_part, cudaStream_t st) {
-  k_adj_t<D, KERN><<<pass_grid(tiles_upper, 4), 256, pass_smem<D>(D == 2 ? 1 : 2), st>>>(
+  cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
+  k_adj_t<D, KERN><<<pass_grid((const void*)k_adj_t<D, KERN>, tiles_upper), 256, pass_smem<D>(D == 2 ? 1 : 2), st>>>(
       t, tiles, ntiles, S, Pp, XBin, VBin, XBout, VBout, nu_part);
 }
 void launch_sum_float_partials(const float* part, int n, double* acc, cudaStream_t st) {
@@ -729,7 +857,8 @@ cudaError_t configure_passes() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
 #define SPH_ATTR(fn, bytes)                                                                                    \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
+  if (e == cudaSuccess) set_occ((const void*)fn, (bytes));
   SPH_ATTR((k_walls_t<2, 0>), pass_smem<2>(0)) SPH_ATTR((k_walls_t<2, 1>), pass_smem<2>(0))
   SPH_ATTR((k_walls_t<3, 0>), pass_smem<3>(0)) SPH_ATTR((k_walls_t<3, 1>), pass_smem<3>(0))
   SPH_ATTR((k_density_t<2, 0>), pass_smem<2>(0)) SPH_ATTR((k_density_t<2, 1>), pass_smem<2>(0))
@@ -746,8 +875,8 @@ cudaError_t configure_passes() {
 }
 
 #define SPH_INST_PD(D)                                                                                       \
-  template void launch_tiles<D>(const DevSeg*, int, const int*, int, const int*, uint32_t*, uint32_t*, uint32_t*, \
-                                Tile*, int*, cudaStream_t);                                                   \
+  template void launch_tiles<D>(const DevSeg*, int, const int*, int, const int*, const uint32_t*, uint32_t*,   \
+                                uint32_t*, uint32_t*, Tile*, int*, cudaStream_t);                             \
   template void launch_pairs_t<D>(const TravArgs&, const Tile*, const int*, int, int32_t*, int32_t*,          \
                                   unsigned long long*, long long, cudaStream_t);
 SPH_INST_PD(2)

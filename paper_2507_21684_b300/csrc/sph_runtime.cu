@@ -11,7 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/sph.h"
+#include "sph.h"
 #include "sph_runtime.h"
 
 namespace sph {
@@ -173,6 +173,13 @@ DevSeg make_seg(const sph_params& p, int n_fluid, int cell_base, int p0, int p1,
   double band = std::max(1e-5, 4.0 * ex / H);
   s.band_lo = (float)(H * H * (1.0 - band));
   s.band_hi = (float)(H * H * (1.0 + band));
+  // cells farther than this from a target (at build time, in the folded frame) hold no
+  // neighbour: H widened by the guard band, half the Verlet skin and FP32 rounding of the faces
+  double Lmax = 1.0;
+  for (int k = 0; k < p.dim; ++k) Lmax = std::max(Lmax, std::fabs(p.box_lo[k]) + s.L_d[k]);
+  double reach = (H * (1.0 + 2.0 * band) + 0.5 * (double)p.skin) * (1.0 + 1e-5) + 16.0 * std::ldexp(Lmax, -23);
+  s.trimR2 = (float)(reach * reach);
+  for (int k = 0; k < 3; ++k) s.cs[k] = (float)s.cs_d[k];
   return s;
 }
 
@@ -299,7 +306,12 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
     line_base_h[s] = n_lines;
     n_lines += segs[s].n[1] * segs[s].n[2];
   }
-  tiles_upper = (D == 2 ? (N + TileCfg<2>::TP - 1) / TileCfg<2>::TP : (N + TileCfg<3>::TP - 1) / TileCfg<3>::TP) + n_lines;
+  // a tile is closed when it is full (TP particles), when its span would pass TP cells, or at
+  // an over-full cell: fewer than 3 N / TP + C_tot / TP + 2 n_lines tiles
+  {
+    const int TP = D == 2 ? TileCfg<2>::TP : TileCfg<3>::TP;
+    tiles_upper = 3 * ((N + TP - 1) / TP) + (C_tot + TP - 1) / TP + 2 * n_lines + 1;
+  }
   bits = key_bits(C_tot);
   passes = (bits + 7) / 8;
   if (N > 16384 * 2048) einval("too many particles for the radix sort scratch (max 33554432)");
@@ -327,6 +339,7 @@ void Scene::alloc_all() {
   tile_counts_copy = (uint32_t*)mem.get(sizeof(uint32_t) * (size_t)n_lines);
   tiles = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
   d_ntiles = (int*)mem.get(sizeof(int) * 2);
+  d_tile_ctr = (int*)mem.get(sizeof(int) * 4);
   d_status = (int*)mem.get(sizeof(int) * 4);
   d_pairs = (unsigned long long*)mem.get(sizeof(unsigned long long) * 2);
   d_nubar = (double*)mem.get(sizeof(double) * 2);
@@ -387,6 +400,7 @@ TravArgs Scene::trav(const Arrays& a, const uint32_t* keys, const int* off) cons
   t.cell_off = off;
   t.status = d_status;
   t.pair_count = d_pairs;
+  t.tile_ctr = d_tile_ctr;
   return t;
 }
 
@@ -458,7 +472,7 @@ std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& o
   }
   launch_cell_offsets(ks, N, C_tot, off_out, st);
   CKL();
-  build_tiles(off_out);
+  build_tiles(off_out, ks);
   if (D == 2)
     launch_permute<2>(dseg, N, pm, in, out, st);
   else
@@ -468,13 +482,13 @@ std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& o
   return {ks, pm};
 }
 
-// Tile table of a cell structure (CSR offsets `off`).
-void Scene::build_tiles(const int* off) {
+// Tile table of a cell structure (CSR offsets `off`, sorted keys `keys`).
+void Scene::build_tiles(const int* off, const uint32_t* keys) {
   uint32_t* sums = scratch + n_lines + 64;
   if (D == 2)
-    launch_tiles<2>(dseg, S, line_base, n_lines, off, tile_counts, tile_counts_copy, sums, tiles, d_ntiles, st);
+    launch_tiles<2>(dseg, S, line_base, n_lines, off, keys, tile_counts, tile_counts_copy, sums, tiles, d_ntiles, st);
   else
-    launch_tiles<3>(dseg, S, line_base, n_lines, off, tile_counts, tile_counts_copy, sums, tiles, d_ntiles, st);
+    launch_tiles<3>(dseg, S, line_base, n_lines, off, keys, tile_counts, tile_counts_copy, sums, tiles, d_ntiles, st);
   CKL();
 }
 
@@ -766,7 +780,7 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
       CKL();
       TravArgs t = trav(slot.a, slot.keys, slot.off);
       t.pair_count = nullptr;
-      build_tiles(slot.off);
+      build_tiles(slot.off, slot.keys);
       prof_begin(4);
       if (D == 2) {
         if (kern == 0)

@@ -6,7 +6,7 @@
 #include <utility>
 #include <vector>
 
-#include "../../include/sph.h"
+#include "sph.h"
 #include "sph_passes.cuh"
 
 namespace sph {
@@ -83,6 +83,7 @@ struct Scene {
   uint32_t *tile_counts = nullptr, *tile_counts_copy = nullptr;
   Tile* tiles = nullptr;
   int* d_ntiles = nullptr;
+  int* d_tile_ctr = nullptr;   // dynamic tile counter (zeroed before each tiled launch)
   int* d_status = nullptr;
   unsigned long long* d_pairs = nullptr;
   double* d_nubar = nullptr;
@@ -135,7 +136,7 @@ struct Scene {
   void prof_end();
   std::pair<uint32_t*, uint32_t*> rebuild(const Arrays& in, const Arrays& out, uint32_t* keys_out,
                                           uint32_t* perm_out, int* off_out);
-  void build_tiles(const int* off);
+  void build_tiles(const int* off, const uint32_t* keys);
   void passes_before_sweep(const TravArgs& t);
   void sweep(const TravArgs& t, const Arrays& out);
   bool rebuild_due() const;

@@ -14,9 +14,11 @@
 
 namespace sph {
 
-// One tile: particle range [p0, p1) inside one cell line of one scene.
+// One tile: particle range [p0, p1) inside one cell line of one scene, with the x cells of its
+// first and last particle and the line's (y, z) cell (filled when the tile table is built).
 struct Tile {
-  int p0, p1, line, seg;
+  int p0, p1, seg, line;
+  int cx0, cx1, cy, cz;
 };
 
 template <int D>
@@ -35,61 +37,64 @@ template <int D>
 constexpr int tile_cols() { return TileCfg<D>::TP + 2; }
 
 // Shared-memory layout of a staged tile.  EXTRA: number of additional float4 payloads per
-// staged particle (adjoint seeds).
+// staged particle (adjoint seeds).  Each staged line holds up to three runs in stencil order:
+// the left periodic image cell, the in-box columns (one contiguous range of sorted particles),
+// the right periodic image cell.
 template <int D, int EXTRA>
 struct TileSmem {
   static constexpr int CAP = TileCfg<D>::CAP;
   static constexpr int NCOL = tile_cols<D>() + 1;
+  static constexpr int NL = TileCfg<D>::NL;
+  static constexpr int NRUN = 3 * NL;
   float4 A[CAP];
   float4 B[CAP];
   float2 C[D == 3 ? CAP : 1];
   float4 E[EXTRA > 0 ? EXTRA * CAP : 1];
-  int gidx[CAP];
-  int colstart[TileCfg<D>::NL * NCOL + 1];
+  int colstart[NL * NCOL + 1];      // staged index of each (line, column) cell start
   unsigned short list[TileCfg<D>::LIST * TileCfg<D>::THREADS];
-  float tshift[TileCfg<D>::NL][3];  // target shift of each line (applied to the target, +L)
-  float cshift[TileCfg<D>::NL][3];  // candidate shift of each line (applied at staging, -L)
+  int run_g[NRUN];                  // global start of each run
+  int run_n[NRUN];                  // length of each run
+  int run_s[NRUN + 1];              // staged start of each run (exclusive scan)
+  float run_sx[NRUN];               // x shift applied at staging (-L for the left image)
+  float tshift[NL][3];              // target shift of each line (upper periodic image: +L)
+  float cshift[NL][3];              // candidate shift of each line (lower periodic image: -L)
   int ncols, colbase, total, fallback;
-  int linecell[TileCfg<D>::NL];     // global cell id of column 0 of each line (-1: no line)
+  int linecell[NL];                 // global cell id of column 0 of each line (-1: no line)
 };
 
 template <int D, int EXTRA>
 constexpr size_t tile_smem_bytes() { return sizeof(TileSmem<D, EXTRA>); }
 
-// Per-scene line indexing: global line id = seg_line_base + cz * ny + cy.
-__device__ __forceinline__ void line_coords(const DevSeg& s, int line_local, int& cy, int& cz) {
-  cy = line_local % s.n[1];
-  cz = line_local / s.n[1];
-}
-
-// Build the column table of a tile and stage its particles.  Returns false (fallback) when the
-// staged region exceeds the shared-memory capacity.  Must be called by all threads of the CTA.
+// Build the run table of a tile and stage its particles (two dependent global round trips:
+// the cell offsets, then the particle records).  Returns false (fallback) when the staged
+// region exceeds the shared-memory capacity or the column table.  All threads of the CTA call it.
 template <int D, int EXTRA>
 __device__ bool stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T, const Arrays& a,
-                           const uint32_t* __restrict__ keys, const int* __restrict__ cell_off,
-                           const float4* __restrict__ extra0, const float* __restrict__ extra1) {
+                           const int* __restrict__ cell_off, const float4* __restrict__ extra0,
+                           const float* __restrict__ extra1) {
   constexpr int NL = TileCfg<D>::NL;
   constexpr int NCOL = TileSmem<D, EXTRA>::NCOL;
+  constexpr int NRUN = TileSmem<D, EXTRA>::NRUN;
   constexpr int CAP = TileCfg<D>::CAP;
   const int tid = threadIdx.x;
   const int nx = s.n[0], ny = s.n[1], nz = s.n[2];
-  int c_first[3], c_last[3];
-  key_coords(s, keys[T.p0], c_first);
-  key_coords(s, keys[T.p1 - 1], c_last);
-  const int colbase = c_first[0] - 1;
-  const int ncols = c_last[0] - c_first[0] + 3;  // columns colbase .. colbase + ncols - 1
-  const int cy = c_first[1], cz = c_first[2];
-  if (ncols > NCOL - 1) {  // a sparse line: the tile spans more cells than the table holds
-    __syncthreads();
+  const int colbase = T.cx0 - 1;
+  const int ncols = T.cx1 - T.cx0 + 3;  // columns colbase .. colbase + ncols - 1
+  if (ncols > NCOL - 1) {               // a sparse line: more cells than the table holds
     if (tid == 0) sm.fallback = 1;
     __syncthreads();
     return false;
   }
   const bool px = s.periodic_mask & 1, py = (s.periodic_mask >> 1) & 1, pz = (s.periodic_mask >> 2) & 1;
+  // in-box column range of the tile and its periodic image cells
+  const int mc0 = max(colbase, 0), mc1 = min(colbase + ncols - 1, nx - 1);
+  const bool left_img = px && colbase < 0;
+  const bool right_img = px && colbase + ncols - 1 >= nx;
+  // 1) line geometry (threads 0..NL-1) and every needed cell offset (one round trip)
   if (tid < NL) {
     const int dy = (D == 2) ? tid - 1 : tid % 3 - 1;
     const int dz = (D == 2) ? 0 : tid / 3 - 1;
-    int ly = cy + dy, lz = cz + dz;
+    int ly = T.cy + dy, lz = T.cz + dz;
     float ty = 0.f, tz = 0.f, cyv = 0.f, czv = 0.f;
     bool ok = true;
     if (ly < 0) { if (py) { ly += ny; cyv = -s.L[1]; } else ok = false; }
@@ -98,71 +103,79 @@ __device__ bool stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& 
       if (lz < 0) { if (pz) { lz += nz; czv = -s.L[2]; } else ok = false; }
       else if (lz >= nz) { if (pz) { lz -= nz; tz = s.L[2]; } else ok = false; }
     }
-    sm.linecell[tid] = ok ? s.cell_base + (lz * ny + ly) * nx : -1;
+    const int lc = ok ? s.cell_base + (lz * ny + ly) * nx : -1;
+    sm.linecell[tid] = lc;
     sm.tshift[tid][0] = 0.f; sm.tshift[tid][1] = ty; sm.tshift[tid][2] = tz;
     sm.cshift[tid][0] = 0.f; sm.cshift[tid][1] = cyv; sm.cshift[tid][2] = czv;
+    // runs: left image cell (nx-1), in-box columns [mc0, mc1], right image cell (0)
+    int g0 = 0, n0 = 0, g1 = 0, n1 = 0, g2 = 0, n2 = 0;
+    if (ok) {
+      if (left_img) { g0 = cell_off[lc + nx - 1]; n0 = cell_off[lc + nx] - g0; }
+      g1 = cell_off[lc + mc0];
+      n1 = cell_off[lc + mc1 + 1] - g1;
+      if (right_img) { g2 = cell_off[lc]; n2 = cell_off[lc + 1] - g2; }
+    }
+    sm.run_g[3 * tid + 0] = g0; sm.run_n[3 * tid + 0] = n0; sm.run_sx[3 * tid + 0] = -s.L[0];
+    sm.run_g[3 * tid + 1] = g1; sm.run_n[3 * tid + 1] = n1; sm.run_sx[3 * tid + 1] = 0.f;
+    sm.run_g[3 * tid + 2] = g2; sm.run_n[3 * tid + 2] = n2; sm.run_sx[3 * tid + 2] = 0.f;
   }
+  // in-box column boundaries of every line: colstart is filled relative to the run start
+  // after the scan; here the raw offsets are kept in colstart.
+  const int nb = NL * (ncols + 1);
   __syncthreads();
-  // counts of every (line, column) cell, then an exclusive scan in stencil order
-  const int nent = NL * ncols;
-  for (int e = tid; e < nent; e += blockDim.x) {
-    const int l = e / ncols, c = e % ncols;
+  for (int e = tid; e < nb; e += blockDim.x) {
+    const int l = e / (ncols + 1), c = e - l * (ncols + 1);
     const int lc = sm.linecell[l];
-    int cnt = 0;
+    int v = 0;
     if (lc >= 0) {
-      int col = colbase + c;
-      bool ok = true;
-      if (col < 0) { if (px) col += nx; else ok = false; }
-      else if (col >= nx) { if (px) col -= nx; else ok = false; }
-      if (ok) cnt = cell_off[lc + col + 1] - cell_off[lc + col];
+      const int col = min(max(colbase + c, mc0), mc1 + 1);  // clamp into the in-box range
+      v = cell_off[lc + col];
     }
-    sm.colstart[l * NCOL + c] = cnt;
+    sm.colstart[l * NCOL + c] = v;
   }
-  __syncthreads();
+  // 2) exclusive scan of the run lengths (one warp, NRUN <= 27)
   if (tid < 32) {
-    // warp scan over the (line, column) entries in order
-    int run = 0;
-    for (int base = 0; base < nent; base += 32) {
-      const int e = base + tid;
-      const int l = e / ncols, c = e % ncols;
-      int v = (e < nent) ? sm.colstart[l * NCOL + c] : 0;
-      int incl = v;
+    const int v = tid < NRUN ? sm.run_n[tid] : 0;
+    int incl = v;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(kFull, incl, o);
-        if (tid >= o) incl += t;
-      }
-      if (e < nent) sm.colstart[l * NCOL + c] = run + incl - v;
-      run += __shfl_sync(kFull, incl, 31);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, o);
+      if (tid >= o) incl += t;
     }
+    if (tid < NRUN) sm.run_s[tid] = incl - v;
+    const int total = __shfl_sync(kFull, incl, 31);
     if (tid == 0) {
-      sm.total = run;
+      sm.run_s[NRUN] = total;
+      sm.total = total;
       sm.ncols = ncols;
       sm.colbase = colbase;
-      sm.fallback = run > CAP;
+      sm.fallback = total > CAP;
     }
   }
   __syncthreads();
-  // the end of each line's last column = start of the next line's first column
-  const int total = sm.total;
   if (sm.fallback) return false;
-  // stage: staged index k -> (line, column) by binary search over the scanned starts
+  const int total = sm.total;
+  // 3) column starts as staged indices: image columns map to their own runs
+  for (int e = tid; e < nb; e += blockDim.x) {
+    const int l = e / (ncols + 1), c = e - l * (ncols + 1);
+    const int col = colbase + c;
+    int v;
+    if (col < 0) v = sm.run_s[3 * l + 0];                           // start of the left image
+    else if (col > nx) v = sm.run_s[3 * l + 2] + sm.run_n[3 * l + 2];  // end of the right image
+    else if (col == nx) v = sm.run_s[3 * l + 2];                    // start of the right image
+    else v = sm.run_s[3 * l + 1] + (sm.colstart[l * NCOL + c] - sm.run_g[3 * l + 1]);
+    if (sm.linecell[l] < 0) v = sm.run_s[3 * l + 0];
+    sm.colstart[l * NCOL + c] = v;
+  }
+  // 4) copy: every thread takes staged indices, finds its run (at most 3 NL runs)
   for (int k = tid; k < total; k += blockDim.x) {
-    int lo = 0, hi = nent - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      const int l = mid / ncols, c = mid % ncols;
-      if (sm.colstart[l * NCOL + c] <= k) lo = mid; else hi = mid - 1;
-    }
-    const int l = lo / ncols, c = lo % ncols;
-    int col = colbase + c;
-    float sx = 0.f;
-    if (col < 0) { col += nx; sx = -s.L[0]; }  // left image: x_j - L is exact near L
-    else if (col >= nx) { col -= nx; }         // right image: the target takes off L
-    const int cell = sm.linecell[l] + col;
-    const int j = cell_off[cell] + (k - sm.colstart[l * NCOL + c]);
+    int r = 0;
+#pragma unroll 1
+    while (r + 1 < NRUN && sm.run_s[r + 1] <= k) ++r;
+    const int j = sm.run_g[r] + (k - sm.run_s[r]);
+    const int l = r / 3;
     float4 A = __ldg(a.A + j), B = __ldg(a.B + j);
-    A.x += sx;
+    A.x += sm.run_sx[r];
     A.y += sm.cshift[l][1];
     if (D == 3) A.z += sm.cshift[l][2];
     sm.A[k] = A;
@@ -170,30 +183,18 @@ __device__ bool stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& 
     if (D == 3) sm.C[k] = __ldg(a.C + j);
     if (EXTRA > 0) sm.E[k] = __ldg(extra0 + j);
     if (EXTRA > 1) sm.E[CAP + k] = make_float4(__ldg(extra1 + j), 0.f, 0.f, 0.f);
-    sm.gidx[k] = j;
   }
   __syncthreads();
   return true;
 }
 
-// Column runs of one target in line l (target in column ccol of the tile): the staged indices
-// of its three cells.  The column right of the box's last cell (periodic) is staged without a
-// shift; its run is returned separately so the caller can take L off the target instead
-// (x_i - L is exact for x_i near L, x_j + L is not for x_j near 0).
+// Global index of staged particle k (for predicates that exclude the target by index).
 template <int D, int EXTRA>
-__device__ __forceinline__ void target_runs(const TileSmem<D, EXTRA>& sm, int l, int ccol, int nx, int& lo, int& mid,
-                                            int& hi) {
-  constexpr int NCOL = TileSmem<D, EXTRA>::NCOL;
-  const int ncols = sm.ncols;
-  lo = sm.colstart[l * NCOL + (ccol - 1)];
-  const int endc = ccol + 2;
-  if (endc < ncols)
-    hi = sm.colstart[l * NCOL + endc];
-  else
-    hi = (l + 1 < TileCfg<D>::NL) ? sm.colstart[(l + 1) * NCOL] : sm.total;
-  // absolute column of ccol + 1; if it lies past the box (wrapped), split it off
-  const int abs_right = sm.colbase + ccol + 1;
-  mid = (abs_right >= nx) ? sm.colstart[l * NCOL + ccol + 1] : hi;
+__device__ __forceinline__ int staged_gidx(const TileSmem<D, EXTRA>& sm, int k) {
+  int r = 0;
+  while (r + 1 < TileSmem<D, EXTRA>::NRUN && sm.run_s[r + 1] <= k) ++r;
+  return sm.run_g[r] + (k - sm.run_s[r]);
 }
+
 
 }  // namespace sph
