@@ -30,7 +30,10 @@
  *   - Results are always returned in the caller's original particle order.
  *   - A scene is bound to one CUDA stream (0 = legacy default stream).  Calls on one scene
  *     are not thread-safe; different scenes may be used from different threads.
- *   - Device memory comes from the allocator set with sph_set_allocator (default cudaMalloc).
+ *   - Device memory comes from the allocator set with sph_set_allocator (default: the device's
+ *     stream-ordered pool, cudaMallocAsync).
+ *   - A scene bound to stream 0 runs on a private non-blocking stream that is ordered after the
+ *     legacy default stream at every call and before it when device outputs are returned.
  */
 #ifndef SPH_B300_H
 #define SPH_B300_H
@@ -95,7 +98,7 @@ typedef struct sph_params {
 typedef struct sph_scene sph_scene;
 
 /* Allocator hooks: alloc(bytes, stream, ctx) returns a device pointer or NULL; free(ptr, bytes,
- * stream, ctx).  Passing NULL restores cudaMalloc/cudaFree.  Applies to scenes created after
+ * stream, ctx).  Passing NULL restores the default (cudaMallocAsync / cudaFreeAsync).  Applies to scenes created after
  * the call.  The hooks must stay valid until every scene using them is destroyed. */
 typedef void* (*sph_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*sph_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
@@ -110,6 +113,19 @@ SPH_API const char* sph_last_error(void);
  * inconsistent parameters (dim, H <= 0, fewer than 3 cells on a periodic axis, ...). */
 SPH_API int sph_init(const sph_params* params, int n_fluid, int n_wall, const float* x, const float* v,
              const float* rho, const float* mass, int ptr_is_device, void* cuda_stream, sph_scene** out);
+
+/* Batched scenes: n_scenes independent problems packed into one scene object (segments), advanced
+ * by the same launches (one launch per stage for all of them; the paper's batched merging of
+ * scenes, Sec. 4.1 "Computational Scaling").  All scenes must share dim, kernel, density mode,
+ * skin and rebuild_interval; every other parameter is per scene.  Arrays are given per scene.
+ * The other calls then act on the whole batch: particle rows of get_state / rates / adjoint are
+ * the scenes' rows concatenated in scene order (sph_batch_info gives each scene's first row and
+ * row count), and sph_adjoint writes one viscosity adjoint per scene.  Each scene's results are
+ * identical (bitwise) to running it alone. */
+SPH_API int sph_init_batch(int n_scenes, const sph_params* params, const int* n_fluid, const int* n_wall,
+                           const float* const* x, const float* const* v, const float* const* rho,
+                           const float* const* mass, int ptr_is_device, void* cuda_stream, sph_scene** out);
+SPH_API int sph_batch_info(const sph_scene* scene, int* n_scenes, int32_t* first_row, int32_t* n_rows);
 
 /* Advance the scene by n_steps steps of the scheme above (no tape kept).  Asynchronous with
  * respect to the host; errors detected on the device surface at the next synchronising call. */
@@ -130,7 +146,8 @@ SPH_API int sph_rollout(sph_scene* scene, int n_steps, int ckpt_every);
 
 /* Reverse pass of the last sph_rollout (vector-Jacobian product, Sec. 2.2): given the adjoints
  * of the final state (xbar_T, vbar_T, rhobar_T; NULL = zero) return those of the initial state
- * (xbar_0, vbar_0, rhobar_0; NULL = skip) and of the viscosity (nubar, host double; may be NULL).
+ * (xbar_0, vbar_0, rhobar_0; NULL = skip) and of the viscosity (nubar: host doubles, one per
+ * scene of a batch; may be NULL).
  * Segments between checkpoints are recomputed forward and replayed backwards.  Continuity
  * mode without wall particles only (SPH_EINVAL otherwise, or without a preceding rollout).
  * The scene's state is left at the end of the rollout. */
@@ -163,6 +180,60 @@ SPH_API int sph_timing(sph_scene* scene, int kernel_class, double* ms, int64_t* 
 SPH_API int sph_counters(sph_scene* scene, int64_t* pairs_per_step, int64_t* launches);
 
 SPH_API void sph_destroy(sph_scene* scene);
+
+/* ------------------------------------------------------------------------------------------
+ * Serving: continuous batching of rollout requests on one GPU (no counterpart in the paper;
+ * it serves many independent scenes the way the paper batches them, Sec. 4.1).
+ *
+ * A server owns two streams and two host threads.  sph_submit copies the request and queues it;
+ * requests are admitted in arrival order while the estimated device bytes of all admitted
+ * requests stay within hbm_budget_bytes and at most max_active run at once.  Admitted forward
+ * rollouts keep their particle state resident in one packed batch that is advanced with shared
+ * launches; arrivals join and finished requests leave at step-chunk boundaries (the batch is
+ * re-packed on the device).  Adjoint requests (forward rollout with checkpoints, then the reverse
+ * pass for the loss L = (1/N) sum_i |x_i^T - x~_i|^2 with target positions x~, Sec. 4.1) run on
+ * the second stream concurrently.  A served result is bitwise the result of the scene alone.
+ * Results stay with the server until sph_wait returns them (once per ticket). */
+#define SPH_REQ_FORWARD 0
+#define SPH_REQ_ADJOINT 1
+
+typedef struct sph_request {
+  sph_params params;
+  int n_fluid, n_wall;
+  const float *x, *v, *rho, *mass;  /* host arrays, copied by sph_submit */
+  int n_steps;                      /* >= 1 */
+  int mode;                         /* SPH_REQ_FORWARD or SPH_REQ_ADJOINT */
+  int ckpt_every;                   /* adjoint: checkpoint interval (0: 20) */
+  const float* x_target;            /* adjoint: target final positions (NULL: the initial positions) */
+} sph_request;
+
+typedef struct sph_result {
+  float *x, *v, *rho;               /* caller buffers for the final state (or NULL) */
+  float *xbar0, *vbar0, *rhobar0;   /* adjoint: caller buffers for dL/d(x0, v0, rho0) (or NULL) */
+  double nubar;                     /* adjoint: dL/dnu */
+  double loss;                      /* adjoint: L */
+  double t_submit, t_admit, t_done; /* server clock, seconds */
+} sph_result;
+
+typedef struct sph_server_info {
+  double particle_steps_fwd;        /* fluid particle-steps done by the forward batch */
+  double particle_steps_adj;        /* forward particle-steps of finished adjoint requests */
+  int queued, active, max_batch;
+  size_t bytes_in_use;
+  long long repacks, iterations;
+} sph_server_info;
+
+typedef struct sph_server sph_server;
+SPH_API int sph_server_create(size_t hbm_budget_bytes, int max_active, sph_server** out);
+/* SPH_EINVAL for malformed requests or one that alone exceeds the budget. */
+SPH_API int sph_submit(sph_server* server, const sph_request* request, uint64_t* ticket);
+SPH_API int sph_poll(sph_server* server, uint64_t ticket, int* done);
+/* Bounded wait: SPH_ETIMEOUT if the request is not done within timeout_ms (it stays queued or
+ * running and can be waited on again); otherwise copies the results and forgets the ticket. */
+SPH_API int sph_wait(sph_server* server, uint64_t ticket, int timeout_ms, sph_result* result);
+SPH_API int sph_server_stats(sph_server* server, sph_server_info* stats);
+/* Stops the loops after the current chunk; unfinished requests are dropped. */
+SPH_API void sph_server_destroy(sph_server* server);
 
 #ifdef __cplusplus
 }

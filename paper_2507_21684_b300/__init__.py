@@ -16,7 +16,7 @@ from pathlib import Path
 
 import numpy as np
 
-__all__ = ["lib", "Params", "Scene", "SphError", "rollout_fn", "library_path"]
+__all__ = ["lib", "Params", "Scene", "Server", "SphError", "rollout_fn", "library_path"]
 
 _HERE = Path(__file__).resolve().parent
 _LIBPATH = _HERE / "libsph_b300.so"
@@ -58,6 +58,27 @@ class Params(C.Structure):
         return o
 
 
+class Request(C.Structure):
+    _fields_ = [("params", Params), ("n_fluid", C.c_int), ("n_wall", C.c_int),
+                ("x", C.c_void_p), ("v", C.c_void_p), ("rho", C.c_void_p), ("mass", C.c_void_p),
+                ("n_steps", C.c_int), ("mode", C.c_int), ("ckpt_every", C.c_int), ("x_target", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("v", C.c_void_p), ("rho", C.c_void_p),
+                ("xbar0", C.c_void_p), ("vbar0", C.c_void_p), ("rhobar0", C.c_void_p),
+                ("nubar", C.c_double), ("loss", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+class ServerInfo(C.Structure):
+    _fields_ = [("particle_steps_fwd", C.c_double), ("particle_steps_adj", C.c_double),
+                ("queued", C.c_int), ("active", C.c_int), ("max_batch", C.c_int),
+                ("bytes_in_use", C.c_size_t), ("repacks", C.c_longlong), ("iterations", C.c_longlong)]
+
+
+REQ_FORWARD, REQ_ADJOINT = 0, 1
+
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 _hooks = None
@@ -81,11 +102,14 @@ def lib() -> C.CDLL:
     L.sph_last_error.restype = C.c_char_p
     L.sph_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, vp]
     L.sph_init.argtypes = [P(Params), C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, vp, P(vp)]
+    L.sph_init_batch.argtypes = [C.c_int, P(Params), P(C.c_int), P(C.c_int), P(vp), P(vp), P(vp), P(vp), C.c_int,
+                                 vp, P(vp)]
+    L.sph_batch_info.argtypes = [vp, P(C.c_int), P(C.c_int32), P(C.c_int32)]
     L.sph_step.argtypes = [vp, C.c_int]
     L.sph_get_state.argtypes = [vp, vp, vp, vp, C.c_int]
     L.sph_rates.argtypes = [vp, vp, vp, vp, C.c_int]
     L.sph_rollout.argtypes = [vp, C.c_int, C.c_int]
-    L.sph_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp, P(C.c_double), C.c_int]
+    L.sph_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
     L.sph_scene_info.argtypes = [vp, P(C.c_int32), P(C.c_int32)]
     L.sph_debug_cells.argtypes = [vp, vp, vp]
     L.sph_debug_pairs.argtypes = [vp, P(C.c_int64), vp, vp, C.c_int64]
@@ -94,6 +118,13 @@ def lib() -> C.CDLL:
     L.sph_counters.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
     L.sph_destroy.argtypes = [vp]
     L.sph_destroy.restype = None
+    L.sph_server_create.argtypes = [C.c_size_t, C.c_int, P(vp)]
+    L.sph_submit.argtypes = [vp, P(Request), P(C.c_uint64)]
+    L.sph_poll.argtypes = [vp, C.c_uint64, P(C.c_int)]
+    L.sph_wait.argtypes = [vp, C.c_uint64, C.c_int, P(Result)]
+    L.sph_server_stats.argtypes = [vp, P(ServerInfo)]
+    L.sph_server_destroy.argtypes = [vp]
+    L.sph_server_destroy.restype = None
     _lib = L
     return L
 
@@ -148,16 +179,41 @@ def _arg(a, dtype=np.float32):
 
 
 class Scene:
-    """One SPH scene in HBM: initial state in, steps, rollouts and adjoints through the C ABI."""
+    """One SPH scene (or a batch of independent scenes) in HBM: initial state in, steps,
+    rollouts and adjoints through the C ABI."""
 
     def __init__(self, params: dict, n_fluid: int, n_wall: int, x, v, rho, mass, stream=None):
+        self._init_batch([params], [n_fluid], [n_wall], [x], [v], [rho], [mass], stream)
+
+    @classmethod
+    def batch(cls, specs: list, stream=None, device: bool = False) -> "Scene":
+        """One scene object advancing several independent scenes with shared launches."""
+        self = cls.__new__(cls)
+        arr = lambda a: _torch().from_numpy(np.ascontiguousarray(a)).cuda() if device else a
+        self._init_batch([s["params"] for s in specs], [s["n_fluid"] for s in specs], [s["n_wall"] for s in specs],
+                         [arr(s["x"]) for s in specs], [arr(s["v"]) for s in specs], [arr(s["rho"]) for s in specs],
+                         [arr(s["mass"]) for s in specs], stream)
+        return self
+
+    def _init_batch(self, params, n_fluid, n_wall, xs, vs, rhos, masses, stream):
         L = lib()
-        self.params = dict(params)
-        self.dim = int(params["dim"])
-        self.n_fluid, self.n_wall = int(n_fluid), int(n_wall)
+        S = len(params)
+        self.n_scenes = S
+        self.params = dict(params[0])
+        self.dim = int(params[0]["dim"])
+        self.n_fluid = int(sum(n_fluid))
+        self.n_wall = int(sum(n_wall))
         self.n = self.n_fluid + self.n_wall
-        args = [_arg(a) for a in (x, v, rho, mass)]
-        dev = {d for _, _, d in args if d is not None}
+        keep = []
+        ptrs = {k: (C.c_void_p * S)() for k in ("x", "v", "rho", "mass")}
+        dev = set()
+        for k in range(S):
+            for name, a in (("x", xs[k]), ("v", vs[k]), ("rho", rhos[k]), ("mass", masses[k])):
+                p, ref, d = _arg(a)
+                ptrs[name][k] = p
+                keep.append(ref)
+                if d is not None:
+                    dev.add(d)
         if len(dev) != 1:
             raise ValueError("inputs must be all host arrays or all CUDA tensors")
         self.device_inputs = dev.pop()
@@ -166,13 +222,18 @@ class Scene:
         if stream is None and self.device_inputs:
             stream = _torch().cuda.current_stream().cuda_stream
         self.stream = int(stream or 0)
-        if self.stream and not self.device_inputs:
-            pass
-        self._p = Params.from_dict(params)
+        self._pa = (Params * S)(*[Params.from_dict(p) for p in params])
+        nf = (C.c_int * S)(*[int(a) for a in n_fluid])
+        nw = (C.c_int * S)(*[int(a) for a in n_wall])
         h = C.c_void_p()
-        _check(L.sph_init(C.byref(self._p), self.n_fluid, self.n_wall, args[0][0], args[1][0], args[2][0],
-                          args[3][0], int(self.device_inputs), C.c_void_p(self.stream), C.byref(h)))
+        _check(L.sph_init_batch(S, self._pa, nf, nw, ptrs["x"], ptrs["v"], ptrs["rho"], ptrs["mass"],
+                                int(self.device_inputs), C.c_void_p(self.stream), C.byref(h)))
         self._h = h
+        first = (C.c_int32 * S)()
+        rows = (C.c_int32 * S)()
+        _check(L.sph_batch_info(h, None, first, rows))
+        self.first_row = list(first)
+        self.rows = list(rows)
 
     # -- lifecycle
     def close(self):
@@ -230,7 +291,7 @@ class Scene:
         if len(flags) > 1:
             raise ValueError("adjoint seeds must be all host or all device")
         is_dev = bool(flags.pop()) if flags else bool(device)
-        nub = C.c_double()
+        nub = (C.c_double * self.n_scenes)()
         if is_dev:
             torch = _torch()
             ox = torch.empty((nf, d), device="cuda", dtype=torch.float32)
@@ -242,8 +303,8 @@ class Scene:
             ov = np.empty((nf, d), np.float32)
             orr = np.empty((nf,), np.float32)
             ptrs = [ox.ctypes.data, ov.ctypes.data, orr.ctypes.data]
-        _check(lib().sph_adjoint(self._h, ins[0][0], ins[1][0], ins[2][0], *ptrs, C.byref(nub), int(is_dev)))
-        return ox, ov, orr, nub.value
+        _check(lib().sph_adjoint(self._h, ins[0][0], ins[1][0], ins[2][0], *ptrs, nub, int(is_dev)))
+        return ox, ov, orr, (nub[0] if self.n_scenes == 1 else list(nub))
 
     # -- inspection
     def info(self):
@@ -285,6 +346,74 @@ class Scene:
         launches = C.c_int64()
         _check(lib().sph_counters(self._h, C.byref(pairs), C.byref(launches)))
         return pairs.value, launches.value
+
+
+class Server:
+    """Continuous-batching request loop of the library (sph_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 256):
+        h = C.c_void_p()
+        _check(lib().sph_server_create(int(hbm_budget_bytes), int(max_active), C.byref(h)))
+        self._h = h
+        self._meta = {}
+
+    def submit(self, spec: dict, n_steps: int, adjoint: bool = False, ckpt_every: int = 20, x_target=None) -> int:
+        keep = [np.ascontiguousarray(spec[k], np.float32) for k in ("x", "v", "rho", "mass")]
+        xt = None if x_target is None else np.ascontiguousarray(x_target, np.float32)
+        r = Request()
+        r.params = Params.from_dict(spec["params"])
+        r.n_fluid, r.n_wall = int(spec["n_fluid"]), int(spec["n_wall"])
+        r.x, r.v, r.rho, r.mass = (a.ctypes.data for a in keep)
+        r.n_steps = int(n_steps)
+        r.mode = REQ_ADJOINT if adjoint else REQ_FORWARD
+        r.ckpt_every = int(ckpt_every)
+        r.x_target = xt.ctypes.data if xt is not None else None
+        t = C.c_uint64()
+        _check(lib().sph_submit(self._h, C.byref(r), C.byref(t)))
+        n, d = spec["x"].shape
+        self._meta[t.value] = (n, d, adjoint)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = C.c_int()
+        _check(lib().sph_poll(self._h, C.c_uint64(ticket), C.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_ms: int = 600000) -> dict:
+        n, d, adj = self._meta[ticket]
+        out = dict(x=np.empty((n, d), np.float32), v=np.empty((n, d), np.float32), rho=np.empty(n, np.float32))
+        if adj:
+            out.update(xbar0=np.empty((n, d), np.float32), vbar0=np.empty((n, d), np.float32),
+                       rhobar0=np.empty(n, np.float32))
+        r = Result()
+        for k, a in out.items():
+            setattr(r, k, a.ctypes.data)
+        _check(lib().sph_wait(self._h, C.c_uint64(ticket), int(timeout_ms), C.byref(r)))
+        del self._meta[ticket]
+        out.update(nubar=r.nubar, loss=r.loss, t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done)
+        return out
+
+    def stats(self) -> dict:
+        i = ServerInfo()
+        _check(lib().sph_server_stats(self._h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in ServerInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sph_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def scene_from(spec: dict, stream=None, device: bool = False) -> Scene:

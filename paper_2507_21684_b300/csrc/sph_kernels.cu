@@ -301,6 +301,43 @@ __global__ void k_adj_store(int N, const uint2* __restrict__ meta, const int* __
   if (rb) rb[o] = a.w;
 }
 
+// Copy a particle range of one scene between packed batches; the scene index of the
+// destination is written into meta (the serving loop re-packs its active scenes).
+template <int D>
+__global__ void k_copy_range(Arrays src, int s0, Arrays dst, int d0, int n, int seg) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int i = s0 + k, j = d0 + k;
+  dst.A[j] = src.A[i];
+  dst.B[j] = src.B[i];
+  dst.X[j] = src.X[i];
+  dst.O[j] = src.O[i];
+  if (D == 3) {
+    dst.C[j] = src.C[i];
+    dst.XL[j] = src.XL[i];
+  }
+  uint2 m = src.meta[i];
+  m.y = (uint32_t)seg;
+  dst.meta[j] = m;
+}
+
+// State of one scene (rows [p0, p0 + n) of a batch) in its original particle order.
+template <int D>
+__global__ void k_download_range(Arrays a, int p0, int n, float* __restrict__ x, float* __restrict__ v,
+                                 float* __restrict__ rho) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int i = p0 + k;
+  const int o = (int)(a.meta[i].x & ~kWallBit);
+  PD<D> r = load_pd<D>(a, i);
+  Cold c = load_cold<D>(a, i);
+  for (int q = 0; q < D; ++q) {
+    x[(size_t)o * D + q] = __fadd_rn(c.hi[q], c.lo[q]);
+    v[(size_t)o * D + q] = r.v[q];
+  }
+  rho[o] = __fadd_rn(r.rho, c.rlo);
+}
+
 // ================================================================== launchers
 template <int D>
 void launch_keys(const DevSeg* segs, int N, const Arrays& a, uint32_t* keys, uint32_t* vals, cudaStream_t st) {
@@ -369,7 +406,18 @@ void launch_adj_store(int N, const uint2* meta, const int* orig_base, const floa
   if (N > 0) k_adj_store<D><<<(N + 255) / 256, 256, 0, st>>>(N, meta, orig_base, XB, VB, xb, vb, rb);
 }
 
+template <int D>
+void launch_copy_range(const Arrays& src, int s0, const Arrays& dst, int d0, int n, int seg, cudaStream_t st) {
+  if (n > 0) k_copy_range<D><<<(n + 255) / 256, 256, 0, st>>>(src, s0, dst, d0, n, seg);
+}
+template <int D>
+void launch_download_range(const Arrays& a, int p0, int n, float* x, float* v, float* rho, cudaStream_t st) {
+  if (n > 0) k_download_range<D><<<(n + 255) / 256, 256, 0, st>>>(a, p0, n, x, v, rho);
+}
+
 #define SPH_INST_D(D)                                                                                          \
+  template void launch_copy_range<D>(const Arrays&, int, const Arrays&, int, int, int, cudaStream_t);          \
+  template void launch_download_range<D>(const Arrays&, int, int, float*, float*, float*, cudaStream_t);       \
   template void launch_keys<D>(const DevSeg*, int, const Arrays&, uint32_t*, uint32_t*, cudaStream_t);           \
   template void launch_permute<D>(const DevSeg*, int, const uint32_t*, const Arrays&, const Arrays&, cudaStream_t); \
   template void launch_upload<D>(const DevSeg*, int, int, int, int, const float*, const float*, const float*,   \

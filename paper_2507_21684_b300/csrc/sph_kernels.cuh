@@ -51,4 +51,9 @@ template <int D>
 void launch_adj_store(int N, const uint2* meta, const int* orig_base, const float4* XB, const float4* VB, float* xb,
                       float* vb, float* rb, cudaStream_t st);
 
+template <int D>
+void launch_copy_range(const Arrays& src, int s0, const Arrays& dst, int d0, int n, int seg, cudaStream_t st);
+template <int D>
+void launch_download_range(const Arrays& a, int p0, int n, float* x, float* v, float* rho, cudaStream_t st);
+
 }  // namespace sph

@@ -768,6 +768,16 @@ __global__ void __launch_bounds__(256, 2) k_adj_t(TravArgs t, const Tile* tiles,
   run_tiles<D, (D == 2 ? 1 : 2), 0>(t, tiles, ntiles, S, D == 2 ? nullptr : Pp, pass);
 }
 
+// Per-scene deterministic sums of per-particle float partials (block s sums scene s, fixed order).
+__global__ void k_sum_segments(const float* __restrict__ part, const DevSeg* __restrict__ segs, double* __restrict__ acc) {
+  __shared__ double sh[32];
+  const DevSeg& s = segs[blockIdx.x];
+  double v = 0.0;
+  for (int k = s.p0 + threadIdx.x; k < s.p1; k += blockDim.x) v += (double)part[k];
+  double tot = block_sum(v, sh);
+  if (threadIdx.x == 0) acc[blockIdx.x] += tot;
+}
+
 // Deterministic sum of per-particle float partials into an FP64 accumulator (fixed order).
 __global__ void k_sum_float_partials(const float* __restrict__ part, int n, double* __restrict__ acc) {
   __shared__ double sh[32];
@@ -847,6 +857,9 @@ void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int t
   cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
   k_adj_t<D, KERN><<<pass_grid((const void*)k_adj_t<D, KERN>, tiles_upper), 256, pass_smem<D>(D == 2 ? 1 : 2), st>>>(
       t, tiles, ntiles, S, Pp, XBin, VBin, XBout, VBout, nu_part);
+}
+void launch_sum_segments(const float* part, const DevSeg* segs, int S, double* acc, cudaStream_t st) {
+  k_sum_segments<<<S, 1024, 0, st>>>(part, segs, acc);
 }
 void launch_sum_float_partials(const float* part, int n, double* acc, cudaStream_t st) {
   k_sum_float_partials<<<1, 1024, 0, st>>>(part, n, acc);

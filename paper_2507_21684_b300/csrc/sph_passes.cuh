@@ -28,5 +28,6 @@ void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int t
                   const float* Pp, const float4* XBin, const float4* VBin, float4* XBout, float4* VBout,
                   float* nu_part, cudaStream_t st);
 void launch_sum_float_partials(const float* part, int n, double* acc, cudaStream_t st);
+void launch_sum_segments(const float* part, const DevSeg* segs, int S, double* acc, cudaStream_t st);
 
 }  // namespace sph

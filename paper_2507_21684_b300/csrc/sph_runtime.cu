@@ -18,30 +18,9 @@ namespace sph {
 
 // ---------------------------------------------------------------- errors
 static thread_local std::string g_err;
-static void set_err(const std::string& s) { g_err = s; }
+void set_err(const std::string& s) { g_err = s; }
 const char* last_error() { return g_err.c_str(); }
-
-struct Fail {
-  int code;
-};
-#define CK(call)                                                                                     \
-  do {                                                                                               \
-    cudaError_t _e = (call);                                                                         \
-    if (_e != cudaSuccess) {                                                                         \
-      sph::set_err(std::string(#call) + ": " + cudaGetErrorString(_e));                                   \
-      throw sph::Fail{SPH_ECUDA};                                                                         \
-    }                                                                                                \
-  } while (0)
-#define CKL()                                                                                        \
-  do {                                                                                               \
-    cudaError_t _e = cudaGetLastError();                                                             \
-    if (_e != cudaSuccess) {                                                                         \
-      sph::set_err(std::string("kernel launch: ") + cudaGetErrorString(_e));                              \
-      throw sph::Fail{SPH_ECUDA};                                                                         \
-    }                                                                                                \
-  } while (0)
-
-static void einval(const std::string& s) {
+void einval(const std::string& s) {
   set_err(s);
   throw Fail{SPH_EINVAL};
 }
@@ -58,6 +37,13 @@ void set_allocator(sph_alloc_fn a, sph_free_fn f, void* ctx) {
   g_free = f;
   g_alloc_ctx = ctx;
 }
+void init_mem(DeviceMem& m) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  m.afn = g_alloc;
+  m.ffn = g_free;
+  m.actx = g_alloc_ctx;
+  m.fctx = g_alloc_ctx;
+}
 
 DeviceMem::~DeviceMem() { release(); }
 void* DeviceMem::get(size_t bytes) {
@@ -71,10 +57,21 @@ void* DeviceMem::get(size_t bytes) {
       throw Fail{SPH_ENOMEM};
     }
   } else {
-    cudaError_t e = cudaMalloc(&p, bytes);
+    // stream-ordered pool allocation: cheap once the pool has grown (scenes of the serving loop
+    // are created and destroyed at a high rate)
+    static std::once_flag pool_once;
+    std::call_once(pool_once, [] {
+      int dev = 0;
+      cudaMemPool_t pool;
+      if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+    });
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      set_err(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+      set_err(std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
       throw Fail{SPH_ENOMEM};
     }
   }
@@ -87,7 +84,7 @@ void DeviceMem::release() {
     if (ffn)
       ffn(b.first, b.second, (void*)stream, fctx);
     else
-      cudaFree(b.first);
+      cudaFreeAsync(b.first, stream);
   }
   blocks.clear();
   total = 0;
@@ -168,8 +165,13 @@ DevSeg make_seg(const sph_params& p, int n_fluid, int cell_base, int p0, int p1,
   s.Kg = (float)((p.kernel == 0 ? -56.0 / 3.0 : -20.0) * Cd / std::pow(H, d + 2));
   s.Kh = (float)((p.kernel == 0 ? 560.0 : 60.0) * Cd / std::pow(H, d + 4));
   for (int k = 0; k < 3; ++k) s.g[k] = k < d ? p.g[k] : 0.f;
-  // FP32 error of r^2 on folded positions is below ~8 ulp(|x|max) * |r|: guard band in r^2
-  double ex = 8.0 * std::ldexp(std::max(max_abs_x, 1.0), -23);
+  // FP32 error of r^2 on folded positions is below ~8 ulp(|x|max) * |r|: guard band in r^2.
+  // Only the box enters (folded positions stay within it up to one step of drift), so every
+  // parameter of a scene, and with it the order of its sums, is fixed by sph_params alone.
+  (void)max_abs_x;
+  double box_abs = 1.0;
+  for (int k = 0; k < p.dim; ++k) box_abs = std::max(box_abs, std::max(std::fabs(p.box_lo[k]), std::fabs(p.box_hi[k])));
+  double ex = 8.0 * std::ldexp(box_abs, -23);
   double band = std::max(1e-5, 4.0 * ex / H);
   s.band_lo = (float)(H * H * (1.0 - band));
   s.band_hi = (float)(H * H * (1.0 + band));
@@ -293,11 +295,10 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
       einval("all scenes of a batch must share skin and rebuild_interval");
   }
   if (S >= 4096) einval("at most 4095 scenes per batch");
-  static bool configured = false;
-  if (!configured) {
-    CK(configure_passes());
-    configured = true;
-  }
+  static std::once_flag cfg_once;
+  static cudaError_t cfg_err = cudaSuccess;
+  std::call_once(cfg_once, [] { cfg_err = configure_passes(); });
+  CK(cfg_err);
   nf_total = 0;
   for (int s = 0; s < S; ++s) nf_total += nfs[s];
   line_base_h.assign(S, 0);
@@ -342,7 +343,7 @@ void Scene::alloc_all() {
   d_tile_ctr = (int*)mem.get(sizeof(int) * 4);
   d_status = (int*)mem.get(sizeof(int) * 4);
   d_pairs = (unsigned long long*)mem.get(sizeof(unsigned long long) * 2);
-  d_nubar = (double*)mem.get(sizeof(double) * 2);
+  d_nubar = (double*)mem.get(sizeof(double) * (size_t)(S + 1));
   CK(cudaMemsetAsync(d_status, 0, sizeof(int) * 4, st));
   CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long) * 2, st));
   cells_valid = false;
@@ -739,7 +740,7 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
   else
     launch_adj_load<3>(N, buf[cur].meta, d_orig_base, dxb, dvb, drb, XB[q], VB[q], st);
   CKL();
-  CK(cudaMemsetAsync(d_nubar, 0, sizeof(double), st));
+  CK(cudaMemsetAsync(d_nubar, 0, sizeof(double) * S, st));
   const int ncp = (n + k - 1) / k;
   for (int sgi = ncp - 1; sgi >= 0; --sgi) {
     const int t0 = sgi * k, t1 = std::min(n, t0 + k);
@@ -795,7 +796,7 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
       }
       CKL();
       prof_end();
-      launch_sum_float_partials(nu_part, N, d_nubar, st);
+      launch_sum_segments(nu_part, dseg, S, d_nubar, st);
       CKL();
       q = 1 - q;
       if (rebuilt[s]) {
@@ -829,7 +830,7 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
     if (vb0) CK(cudaMemcpyAsync(vb0, ovb, 4 * nd, cudaMemcpyDeviceToHost, st));
     if (rb0) CK(cudaMemcpyAsync(rb0, orb, 4 * (size_t)nf_total, cudaMemcpyDeviceToHost, st));
   }
-  if (nub) CK(cudaMemcpyAsync(nub, d_nubar, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (nub) CK(cudaMemcpyAsync(nub, d_nubar, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
 }
 
@@ -1025,52 +1026,75 @@ int sph_set_allocator(sph_alloc_fn a, sph_free_fn f, void* ctx) {
   return SPH_OK;
 }
 
-int sph_init(const sph_params* params, int n_fluid, int n_wall, const float* x, const float* v, const float* rho,
-             const float* mass, int ptr_is_device, void* cuda_stream, sph_scene** out) {
-  if (!params || !x || !rho || !mass || !out) {
-    sph::set_err("sph_init: params, x, rho, mass and out must be non-NULL");
+static int init_scenes(int S, const sph_params* params, const int* n_fluid, const int* n_wall, const float* const* x,
+                       const float* const* v, const float* const* rho, const float* const* mass, int ptr_is_device,
+                       void* cuda_stream, sph_scene** out) {
+  if (S < 1 || !params || !n_fluid || !n_wall || !x || !rho || !mass || !out) {
+    sph::set_err("sph_init: params, counts, x, rho, mass and out must be non-NULL");
     return SPH_EINVAL;
   }
   *out = nullptr;
   sph_scene* sc = nullptr;
-  API_BEGIN
-  sc = new sph_scene();
-  Scene& s = sc->s;
-  {
-    std::lock_guard<std::mutex> lk(sph::g_alloc_mu);
-    s.mem.afn = sph::g_alloc;
-    s.mem.ffn = sph::g_free;
-    s.mem.actx = sph::g_alloc_ctx;
-    s.mem.fctx = sph::g_alloc_ctx;
-  }
-  double mx = 1.0;
-  for (int k = 0; k < 3; ++k) mx = std::max(mx, std::max(std::fabs(params->box_lo[k]), std::fabs(params->box_hi[k])));
-  if (!ptr_is_device) {
-    size_t nd = (size_t)(n_fluid + n_wall) * params->dim;
-    for (size_t q = 0; q < nd; ++q) {
-      if (!std::isfinite(x[q])) sph::einval("non-finite initial position");
-      mx = std::max(mx, (double)std::fabs(x[q]));
+  try {
+    std::vector<sph_params> prm(params, params + S);
+    std::vector<int> nf(n_fluid, n_fluid + S), nw(n_wall, n_wall + S);
+    std::vector<double> mx(S, 1.0);
+    for (int k = 0; k < S; ++k) {
+      if (!x[k] || !rho[k] || !mass[k]) sph::einval("sph_init: missing array of scene " + std::to_string(k));
+      for (int q = 0; q < 3; ++q)
+        mx[k] = std::max(mx[k], std::max(std::fabs(params[k].box_lo[q]), std::fabs(params[k].box_hi[q])));
+      if (!ptr_is_device) {
+        const size_t nd = (size_t)(n_fluid[k] + n_wall[k]) * (size_t)std::max(params[k].dim, 1);
+        for (size_t q = 0; q < nd; ++q) {
+          if (!std::isfinite(x[k][q])) sph::einval("non-finite initial position");
+          mx[k] = std::max(mx[k], (double)std::fabs(x[k][q]));
+        }
+      } else {
+        mx[k] = std::max(mx[k], 16.0);
+      }
     }
-  } else {
-    mx = std::max(mx, 16.0);
-  }
-  s.setup_checked({*params}, {n_fluid}, {n_wall}, {mx});
-  s.bind_stream((cudaStream_t)cuda_stream);
-  s.enter();
-  s.alloc_all();
-  s.upload(0, x, v, rho, mass, ptr_is_device);
-  CK(cudaStreamSynchronize(s.st));
-  *out = sc;
-  sc = nullptr;
-  }
-  catch (const Fail& f) {
+    sc = new sph_scene();
+    Scene& s = sc->s;
+    sph::init_mem(s.mem);
+    s.setup_checked(prm, nf, nw, mx);
+    s.bind_stream((cudaStream_t)cuda_stream);
+    s.enter();
+    s.alloc_all();
+    for (int k = 0; k < S; ++k) s.upload(k, x[k], v ? v[k] : nullptr, rho[k], mass[k], ptr_is_device);
+    CK(cudaStreamSynchronize(s.st));
+    *out = sc;
+    sc = nullptr;
+  } catch (const Fail& f) {
     delete sc;
     return f.code;
-  }
-  catch (...) {
+  } catch (...) {
     delete sc;
     sph::set_err("sph_init: unexpected failure");
     return SPH_EINTERNAL;
+  }
+  return SPH_OK;
+}
+
+int sph_init(const sph_params* params, int n_fluid, int n_wall, const float* x, const float* v, const float* rho,
+             const float* mass, int ptr_is_device, void* cuda_stream, sph_scene** out) {
+  return init_scenes(1, params, &n_fluid, &n_wall, &x, &v, &rho, &mass, ptr_is_device, cuda_stream, out);
+}
+
+int sph_init_batch(int n_scenes, const sph_params* params, const int* n_fluid, const int* n_wall,
+                   const float* const* x, const float* const* v, const float* const* rho, const float* const* mass,
+                   int ptr_is_device, void* cuda_stream, sph_scene** out) {
+  return init_scenes(n_scenes, params, n_fluid, n_wall, x, v, rho, mass, ptr_is_device, cuda_stream, out);
+}
+
+int sph_batch_info(const sph_scene* sc, int* n_scenes, int32_t* first_row, int32_t* n_rows) {
+  if (!sc) {
+    sph::set_err("sph_batch_info: NULL scene");
+    return SPH_EINVAL;
+  }
+  if (n_scenes) *n_scenes = sc->s.S;
+  for (int k = 0; k < sc->s.S; ++k) {
+    if (first_row) first_row[k] = sc->s.orig_base[k];
+    if (n_rows) n_rows[k] = sc->s.segs[k].p1 - sc->s.segs[k].p0;
   }
   return SPH_OK;
 }

@@ -11,8 +11,31 @@
 
 namespace sph {
 
+// Errors: internal code throws Fail{status}; the C entry points turn it into the return value.
+struct Fail {
+  int code;
+};
+void set_err(const std::string& s);
+void einval(const std::string& s);
 const char* last_error();
 void set_allocator(sph_alloc_fn a, sph_free_fn f, void* ctx);
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t _e = (call);                                                         \
+    if (_e != cudaSuccess) {                                                         \
+      sph::set_err(std::string(#call) + ": " + cudaGetErrorString(_e));              \
+      throw sph::Fail{SPH_ECUDA};                                                    \
+    }                                                                                \
+  } while (0)
+#define CKL()                                                                        \
+  do {                                                                               \
+    cudaError_t _e = cudaGetLastError();                                             \
+    if (_e != cudaSuccess) {                                                         \
+      sph::set_err(std::string("kernel launch: ") + cudaGetErrorString(_e));         \
+      throw sph::Fail{SPH_ECUDA};                                                    \
+    }                                                                                \
+  } while (0)
 
 // Device memory owned by one scene (allocator hook or cudaMalloc); freed with the scene.
 struct DeviceMem {
@@ -27,6 +50,7 @@ struct DeviceMem {
   void release();
   ~DeviceMem();
 };
+void init_mem(DeviceMem& m);
 
 struct ProfEvent {
   int cls;

@@ -1,0 +1,79 @@
+"""Serving loop: continuous batching gives each request the same result as running it alone;
+admission honours the HBM budget; waits are bounded."""
+import time
+
+import numpy as np
+import pytest
+
+import sph_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sph():
+    from paper_2507_21684_b300 import build
+    build.build()
+    import paper_2507_21684_b300 as m
+    return m
+
+
+def _alone(sph, spec, steps, adjoint=False, ckpt=20, x_target=None):
+    with sph.scene_from(spec) as sc:
+        if not adjoint:
+            sc.step(steps)
+            return dict(zip(("x", "v", "rho"), sc.get_state()))
+        sc.rollout(steps, ckpt)
+        x, v, r = sc.get_state()
+        tgt = spec["x"] if x_target is None else x_target
+        seed = (2.0 * (x.astype(np.float64) - tgt) / spec["n_fluid"]).astype(np.float32)
+        gx, gv, gr, nub = sc.adjoint(seed, None, None)
+        return dict(x=x, v=v, rho=r, xbar0=gx, vbar0=gv, rhobar0=gr, nubar=nub)
+
+
+def test_served_results_equal_alone(sph):
+    specs = [si.taylor_green_2d(n, seed=k) for k, n in enumerate([16, 40, 24, 32, 20])]
+    steps = [13, 31, 7, 20, 26]
+    adj = [False, False, True, False, True]
+    with sph.Server(8 << 30, 64) as sv:
+        tickets = []
+        for sp, st, a in zip(specs, steps, adj):
+            tickets.append(sv.submit(sp, st, adjoint=a, ckpt_every=5))
+            time.sleep(0.002)  # staggered arrivals: requests join a batch that is already running
+        got = [sv.wait(t) for t in tickets]
+        info = sv.stats()
+    assert info["repacks"] >= 2
+    for sp, st, a, g in zip(specs, steps, adj, got):
+        ref = _alone(sph, sp, st, adjoint=a, ckpt=5)
+        for k in ("x", "v", "rho"):
+            assert np.array_equal(g[k], ref[k]), k
+        if a:
+            for k in ("xbar0", "vbar0", "rhobar0"):
+                assert np.array_equal(g[k], ref[k]), k
+            assert g["nubar"] == ref["nubar"]
+
+
+def test_admission_respects_budget_and_wait_is_bounded(sph):
+    specs = [si.taylor_green_2d(48, seed=k) for k in range(4)]
+    # budget for about one scene at a time: requests queue and run one after another
+    with sph.Server(2 << 20, 16) as sv:
+        tickets = [sv.submit(sp, 60) for sp in specs]
+        with pytest.raises(sph.SphError) as e:
+            sv.wait(tickets[-1], timeout_ms=0)
+        assert e.value.code == sph.SPH_ETIMEOUT
+        res = [sv.wait(t) for t in tickets]
+        info = sv.stats()
+    assert info["max_batch"] == 1
+    t_admit = [r["t_admit"] for r in res]
+    t_done = [r["t_done"] for r in res]
+    assert all(t_admit[k + 1] >= t_done[k] - 1e-3 for k in range(3))
+    ref = _alone(sph, specs[2], 60)
+    assert np.array_equal(res[2]["x"], ref["x"])
+
+
+def test_request_over_budget_is_rejected(sph):
+    sp = si.taylor_green_2d(64)
+    with sph.Server(1 << 20, 4) as sv:
+        with pytest.raises(sph.SphError) as e:
+            sv.submit(sp, 10)
+        assert e.value.code == sph.SPH_EINVAL
