@@ -182,6 +182,65 @@ def run_adjoint(sph, torch, spec, steps, ckpt):
     return dict(ms=total, pairs_per_step=pairs_per_step, adj_sweep_ms=adj_ms / max(adj_n, 1), adj_sweeps=adj_n)
 
 
+def _stream_specs(n_scenes: int, rate: float, seed: int = 0):
+    import sph_inputs as si
+    reqs = si.served_stream(n_scenes=n_scenes, rate_hz=rate, seed=seed)
+    out = []
+    for r in reqs:
+        sp = si.taylor_green_2d(r.n_side, seed=r.seed)
+        out.append((r, sp))
+    return out
+
+
+def run_plain(sph, reqs):
+    """Each request alone, in arrival order, one after another (the per-scene GPU path)."""
+    import torch
+    t0 = time.perf_counter()
+    lat, ps = [], 0.0
+    for r, sp in reqs:
+        now = time.perf_counter() - t0
+        if now < r.arrival_s:
+            time.sleep(r.arrival_s - now)
+        with sph.scene_from(sp) as sc:
+            if r.adjoint:
+                sc.rollout(r.steps, 20)
+                x, _, _ = sc.get_state()
+                seed = (2.0 * (x.astype(np.float64) - sp["x"]) / sp["n_fluid"]).astype(np.float32)
+                sc.adjoint(seed, None, None)
+            else:
+                sc.step(r.steps)
+                sc.get_state()
+        lat.append(time.perf_counter() - t0 - r.arrival_s)
+        ps += sp["n_fluid"] * r.steps
+    span = time.perf_counter() - t0
+    return dict(particle_steps_per_s=ps / span, p50_s=float(np.percentile(lat, 50)),
+                p99_s=float(np.percentile(lat, 99)), makespan_s=span)
+
+
+def run_served(sph, reqs, budget=120 << 30):
+    """Requests submitted at their arrival times to the continuous-batching server."""
+    with sph.Server(budget, 1024) as sv:
+        t0 = time.perf_counter()
+        tickets = []
+        for r, sp in reqs:
+            now = time.perf_counter() - t0
+            if now < r.arrival_s:
+                time.sleep(r.arrival_s - now)
+            tickets.append((sv.submit(sp, r.steps, adjoint=r.adjoint, ckpt_every=20), r, sp))
+        lat, ps = [], 0.0
+        t_end = 0.0
+        for t, r, sp in tickets:
+            res = sv.wait(t)
+            lat.append(res["t_done"] - res["t_submit"])
+            t_end = max(t_end, res["t_done"])
+            ps += sp["n_fluid"] * r.steps
+        span = time.perf_counter() - t0
+        info = sv.stats()
+    return dict(particle_steps_per_s=ps / span, p50_s=float(np.percentile(lat, 50)),
+                p99_s=float(np.percentile(lat, 99)), makespan_s=span, max_batch=info["max_batch"],
+                repacks=info["repacks"])
+
+
 def cpu_baseline(spec, budget_s: float = 15.0):
     """The FP64 oracle as it stands, on the host cores: pair interactions/s on a bounded sample
     (a short rollout of the same scene)."""
@@ -213,6 +272,8 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="forward steps of one workload only (for ncu): no extras, e2e or CPU leg")
     ap.add_argument("--workload", default="dambreak", choices=["dambreak", "tgv3d"])
+    ap.add_argument("--stream-scenes", type=int, default=64, help="requests of the served mixed-size stream")
+    ap.add_argument("--stream-rates", type=float, nargs="*", default=[20.0, 80.0, 320.0])
     args = ap.parse_args()
     ws, rank = _dist()
     import sph_inputs as si
@@ -301,6 +362,18 @@ def main():
             "adjoint_sweep_ms": ad["adj_sweep_ms"],
             "adjoint_sweep_pairs_per_s": ad["pairs_per_step"] / (ad["adj_sweep_ms"] / 1e3),
             "note": "time of sph_adjoint: 10 segment recomputes (forward replay) + 200 adjoint sweeps"}
+        stream = {}
+        for rate in args.stream_rates:
+            reqs = _stream_specs(args.stream_scenes, rate)
+            pl = run_plain(sph, reqs)
+            sv = run_served(sph, reqs)
+            stream[f"{rate:g}_req_s"] = {"plain": pl, "served": sv,
+                                         "served_over_plain_throughput": sv["particle_steps_per_s"] / pl["particle_steps_per_s"],
+                                         "served_over_plain_p99": sv["p99_s"] / pl["p99_s"]}
+        extras["served_stream"] = {
+            "scenes": args.stream_scenes, "sizes": "log-uniform in [1024, 262144] (square lattices)",
+            "steps": "uniform in [50, 500]", "adjoint_fraction": 0.2, "arrivals": "Poisson", "by_rate": stream,
+            "metric": "fluid particle-steps/s over the makespan; latency = completion - arrival"}
     e2e = None
     if rank == 0:
         ee = run_e2e(sph, torch, spec, 2000, 2)

@@ -12,10 +12,7 @@ namespace sph {
 // Cell key of every particle in the current storage order (P2: floor-modulo wrap on
 // periodic axes, clamp on open axes; all in FP64 from the float32 unwrapped position).
 template <int D>
-__global__ void k_keys(const DevSeg* __restrict__ segs, int N, Arrays a, uint32_t* __restrict__ keys,
-                       uint32_t* __restrict__ vals) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+__device__ __forceinline__ uint32_t cell_key_of(const DevSeg* __restrict__ segs, const Arrays& a, int i) {
   const DevSeg& s = segs[a.meta[i].y];
   Cold c = load_cold<D>(a, i);
   int cc3[3] = {0, 0, 0};
@@ -31,8 +28,7 @@ __global__ void k_keys(const DevSeg* __restrict__ segs, int N, Arrays a, uint32_
     cc = fmin(fmax(cc, 0.0), (double)(s.n[k] - 1));
     cc3[k] = (int)cc;
   }
-  keys[i] = (uint32_t)(s.cell_base + (cc3[2] * s.n[1] + cc3[1]) * s.n[0] + cc3[0]);
-  vals[i] = (uint32_t)i;
+  return (uint32_t)(s.cell_base + (cc3[2] * s.n[1] + cc3[1]) * s.n[0] + cc3[0]);
 }
 
 // ---- stable LSD radix sort, 8-bit digits, 2048-key tiles ---------------------------------
@@ -40,8 +36,12 @@ constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;
 constexpr int kSortTile = kSortThreads * kSortIPT;
 
+// Histogram of one digit per 2048-key tile.  KEYS_FROM_STATE: the keys are the cell keys of the
+// current storage order, computed here (first pass of a rebuild) instead of read.
+template <int D, bool KEYS_FROM_STATE>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, int N, int shift,
-                                                            uint32_t* __restrict__ hist, int nblocks) {
+                                                            uint32_t* __restrict__ hist, int nblocks,
+                                                            const DevSeg* __restrict__ segs, Arrays a) {
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
@@ -49,7 +49,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
 #pragma unroll
   for (int k = 0; k < kSortIPT; ++k) {
     int i = base + k * kSortThreads + threadIdx.x;
-    if (i < N) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    if (i < N) {
+      const uint32_t key = KEYS_FROM_STATE ? cell_key_of<D>(segs, a, i) : keys[i];
+      atomicAdd(&h[(key >> shift) & 255u], 1u);
+    }
   }
   __syncthreads();
   hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
@@ -85,6 +88,44 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ a, 
     if (base + k < n) a[base + k] = sh[k];
 }
 
+// Exclusive scan of up to 16384 values in one CTA of 1024 threads (16 consecutive per thread).
+__global__ void __launch_bounds__(1024) k_scan_single(uint32_t* __restrict__ a, int n) {
+  __shared__ uint32_t wsum[32];
+  const int t = threadIdx.x, base = t * 16;
+  uint32_t v[16], run = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    v[k] = (base + k < n) ? a[base + k] : 0u;
+    const uint32_t x = v[k];
+    v[k] = run;
+    run += x;
+  }
+  // exclusive scan of the per-thread totals: warp shuffles, then the warp totals
+  const int lane = t & 31, w = t >> 5;
+  uint32_t incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t ws = wsum[lane], wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, wi, o);
+      if (lane >= o) wi += y;
+    }
+    wsum[lane] = wi - ws;
+  }
+  __syncthreads();
+  const uint32_t off = wsum[w] + incl - run;
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    if (base + k < n) a[base + k] = v[k] + off;
+}
+
 __global__ void k_scan_add(uint32_t* __restrict__ a, int n, const uint32_t* __restrict__ sums) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] += sums[i / 2048];
@@ -92,11 +133,12 @@ __global__ void k_scan_add(uint32_t* __restrict__ a, int n, const uint32_t* __re
 
 // Scatter with stable ranks: warp w owns the contiguous sub-tile [w*256, w*256+256) and walks
 // it in 8 rounds of 32; within a round, equal digits are ranked by lane via match_any.
+template <int D, bool KEYS_FROM_STATE>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
                                                                const uint32_t* __restrict__ vin,
                                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                                int N, int shift, const uint32_t* __restrict__ hist,
-                                                               int nblocks) {
+                                                               int nblocks, const DevSeg* __restrict__ segs, Arrays a) {
   constexpr int W = kSortThreads / 32;
   __shared__ uint32_t cnt[W][257];
   __shared__ uint32_t goff[256];
@@ -110,8 +152,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
   for (int r = 0; r < kSortIPT; ++r) {
     int i = base + r * 32 + lane;
     bool ok = i < N;
-    kk[r] = ok ? kin[i] : 0u;
-    vv[r] = ok ? vin[i] : 0u;
+    if (KEYS_FROM_STATE) {
+      kk[r] = ok ? cell_key_of<D>(segs, a, i) : 0u;
+      vv[r] = (uint32_t)i;
+    } else {
+      kk[r] = ok ? kin[i] : 0u;
+      vv[r] = ok ? vin[i] : 0u;
+    }
     uint32_t dg = ok ? ((kk[r] >> shift) & 255u) : 256u;
     uint32_t peers = __match_any_sync(kFull, dg);
     uint32_t before = __popc(peers & ((1u << lane) - 1u));
@@ -143,20 +190,19 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
   }
 }
 
-// CSR cell offsets: off[c] = first sorted index whose key >= c, for c in [0, C].
-__global__ void k_cell_offsets(const uint32_t* __restrict__ keys, int N, int C, int* __restrict__ off) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k > N) return;
-  int lo = (k == 0) ? 0 : (int)keys[k - 1] + 1;
-  int hi = (k < N) ? (int)keys[k] : C;
-  for (int c = lo; c <= hi; ++c) off[c] = k;
-}
 
-// Gather the state into sorted order; re-fold positions into the primary box.
+// Gather the state into sorted order and re-fold positions into the primary box; thread k also
+// writes the CSR offsets of the cells in (key[k-1], key[k]] (off[c] = first index with key >= c).
 template <int D>
 __global__ void k_permute(const DevSeg* __restrict__ segs, int N, const uint32_t* __restrict__ perm, Arrays in,
-                          Arrays out) {
+                          Arrays out, const uint32_t* __restrict__ keys, int C, int* __restrict__ off) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > N) return;
+  {
+    const int lo = (k == 0) ? 0 : (int)keys[k - 1] + 1;
+    const int hi = (k < N) ? (int)keys[k] : C;
+    for (int c = lo; c <= hi; ++c) off[c] = k;
+  }
   if (k >= N) return;
   int src = (int)perm[k];
   uint2 m = in.meta[src];
@@ -339,28 +385,37 @@ __global__ void k_download_range(Arrays a, int p0, int n, float* __restrict__ x,
 }
 
 // ================================================================== launchers
-template <int D>
-void launch_keys(const DevSeg* segs, int N, const Arrays& a, uint32_t* keys, uint32_t* vals, cudaStream_t st) {
-  if (N > 0) k_keys<D><<<(N + 255) / 256, 256, 0, st>>>(segs, N, a, keys, vals);
-}
 
-// Exclusive scan of n uint32 values in place (2048 per block, block totals in sums).
+// Exclusive scan of n uint32 values in place: one CTA up to 16384 values, else 2048 per block
+// with the block totals in sums.
 void launch_exclusive_scan(uint32_t* a, int n, uint32_t* sums, cudaStream_t st) {
   if (n <= 0) return;
-  const int sb = (n + 2047) / 2048;
-  k_scan_blocks<<<sb, 1024, 0, st>>>(a, n, sb > 1 ? sums : nullptr);
-  if (sb > 1) {
-    k_scan_blocks<<<1, 1024, 0, st>>>(sums, sb, nullptr);
-    k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(a, n, sums);
+  if (n <= 16384) {
+    k_scan_single<<<1, 1024, 0, st>>>(a, n);
+    return;
   }
+  const int sb = (n + 2047) / 2048;
+  k_scan_blocks<<<sb, 1024, 0, st>>>(a, n, sums);
+  k_scan_blocks<<<1, 1024, 0, st>>>(sums, sb, nullptr);
+  k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(a, n, sums);
 }
 
+// One LSD pass.  With segs set, the keys of the current storage order are computed on the fly
+// (first pass) and the values are the storage indices.
+template <int D>
 void launch_sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, int N, int shift,
-                      uint32_t* hist, uint32_t* sums, cudaStream_t st) {
+                      uint32_t* hist, uint32_t* sums, const DevSeg* segs, const Arrays& a, cudaStream_t st) {
+  if (N <= 0) return;
   int nb = (N + kSortTile - 1) / kSortTile;
-  k_sort_hist<<<nb, kSortThreads, 0, st>>>(kin, N, shift, hist, nb);
-  launch_exclusive_scan(hist, 256 * nb, sums, st);
-  k_sort_scatter<<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, shift, hist, nb);
+  if (segs) {
+    k_sort_hist<D, true><<<nb, kSortThreads, 0, st>>>(kin, N, shift, hist, nb, segs, a);
+    launch_exclusive_scan(hist, 256 * nb, sums, st);
+    k_sort_scatter<D, true><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, shift, hist, nb, segs, a);
+  } else {
+    k_sort_hist<D, false><<<nb, kSortThreads, 0, st>>>(kin, N, shift, hist, nb, segs, a);
+    launch_exclusive_scan(hist, 256 * nb, sums, st);
+    k_sort_scatter<D, false><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, shift, hist, nb, segs, a);
+  }
 }
 
 int sort_scratch_words(int N) {
@@ -368,14 +423,10 @@ int sort_scratch_words(int N) {
   return 256 * nb + 2048 + 64;
 }
 
-void launch_cell_offsets(const uint32_t* keys, int N, int C, int* off, cudaStream_t st) {
-  k_cell_offsets<<<(N + 1 + 255) / 256, 256, 0, st>>>(keys, N, C, off);
-}
-
 template <int D>
 void launch_permute(const DevSeg* segs, int N, const uint32_t* perm, const Arrays& in, const Arrays& out,
-                    cudaStream_t st) {
-  if (N > 0) k_permute<D><<<(N + 255) / 256, 256, 0, st>>>(segs, N, perm, in, out);
+                    const uint32_t* keys, int C, int* off, cudaStream_t st) {
+  k_permute<D><<<(N + 1 + 255) / 256, 256, 0, st>>>(segs, N, perm, in, out, keys, C, off);
 }
 template <int D>
 void launch_upload(const DevSeg* segs, int seg, int n, int nf, int p0, const float* x, const float* v, const float* rho,
@@ -418,8 +469,10 @@ void launch_download_range(const Arrays& a, int p0, int n, float* x, float* v, f
 #define SPH_INST_D(D)                                                                                          \
   template void launch_copy_range<D>(const Arrays&, int, const Arrays&, int, int, int, cudaStream_t);          \
   template void launch_download_range<D>(const Arrays&, int, int, float*, float*, float*, cudaStream_t);       \
-  template void launch_keys<D>(const DevSeg*, int, const Arrays&, uint32_t*, uint32_t*, cudaStream_t);           \
-  template void launch_permute<D>(const DevSeg*, int, const uint32_t*, const Arrays&, const Arrays&, cudaStream_t); \
+  template void launch_permute<D>(const DevSeg*, int, const uint32_t*, const Arrays&, const Arrays&, const uint32_t*, \
+                                  int, int*, cudaStream_t);                                                     \
+  template void launch_sort_pass<D>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int, int, uint32_t*,   \
+                                    uint32_t*, const DevSeg*, const Arrays&, cudaStream_t);                     \
   template void launch_upload<D>(const DevSeg*, int, int, int, int, const float*, const float*, const float*,   \
                                  const float*, const Arrays&, cudaStream_t);                                   \
   template void launch_download<D>(int, const Arrays&, const int*, float*, float*, float*, cudaStream_t);       \

@@ -27,13 +27,11 @@ struct RateOut {
 int sort_scratch_words(int N);
 void launch_exclusive_scan(uint32_t* a, int n, uint32_t* sums, cudaStream_t st);
 template <int D>
-void launch_keys(const DevSeg* segs, int N, const Arrays& a, uint32_t* keys, uint32_t* vals, cudaStream_t st);
 void launch_sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, int N, int shift,
-                      uint32_t* hist, uint32_t* sums, cudaStream_t st);
-void launch_cell_offsets(const uint32_t* keys, int N, int C, int* off, cudaStream_t st);
+                      uint32_t* hist, uint32_t* sums, const DevSeg* segs, const Arrays& a, cudaStream_t st);
 template <int D>
 void launch_permute(const DevSeg* segs, int N, const uint32_t* perm, const Arrays& in, const Arrays& out,
-                    cudaStream_t st);
+                    const uint32_t* keys, int C, int* off, cudaStream_t st);
 template <int D>
 void launch_upload(const DevSeg* segs, int seg, int n, int nf, int p0, const float* x, const float* v,
                    const float* rho, const float* mass, const Arrays& a, cudaStream_t st);

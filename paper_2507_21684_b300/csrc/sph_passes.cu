@@ -14,63 +14,13 @@
 namespace sph {
 
 // ================================================================== tile table
-// Tiles of one cell line are cut at cell boundaries: a tile holds at most TP particles and spans
-// at most TP cells (so its column table fits); a cell with more than TP particles is split into
-// tiles of its own.  One thread per line walks the line's cells twice (count, then emit).
-template <int D, bool EMIT>
-__device__ __forceinline__ int line_tiles(const DevSeg& s, int first, int ll, const int* __restrict__ cell_off,
-                                          Tile* __restrict__ out, int seg, int line) {
-  constexpr int TP = TileCfg<D>::TP;
-  const int nx = s.n[0];
-  int nt = 0;
-  int t_start = -1, t_c0 = 0, t_c1 = 0, t_cnt = 0;
-  auto close = [&]() {
-    if (t_start >= 0) {
-      if (EMIT) {
-        Tile t;
-        t.p0 = t_start;
-        t.p1 = t_start + t_cnt;
-        t.seg = seg;
-        t.line = line;
-        t.cx0 = t_c0;
-        t.cx1 = t_c1;
-        t.cy = ll % s.n[1];
-        t.cz = ll / s.n[1];
-        out[nt] = t;
-      }
-      ++nt;
-      t_start = -1;
-      t_cnt = 0;
-    }
-  };
-  int o0 = cell_off[first];
-  for (int c = 0; c < nx; ++c) {
-    const int o1 = cell_off[first + c + 1];
-    const int n = o1 - o0;
-    if (n > 0) {
-      if (t_start >= 0 && (t_cnt + n > TP || c - t_c0 > TP - 1)) close();
-      if (n > TP) {
-        for (int k = 0; k < n; k += TP) {  // an over-full cell: tiles of its own
-          t_start = o0 + k;
-          t_cnt = min(TP, n - k);
-          t_c0 = t_c1 = c;
-          close();
-        }
-      } else {
-        if (t_start < 0) {
-          t_start = o0;
-          t_c0 = c;
-        }
-        t_cnt += n;
-        t_c1 = c;
-      }
-    }
-    o0 = o1;
-  }
-  close();
-  return nt;
-}
-
+// Tiles of one cell line are cut at cell boundaries, greedily from the left: a tile holds at
+// most TP particles and spans at most TP cells (so its column table fits); a cell with more
+// than TP particles is split into tiles of its own.  One warp per line: the lanes hold the
+// offsets of 32 consecutive cells, and each tile boundary is one ballot over them (the
+// conditions "count <= TP" and "span <= TP" are monotone along the line).  Finished tiles
+// wait in the registers of lane (k mod 32) and are written in batches of 32 at slots
+// reserved with one atomic; the order of the tiles in the table affects no result.
 __device__ __forceinline__ int seg_of_line(const int* __restrict__ line_base, int S, int l) {
   int lo = 0, hi = S - 1;
   while (lo < hi) {
@@ -81,32 +31,88 @@ __device__ __forceinline__ int seg_of_line(const int* __restrict__ line_base, in
 }
 
 template <int D>
-__global__ void k_tile_count(const DevSeg* __restrict__ segs, int S, const int* __restrict__ line_base, int n_lines,
-                             const int* __restrict__ cell_off, uint32_t* __restrict__ counts) {
-  int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= n_lines) return;
+__global__ void __launch_bounds__(256) k_tiles(const DevSeg* __restrict__ segs, int S,
+                                               const int* __restrict__ line_base, int n_lines,
+                                               const int* __restrict__ cell_off, Tile* __restrict__ tiles,
+                                               int* __restrict__ ntiles) {
+  constexpr int TP = TileCfg<D>::TP;
+  const int lane = threadIdx.x & 31;
+  const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (l >= n_lines) return;  // warp-uniform
   const int sg = seg_of_line(line_base, S, l);
   const DevSeg& s = segs[sg];
   const int ll = l - line_base[sg];
-  const int first = s.cell_base + ll * s.n[0];
-  counts[l] = (uint32_t)line_tiles<D, false>(s, first, ll, cell_off, nullptr, sg, l);
-}
-
-template <int D>
-__global__ void k_tile_emit(const DevSeg* __restrict__ segs, int S, const int* __restrict__ line_base, int n_lines,
-                            const int* __restrict__ cell_off, const uint32_t* __restrict__ keys,
-                            const uint32_t* __restrict__ base, const uint32_t* __restrict__ counts_copy,
-                            Tile* __restrict__ tiles, int* __restrict__ ntiles) {
-  int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= n_lines) return;
-  const int sg = seg_of_line(line_base, S, l);
-  const DevSeg& s = segs[sg];
-  const int ll = l - line_base[sg];
-  const int first = s.cell_base + ll * s.n[0];
-  const int b = (int)base[l];
-  line_tiles<D, true>(s, first, ll, cell_off, tiles + b, sg, l);
-  if (l == n_lines - 1) *ntiles = b + (int)counts_copy[l];
-  (void)keys;
+  const int nx = s.n[0];
+  const int first = s.cell_base + ll * nx;
+  const int cy = ll % s.n[1], cz = ll / s.n[1];
+  Tile mine;  // the pending tile this lane holds
+  int pending = 0;
+  auto emit = [&](int p0, int p1, int c0, int c1) {  // warp-uniform arguments
+    if (lane == pending) {
+      mine.p0 = p0; mine.p1 = p1; mine.seg = sg; mine.line = l;
+      mine.cx0 = c0; mine.cx1 = c1; mine.cy = cy; mine.cz = cz;
+    }
+    if (++pending == 32) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(ntiles, 32);
+      base = __shfl_sync(kFull, base, 0);
+      tiles[base + lane] = mine;
+      pending = 0;
+    }
+  };
+  // open tile: first cell, first particle, last non-empty cell and its end offset
+  bool open = false;
+  int t_a = 0, t_p = 0, t_last = 0, t_end = 0;
+  for (int w0 = 0; w0 < nx; w0 += 32) {
+    const int c = w0 + lane;
+    const bool in = c < nx;
+    const int o0 = in ? cell_off[first + c] : 0;
+    const int o1 = in ? cell_off[first + c + 1] : 0;
+    const unsigned nonempty = __ballot_sync(kFull, in && o1 > o0);
+    const bool last_window = w0 + 32 >= nx;
+    int cur = 0;  // first lane not yet consumed
+    while (cur < 32) {
+      if (!open) {
+        const unsigned m = nonempty & (~0u << cur);
+        if (!m) break;
+        const int j = __ffs(m) - 1;
+        const int p0 = __shfl_sync(kFull, o0, j), p1 = __shfl_sync(kFull, o1, j);
+        if (p1 - p0 > TP) {  // an over-full cell: tiles of its own
+          for (int k = p0; k < p1; k += TP) emit(k, min(k + TP, p1), w0 + j, w0 + j);
+          cur = j + 1;
+          continue;
+        }
+        open = true;
+        t_a = w0 + j; t_p = p0; t_last = w0 + j; t_end = p1;
+        cur = j + 1;
+        continue;
+      }
+      // extend the open tile over lanes cur..hi
+      const bool ok = in && lane >= cur && o1 - t_p <= TP && c - t_a <= TP - 1;
+      const unsigned okm = __ballot_sync(kFull, ok);
+      const int hi = okm ? 31 - __clz(okm) : cur - 1;  // contiguous from cur
+      const unsigned ne = nonempty & okm;
+      if (ne) {
+        const int j = 31 - __clz(ne);
+        t_last = w0 + j;
+        t_end = __shfl_sync(kFull, o1, j);
+      }
+      if (hi == 31 && !last_window) {  // the tile may continue in the next window
+        cur = 32;
+        break;
+      }
+      emit(t_p, t_end, t_a, t_last);
+      open = false;
+      cur = hi + 1;
+    }
+  }
+  if (open) emit(t_p, t_end, t_a, t_last);
+  if (pending) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(ntiles, pending);
+    base = __shfl_sync(kFull, base, 0);
+    if (lane < pending) tiles[base + lane] = mine;
+  }
 }
 
 // ================================================================== staged particle data
@@ -810,16 +816,10 @@ static void set_occ(const void* fn, size_t smem) {
 }
 
 template <int D>
-void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, const int* cell_off,
-                  const uint32_t* keys, uint32_t* counts, uint32_t* counts_copy, uint32_t* sums, Tile* tiles,
+void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, const int* cell_off, Tile* tiles,
                   int* ntiles, cudaStream_t st) {
-  const int nb = (n_lines + 255) / 256;
-  k_tile_count<D><<<nb, 256, 0, st>>>(segs, S, line_base, n_lines, cell_off, counts);
-  cudaMemcpyAsync(counts_copy, counts, sizeof(uint32_t) * n_lines, cudaMemcpyDeviceToDevice, st);
-  const int sb = (n_lines + 2047) / 2048;
-  launch_exclusive_scan(counts, n_lines, sums, st);
-  (void)sb;
-  k_tile_emit<D><<<nb, 256, 0, st>>>(segs, S, line_base, n_lines, cell_off, keys, counts, counts_copy, tiles, ntiles);
+  cudaMemsetAsync(ntiles, 0, sizeof(int), st);
+  if (n_lines > 0) k_tiles<D><<<(n_lines + 7) / 8, 256, 0, st>>>(segs, S, line_base, n_lines, cell_off, tiles, ntiles);
 }
 
 template <int D, int KERN>
@@ -888,8 +888,7 @@ cudaError_t configure_passes() {
 }
 
 #define SPH_INST_PD(D)                                                                                       \
-  template void launch_tiles<D>(const DevSeg*, int, const int*, int, const int*, const uint32_t*, uint32_t*,   \
-                                uint32_t*, uint32_t*, Tile*, int*, cudaStream_t);                             \
+  template void launch_tiles<D>(const DevSeg*, int, const int*, int, const int*, Tile*, int*, cudaStream_t);    \
   template void launch_pairs_t<D>(const TravArgs&, const Tile*, const int*, int, int32_t*, int32_t*,          \
                                   unsigned long long*, long long, cudaStream_t);
 SPH_INST_PD(2)

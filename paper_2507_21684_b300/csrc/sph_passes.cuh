@@ -7,8 +7,7 @@ namespace sph {
 
 cudaError_t configure_passes();
 template <int D>
-void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, const int* cell_off,
-                  const uint32_t* keys, uint32_t* counts, uint32_t* counts_copy, uint32_t* sums, Tile* tiles,
+void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, const int* cell_off, Tile* tiles,
                   int* ntiles, cudaStream_t st);
 template <int D, int KERN>
 void launch_walls_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st);

@@ -314,7 +314,7 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
     tiles_upper = 3 * ((N + TP - 1) / TP) + (C_tot + TP - 1) / TP + 2 * n_lines + 1;
   }
   bits = key_bits(C_tot);
-  passes = (bits + 7) / 8;
+  passes = std::max(1, (bits + 7) / 8);
   if (N > 16384 * 2048) einval("too many particles for the radix sort scratch (max 33554432)");
 }
 
@@ -333,11 +333,9 @@ void Scene::alloc_all() {
   keys_sorted = kA;
   perm = vA;
   cell_off = (int*)mem.get(sizeof(int) * ((size_t)C_tot + 1));
-  scratch = (uint32_t*)mem.get(4 * (size_t)std::max(sort_scratch_words(N), n_lines + 2048 + 64));
+  scratch = (uint32_t*)mem.get(4 * (size_t)sort_scratch_words(N));
   line_base = (int*)mem.get(sizeof(int) * S);
   CK(cudaMemcpyAsync(line_base, line_base_h.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
-  tile_counts = (uint32_t*)mem.get(sizeof(uint32_t) * (size_t)n_lines);
-  tile_counts_copy = (uint32_t*)mem.get(sizeof(uint32_t) * (size_t)n_lines);
   tiles = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
   d_ntiles = (int*)mem.get(sizeof(int) * 2);
   d_tile_ctr = (int*)mem.get(sizeof(int) * 4);
@@ -441,22 +439,20 @@ void Scene::prof_end() {
     CK(cudaEventRecord(prof_events.back().b, st));
 }
 
-// Rebuild: keys of the current order -> stable sort -> cell offsets -> permute `in` into
-// `out`.  Returns the sorted keys and the permutation (in kA/kB, vA/vB unless copied to the
-// given tape buffers); cell offsets go to off_out.
+// Rebuild: stable sort of the current order by cell key (the first pass computes the keys) ->
+// permute `in` into `out` and write the cell offsets to off_out -> tile table.  Returns the
+// sorted keys and the permutation (in kA/kB, vA/vB unless copied to the given tape buffers).
 std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& out, uint32_t* keys_out,
                                                uint32_t* perm_out, int* off_out) {
   prof_begin(1);
-  if (D == 2)
-    launch_keys<2>(dseg, N, in, kA, vA, st);
-  else
-    launch_keys<3>(dseg, N, in, kA, vA, st);
-  CKL();
   uint32_t *ki = kA, *vi = vA, *ko = kB, *vo = vB;
   uint32_t* hist = scratch;
   uint32_t* sums = scratch + (sort_scratch_words(N) - 2048 - 64);
   for (int p = 0; p < passes; ++p) {
-    launch_sort_pass(ki, vi, ko, vo, N, 8 * p, hist, sums, st);
+    if (D == 2)
+      launch_sort_pass<2>(ki, vi, ko, vo, N, 8 * p, hist, sums, p == 0 ? dseg : nullptr, in, st);
+    else
+      launch_sort_pass<3>(ki, vi, ko, vo, N, 8 * p, hist, sums, p == 0 ? dseg : nullptr, in, st);
     CKL();
     std::swap(ki, ko);
     std::swap(vi, vo);
@@ -471,26 +467,26 @@ std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& o
     CK(cudaMemcpyAsync(perm_out, pm, 4 * (size_t)N, cudaMemcpyDeviceToDevice, st));
     pm = perm_out;
   }
-  launch_cell_offsets(ks, N, C_tot, off_out, st);
-  CKL();
-  build_tiles(off_out, ks);
   if (D == 2)
-    launch_permute<2>(dseg, N, pm, in, out, st);
+    launch_permute<2>(dseg, N, pm, in, out, ks, C_tot, off_out, st);
   else
-    launch_permute<3>(dseg, N, pm, in, out, st);
+    launch_permute<3>(dseg, N, pm, in, out, ks, C_tot, off_out, st);
   CKL();
+  build_tiles(off_out);
   prof_end();
+  const int scan_launches = 256 * ((N + 2047) / 2048) <= 16384 ? 1 : 3;
+  launches += passes * (2 + scan_launches) + 1;
   return {ks, pm};
 }
 
-// Tile table of a cell structure (CSR offsets `off`, sorted keys `keys`).
-void Scene::build_tiles(const int* off, const uint32_t* keys) {
-  uint32_t* sums = scratch + n_lines + 64;
+// Tile table of a cell structure (CSR offsets `off`).
+void Scene::build_tiles(const int* off) {
   if (D == 2)
-    launch_tiles<2>(dseg, S, line_base, n_lines, off, keys, tile_counts, tile_counts_copy, sums, tiles, d_ntiles, st);
+    launch_tiles<2>(dseg, S, line_base, n_lines, off, tiles, d_ntiles, st);
   else
-    launch_tiles<3>(dseg, S, line_base, n_lines, off, keys, tile_counts, tile_counts_copy, sums, tiles, d_ntiles, st);
+    launch_tiles<3>(dseg, S, line_base, n_lines, off, tiles, d_ntiles, st);
   CKL();
+  ++launches;
 }
 
 void Scene::passes_before_sweep(const TravArgs& t) {
@@ -505,6 +501,7 @@ void Scene::passes_before_sweep(const TravArgs& t) {
     }
     CKL();
     prof_end();
+    ++launches;
   }
   if (summation) {
     prof_begin(3);
@@ -517,6 +514,7 @@ void Scene::passes_before_sweep(const TravArgs& t) {
     }
     CKL();
     prof_end();
+    ++launches;
   }
 }
 
@@ -545,7 +543,6 @@ void Scene::step_once() {
     cur = 1 - cur;
     cells_valid = true;
     steps_since_build = 0;
-    launches += 3 + 4 * passes;
   }
   TravArgs t = trav(buf[cur], keys_sorted, cell_off);
   passes_before_sweep(t);
@@ -781,7 +778,7 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
       CKL();
       TravArgs t = trav(slot.a, slot.keys, slot.off);
       t.pair_count = nullptr;
-      build_tiles(slot.off, slot.keys);
+      build_tiles(slot.off);
       prof_begin(4);
       if (D == 2) {
         if (kern == 0)
@@ -803,8 +800,9 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
         launch_adj_unpermute(N, slot.perm, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
         CKL();
         q = 1 - q;
+        ++launches;
       }
-      launches += 3;
+      launches += 3;  // seed, adjoint sweep, segment sums
     }
   }
   // XB[q] is in the storage order of checkpoint 0; deliver in original order

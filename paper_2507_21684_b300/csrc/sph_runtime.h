@@ -104,7 +104,6 @@ struct Scene {
   std::vector<int> line_base_h;
   int* line_base = nullptr;
   int n_lines = 0, tiles_upper = 0;
-  uint32_t *tile_counts = nullptr, *tile_counts_copy = nullptr;
   Tile* tiles = nullptr;
   int* d_ntiles = nullptr;
   int* d_tile_ctr = nullptr;   // dynamic tile counter (zeroed before each tiled launch)
@@ -160,7 +159,7 @@ struct Scene {
   void prof_end();
   std::pair<uint32_t*, uint32_t*> rebuild(const Arrays& in, const Arrays& out, uint32_t* keys_out,
                                           uint32_t* perm_out, int* off_out);
-  void build_tiles(const int* off, const uint32_t* keys);
+  void build_tiles(const int* off);
   void passes_before_sweep(const TravArgs& t);
   void sweep(const TravArgs& t, const Arrays& out);
   bool rebuild_due() const;
