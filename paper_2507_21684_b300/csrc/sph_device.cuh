@@ -46,6 +46,7 @@ struct DevSeg {
   float nu, pad1;
   float cs[3];             // cell edge (FP32) of the folded frame
   float trimR2;            // squared reach used to skip neighbour cells (H + skin/2 + margins)
+  float invcs[3];          // FP32 reciprocal cell edge (fast path of the cell key)
 };
 
 // ---------------------------------------------------------------- Wendland kernels

@@ -11,22 +11,47 @@ namespace sph {
 // ================================================================== neighbour search
 // Cell key of every particle in the current storage order (P2: floor-modulo wrap on
 // periodic axes, clamp on open axes; all in FP64 from the float32 unwrapped position).
+// Cell key of particle i, decided in FP64 from x = hi + lo exactly as floor(((x wrapped) - lo) /
+// cell edge), clamped to the grid.  Fast path: an FP32 estimate from hi alone decides the floor
+// whenever it lies farther than a margin from an integer; the margin, 2^-18 (|x| + |lo|) /
+// cell edge + 2^-18, exceeds the estimate's error (five FP32 roundings, and |lo part| <= 2^-24
+// |hi|) by more than ten times, so the FP64 decision is only taken near a cell face (and for
+// NaN or huge coordinates).  Both paths give the same key.
 template <int D>
 __device__ __forceinline__ uint32_t cell_key_of(const DevSeg* __restrict__ segs, const Arrays& a, int i) {
   const DevSeg& s = segs[a.meta[i].y];
   Cold c = load_cold<D>(a, i);
   int cc3[3] = {0, 0, 0};
+  bool fast = true;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    double x = __dadd_rn((double)c.hi[k], (double)c.lo[k]);
-    double xw = x;
-    if ((s.periodic_mask >> k) & 1) {
-      double f = floor(__ddiv_rn(__dsub_rn(x, s.lo_d[k]), s.L_d[k]));
-      xw = __dsub_rn(x, __dmul_rn(s.L_d[k], f));
+    const float d = c.hi[k] - s.lo[k];
+    const float mag = fabsf(c.hi[k]) + fabsf(s.lo[k]);
+    if ((s.periodic_mask >> k) & 1) {  // inside the primary box: no wrap
+      const float w = d * s.invL[k];
+      const float mw = 0x1p-18f * fmaf(mag, s.invL[k], 1.f);
+      fast = fast && w >= mw && w <= 1.f - mw;
     }
-    double cc = floor(__ddiv_rn(__dsub_rn(xw, s.lo_d[k]), s.cs_d[k]));
-    cc = fmin(fmax(cc, 0.0), (double)(s.n[k] - 1));
-    cc3[k] = (int)cc;
+    const float t = d * s.invcs[k];
+    const float f = floorf(t);
+    const float fr = t - f;
+    const float mt = 0x1p-18f * fmaf(mag, s.invcs[k], 1.f);
+    fast = fast && fr >= mt && fr <= 1.f - mt && fabsf(t) < 0x1p30f;
+    cc3[k] = fast ? min(max((int)f, 0), s.n[k] - 1) : 0;
+  }
+  if (!fast) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      double x = __dadd_rn((double)c.hi[k], (double)c.lo[k]);
+      double xw = x;
+      if ((s.periodic_mask >> k) & 1) {
+        double f = floor(__ddiv_rn(__dsub_rn(x, s.lo_d[k]), s.L_d[k]));
+        xw = __dsub_rn(x, __dmul_rn(s.L_d[k], f));
+      }
+      double cc = floor(__ddiv_rn(__dsub_rn(xw, s.lo_d[k]), s.cs_d[k]));
+      cc = fmin(fmax(cc, 0.0), (double)(s.n[k] - 1));
+      cc3[k] = (int)cc;
+    }
   }
   return (uint32_t)(s.cell_base + (cc3[2] * s.n[1] + cc3[1]) * s.n[0] + cc3[0]);
 }
@@ -252,7 +277,7 @@ __global__ void k_upload(const DevSeg* __restrict__ segs, int seg, int n, int nf
     r.v[q] = wall ? 0.f : v[(size_t)k * D + q];
   }
   r.rho = rho[k];
-  r.m = wall ? -mass[k] : mass[k];
+  r.m = wall ? -fabsf(mass[k]) : mass[k];
   r.p = tait_p(s, r.rho);
   r.V = mass[k] / r.rho;
   int j = p0 + k;

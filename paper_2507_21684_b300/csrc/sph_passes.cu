@@ -63,11 +63,9 @@ __global__ void __launch_bounds__(256) k_tiles(const DevSeg* __restrict__ segs, 
   // open tile: first cell, first particle, last non-empty cell and its end offset
   bool open = false;
   int t_a = 0, t_p = 0, t_last = 0, t_end = 0;
-  for (int w0 = 0; w0 < nx; w0 += 32) {
+  auto window = [&](int w0, int o0, int o1) {
     const int c = w0 + lane;
     const bool in = c < nx;
-    const int o0 = in ? cell_off[first + c] : 0;
-    const int o1 = in ? cell_off[first + c + 1] : 0;
     const unsigned nonempty = __ballot_sync(kFull, in && o1 > o0);
     const bool last_window = w0 + 32 >= nx;
     int cur = 0;  // first lane not yet consumed
@@ -97,14 +95,28 @@ __global__ void __launch_bounds__(256) k_tiles(const DevSeg* __restrict__ segs, 
         t_last = w0 + j;
         t_end = __shfl_sync(kFull, o1, j);
       }
-      if (hi == 31 && !last_window) {  // the tile may continue in the next window
-        cur = 32;
-        break;
-      }
+      if (hi == 31 && !last_window) break;  // the tile may continue in the next window
       emit(t_p, t_end, t_a, t_last);
       open = false;
       cur = hi + 1;
     }
+  };
+  // the offsets of the first kPre windows are loaded up front (one round trip for lines of up
+  // to 32 kPre cells); longer lines load the rest window by window
+  constexpr int kPre = 6;
+  int o0s[kPre], o1s[kPre];
+#pragma unroll
+  for (int w = 0; w < kPre; ++w) {
+    const int c = 32 * w + lane;
+    o0s[w] = c < nx ? cell_off[first + c] : 0;
+    o1s[w] = c < nx ? cell_off[first + c + 1] : 0;
+  }
+#pragma unroll
+  for (int w = 0; w < kPre; ++w)
+    if (32 * w < nx) window(32 * w, o0s[w], o1s[w]);
+  for (int w0 = 32 * kPre; w0 < nx; w0 += 32) {
+    const int c = w0 + lane;
+    window(w0, c < nx ? cell_off[first + c] : 0, c < nx ? cell_off[first + c + 1] : 0);
   }
   if (open) emit(t_p, t_end, t_a, t_last);
   if (pending) {
@@ -333,9 +345,19 @@ __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restr
   for (int ti = s_tile; ti < nt; ti = s_tile) {
     const Tile T = tiles[ti];
     const DevSeg& s = t.segs[T.seg];
-    const bool staged = stage_tile<D, E>(sm, s, T, t.a, t.cell_off, extra0, extra1);
     const int i = T.p0 + tgt;
     const bool valid = i < T.p1;
+    // tiles without a target of this pass (walls only, fluid only) are skipped unstaged
+    const bool want = valid && lane == 0 && Pass::wants(t.a.meta[i].x);
+    const int stg = stage_tile<D, E>(sm, s, T, t.a, t.cell_off, extra0, extra1, want);
+    if (stg < 0) {
+      if (valid && lane == 0) pass.skip(i);
+      __syncthreads();
+      if (threadIdx.x == 0) s_tile = atomicAdd(t.tile_ctr, 1);
+      __syncthreads();
+      continue;
+    }
+    const bool staged = stg > 0;
     typename Pass::Body body;
     bool active = false;
     int ccol = 0;
@@ -402,6 +424,9 @@ struct WallPass {
     }
   };
   Arrays a;
+  // superset of the targets init() activates, from the meta word alone
+  __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) != 0; }
+  __device__ __forceinline__ void skip(int) {}
   __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
     b.s = &s;
     b.sW = b.sp = b.sh = 0.f;
@@ -439,6 +464,8 @@ struct DensityPass {
     __device__ __forceinline__ void reduce() { rho = group_sum<L>(rho); }
   };
   Arrays a;
+  __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) == 0; }
+  __device__ __forceinline__ void skip(int) {}
   __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
     b.s = &s;
     b.rho = 0.0;
@@ -501,6 +528,14 @@ struct SweepPass {
   Arrays a, out;
   RateOut ro;
   int* status;
+  // fluid targets only (walls carry m <= 0); a skipped wall keeps its state
+  __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) == 0; }
+  __device__ __forceinline__ void skip(int i) {
+    if (!INTEGRATE) return;
+    store_pd<D>(out, i, load_pd<D>(a, i));
+    store_cold<D>(out, i, load_cold<D>(a, i));
+    out.meta[i] = a.meta[i];
+  }
   __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
     b.s = &s;
     const PD<D> me = load_pd<D>(a, i);
@@ -584,6 +619,8 @@ struct PairPass {
   int32_t *pi, *pj;
   unsigned long long* count;
   long long cap;
+  __device__ static __forceinline__ bool wants(uint32_t) { return true; }
+  __device__ __forceinline__ void skip(int) {}
   __device__ __forceinline__ bool init(Body& b, const DevSeg&, int i) {
     b.id_i = a.meta[i].x & ~kWallBit;
     b.meta = a.meta;
@@ -687,6 +724,8 @@ struct AdjPass {
   const float* Pp;
   float4 *XBout, *VBout;
   float* nu_part;  // per particle viscosity partials (summed deterministically afterwards)
+  __device__ static __forceinline__ bool wants(uint32_t) { return true; }
+  __device__ __forceinline__ void skip(int) {}
   __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
     b.s = &s;
     const PD<D> me = load_pd<D>(a, i);

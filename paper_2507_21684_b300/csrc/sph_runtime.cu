@@ -181,7 +181,10 @@ DevSeg make_seg(const sph_params& p, int n_fluid, int cell_base, int p0, int p1,
   for (int k = 0; k < p.dim; ++k) Lmax = std::max(Lmax, std::fabs(p.box_lo[k]) + s.L_d[k]);
   double reach = (H * (1.0 + 2.0 * band) + 0.5 * (double)p.skin) * (1.0 + 1e-5) + 16.0 * std::ldexp(Lmax, -23);
   s.trimR2 = (float)(reach * reach);
-  for (int k = 0; k < 3; ++k) s.cs[k] = (float)s.cs_d[k];
+  for (int k = 0; k < 3; ++k) {
+    s.cs[k] = (float)s.cs_d[k];
+    s.invcs[k] = (float)(1.0 / s.cs_d[k]);
+  }
   return s;
 }
 

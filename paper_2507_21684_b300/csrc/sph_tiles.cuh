@@ -66,12 +66,14 @@ template <int D, int EXTRA>
 constexpr size_t tile_smem_bytes() { return sizeof(TileSmem<D, EXTRA>); }
 
 // Build the run table of a tile and stage its particles (two dependent global round trips:
-// the cell offsets, then the particle records).  Returns false (fallback) when the staged
-// region exceeds the shared-memory capacity or the column table.  All threads of the CTA call it.
+// the cell offsets, then the particle records).  Returns 1 when staged, 0 (fallback) when the
+// staged region exceeds the shared-memory capacity or the column table, -1 when no thread
+// passed want (no target of the pass in this tile: nothing is staged; the decision rides on
+// the first barrier, so it costs no extra round trip).  All threads of the CTA call it.
 template <int D, int EXTRA>
-__device__ bool stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T, const Arrays& a,
-                           const int* __restrict__ cell_off, const float4* __restrict__ extra0,
-                           const float* __restrict__ extra1) {
+__device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T, const Arrays& a,
+                          const int* __restrict__ cell_off, const float4* __restrict__ extra0,
+                          const float* __restrict__ extra1, bool want) {
   constexpr int NL = TileCfg<D>::NL;
   constexpr int NCOL = TileSmem<D, EXTRA>::NCOL;
   constexpr int NRUN = TileSmem<D, EXTRA>::NRUN;
@@ -82,8 +84,7 @@ __device__ bool stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& 
   const int ncols = T.cx1 - T.cx0 + 3;  // columns colbase .. colbase + ncols - 1
   if (ncols > NCOL - 1) {               // a sparse line: more cells than the table holds
     if (tid == 0) sm.fallback = 1;
-    __syncthreads();
-    return false;
+    return __syncthreads_or(want) ? 0 : -1;
   }
   const bool px = s.periodic_mask & 1, py = (s.periodic_mask >> 1) & 1, pz = (s.periodic_mask >> 2) & 1;
   // in-box column range of the tile and its periodic image cells
@@ -122,7 +123,7 @@ __device__ bool stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& 
   // in-box column boundaries of every line: colstart is filled relative to the run start
   // after the scan; here the raw offsets are kept in colstart.
   const int nb = NL * (ncols + 1);
-  __syncthreads();
+  if (!__syncthreads_or(want)) return -1;
   for (int e = tid; e < nb; e += blockDim.x) {
     const int l = e / (ncols + 1), c = e - l * (ncols + 1);
     const int lc = sm.linecell[l];
@@ -153,7 +154,7 @@ __device__ bool stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& 
     }
   }
   __syncthreads();
-  if (sm.fallback) return false;
+  if (sm.fallback) return 0;
   const int total = sm.total;
   // 3) column starts as staged indices: image columns map to their own runs
   for (int e = tid; e < nb; e += blockDim.x) {
@@ -185,7 +186,7 @@ __device__ bool stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& 
     if (EXTRA > 1) sm.E[CAP + k] = make_float4(__ldg(extra1 + j), 0.f, 0.f, 0.f);
   }
   __syncthreads();
-  return true;
+  return 1;
 }
 
 // Global index of staged particle k (for predicates that exclude the target by index).
