@@ -125,6 +125,7 @@ def lib() -> C.CDLL:
     L.sph_server_stats.argtypes = [vp, P(ServerInfo)]
     L.sph_server_destroy.argtypes = [vp]
     L.sph_server_destroy.restype = None
+    L.sph_cells_noalloc.argtypes = [P(Params), vp, C.c_int32, vp, C.c_int64, vp, P(C.c_int32), vp]
     _lib = L
     return L
 
@@ -414,6 +415,28 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+NOALLOC_MAX_PARTICLES = 524288
+
+
+def cells_noalloc(params: dict, x, cell_start, sorted_ids, stream=None) -> int:
+    """Cell binning without allocation (sph_cells_noalloc): x is a CUDA float32 tensor (n, dim)
+    in original order; cell_start (n_cells + 1) and sorted_ids (n) are caller-owned CUDA int32
+    tensors that receive the CSR cell offsets and the stably sorted original indices.  Work is
+    enqueued on `stream` (a torch.cuda.Stream; None = the legacy default stream).  Returns
+    n_cells.  Passing cell_start=None only reports n_cells (SPH_EINVAL is swallowed)."""
+    n = int(x.shape[0]) if x is not None else 0
+    nc = C.c_int32(0)
+    st = None if stream is None else C.c_void_p(stream.cuda_stream)
+    pp = Params.from_dict(params)
+    if cell_start is None:
+        lib().sph_cells_noalloc(C.byref(pp), None, 0, None, 0, None, C.byref(nc), st)
+        return nc.value
+    _check(lib().sph_cells_noalloc(C.byref(pp), x.data_ptr() if n else None, n, cell_start.data_ptr(),
+                                   int(cell_start.numel()), sorted_ids.data_ptr() if n else None,
+                                   C.byref(nc), st))
+    return nc.value
 
 
 def scene_from(spec: dict, stream=None, device: bool = False) -> Scene:
