@@ -35,6 +35,36 @@ FLOPS_PER_PAIR = {2: 42, 3: 50}
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 
+# Kernel sources whose change invalidates a stored ncu traffic figure.
+KERNEL_SOURCES = ("sph_device.cuh", "sph_tiles.cuh", "sph_passes.cuh", "sph_passes.cu", "sph_kernels.cuh",
+                  "sph_kernels.cu")
+
+
+def kernel_fingerprint() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2507_21684_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(profile: str):
+    """DRAM bytes per launch from a committed ncu summary, or None when the kernel sources have
+    changed since that capture (the summary records their fingerprint)."""
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", profile)) as fh:
+            txt = fh.read()
+    except OSError:
+        return None
+    fp = re.search(r"fingerprint[^`]*`([0-9a-f]+)`", txt)
+    tb = re.search(r"DRAM bytes per launch \(read \+ write\): (\d+)", txt)
+    if not fp or not tb or fp.group(1) != kernel_fingerprint():
+        return None
+    return int(tb.group(1))
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -394,7 +424,9 @@ def main():
             "clocks": clocks,
             "roofline": {"bound": "alu", "kernel": "k_sweep (fused rates + kick-drift)",
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved / FP32_PEAK_TFLOPS,
+                         "traffic": stored_traffic("k_sweep_t_dambreak_128.md"),
+                         "traffic_source": "profiles/k_sweep_t_dambreak_128.md (ncu, cold caches, one launch)",
                          "flops_per_pair": FLOPS_PER_PAIR[2], "pairs_per_launch": fw["pairs_per_step"],
                          "sweep_ms_avg": fw["sweep_ms"], "sweep_launches": fw["sweep_n"],
                          "peak_source": "148 SM x 128 FP32 lanes x 2 x 2.032 GHz (unit counts and max clock)"},
