@@ -73,8 +73,11 @@ extern "C" {
  * Box: [box_lo, box_hi) per axis; periodic axes (bit k of periodic_mask) use the minimum
  * image on absolute, unwrapped positions (Sec. 3.2); open axes clamp particles into the edge
  * cells.  Cells have edge >= H + skin; a periodic axis needs at least 3 cells.
- * Neighbour lists are rebuilt every step when skin == 0; with skin > 0 they are rebuilt every
- * rebuild_interval steps (a Verlet list in the sense of App. B). */
+ * The cell structure is rebuilt every step when skin == 0.  With skin > 0 (a Verlet list in the
+ * sense of App. B) a captured step rebuilds only when rebuild_interval sweeps have used the
+ * current cells or when some particle has moved farther than skin/2 since the last build (the
+ * sweep measures the displacement; the decision is a conditional node of the step's CUDA graph,
+ * taken on the device).  Steps run without graphs, and the adjoint's replay, rebuild every step. */
 typedef struct sph_params {
   int32_t dim;            /* 2 or 3 */
   int32_t kernel;         /* SPH_KERNEL_* */
@@ -176,8 +179,13 @@ SPH_API int sph_profile(sph_scene* scene, int enable);
 SPH_API int sph_timing(sph_scene* scene, int kernel_class, double* ms, int64_t* launches);
 
 /* Counters of the last sph_step/sph_rollout/sph_adjoint call: in-radius ordered pairs per step
- * (fluid i), kernel launches issued. */
+ * (fluid i), kernel launches executed (conditional rebuilds included).  Synchronises. */
 SPH_API int sph_counters(sph_scene* scene, int64_t* pairs_per_step, int64_t* launches);
+
+/* Cumulative counters since sph_init: forward steps, cell-structure rebuilds (host-launched and
+ * those decided on the device under a Verlet skin), kernel launches executed.  Synchronises.
+ * Any output may be NULL. */
+SPH_API int sph_stats(sph_scene* scene, int64_t* steps, int64_t* rebuilds, int64_t* launches);
 
 SPH_API void sph_destroy(sph_scene* scene);
 

@@ -116,6 +116,7 @@ def lib() -> C.CDLL:
     L.sph_profile.argtypes = [vp, C.c_int]
     L.sph_timing.argtypes = [vp, C.c_int, P(C.c_double), P(C.c_int64)]
     L.sph_counters.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
+    L.sph_stats.argtypes = [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64)]
     L.sph_destroy.argtypes = [vp]
     L.sph_destroy.restype = None
     L.sph_server_create.argtypes = [C.c_size_t, C.c_int, P(vp)]
@@ -347,6 +348,12 @@ class Scene:
         launches = C.c_int64()
         _check(lib().sph_counters(self._h, C.byref(pairs), C.byref(launches)))
         return pairs.value, launches.value
+
+    def stats(self) -> dict:
+        """Cumulative steps, cell rebuilds and kernel launches since the scene was created."""
+        st, rb, ln = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().sph_stats(self._h, C.byref(st), C.byref(rb), C.byref(ln)))
+        return {"steps": st.value, "rebuilds": rb.value, "launches": ln.value}
 
 
 class Server:

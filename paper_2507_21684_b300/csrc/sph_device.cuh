@@ -284,4 +284,14 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+// True when the FP32 estimate (hi - lo) / L of periodic axis q lies farther than a safety
+// margin inside (0, 1), so that the FP64 fold floor((x - lo) / L) of x = hi + lo is 0 (the
+// particle is in the primary box).  The margin 2^-18 (|hi| + |lo|) / L + 2^-18 exceeds the
+// estimate's error (a few FP32 roundings and |lo part| <= 2^-24 |hi|) more than ten times.
+__device__ __forceinline__ bool in_primary_box(const DevSeg& s, int q, float hi) {
+  const float w = (hi - s.lo[q]) * s.invL[q];
+  const float m = 0x1p-18f * fmaf(fabsf(hi) + fabsf(s.lo[q]), s.invL[q], 1.f);
+  return w >= m && w <= 1.f - m;
+}
+
 }  // namespace sph

@@ -27,11 +27,7 @@ __device__ __forceinline__ uint32_t cell_key_of(const DevSeg* __restrict__ segs,
   for (int k = 0; k < D; ++k) {
     const float d = c.hi[k] - s.lo[k];
     const float mag = fabsf(c.hi[k]) + fabsf(s.lo[k]);
-    if ((s.periodic_mask >> k) & 1) {  // inside the primary box: no wrap
-      const float w = d * s.invL[k];
-      const float mw = 0x1p-18f * fmaf(mag, s.invL[k], 1.f);
-      fast = fast && w >= mw && w <= 1.f - mw;
-    }
+    if ((s.periodic_mask >> k) & 1) fast = fast && in_primary_box(s, k, c.hi[k]);  // no wrap
     const float t = d * s.invcs[k];
     const float f = floorf(t);
     const float fr = t - f;
@@ -217,10 +213,14 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 
 
 // Gather the state into sorted order and re-fold positions into the primary box; thread k also
-// writes the CSR offsets of the cells in (key[k-1], key[k]] (off[c] = first index with key >= c).
+// writes the CSR offsets of the cells in (key[k-1], key[k]] (off[c] = first index with key >= c)
+// and, when xb is set, the folded position (the reference of the displacement check).
+// The fold floor((x - lo) / L) is decided in FP64; in_primary_box() settles the common case
+// (0) without the FP64 division and gives the same result.
 template <int D>
 __global__ void k_permute(const DevSeg* __restrict__ segs, int N, const uint32_t* __restrict__ perm, Arrays in,
-                          Arrays out, const uint32_t* __restrict__ keys, int C, int* __restrict__ off) {
+                          Arrays out, const uint32_t* __restrict__ keys, int C, int* __restrict__ off,
+                          float* __restrict__ xb) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k > N) return;
   {
@@ -239,16 +239,19 @@ __global__ void k_permute(const DevSeg* __restrict__ segs, int N, const uint32_t
   for (int q = 0; q < D; ++q) {
     double x = __dadd_rn((double)c.hi[q], (double)c.lo[q]);
     double f = 0.0;
-    if ((s.periodic_mask >> q) & 1) f = floor(__ddiv_rn(__dsub_rn(x, s.lo_d[q]), s.L_d[q]));
+    if (((s.periodic_mask >> q) & 1) && !in_primary_box(s, q, c.hi[q]))
+      f = floor(__ddiv_rn(__dsub_rn(x, s.lo_d[q]), s.L_d[q]));
     double o = __dmul_rn(s.L_d[q], f);
     c.off[q] = (float)o;
     xh[q] = (float)__dsub_rn(x, o);
   }
   if (D == 2) {
     out.A[k] = make_float4(xh[0], xh[1], a.z, a.w);
+    if (xb) reinterpret_cast<float2*>(xb)[k] = make_float2(xh[0], xh[1]);
   } else {
     out.A[k] = make_float4(xh[0], xh[1], xh[2], a.w);
     out.C[k] = in.C[src];
+    if (xb) reinterpret_cast<float4*>(xb)[k] = make_float4(xh[0], xh[1], xh[2], 0.f);
   }
   store_cold<D>(out, k, c);
   out.B[k] = b;
@@ -450,8 +453,43 @@ int sort_scratch_words(int N) {
 
 template <int D>
 void launch_permute(const DevSeg* segs, int N, const uint32_t* perm, const Arrays& in, const Arrays& out,
-                    const uint32_t* keys, int C, int* off, cudaStream_t st) {
-  k_permute<D><<<(N + 1 + 255) / 256, 256, 0, st>>>(segs, N, perm, in, out, keys, C, off);
+                    const uint32_t* keys, int C, int* off, float* xb, cudaStream_t st) {
+  k_permute<D><<<(N + 1 + 255) / 256, 256, 0, st>>>(segs, N, perm, in, out, keys, C, off, xb);
+}
+
+// Whole-state copy (every array of the records) in one launch.
+template <int D>
+__global__ void k_copy_state(int N, Arrays src, Arrays dst) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  dst.A[k] = src.A[k];
+  dst.B[k] = src.B[k];
+  dst.X[k] = src.X[k];
+  dst.O[k] = src.O[k];
+  dst.meta[k] = src.meta[k];
+  if (D == 3) {
+    dst.C[k] = src.C[k];
+    dst.XL[k] = src.XL[k];
+  }
+}
+template <int D>
+void launch_copy_state(int N, const Arrays& src, const Arrays& dst, cudaStream_t st) {
+  if (N > 0) k_copy_state<D><<<(N + 255) / 256, 256, 0, st>>>(N, src, dst);
+}
+
+// Rebuild decision of one step, taken on the device: rebuild when the cells have served
+// `interval` sweeps or when some particle has moved farther than half the skin since the last
+// build (maxr > 1, from the previous sweep).  Sets the graph's conditional and the counters.
+__global__ void k_rebuild_decide(RebuildCtl* ctl, int interval, cudaGraphConditionalHandle h) {
+  const unsigned r = (ctl->since >= interval || __uint_as_float(ctl->maxr) > 1.f) ? 1u : 0u;
+  cudaGraphSetConditional(h, r);
+  ctl->since = r ? 1 : ctl->since + 1;
+  ctl->maxr = 0u;
+  ctl->rebuilds += r;
+  ctl->call_rebuilds += r;
+}
+void launch_rebuild_decide(RebuildCtl* ctl, int interval, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_rebuild_decide<<<1, 1, 0, st>>>(ctl, interval, h);
 }
 template <int D>
 void launch_upload(const DevSeg* segs, int seg, int n, int nf, int p0, const float* x, const float* v, const float* rho,
@@ -495,7 +533,8 @@ void launch_download_range(const Arrays& a, int p0, int n, float* x, float* v, f
   template void launch_copy_range<D>(const Arrays&, int, const Arrays&, int, int, int, cudaStream_t);          \
   template void launch_download_range<D>(const Arrays&, int, int, float*, float*, float*, cudaStream_t);       \
   template void launch_permute<D>(const DevSeg*, int, const uint32_t*, const Arrays&, const Arrays&, const uint32_t*, \
-                                  int, int*, cudaStream_t);                                                     \
+                                  int, int*, float*, cudaStream_t);                                             \
+  template void launch_copy_state<D>(int, const Arrays&, const Arrays&, cudaStream_t);                        \
   template void launch_sort_pass<D>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int, int, uint32_t*,   \
                                     uint32_t*, const DevSeg*, const Arrays&, cudaStream_t);                     \
   template void launch_upload<D>(const DevSeg*, int, int, int, int, const float*, const float*, const float*,   \

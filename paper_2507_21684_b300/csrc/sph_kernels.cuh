@@ -16,6 +16,21 @@ struct TravArgs {
   int* tile_ctr;             // dynamic tile counter of the launch (zeroed before it)
 };
 
+// Device-side rebuild policy state of a scene (Verlet skin).
+struct RebuildCtl {
+  int since;             // sweeps served by the current cell structure
+  unsigned maxr;         // max over fluid of |x - x_build|^2 / (skin/2 - margin)^2 (float bits)
+  long long rebuilds;    // conditional rebuilds taken (cumulative)
+  long long call_rebuilds;  // conditional rebuilds since the host last zeroed it (one API call)
+};
+
+// Displacement check written by the sweep's epilogue (all null: no check).
+struct Displace {
+  const float* xb;       // folded positions at the last build (float2 in 2D, float4 in 3D)
+  unsigned* maxr;        // running maximum (float bits, non-negative)
+  float inv_r2;          // 1 / (skin/2 - margin)^2
+};
+
 // Outputs of the rate evaluation (original order, fluid only).
 struct RateOut {
   float* a;
@@ -31,7 +46,10 @@ void launch_sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, 
                       uint32_t* hist, uint32_t* sums, const DevSeg* segs, const Arrays& a, cudaStream_t st);
 template <int D>
 void launch_permute(const DevSeg* segs, int N, const uint32_t* perm, const Arrays& in, const Arrays& out,
-                    const uint32_t* keys, int C, int* off, cudaStream_t st);
+                    const uint32_t* keys, int C, int* off, float* xb, cudaStream_t st);
+template <int D>
+void launch_copy_state(int N, const Arrays& src, const Arrays& dst, cudaStream_t st);
+void launch_rebuild_decide(RebuildCtl* ctl, int interval, cudaGraphConditionalHandle h, cudaStream_t st);
 template <int D>
 void launch_upload(const DevSeg* segs, int seg, int n, int nf, int p0, const float* x, const float* v,
                    const float* rho, const float* mass, const Arrays& a, cudaStream_t st);

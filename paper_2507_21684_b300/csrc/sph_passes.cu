@@ -389,6 +389,7 @@ __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restr
     if (threadIdx.x == 0) s_tile = atomicAdd(t.tile_ctr, 1);
     __syncthreads();
   }
+  pass.flush();
   if (t.pair_count) {
     long long v = pairs_cta;
 #pragma unroll
@@ -427,6 +428,7 @@ struct WallPass {
   // superset of the targets init() activates, from the meta word alone
   __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) != 0; }
   __device__ __forceinline__ void skip(int) {}
+  __device__ __forceinline__ void flush() {}
   __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
     b.s = &s;
     b.sW = b.sp = b.sh = 0.f;
@@ -466,6 +468,7 @@ struct DensityPass {
   Arrays a;
   __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) == 0; }
   __device__ __forceinline__ void skip(int) {}
+  __device__ __forceinline__ void flush() {}
   __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
     b.s = &s;
     b.rho = 0.0;
@@ -528,6 +531,14 @@ struct SweepPass {
   Arrays a, out;
   RateOut ro;
   int* status;
+  Displace disp;
+  float dmax = 0.f;  // largest scaled displacement of this thread's targets
+  // the CTA's warps fold their maxima into the scene's running maximum
+  __device__ __forceinline__ void flush() {
+    if (!INTEGRATE || !disp.maxr) return;
+    const unsigned v = __reduce_max_sync(kFull, __float_as_uint(dmax));
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(disp.maxr, v);
+  }
   // fluid targets only (walls carry m <= 0); a skipped wall keeps its state
   __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) == 0; }
   __device__ __forceinline__ void skip(int i) {
@@ -585,6 +596,19 @@ struct SweepPass {
         me.p = s.B * expm1f(s.gamma * log1pf(e));
         me.V = me.m / me.rho;
       }
+      if (disp.xb) {  // displacement since the last build, in units of (skin/2 - margin)
+        float d2 = 0.f;
+        if (D == 2) {
+          const float2 b = reinterpret_cast<const float2*>(disp.xb)[i];
+          const float e0 = me.x[0] - b.x, e1 = me.x[1] - b.y;
+          d2 = fmaf(e0, e0, e1 * e1);
+        } else {
+          const float4 b = reinterpret_cast<const float4*>(disp.xb)[i];
+          const float e0 = me.x[0] - b.x, e1 = me.x[1] - b.y, e2 = me.x[D - 1] - b.z;
+          d2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+        }
+        dmax = fmaxf(dmax, d2 * disp.inv_r2);
+      }
       bool bad = !(me.rho > 0.5f * s.rho0 && me.rho < 2.f * s.rho0);
 #pragma unroll
       for (int k = 0; k < D; ++k) bad |= !isfinite(c.hi[k]) || !isfinite(me.v[k]);
@@ -621,6 +645,7 @@ struct PairPass {
   long long cap;
   __device__ static __forceinline__ bool wants(uint32_t) { return true; }
   __device__ __forceinline__ void skip(int) {}
+  __device__ __forceinline__ void flush() {}
   __device__ __forceinline__ bool init(Body& b, const DevSeg&, int i) {
     b.id_i = a.meta[i].x & ~kWallBit;
     b.meta = a.meta;
@@ -726,6 +751,7 @@ struct AdjPass {
   float* nu_part;  // per particle viscosity partials (summed deterministically afterwards)
   __device__ static __forceinline__ bool wants(uint32_t) { return true; }
   __device__ __forceinline__ void skip(int) {}
+  __device__ __forceinline__ void flush() {}
   __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
     b.s = &s;
     const PD<D> me = load_pd<D>(a, i);
@@ -778,12 +804,13 @@ __global__ void __launch_bounds__(256, 4) k_density_t(TravArgs t, const Tile* ti
 }
 template <int D, int KERN, bool INTEGRATE>
 __global__ void __launch_bounds__(256, 4) k_sweep_t(TravArgs t, const Tile* tiles, const int* ntiles, Arrays out,
-                                                 RateOut ro) {
+                                                 RateOut ro, Displace disp) {
   SweepPass<D, KERN, INTEGRATE> pass;
   pass.a = t.a;
   pass.out = out;
   pass.ro = ro;
   pass.status = t.status;
+  pass.disp = disp;
   run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
 template <int D>
@@ -873,15 +900,15 @@ void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, i
 }
 template <int D, int KERN>
 void launch_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
-                    cudaStream_t st) {
+                    const Displace& disp, cudaStream_t st) {
   cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
-  k_sweep_t<D, KERN, true><<<pass_grid((const void*)k_sweep_t<D, KERN, true>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, out, RateOut{});
+  k_sweep_t<D, KERN, true><<<pass_grid((const void*)k_sweep_t<D, KERN, true>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, out, RateOut{}, disp);
 }
 template <int D, int KERN>
 void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const RateOut& ro,
                     cudaStream_t st) {
   cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
-  k_sweep_t<D, KERN, false><<<pass_grid((const void*)k_sweep_t<D, KERN, false>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, Arrays{}, ro);
+  k_sweep_t<D, KERN, false><<<pass_grid((const void*)k_sweep_t<D, KERN, false>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, Arrays{}, ro, Displace{});
 }
 template <int D>
 void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
@@ -935,7 +962,8 @@ SPH_INST_PD(3)
 #define SPH_INST_PDK(D, K)                                                                                   \
   template void launch_walls_t<D, K>(const TravArgs&, const Tile*, const int*, int, cudaStream_t);          \
   template void launch_density_t<D, K>(const TravArgs&, const Tile*, const int*, int, cudaStream_t);        \
-  template void launch_sweep_t<D, K>(const TravArgs&, const Tile*, const int*, int, const Arrays&, cudaStream_t); \
+  template void launch_sweep_t<D, K>(const TravArgs&, const Tile*, const int*, int, const Arrays&, const Displace&, \
+                                     cudaStream_t);                                                          \
   template void launch_rates_t<D, K>(const TravArgs&, const Tile*, const int*, int, const RateOut&, cudaStream_t); \
   template void launch_adj_t<D, K>(const TravArgs&, const Tile*, const int*, int, const float4*, const float*,  \
                                    const float4*, const float4*, float4*, float4*, float*, cudaStream_t);

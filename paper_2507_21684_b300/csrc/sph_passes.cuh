@@ -15,7 +15,7 @@ template <int D, int KERN>
 void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st);
 template <int D, int KERN>
 void launch_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
-                    cudaStream_t st);
+                    const Displace& disp, cudaStream_t st);
 template <int D, int KERN>
 void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const RateOut& ro,
                     cudaStream_t st);

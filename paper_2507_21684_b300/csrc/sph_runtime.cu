@@ -237,6 +237,7 @@ Scene::~Scene() {
     cudaEventDestroy(ev_out);
     cudaStreamDestroy(st);
   }
+  if (st_body) cudaStreamDestroy(st_body);
 }
 
 void Scene::alloc_arrays(Arrays& a) {
@@ -318,6 +319,18 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
   }
   bits = key_bits(C_tot);
   passes = std::max(1, (bits + 7) / 8);
+  // Verlet skin: rebuild only when a particle has moved farther than skin/2 since the last
+  // build (cells of edge >= H + skin then still hold every neighbour) or after `interval`
+  // sweeps.  The threshold keeps 8 FP32 ulps of the largest coordinate in hand.
+  {
+    double Lmax = 1.0;
+    for (int s = 0; s < S; ++s)
+      for (int k = 0; k < D; ++k)
+        Lmax = std::max(Lmax, std::max(std::fabs(segs[s].lo_d[k]), std::fabs(segs[s].lo_d[k] + segs[s].L_d[k])));
+    const double half = 0.5 * (double)skin - 8.0 * std::ldexp(Lmax, -23);
+    dev_policy = skin > 0.f && half > 0.0;
+    inv_r2 = dev_policy ? (float)(1.0 / (half * half)) : 0.f;
+  }
   if (N > 16384 * 2048) einval("too many particles for the radix sort scratch (max 33554432)");
 }
 
@@ -344,6 +357,9 @@ void Scene::alloc_all() {
   d_tile_ctr = (int*)mem.get(sizeof(int) * 4);
   d_status = (int*)mem.get(sizeof(int) * 4);
   d_pairs = (unsigned long long*)mem.get(sizeof(unsigned long long) * 2);
+  d_ctl = (RebuildCtl*)mem.get(sizeof(RebuildCtl));
+  CK(cudaMemsetAsync(d_ctl, 0, sizeof(RebuildCtl), st));
+  xbuild = (float*)mem.get((D == 2 ? 8 : 16) * (size_t)N);
   d_nubar = (double*)mem.get(sizeof(double) * (size_t)(S + 1));
   CK(cudaMemsetAsync(d_status, 0, sizeof(int) * 4, st));
   CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long) * 2, st));
@@ -421,7 +437,7 @@ cudaEvent_t Scene::take_event() {
 // capture the records become event-record nodes of the graph; every replay re-points them
 // at fresh events (cudaGraphExecEventRecordNodeSetEvent), so each launch is timed.
 void Scene::prof_begin(int cls) {
-  if (!profiling) return;
+  if (!profiling || in_body) return;
   ProfEvent e;
   e.cls = cls;
   e.a = take_event();
@@ -435,7 +451,7 @@ void Scene::prof_begin(int cls) {
   }
 }
 void Scene::prof_end() {
-  if (!profiling) return;
+  if (!profiling || in_body) return;
   if (capturing)
     CK(cudaEventRecordWithFlags(capture_events.back().b, st, cudaEventRecordExternal));
   else
@@ -471,9 +487,9 @@ std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& o
     pm = perm_out;
   }
   if (D == 2)
-    launch_permute<2>(dseg, N, pm, in, out, ks, C_tot, off_out, st);
+    launch_permute<2>(dseg, N, pm, in, out, ks, C_tot, off_out, xbuild, st);
   else
-    launch_permute<3>(dseg, N, pm, in, out, ks, C_tot, off_out, st);
+    launch_permute<3>(dseg, N, pm, in, out, ks, C_tot, off_out, xbuild, st);
   CKL();
   build_tiles(off_out);
   prof_end();
@@ -523,30 +539,40 @@ void Scene::passes_before_sweep(const TravArgs& t) {
 
 void Scene::sweep(const TravArgs& t, const Arrays& out) {
   prof_begin(0);
+  const Displace dp = dev_policy ? Displace{xbuild, &d_ctl->maxr, inv_r2} : Displace{nullptr, nullptr, 0.f};
   if (D == 2) {
-    if (kern == 0) launch_sweep_t<2, 0>(t, tiles, d_ntiles, tiles_upper, out, st);
-    else launch_sweep_t<2, 1>(t, tiles, d_ntiles, tiles_upper, out, st);
+    if (kern == 0) launch_sweep_t<2, 0>(t, tiles, d_ntiles, tiles_upper, out, dp, st);
+    else launch_sweep_t<2, 1>(t, tiles, d_ntiles, tiles_upper, out, dp, st);
   } else {
-    if (kern == 0) launch_sweep_t<3, 0>(t, tiles, d_ntiles, tiles_upper, out, st);
-    else launch_sweep_t<3, 1>(t, tiles, d_ntiles, tiles_upper, out, st);
+    if (kern == 0) launch_sweep_t<3, 0>(t, tiles, d_ntiles, tiles_upper, out, dp, st);
+    else launch_sweep_t<3, 1>(t, tiles, d_ntiles, tiles_upper, out, dp, st);
   }
   CKL();
   prof_end();
   ++launches;
 }
 
-bool Scene::rebuild_due() const { return skin == 0.f || !cells_valid || steps_since_build >= interval; }
+// Rebuild launched by the host (eager steps, cells needed by a query): permute into the other
+// buffer; the device-side policy counters restart from this build.
+void Scene::host_rebuild() {
+  auto kp = rebuild(buf[cur], buf[1 - cur], nullptr, nullptr, cell_off);
+  keys_sorted = kp.first;
+  perm = kp.second;
+  cur = 1 - cur;
+  cells_valid = true;
+  steps_since_build = 0;
+  if (!capturing) ++host_rebuilds;  // captured rebuilds are counted per graph launch
+  if (dev_policy) CK(cudaMemsetAsync(d_ctl, 0, 2 * sizeof(int), st));  // since = 0, maxr = 0
+}
 
-// One forward step on the scene's own buffers.
+// One forward step on the scene's own buffers.  Eager steps rebuild every time (the host does
+// not see the displacements); captured steps of a scene with a Verlet skin decide on the device.
 void Scene::step_once() {
-  if (rebuild_due()) {
-    auto kp = rebuild(buf[cur], buf[1 - cur], nullptr, nullptr, cell_off);
-    keys_sorted = kp.first;
-    perm = kp.second;
-    cur = 1 - cur;
-    cells_valid = true;
-    steps_since_build = 0;
+  if (dev_policy && capturing && cells_valid) {
+    step_conditional();
+    return;
   }
+  host_rebuild();
   TravArgs t = trav(buf[cur], keys_sorted, cell_off);
   passes_before_sweep(t);
   sweep(t, buf[1 - cur]);
@@ -554,15 +580,75 @@ void Scene::step_once() {
   ++steps_since_build;
 }
 
-// Host-side replay of the schedule of step_once without launching (graph bookkeeping).
-void Scene::advance_schedule() {
-  if (rebuild_due()) {
-    cur = 1 - cur;
-    cells_valid = true;
-    steps_since_build = 0;
+// A captured step whose rebuild is a conditional graph node: a one-thread kernel decides
+// (interval reached, or the previous sweep saw a displacement beyond skin/2), the node's body
+// sorts and permutes into the other buffer and copies the result back, so the buffer parity of
+// the step does not depend on the decision.
+void Scene::step_conditional() {
+  prof_begin(1);
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+  launch_rebuild_decide(d_ctl, interval, h, st);
+  CKL();
+  ++launches;
+  CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeIf;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, ed, nd, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  if (!st_body) CK(cudaStreamCreateWithFlags(&st_body, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCaptureToGraph(st_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  const long long l0 = launches;
+  std::swap(st, st_body);
+  in_body = true;
+  try {
+    rebuild(buf[cur], buf[1 - cur], nullptr, nullptr, cell_off);
+    if (D == 2)
+      launch_copy_state<2>(N, buf[1 - cur], buf[cur], st);
+    else
+      launch_copy_state<3>(N, buf[1 - cur], buf[cur], st);
+    CKL();
+    ++launches;
+  } catch (...) {
+    in_body = false;
+    std::swap(st, st_body);
+    cudaGraph_t dummy;
+    cudaStreamEndCapture(st_body, &dummy);
+    throw;
   }
+  in_body = false;
+  std::swap(st, st_body);
+  body_launches = launches - l0;
+  launches = l0;
+  cudaGraph_t dummy;
+  CK(cudaStreamEndCapture(st_body, &dummy));
+  CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  prof_end();
+  keys_sorted = (passes % 2 == 0) ? kA : kB;
+  perm = (passes % 2 == 0) ? vA : vB;
+  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  passes_before_sweep(t);
+  sweep(t, buf[1 - cur]);
   cur = 1 - cur;
-  ++steps_since_build;
+}
+
+// Host-side replay of the buffer schedule of one captured step (graph bookkeeping).
+void Scene::advance_schedule() {
+  if (!dev_policy) cur = 1 - cur;  // the rebuild's permute
+  cur = 1 - cur;                   // the sweep
+  cells_valid = true;
+  keys_sorted = (passes % 2 == 0) ? kA : kB;
+  perm = (passes % 2 == 0) ? vA : vB;
 }
 
 void Scene::steps(int n) {
@@ -570,15 +656,20 @@ void Scene::steps(int n) {
   CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st));
   launches = 0;
   const int chunk = std::min(graph_chunk, n);
+  steps_total += n;
+  if (dev_policy) CK(cudaMemsetAsync(&d_ctl->call_rebuilds, 0, sizeof(long long), st));
   if (!use_graphs) {
     for (int k = 0; k < n; ++k) step_once();
     last_steps = n;
+    launches_total += launches;
     return;
   }
   int done = 0;
   long long per_chunk = 0;
-  while (n - done >= chunk) {
-    GraphKey key{chunk, cur, cells_valid ? std::min(steps_since_build, interval) : -1, profiling ? 1 : 0};
+  if (dev_policy && !cells_valid) host_rebuild();
+  while (done < n) {
+    const int c = std::min(chunk, n - done);  // the last graph takes the remainder
+    GraphKey key{c, cur, dev_policy ? 1 : 0, profiling ? 1 : 0};
     auto it = graphs.find(key);
     // capture records the launches of `chunk` steps without running them; the host-side
     // schedule (buffer parity, rebuild counter, sorted-key pointers) advances exactly as in
@@ -589,7 +680,7 @@ void Scene::steps(int n) {
       capturing = true;
       CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       try {
-        for (int k = 0; k < chunk; ++k) step_once();
+        for (int k = 0; k < c; ++k) step_once();
       } catch (...) {
         cudaStreamEndCapture(st, &g);
         capturing = false;
@@ -633,15 +724,10 @@ void Scene::steps(int n) {
       per_chunk = launches - l0;
       graph_launch_count[key] = per_chunk;
     } else {
-      for (int k = 0; k < chunk; ++k) {
-        if (rebuild_due()) {
-          keys_sorted = (passes % 2 == 0) ? kA : kB;
-          perm = (passes % 2 == 0) ? vA : vB;
-        }
-        advance_schedule();
-      }
+      for (int k = 0; k < c; ++k) advance_schedule();
       launches += graph_launch_count[key];
     }
+    if (!dev_policy) host_rebuilds += c;  // every captured step rebuilds
     for (auto& gn : graph_prof[key]) {
       ProfEvent e;
       e.cls = gn.cls;
@@ -652,20 +738,15 @@ void Scene::steps(int n) {
       prof_events.push_back(e);
     }
     CK(cudaGraphLaunch(it->second, st));
-    done += chunk;
+    done += c;
   }
-  for (; done < n; ++done) step_once();
   last_steps = n;
+  launches_total += launches;
 }
 
 void Scene::ensure_cells() {
   if (cells_valid) return;
-  auto kp = rebuild(buf[cur], buf[1 - cur], nullptr, nullptr, cell_off);
-  keys_sorted = kp.first;
-  perm = kp.second;
-  cur = 1 - cur;
-  cells_valid = true;
-  steps_since_build = 0;
+  host_rebuild();
 }
 
 // ---------------------------------------------------------------- adjoint tape
@@ -691,6 +772,8 @@ void Scene::rollout(int n, int k) {
     step_once();
   }
   last_steps = n;
+  steps_total += n;
+  launches_total += launches;
   tape_valid = true;
 }
 
@@ -745,31 +828,16 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
   for (int sgi = ncp - 1; sgi >= 0; --sgi) {
     const int t0 = sgi * k, t1 = std::min(n, t0 + k);
     const int L = t1 - t0;
-    // replay the segment forward, keeping the sweep input of every step
-    std::vector<char> rebuilt(L, 0);
-    bool valid = false;
-    int since = 0;
+    // replay the segment forward, keeping the sweep input of every step; every replayed step
+    // rebuilds (the forward's displacement checks are not replayed)
     const Arrays* prev = &ckpts[sgi];
     for (int s = 0; s < L; ++s) {
-      bool due = skin == 0.f || !valid || since >= interval;
       TapeSlot& slot = tape[s];
-      if (due) {
-        rebuild(*prev, slot.a, slot.keys, slot.perm, slot.off);  // keys/perm copied into the slot
-        valid = true;
-        since = 0;
-        rebuilt[s] = 1;
-      } else {
-        // no rebuild: the previous sweep wrote straight into this slot
-        CK(cudaMemcpyAsync(slot.keys, tape[s - 1].keys, 4 * (size_t)N, cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(slot.off, tape[s - 1].off, sizeof(int) * ((size_t)C_tot + 1), cudaMemcpyDeviceToDevice, st));
-      }
+      rebuild(*prev, slot.a, slot.keys, slot.perm, slot.off);  // keys/perm copied into the slot
       TravArgs t = trav(slot.a, slot.keys, slot.off);
       passes_before_sweep(t);
-      bool next_due = (s + 1 < L) && (skin == 0.f || since + 1 >= interval);
-      const Arrays& dst = (s + 1 < L && !next_due) ? tape[s + 1].a : scratch_arr;
-      sweep(t, dst);
+      sweep(t, scratch_arr);
       prev = &scratch_arr;
-      ++since;
     }
     // backward through the segment
     for (int s = L - 1; s >= 0; --s) {
@@ -799,13 +867,10 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
       launch_sum_segments(nu_part, dseg, S, d_nubar, st);
       CKL();
       q = 1 - q;
-      if (rebuilt[s]) {
-        launch_adj_unpermute(N, slot.perm, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
-        CKL();
-        q = 1 - q;
-        ++launches;
-      }
-      launches += 3;  // seed, adjoint sweep, segment sums
+      launch_adj_unpermute(N, slot.perm, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
+      CKL();
+      q = 1 - q;
+      launches += 4;  // seed, adjoint sweep, segment sums, un-permute
     }
   }
   // XB[q] is in the storage order of checkpoint 0; deliver in original order
@@ -826,6 +891,7 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
   CKL();
   // the replay reused the sort buffers: the live state must rebuild before its next step
   cells_valid = false;
+  launches_total += launches;
   if (!is_dev) {
     if (xb0) CK(cudaMemcpyAsync(xb0, oxb, 4 * nd, cudaMemcpyDeviceToHost, st));
     if (vb0) CK(cudaMemcpyAsync(vb0, ovb, 4 * nd, cudaMemcpyDeviceToHost, st));
@@ -906,7 +972,20 @@ void Scene::rates(float* a, float* drho, float* rho, int is_dev) {
   CK(cudaStreamSynchronize(st));
 }
 
+// Launch and rebuild counters since the scene was created (device rebuilds read back).
+void Scene::stats(int64_t* steps, int64_t* rebuilds, int64_t* n_launches) {
+  RebuildCtl c{};
+  if (d_ctl) {
+    CK(cudaMemcpyAsync(&c, d_ctl, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  if (steps) *steps = steps_total;
+  if (rebuilds) *rebuilds = host_rebuilds + c.rebuilds;
+  if (n_launches) *n_launches = launches_total + c.rebuilds * body_launches;
+}
+
 void Scene::debug_cells(int64_t* start, int32_t* ids) {
+  if (skin > 0.f) cells_valid = false;  // report the cells of the current positions
   ensure_cells();
   std::vector<int> off((size_t)C_tot + 1);
   std::vector<uint2> meta(N);
@@ -921,6 +1000,7 @@ void Scene::debug_cells(int64_t* start, int32_t* ids) {
 
 void Scene::debug_pairs(int64_t* n_pairs, int32_t* pi, int32_t* pj, int64_t cap) {
   if (S > 1) einval("sph_debug_pairs supports single scenes");
+  if (skin > 0.f) cells_valid = false;
   ensure_cells();
   // widen the FP32 guard band of the exact predicate to the actual coordinate range
   {
@@ -1172,6 +1252,17 @@ int sph_scene_info(const sph_scene* sc, int32_t* ncell3, int32_t* n) {
   return SPH_OK;
 }
 
+int sph_stats(sph_scene* sc, int64_t* steps, int64_t* rebuilds, int64_t* launches) {
+  if (!sc) {
+    sph::set_err("sph_stats: NULL scene");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  sc->s.enter();
+  sc->s.stats(steps, rebuilds, launches);
+  API_END
+}
+
 int sph_debug_cells(sph_scene* sc, int64_t* cell_start, int32_t* sorted_ids) {
   if (!sc) {
     sph::set_err("sph_debug_cells: NULL scene");
@@ -1214,7 +1305,12 @@ int sph_counters(sph_scene* sc, int64_t* pairs_per_step, int64_t* launches) {
   CK(cudaMemcpyAsync(&h, sc->s.d_pairs, sizeof(h), cudaMemcpyDeviceToHost, sc->s.st));
   CK(cudaStreamSynchronize(sc->s.st));
   if (pairs_per_step) *pairs_per_step = sc->s.last_steps > 0 ? (int64_t)(h / (unsigned long long)sc->s.last_steps) : 0;
-  if (launches) *launches = sc->s.launches;
+  long long cr = 0;
+  if (sc->s.dev_policy) {
+    CK(cudaMemcpyAsync(&cr, &sc->s.d_ctl->call_rebuilds, sizeof(cr), cudaMemcpyDeviceToHost, sc->s.st));
+    CK(cudaStreamSynchronize(sc->s.st));
+  }
+  if (launches) *launches = sc->s.launches + cr * sc->s.body_launches;
   API_END
 }
 

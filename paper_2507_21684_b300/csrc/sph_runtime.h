@@ -114,6 +114,16 @@ struct Scene {
   size_t tmp_bytes = 0;
   bool cells_valid = false;
   int steps_since_build = 0;
+  // Verlet skin: the rebuild is decided on the device inside the step graph (conditional node)
+  bool dev_policy = false;          // skin large enough for the displacement check
+  float inv_r2 = 0.f;               // 1 / (skin/2 - margin)^2
+  RebuildCtl* d_ctl = nullptr;
+  float* xbuild = nullptr;          // folded positions at the last build
+  cudaStream_t st_body = nullptr;   // captures the rebuild body of a conditional node
+  bool in_body = false;
+  long long body_launches = 0;      // kernels in one conditional rebuild body
+  // cumulative counters (since the scene was created)
+  long long launches_total = 0, steps_total = 0, host_rebuilds = 0;
   // execution
   bool use_graphs = true;
   int graph_chunk = 8;
@@ -162,8 +172,9 @@ struct Scene {
   void build_tiles(const int* off);
   void passes_before_sweep(const TravArgs& t);
   void sweep(const TravArgs& t, const Arrays& out);
-  bool rebuild_due() const;
+  void host_rebuild();
   void step_once();
+  void step_conditional();
   void advance_schedule();
   void steps(int n);
   void ensure_cells();
@@ -177,6 +188,7 @@ struct Scene {
   void debug_cells(int64_t* start, int32_t* ids);
   void debug_pairs(int64_t* n_pairs, int32_t* pi, int32_t* pj, int64_t cap);
   void timing(int cls, double* ms, int64_t* count);
+  void stats(int64_t* steps, int64_t* rebuilds, int64_t* launches);
 };
 
 }  // namespace sph

@@ -190,6 +190,52 @@ def test_dam_break_hundred_steps(sph, orc):
     assert rel(rho - 1.0, ro - 1.0) < 1e-3
 
 
+def _verlet(s, skin_over_H, interval=1 << 20):
+    p = dict(s["params"])
+    p["skin"] = float(np.float32(skin_over_H * p["H"]))
+    p["rebuild_interval"] = int(interval)
+    return dict(s, params=p)
+
+
+@pytest.mark.parametrize("case,skin,n", [("tgv2d_64", 0.1, 40), ("dambreak_128", 0.02, 300)])
+def test_verlet_skin_rebuilds_on_displacement(sph, orc, case, skin, n):
+    """Skin and no interval limit: the device-side displacement check alone decides when the cells
+    are rebuilt (fewer rebuilds than steps, more than the initial one), and the rollout still
+    matches the oracle, which searches neighbours every step."""
+    base = si.taylor_green_2d(64, seed=0) if case == "tgv2d_64" else si.dam_break(res=128)
+    s = _verlet(base, skin)
+    with make(sph, s) as sc:
+        sc.step(n)
+        st = sc.stats()
+        x, v, rho = sc.get_state()
+    assert st["steps"] == n
+    assert 1 < st["rebuilds"] < n, st
+    xo, vo, ro = orc.rollout(s, n)
+    x0 = s["x"].astype(np.float64)
+    assert rel(x - x0, xo - x0) < 1e-3
+    assert rel(v, vo) < 1e-3
+    r0 = s["params"]["rho0"]
+    assert rel(rho - r0, ro - r0) < 1e-3
+
+
+def test_verlet_interval_counts_rebuilds_and_launches(sph):
+    """Skin wide enough that displacement never triggers: cells serve exactly `interval` sweeps
+    (the initial host build, then a conditional rebuild every 3rd step), and the launch counter
+    includes the kernels of the rebuilds taken inside the graphs."""
+    s = _verlet(si.taylor_green_2d(32, seed=1), 0.5, interval=3)
+    with make(sph, s) as sc:
+        sc.step(30)
+        st = sc.stats()
+        _, launches = sc.counters()
+        sc.step(30)
+        st2 = sc.stats()
+        _, launches2 = sc.counters()
+    assert st["rebuilds"] == 10, st
+    assert st2["rebuilds"] - st["rebuilds"] == 10, st2  # steps 31..60: rebuilds at 31, 34, ..., 58
+    assert launches2 >= 2 * 30  # at least the decision and the sweep of every step
+    assert st2["launches"] - st["launches"] == launches2
+
+
 def test_graph_replay_is_bitwise_eager(sph):
     s = si.taylor_green_2d(48, seed=3)
     with make(sph, s) as a, make(sph, s) as b:
