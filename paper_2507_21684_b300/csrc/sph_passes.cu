@@ -339,55 +339,60 @@ __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restr
   const int lane = threadIdx.x % Cfg::LANES;
   long long pairs_cta = 0;
   // tiles are handed out dynamically (one atomic per CTA and tile): load balance whatever the
-  // occupancy and the tile sizes
+  // occupancy and the tile sizes (a CTA asks for its next tile only when it is free)
   if (threadIdx.x == 0) s_tile = atomicAdd(t.tile_ctr, 1);
   __syncthreads();
-  for (int ti = s_tile; ti < nt; ti = s_tile) {
+  int ti = s_tile;
+  while (ti < nt) {
     const Tile T = tiles[ti];
     const DevSeg& s = t.segs[T.seg];
     const int i = T.p0 + tgt;
     const bool valid = i < T.p1;
-    // tiles without a target of this pass (walls only, fluid only) are skipped unstaged
-    const bool want = valid && lane == 0 && Pass::wants(t.a.meta[i].x);
-    const int stg = stage_tile<D, E>(sm, s, T, t.a, t.cell_off, extra0, extra1, want);
-    if (stg < 0) {
-      if (valid && lane == 0) pass.skip(i);
-      __syncthreads();
-      if (threadIdx.x == 0) s_tile = atomicAdd(t.tile_ctr, 1);
-      __syncthreads();
-      continue;
-    }
-    const bool staged = stg > 0;
+    // the target's own data and key are requested before staging, so their loads overlap it
     typename Pass::Body body;
     bool active = false;
-    int ccol = 0;
-    float xi[3] = {0.f, 0.f, 0.f}, flo[3] = {0.f, 0.f, 0.f}, fhi[3] = {0.f, 0.f, 0.f};
+    int key = 0;
+    float xi[3] = {0.f, 0.f, 0.f};
     if (valid) {
       active = pass.init(body, s, i);
       const float4 A = __ldg(t.a.A + i);
       xi[0] = A.x; xi[1] = A.y; xi[2] = A.z;
-      int c[3] = {(int)t.keys[i] - (s.cell_base + (T.cz * s.n[1] + T.cy) * s.n[0]), T.cy, T.cz};
-      ccol = c[0] - (staged ? sm.colbase : 0);
+      key = (int)t.keys[i];
+    }
+    // tiles without a target of this pass (walls only, fluid only) are skipped unstaged
+    const bool want = valid && lane == 0 && Pass::wants(t.a.meta[i].x);
+    const int stg = stage_tile<D, E>(sm, s, T, t.a, t.cell_off, extra0, extra1, want);
+    if (stg >= 0) {
+      const bool staged = stg > 0;
+      int ccol = 0;
+      float flo[3] = {0.f, 0.f, 0.f}, fhi[3] = {0.f, 0.f, 0.f};
+      if (valid) {
+        const int c[3] = {key - (s.cell_base + (T.cz * s.n[1] + T.cy) * s.n[0]), T.cy, T.cz};
+        ccol = c[0] - (staged ? sm.colbase : 0);
 #pragma unroll
-      for (int q = 0; q < D; ++q) {
-        flo[q] = s.lo[q] + s.cs[q] * (float)c[q];
-        fhi[q] = flo[q] + s.cs[q];
+        for (int q = 0; q < D; ++q) {
+          flo[q] = s.lo[q] + s.cs[q] * (float)c[q];
+          fhi[q] = flo[q] + s.cs[q];
+        }
       }
+      int np = 0;
+      if (active) {
+        if (staged)
+          np = gather_staged<D, E, SELF>(sm, s, t.a, i, ccol, xi, flo, fhi, body);
+        else if (lane == 0)
+          np = gather_global<D, SELF>(s, t.a, t.keys, t.cell_off, extra0, extra1, i, xi, body);
+      }
+      __syncwarp();
+      body.template reduce<Cfg::LANES>();
+      if (valid && lane == 0) pass.finish(body, s, i);
+      pairs_cta += np;
+    } else if (valid && lane == 0) {
+      pass.skip(i);
     }
-    int np = 0;
-    if (active) {
-      if (staged)
-        np = gather_staged<D, E, SELF>(sm, s, t.a, i, ccol, xi, flo, fhi, body);
-      else if (lane == 0)
-        np = gather_global<D, SELF>(s, t.a, t.keys, t.cell_off, extra0, extra1, i, xi, body);
-    }
-    __syncwarp();
-    body.template reduce<Cfg::LANES>();
-    if (valid && lane == 0) pass.finish(body, s, i);
-    pairs_cta += np;
     __syncthreads();  // shared memory is restaged for the next tile
     if (threadIdx.x == 0) s_tile = atomicAdd(t.tile_ctr, 1);
     __syncthreads();
+    ti = s_tile;
   }
   pass.flush();
   if (t.pair_count) {

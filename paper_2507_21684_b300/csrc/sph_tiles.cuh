@@ -60,16 +60,48 @@ struct TileSmem {
   float cshift[NL][3];              // candidate shift of each line (lower periodic image: -L)
   int ncols, colbase, total, fallback;
   int linecell[NL];                 // global cell id of column 0 of each line (-1: no line)
+  int img[NL][4];                   // offsets bounding the left and right periodic image cells
 };
 
 template <int D, int EXTRA>
 constexpr size_t tile_smem_bytes() { return sizeof(TileSmem<D, EXTRA>); }
 
-// Build the run table of a tile and stage its particles (two dependent global round trips:
-// the cell offsets, then the particle records).  Returns 1 when staged, 0 (fallback) when the
-// staged region exceeds the shared-memory capacity or the column table, -1 when no thread
-// passed want (no target of the pass in this tile: nothing is staged; the decision rides on
-// the first barrier, so it costs no extra round trip).  All threads of the CTA call it.
+// Geometry of staged line l of a tile: global cell id of its column 0 (-1 when the line lies
+// outside a closed box), the target shift (upper periodic image: +L) and the candidate shift
+// (lower periodic image: -L) on the y and z axes.  Pure arithmetic.
+template <int D>
+__device__ __forceinline__ int tile_line(const DevSeg& s, const Tile& T, int l, float* tsh, float* csh) {
+  const int dy = (D == 2) ? l - 1 : l % 3 - 1;
+  const int dz = (D == 2) ? 0 : l / 3 - 1;
+  const int nx = s.n[0], ny = s.n[1], nz = s.n[2];
+  int ly = T.cy + dy, lz = T.cz + dz;
+  tsh[0] = tsh[1] = csh[0] = csh[1] = 0.f;
+  if (ly < 0) { if ((s.periodic_mask >> 1) & 1) { ly += ny; csh[0] = -s.L[1]; } else return -1; }
+  else if (ly >= ny) { if ((s.periodic_mask >> 1) & 1) { ly -= ny; tsh[0] = s.L[1]; } else return -1; }
+  if (D == 3) {
+    if (lz < 0) { if ((s.periodic_mask >> 2) & 1) { lz += nz; csh[1] = -s.L[2]; } else return -1; }
+    else if (lz >= nz) { if ((s.periodic_mask >> 2) & 1) { lz -= nz; tsh[1] = s.L[2]; } else return -1; }
+  }
+  return s.cell_base + (lz * ny + ly) * nx;
+}
+
+// Run containing staged index k: the largest r with run_s[r] <= k (run_s is non-decreasing and
+// k < total, so that run is not empty).
+template <int D, int EXTRA>
+__device__ __forceinline__ int staged_run(const TileSmem<D, EXTRA>& sm, int k) {
+  constexpr int NRUN = TileSmem<D, EXTRA>::NRUN;
+  int r = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1)
+    if (r + step < NRUN && sm.run_s[r + step] <= k) r += step;
+  return r;
+}
+
+// Build the run table of a tile and stage its particles: two dependent global round trips (every
+// cell offset the tile needs, then the particle records).  Returns 1 when staged, 0 (fallback)
+// when the staged region exceeds the shared-memory capacity or the column table, -1 when no
+// thread passed want (no target of the pass in this tile: nothing is staged; the decision rides
+// on the first barrier, so it costs no extra round trip).  All threads of the CTA call it.
 template <int D, int EXTRA>
 __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T, const Arrays& a,
                           const int* __restrict__ cell_off, const float4* __restrict__ extra0,
@@ -79,71 +111,64 @@ __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T
   constexpr int NRUN = TileSmem<D, EXTRA>::NRUN;
   constexpr int CAP = TileCfg<D>::CAP;
   const int tid = threadIdx.x;
-  const int nx = s.n[0], ny = s.n[1], nz = s.n[2];
+  const int nx = s.n[0];
   const int colbase = T.cx0 - 1;
   const int ncols = T.cx1 - T.cx0 + 3;  // columns colbase .. colbase + ncols - 1
   if (ncols > NCOL - 1) {               // a sparse line: more cells than the table holds
     if (tid == 0) sm.fallback = 1;
     return __syncthreads_or(want) ? 0 : -1;
   }
-  const bool px = s.periodic_mask & 1, py = (s.periodic_mask >> 1) & 1, pz = (s.periodic_mask >> 2) & 1;
+  const bool px = s.periodic_mask & 1;
   // in-box column range of the tile and its periodic image cells
   const int mc0 = max(colbase, 0), mc1 = min(colbase + ncols - 1, nx - 1);
   const bool left_img = px && colbase < 0;
   const bool right_img = px && colbase + ncols - 1 >= nx;
-  // 1) line geometry (threads 0..NL-1) and every needed cell offset (one round trip)
+  // 1) one round trip: the column boundaries of every staged line (clamped into the in-box
+  //    range, raw offsets) and the bounds of the two periodic image cells
   if (tid < NL) {
-    const int dy = (D == 2) ? tid - 1 : tid % 3 - 1;
-    const int dz = (D == 2) ? 0 : tid / 3 - 1;
-    int ly = T.cy + dy, lz = T.cz + dz;
-    float ty = 0.f, tz = 0.f, cyv = 0.f, czv = 0.f;
-    bool ok = true;
-    if (ly < 0) { if (py) { ly += ny; cyv = -s.L[1]; } else ok = false; }
-    else if (ly >= ny) { if (py) { ly -= ny; ty = s.L[1]; } else ok = false; }
-    if (D == 3) {
-      if (lz < 0) { if (pz) { lz += nz; czv = -s.L[2]; } else ok = false; }
-      else if (lz >= nz) { if (pz) { lz -= nz; tz = s.L[2]; } else ok = false; }
-    }
-    const int lc = ok ? s.cell_base + (lz * ny + ly) * nx : -1;
-    sm.linecell[tid] = lc;
-    sm.tshift[tid][0] = 0.f; sm.tshift[tid][1] = ty; sm.tshift[tid][2] = tz;
-    sm.cshift[tid][0] = 0.f; sm.cshift[tid][1] = cyv; sm.cshift[tid][2] = czv;
-    // runs: left image cell (nx-1), in-box columns [mc0, mc1], right image cell (0)
-    int g0 = 0, n0 = 0, g1 = 0, n1 = 0, g2 = 0, n2 = 0;
-    if (ok) {
-      if (left_img) { g0 = cell_off[lc + nx - 1]; n0 = cell_off[lc + nx] - g0; }
-      g1 = cell_off[lc + mc0];
-      n1 = cell_off[lc + mc1 + 1] - g1;
-      if (right_img) { g2 = cell_off[lc]; n2 = cell_off[lc + 1] - g2; }
-    }
-    sm.run_g[3 * tid + 0] = g0; sm.run_n[3 * tid + 0] = n0; sm.run_sx[3 * tid + 0] = -s.L[0];
-    sm.run_g[3 * tid + 1] = g1; sm.run_n[3 * tid + 1] = n1; sm.run_sx[3 * tid + 1] = 0.f;
-    sm.run_g[3 * tid + 2] = g2; sm.run_n[3 * tid + 2] = n2; sm.run_sx[3 * tid + 2] = 0.f;
+    float tsh[2], csh[2];
+    sm.linecell[tid] = tile_line<D>(s, T, tid, tsh, csh);
+    sm.tshift[tid][0] = 0.f; sm.tshift[tid][1] = tsh[0]; sm.tshift[tid][2] = tsh[1];
+    sm.cshift[tid][0] = 0.f; sm.cshift[tid][1] = csh[0]; sm.cshift[tid][2] = csh[1];
   }
-  // in-box column boundaries of every line: colstart is filled relative to the run start
-  // after the scan; here the raw offsets are kept in colstart.
   const int nb = NL * (ncols + 1);
-  if (!__syncthreads_or(want)) return -1;
-  for (int e = tid; e < nb; e += blockDim.x) {
-    const int l = e / (ncols + 1), c = e - l * (ncols + 1);
-    const int lc = sm.linecell[l];
-    int v = 0;
-    if (lc >= 0) {
-      const int col = min(max(colbase + c, mc0), mc1 + 1);  // clamp into the in-box range
-      v = cell_off[lc + col];
+  for (int e = tid; e < nb + 4 * NL; e += blockDim.x) {
+    float tsh[2], csh[2];
+    if (e < nb) {
+      const int l = e / (ncols + 1), c = e - l * (ncols + 1);
+      const int lc = tile_line<D>(s, T, l, tsh, csh);
+      const int col = min(max(colbase + c, mc0), mc1 + 1);
+      sm.colstart[l * NCOL + c] = lc >= 0 ? cell_off[lc + col] : 0;
+    } else {
+      const int l = (e - nb) >> 2, w = (e - nb) & 3;
+      const int lc = tile_line<D>(s, T, l, tsh, csh);
+      int v = 0;
+      if (lc >= 0 && (w < 2 ? left_img : right_img)) v = cell_off[lc + (w < 2 ? nx - 1 + w : w - 2)];
+      sm.img[l][w] = v;
     }
-    sm.colstart[l * NCOL + c] = v;
   }
-  // 2) exclusive scan of the run lengths (one warp, NRUN <= 27)
+  if (!__syncthreads_or(want)) return -1;
+  // 2) run table (left image, in-box columns, right image per line) and its exclusive scan
   if (tid < 32) {
-    const int v = tid < NRUN ? sm.run_n[tid] : 0;
-    int incl = v;
+    int g = 0, n = 0;
+    if (tid < NRUN) {
+      const int l = tid / 3, kind = tid - 3 * (tid / 3);
+      if (sm.linecell[l] >= 0) {
+        if (kind == 0) { g = sm.img[l][0]; n = sm.img[l][1] - g; }
+        else if (kind == 1) { g = sm.colstart[l * NCOL + (mc0 - colbase)]; n = sm.colstart[l * NCOL + (mc1 + 1 - colbase)] - g; }
+        else { g = sm.img[l][2]; n = sm.img[l][3] - g; }
+      }
+      sm.run_g[tid] = g;
+      sm.run_n[tid] = n;
+      sm.run_sx[tid] = kind == 0 ? -s.L[0] : 0.f;
+    }
+    int incl = n;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(kFull, incl, o);
       if (tid >= o) incl += t;
     }
-    if (tid < NRUN) sm.run_s[tid] = incl - v;
+    if (tid < NRUN) sm.run_s[tid] = incl - n;
     const int total = __shfl_sync(kFull, incl, 31);
     if (tid == 0) {
       sm.run_s[NRUN] = total;
@@ -156,7 +181,8 @@ __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T
   __syncthreads();
   if (sm.fallback) return 0;
   const int total = sm.total;
-  // 3) column starts as staged indices: image columns map to their own runs
+  // 3) column starts as staged indices (image columns map to their own runs), and the copy of
+  //    the records (second round trip)
   for (int e = tid; e < nb; e += blockDim.x) {
     const int l = e / (ncols + 1), c = e - l * (ncols + 1);
     const int col = colbase + c;
@@ -168,11 +194,8 @@ __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T
     if (sm.linecell[l] < 0) v = sm.run_s[3 * l + 0];
     sm.colstart[l * NCOL + c] = v;
   }
-  // 4) copy: every thread takes staged indices, finds its run (at most 3 NL runs)
   for (int k = tid; k < total; k += blockDim.x) {
-    int r = 0;
-#pragma unroll 1
-    while (r + 1 < NRUN && sm.run_s[r + 1] <= k) ++r;
+    const int r = staged_run(sm, k);
     const int j = sm.run_g[r] + (k - sm.run_s[r]);
     const int l = r / 3;
     float4 A = __ldg(a.A + j), B = __ldg(a.B + j);
@@ -192,8 +215,7 @@ __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T
 // Global index of staged particle k (for predicates that exclude the target by index).
 template <int D, int EXTRA>
 __device__ __forceinline__ int staged_gidx(const TileSmem<D, EXTRA>& sm, int k) {
-  int r = 0;
-  while (r + 1 < TileSmem<D, EXTRA>::NRUN && sm.run_s[r + 1] <= k) ++r;
+  const int r = staged_run(sm, k);
   return sm.run_g[r] + (k - sm.run_s[r]);
 }
 
