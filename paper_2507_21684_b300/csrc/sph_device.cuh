@@ -213,6 +213,23 @@ __device__ __forceinline__ PD<D> load_pd(const Arrays& a, int j) {
   return r;
 }
 
+// Same as load_pd through plain loads (for Arrays views of shared memory).
+template <int D>
+__device__ __forceinline__ PD<D> load_pd_plain(const Arrays& a, int j) {
+  PD<D> r;
+  const float4 A = a.A[j], B = a.B[j];
+  if (D == 2) {
+    r.x[0] = A.x; r.x[1] = A.y; r.v[0] = A.z; r.v[1] = A.w;
+    r.rho = B.x; r.p = B.y; r.V = B.z; r.m = B.w;
+  } else {
+    const float2 C = a.C[j];
+    r.x[0] = A.x; r.x[1] = A.y; r.x[2] = A.z; r.V = A.w;
+    r.v[0] = B.x; r.v[1] = B.y; r.v[2] = B.z; r.p = B.w;
+    r.rho = C.x; r.m = C.y;
+  }
+  return r;
+}
+
 template <int D>
 __device__ __forceinline__ void store_pd(const Arrays& a, int j, const PD<D>& r) {
   if (D == 2) {

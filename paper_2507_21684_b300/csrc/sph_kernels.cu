@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 template <int D>
 __global__ void k_permute(const DevSeg* __restrict__ segs, int N, const uint32_t* __restrict__ perm, Arrays in,
                           Arrays out, const uint32_t* __restrict__ keys, int C, int* __restrict__ off,
-                          float* __restrict__ xb) {
+                          float4* __restrict__ xb) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k > N) return;
   {
@@ -247,11 +247,11 @@ __global__ void k_permute(const DevSeg* __restrict__ segs, int N, const uint32_t
   }
   if (D == 2) {
     out.A[k] = make_float4(xh[0], xh[1], a.z, a.w);
-    if (xb) reinterpret_cast<float2*>(xb)[k] = make_float2(xh[0], xh[1]);
+    if (xb) xb[k] = make_float4(xh[0], xh[1], 0.f, 0.f);
   } else {
     out.A[k] = make_float4(xh[0], xh[1], xh[2], a.w);
     out.C[k] = in.C[src];
-    if (xb) reinterpret_cast<float4*>(xb)[k] = make_float4(xh[0], xh[1], xh[2], 0.f);
+    if (xb) xb[k] = make_float4(xh[0], xh[1], xh[2], 0.f);
   }
   store_cold<D>(out, k, c);
   out.B[k] = b;
@@ -453,7 +453,7 @@ int sort_scratch_words(int N) {
 
 template <int D>
 void launch_permute(const DevSeg* segs, int N, const uint32_t* perm, const Arrays& in, const Arrays& out,
-                    const uint32_t* keys, int C, int* off, float* xb, cudaStream_t st) {
+                    const uint32_t* keys, int C, int* off, float4* xb, cudaStream_t st) {
   k_permute<D><<<(N + 1 + 255) / 256, 256, 0, st>>>(segs, N, perm, in, out, keys, C, off, xb);
 }
 
@@ -533,7 +533,7 @@ void launch_download_range(const Arrays& a, int p0, int n, float* x, float* v, f
   template void launch_copy_range<D>(const Arrays&, int, const Arrays&, int, int, int, cudaStream_t);          \
   template void launch_download_range<D>(const Arrays&, int, int, float*, float*, float*, cudaStream_t);       \
   template void launch_permute<D>(const DevSeg*, int, const uint32_t*, const Arrays&, const Arrays&, const uint32_t*, \
-                                  int, int*, float*, cudaStream_t);                                             \
+                                  int, int*, float4*, cudaStream_t);                                            \
   template void launch_copy_state<D>(int, const Arrays&, const Arrays&, cudaStream_t);                        \
   template void launch_sort_pass<D>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int, int, uint32_t*,   \
                                     uint32_t*, const DevSeg*, const Arrays&, cudaStream_t);                     \

@@ -26,7 +26,7 @@ struct RebuildCtl {
 
 // Displacement check written by the sweep's epilogue (all null: no check).
 struct Displace {
-  const float* xb;       // folded positions at the last build (float2 in 2D, float4 in 3D)
+  const float4* xb;      // folded positions at the last build (x, y[, z], 0)
   unsigned* maxr;        // running maximum (float bits, non-negative)
   float inv_r2;          // 1 / (skin/2 - margin)^2
 };
@@ -46,7 +46,7 @@ void launch_sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, 
                       uint32_t* hist, uint32_t* sums, const DevSeg* segs, const Arrays& a, cudaStream_t st);
 template <int D>
 void launch_permute(const DevSeg* segs, int N, const uint32_t* perm, const Arrays& in, const Arrays& out,
-                    const uint32_t* keys, int C, int* off, float* xb, cudaStream_t st);
+                    const uint32_t* keys, int C, int* off, float4* xb, cudaStream_t st);
 template <int D>
 void launch_copy_state(int N, const Arrays& src, const Arrays& dst, cudaStream_t st);
 void launch_rebuild_decide(RebuildCtl* ctl, int interval, cudaGraphConditionalHandle h, cudaStream_t st);

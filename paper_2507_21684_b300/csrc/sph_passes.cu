@@ -338,35 +338,33 @@ __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restr
   const int tgt = threadIdx.x / Cfg::LANES;
   const int lane = threadIdx.x % Cfg::LANES;
   long long pairs_cta = 0;
-  // tiles are handed out dynamically (one atomic per CTA and tile): load balance whatever the
-  // occupancy and the tile sizes (a CTA asks for its next tile only when it is free)
-  if (threadIdx.x == 0) s_tile = atomicAdd(t.tile_ctr, 1);
-  __syncthreads();
-  int ti = s_tile;
+  // tiles are handed out dynamically (one atomic per CTA and tile) after a first tile per CTA
+  // by block index: load balance whatever the occupancy and the tile sizes, and no atomic on the
+  // first tile's path
+  int ti = blockIdx.x;
   while (ti < nt) {
     const Tile T = tiles[ti];
     const DevSeg& s = t.segs[T.seg];
     const int i = T.p0 + tgt;
     const bool valid = i < T.p1;
-    // the target's own data and key are requested before staging, so their loads overlap it
-    typename Pass::Body body;
-    bool active = false;
-    int key = 0;
-    float xi[3] = {0.f, 0.f, 0.f};
-    if (valid) {
-      active = pass.init(body, s, i);
-      const float4 A = __ldg(t.a.A + i);
-      xi[0] = A.x; xi[1] = A.y; xi[2] = A.z;
-      key = (int)t.keys[i];
-    }
+    // the targets' own records go to the cache while the neighbours are staged; the key and the
+    // meta word (for the skip decision) are requested now so that their loads overlap too
+    fill_target_cache<D>(sm.tc, t.a, pass.tex0(), pass.tex1(), T.p0, T.p1 - T.p0);
+    const int key = valid ? (int)t.keys[i] : 0;
     // tiles without a target of this pass (walls only, fluid only) are skipped unstaged
     const bool want = valid && lane == 0 && Pass::wants(t.a.meta[i].x);
     const int stg = stage_tile<D, E>(sm, s, T, t.a, t.cell_off, extra0, extra1, want);
+    const TgtView tv{sm.tc.view(), sm.tc.E0, sm.tc.E1, tgt};
     if (stg >= 0) {
       const bool staged = stg > 0;
+      typename Pass::Body body;
+      bool active = false;
       int ccol = 0;
-      float flo[3] = {0.f, 0.f, 0.f}, fhi[3] = {0.f, 0.f, 0.f};
+      float xi[3] = {0.f, 0.f, 0.f}, flo[3] = {0.f, 0.f, 0.f}, fhi[3] = {0.f, 0.f, 0.f};
       if (valid) {
+        active = pass.init(body, s, i, tv);
+        const float4 A = tv.a.A[tgt];
+        xi[0] = A.x; xi[1] = A.y; xi[2] = A.z;
         const int c[3] = {key - (s.cell_base + (T.cz * s.n[1] + T.cy) * s.n[0]), T.cy, T.cz};
         ccol = c[0] - (staged ? sm.colbase : 0);
 #pragma unroll
@@ -384,13 +382,13 @@ __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restr
       }
       __syncwarp();
       body.template reduce<Cfg::LANES>();
-      if (valid && lane == 0) pass.finish(body, s, i);
+      if (valid && lane == 0) pass.finish(body, s, i, tv);
       pairs_cta += np;
     } else if (valid && lane == 0) {
-      pass.skip(i);
+      pass.skip(i, tv);
     }
     __syncthreads();  // shared memory is restaged for the next tile
-    if (threadIdx.x == 0) s_tile = atomicAdd(t.tile_ctr, 1);
+    if (threadIdx.x == 0) s_tile = gridDim.x + atomicAdd(t.tile_ctr, 1);
     __syncthreads();
     ti = s_tile;
   }
@@ -432,22 +430,24 @@ struct WallPass {
   Arrays a;
   // superset of the targets init() activates, from the meta word alone
   __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) != 0; }
-  __device__ __forceinline__ void skip(int) {}
+  __device__ __forceinline__ void skip(int, const TgtView&) {}
   __device__ __forceinline__ void flush() {}
-  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
+  __device__ __forceinline__ const float4* tex0() const { return nullptr; }
+  __device__ __forceinline__ const float4* tex1() const { return nullptr; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView& tv) {
     b.s = &s;
     b.sW = b.sp = b.sh = 0.f;
-    const uint2 m = a.meta[i];
-    const float4 A = __ldg(a.A + i);
+    const uint2 m = tv.a.meta[tv.k];
+    const float4 A = tv.a.A[tv.k];
     b.xi[0] = A.x; b.xi[1] = A.y;
     if (D == 3) b.xi[2] = A.z;
     return (m.x & kWallBit) != 0;
   }
-  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i) {
-    if (!(a.meta[i].x & kWallBit)) return;
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i, const TgtView& tv) {
+    if (!(tv.a.meta[tv.k].x & kWallBit)) return;
     const float pw = b.sW > 0.f ? (b.sp + b.sh) / b.sW : 0.f;
     const float rw = tait_rho(s, pw);
-    PD<D> me = load_pd<D>(a, i);
+    PD<D> me = load_pd_plain<D>(tv.a, tv.k);
     me.rho = rw;
     me.p = pw;
     me.V = fabsf(me.m) / rw;
@@ -472,26 +472,28 @@ struct DensityPass {
   };
   Arrays a;
   __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) == 0; }
-  __device__ __forceinline__ void skip(int) {}
+  __device__ __forceinline__ void skip(int, const TgtView&) {}
   __device__ __forceinline__ void flush() {}
-  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
+  __device__ __forceinline__ const float4* tex0() const { return nullptr; }
+  __device__ __forceinline__ const float4* tex1() const { return nullptr; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView& tv) {
     b.s = &s;
     b.rho = 0.0;
-    const float4 A = __ldg(a.A + i);
+    const float4 A = tv.a.A[tv.k];
     b.xi[0] = A.x; b.xi[1] = A.y;
     if (D == 3) b.xi[2] = A.z;
-    return !(a.meta[i].x & kWallBit);
+    return !(tv.a.meta[tv.k].x & kWallBit);
   }
-  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i) {
-    if (a.meta[i].x & kWallBit) return;
-    PD<D> me = load_pd<D>(a, i);
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i, const TgtView& tv) {
+    if (tv.a.meta[tv.k].x & kWallBit) return;
+    PD<D> me = load_pd_plain<D>(tv.a, tv.k);
     const double rho = b.rho + (double)(me.m * s.Kw);  // self term, w(0) = 1
     const float e = (float)((rho - (double)s.rho0) / (double)s.rho0);
     me.rho = (float)rho;
     me.p = s.B * expm1f(s.gamma * log1pf(e));
     me.V = me.m / me.rho;
     store_pd<D>(a, i, me);
-    Cold c = load_cold<D>(a, i);
+    Cold c = load_cold<D>(tv.a, tv.k);
     c.rlo = (float)(rho - (double)me.rho);
     store_cold<D>(a, i, c);
   }
@@ -546,15 +548,17 @@ struct SweepPass {
   }
   // fluid targets only (walls carry m <= 0); a skipped wall keeps its state
   __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) == 0; }
-  __device__ __forceinline__ void skip(int i) {
+  __device__ __forceinline__ void skip(int i, const TgtView& tv) {
     if (!INTEGRATE) return;
-    store_pd<D>(out, i, load_pd<D>(a, i));
-    store_cold<D>(out, i, load_cold<D>(a, i));
-    out.meta[i] = a.meta[i];
+    store_pd<D>(out, i, load_pd_plain<D>(tv.a, tv.k));
+    store_cold<D>(out, i, load_cold<D>(tv.a, tv.k));
+    out.meta[i] = tv.a.meta[tv.k];
   }
-  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
+  __device__ __forceinline__ const float4* tex0() const { return INTEGRATE ? disp.xb : nullptr; }
+  __device__ __forceinline__ const float4* tex1() const { return nullptr; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView& tv) {
     b.s = &s;
-    const PD<D> me = load_pd<D>(a, i);
+    const PD<D> me = load_pd_plain<D>(tv.a, tv.k);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       b.xi[k] = me.x[k];
@@ -566,9 +570,9 @@ struct SweepPass {
     b.c1 = b.c2 = 0.f;
     return me.m > 0.f;  // fluid
   }
-  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i) {
-    PD<D> me = load_pd<D>(a, i);
-    const uint2 m = a.meta[i];
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i, const TgtView& tv) {
+    PD<D> me = load_pd_plain<D>(tv.a, tv.k);
+    const uint2 m = tv.a.meta[tv.k];
     const bool fluid = me.m > 0.f;
     float acc_a[D];
     const float inv_rho = 1.f / me.rho;
@@ -585,7 +589,7 @@ struct SweepPass {
       }
       return;
     }
-    Cold c = load_cold<D>(a, i);
+    Cold c = load_cold<D>(tv.a, tv.k);
     if (fluid) {
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -602,14 +606,13 @@ struct SweepPass {
         me.V = me.m / me.rho;
       }
       if (disp.xb) {  // displacement since the last build, in units of (skin/2 - margin)
+        const float4 xb = tv.e0[tv.k];
         float d2 = 0.f;
         if (D == 2) {
-          const float2 b = reinterpret_cast<const float2*>(disp.xb)[i];
-          const float e0 = me.x[0] - b.x, e1 = me.x[1] - b.y;
+          const float e0 = me.x[0] - xb.x, e1 = me.x[1] - xb.y;
           d2 = fmaf(e0, e0, e1 * e1);
         } else {
-          const float4 b = reinterpret_cast<const float4*>(disp.xb)[i];
-          const float e0 = me.x[0] - b.x, e1 = me.x[1] - b.y, e2 = me.x[D - 1] - b.z;
+          const float e0 = me.x[0] - xb.x, e1 = me.x[1] - xb.y, e2 = me.x[D - 1] - xb.z;
           d2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
         }
         dmax = fmaxf(dmax, d2 * disp.inv_r2);
@@ -649,10 +652,12 @@ struct PairPass {
   unsigned long long* count;
   long long cap;
   __device__ static __forceinline__ bool wants(uint32_t) { return true; }
-  __device__ __forceinline__ void skip(int) {}
+  __device__ __forceinline__ void skip(int, const TgtView&) {}
   __device__ __forceinline__ void flush() {}
-  __device__ __forceinline__ bool init(Body& b, const DevSeg&, int i) {
-    b.id_i = a.meta[i].x & ~kWallBit;
+  __device__ __forceinline__ const float4* tex0() const { return nullptr; }
+  __device__ __forceinline__ const float4* tex1() const { return nullptr; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg&, int, const TgtView& tv) {
+    b.id_i = tv.a.meta[tv.k].x & ~kWallBit;
     b.meta = a.meta;
     b.pi = pi;
     b.pj = pj;
@@ -660,7 +665,7 @@ struct PairPass {
     b.cap = cap;
     return true;
   }
-  __device__ __forceinline__ void finish(Body&, const DevSeg&, int) {}
+  __device__ __forceinline__ void finish(Body&, const DevSeg&, int, const TgtView&) {}
 };
 
 // ================================================================== adjoint sweep (Sec. 2.2)
@@ -755,11 +760,13 @@ struct AdjPass {
   float4 *XBout, *VBout;
   float* nu_part;  // per particle viscosity partials (summed deterministically afterwards)
   __device__ static __forceinline__ bool wants(uint32_t) { return true; }
-  __device__ __forceinline__ void skip(int) {}
+  __device__ __forceinline__ void skip(int, const TgtView&) {}
   __device__ __forceinline__ void flush() {}
-  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i) {
+  __device__ __forceinline__ const float4* tex0() const { return XBin; }
+  __device__ __forceinline__ const float4* tex1() const { return VBin; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i, const TgtView& tv) {
     b.s = &s;
-    const PD<D> me = load_pd<D>(a, i);
+    const PD<D> me = load_pd_plain<D>(tv.a, tv.k);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       b.xi[k] = me.x[k];
@@ -778,8 +785,8 @@ struct AdjPass {
     b.grho = b.gnu = 0.f;
     return me.m > 0.f;
   }
-  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i) {
-    const float4 xb = XBin[i], vb = VBin[i];
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i, const TgtView& tv) {
+    const float4 xb = tv.e0[tv.k], vb = tv.e1[tv.k];
     const float xbs[3] = {xb.x, xb.y, xb.z}, vbs[3] = {vb.x, vb.y, vb.z};
     float ox[3] = {0.f, 0.f, 0.f}, ov[3] = {0.f, 0.f, 0.f};
 #pragma unroll

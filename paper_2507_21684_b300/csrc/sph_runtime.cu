@@ -359,7 +359,7 @@ void Scene::alloc_all() {
   d_pairs = (unsigned long long*)mem.get(sizeof(unsigned long long) * 2);
   d_ctl = (RebuildCtl*)mem.get(sizeof(RebuildCtl));
   CK(cudaMemsetAsync(d_ctl, 0, sizeof(RebuildCtl), st));
-  xbuild = (float*)mem.get((D == 2 ? 8 : 16) * (size_t)N);
+  xbuild = (float4*)mem.get(sizeof(float4) * (size_t)N);
   d_nubar = (double*)mem.get(sizeof(double) * (size_t)(S + 1));
   CK(cudaMemsetAsync(d_status, 0, sizeof(int) * 4, st));
   CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long) * 2, st));

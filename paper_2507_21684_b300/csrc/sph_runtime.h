@@ -118,7 +118,7 @@ struct Scene {
   bool dev_policy = false;          // skin large enough for the displacement check
   float inv_r2 = 0.f;               // 1 / (skin/2 - margin)^2
   RebuildCtl* d_ctl = nullptr;
-  float* xbuild = nullptr;          // folded positions at the last build
+  float4* xbuild = nullptr;         // folded positions at the last build
   cudaStream_t st_body = nullptr;   // captures the rebuild body of a conditional node
   bool in_body = false;
   long long body_launches = 0;      // kernels in one conditional rebuild body

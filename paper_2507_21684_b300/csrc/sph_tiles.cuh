@@ -32,6 +32,65 @@ struct TileCfg<3> {
   static constexpr int TP = 32, LANES = 8, THREADS = 256, CAP = 1024, LIST = 16, NL = 9;
 };
 
+// The records of a tile's own targets (a contiguous range of sorted particles), copied into
+// shared memory with cp.async while the neighbour lines are staged, so that a pass's prologue
+// and epilogue read them without a global round trip.  E0/E1: per-target extras of the pass.
+template <int D>
+struct TargetCache {
+  static constexpr int TP = TileCfg<D>::TP;
+  float4 A[TP], B[TP], X[TP], O[TP];
+  float4 XL[D == 3 ? TP : 1];
+  float2 C[D == 3 ? TP : 1];
+  uint2 meta[TP];
+  float4 E0[TP], E1[TP];
+  // the cache seen through the Arrays interface (local index = i - tile start)
+  __device__ __forceinline__ Arrays view() {
+    Arrays v;
+    v.A = A; v.B = B; v.C = C; v.X = X; v.XL = XL; v.O = O; v.meta = meta;
+    return v;
+  }
+};
+
+// A pass's view of its target in the cache: records (local index k) and the two extras.
+struct TgtView {
+  Arrays a;
+  const float4* e0;
+  const float4* e1;
+  int k;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Issue the copies of targets [p0, p0 + n) into the cache (all threads of the CTA; completion is
+// awaited by stage_tile before its first barrier).
+template <int D>
+__device__ __forceinline__ void fill_target_cache(TargetCache<D>& tc, const Arrays& a, const float4* e0,
+                                                  const float4* e1, int p0, int n) {
+  constexpr int NF = (D == 3) ? 5 : 4;  // float4 arrays A, B, X, O (, XL)
+  for (int e = threadIdx.x; e < n * NF; e += blockDim.x) {
+    const int f = e / n, k = e - f * n, g = p0 + k;
+    const float4* src = f == 0 ? a.A : f == 1 ? a.B : f == 2 ? a.X : f == 3 ? a.O : a.XL;
+    float4* dst = f == 0 ? tc.A : f == 1 ? tc.B : f == 2 ? tc.X : f == 3 ? tc.O : tc.XL;
+    cp_async16(dst + k, src + g);
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    cp_async8(&tc.meta[k], a.meta + p0 + k);
+    if (D == 3) cp_async8(&tc.C[k], a.C + p0 + k);
+    if (e0) cp_async16(&tc.E0[k], e0 + p0 + k);
+    if (e1) cp_async16(&tc.E1[k], e1 + p0 + k);
+  }
+  cp_async_commit();
+}
+
 // Maximum columns per staged line: TP targets can span TP cells, plus the two neighbours.
 template <int D>
 constexpr int tile_cols() { return TileCfg<D>::TP + 2; }
@@ -50,6 +109,7 @@ struct TileSmem {
   float4 B[CAP];
   float2 C[D == 3 ? CAP : 1];
   float4 E[EXTRA > 0 ? EXTRA * CAP : 1];
+  TargetCache<D> tc;
   int colstart[NL * NCOL + 1];      // staged index of each (line, column) cell start
   unsigned short list[TileCfg<D>::LIST * TileCfg<D>::THREADS];
   int run_g[NRUN];                  // global start of each run
@@ -98,7 +158,8 @@ __device__ __forceinline__ int staged_run(const TileSmem<D, EXTRA>& sm, int k) {
 }
 
 // Build the run table of a tile and stage its particles: two dependent global round trips (every
-// cell offset the tile needs, then the particle records).  Returns 1 when staged, 0 (fallback)
+// cell offset the tile needs, then the particle records).  The caller's cp.async copies into the
+// target cache are complete and visible after the first barrier.  Returns 1 when staged, 0 (fallback)
 // when the staged region exceeds the shared-memory capacity or the column table, -1 when no
 // thread passed want (no target of the pass in this tile: nothing is staged; the decision rides
 // on the first barrier, so it costs no extra round trip).  All threads of the CTA call it.
@@ -116,6 +177,7 @@ __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T
   const int ncols = T.cx1 - T.cx0 + 3;  // columns colbase .. colbase + ncols - 1
   if (ncols > NCOL - 1) {               // a sparse line: more cells than the table holds
     if (tid == 0) sm.fallback = 1;
+    cp_async_wait_all();
     return __syncthreads_or(want) ? 0 : -1;
   }
   const bool px = s.periodic_mask & 1;
@@ -147,6 +209,7 @@ __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T
       sm.img[l][w] = v;
     }
   }
+  cp_async_wait_all();  // the target cache (issued by the caller) is complete at this barrier
   if (!__syncthreads_or(want)) return -1;
   // 2) run table (left image, in-box columns, right image per line) and its exclusive scan
   if (tid < 32) {
