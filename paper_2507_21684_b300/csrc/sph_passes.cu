@@ -166,7 +166,7 @@ __device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s
   auto drain = [&]() {
     for (int e = 0; e < cnt; ++e) {
       const unsigned code = list[e * Cfg::THREADS];
-      const int k = (int)(code & 0x3ffu);
+      const int k = (int)(code & 0x1fffu);  // bits 0..12: staged index (CAP <= 8192)
       PD<D> pj = smem_pd<D, E>(sm, k);
       // periodic image of the entry: the target takes off the box length on the flagged axes
       float xs[D];

@@ -29,7 +29,7 @@ struct TileCfg<2> {
 };
 template <>
 struct TileCfg<3> {
-  static constexpr int TP = 32, LANES = 8, THREADS = 256, CAP = 1024, LIST = 16, NL = 9;
+  static constexpr int TP = 32, LANES = 8, THREADS = 256, CAP = 1024, LIST = 18, NL = 9;
 };
 
 // The records of a tile's own targets (a contiguous range of sorted particles), copied into
@@ -102,6 +102,8 @@ constexpr int tile_cols() { return TileCfg<D>::TP + 2; }
 template <int D, int EXTRA>
 struct TileSmem {
   static constexpr int CAP = TileCfg<D>::CAP;
+  static_assert(CAP <= 8192, "hit-list entries hold the staged index in 13 bits");
+  static_assert(TileCfg<D>::TP * TileCfg<D>::LANES == TileCfg<D>::THREADS, "one group of LANES per target");
   static constexpr int NCOL = tile_cols<D>() + 1;
   static constexpr int NL = TileCfg<D>::NL;
   static constexpr int NRUN = 3 * NL;
