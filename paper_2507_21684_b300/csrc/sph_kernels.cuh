@@ -13,7 +13,7 @@ struct TravArgs {
   const int* cell_off;       // CSR offsets over global cells
   int* status;               // device error word (bit 0: unstable state)
   unsigned long long* pair_count;  // optional: in-radius pairs of fluid particles
-  int* tile_ctr;             // dynamic tile counter of the launch (zeroed before it)
+  int* tile_ctr;             // [0] dynamic tile counter, [1] finished CTAs (both zero between launches)
 };
 
 // Device-side rebuild policy state of a scene (Verlet skin).

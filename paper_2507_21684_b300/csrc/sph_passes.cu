@@ -169,9 +169,20 @@ __device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s
       const int k = (int)(code & 0x1fffu);  // bits 0..12: staged index (CAP <= 8192)
       PD<D> pj = smem_pd<D, E>(sm, k);
       // periodic image of the entry: the target takes off the box length on the flagged axes
+      // (an exact shift: the target lies in the upper half of the box on those axes)
       float xs[D];
+      if (D == 2) {  // (2D: most entries carry no shift)
 #pragma unroll
-      for (int q = 0; q < D; ++q) xs[q] = xt0[q] - ((code >> (13 + q)) & 1u ? s.L[q] : 0.f);
+        for (int q = 0; q < D; ++q) xs[q] = xt0[q];
+        if (code >> 13) {
+#pragma unroll
+          for (int q = 0; q < D; ++q)
+            if ((code >> (13 + q)) & 1u) xs[q] -= s.L[q];
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < D; ++q) xs[q] = xt0[q] - ((code >> (13 + q)) & 1u ? s.L[q] : 0.f);
+      }
       float4 ex = make_float4(0.f, 0.f, 0.f, 0.f);
       float pp = 0.f;
       if (E > 0) ex = sm.E[k];
@@ -329,7 +340,7 @@ __device__ __forceinline__ double group_sum(double v) {
 template <int D, int E, int SELF, class Pass>
 __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restrict__ tiles, const int* __restrict__ ntiles,
                                           const float4* __restrict__ extra0, const float* __restrict__ extra1,
-                                          Pass& pass) {
+                                          Pass& pass, const int* __restrict__ tile_list = nullptr) {
   using Cfg = TileCfg<D>;
   extern __shared__ __align__(16) unsigned char smraw[];
   TileSmem<D, E>& sm = *reinterpret_cast<TileSmem<D, E>*>(smraw);
@@ -343,7 +354,7 @@ __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restr
   // first tile's path
   int ti = blockIdx.x;
   while (ti < nt) {
-    const Tile T = tiles[ti];
+    const Tile T = tiles[tile_list ? tile_list[ti] : ti];  // a list selects a subset of the tiles
     const DevSeg& s = t.segs[T.seg];
     const int i = T.p0 + tgt;
     const bool valid = i < T.p1;
@@ -398,6 +409,15 @@ __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restr
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(t.pair_count, (unsigned long long)v);
+  }
+  // the last CTA to finish zeroes the tile counter (and its own) for the next tiled launch:
+  // every CTA has taken its last tile index before it counts itself done
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(t.tile_ctr + 1, 1) == (int)gridDim.x - 1) {
+      t.tile_ctr[0] = 0;
+      t.tile_ctr[1] = 0;
+    }
   }
 }
 
@@ -510,18 +530,20 @@ struct SweepPass {
     const DevSeg* s;
     float xi[D], vi[D], rho_i, p_i;
     float acc[D], c1, c2;
+    float invH, Kg, Cv, eH2;  // 2D: the scene's constants kept in registers (3D reads them)
     __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4, float, int) {
-      const DevSeg& c = *s;
+      const float cinvH = D == 2 ? invH : s->invH, cKg = D == 2 ? Kg : s->Kg;
+      const float cCv = D == 2 ? Cv : s->Cv, ceH2 = D == 2 ? eH2 : s->eH2;
       float r[D];
       const float r2 = diff<D>(xs, pj.x, r);
-      const float q = safe_q(r2, c.invH);
-      const float gK = c.Kg * kern_gt<KERN>(q);
+      const float q = safe_q(r2, cinvH);
+      const float gK = cKg * kern_gt<KERN>(q);
       float w = 0.f;
 #pragma unroll
       for (int k = 0; k < D; ++k) w = fmaf(vi[k] - pj.v[k], r[k], w);
-      const float sd = __fdividef(1.f, r2 + c.eH2);
+      const float sd = __fdividef(1.f, r2 + ceH2);
       const float VgK = pj.V * gK;
-      const float tt = VgK * fmaf(c.Cv * w, sd, -(p_i + pj.p));
+      const float tt = VgK * fmaf(cCv * w, sd, -(p_i + pj.p));
 #pragma unroll
       for (int k = 0; k < D; ++k) acc[k] = fmaf(tt, r[k], acc[k]);
       c1 = fmaf(VgK, w, c1);
@@ -558,6 +580,12 @@ struct SweepPass {
   __device__ __forceinline__ const float4* tex1() const { return nullptr; }
   __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView& tv) {
     b.s = &s;
+    if (D == 2) {
+      b.invH = s.invH;
+      b.Kg = s.Kg;
+      b.Cv = s.Cv;
+      b.eH2 = s.eH2;
+    }
     const PD<D> me = load_pd_plain<D>(tv.a, tv.k);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -802,11 +830,24 @@ struct AdjPass {
 };
 
 // ================================================================== kernels
+// The wall pass visits only the tiles that hold a wall particle (listed at each rebuild).
 template <int D, int KERN>
-__global__ void __launch_bounds__(256, 4) k_walls_t(TravArgs t, const Tile* tiles, const int* ntiles) {
+__global__ void __launch_bounds__(256, 4) k_walls_t(TravArgs t, const Tile* tiles, const int* wall_tiles,
+                                                 const int* n_wall_tiles) {
   WallPass<D, KERN> pass;
   pass.a = t.a;
-  run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
+  run_tiles<D, 0, 0>(t, tiles, n_wall_tiles, nullptr, nullptr, pass, wall_tiles);
+}
+
+// List of the tiles holding at least one wall particle: one warp per tile.
+__global__ void k_wall_tiles(const Tile* __restrict__ tiles, const int* __restrict__ ntiles,
+                             const uint2* __restrict__ meta, int* __restrict__ list, int* __restrict__ count) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= *ntiles) return;  // warp-uniform
+  const Tile T = tiles[w];
+  bool wall = false;
+  for (int k = T.p0 + lane; k < T.p1; k += 32) wall |= (meta[k].x & kWallBit) != 0;
+  if (__any_sync(kFull, wall) && lane == 0) list[atomicAdd(count, 1)] = w;
 }
 template <int D, int KERN>
 __global__ void __launch_bounds__(256, 4) k_density_t(TravArgs t, const Tile* tiles, const int* ntiles) {
@@ -899,40 +940,41 @@ void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, 
   cudaMemsetAsync(ntiles, 0, sizeof(int), st);
   if (n_lines > 0) k_tiles<D><<<(n_lines + 7) / 8, 256, 0, st>>>(segs, S, line_base, n_lines, cell_off, tiles, ntiles);
 }
+void launch_wall_tiles(const Tile* tiles, const int* ntiles, int tiles_upper, const uint2* meta, int* list, int* count,
+                       cudaStream_t st) {
+  cudaMemsetAsync(count, 0, sizeof(int), st);
+  k_wall_tiles<<<(tiles_upper + 7) / 8, 256, 0, st>>>(tiles, ntiles, meta, list, count);
+}
 
 template <int D, int KERN>
-void launch_walls_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st) {
-  cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
-  k_walls_t<D, KERN><<<pass_grid((const void*)k_walls_t<D, KERN>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles);
+void launch_walls_t(const TravArgs& t, const Tile* tiles, const int* wall_tiles, const int* n_wall_tiles,
+                    int tiles_upper, cudaStream_t st) {
+  k_walls_t<D, KERN><<<pass_grid((const void*)k_walls_t<D, KERN>, tiles_upper), 256, pass_smem<D>(0), st>>>(
+      t, tiles, wall_tiles, n_wall_tiles);
 }
 template <int D, int KERN>
 void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st) {
-  cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
   k_density_t<D, KERN><<<pass_grid((const void*)k_density_t<D, KERN>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles);
 }
 template <int D, int KERN>
 void launch_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
                     const Displace& disp, cudaStream_t st) {
-  cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
   k_sweep_t<D, KERN, true><<<pass_grid((const void*)k_sweep_t<D, KERN, true>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, out, RateOut{}, disp);
 }
 template <int D, int KERN>
 void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const RateOut& ro,
                     cudaStream_t st) {
-  cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
   k_sweep_t<D, KERN, false><<<pass_grid((const void*)k_sweep_t<D, KERN, false>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, Arrays{}, ro, Displace{});
 }
 template <int D>
 void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
                     unsigned long long* count, long long cap, cudaStream_t st) {
-  cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
   k_pairs_t<D><<<pass_grid((const void*)k_pairs_t<D>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, pi, pj, count, cap);
 }
 template <int D, int KERN>
 void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* S,
                   const float* Pp, const float4* XBin, const float4* VBin, float4* XBout, float4* VBout,
                   float* nu_part, cudaStream_t st) {
-  cudaMemsetAsync(t.tile_ctr, 0, sizeof(int), st);
   k_adj_t<D, KERN><<<pass_grid((const void*)k_adj_t<D, KERN>, tiles_upper), 256, pass_smem<D>(D == 2 ? 1 : 2), st>>>(
       t, tiles, ntiles, S, Pp, XBin, VBin, XBout, VBout, nu_part);
 }
@@ -972,7 +1014,7 @@ cudaError_t configure_passes() {
 SPH_INST_PD(2)
 SPH_INST_PD(3)
 #define SPH_INST_PDK(D, K)                                                                                   \
-  template void launch_walls_t<D, K>(const TravArgs&, const Tile*, const int*, int, cudaStream_t);          \
+  template void launch_walls_t<D, K>(const TravArgs&, const Tile*, const int*, const int*, int, cudaStream_t); \
   template void launch_density_t<D, K>(const TravArgs&, const Tile*, const int*, int, cudaStream_t);        \
   template void launch_sweep_t<D, K>(const TravArgs&, const Tile*, const int*, int, const Arrays&, const Displace&, \
                                      cudaStream_t);                                                          \

@@ -353,8 +353,13 @@ void Scene::alloc_all() {
   line_base = (int*)mem.get(sizeof(int) * S);
   CK(cudaMemcpyAsync(line_base, line_base_h.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
   tiles = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
+  if (any_walls) {
+    wall_tiles = (int*)mem.get(sizeof(int) * (size_t)tiles_upper);
+    d_nwall = (int*)mem.get(sizeof(int) * 2);
+  }
   d_ntiles = (int*)mem.get(sizeof(int) * 2);
   d_tile_ctr = (int*)mem.get(sizeof(int) * 4);
+  CK(cudaMemsetAsync(d_tile_ctr, 0, sizeof(int) * 4, st));  // tiled kernels leave it zeroed
   d_status = (int*)mem.get(sizeof(int) * 4);
   d_pairs = (unsigned long long*)mem.get(sizeof(unsigned long long) * 2);
   d_ctl = (RebuildCtl*)mem.get(sizeof(RebuildCtl));
@@ -491,32 +496,38 @@ std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& o
   else
     launch_permute<3>(dseg, N, pm, in, out, ks, C_tot, off_out, xbuild, st);
   CKL();
-  build_tiles(off_out);
+  build_tiles(off_out, out.meta);
   prof_end();
   const int scan_launches = 256 * ((N + 2047) / 2048) <= 16384 ? 1 : 3;
   launches += passes * (2 + scan_launches) + 1;
   return {ks, pm};
 }
 
-// Tile table of a cell structure (CSR offsets `off`).
-void Scene::build_tiles(const int* off) {
+// Tile table of a cell structure (CSR offsets `off`), and the list of tiles holding wall
+// particles (from the sorted meta words) when the scene has walls.
+void Scene::build_tiles(const int* off, const uint2* meta) {
   if (D == 2)
     launch_tiles<2>(dseg, S, line_base, n_lines, off, tiles, d_ntiles, st);
   else
     launch_tiles<3>(dseg, S, line_base, n_lines, off, tiles, d_ntiles, st);
   CKL();
   ++launches;
+  if (any_walls && meta) {
+    launch_wall_tiles(tiles, d_ntiles, tiles_upper, meta, wall_tiles, d_nwall, st);
+    CKL();
+    ++launches;
+  }
 }
 
 void Scene::passes_before_sweep(const TravArgs& t) {
   if (any_walls) {
     prof_begin(2);
     if (D == 2) {
-      if (kern == 0) launch_walls_t<2, 0>(t, tiles, d_ntiles, tiles_upper, st);
-      else launch_walls_t<2, 1>(t, tiles, d_ntiles, tiles_upper, st);
+      if (kern == 0) launch_walls_t<2, 0>(t, tiles, wall_tiles, d_nwall, tiles_upper, st);
+      else launch_walls_t<2, 1>(t, tiles, wall_tiles, d_nwall, tiles_upper, st);
     } else {
-      if (kern == 0) launch_walls_t<3, 0>(t, tiles, d_ntiles, tiles_upper, st);
-      else launch_walls_t<3, 1>(t, tiles, d_ntiles, tiles_upper, st);
+      if (kern == 0) launch_walls_t<3, 0>(t, tiles, wall_tiles, d_nwall, tiles_upper, st);
+      else launch_walls_t<3, 1>(t, tiles, wall_tiles, d_nwall, tiles_upper, st);
     }
     CKL();
     prof_end();
@@ -849,7 +860,7 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
       CKL();
       TravArgs t = trav(slot.a, slot.keys, slot.off);
       t.pair_count = nullptr;
-      build_tiles(slot.off);
+      build_tiles(slot.off, nullptr);
       prof_begin(4);
       if (D == 2) {
         if (kern == 0)

@@ -107,6 +107,8 @@ struct Scene {
   Tile* tiles = nullptr;
   int* d_ntiles = nullptr;
   int* d_tile_ctr = nullptr;   // dynamic tile counter (zeroed before each tiled launch)
+  int* wall_tiles = nullptr;   // tiles holding a wall particle (wall pass), and their count
+  int* d_nwall = nullptr;
   int* d_status = nullptr;
   unsigned long long* d_pairs = nullptr;
   double* d_nubar = nullptr;
@@ -169,7 +171,7 @@ struct Scene {
   void prof_end();
   std::pair<uint32_t*, uint32_t*> rebuild(const Arrays& in, const Arrays& out, uint32_t* keys_out,
                                           uint32_t* perm_out, int* off_out);
-  void build_tiles(const int* off);
+  void build_tiles(const int* off, const uint2* meta);
   void passes_before_sweep(const TravArgs& t);
   void sweep(const TravArgs& t, const Arrays& out);
   void host_rebuild();
