@@ -178,6 +178,13 @@ SPH_API int sph_debug_pairs(sph_scene* scene, int64_t* n_pairs, int32_t* pi, int
 SPH_API int sph_profile(sph_scene* scene, int enable);
 SPH_API int sph_timing(sph_scene* scene, int kernel_class, double* ms, int64_t* launches);
 
+/* How sph_step issues its work: use_graphs = 1 (default) captures chunks of graph_chunk steps
+ * (default 8) into CUDA graphs and replays them; 0 launches every kernel from the host, one step
+ * at a time, and then rebuilds the cell structure every step (the device-side skin check needs
+ * the graphs' conditional nodes).  Results do not depend on the choice, except through the
+ * summation order that the rebuild schedule sets.  SPH_EINVAL for graph_chunk outside [1, 4096]. */
+SPH_API int sph_set_execution(sph_scene* scene, int use_graphs, int graph_chunk);
+
 /* Counters of the last sph_step/sph_rollout/sph_adjoint call: in-radius ordered pairs per step
  * (fluid i), kernel launches executed (conditional rebuilds included).  Synchronises. */
 SPH_API int sph_counters(sph_scene* scene, int64_t* pairs_per_step, int64_t* launches);

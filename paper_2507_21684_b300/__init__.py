@@ -117,6 +117,7 @@ def lib() -> C.CDLL:
     L.sph_timing.argtypes = [vp, C.c_int, P(C.c_double), P(C.c_int64)]
     L.sph_counters.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
     L.sph_stats.argtypes = [vp, P(C.c_int64), P(C.c_int64), P(C.c_int64)]
+    L.sph_set_execution.argtypes = [vp, C.c_int, C.c_int]
     L.sph_destroy.argtypes = [vp]
     L.sph_destroy.restype = None
     L.sph_server_create.argtypes = [C.c_size_t, C.c_int, P(vp)]
@@ -348,6 +349,10 @@ class Scene:
         launches = C.c_int64()
         _check(lib().sph_counters(self._h, C.byref(pairs), C.byref(launches)))
         return pairs.value, launches.value
+
+    def set_execution(self, use_graphs: bool = True, graph_chunk: int = 8):
+        """Graph-captured chunks of steps (default) or eager launches (sph_set_execution)."""
+        _check(lib().sph_set_execution(self._h, 1 if use_graphs else 0, int(graph_chunk)))
 
     def stats(self) -> dict:
         """Cumulative steps, cell rebuilds and kernel launches since the scene was created."""

@@ -1296,6 +1296,16 @@ int sph_debug_pairs(sph_scene* sc, int64_t* n_pairs, int32_t* pi, int32_t* pj, i
   API_END
 }
 
+int sph_set_execution(sph_scene* sc, int use_graphs, int graph_chunk) {
+  if (!sc || graph_chunk < 1 || graph_chunk > 4096) {
+    sph::set_err("sph_set_execution: NULL scene or graph_chunk outside [1, 4096]");
+    return SPH_EINVAL;
+  }
+  sc->s.use_graphs = use_graphs != 0;
+  sc->s.graph_chunk = graph_chunk;
+  return SPH_OK;
+}
+
 int sph_profile(sph_scene* sc, int enable) {
   if (!sc) return SPH_EINVAL;
   sc->s.profiling = enable != 0;

@@ -11,10 +11,11 @@ from __future__ import annotations
 
 import numpy as np
 
-DEFAULT_SKINS = (0.0, 0.05, 0.1, 0.15, 0.2, 0.3)
+DEFAULT_SKINS = (0.0, 0.02, 0.05, 0.1, 0.2, 0.3)
 
 
-def _with_skin(spec: dict, skin_over_H: float, interval: int) -> dict:
+def with_skin(spec: dict, skin_over_H: float, interval: int = 1 << 20) -> dict:
+    """The scene with a Verlet skin of skin_over_H * H (0: rebuild every step)."""
     p = dict(spec["params"])
     p["skin"] = float(np.float32(skin_over_H * p["H"]))
     p["rebuild_interval"] = int(interval if skin_over_H > 0 else 1)
@@ -51,7 +52,7 @@ def tune_skin(spec: dict, skins=DEFAULT_SKINS, interval: int = 1 << 20, steps: i
     """Time each skin (a fraction of H) on `spec` and return the best parameters with the table."""
     table = []
     for f in skins:
-        r = time_steps(_with_skin(spec, f, interval), steps=steps, warmup=warmup, chunk=chunk)
+        r = time_steps(with_skin(spec, f, interval), steps=steps, warmup=warmup, chunk=chunk)
         table.append(dict(skin_over_H=float(f), **r))
     best = min(table, key=lambda r: r["ms_per_step"])
-    return {"params": _with_skin(spec, best["skin_over_H"], interval)["params"], "best": best, "table": table}
+    return {"params": with_skin(spec, best["skin_over_H"], interval)["params"], "best": best, "table": table}
