@@ -10,7 +10,7 @@ HERE = Path(__file__).resolve().parent
 CSRC = HERE / "csrc"
 INCLUDE = HERE.parent / "include"
 LIB = HERE / "libsph_b300.so"
-SOURCES = ["sph_kernels.cu", "sph_passes.cu", "sph_runtime.cu", "sph_server.cu", "sph_noalloc.cu"]
+SOURCES = ["sph_kernels.cu", "sph_passes.cu", "sph_runtime.cu", "sph_server.cu", "sph_noalloc.cu", "sph_rebuild.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -5,78 +5,18 @@
 //      kick-drift epilogue                                          (Sec. 2.3, Sec. 3.4)
 // and the mirrored adjoint sweep of a step (Sec. 2.2, 3.3).
 #include "sph_kernels.cuh"
+#include "sph_sort.cuh"
 
 namespace sph {
 
 // ================================================================== neighbour search
-// Cell key of every particle in the current storage order (P2: floor-modulo wrap on
-// periodic axes, clamp on open axes; all in FP64 from the float32 unwrapped position).
-// Cell key of particle i, decided in FP64 from x = hi + lo exactly as floor(((x wrapped) - lo) /
-// cell edge), clamped to the grid.  Fast path: an FP32 estimate from hi alone decides the floor
-// whenever it lies farther than a margin from an integer; the margin, 2^-18 (|x| + |lo|) /
-// cell edge + 2^-18, exceeds the estimate's error (five FP32 roundings, and |lo part| <= 2^-24
-// |hi|) by more than ten times, so the FP64 decision is only taken near a cell face (and for
-// NaN or huge coordinates).  Both paths give the same key.
-template <int D>
-__device__ __forceinline__ uint32_t cell_key_of(const DevSeg* __restrict__ segs, const Arrays& a, int i) {
-  const DevSeg& s = segs[a.meta[i].y];
-  Cold c = load_cold<D>(a, i);
-  int cc3[3] = {0, 0, 0};
-  bool fast = true;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const float d = c.hi[k] - s.lo[k];
-    const float mag = fabsf(c.hi[k]) + fabsf(s.lo[k]);
-    if ((s.periodic_mask >> k) & 1) fast = fast && in_primary_box(s, k, c.hi[k]);  // no wrap
-    const float t = d * s.invcs[k];
-    const float f = floorf(t);
-    const float fr = t - f;
-    const float mt = 0x1p-18f * fmaf(mag, s.invcs[k], 1.f);
-    fast = fast && fr >= mt && fr <= 1.f - mt && fabsf(t) < 0x1p30f;
-    cc3[k] = fast ? min(max((int)f, 0), s.n[k] - 1) : 0;
-  }
-  if (!fast) {
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      double x = __dadd_rn((double)c.hi[k], (double)c.lo[k]);
-      double xw = x;
-      if ((s.periodic_mask >> k) & 1) {
-        double f = floor(__ddiv_rn(__dsub_rn(x, s.lo_d[k]), s.L_d[k]));
-        xw = __dsub_rn(x, __dmul_rn(s.L_d[k], f));
-      }
-      double cc = floor(__ddiv_rn(__dsub_rn(xw, s.lo_d[k]), s.cs_d[k]));
-      cc = fmin(fmax(cc, 0.0), (double)(s.n[k] - 1));
-      cc3[k] = (int)cc;
-    }
-  }
-  return (uint32_t)(s.cell_base + (cc3[2] * s.n[1] + cc3[1]) * s.n[0] + cc3[0]);
-}
-
-// ---- stable LSD radix sort, 8-bit digits, 2048-key tiles ---------------------------------
-constexpr int kSortThreads = 256;
-constexpr int kSortIPT = 8;
-constexpr int kSortTile = kSortThreads * kSortIPT;
-
-// Histogram of one digit per 2048-key tile.  KEYS_FROM_STATE: the keys are the cell keys of the
-// current storage order, computed here (first pass of a rebuild) instead of read.
+// ---- stable LSD radix sort, 8-bit digits, 2048-key tiles (device parts in sph_sort.cuh) ----
 template <int D, bool KEYS_FROM_STATE>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, int N, int shift,
                                                             uint32_t* __restrict__ hist, int nblocks,
                                                             const DevSeg* __restrict__ segs, Arrays a) {
   __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const int base = blockIdx.x * kSortTile;
-#pragma unroll
-  for (int k = 0; k < kSortIPT; ++k) {
-    int i = base + k * kSortThreads + threadIdx.x;
-    if (i < N) {
-      const uint32_t key = KEYS_FROM_STATE ? cell_key_of<D>(segs, a, i) : keys[i];
-      atomicAdd(&h[(key >> shift) & 255u], 1u);
-    }
-  }
-  __syncthreads();
-  hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+  sort_hist_tile<D, KEYS_FROM_STATE>(blockIdx.x, keys, N, shift, hist, nblocks, segs, a, h);
 }
 
 // Exclusive scan of n uint32 in place, 2048 per block; block totals to sums.
@@ -152,110 +92,22 @@ __global__ void k_scan_add(uint32_t* __restrict__ a, int n, const uint32_t* __re
   if (i < n) a[i] += sums[i / 2048];
 }
 
-// Scatter with stable ranks: warp w owns the contiguous sub-tile [w*256, w*256+256) and walks
-// it in 8 rounds of 32; within a round, equal digits are ranked by lane via match_any.
 template <int D, bool KEYS_FROM_STATE>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
                                                                const uint32_t* __restrict__ vin,
                                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                                int N, int shift, const uint32_t* __restrict__ hist,
                                                                int nblocks, const DevSeg* __restrict__ segs, Arrays a) {
-  constexpr int W = kSortThreads / 32;
-  __shared__ uint32_t cnt[W][257];
-  __shared__ uint32_t goff[256];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int k = threadIdx.x; k < W * 257; k += kSortThreads) (&cnt[0][0])[k] = 0;
-  goff[threadIdx.x] = hist[threadIdx.x * nblocks + blockIdx.x];
-  __syncthreads();
-  uint32_t kk[kSortIPT], vv[kSortIPT], rk[kSortIPT];
-  const int base = blockIdx.x * kSortTile + w * 32 * kSortIPT;
-#pragma unroll
-  for (int r = 0; r < kSortIPT; ++r) {
-    int i = base + r * 32 + lane;
-    bool ok = i < N;
-    if (KEYS_FROM_STATE) {
-      kk[r] = ok ? cell_key_of<D>(segs, a, i) : 0u;
-      vv[r] = (uint32_t)i;
-    } else {
-      kk[r] = ok ? kin[i] : 0u;
-      vv[r] = ok ? vin[i] : 0u;
-    }
-    uint32_t dg = ok ? ((kk[r] >> shift) & 255u) : 256u;
-    uint32_t peers = __match_any_sync(kFull, dg);
-    uint32_t before = __popc(peers & ((1u << lane) - 1u));
-    rk[r] = cnt[w][dg] + before;
-    __syncwarp();
-    if (before == 0) cnt[w][dg] += __popc(peers);
-    __syncwarp();
-    rk[r] |= dg << 20;  // keep the digit beside the warp-local rank (rank < 256 per warp)
-  }
-  __syncthreads();
-  // exclusive prefix over warps for each digit (thread t handles digit t)
-  {
-    uint32_t run = 0;
-    for (int q = 0; q < W; ++q) {
-      uint32_t c = cnt[q][threadIdx.x];
-      cnt[q][threadIdx.x] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < kSortIPT; ++r) {
-    uint32_t dg = rk[r] >> 20;
-    if (dg < 256u) {
-      uint32_t pos = goff[dg] + cnt[w][dg] + (rk[r] & 0xfffffu);
-      kout[pos] = kk[r];
-      vout[pos] = vv[r];
-    }
-  }
+  __shared__ ScatterSmem sm;
+  sort_scatter_tile<D, KEYS_FROM_STATE>(blockIdx.x, kin, vin, kout, vout, N, shift, hist, nblocks, segs, a, sm);
 }
 
-
-// Gather the state into sorted order and re-fold positions into the primary box; thread k also
-// writes the CSR offsets of the cells in (key[k-1], key[k]] (off[c] = first index with key >= c)
-// and, when xb is set, the folded position (the reference of the displacement check).
-// The fold floor((x - lo) / L) is decided in FP64; in_primary_box() settles the common case
-// (0) without the FP64 division and gives the same result.
 template <int D>
 __global__ void k_permute(const DevSeg* __restrict__ segs, int N, const uint32_t* __restrict__ perm, Arrays in,
                           Arrays out, const uint32_t* __restrict__ keys, int C, int* __restrict__ off,
                           float4* __restrict__ xb) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k > N) return;
-  {
-    const int lo = (k == 0) ? 0 : (int)keys[k - 1] + 1;
-    const int hi = (k < N) ? (int)keys[k] : C;
-    for (int c = lo; c <= hi; ++c) off[c] = k;
-  }
-  if (k >= N) return;
-  int src = (int)perm[k];
-  uint2 m = in.meta[src];
-  const DevSeg& s = segs[m.y];
-  float4 a = in.A[src], b = in.B[src];
-  Cold c = load_cold<D>(in, src);
-  float xh[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-  for (int q = 0; q < D; ++q) {
-    double x = __dadd_rn((double)c.hi[q], (double)c.lo[q]);
-    double f = 0.0;
-    if (((s.periodic_mask >> q) & 1) && !in_primary_box(s, q, c.hi[q]))
-      f = floor(__ddiv_rn(__dsub_rn(x, s.lo_d[q]), s.L_d[q]));
-    double o = __dmul_rn(s.L_d[q], f);
-    c.off[q] = (float)o;
-    xh[q] = (float)__dsub_rn(x, o);
-  }
-  if (D == 2) {
-    out.A[k] = make_float4(xh[0], xh[1], a.z, a.w);
-    if (xb) xb[k] = make_float4(xh[0], xh[1], 0.f, 0.f);
-  } else {
-    out.A[k] = make_float4(xh[0], xh[1], xh[2], a.w);
-    out.C[k] = in.C[src];
-    if (xb) xb[k] = make_float4(xh[0], xh[1], xh[2], 0.f);
-  }
-  store_cold<D>(out, k, c);
-  out.B[k] = b;
-  out.meta[k] = m;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k <= N) permute_one<D>(k, segs, N, perm, in, out, keys, C, off, xb);
 }
 
 // ================================================================== state in/out
@@ -461,16 +313,7 @@ void launch_permute(const DevSeg* segs, int N, const uint32_t* perm, const Array
 template <int D>
 __global__ void k_copy_state(int N, Arrays src, Arrays dst) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  dst.A[k] = src.A[k];
-  dst.B[k] = src.B[k];
-  dst.X[k] = src.X[k];
-  dst.O[k] = src.O[k];
-  dst.meta[k] = src.meta[k];
-  if (D == 3) {
-    dst.C[k] = src.C[k];
-    dst.XL[k] = src.XL[k];
-  }
+  if (k < N) copy_state_one<D>(k, src, dst);
 }
 template <int D>
 void launch_copy_state(int N, const Arrays& src, const Arrays& dst, cudaStream_t st) {

@@ -20,8 +20,10 @@ struct TravArgs {
 struct RebuildCtl {
   int since;             // sweeps served by the current cell structure
   unsigned maxr;         // max over fluid of |x - x_build|^2 / (skin/2 - margin)^2 (float bits)
-  long long rebuilds;    // conditional rebuilds taken (cumulative)
-  long long call_rebuilds;  // conditional rebuilds since the host last zeroed it (one API call)
+  long long rebuilds;    // device-decided rebuilds taken (cumulative)
+  long long call_rebuilds;  // device-decided rebuilds since the host last zeroed it (one API call)
+  int flag;              // the next step rebuilds (set by the sweep's last CTA)
+  int pad;
 };
 
 // Displacement check written by the sweep's epilogue (all null: no check).
@@ -29,6 +31,8 @@ struct Displace {
   const float4* xb;      // folded positions at the last build (x, y[, z], 0)
   unsigned* maxr;        // running maximum (float bits, non-negative)
   float inv_r2;          // 1 / (skin/2 - margin)^2
+  RebuildCtl* ctl;       // set: the sweep's last CTA decides the next step's rebuild
+  int interval;          // rebuild_interval
 };
 
 // Outputs of the rate evaluation (original order, fluid only).

@@ -13,6 +13,7 @@
 
 #include "sph.h"
 #include "sph_runtime.h"
+#include "sph_rebuild.cuh"
 
 namespace sph {
 
@@ -331,6 +332,13 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
     dev_policy = skin > 0.f && half > 0.0;
     inv_r2 = dev_policy ? (float)(1.0 / (half * half)) : 0.f;
   }
+  // the decision is taken by the sweep and the rebuild is one cooperative launch when the
+  // device supports it; otherwise a one-thread kernel decides and a conditional graph node rebuilds
+  coop_grid = D == 2 ? rebuild_coop_grid<2>() : rebuild_coop_grid<3>();
+  int coop_attr = 0, dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, dev));
+  use_coop = dev_policy && coop_grid > 0 && coop_attr != 0;
   if (N > 16384 * 2048) einval("too many particles for the radix sort scratch (max 33554432)");
 }
 
@@ -364,6 +372,8 @@ void Scene::alloc_all() {
   d_pairs = (unsigned long long*)mem.get(sizeof(unsigned long long) * 2);
   d_ctl = (RebuildCtl*)mem.get(sizeof(RebuildCtl));
   CK(cudaMemsetAsync(d_ctl, 0, sizeof(RebuildCtl), st));
+  d_bar = (unsigned*)mem.get(sizeof(unsigned) * 2);
+  CK(cudaMemsetAsync(d_bar, 0, sizeof(unsigned) * 2, st));
   xbuild = (float4*)mem.get(sizeof(float4) * (size_t)N);
   d_nubar = (double*)mem.get(sizeof(double) * (size_t)(S + 1));
   CK(cudaMemsetAsync(d_status, 0, sizeof(int) * 4, st));
@@ -550,7 +560,8 @@ void Scene::passes_before_sweep(const TravArgs& t) {
 
 void Scene::sweep(const TravArgs& t, const Arrays& out) {
   prof_begin(0);
-  const Displace dp = dev_policy ? Displace{xbuild, &d_ctl->maxr, inv_r2} : Displace{nullptr, nullptr, 0.f};
+  const Displace dp = dev_policy ? Displace{xbuild, &d_ctl->maxr, inv_r2, use_coop ? d_ctl : nullptr, interval}
+                                 : Displace{nullptr, nullptr, 0.f, nullptr, 0};
   if (D == 2) {
     if (kern == 0) launch_sweep_t<2, 0>(t, tiles, d_ntiles, tiles_upper, out, dp, st);
     else launch_sweep_t<2, 1>(t, tiles, d_ntiles, tiles_upper, out, dp, st);
@@ -573,14 +584,20 @@ void Scene::host_rebuild() {
   cells_valid = true;
   steps_since_build = 0;
   if (!capturing) ++host_rebuilds;  // captured rebuilds are counted per graph launch
-  if (dev_policy) CK(cudaMemsetAsync(d_ctl, 0, 2 * sizeof(int), st));  // since = 0, maxr = 0
+  if (dev_policy) {  // since = 0, maxr = 0, no rebuild pending
+    CK(cudaMemsetAsync(d_ctl, 0, 2 * sizeof(int), st));
+    CK(cudaMemsetAsync(&d_ctl->flag, 0, sizeof(int), st));
+  }
 }
 
 // One forward step on the scene's own buffers.  Eager steps rebuild every time (the host does
 // not see the displacements); captured steps of a scene with a Verlet skin decide on the device.
 void Scene::step_once() {
   if (dev_policy && capturing && cells_valid) {
-    step_conditional();
+    if (use_coop)
+      step_coop();
+    else
+      step_conditional();
     return;
   }
   host_rebuild();
@@ -644,6 +661,47 @@ void Scene::step_conditional() {
   cudaGraph_t dummy;
   CK(cudaStreamEndCapture(st_body, &dummy));
   CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  prof_end();
+  keys_sorted = (passes % 2 == 0) ? kA : kB;
+  perm = (passes % 2 == 0) ? vA : vB;
+  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  passes_before_sweep(t);
+  sweep(t, buf[1 - cur]);
+  cur = 1 - cur;
+}
+
+// A captured step whose rebuild is one cooperative launch that returns at once unless the
+// previous sweep asked for a rebuild; when it rebuilds it sorts and permutes into the other
+// buffer and copies the result back, so the buffer parity does not depend on the decision.
+void Scene::step_coop() {
+  prof_begin(1);
+  RebuildArgs r{};
+  r.segs = dseg;
+  r.S = S;
+  r.N = N;
+  r.C = C_tot;
+  r.passes = passes;
+  r.nb = (N + 2047) / 2048;
+  r.in = buf[cur];
+  r.out = buf[1 - cur];
+  r.copy_back = 1;
+  r.kA = kA; r.vA = vA; r.kB = kB; r.vB = vB;
+  r.hist = scratch;
+  r.sums = scratch + (sort_scratch_words(N) - 2048 - 64);
+  r.off = cell_off;
+  r.xb = xbuild;
+  r.line_base = line_base;
+  r.n_lines = n_lines;
+  r.tiles = tiles;
+  r.ntiles = d_ntiles;
+  r.wall_list = any_walls ? wall_tiles : nullptr;
+  r.nwall = any_walls ? d_nwall : nullptr;
+  r.flag = &d_ctl->flag;
+  r.ctl = d_ctl;
+  r.bar = d_bar;
+  r.status = d_status;
+  CK(D == 2 ? launch_rebuild_coop<2>(r, coop_grid, st) : launch_rebuild_coop<3>(r, coop_grid, st));
+  ++launches;
   prof_end();
   keys_sorted = (passes % 2 == 0) ? kA : kB;
   perm = (passes % 2 == 0) ? vA : vB;
@@ -939,6 +997,10 @@ void Scene::check_status() {
   int h = 0;
   CK(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (h & 2) {
+    set_err("a grid barrier of the cooperative rebuild gave up waiting");
+    throw Fail{SPH_EINTERNAL};
+  }
   if (h & 1) {
     set_err("unstable state: non-finite values or density outside [0.5, 2] rho0");
     throw Fail{SPH_EUNSTABLE};

@@ -122,6 +122,9 @@ struct Scene {
   RebuildCtl* d_ctl = nullptr;
   float4* xbuild = nullptr;         // folded positions at the last build
   cudaStream_t st_body = nullptr;   // captures the rebuild body of a conditional node
+  bool use_coop = false;            // decide in the sweep, rebuild in one cooperative launch
+  int coop_grid = 0;
+  unsigned* d_bar = nullptr;        // grid barrier of the cooperative rebuild
   bool in_body = false;
   long long body_launches = 0;      // kernels in one conditional rebuild body
   // cumulative counters (since the scene was created)
@@ -177,6 +180,7 @@ struct Scene {
   void host_rebuild();
   void step_once();
   void step_conditional();
+  void step_coop();
   void advance_schedule();
   void steps(int n);
   void ensure_cells();

@@ -1,0 +1,126 @@
+// Device-side tile-table builders (one warp per cell line, one warp per tile for the wall
+// list), shared by the stand-alone kernels of sph_passes.cu and the single-launch rebuild.
+#pragma once
+#include "sph_tiles.cuh"
+
+namespace sph {
+
+// Tiles of one cell line are cut at cell boundaries, greedily from the left: a tile holds at
+// most TP particles and spans at most TP cells (so its column table fits); a cell with more
+// than TP particles is split into tiles of its own.  One warp per line: the lanes hold the
+// offsets of 32 consecutive cells, and each tile boundary is one ballot over them (the
+// conditions "count <= TP" and "span <= TP" are monotone along the line).  Finished tiles
+// wait in the registers of lane (k mod 32) and are written in batches of 32 at slots
+// reserved with one atomic; the order of the tiles in the table affects no result.
+__device__ __forceinline__ int seg_of_line(const int* __restrict__ line_base, int S, int l) {
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (line_base[mid] <= l) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Tiles of line l (one warp, all 32 lanes call it; lane = lane index).
+template <int D>
+__device__ __forceinline__ void tiles_line(int l, int lane, const DevSeg* __restrict__ segs, int S,
+                                           const int* __restrict__ line_base, const int* __restrict__ cell_off,
+                                           Tile* __restrict__ tiles, int* __restrict__ ntiles) {
+  constexpr int TP = TileCfg<D>::TP;
+  const int sg = seg_of_line(line_base, S, l);
+  const DevSeg& s = segs[sg];
+  const int ll = l - line_base[sg];
+  const int nx = s.n[0];
+  const int first = s.cell_base + ll * nx;
+  const int cy = ll % s.n[1], cz = ll / s.n[1];
+  Tile mine;  // the pending tile this lane holds
+  int pending = 0;
+  auto emit = [&](int p0, int p1, int c0, int c1) {  // warp-uniform arguments
+    if (lane == pending) {
+      mine.p0 = p0; mine.p1 = p1; mine.seg = sg; mine.line = l;
+      mine.cx0 = c0; mine.cx1 = c1; mine.cy = cy; mine.cz = cz;
+    }
+    if (++pending == 32) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(ntiles, 32);
+      base = __shfl_sync(kFull, base, 0);
+      tiles[base + lane] = mine;
+      pending = 0;
+    }
+  };
+  // open tile: first cell, first particle, last non-empty cell and its end offset
+  bool open = false;
+  int t_a = 0, t_p = 0, t_last = 0, t_end = 0;
+  auto window = [&](int w0, int o0, int o1) {
+    const int c = w0 + lane;
+    const bool in = c < nx;
+    const unsigned nonempty = __ballot_sync(kFull, in && o1 > o0);
+    const bool last_window = w0 + 32 >= nx;
+    int cur = 0;  // first lane not yet consumed
+    while (cur < 32) {
+      if (!open) {
+        const unsigned m = nonempty & (~0u << cur);
+        if (!m) break;
+        const int j = __ffs(m) - 1;
+        const int p0 = __shfl_sync(kFull, o0, j), p1 = __shfl_sync(kFull, o1, j);
+        if (p1 - p0 > TP) {  // an over-full cell: tiles of its own
+          for (int k = p0; k < p1; k += TP) emit(k, min(k + TP, p1), w0 + j, w0 + j);
+          cur = j + 1;
+          continue;
+        }
+        open = true;
+        t_a = w0 + j; t_p = p0; t_last = w0 + j; t_end = p1;
+        cur = j + 1;
+        continue;
+      }
+      // extend the open tile over lanes cur..hi
+      const bool ok = in && lane >= cur && o1 - t_p <= TP && c - t_a <= TP - 1;
+      const unsigned okm = __ballot_sync(kFull, ok);
+      const int hi = okm ? 31 - __clz(okm) : cur - 1;  // contiguous from cur
+      const unsigned ne = nonempty & okm;
+      if (ne) {
+        const int j = 31 - __clz(ne);
+        t_last = w0 + j;
+        t_end = __shfl_sync(kFull, o1, j);
+      }
+      if (hi == 31 && !last_window) break;  // the tile may continue in the next window
+      emit(t_p, t_end, t_a, t_last);
+      open = false;
+      cur = hi + 1;
+    }
+  };
+  // the offsets of the first kPre windows are loaded up front (one round trip for lines of up
+  // to 32 kPre cells); longer lines load the rest window by window
+  constexpr int kPre = 6;
+  int o0s[kPre], o1s[kPre];
+#pragma unroll
+  for (int w = 0; w < kPre; ++w) {
+    const int c = 32 * w + lane;
+    o0s[w] = c < nx ? cell_off[first + c] : 0;
+    o1s[w] = c < nx ? cell_off[first + c + 1] : 0;
+  }
+#pragma unroll
+  for (int w = 0; w < kPre; ++w)
+    if (32 * w < nx) window(32 * w, o0s[w], o1s[w]);
+  for (int w0 = 32 * kPre; w0 < nx; w0 += 32) {
+    const int c = w0 + lane;
+    window(w0, c < nx ? cell_off[first + c] : 0, c < nx ? cell_off[first + c + 1] : 0);
+  }
+  if (open) emit(t_p, t_end, t_a, t_last);
+  if (pending) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(ntiles, pending);
+    base = __shfl_sync(kFull, base, 0);
+    if (lane < pending) tiles[base + lane] = mine;
+  }
+}
+
+
+// True (all lanes) when tile w holds a wall particle; one warp.
+__device__ __forceinline__ bool tile_has_wall(const Tile& T, int lane, const uint2* __restrict__ meta) {
+  bool wall = false;
+  for (int k = T.p0 + lane; k < T.p1; k += 32) wall |= (meta[k].x & kWallBit) != 0;
+  return __any_sync(kFull, wall);
+}
+
+}  // namespace sph
