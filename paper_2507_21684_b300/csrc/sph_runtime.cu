@@ -673,8 +673,7 @@ void Scene::step_conditional() {
 // A captured step whose rebuild is one cooperative launch that returns at once unless the
 // previous sweep asked for a rebuild; when it rebuilds it sorts and permutes into the other
 // buffer and copies the result back, so the buffer parity does not depend on the decision.
-void Scene::step_coop() {
-  prof_begin(1);
+RebuildArgs Scene::coop_args(const Arrays& in, const Arrays& out, int* off, const int* flag, int copy_back) {
   RebuildArgs r{};
   r.segs = dseg;
   r.S = S;
@@ -682,13 +681,13 @@ void Scene::step_coop() {
   r.C = C_tot;
   r.passes = passes;
   r.nb = (N + 2047) / 2048;
-  r.in = buf[cur];
-  r.out = buf[1 - cur];
-  r.copy_back = 1;
+  r.in = in;
+  r.out = out;
+  r.copy_back = copy_back;
   r.kA = kA; r.vA = vA; r.kB = kB; r.vB = vB;
   r.hist = scratch;
   r.sums = scratch + (sort_scratch_words(N) - 2048 - 64);
-  r.off = cell_off;
+  r.off = off;
   r.xb = xbuild;
   r.line_base = line_base;
   r.n_lines = n_lines;
@@ -696,10 +695,16 @@ void Scene::step_coop() {
   r.ntiles = d_ntiles;
   r.wall_list = any_walls ? wall_tiles : nullptr;
   r.nwall = any_walls ? d_nwall : nullptr;
-  r.flag = &d_ctl->flag;
-  r.ctl = d_ctl;
+  r.flag = flag;
+  r.ctl = flag ? d_ctl : nullptr;
   r.bar = d_bar;
   r.status = d_status;
+  return r;
+}
+
+void Scene::step_coop() {
+  prof_begin(1);
+  const RebuildArgs r = coop_args(buf[cur], buf[1 - cur], cell_off, &d_ctl->flag, 1);
   CK(D == 2 ? launch_rebuild_coop<2>(r, coop_grid, st) : launch_rebuild_coop<3>(r, coop_grid, st));
   ++launches;
   prof_end();

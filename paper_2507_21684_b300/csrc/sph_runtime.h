@@ -8,6 +8,7 @@
 
 #include "sph.h"
 #include "sph_passes.cuh"
+#include "sph_rebuild.cuh"
 
 namespace sph {
 
@@ -181,6 +182,7 @@ struct Scene {
   void step_once();
   void step_conditional();
   void step_coop();
+  RebuildArgs coop_args(const Arrays& in, const Arrays& out, int* off, const int* flag, int copy_back);
   void advance_schedule();
   void steps(int n);
   void ensure_cells();
