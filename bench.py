@@ -318,7 +318,7 @@ def main():
                     help="--profile-run: launch kernels from the host (ncu cannot profile kernel nodes of graphs "
                          "with conditional nodes); the cells are then rebuilt every step")
     ap.add_argument("--skin", type=float, default=None,
-                    help="--profile-run: Verlet skin as a fraction of H (default: 0.1 dam break, 0 3D)")
+                    help="--profile-run: Verlet skin as a fraction of H (default: 0.02 dam break, 0 3D)")
     ap.add_argument("--stream-scenes", type=int, default=64, help="requests of the served mixed-size stream")
     ap.add_argument("--stream-rates", type=float, nargs="*", default=[20.0, 80.0, 320.0])
     args = ap.parse_args()
@@ -333,7 +333,7 @@ def main():
         sph.use_torch_allocator()
         from paper_2507_21684_b300 import tune
         sp = si.dam_break(res=128) if args.workload == "dambreak" else si.taylor_green_3d(128, seed=0)
-        skin = args.skin if args.skin is not None else (0.1 if args.workload == "dambreak" else 0.0)
+        skin = args.skin if args.skin is not None else (0.02 if args.workload == "dambreak" else 0.0)
         sp = dict(sp, params=tune.with_skin(sp, skin)["params"])
         r = run_forward(sph, torch, sp, args.steps, args.warmup, args.workload == "dambreak", torch.cuda.Stream(),
                         prof_steps=0, eager=args.eager)
