@@ -529,7 +529,9 @@ void Scene::build_tiles(const int* off, const uint2* meta) {
   }
 }
 
-void Scene::passes_before_sweep(const TravArgs& t) {
+void Scene::passes_before_sweep(const TravArgs& t_in) {
+  TravArgs t = t_in;
+  t.pair_count = nullptr;  // pair counts are those of the sweep (fluid targets) only
   if (any_walls) {
     prof_begin(2);
     if (D == 2) {
