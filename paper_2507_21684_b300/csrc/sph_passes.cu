@@ -99,26 +99,50 @@ __device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s
     fl[q] = a0 * a0;
     fh[q] = a1 * a1;
   }
+  // Each lane of the target's group sets up the candidate runs of one staged line (lane j: lines
+  // j, j + LANES, ...): [lo, hi) in staged order, mid = start of the right periodic image (the
+  // target takes off L in x from there on), and the line's y/z image bits.  The loop over lines
+  // then fetches each line's run with two shuffles instead of every lane redoing the setup.
+  constexpr int NL = Cfg::NL, LANES = Cfg::LANES;
+  constexpr int NSLOT = (NL + LANES - 1) / LANES;
+  static_assert(NSLOT <= 2, "a lane sets up at most two lines");
+  const unsigned gmask = (LANES == 32 ? 0xffffffffu : ((1u << LANES) - 1u)) << ((threadIdx.x & 31) & ~(LANES - 1));
+  unsigned runA[NSLOT], runB[NSLOT];
+#pragma unroll
+  for (int q = 0; q < NSLOT; ++q) {
+    const int l = lane + q * LANES;
+    unsigned A = 0u, B = 0u;  // empty run
+    if (l < NL && sm.linecell[l] >= 0) {
+      const int dy = (D == 2) ? l - 1 : l % 3 - 1;
+      const int dz = (D == 2) ? 0 : l / 3 - 1;
+      const float dyz = (dy < 0 ? fl[1] : dy > 0 ? fh[1] : 0.f) + (dz < 0 ? fl[2] : dz > 0 ? fh[2] : 0.f);
+      if (dyz < R2) {
+        const bool need_left = fl[0] + dyz < R2, need_right = fh[0] + dyz < R2;
+        constexpr int NCOL = TileSmem<D, E>::NCOL;
+        const int lo = sm.colstart[l * NCOL + (need_left ? ccol - 1 : ccol)];
+        const int hi = sm.colstart[l * NCOL + (need_right ? ccol + 2 : ccol + 1)];
+        const bool wrap_right = need_right && (sm.colbase + ccol + 1 >= s.n[0]);
+        const int mid = wrap_right ? sm.colstart[l * NCOL + ccol + 1] : hi;
+        const unsigned lbits = (sm.tshift[l][1] != 0.f ? 2u : 0u) | (D == 3 && sm.tshift[l][2] != 0.f ? 4u : 0u);
+        A = (unsigned)lo | ((unsigned)hi << 16);
+        B = (unsigned)mid | (lbits << 16);
+      }
+    }
+    runA[q] = A;
+    runB[q] = B;
+  }
 #pragma unroll 1
-  for (int l = 0; l < Cfg::NL; ++l) {
-    if (sm.linecell[l] < 0) continue;
-    const int dy = (D == 2) ? l - 1 : l % 3 - 1;
-    const int dz = (D == 2) ? 0 : l / 3 - 1;
-    const float dyz = (dy < 0 ? fl[1] : dy > 0 ? fh[1] : 0.f) + (dz < 0 ? fl[2] : dz > 0 ? fh[2] : 0.f);
-    if (dyz >= R2) continue;
-    const bool need_left = fl[0] + dyz < R2, need_right = fh[0] + dyz < R2;
-    constexpr int NCOL = TileSmem<D, E>::NCOL;
-    const int ncols = sm.ncols;
-    const int lo = sm.colstart[l * NCOL + (need_left ? ccol - 1 : ccol)];
-    const int endc = need_right ? ccol + 2 : ccol + 1;
-    const int hi = sm.colstart[l * NCOL + endc];
-    (void)ncols;
-    const bool wrap_right = need_right && (sm.colbase + ccol + 1 >= s.n[0]);
-    const int mid = wrap_right ? sm.colstart[l * NCOL + ccol + 1] : hi;
-    const unsigned lshift = (sm.tshift[l][1] != 0.f ? (1u << 14) : 0u) | (D == 3 && sm.tshift[l][2] != 0.f ? (1u << 15) : 0u);
+  for (int l = 0; l < NL; ++l) {
+    const int src = l % LANES;
+    const bool second = NSLOT > 1 && l >= LANES;
+    const unsigned A = __shfl_sync(gmask, second ? runA[NSLOT - 1] : runA[0], src, LANES);
+    const unsigned B = __shfl_sync(gmask, second ? runB[NSLOT - 1] : runB[0], src, LANES);
+    const int lo = (int)(A & 0xffffu), hi = (int)(A >> 16), mid = (int)(B & 0xffffu);
+    if (lo >= hi) continue;
+    const unsigned lshift = (B >> 16) << 13;
     float tx = xt0[0];
-    const float ty = xt0[1] - sm.tshift[l][1];
-    const float tz = (D == 3) ? xt0[2] - sm.tshift[l][2] : 0.f;
+    const float ty = (lshift & (1u << 14)) ? xt0[1] - s.L[1] : xt0[1];
+    const float tz = (D == 3) ? ((lshift & (1u << 15)) ? xt0[2] - s.L[2] : xt0[2]) : 0.f;
 #pragma unroll 1
     for (int part = 0; part < 2; ++part) {
       const int b = part == 0 ? lo : mid, en = part == 0 ? mid : hi;
