@@ -773,7 +773,7 @@ struct AdjPass {
 // ================================================================== kernels
 // The wall pass visits only the tiles that hold a wall particle (listed at each rebuild).
 template <int D, int KERN>
-__global__ void __launch_bounds__(256, 4) k_walls_t(TravArgs t, const Tile* tiles, const int* wall_tiles,
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_walls_t(TravArgs t, const Tile* tiles, const int* wall_tiles,
                                                  const int* n_wall_tiles) {
   WallPass<D, KERN> pass;
   pass.a = t.a;
@@ -788,13 +788,13 @@ __global__ void k_wall_tiles(const Tile* __restrict__ tiles, const int* __restri
   if (tile_has_wall(tiles[w], lane, meta) && lane == 0) list[atomicAdd(count, 1)] = w;
 }
 template <int D, int KERN>
-__global__ void __launch_bounds__(256, 4) k_density_t(TravArgs t, const Tile* tiles, const int* ntiles) {
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_density_t(TravArgs t, const Tile* tiles, const int* ntiles) {
   DensityPass<D, KERN> pass;
   pass.a = t.a;
   run_tiles<D, 0, 1>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
 template <int D, int KERN, bool INTEGRATE>
-__global__ void __launch_bounds__(256, 4) k_sweep_t(TravArgs t, const Tile* tiles, const int* ntiles, Arrays out,
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_sweep_t(TravArgs t, const Tile* tiles, const int* ntiles, Arrays out,
                                                  RateOut ro, Displace disp) {
   SweepPass<D, KERN, INTEGRATE> pass;
   pass.a = t.a;
@@ -805,7 +805,7 @@ __global__ void __launch_bounds__(256, 4) k_sweep_t(TravArgs t, const Tile* tile
   run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
 template <int D>
-__global__ void __launch_bounds__(256, 4) k_pairs_t(TravArgs t, const Tile* tiles, const int* ntiles, int32_t* pi,
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_pairs_t(TravArgs t, const Tile* tiles, const int* ntiles, int32_t* pi,
                                                  int32_t* pj, unsigned long long* count, long long cap) {
   PairPass<D> pass;
   pass.a = t.a;
@@ -816,7 +816,7 @@ __global__ void __launch_bounds__(256, 4) k_pairs_t(TravArgs t, const Tile* tile
   run_tiles<D, 0, 2>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
 template <int D, int KERN>
-__global__ void __launch_bounds__(256, 2) k_adj_t(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S,
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, 512 / TileCfg<D>::THREADS) k_adj_t(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S,
                                                const float* Pp, const float4* XBin, const float4* VBin, float4* XBout,
                                                float4* VBout, float* nu_part) {
   AdjPass<D, KERN> pass;
@@ -867,9 +867,9 @@ static int pass_grid(const void* fn, int tiles_upper) {
   long long g = (long long)g_num_sms * occ;
   return (int)std::max<long long>(1, std::min<long long>(g, tiles_upper));
 }
-static void set_occ(const void* fn, size_t smem) {
+static void set_occ(const void* fn, size_t smem, int threads) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 256, smem) == cudaSuccess) g_occ[fn] = n;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) == cudaSuccess) g_occ[fn] = n;
 }
 
 template <int D>
@@ -887,33 +887,33 @@ void launch_wall_tiles(const Tile* tiles, const int* ntiles, int tiles_upper, co
 template <int D, int KERN>
 void launch_walls_t(const TravArgs& t, const Tile* tiles, const int* wall_tiles, const int* n_wall_tiles,
                     int tiles_upper, cudaStream_t st) {
-  k_walls_t<D, KERN><<<pass_grid((const void*)k_walls_t<D, KERN>, tiles_upper), 256, pass_smem<D>(0), st>>>(
+  k_walls_t<D, KERN><<<pass_grid((const void*)k_walls_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(
       t, tiles, wall_tiles, n_wall_tiles);
 }
 template <int D, int KERN>
 void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st) {
-  k_density_t<D, KERN><<<pass_grid((const void*)k_density_t<D, KERN>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles);
+  k_density_t<D, KERN><<<pass_grid((const void*)k_density_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles);
 }
 template <int D, int KERN>
 void launch_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
                     const Displace& disp, cudaStream_t st) {
-  k_sweep_t<D, KERN, true><<<pass_grid((const void*)k_sweep_t<D, KERN, true>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, out, RateOut{}, disp);
+  k_sweep_t<D, KERN, true><<<pass_grid((const void*)k_sweep_t<D, KERN, true>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, out, RateOut{}, disp);
 }
 template <int D, int KERN>
 void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const RateOut& ro,
                     cudaStream_t st) {
-  k_sweep_t<D, KERN, false><<<pass_grid((const void*)k_sweep_t<D, KERN, false>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, Arrays{}, ro, Displace{});
+  k_sweep_t<D, KERN, false><<<pass_grid((const void*)k_sweep_t<D, KERN, false>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, Arrays{}, ro, Displace{});
 }
 template <int D>
 void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
                     unsigned long long* count, long long cap, cudaStream_t st) {
-  k_pairs_t<D><<<pass_grid((const void*)k_pairs_t<D>, tiles_upper), 256, pass_smem<D>(0), st>>>(t, tiles, ntiles, pi, pj, count, cap);
+  k_pairs_t<D><<<pass_grid((const void*)k_pairs_t<D>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, pi, pj, count, cap);
 }
 template <int D, int KERN>
 void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* S,
                   const float* Pp, const float4* XBin, const float4* VBin, float4* XBout, float4* VBout,
                   float* nu_part, cudaStream_t st) {
-  k_adj_t<D, KERN><<<pass_grid((const void*)k_adj_t<D, KERN>, tiles_upper), 256, pass_smem<D>(D == 2 ? 1 : 2), st>>>(
+  k_adj_t<D, KERN><<<pass_grid((const void*)k_adj_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(D == 2 ? 1 : 2), st>>>(
       t, tiles, ntiles, S, Pp, XBin, VBin, XBout, VBout, nu_part);
 }
 void launch_sum_segments(const float* part, const DevSeg* segs, int S, double* acc, cudaStream_t st) {
@@ -927,20 +927,20 @@ cudaError_t configure_passes() {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-#define SPH_ATTR(fn, bytes)                                                                                    \
+#define SPH_ATTR(DIM, fn, bytes)                                                                                  \
   if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
-  if (e == cudaSuccess) set_occ((const void*)fn, (bytes));
-  SPH_ATTR((k_walls_t<2, 0>), pass_smem<2>(0)) SPH_ATTR((k_walls_t<2, 1>), pass_smem<2>(0))
-  SPH_ATTR((k_walls_t<3, 0>), pass_smem<3>(0)) SPH_ATTR((k_walls_t<3, 1>), pass_smem<3>(0))
-  SPH_ATTR((k_density_t<2, 0>), pass_smem<2>(0)) SPH_ATTR((k_density_t<2, 1>), pass_smem<2>(0))
-  SPH_ATTR((k_density_t<3, 0>), pass_smem<3>(0)) SPH_ATTR((k_density_t<3, 1>), pass_smem<3>(0))
-  SPH_ATTR((k_sweep_t<2, 0, true>), pass_smem<2>(0)) SPH_ATTR((k_sweep_t<2, 1, true>), pass_smem<2>(0))
-  SPH_ATTR((k_sweep_t<3, 0, true>), pass_smem<3>(0)) SPH_ATTR((k_sweep_t<3, 1, true>), pass_smem<3>(0))
-  SPH_ATTR((k_sweep_t<2, 0, false>), pass_smem<2>(0)) SPH_ATTR((k_sweep_t<2, 1, false>), pass_smem<2>(0))
-  SPH_ATTR((k_sweep_t<3, 0, false>), pass_smem<3>(0)) SPH_ATTR((k_sweep_t<3, 1, false>), pass_smem<3>(0))
-  SPH_ATTR((k_pairs_t<2>), pass_smem<2>(0)) SPH_ATTR((k_pairs_t<3>), pass_smem<3>(0))
-  SPH_ATTR((k_adj_t<2, 0>), pass_smem<2>(1)) SPH_ATTR((k_adj_t<2, 1>), pass_smem<2>(1))
-  SPH_ATTR((k_adj_t<3, 0>), pass_smem<3>(2)) SPH_ATTR((k_adj_t<3, 1>), pass_smem<3>(2))
+  if (e == cudaSuccess) set_occ((const void*)fn, (bytes), TileCfg<DIM>::THREADS);
+  SPH_ATTR(2, (k_walls_t<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_walls_t<2, 1>), pass_smem<2>(0))
+  SPH_ATTR(3, (k_walls_t<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_walls_t<3, 1>), pass_smem<3>(0))
+  SPH_ATTR(2, (k_density_t<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_density_t<2, 1>), pass_smem<2>(0))
+  SPH_ATTR(3, (k_density_t<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_density_t<3, 1>), pass_smem<3>(0))
+  SPH_ATTR(2, (k_sweep_t<2, 0, true>), pass_smem<2>(0)) SPH_ATTR(2, (k_sweep_t<2, 1, true>), pass_smem<2>(0))
+  SPH_ATTR(3, (k_sweep_t<3, 0, true>), pass_smem<3>(0)) SPH_ATTR(3, (k_sweep_t<3, 1, true>), pass_smem<3>(0))
+  SPH_ATTR(2, (k_sweep_t<2, 0, false>), pass_smem<2>(0)) SPH_ATTR(2, (k_sweep_t<2, 1, false>), pass_smem<2>(0))
+  SPH_ATTR(3, (k_sweep_t<3, 0, false>), pass_smem<3>(0)) SPH_ATTR(3, (k_sweep_t<3, 1, false>), pass_smem<3>(0))
+  SPH_ATTR(2, (k_pairs_t<2>), pass_smem<2>(0)) SPH_ATTR(3, (k_pairs_t<3>), pass_smem<3>(0))
+  SPH_ATTR(2, (k_adj_t<2, 0>), pass_smem<2>(1)) SPH_ATTR(2, (k_adj_t<2, 1>), pass_smem<2>(1))
+  SPH_ATTR(3, (k_adj_t<3, 0>), pass_smem<3>(2)) SPH_ATTR(3, (k_adj_t<3, 1>), pass_smem<3>(2))
 #undef SPH_ATTR
   return e;
 }
