@@ -226,6 +226,7 @@ void Scene::leave() {
 Scene::~Scene() {
   if (st) cudaStreamSynchronize(st);
   for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : adj_graphs) cudaGraphExecDestroy(kv.second.first);
   for (auto g : graph_templates) cudaGraphDestroy(g);
   for (auto e : event_pool) cudaEventDestroy(e);
   for (auto& e : prof_events) {
@@ -477,7 +478,8 @@ void Scene::prof_end() {
 // permute `in` into `out` and write the cell offsets to off_out -> tile table.  Returns the
 // sorted keys and the permutation (in kA/kB, vA/vB unless copied to the given tape buffers).
 std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& out, uint32_t* keys_out,
-                                               uint32_t* perm_out, int* off_out) {
+                                               uint32_t* perm_out, int* off_out, Tile* tiles_out,
+                                               int* ntiles_out) {
   prof_begin(1);
   uint32_t *ki = kA, *vi = vA, *ko = kB, *vo = vB;
   uint32_t* hist = scratch;
@@ -506,7 +508,7 @@ std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& o
   else
     launch_permute<3>(dseg, N, pm, in, out, ks, C_tot, off_out, xbuild, st);
   CKL();
-  build_tiles(off_out, out.meta);
+  build_tiles(off_out, out.meta, tiles_out ? tiles_out : tiles, ntiles_out ? ntiles_out : d_ntiles);
   prof_end();
   const int scan_launches = 256 * ((N + 2047) / 2048) <= 16384 ? 1 : 3;
   launches += passes * (2 + scan_launches) + 1;
@@ -515,31 +517,35 @@ std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& o
 
 // Tile table of a cell structure (CSR offsets `off`), and the list of tiles holding wall
 // particles (from the sorted meta words) when the scene has walls.
-void Scene::build_tiles(const int* off, const uint2* meta) {
+void Scene::build_tiles(const int* off, const uint2* meta, Tile* tl, int* ntl) {
   if (D == 2)
-    launch_tiles<2>(dseg, S, line_base, n_lines, off, tiles, d_ntiles, st);
+    launch_tiles<2>(dseg, S, line_base, n_lines, off, tl, ntl, st);
   else
-    launch_tiles<3>(dseg, S, line_base, n_lines, off, tiles, d_ntiles, st);
+    launch_tiles<3>(dseg, S, line_base, n_lines, off, tl, ntl, st);
   CKL();
   ++launches;
   if (any_walls && meta) {
-    launch_wall_tiles(tiles, d_ntiles, tiles_upper, meta, wall_tiles, d_nwall, st);
+    launch_wall_tiles(tl, ntl, tiles_upper, meta, wall_tiles, d_nwall, st);
     CKL();
     ++launches;
   }
 }
 
-void Scene::passes_before_sweep(const TravArgs& t_in) {
+void Scene::passes_before_sweep(const TravArgs& t_in, const Tile* tl, const int* ntl) {
+  if (!tl) {
+    tl = tiles;
+    ntl = d_ntiles;
+  }
   TravArgs t = t_in;
   t.pair_count = nullptr;  // pair counts are those of the sweep (fluid targets) only
   if (any_walls) {
     prof_begin(2);
     if (D == 2) {
-      if (kern == 0) launch_walls_t<2, 0>(t, tiles, wall_tiles, d_nwall, tiles_upper, st);
-      else launch_walls_t<2, 1>(t, tiles, wall_tiles, d_nwall, tiles_upper, st);
+      if (kern == 0) launch_walls_t<2, 0>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
+      else launch_walls_t<2, 1>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
     } else {
-      if (kern == 0) launch_walls_t<3, 0>(t, tiles, wall_tiles, d_nwall, tiles_upper, st);
-      else launch_walls_t<3, 1>(t, tiles, wall_tiles, d_nwall, tiles_upper, st);
+      if (kern == 0) launch_walls_t<3, 0>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
+      else launch_walls_t<3, 1>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
     }
     CKL();
     prof_end();
@@ -548,11 +554,11 @@ void Scene::passes_before_sweep(const TravArgs& t_in) {
   if (summation) {
     prof_begin(3);
     if (D == 2) {
-      if (kern == 0) launch_density_t<2, 0>(t, tiles, d_ntiles, tiles_upper, st);
-      else launch_density_t<2, 1>(t, tiles, d_ntiles, tiles_upper, st);
+      if (kern == 0) launch_density_t<2, 0>(t, tl, ntl, tiles_upper, st);
+      else launch_density_t<2, 1>(t, tl, ntl, tiles_upper, st);
     } else {
-      if (kern == 0) launch_density_t<3, 0>(t, tiles, d_ntiles, tiles_upper, st);
-      else launch_density_t<3, 1>(t, tiles, d_ntiles, tiles_upper, st);
+      if (kern == 0) launch_density_t<3, 0>(t, tl, ntl, tiles_upper, st);
+      else launch_density_t<3, 1>(t, tl, ntl, tiles_upper, st);
     }
     CKL();
     prof_end();
@@ -560,16 +566,20 @@ void Scene::passes_before_sweep(const TravArgs& t_in) {
   }
 }
 
-void Scene::sweep(const TravArgs& t, const Arrays& out) {
+void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const int* ntl) {
+  if (!tl) {
+    tl = tiles;
+    ntl = d_ntiles;
+  }
   prof_begin(0);
   const Displace dp = dev_policy ? Displace{xbuild, &d_ctl->maxr, inv_r2, use_coop ? d_ctl : nullptr, interval}
                                  : Displace{nullptr, nullptr, 0.f, nullptr, 0};
   if (D == 2) {
-    if (kern == 0) launch_sweep_t<2, 0>(t, tiles, d_ntiles, tiles_upper, out, dp, st);
-    else launch_sweep_t<2, 1>(t, tiles, d_ntiles, tiles_upper, out, dp, st);
+    if (kern == 0) launch_sweep_t<2, 0>(t, tl, ntl, tiles_upper, out, dp, st);
+    else launch_sweep_t<2, 1>(t, tl, ntl, tiles_upper, out, dp, st);
   } else {
-    if (kern == 0) launch_sweep_t<3, 0>(t, tiles, d_ntiles, tiles_upper, out, dp, st);
-    else launch_sweep_t<3, 1>(t, tiles, d_ntiles, tiles_upper, out, dp, st);
+    if (kern == 0) launch_sweep_t<3, 0>(t, tl, ntl, tiles_upper, out, dp, st);
+    else launch_sweep_t<3, 1>(t, tl, ntl, tiles_upper, out, dp, st);
   }
   CKL();
   prof_end();
@@ -838,18 +848,16 @@ void Scene::rollout(int n, int k) {
       ckpts.push_back(a);
     }
   }
-  CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st));
-  launches = 0;
-  for (int s = 0; s < n; ++s) {
-    if (s % k == 0) {
-      copy_arrays(ckpts[s / k], buf[cur]);
-      cells_valid = false;  // each segment starts with a rebuild (replayed identically)
-    }
-    step_once();
+  // segment by segment: checkpoint, then the segment's steps exactly as sph_step runs them
+  // (graph chunks, the same rebuild schedule), starting from a fresh build like the replay
+  long long seg_launches = 0;
+  for (int s0 = 0; s0 < n; s0 += k) {
+    copy_arrays(ckpts[s0 / k], buf[cur]);
+    cells_valid = false;
+    steps(std::min(k, n - s0));
+    seg_launches += launches;
   }
-  last_steps = n;
-  steps_total += n;
-  launches_total += launches;
+  launches = seg_launches;  // (pair counts: those of the last segment's steps)
   tape_valid = true;
 }
 
@@ -861,6 +869,8 @@ void Scene::alloc_tape(int k) {
     t.keys = (uint32_t*)mem.get(4 * (size_t)N);
     t.perm = (uint32_t*)mem.get(4 * (size_t)N);
     t.off = (int*)mem.get(sizeof(int) * ((size_t)C_tot + 1));
+    t.tiles = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
+    t.ntiles = (int*)mem.get(sizeof(int) * 2);
     tape.push_back(t);
   }
   if (!adj_alloc) {
@@ -872,9 +882,60 @@ void Scene::alloc_tape(int k) {
     Pp = (float*)mem.get(sizeof(float) * N);
     nu_part = (float*)mem.get(sizeof(float) * (size_t)N);
     alloc_arrays(scratch_arr);
+    alloc_arrays(ckpt_work);
     adj_alloc = true;
   }
   tape_cap = k;
+}
+
+// Replay one segment forward from ckpt_work (keeping each step's sweep input, keys, permutation
+// and cell offsets in the tape), then run its adjoint steps backwards.  The adjoint state stays
+// in XB[0]/VB[0] at the segment's end (each backward step swaps the buffers twice).
+void Scene::adjoint_segment(int L) {
+  int q = 0;
+  // replay the segment forward, keeping the sweep input of every step; every replayed step
+  // rebuilds (the forward's displacement checks are not replayed)
+  const Arrays* prev = &ckpt_work;
+  for (int s = 0; s < L; ++s) {
+    TapeSlot& slot = tape[s];
+    rebuild(*prev, slot.a, slot.keys, slot.perm, slot.off, slot.tiles, slot.ntiles);  // kept in the slot
+    TravArgs t = trav(slot.a, slot.keys, slot.off);
+    passes_before_sweep(t, slot.tiles, slot.ntiles);
+    sweep(t, scratch_arr, slot.tiles, slot.ntiles);
+    prev = &scratch_arr;
+  }
+  // backward through the segment
+  for (int s = L - 1; s >= 0; --s) {
+    TapeSlot& slot = tape[s];
+    if (D == 2)
+      launch_adj_seed<2>(dseg, N, slot.a, XB[q], VB[q], Sd, Pp, st);
+    else
+      launch_adj_seed<3>(dseg, N, slot.a, XB[q], VB[q], Sd, Pp, st);
+    CKL();
+    TravArgs t = trav(slot.a, slot.keys, slot.off);
+    t.pair_count = nullptr;
+    prof_begin(4);
+    if (D == 2) {
+      if (kern == 0)
+        launch_adj_t<2, 0>(t, slot.tiles, slot.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+      else
+        launch_adj_t<2, 1>(t, slot.tiles, slot.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+    } else {
+      if (kern == 0)
+        launch_adj_t<3, 0>(t, slot.tiles, slot.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+      else
+        launch_adj_t<3, 1>(t, slot.tiles, slot.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+    }
+    CKL();
+    prof_end();
+    launch_sum_segments(nu_part, dseg, S, d_nubar, st);
+    CKL();
+    q = 1 - q;
+    launch_adj_unpermute(N, slot.perm, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
+    CKL();
+    q = 1 - q;
+    launches += 4;  // seed, adjoint sweep, segment sums, un-permute
+  }
 }
 
 void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb0, float* vb0, float* rb0, double* nub,
@@ -904,50 +965,41 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
   for (int sgi = ncp - 1; sgi >= 0; --sgi) {
     const int t0 = sgi * k, t1 = std::min(n, t0 + k);
     const int L = t1 - t0;
-    // replay the segment forward, keeping the sweep input of every step; every replayed step
-    // rebuilds (the forward's displacement checks are not replayed)
-    const Arrays* prev = &ckpts[sgi];
-    for (int s = 0; s < L; ++s) {
-      TapeSlot& slot = tape[s];
-      rebuild(*prev, slot.a, slot.keys, slot.perm, slot.off);  // keys/perm copied into the slot
-      TravArgs t = trav(slot.a, slot.keys, slot.off);
-      passes_before_sweep(t);
-      sweep(t, scratch_arr);
-      prev = &scratch_arr;
+    // the segment starts from a working copy of its checkpoint, so that one captured graph per
+    // segment length serves every segment
+    if (D == 2)
+      launch_copy_state<2>(N, ckpts[sgi], ckpt_work, st);
+    else
+      launch_copy_state<3>(N, ckpts[sgi], ckpt_work, st);
+    CKL();
+    ++launches;
+    if (!use_graphs || profiling) {
+      adjoint_segment(L);
+      continue;
     }
-    // backward through the segment
-    for (int s = L - 1; s >= 0; --s) {
-      TapeSlot& slot = tape[s];
-      if (D == 2)
-        launch_adj_seed<2>(dseg, N, slot.a, XB[q], VB[q], Sd, Pp, st);
-      else
-        launch_adj_seed<3>(dseg, N, slot.a, XB[q], VB[q], Sd, Pp, st);
-      CKL();
-      TravArgs t = trav(slot.a, slot.keys, slot.off);
-      t.pair_count = nullptr;
-      build_tiles(slot.off, nullptr);
-      prof_begin(4);
-      if (D == 2) {
-        if (kern == 0)
-          launch_adj_t<2, 0>(t, tiles, d_ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
-        else
-          launch_adj_t<2, 1>(t, tiles, d_ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
-      } else {
-        if (kern == 0)
-          launch_adj_t<3, 0>(t, tiles, d_ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
-        else
-          launch_adj_t<3, 1>(t, tiles, d_ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+    auto it = adj_graphs.find(L);
+    if (it == adj_graphs.end()) {
+      const long long l0 = launches;
+      cudaGraph_t g;
+      capturing = true;
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      try {
+        adjoint_segment(L);
+      } catch (...) {
+        cudaStreamEndCapture(st, &g);
+        capturing = false;
+        throw;
       }
-      CKL();
-      prof_end();
-      launch_sum_segments(nu_part, dseg, S, d_nubar, st);
-      CKL();
-      q = 1 - q;
-      launch_adj_unpermute(N, slot.perm, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
-      CKL();
-      q = 1 - q;
-      launches += 4;  // seed, adjoint sweep, segment sums, un-permute
+      CK(cudaStreamEndCapture(st, &g));
+      capturing = false;
+      cudaGraphExec_t ge;
+      CK(cudaGraphInstantiate(&ge, g, 0));
+      cudaGraphDestroy(g);
+      it = adj_graphs.emplace(L, std::make_pair(ge, launches - l0)).first;
+    } else {
+      launches += it->second.second;
     }
+    CK(cudaGraphLaunch(it->second.first, st));
   }
   // XB[q] is in the storage order of checkpoint 0; deliver in original order
   float* oxb = xb0;

@@ -63,6 +63,8 @@ struct TapeSlot {
   uint32_t* keys;      // sorted cell keys in effect
   uint32_t* perm;      // permutation applied at that step's rebuild (if any)
   int* off;            // cell offsets in effect
+  Tile* tiles;         // tile table of that cell structure, and its count
+  int* ntiles;
 };
 
 struct GraphKey {
@@ -158,6 +160,8 @@ struct Scene {
   float* Pp = nullptr;
   float* nu_part = nullptr;
   Arrays scratch_arr{};
+  Arrays ckpt_work{};               // the segment's checkpoint, copied (graphs do not depend on it)
+  std::map<int, std::pair<cudaGraphExec_t, long long>> adj_graphs;  // by segment length
 
   ~Scene();
   void bind_stream(cudaStream_t user);
@@ -174,10 +178,11 @@ struct Scene {
   void prof_begin(int cls);
   void prof_end();
   std::pair<uint32_t*, uint32_t*> rebuild(const Arrays& in, const Arrays& out, uint32_t* keys_out,
-                                          uint32_t* perm_out, int* off_out);
-  void build_tiles(const int* off, const uint2* meta);
-  void passes_before_sweep(const TravArgs& t);
-  void sweep(const TravArgs& t, const Arrays& out);
+                                          uint32_t* perm_out, int* off_out, Tile* tiles_out = nullptr,
+                                          int* ntiles_out = nullptr);
+  void build_tiles(const int* off, const uint2* meta, Tile* tl, int* ntl);
+  void passes_before_sweep(const TravArgs& t, const Tile* tl = nullptr, const int* ntl = nullptr);
+  void sweep(const TravArgs& t, const Arrays& out, const Tile* tl = nullptr, const int* ntl = nullptr);
   void host_rebuild();
   void step_once();
   void step_conditional();
@@ -188,6 +193,7 @@ struct Scene {
   void ensure_cells();
   void rollout(int n, int k);
   void alloc_tape(int k);
+  void adjoint_segment(int L);
   void adjoint(const float* xb, const float* vb, const float* rb, float* xb0, float* vb0, float* rb0, double* nub,
                int is_dev);
   void get_state(float* x, float* v, float* rho, int is_dev);

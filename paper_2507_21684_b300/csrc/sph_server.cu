@@ -32,13 +32,17 @@ static double now_s() {
 }
 
 // Device bytes one admitted request may hold (state buffers, sort and tile scratch, adjoint tape).
+// Upper bound of the device bytes a request's scene uses (admission): per particle, the two
+// state buffers, sort keys and values, cell offsets, tiles, staging and the build positions;
+// an adjoint adds its checkpoints, the tape slots (state, keys, permutation, offsets, tiles)
+// and the adjoint work arrays.
 static size_t request_bytes(const sph_params& p, int n, int steps, int mode, int ckpt) {
-  const size_t per = p.dim == 2 ? 200 : 280;
+  const size_t per = p.dim == 2 ? 256 : 320;
   size_t b = (size_t)n * per + (1 << 20);
   if (mode == SPH_REQ_ADJOINT) {
-    const size_t rec = p.dim == 2 ? 56 : 88;
+    const size_t rec = p.dim == 2 ? 72 : 96;  // one copy of the records
     const int k = std::max(ckpt, 1);
-    b += (size_t)((steps + k - 1) / k) * n * rec + (size_t)(k + 1) * n * (rec + 8) + (size_t)n * 96;
+    b += (size_t)((steps + k - 1) / k) * n * rec + (size_t)(k + 1) * n * (rec + 16) + (size_t)n * (2 * rec + 64);
   }
   return b;
 }

@@ -27,7 +27,7 @@ import numpy as np
 __all__ = [
     "splitmix64", "uniform24", "normal01",
     "taylor_green_2d", "taylor_green_3d", "dam_break", "perturbed_velocity",
-    "served_stream", "SceneSpec", "scene_bytes_estimate",
+    "served_stream", "SceneSpec",
     "KERNEL_WENDLAND4", "KERNEL_WENDLAND2", "DENSITY_CONTINUITY", "DENSITY_SUMMATION",
 ]
 
@@ -270,14 +270,3 @@ def served_stream(n_scenes: int = 512, rate_hz: float = 80.0, seed: int = 0, n_m
     t = np.cumsum(gaps) - gaps[0]
     return [SceneSpec(int(i), int(n_side[i]), int(steps[i]), bool(adj[i]), float(t[i]), seed=int(i))
             for i in range(n_scenes)]
-
-
-def scene_bytes_estimate(n: int, dim: int = 2, steps: int = 0, adjoint: bool = False,
-                         ckpt_every: int = 20) -> int:
-    """Upper bound of the device bytes one resident scene needs (used for admission)."""
-    per = 160 if dim == 2 else 200
-    b = n * per + (1 << 16)
-    if adjoint:
-        n_ck = (steps + ckpt_every - 1) // max(ckpt_every, 1)
-        b += n_ck * n * 48 + ckpt_every * n * 64 + n * 96
-    return int(b)
