@@ -65,6 +65,31 @@ def stored_traffic(profile: str):
     return int(tb.group(1))
 
 
+def replica_reduce(t_local: float, units_local: float, device: str = "cpu"):
+    """Whole-job figures of replicas: the slowest rank's time and the units of all ranks
+    (identity for a single process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_local, units_local
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.barrier()
+    return float(t.item()), float(u.item())
+
+
+def replica_choice(value):
+    """Rank 0's value on every rank (one configuration for all replicas)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    box = [value]
+    dist.broadcast_object_list(box, src=0)
+    return box[0]
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -377,8 +402,9 @@ def main():
     # skin; every candidate finds the same neighbours each step)
     from paper_2507_21684_b300 import tune
     tuned = tune.tune_skin(spec, skins=(0.0, 0.02, 0.05, 0.1, 0.2), steps=100, warmup=100)
-    spec = dict(spec, params=tuned["params"])
-    workload = dict(workload, verlet_skin_over_H=tuned["best"]["skin_over_H"],
+    best_skin = replica_choice(tuned["best"]["skin_over_H"])
+    spec = dict(spec, params=tune.with_skin(spec, best_skin)["params"])
+    workload = dict(workload, verlet_skin_over_H=best_skin,
                     rebuild="on the device when a particle has moved skin/2 since the last build")
 
     clk = Clocks(torch.cuda.current_device())
@@ -389,13 +415,8 @@ def main():
     fw = run_forward(sph, torch, spec, args.steps, args.warmup, True, stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    t_total = sum(fw["ms"]) / 1e3
-    if ws > 1:
-        t = torch.tensor([t_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
-        torch.distributed.barrier()
-    pairs_total = fw["pairs_per_step"] * args.steps * ws
+    t_total, pairs_total = replica_reduce(sum(fw["ms"]) / 1e3, float(fw["pairs_per_step"] * args.steps),
+                                          device="cuda")
     value = pairs_total / t_total
     sweep_flops = FLOPS_PER_PAIR[2] * fw["pairs_per_step"]
     achieved = sweep_flops / (fw["sweep_ms"] / 1e3) / 1e12
