@@ -268,6 +268,7 @@ struct Server {
         for (float c : r->x) m = std::max(m, (double)std::fabs(c));
         sc.setup_checked({r->p}, {r->nf}, {r->nw}, {m});
         sc.bind_stream(st_adj);
+        sc.use_graphs = false;  // a one-off scene: capturing graphs would cost more than it saves
         sc.alloc_all();
         sc.upload(0, r->x.data(), r->v.data(), r->rho.data(), r->mass.data(), 0);
         sc.rollout(r->n_steps, r->ckpt);
