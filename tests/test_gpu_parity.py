@@ -291,6 +291,31 @@ def test_adjoint_matches_oracle_and_fd(sph, orc):
     assert abs(gnu - fd_nu) < 1e-3 * abs(fd_nu)
 
 
+def test_autograd_function_matches_adjoint(sph):
+    """rollout_fn (torch.autograd.Function: forward sph_rollout, backward sph_adjoint) gives the
+    gradients of the direct adjoint call, for a loss on the final positions."""
+    import torch
+    s = si.adjoint_problem(16, steps=40)
+    N = s["n_fluid"]
+    tgt = torch.from_numpy(s["x"]).cuda() + 0.01
+    f = sph.rollout_fn()
+    x0 = torch.from_numpy(s["x"]).cuda()
+    v0 = torch.from_numpy(s["v"]).cuda().requires_grad_(True)
+    r0 = torch.from_numpy(s["rho"]).cuda()
+    nu = torch.tensor(s["params"]["nu"], device="cuda", requires_grad=True)
+    m = torch.from_numpy(s["mass"]).cuda()
+    xT, vT, rT = f.apply(x0, v0, r0, nu, m, s["params"], 40, 10)
+    loss = ((xT - tgt) ** 2).sum() / N
+    loss.backward()
+    with make(sph, s) as sc:
+        sc.rollout(40, 10)
+        x, _, _ = sc.get_state()
+        seed = (2.0 * (x.astype(np.float64) - tgt.cpu().numpy()) / N).astype(np.float32)
+        gx, gv, gr, gnu = sc.adjoint(seed, np.zeros_like(seed), np.zeros(N, np.float32))
+    np.testing.assert_allclose(v0.grad.cpu().numpy(), gv, rtol=1e-5, atol=1e-9)
+    assert abs(float(nu.grad) - gnu) <= 1e-5 * abs(gnu)
+
+
 def test_checkpoint_recompute_is_bitwise_store_all(sph):
     s = si.taylor_green_2d(16, seed=1)
     N = s["n_fluid"]
