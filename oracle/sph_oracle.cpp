@@ -46,6 +46,7 @@ struct OrcParams {
   double g[3];
   int32_t rebuild_interval;
   double skin;
+  int32_t diffusion;  // 0: Molteni-Colagrossi psi_ij, 1: renormalised (Antuono) psi_ij
 };
 }
 
@@ -366,18 +367,148 @@ void wall_extrapolation(const OrcParams& P, State<T>& S, const Pairs& pr, std::v
   for (int w = 0; w < S.nw; ++w) S.rho[S.nf + w] = T(tait_inverse(P, p_wall[w]));
 }
 
+// values of a state (the renormalised gradient is evaluated on plain doubles; its mode has no
+// derivative pass)
+inline const State<double>& plain(const State<double>& S) { return S; }
+template <class T>
+State<double> plain(const State<T>& S) {
+  State<double> R;
+  R.nf = S.nf; R.nw = S.nw; R.d = S.d; R.m = S.m;
+  for (const T& e : S.x) R.x.push_back(val(e));
+  for (const T& e : S.v) R.v.push_back(val(e));
+  for (const T& e : S.rho) R.rho.push_back(val(e));
+  for (const T& e : S.nu) R.nu.push_back(val(e));
+  return R;
+}
+
+// the renormalised diffusion is active (it belongs to the continuity form of the density)
+inline bool renormalised(const OrcParams& P) { return P.diffusion == 1 && P.density_mode == 0; }
+
+// ---------------------------------------------------------------- kernel renormalisation
+// Renormalised density gradient of the full delta-SPH diffusion (the paper's "Kernel
+// renormalization" paragraph, after Marrone et al. 2011):
+//   M_i = sum_j V_j (x_j - x_i) (x) grad_i W_ij ,   L_i = pinv(M_i)
+//   <grad rho>_i^L = sum_j V_j (rho_j - rho_i) L_i grad_i W_ij
+// over every neighbour j (fluid and wall), V_j = m_j / rho_j, for every particle i (fluid and
+// wall: the diffusion term of a fluid particle uses the gradients of both ends of each pair).
+// The paper inverts M_i by a pseudo-inverse and states no cut-off; this one drops the
+// eigen-directions with |lambda| <= kPinvRtol * max|lambda|.
+constexpr double kPinvRtol = 1e-3;
+
+// A = Q diag(lam) Q^T for a symmetric d x d matrix by cyclic Jacobi rotations (the textbook
+// method, Golub & Van Loan, "Matrix Computations", Sec. 8.5).  Columns of Q are eigenvectors.
+void sym_eigen(int d, double A[3][3], double lam[3], double Q[3][3]) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Q[a][b] = a == b ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = 0.0, all = 0.0;
+    for (int p = 0; p < d; ++p)
+      for (int q = 0; q < d; ++q) {
+        all += A[p][q] * A[p][q];
+        if (p != q) off += A[p][q] * A[p][q];
+      }
+    if (off <= 1e-36 * all) break;
+    for (int p = 0; p < d; ++p)
+      for (int q = p + 1; q < d; ++q) {
+        if (A[p][q] == 0.0) continue;
+        // rotation J in the (p, q) plane with (J^T A J)_pq = 0: t = tan(theta) is the smaller
+        // root of t^2 + 2 tau t - 1 = 0, tau = (A_qq - A_pp) / (2 A_pq)
+        double tau = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+        double t = (tau >= 0.0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < d; ++k) {  // A <- A J
+          double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < d; ++k) {  // A <- J^T A
+          double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < d; ++k) {  // Q <- Q J
+          double qkp = Q[k][p], qkq = Q[k][q];
+          Q[k][p] = c * qkp - s * qkq;
+          Q[k][q] = s * qkp + c * qkq;
+        }
+      }
+  }
+  for (int k = 0; k < d; ++k) lam[k] = A[k][k];
+}
+
+// Moore-Penrose pseudo-inverse of M_i.  M_i is symmetric (grad_i W_ij is parallel to
+// x_i - x_j), so it follows from the eigen-decomposition; the average (M + M^T)/2 only removes
+// the rounding of the products.
+void sym_pinv(int d, const double M[3][3], double L[3][3]) {
+  double A[3][3] = {{0.0}}, Q[3][3], lam[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) A[a][b] = 0.5 * (M[a][b] + M[b][a]);
+  sym_eigen(d, A, lam, Q);
+  double lmax = 0.0;
+  for (int k = 0; k < d; ++k) lmax = std::max(lmax, std::fabs(lam[k]));
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) L[a][b] = 0.0;
+  for (int k = 0; k < d; ++k) {
+    if (!(std::fabs(lam[k]) > kPinvRtol * lmax)) continue;
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) L[a][b] += Q[a][k] * Q[b][k] / lam[k];
+  }
+}
+
+// <grad rho>^L of the particles in `who` (neighbour lists `pr` aligned with `who`), written to
+// grad[i * d + k]; M_out (optional) receives M_i as 9 row-major entries per listed particle.
+void renorm_gradient(const OrcParams& P, const State<double>& S, const Pairs& pr, const std::vector<int>& who,
+                     std::vector<double>& grad, double* M_out = nullptr) {
+  const int d = S.d;
+  grad.assign((size_t)S.N() * d, 0.0);
+#pragma omp parallel for schedule(static)
+  for (int a = 0; a < (int)who.size(); ++a) {
+    const int i = who[a];
+    double M[3][3] = {{0.0}}, L[3][3];
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1) sym_pinv(d, M, L);
+      for (int64_t t = pr.off[a]; t < pr.off[a + 1]; ++t) {
+        const int j = pr.nb[t];
+        double r[3] = {0.0, 0.0, 0.0}, G[3];
+        for (int k = 0; k < d; ++k) r[k] = min_image(P, k, S.x[(size_t)i * d + k] - S.x[(size_t)j * d + k]);
+        kernel_gradW<double>(P, r, G);
+        const double Vj = S.m[j] / S.rho[j];
+        if (pass == 0) {  // (x_j - x_i) (x) grad_i W_ij
+          for (int p = 0; p < d; ++p)
+            for (int q = 0; q < d; ++q) M[p][q] += Vj * (-r[p]) * G[q];
+        } else {  // (rho_j - rho_i) L_i grad_i W_ij
+          for (int p = 0; p < d; ++p) {
+            double LG = 0.0;
+            for (int q = 0; q < d; ++q) LG += L[p][q] * G[q];
+            grad[(size_t)i * d + p] += Vj * (S.rho[j] - S.rho[i]) * LG;
+          }
+        }
+      }
+    }
+    if (M_out)
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) M_out[(size_t)a * 9 + p * 3 + q] = M[p][q];
+  }
+}
+
 // Rates of the fluid particles (Sec. 2.3, delta-SPH):
 //   drho_i/dt = -rho_i sum_j V_j (v_j - v_i) . gradW_ij + delta h c0 sum_j V_j psi_ij . gradW_ij
-//   psi_ij    = 2 (rho_j - rho_i) (x_j - x_i) / (|x_ij|^2 + eps h^2)
+//   psi_ij    = 2 (rho_j - rho_i) (x_j - x_i) / (|x_ij|^2 + eps h^2)                (diffusion 0)
+//   psi_ij    = 2 [(rho_j - rho_i) - (<grad rho>_i^L + <grad rho>_j^L) . (x_j - x_i) / 2]
+//               (x_j - x_i) / (|x_ij|^2 + eps h^2)                                   (diffusion 1)
 //   dv_i/dt   = -(1/rho_i) sum_j V_j (p_i + p_j) gradW_ij
 //               + 2(d+2) nu (rho0/rho_i) sum_j V_j pi_ij gradW_ij + g
 //   pi_ij     = (v_i - v_j) . (x_i - x_j) / (|x_ij|^2 + eps h^2),   V_j = m_j / rho_j
 // h = H/2 is the smoothing length of the delta-SPH literature the scheme is cited from (the
 // paper's "common choice H/h = 2, h = 2 dx", App. A.1); H is the kernel support.
-// With a summation density the diffusion term is off (rho is not integrated).
+// With a summation density the diffusion term is off (rho is not integrated).  Diffusion 1 is the
+// renormalised form of Antuono et al. (the delta-SPH model the paper cites): the first-order part
+// of the density difference is removed with the renormalised gradients `grad` (N * d), so the term
+// vanishes for a linear density field.
 template <class T>
 void rates(const OrcParams& P, const State<T>& S, const Pairs& pr, const std::vector<double>& p_wall,
-           std::vector<T>& a, std::vector<T>& drho, const std::vector<int>* who = nullptr) {
+           std::vector<T>& a, std::vector<T>& drho, const std::vector<int>* who = nullptr,
+           const std::vector<double>* grad = nullptr) {
   const int d = S.d;
   const int M = who ? (int)who->size() : S.nf;
   a.assign((size_t)M * d, T(0.0));
@@ -411,11 +542,18 @@ void rates(const OrcParams& P, const State<T>& S, const Pairs& pr, const std::ve
       T pi_ij = uv / den;
       T pp = p_i + pres(j);
       T cont = T(0.0), diff = T(0.0);
+      T drho_ji = S.rho[j] - rho_i;
+      if (grad) {  // (<grad rho>_i^L + <grad rho>_j^L) . (x_j - x_i) / 2, x_j - x_i = -r
+        T corr = T(0.0);
+        for (int k = 0; k < d; ++k)
+          corr += T((*grad)[(size_t)i * d + k] + (*grad)[(size_t)j * d + k]) * (-r[k]);
+        drho_ji = drho_ji - T(0.5) * corr;
+      }
       for (int k = 0; k < d; ++k) {
         sum_p[k] += Vj * pp * G[k];
         sum_v[k] += Vj * pi_ij * G[k];
         cont += vji[k] * G[k];
-        diff += T(2.0) * (S.rho[j] - rho_i) * (-r[k]) / den * G[k];
+        diff += T(2.0) * drho_ji * (-r[k]) / den * G[k];
       }
       sum_c += Vj * cont;
       sum_d += Vj * diff;
@@ -434,7 +572,15 @@ void step(const OrcParams& P, State<T>& S) {
   std::vector<double> p_wall;
   wall_extrapolation(P, S, pr, p_wall);
   std::vector<T> a, drho;
-  rates(P, S, pr, p_wall, a, drho);
+  if (renormalised(P)) {
+    std::vector<double> grad;
+    std::vector<int> all(S.N());
+    std::iota(all.begin(), all.end(), 0);
+    renorm_gradient(P, plain(S), pr, all, grad);
+    rates(P, S, pr, p_wall, a, drho, nullptr, &grad);
+  } else {
+    rates(P, S, pr, p_wall, a, drho);
+  }
   const int d = S.d;
   for (int i = 0; i < S.nf; ++i) {
     for (int k = 0; k < d; ++k) {
@@ -752,7 +898,20 @@ int orc_rates(const OrcParams* P, int nf, int nw, const float* x, const float* v
     std::vector<double> xr(S.x.begin(), S.x.end());
     Pairs sub;
     neighbour_lists(*P, nf, xr.data(), w, sub.off, sub.nb);
-    rates(*P, S, sub, p_wall, av, dr, &w);
+    if (renormalised(*P)) {
+      // the gradients are needed at the sampled particles and at all their neighbours
+      std::vector<int> u(w.begin(), w.end());
+      u.insert(u.end(), sub.nb.begin(), sub.nb.end());
+      std::sort(u.begin(), u.end());
+      u.erase(std::unique(u.begin(), u.end()), u.end());
+      Pairs pu;
+      neighbour_lists(*P, nf, xr.data(), u, pu.off, pu.nb);
+      std::vector<double> grad;
+      renorm_gradient(*P, S, pu, u, grad);
+      rates(*P, S, sub, p_wall, av, dr, &w, &grad);
+    } else {
+      rates(*P, S, sub, p_wall, av, dr, &w);
+    }
     const int d = P->dim;
     for (size_t aidx = 0; aidx < w.size(); ++aidx) {
       int i = w[aidx];
@@ -766,6 +925,13 @@ int orc_rates(const OrcParams* P, int nf, int nw, const float* x, const float* v
   Pairs pr = pairs_of(*P, S);
   if (P->density_mode == 1) density_summation(*P, S, pr);
   wall_extrapolation(*P, S, pr, p_wall);
+  std::vector<double> grad;
+  if (renormalised(*P)) {
+    std::vector<int> all(S.N());
+    std::iota(all.begin(), all.end(), 0);
+    renorm_gradient(*P, S, pr, all, grad);
+  }
+  const std::vector<double>* gp = renormalised(*P) ? &grad : nullptr;
   if (who) {
     w.assign(who, who + n_who);
     for (int i : w)
@@ -777,9 +943,9 @@ int orc_rates(const OrcParams* P, int nf, int nw, const float* x, const float* v
       sub.off[aidx + 1] = sub.off[aidx] + (pr.off[i + 1] - pr.off[i]);
       sub.nb.insert(sub.nb.end(), pr.nb.begin() + pr.off[i], pr.nb.begin() + pr.off[i + 1]);
     }
-    rates(*P, S, sub, p_wall, av, dr, &w);
+    rates(*P, S, sub, p_wall, av, dr, &w, gp);
   } else {
-    rates(*P, S, pr, p_wall, av, dr, nullptr);
+    rates(*P, S, pr, p_wall, av, dr, nullptr, gp);
     w.resize(nf);
     std::iota(w.begin(), w.end(), 0);
   }
@@ -793,6 +959,33 @@ int orc_rates(const OrcParams* P, int nf, int nw, const float* x, const float* v
   }
   if (p_wall_out)
     for (int k = 0; k < nw; ++k) p_wall_out[k] = p_wall[k];
+  return 0;
+}
+
+// Pseudo-inverse of a d x d matrix M (row-major 3 x 3 storage, symmetric by assumption) as the
+// renormalisation uses it; L out in the same storage.
+void orc_sym_pinv(int d, const double* M, double* L) {
+  double A[3][3], R[3][3];
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) A[p][q] = M[p * 3 + q];
+  sym_pinv(d, A, R);
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) L[p * 3 + q] = R[p][q];
+}
+
+// Renormalised density gradient <grad rho>^L (N * dim) of every particle at the given float32
+// state, after the wall extrapolation the step applies (rho as given for the fluid); M_out
+// (optional, N * 9) receives the matrices M_i.
+int orc_renorm_gradient(const OrcParams* P, int nf, int nw, const float* x, const float* v, const float* rho,
+                        const float* m, double* grad_out, double* M_out) {
+  State<double> S = load_state<double>(*P, nf, nw, x, v, rho, m);
+  Pairs pr = pairs_of(*P, S);
+  std::vector<double> p_wall, grad;
+  wall_extrapolation(*P, S, pr, p_wall);
+  std::vector<int> all(S.N());
+  std::iota(all.begin(), all.end(), 0);
+  renorm_gradient(*P, S, pr, all, grad, M_out);
+  std::copy(grad.begin(), grad.end(), grad_out);
   return 0;
 }
 
@@ -827,6 +1020,7 @@ int orc_rollout64(const OrcParams* P, int nf, int nw, const double* x, const dou
 int orc_jvp(const OrcParams* P, int nf, int nw, const double* x, const double* v, const double* rho, const float* m,
             double nu, const double* dx0, const double* dv0, const double* drho0, double dnu, int n_steps,
             double* x_out, double* v_out, double* rho_out, double* dx_out, double* dv_out, double* drho_out) {
+  if (renormalised(*P)) return -4;  // no derivative of the renormalised gradient
   int N = nf + nw, d = P->dim;
   State<Dual> S;
   S.nf = nf; S.nw = nw; S.d = d;
@@ -847,6 +1041,7 @@ int orc_adjoint(const OrcParams* P, int nf, int nw, const double* x, const doubl
                 const double* rb_T, double* xb_0, double* vb_0, double* rb_0, double* nub,
                 double* x_T, double* v_T, double* rho_T) {
   if (nw != 0 || P->density_mode != 0) return -1;
+  if (renormalised(*P)) return -4;  // no derivative of the renormalised gradient
   int N = nf, d = P->dim;
   State<double> S;
   S.nf = nf; S.nw = 0; S.d = d;
