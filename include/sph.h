@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define SPH_ABI_VERSION 1
+#define SPH_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define SPH_API __attribute__((visibility("default")))
@@ -67,6 +67,17 @@ extern "C" {
 #define SPH_KERNEL_WENDLAND2 1   /* Wendland C2, 2D and 3D */
 #define SPH_DENSITY_CONTINUITY 0 /* integrate drho/dt with delta diffusion (Sec. 2.3) */
 #define SPH_DENSITY_SUMMATION 1  /* rho_i = sum_j m_j W_ij each step, no diffusion (Sec. 2.3) */
+/* delta-SPH density diffusion of the continuity mode, delta h c0 sum_j V_j psi_ij . grad_i W_ij
+ * (Sec. 2.3 cites the delta-SPH model without printing the term):
+ *   MC      psi_ij = 2 (rho_j - rho_i) (x_j - x_i) / (|x_ij|^2 + eps h^2)   (Molteni-Colagrossi)
+ *   RENORM  psi_ij = 2 [(rho_j - rho_i) - (g_i + g_j) . (x_j - x_i) / 2] (x_j - x_i) / (|x_ij|^2 + eps h^2)
+ *           with g_i = <grad rho>_i^L = sum_j V_j (rho_j - rho_i) L_i grad_i W_ij and
+ *           L_i = pinv(sum_j V_j (x_j - x_i) (x) grad_i W_ij) over all neighbours, walls included
+ *           (the kernel renormalisation of App. A; the pseudo-inverse drops eigen-directions with
+ *           |lambda| <= 1e-3 max|lambda|).  The term then vanishes for a linear density, also at a
+ *           free surface.  One extra neighbour pass per step; no adjoint (sph_rollout rejects it). */
+#define SPH_DIFFUSION_MC 0
+#define SPH_DIFFUSION_RENORM 1
 
 /* Global parameters sigma of one scene (Sec. 2.2; App. C "global state dictionary").
  * The support radius H is the kernel's cut-off (the paper stores the support and calls it h).
@@ -96,6 +107,7 @@ typedef struct sph_params {
   float g[3];             /* body acceleration */
   int32_t rebuild_interval; /* >= 1, used when skin > 0 */
   float skin;             /* Verlet skin (absolute length, >= 0) */
+  int32_t diffusion;      /* SPH_DIFFUSION_* (continuity mode; no effect with summation density) */
 } sph_params;
 
 typedef struct sph_scene sph_scene;
@@ -143,8 +155,15 @@ SPH_API int sph_get_state(const sph_scene* scene, float* x, float* v, float* rho
  * summation mode).  Original order, fluid particles only.  Any output may be NULL. */
 SPH_API int sph_rates(sph_scene* scene, float* a, float* drho, float* rho_used, int ptr_is_device);
 
+/* Renormalised density gradient <grad rho>^L (see SPH_DIFFUSION_RENORM) at the current state,
+ * after the wall extrapolation a step applies: (n_fluid + n_wall) * dim floats, original order
+ * (fluid rows, then wall rows; per scene for a batch, n_rows of sph_batch_info plus the walls).
+ * Any diffusion mode; synchronises the scene's stream. */
+SPH_API int sph_density_gradient(sph_scene* scene, float* grad, int ptr_is_device);
+
 /* Forward rollout of n_steps that keeps what the adjoint needs: the state every ckpt_every
- * steps (gradient checkpointing, Sec. 3.3).  Replaces any previous tape of this scene. */
+ * steps (gradient checkpointing, Sec. 3.3).  Replaces any previous tape of this scene.
+ * SPH_EINVAL with SPH_DIFFUSION_RENORM in continuity mode (no reverse pass of that term). */
 SPH_API int sph_rollout(sph_scene* scene, int n_steps, int ckpt_every);
 
 /* Reverse pass of the last sph_rollout (vector-Jacobian product, Sec. 2.2): given the adjoints
@@ -174,7 +193,7 @@ SPH_API int sph_debug_pairs(sph_scene* scene, int64_t* n_pairs, int32_t* pi, int
 /* Per-kernel device timing.  When enabled, the scene records CUDA events around its launches
  * on its stream; sph_timing returns the accumulated milliseconds and launch count of one
  * kernel class (0 = fused sweep, 1 = rebuild (keys+sort+ranges+permute), 2 = walls,
- * 3 = density, 4 = adjoint sweep) and resets it.  Synchronises the stream. */
+ * 3 = density, 4 = adjoint sweep, 5 = renormalised density gradient) and resets it.  Synchronises the stream. */
 SPH_API int sph_profile(sph_scene* scene, int enable);
 SPH_API int sph_timing(sph_scene* scene, int kernel_class, double* ms, int64_t* launches);
 
@@ -208,6 +227,9 @@ SPH_API void sph_destroy(sph_scene* scene);
  * re-packed on the device).  Adjoint requests (forward rollout with checkpoints, then the reverse
  * pass for the loss L = (1/N) sum_i |x_i^T - x~_i|^2 with target positions x~, Sec. 4.1) run on
  * the second stream concurrently.  A served result is bitwise the result of the scene alone.
+ * Forward requests share the batch only with requests of the same dim, kernel, density mode,
+ * diffusion form, skin and rebuild_interval; one of another kind waits, in arrival order, until
+ * the running batch has drained.
  * Results stay with the server until sph_wait returns them (once per ticket). */
 #define SPH_REQ_FORWARD 0
 #define SPH_REQ_ADJOINT 1

@@ -41,7 +41,7 @@ class Params(C.Structure):
         ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
         ("H", C.c_float), ("dt", C.c_float), ("rho0", C.c_float), ("c0", C.c_float), ("gamma", C.c_float),
         ("nu", C.c_float), ("delta", C.c_float), ("eps", C.c_float), ("g", C.c_float * 3),
-        ("rebuild_interval", C.c_int32), ("skin", C.c_float),
+        ("rebuild_interval", C.c_int32), ("skin", C.c_float), ("diffusion", C.c_int32),
     ]
 
     @classmethod
@@ -51,6 +51,7 @@ class Params(C.Structure):
             setattr(o, k, int(p[k]))
         for k in ("H", "dt", "rho0", "c0", "gamma", "nu", "delta", "eps", "skin"):
             setattr(o, k, float(p[k]))
+        o.diffusion = int(p.get("diffusion", 0))
         for k in range(3):
             o.box_lo[k] = float(p["box_lo"][k])
             o.box_hi[k] = float(p["box_hi"][k])
@@ -108,6 +109,7 @@ def lib() -> C.CDLL:
     L.sph_step.argtypes = [vp, C.c_int]
     L.sph_get_state.argtypes = [vp, vp, vp, vp, C.c_int]
     L.sph_rates.argtypes = [vp, vp, vp, vp, C.c_int]
+    L.sph_density_gradient.argtypes = [vp, vp, C.c_int]
     L.sph_rollout.argtypes = [vp, C.c_int, C.c_int]
     L.sph_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
     L.sph_scene_info.argtypes = [vp, P(C.c_int32), P(C.c_int32)]
@@ -282,6 +284,13 @@ class Scene:
         ru = np.empty((nf,), np.float32)
         _check(lib().sph_rates(self._h, a.ctypes.data, dr.ctypes.data, ru.ctypes.data, 0))
         return dict(a=a, drho=dr, rho=ru)
+
+    def density_gradient(self):
+        """Renormalised density gradient <grad rho>^L of every particle (n x dim, original order,
+        fluid rows then wall rows), after the wall extrapolation a step applies."""
+        g = np.empty((self.n, self.dim), np.float32)
+        _check(lib().sph_density_gradient(self._h, g.ctypes.data, 0))
+        return g
 
     # -- differentiation
     def rollout(self, n_steps: int, ckpt_every: int = 20):

@@ -2,6 +2,7 @@
 //   tile table      (built after every rebuild from the cell offsets)
 //   walls           Shepard extrapolation of the fluid pressure onto wall particles
 //   density         summation density rho_i = sum_j m_j W_ij            (Sec. 2.3)
+//   gradient        renormalised density gradient <grad rho>^L (kernel renormalisation, App. A)
 //   sweep           continuity + delta diffusion, Tait pressure, viscosity, gravity, and the
 //                   kick-drift epilogue (Sec. 2.3, Sec. 3.4); also the rate-only evaluation
 //   pairs           exact pair export (FP64 predicate in a guard band)
@@ -447,19 +448,181 @@ struct DensityPass {
   }
 };
 
+// ================================================================== renormalised density gradient
+// Kernel renormalisation (App. A, after Marrone et al.), for every particle (fluid and wall):
+//   M_i = sum_j V_j (x_j - x_i) (x) grad_i W_ij = -sum_j V_j gK r (x) r      (symmetric)
+//   s_i = sum_j V_j (rho_j - rho_i) grad_i W_ij,       <grad rho>_i^L = pinv(M_i) s_i
+// (L_i applies to every term of the sum, so it is taken out of it).  The pseudo-inverse keeps
+// the eigen-directions with |lambda| > kPinvRtol max|lambda|.
+constexpr float kPinvRtol = 1e-3f;
+
+// pinv of the symmetric 2x2 [a b; b c] in closed form: (Lxx, Lxy, Lyy)
+__device__ __forceinline__ void pinv_sym2(float a, float b, float c, float* L) {
+  const float mean = 0.5f * (a + c), half = 0.5f * (a - c);
+  const float rt = sqrtf(fmaf(half, half, b * b));
+  const float l1 = mean + rt, l2 = mean - rt;
+  const float cut = kPinvRtol * fmaxf(fabsf(l1), fabsf(l2));
+  const bool k1 = fabsf(l1) > cut, k2 = fabsf(l2) > cut;
+  L[0] = L[1] = L[2] = 0.f;
+  if (k1 && k2) {
+    const float inv = 1.f / fmaf(a, c, -b * b);
+    L[0] = c * inv;
+    L[1] = -b * inv;
+    L[2] = a * inv;
+  } else if (k1 || k2) {
+    const float l = k1 ? l1 : l2;
+    // eigenvector of l: (b, l - a) or (l - c, b), whichever is longer
+    float ex = b, ey = l - a;
+    const float fx = l - c, fy = b;
+    if (fmaf(fx, fx, fy * fy) > fmaf(ex, ex, ey * ey)) {
+      ex = fx;
+      ey = fy;
+    }
+    const float n2 = fmaf(ex, ex, ey * ey);
+    if (n2 > 0.f) {
+      const float w = 1.f / (n2 * l);
+      L[0] = ex * ex * w;
+      L[1] = ex * ey * w;
+      L[2] = ey * ey * w;
+    } else {  // b = 0 and l on the diagonal
+      L[0] = fabsf(a) > cut ? 1.f / a : 0.f;
+      L[2] = fabsf(c) > cut ? 1.f / c : 0.f;
+    }
+  }
+}
+
+// pinv of a symmetric 3x3 by cyclic Jacobi rotations (Golub & Van Loan, Sec. 8.5), FP32.
+// m = (xx, xy, xz, yy, yz, zz) in and L (same packing) out.
+__device__ __forceinline__ void pinv_sym3(const float* m, float* L) {
+  float A[3][3] = {{m[0], m[1], m[2]}, {m[1], m[3], m[4]}, {m[2], m[4], m[5]}};
+  float Q[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+#pragma unroll 1
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    const float off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    const float dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (!(off > 1e-14f * dia)) break;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      const float apq = A[p][q];
+      if (apq == 0.f) continue;
+      const float tau = (A[q][q] - A[p][p]) / (2.f * apq);
+      const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+      const float c = rsqrtf(fmaf(t, t, 1.f)), sn = t * c;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float akp = A[k][p], akq = A[k][q];
+        A[k][p] = c * akp - sn * akq;
+        A[k][q] = sn * akp + c * akq;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float apk = A[p][k], aqk = A[q][k];
+        A[p][k] = c * apk - sn * aqk;
+        A[q][k] = sn * apk + c * aqk;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float qkp = Q[k][p], qkq = Q[k][q];
+        Q[k][p] = c * qkp - sn * qkq;
+        Q[k][q] = sn * qkp + c * qkq;
+      }
+    }
+  }
+  const float lam[3] = {A[0][0], A[1][1], A[2][2]};
+  const float cut = kPinvRtol * fmaxf(fabsf(lam[0]), fmaxf(fabsf(lam[1]), fabsf(lam[2])));
+#pragma unroll
+  for (int e = 0; e < 6; ++e) L[e] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (!(fabsf(lam[k]) > cut)) continue;
+    const float w = 1.f / lam[k];
+    L[0] = fmaf(Q[0][k] * Q[0][k], w, L[0]);
+    L[1] = fmaf(Q[0][k] * Q[1][k], w, L[1]);
+    L[2] = fmaf(Q[0][k] * Q[2][k], w, L[2]);
+    L[3] = fmaf(Q[1][k] * Q[1][k], w, L[3]);
+    L[4] = fmaf(Q[1][k] * Q[2][k], w, L[4]);
+    L[5] = fmaf(Q[2][k] * Q[2][k], w, L[5]);
+  }
+}
+
+template <int D, int KERN>
+struct GradPass {
+  static constexpr int NM = D * (D + 1) / 2;  // packed upper triangle of M
+  struct Body {
+    const DevSeg* s;
+    float rho_i;
+    float m[NM], g[D];
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4, float, int) {
+      float r[D];
+      const float r2 = diff<D>(xs, pj.x, r);
+      const float VgK = pj.V * (s->Kg * kern_gt<KERN>(safe_q(r2, s->invH)));
+      int e = 0;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = a; b < D; ++b, ++e) m[e] = fmaf(-VgK * r[a], r[b], m[e]);
+      const float dr = VgK * (pj.rho - rho_i);
+#pragma unroll
+      for (int k = 0; k < D; ++k) g[k] = fmaf(dr, r[k], g[k]);
+    }
+    template <int L>
+    __device__ __forceinline__ void reduce() {
+#pragma unroll
+      for (int e = 0; e < NM; ++e) m[e] = group_sum<L>(m[e]);
+#pragma unroll
+      for (int k = 0; k < D; ++k) g[k] = group_sum<L>(g[k]);
+    }
+  };
+  float4* grad;
+  __device__ static __forceinline__ bool wants(uint32_t) { return true; }
+  __device__ __forceinline__ void skip(int, const TgtView&) {}
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ void last_cta() {}
+  __device__ __forceinline__ const float4* tex0() const { return nullptr; }
+  __device__ __forceinline__ const float4* tex1() const { return nullptr; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView& tv) {
+    b.s = &s;
+    b.rho_i = load_pd_plain<D>(tv.a, tv.k).rho;
+#pragma unroll
+    for (int e = 0; e < NM; ++e) b.m[e] = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) b.g[k] = 0.f;
+    return true;
+  }
+  __device__ __forceinline__ void finish(Body& b, const DevSeg&, int i, const TgtView&) {
+    float L[6];
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (D == 2) {
+      pinv_sym2(b.m[0], b.m[1], b.m[2], L);
+      out.x = fmaf(L[0], b.g[0], L[1] * b.g[1]);
+      out.y = fmaf(L[1], b.g[0], L[2] * b.g[1]);
+    } else {
+      pinv_sym3(b.m, L);
+      out.x = fmaf(L[0], b.g[0], fmaf(L[1], b.g[1], L[2] * b.g[2]));
+      out.y = fmaf(L[1], b.g[0], fmaf(L[3], b.g[1], L[4] * b.g[2]));
+      out.z = fmaf(L[2], b.g[0], fmaf(L[4], b.g[1], L[5] * b.g[2]));
+    }
+    grad[i] = out;
+  }
+};
+
 // ================================================================== fused sweep
 // a_i    = (1/rho_i) sum_j V_j gK (Cv w s - (p_i + p_j)) r + g
 // drho_i = rho_i sum_j V_j gK w - 2 Cdel sum_j V_j gK (rho_j - rho_i) r^2 s
 // (r = x_i - x_j, grad_i W_ij = gK r, w = (v_i - v_j).r, s = 1/(r^2 + eps h^2),
 //  Cv = 2(d+2) nu rho0, Cdel = delta h c0): the paper's terms regrouped per pair.
-template <int D, int KERN, bool INTEGRATE>
+// RENORM: the renormalised diffusion, rho_j - rho_i -> rho_j - rho_i + (g_i + g_j).r / 2 with
+// g = <grad rho>^L of both ends (g_j staged with the neighbour records, g_i in the target cache).
+template <int D, int KERN, bool INTEGRATE, bool RENORM>
 struct SweepPass {
   struct Body {
     const DevSeg* s;
     float xi[D], vi[D], rho_i, p_i;
     float acc[D], c1, c2;
+    float gi[D];              // RENORM: half the target's renormalised density gradient
     float invH, Kg, Cv, eH2;  // 2D: the scene's constants kept in registers (3D reads them)
-    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4, float, int) {
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4 gj, float, int) {
       const float cinvH = D == 2 ? invH : s->invH, cKg = D == 2 ? Kg : s->Kg;
       const float cCv = D == 2 ? Cv : s->Cv, ceH2 = D == 2 ? eH2 : s->eH2;
       float r[D];
@@ -475,7 +638,13 @@ struct SweepPass {
 #pragma unroll
       for (int k = 0; k < D; ++k) acc[k] = fmaf(tt, r[k], acc[k]);
       c1 = fmaf(VgK, w, c1);
-      c2 = fmaf(VgK * (pj.rho - rho_i), r2 * sd, c2);
+      float drho_ji = pj.rho - rho_i;
+      if (RENORM) {
+        const float gjs[3] = {gj.x, gj.y, gj.z};
+#pragma unroll
+        for (int k = 0; k < D; ++k) drho_ji = fmaf(fmaf(0.5f, gjs[k], gi[k]), r[k], drho_ji);
+      }
+      c2 = fmaf(VgK * drho_ji, r2 * sd, c2);
     }
     template <int L>
     __device__ __forceinline__ void reduce() {
@@ -489,6 +658,7 @@ struct SweepPass {
   RateOut ro;
   int* status;
   Displace disp;
+  const float4* grad;  // RENORM: <grad rho>^L per particle (sorted order)
   float dmax = 0.f;  // largest scaled displacement of this thread's targets
   // with the decision on the device: every CTA has folded its maximum in, so the last one
   // decides whether the next step rebuilds (interval reached or a displacement past skin/2)
@@ -516,9 +686,15 @@ struct SweepPass {
     out.meta[i] = tv.a.meta[tv.k];
   }
   __device__ __forceinline__ const float4* tex0() const { return INTEGRATE ? disp.xb : nullptr; }
-  __device__ __forceinline__ const float4* tex1() const { return nullptr; }
+  __device__ __forceinline__ const float4* tex1() const { return RENORM ? grad : nullptr; }
   __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView& tv) {
     b.s = &s;
+    if (RENORM) {
+      const float4 g = tv.e1[tv.k];
+      const float gs[3] = {g.x, g.y, g.z};
+#pragma unroll
+      for (int k = 0; k < D; ++k) b.gi[k] = 0.5f * gs[k];
+    }
     if (D == 2) {
       b.invH = s.invH;
       b.Kg = s.Kg;
@@ -793,16 +969,24 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREAD
   pass.a = t.a;
   run_tiles<D, 0, 1>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
-template <int D, int KERN, bool INTEGRATE>
-__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_sweep_t(TravArgs t, const Tile* tiles, const int* ntiles, Arrays out,
-                                                 RateOut ro, Displace disp) {
-  SweepPass<D, KERN, INTEGRATE> pass;
+template <int D, int KERN>
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_grad_t(TravArgs t, const Tile* tiles, const int* ntiles, float4* grad) {
+  GradPass<D, KERN> pass;
+  pass.grad = grad;
+  run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
+}
+// (3D with the renormalised diffusion: three CTAs per SM, so that its registers do not spill)
+template <int D, int KERN, bool INTEGRATE, bool RENORM>
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, (D == 3 && RENORM ? 768 : 1024) / TileCfg<D>::THREADS) k_sweep_t(TravArgs t, const Tile* tiles, const int* ntiles, Arrays out,
+                                                 RateOut ro, Displace disp, const float4* grad) {
+  SweepPass<D, KERN, INTEGRATE, RENORM> pass;
   pass.a = t.a;
   pass.out = out;
   pass.ro = ro;
   pass.status = t.status;
   pass.disp = disp;
-  run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
+  pass.grad = grad;
+  run_tiles<D, RENORM ? 1 : 0, 0>(t, tiles, ntiles, RENORM ? grad : nullptr, nullptr, pass);
 }
 template <int D>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_pairs_t(TravArgs t, const Tile* tiles, const int* ntiles, int32_t* pi,
@@ -895,14 +1079,27 @@ void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, i
   k_density_t<D, KERN><<<pass_grid((const void*)k_density_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles);
 }
 template <int D, int KERN>
+void launch_grad_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, float4* grad,
+                   cudaStream_t st) {
+  k_grad_t<D, KERN><<<pass_grid((const void*)k_grad_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, grad);
+}
+template <int D, int KERN, bool INTEGRATE, bool RENORM>
+static void launch_sweep_any(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
+                             const RateOut& ro, const Displace& disp, const float4* grad, cudaStream_t st) {
+  auto fn = k_sweep_t<D, KERN, INTEGRATE, RENORM>;
+  fn<<<pass_grid((const void*)fn, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(RENORM ? 1 : 0), st>>>(t, tiles, ntiles, out, ro, disp, grad);
+}
+template <int D, int KERN>
 void launch_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
-                    const Displace& disp, cudaStream_t st) {
-  k_sweep_t<D, KERN, true><<<pass_grid((const void*)k_sweep_t<D, KERN, true>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, out, RateOut{}, disp);
+                    const Displace& disp, const float4* grad, cudaStream_t st) {
+  if (grad) launch_sweep_any<D, KERN, true, true>(t, tiles, ntiles, tiles_upper, out, RateOut{}, disp, grad, st);
+  else launch_sweep_any<D, KERN, true, false>(t, tiles, ntiles, tiles_upper, out, RateOut{}, disp, nullptr, st);
 }
 template <int D, int KERN>
 void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const RateOut& ro,
-                    cudaStream_t st) {
-  k_sweep_t<D, KERN, false><<<pass_grid((const void*)k_sweep_t<D, KERN, false>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, Arrays{}, ro, Displace{});
+                    const float4* grad, cudaStream_t st) {
+  if (grad) launch_sweep_any<D, KERN, false, true>(t, tiles, ntiles, tiles_upper, Arrays{}, ro, Displace{}, grad, st);
+  else launch_sweep_any<D, KERN, false, false>(t, tiles, ntiles, tiles_upper, Arrays{}, ro, Displace{}, nullptr, st);
 }
 template <int D>
 void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
@@ -934,10 +1131,16 @@ cudaError_t configure_passes() {
   SPH_ATTR(3, (k_walls_t<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_walls_t<3, 1>), pass_smem<3>(0))
   SPH_ATTR(2, (k_density_t<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_density_t<2, 1>), pass_smem<2>(0))
   SPH_ATTR(3, (k_density_t<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_density_t<3, 1>), pass_smem<3>(0))
-  SPH_ATTR(2, (k_sweep_t<2, 0, true>), pass_smem<2>(0)) SPH_ATTR(2, (k_sweep_t<2, 1, true>), pass_smem<2>(0))
-  SPH_ATTR(3, (k_sweep_t<3, 0, true>), pass_smem<3>(0)) SPH_ATTR(3, (k_sweep_t<3, 1, true>), pass_smem<3>(0))
-  SPH_ATTR(2, (k_sweep_t<2, 0, false>), pass_smem<2>(0)) SPH_ATTR(2, (k_sweep_t<2, 1, false>), pass_smem<2>(0))
-  SPH_ATTR(3, (k_sweep_t<3, 0, false>), pass_smem<3>(0)) SPH_ATTR(3, (k_sweep_t<3, 1, false>), pass_smem<3>(0))
+  SPH_ATTR(2, (k_sweep_t<2, 0, true, false>), pass_smem<2>(0)) SPH_ATTR(2, (k_sweep_t<2, 1, true, false>), pass_smem<2>(0))
+  SPH_ATTR(3, (k_sweep_t<3, 0, true, false>), pass_smem<3>(0)) SPH_ATTR(3, (k_sweep_t<3, 1, true, false>), pass_smem<3>(0))
+  SPH_ATTR(2, (k_sweep_t<2, 0, false, false>), pass_smem<2>(0)) SPH_ATTR(2, (k_sweep_t<2, 1, false, false>), pass_smem<2>(0))
+  SPH_ATTR(3, (k_sweep_t<3, 0, false, false>), pass_smem<3>(0)) SPH_ATTR(3, (k_sweep_t<3, 1, false, false>), pass_smem<3>(0))
+  SPH_ATTR(2, (k_sweep_t<2, 0, true, true>), pass_smem<2>(1)) SPH_ATTR(2, (k_sweep_t<2, 1, true, true>), pass_smem<2>(1))
+  SPH_ATTR(3, (k_sweep_t<3, 0, true, true>), pass_smem<3>(1)) SPH_ATTR(3, (k_sweep_t<3, 1, true, true>), pass_smem<3>(1))
+  SPH_ATTR(2, (k_sweep_t<2, 0, false, true>), pass_smem<2>(1)) SPH_ATTR(2, (k_sweep_t<2, 1, false, true>), pass_smem<2>(1))
+  SPH_ATTR(3, (k_sweep_t<3, 0, false, true>), pass_smem<3>(1)) SPH_ATTR(3, (k_sweep_t<3, 1, false, true>), pass_smem<3>(1))
+  SPH_ATTR(2, (k_grad_t<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_grad_t<2, 1>), pass_smem<2>(0))
+  SPH_ATTR(3, (k_grad_t<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_grad_t<3, 1>), pass_smem<3>(0))
   SPH_ATTR(2, (k_pairs_t<2>), pass_smem<2>(0)) SPH_ATTR(3, (k_pairs_t<3>), pass_smem<3>(0))
   SPH_ATTR(2, (k_adj_t<2, 0>), pass_smem<2>(1)) SPH_ATTR(2, (k_adj_t<2, 1>), pass_smem<2>(1))
   SPH_ATTR(3, (k_adj_t<3, 0>), pass_smem<3>(2)) SPH_ATTR(3, (k_adj_t<3, 1>), pass_smem<3>(2))
@@ -954,9 +1157,11 @@ SPH_INST_PD(3)
 #define SPH_INST_PDK(D, K)                                                                                   \
   template void launch_walls_t<D, K>(const TravArgs&, const Tile*, const int*, const int*, int, cudaStream_t); \
   template void launch_density_t<D, K>(const TravArgs&, const Tile*, const int*, int, cudaStream_t);        \
+  template void launch_grad_t<D, K>(const TravArgs&, const Tile*, const int*, int, float4*, cudaStream_t);   \
   template void launch_sweep_t<D, K>(const TravArgs&, const Tile*, const int*, int, const Arrays&, const Displace&, \
+                                     const float4*, cudaStream_t);                                           \
+  template void launch_rates_t<D, K>(const TravArgs&, const Tile*, const int*, int, const RateOut&, const float4*, \
                                      cudaStream_t);                                                          \
-  template void launch_rates_t<D, K>(const TravArgs&, const Tile*, const int*, int, const RateOut&, cudaStream_t); \
   template void launch_adj_t<D, K>(const TravArgs&, const Tile*, const int*, int, const float4*, const float*,  \
                                    const float4*, const float4*, float4*, float4*, float*, cudaStream_t);
 SPH_INST_PDK(2, 0)

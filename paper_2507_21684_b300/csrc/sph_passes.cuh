@@ -17,11 +17,15 @@ void launch_wall_tiles(const Tile* tiles, const int* ntiles, int tiles_upper, co
 template <int D, int KERN>
 void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st);
 template <int D, int KERN>
+void launch_grad_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, float4* grad,
+                   cudaStream_t st);
+// grad != nullptr selects the renormalised diffusion (gradients from launch_grad_t)
+template <int D, int KERN>
 void launch_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
-                    const Displace& disp, cudaStream_t st);
+                    const Displace& disp, const float4* grad, cudaStream_t st);
 template <int D, int KERN>
 void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const RateOut& ro,
-                    cudaStream_t st);
+                    const float4* grad, cudaStream_t st);
 template <int D>
 void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
                     unsigned long long* count, long long cap, cudaStream_t st);

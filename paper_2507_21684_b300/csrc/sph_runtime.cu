@@ -105,6 +105,7 @@ DevSeg make_seg(const sph_params& p, int n_fluid, int cell_base, int p0, int p1,
   if (p.dim != 2 && p.dim != 3) einval("dim must be 2 or 3");
   if (p.kernel != 0 && p.kernel != 1) einval("kernel must be SPH_KERNEL_WENDLAND4 or SPH_KERNEL_WENDLAND2");
   if (p.density_mode != 0 && p.density_mode != 1) einval("density_mode must be 0 or 1");
+  if (p.diffusion != 0 && p.diffusion != 1) einval("diffusion must be SPH_DIFFUSION_MC or SPH_DIFFUSION_RENORM");
   if (!(p.H > 0.f) || !(p.dt > 0.f) || !(p.rho0 > 0.f) || !(p.c0 > 0.f) || !(p.gamma > 0.f))
     einval("H, dt, rho0, c0 and gamma must be positive");
   if (!(p.nu >= 0.f) || !(p.eps > 0.f) || !(p.skin >= 0.f) || p.rebuild_interval < 1)
@@ -275,6 +276,7 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
   D = prms[0].dim;
   kern = prms[0].kernel;
   summation = prms[0].density_mode == 1;
+  renorm = !summation && prms[0].diffusion == 1;
   any_walls = false;
   skin = prms[0].skin;
   interval = prms[0].rebuild_interval;
@@ -286,6 +288,7 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
     const sph_params& p = prms[s];
     if (p.dim != D || p.kernel != kern || (p.density_mode == 1) != summation)
       einval("all scenes of a batch must share dim, kernel and density mode");
+    if (p.diffusion != prms[0].diffusion) einval("all scenes of a batch must share the diffusion form");
     int n = nfs[s] + nws[s];
     if (nfs[s] < 0 || nws[s] < 0 || n < 1) einval("particle counts must be non-negative with at least one particle");
     if ((long long)N + n >= (1LL << 30)) einval("too many particles");
@@ -366,6 +369,7 @@ void Scene::alloc_all() {
     wall_tiles = (int*)mem.get(sizeof(int) * (size_t)tiles_upper);
     d_nwall = (int*)mem.get(sizeof(int) * 2);
   }
+  if (renorm) gradrho = (float4*)mem.get(sizeof(float4) * N);  // before any step is captured
   d_ntiles = (int*)mem.get(sizeof(int) * 2);
   d_tile_ctr = (int*)mem.get(sizeof(int) * 4);
   CK(cudaMemsetAsync(d_tile_ctr, 0, sizeof(int) * 4, st));  // tiled kernels leave it zeroed
@@ -531,6 +535,36 @@ void Scene::build_tiles(const int* off, const uint2* meta, Tile* tl, int* ntl) {
   }
 }
 
+void Scene::walls_pass(const TravArgs& t, const Tile* tl) {
+  prof_begin(2);
+  if (D == 2) {
+    if (kern == 0) launch_walls_t<2, 0>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
+    else launch_walls_t<2, 1>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
+  } else {
+    if (kern == 0) launch_walls_t<3, 0>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
+    else launch_walls_t<3, 1>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
+  }
+  CKL();
+  prof_end();
+  ++launches;
+}
+
+// <grad rho>^L of every particle into gradrho (after the wall pass has set the walls' density)
+void Scene::grad_pass(const TravArgs& t, const Tile* tl, const int* ntl) {
+  if (!gradrho) gradrho = (float4*)mem.get(sizeof(float4) * N);
+  prof_begin(5);
+  if (D == 2) {
+    if (kern == 0) launch_grad_t<2, 0>(t, tl, ntl, tiles_upper, gradrho, st);
+    else launch_grad_t<2, 1>(t, tl, ntl, tiles_upper, gradrho, st);
+  } else {
+    if (kern == 0) launch_grad_t<3, 0>(t, tl, ntl, tiles_upper, gradrho, st);
+    else launch_grad_t<3, 1>(t, tl, ntl, tiles_upper, gradrho, st);
+  }
+  CKL();
+  prof_end();
+  ++launches;
+}
+
 void Scene::passes_before_sweep(const TravArgs& t_in, const Tile* tl, const int* ntl) {
   if (!tl) {
     tl = tiles;
@@ -538,19 +572,8 @@ void Scene::passes_before_sweep(const TravArgs& t_in, const Tile* tl, const int*
   }
   TravArgs t = t_in;
   t.pair_count = nullptr;  // pair counts are those of the sweep (fluid targets) only
-  if (any_walls) {
-    prof_begin(2);
-    if (D == 2) {
-      if (kern == 0) launch_walls_t<2, 0>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
-      else launch_walls_t<2, 1>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
-    } else {
-      if (kern == 0) launch_walls_t<3, 0>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
-      else launch_walls_t<3, 1>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
-    }
-    CKL();
-    prof_end();
-    ++launches;
-  }
+  if (any_walls) walls_pass(t, tl);
+  if (renorm) grad_pass(t, tl, ntl);
   if (summation) {
     prof_begin(3);
     if (D == 2) {
@@ -574,12 +597,13 @@ void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const in
   prof_begin(0);
   const Displace dp = dev_policy ? Displace{xbuild, &d_ctl->maxr, inv_r2, use_coop ? d_ctl : nullptr, interval}
                                  : Displace{nullptr, nullptr, 0.f, nullptr, 0};
+  const float4* g = renorm ? gradrho : nullptr;
   if (D == 2) {
-    if (kern == 0) launch_sweep_t<2, 0>(t, tl, ntl, tiles_upper, out, dp, st);
-    else launch_sweep_t<2, 1>(t, tl, ntl, tiles_upper, out, dp, st);
+    if (kern == 0) launch_sweep_t<2, 0>(t, tl, ntl, tiles_upper, out, dp, g, st);
+    else launch_sweep_t<2, 1>(t, tl, ntl, tiles_upper, out, dp, g, st);
   } else {
-    if (kern == 0) launch_sweep_t<3, 0>(t, tl, ntl, tiles_upper, out, dp, st);
-    else launch_sweep_t<3, 1>(t, tl, ntl, tiles_upper, out, dp, st);
+    if (kern == 0) launch_sweep_t<3, 0>(t, tl, ntl, tiles_upper, out, dp, g, st);
+    else launch_sweep_t<3, 1>(t, tl, ntl, tiles_upper, out, dp, g, st);
   }
   CKL();
   prof_end();
@@ -838,6 +862,7 @@ void Scene::ensure_cells() {
 // ---------------------------------------------------------------- adjoint tape
 void Scene::rollout(int n, int k) {
   if (n < 1 || k < 1) einval("n_steps and ckpt_every must be >= 1");
+  if (renorm) einval("the renormalised diffusion (SPH_DIFFUSION_RENORM) has no adjoint; use sph_step");
   tape_n = n;
   tape_k = k;
   int ncp = (n + k - 1) / k;
@@ -1089,18 +1114,41 @@ void Scene::rates(float* a, float* drho, float* rho, int is_dev) {
   if (!d_fluid_base) d_fluid_base = (int*)mem.get(sizeof(int) * S);
   CK(cudaMemcpyAsync(d_fluid_base, fbase.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
   ro.orig_base = d_fluid_base;
+  const float4* g = renorm ? gradrho : nullptr;
   if (D == 2) {
-    if (kern == 0) launch_rates_t<2, 0>(t, tiles, d_ntiles, tiles_upper, ro, st);
-    else launch_rates_t<2, 1>(t, tiles, d_ntiles, tiles_upper, ro, st);
+    if (kern == 0) launch_rates_t<2, 0>(t, tiles, d_ntiles, tiles_upper, ro, g, st);
+    else launch_rates_t<2, 1>(t, tiles, d_ntiles, tiles_upper, ro, g, st);
   } else {
-    if (kern == 0) launch_rates_t<3, 0>(t, tiles, d_ntiles, tiles_upper, ro, st);
-    else launch_rates_t<3, 1>(t, tiles, d_ntiles, tiles_upper, ro, st);
+    if (kern == 0) launch_rates_t<3, 0>(t, tiles, d_ntiles, tiles_upper, ro, g, st);
+    else launch_rates_t<3, 1>(t, tiles, d_ntiles, tiles_upper, ro, g, st);
   }
   CKL();
   cudaMemcpyKind kind = is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (a) CK(cudaMemcpyAsync(a, ro.a, 4 * nd, kind, st));
   if (drho) CK(cudaMemcpyAsync(drho, ro.drho, 4 * (size_t)nf_total, kind, st));
   if (rho) CK(cudaMemcpyAsync(rho, ro.rho, 4 * (size_t)nf_total, kind, st));
+  CK(cudaStreamSynchronize(st));
+}
+
+// <grad rho>^L at the current state in original order (all particles), on a copy of the records
+// (the wall pass writes the walls' density in place).
+void Scene::density_gradient(float* grad, int is_dev) {
+  ensure_cells();
+  if (!adj_alloc) alloc_tape(1);
+  copy_arrays(scratch_arr, buf[cur]);
+  TravArgs t = trav(scratch_arr, keys_sorted, cell_off);
+  t.pair_count = nullptr;
+  if (any_walls) walls_pass(t, tiles);
+  grad_pass(t, tiles, d_ntiles);
+  const size_t nd = (size_t)N * D;
+  float* out = is_dev ? grad : (float*)mem_tmp(sizeof(float) * (nd + 64));
+  // the adjoint's unpermuting store writes the xyz of a float4 array to original rows
+  if (D == 2)
+    launch_adj_store<2>(N, scratch_arr.meta, d_orig_base, gradrho, gradrho, out, nullptr, nullptr, st);
+  else
+    launch_adj_store<3>(N, scratch_arr.meta, d_orig_base, gradrho, gradrho, out, nullptr, nullptr, st);
+  CKL();
+  if (!is_dev) CK(cudaMemcpyAsync(grad, out, 4 * nd, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
 }
 
@@ -1345,6 +1393,18 @@ int sph_rates(sph_scene* sc, float* a, float* drho, float* rho_used, int ptr_is_
   API_BEGIN
   sc->s.enter();
   sc->s.rates(a, drho, rho_used, ptr_is_device);
+  sc->s.leave();
+  API_END
+}
+
+int sph_density_gradient(sph_scene* sc, float* grad, int ptr_is_device) {
+  if (!sc || !grad) {
+    sph::set_err("sph_density_gradient: NULL scene or output");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  sc->s.enter();
+  sc->s.density_gradient(grad, ptr_is_device);
   sc->s.leave();
   API_END
 }

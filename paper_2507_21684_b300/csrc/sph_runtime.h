@@ -89,6 +89,8 @@ struct Scene {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int S = 0, D = 2, kern = 0, N = 0, nf_total = 0, C_tot = 0, bits = 0, passes = 0;
   bool summation = false, any_walls = false;
+  bool renorm = false;              // renormalised delta-SPH diffusion (continuity mode)
+  float4* gradrho = nullptr;        // <grad rho>^L per particle, sorted order (renorm, or on request)
   float skin = 0.f;
   int interval = 1;
   std::vector<DevSeg> segs;
@@ -182,6 +184,8 @@ struct Scene {
                                           int* ntiles_out = nullptr);
   void build_tiles(const int* off, const uint2* meta, Tile* tl, int* ntl);
   void passes_before_sweep(const TravArgs& t, const Tile* tl = nullptr, const int* ntl = nullptr);
+  void walls_pass(const TravArgs& t, const Tile* tl);
+  void grad_pass(const TravArgs& t, const Tile* tl, const int* ntl);
   void sweep(const TravArgs& t, const Arrays& out, const Tile* tl = nullptr, const int* ntl = nullptr);
   void host_rebuild();
   void step_once();
@@ -199,6 +203,7 @@ struct Scene {
   void get_state(float* x, float* v, float* rho, int is_dev);
   void check_status();
   void rates(float* a, float* drho, float* rho, int is_dev);
+  void density_gradient(float* grad, int is_dev);
   void debug_cells(int64_t* start, int32_t* ids);
   void debug_pairs(int64_t* n_pairs, int32_t* pi, int32_t* pj, int64_t cap);
   void timing(int cls, double* ms, int64_t* count);

@@ -39,6 +39,7 @@ static double now_s() {
 static size_t request_bytes(const sph_params& p, int n, int steps, int mode, int ckpt) {
   const size_t per = p.dim == 2 ? 256 : 320;
   size_t b = (size_t)n * per + (1 << 20);
+  if (p.diffusion == SPH_DIFFUSION_RENORM && p.density_mode == SPH_DENSITY_CONTINUITY) b += (size_t)n * 16;
   if (mode == SPH_REQ_ADJOINT) {
     const size_t rec = p.dim == 2 ? 72 : 96;  // one copy of the records
     const int k = std::max(ckpt, 1);
@@ -87,11 +88,23 @@ struct Server {
   int max_batch = 0;
   long long repacks = 0, iterations = 0;
 
+  // Forward requests share one batch only when they share the settings a batch holds in common
+  // (the launches' template choices and the rebuild policy).
+  static bool same_class(const sph_params& a, const sph_params& b) {
+    return a.dim == b.dim && a.kernel == b.kernel && (a.density_mode == 1) == (b.density_mode == 1) &&
+           a.skin == b.skin && a.rebuild_interval == b.rebuild_interval && a.diffusion == b.diffusion;
+  }
+
   void admit_locked() {
     while (!queue.empty()) {
       auto& r = queue.front();
       const int running = (int)(active.size() + joining.size()) + adj_running + (int)adj_queue.size();
       if (used + r->bytes > budget || running >= max_active) break;
+      // a forward request of another class waits (in arrival order) until the batch has drained
+      if (r->mode == SPH_REQ_FORWARD) {
+        const Request* other = !active.empty() ? active.front().get() : !joining.empty() ? joining.front().get() : nullptr;
+        if (other && !same_class(other->p, r->p)) break;
+      }
       used += r->bytes;
       r->phase = 1;
       r->t_admit = now_s();
@@ -355,8 +368,9 @@ int sph_submit(sph_server* sv, const sph_request* rq, uint64_t* ticket) {
     sph::set_err("sph_submit: bad particle counts or dimension");
     return SPH_EINVAL;
   }
-  if (rq->mode == SPH_REQ_ADJOINT && (r->nw != 0 || rq->params.density_mode != SPH_DENSITY_CONTINUITY)) {
-    sph::set_err("sph_submit: adjoint requests need continuity mode without wall particles");
+  if (rq->mode == SPH_REQ_ADJOINT && (r->nw != 0 || rq->params.density_mode != SPH_DENSITY_CONTINUITY ||
+                                      rq->params.diffusion != SPH_DIFFUSION_MC)) {
+    sph::set_err("sph_submit: adjoint requests need continuity mode, the MC diffusion and no wall particles");
     return SPH_EINVAL;
   }
   const size_t nd = (size_t)r->n * r->d;

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_abi_version_and_error_string(L):
-    assert L.sph_abi_version() == 1
+    assert L.sph_abi_version() == 2
     assert isinstance(L.sph_last_error(), bytes)
 
 

@@ -53,6 +53,22 @@ def test_served_results_equal_alone(sph):
             assert g["nubar"] == ref["nubar"]
 
 
+def test_mixed_kinds_are_served_in_separate_batches(sph):
+    """Requests of another dimension or diffusion form wait for the running batch to drain and
+    then run in their own; every result is still the scene's result alone."""
+    specs = [si.taylor_green_2d(24, seed=1), si.taylor_green_2d(20, seed=2, diffusion=1),
+             si.taylor_green_3d(8, seed=3), si.taylor_green_2d(16, seed=4),
+             si.dam_break(res=16, diffusion=1)]
+    steps = [9, 12, 5, 7, 6]
+    with sph.Server(8 << 30, 64) as sv:
+        tickets = [sv.submit(sp, st) for sp, st in zip(specs, steps)]
+        got = [sv.wait(t) for t in tickets]
+    for sp, st, g in zip(specs, steps, got):
+        ref = _alone(sph, sp, st)
+        for k in ("x", "v", "rho"):
+            assert np.array_equal(g[k], ref[k]), k
+
+
 def test_admission_respects_budget_and_wait_is_bounded(sph):
     specs = [si.taylor_green_2d(48, seed=k) for k in range(4)]
     # budget for about one scene at a time: requests queue and run one after another
