@@ -178,6 +178,7 @@ def run_forward(sph, torch, spec, steps, warmup, flush_l2: bool, stream, prof_st
     sc.timing(sph.TIMING_SWEEP)
     sc.timing(sph.TIMING_REBUILD)
     sc.timing(sph.TIMING_WALLS)
+    sc.timing(sph.TIMING_GRADIENT)
     for k in range(prof_steps):
         if flush:
             flush()
@@ -186,10 +187,12 @@ def run_forward(sph, torch, spec, steps, warmup, flush_l2: bool, stream, prof_st
     sweep_ms, sweep_n = sc.timing(sph.TIMING_SWEEP)
     reb_ms, reb_n = sc.timing(sph.TIMING_REBUILD)
     wall_ms, wall_n = sc.timing(sph.TIMING_WALLS)
+    grad_ms, grad_n = sc.timing(sph.TIMING_GRADIENT)
     sc.close()
     return dict(ms=ms, pairs_per_step=pairs_per_step, launches=st1["launches"] - st0["launches"],
                 rebuilds=st1["rebuilds"] - st0["rebuilds"], sweep_ms=sweep_ms / max(sweep_n, 1), sweep_n=sweep_n,
-                rebuild_ms=reb_ms / max(reb_n, 1), walls_ms=wall_ms / max(wall_n, 1))
+                rebuild_ms=reb_ms / max(reb_n, 1), walls_ms=wall_ms / max(wall_n, 1),
+                gradient_ms=grad_ms / max(grad_n, 1))
 
 
 def run_e2e(sph, torch, spec, n_steps, reps):
@@ -348,6 +351,8 @@ def main():
                          "with conditional nodes); the cells are then rebuilt every step")
     ap.add_argument("--skin", type=float, default=None,
                     help="--profile-run: Verlet skin as a fraction of H (default: 0.02 dam break, 0 3D)")
+    ap.add_argument("--diffusion", type=int, default=0, choices=[0, 1],
+                    help="--profile-run: 0 Molteni-Colagrossi, 1 renormalised delta-SPH diffusion")
     ap.add_argument("--stream-scenes", type=int, default=64, help="requests of the served mixed-size stream")
     ap.add_argument("--stream-rates", type=float, nargs="*", default=[20.0, 80.0, 320.0])
     args = ap.parse_args()
@@ -361,12 +366,14 @@ def main():
         import paper_2507_21684_b300 as sph
         sph.use_torch_allocator()
         from paper_2507_21684_b300 import tune
-        sp = si.dam_break(res=128) if args.workload == "dambreak" else si.taylor_green_3d(128, seed=0)
+        sp = (si.dam_break(res=128, diffusion=args.diffusion) if args.workload == "dambreak"
+              else si.taylor_green_3d(128, seed=0, diffusion=args.diffusion))
         skin = args.skin if args.skin is not None else (0.02 if args.workload == "dambreak" else 0.0)
         sp = dict(sp, params=tune.with_skin(sp, skin)["params"])
         r = run_forward(sph, torch, sp, args.steps, args.warmup, args.workload == "dambreak", torch.cuda.Stream(),
                         prof_steps=0, eager=args.eager)
-        print(json.dumps({"profile_run": args.workload, "skin_over_H": skin, "eager": args.eager,
+        print(json.dumps({"profile_run": args.workload, "diffusion": args.diffusion, "skin_over_H": skin,
+                          "eager": args.eager,
                           "ms_per_step": sum(r["ms"]) / len(r["ms"]), "pairs_per_step": r["pairs_per_step"]}))
         return
 
@@ -438,6 +445,16 @@ def main():
             "sweep_ms": f3["sweep_ms"], "rebuild_ms": f3["rebuild_ms"],
             "sweep_fp32_tflops": FLOPS_PER_PAIR[3] * f3["pairs_per_step"] / (f3["sweep_ms"] / 1e3) / 1e12,
             "l2": "state 2M particles x 112 B > L2, no flush"}
+        # the same dam break with the renormalised delta-SPH diffusion (one more neighbour pass)
+        sr = dict(si.dam_break(res=128, diffusion=1), params=dict(spec["params"], diffusion=1))
+        fr = run_forward(sph, torch, sr, args.steps, args.warmup, True, torch.cuda.Stream())
+        tr = sum(fr["ms"]) / 1e3
+        extras["dambreak_128_renorm"] = {
+            "diffusion": "renormalised delta-SPH (kernel renormalisation L_i, Antuono psi_ij)",
+            "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * tr / args.steps,
+            "pair_interactions_per_s": fr["pairs_per_step"] * args.steps / tr,
+            "sweep_ms": fr["sweep_ms"], "gradient_ms": fr["gradient_ms"], "walls_ms": fr["walls_ms"],
+            "l2": "flushed between timed steps"}
         sa = si.adjoint_problem(128)
         ad = run_adjoint(sph, torch, sa, 200, 20)
         extras["adjoint_128"] = {

@@ -26,7 +26,8 @@ SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EUNSTABLE, SPH_ETIMEOUT, SPH_EBUS
 _NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT", 6: "EBUSY", 7: "EINTERNAL"}
 
 # kernel classes of sph_timing
-TIMING_SWEEP, TIMING_REBUILD, TIMING_WALLS, TIMING_DENSITY, TIMING_ADJOINT = range(5)
+TIMING_SWEEP, TIMING_REBUILD, TIMING_WALLS, TIMING_DENSITY, TIMING_ADJOINT, TIMING_GRADIENT = range(6)
+DIFFUSION_MC, DIFFUSION_RENORM = 0, 1
 
 
 class SphError(RuntimeError):
