@@ -39,7 +39,7 @@ class OrcParams(C.Structure):
         ("H", C.c_double), ("dt", C.c_double), ("rho0", C.c_double), ("c0", C.c_double),
         ("gamma", C.c_double), ("nu", C.c_double), ("delta", C.c_double), ("eps", C.c_double),
         ("g", C.c_double * 3), ("rebuild_interval", C.c_int32), ("skin", C.c_double),
-        ("diffusion", C.c_int32),
+        ("diffusion", C.c_int32), ("shift", C.c_double),
     ]
 
 
@@ -50,6 +50,7 @@ def params(p: dict) -> OrcParams:
     for k in ("H", "dt", "rho0", "c0", "gamma", "nu", "delta", "eps", "skin"):
         setattr(o, k, float(p[k]))
     o.diffusion = int(p.get("diffusion", 0))
+    o.shift = float(p.get("shift", 0.0))
     for k in range(3):
         o.box_lo[k] = float(p["box_lo"][k])
         o.box_hi[k] = float(p["box_hi"][k])
@@ -87,6 +88,7 @@ def lib():
                                   _d, _d, _d, _d, _d, _d, _d, _d, _d, _d]
         L.orc_sym_pinv.argtypes = [C.c_int, _d, _d]
         L.orc_renorm_gradient.argtypes = [_P(OrcParams), C.c_int, C.c_int, _f, _f, _f, _f, _d, _d]
+        L.orc_shift.argtypes = [_P(OrcParams), C.c_int, C.c_int, _f, _f, _f, _f, _d, _d]
         _lib = L
     return _lib
 
@@ -208,6 +210,22 @@ def renorm_gradient(scene: dict, x=None, v=None, rho=None, with_M: bool = False)
     return g
 
 
+def shift(scene: dict, x=None, v=None, rho=None):
+    """Particle-shifting displacements (n_fluid x dim) and lambda_i of the fluid at a float32 state."""
+    p = scene["params"]
+    P = params(p)
+    x = np.ascontiguousarray(scene["x"] if x is None else x, np.float32)
+    v = np.ascontiguousarray(scene["v"] if v is None else v, np.float32)
+    rho = np.ascontiguousarray(scene["rho"] if rho is None else rho, np.float32)
+    m = np.ascontiguousarray(scene["mass"], np.float32)
+    nf, nw, d = scene["n_fluid"], scene["n_wall"], p["dim"]
+    dx = np.zeros((nf, d))
+    lam = np.zeros(nf)
+    lib().orc_shift(C.byref(P), nf, nw, _ptr(x, C.c_float), _ptr(v, C.c_float), _ptr(rho, C.c_float),
+                    _ptr(m, C.c_float), _ptr(dx, C.c_double), _ptr(lam, C.c_double))
+    return dx, lam
+
+
 def rollout(scene: dict, n_steps: int, x=None, v=None, rho=None):
     """FP64 rollout from the scene's float32 state (or the given float32 arrays)."""
     p = scene["params"]
@@ -251,8 +269,8 @@ def jvp(scene: dict, n_steps: int, x, v, rho, dx, dv, drho, dnu: float = 0.0, nu
     m = np.ascontiguousarray(scene["mass"], np.float32)
     nu = p["nu"] if nu is None else nu
     out = [np.zeros((N, d)), np.zeros((N, d)), np.zeros(N), np.zeros((N, d)), np.zeros((N, d)), np.zeros(N)]
-    if P.diffusion == 1 and P.density_mode == 0:
-        raise ValueError("orc_jvp: the renormalised diffusion has no tangent pass")
+    if (P.diffusion == 1 and P.density_mode == 0) or P.shift > 0:
+        raise ValueError("orc_jvp: the renormalised diffusion and particle shifting have no tangent pass")
     lib().orc_jvp(C.byref(P), nf, nw, *[_ptr(a, C.c_double) for a in arrs[:3]], _ptr(m, C.c_float), float(nu),
                   *[_ptr(a, C.c_double) for a in arrs[3:]], float(dnu), int(n_steps),
                   *[_ptr(a, C.c_double) for a in out])
@@ -274,8 +292,8 @@ def adjoint(scene: dict, n_steps: int, xb_T, vb_T, rb_T, x=None, v=None, rho=Non
     xb0, vb0, rb0 = np.zeros((N, d)), np.zeros((N, d)), np.zeros(N)
     nub = C.c_double()
     xT, vT, rT = np.zeros((N, d)), np.zeros((N, d)), np.zeros(N)
-    if P.diffusion == 1 and P.density_mode == 0:
-        raise ValueError("orc_adjoint: the renormalised diffusion has no reverse pass")
+    if (P.diffusion == 1 and P.density_mode == 0) or P.shift > 0:
+        raise ValueError("orc_adjoint: the renormalised diffusion and particle shifting have no reverse pass")
     rc = lib().orc_adjoint(C.byref(P), nf, nw, _ptr(x, C.c_double), _ptr(v, C.c_double), _ptr(rho, C.c_double),
                            _ptr(m, C.c_float), float(nu), int(n_steps), *[_ptr(a, C.c_double) for a in ins],
                            _ptr(xb0, C.c_double), _ptr(vb0, C.c_double), _ptr(rb0, C.c_double), C.byref(nub),

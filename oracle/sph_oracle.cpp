@@ -47,6 +47,7 @@ struct OrcParams {
   int32_t rebuild_interval;
   double skin;
   int32_t diffusion;  // 0: Molteni-Colagrossi psi_ij, 1: renormalised (Antuono) psi_ij
+  double shift;       // explicit particle shifting coefficient (0: off)
 };
 }
 
@@ -564,7 +565,82 @@ void rates(const OrcParams& P, const State<T>& S, const Pairs& pr, const std::ve
   }
 }
 
-// One full step (Sec. 3.4): [summation density] -> walls -> rates -> kick-drift of the fluid.
+// ---------------------------------------------------------------- explicit particle shifting
+// Post-step particle shifting (the paper applies shifting at the end of each time step and
+// cites the explicit scheme of Sun et al.; the formulas are not printed).  Reading, after the
+// delta+-SPH form of Sun et al.:
+//   dx_i = -C (2h)^2 sum_j V_j [1 + R (W_ij / W(dp_i))^4] grad_i W_ij,   R = 0.2, 2h = H,
+// dp_i = (m_i / rho0)^(1/d) the particle spacing, C = P.shift, over all neighbours j at the
+// post-step positions.  Free surface by the smallest eigenvalue lambda_i of the renormalisation
+// matrix M_i = sum_j V_j (x_j - x_i) (x) grad_i W_ij (about 1 in the bulk):
+//   lambda_i >= 0.75          bulk: dx_i as above
+//   0.4 <= lambda_i < 0.75    free-surface band: tangential part (I - n n^T) dx_i with the
+//                             outward normal n_i = -c_i / |c_i|, c_i = sum_j V_j grad_i W_ij
+//   lambda_i < 0.4            isolated / splashed: no shift
+// Only positions move; velocity and density are carried unchanged; walls do not move.
+constexpr double kShiftR = 0.2, kLambdaBulk = 0.75, kLambdaSplash = 0.4;
+
+// the smallest eigenvalue of the symmetric part of M (d x d)
+double sym_min_eigen(int d, const double M[3][3]) {
+  double A[3][3] = {{0.0}}, Q[3][3], lam[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) A[a][b] = 0.5 * (M[a][b] + M[b][a]);
+  sym_eigen(d, A, lam, Q);
+  double m = lam[0];
+  for (int k = 1; k < d; ++k) m = std::min(m, lam[k]);
+  return m;
+}
+
+// Shift displacements of the fluid particles at the state S (pr: neighbour lists of all particles).
+void shift_displacements(const OrcParams& P, const State<double>& S, const Pairs& pr, std::vector<double>& dx,
+                         std::vector<double>* lambda_out = nullptr) {
+  const int d = S.d;
+  dx.assign((size_t)S.nf * d, 0.0);
+  if (lambda_out) lambda_out->assign(S.nf, 0.0);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < S.nf; ++i) {
+    const double dp = std::pow(S.m[i] / P.rho0, 1.0 / d);
+    const double W0 = kernel_W<double>(P, dp);
+    double a[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0}, M[3][3] = {{0.0}};
+    for (int64_t t = pr.off[i]; t < pr.off[i + 1]; ++t) {
+      const int j = pr.nb[t];
+      double r[3] = {0.0, 0.0, 0.0}, G[3];
+      double r2 = 0.0;
+      for (int k = 0; k < d; ++k) {
+        r[k] = min_image(P, k, S.x[(size_t)i * d + k] - S.x[(size_t)j * d + k]);
+        r2 += r[k] * r[k];
+      }
+      kernel_gradW<double>(P, r, G);
+      const double Vj = S.m[j] / S.rho[j];
+      const double wr = kernel_W<double>(P, std::sqrt(r2)) / W0;
+      const double f = 1.0 + kShiftR * (wr * wr) * (wr * wr);
+      for (int p = 0; p < d; ++p) {
+        a[p] += Vj * f * G[p];
+        c[p] += Vj * G[p];
+        for (int q = 0; q < d; ++q) M[p][q] += Vj * (-r[p]) * G[q];
+      }
+    }
+    const double lam = sym_min_eigen(d, M);
+    if (lambda_out) (*lambda_out)[i] = lam;
+    if (!(lam >= kLambdaSplash)) continue;
+    double s[3];
+    for (int k = 0; k < d; ++k) s[k] = -P.shift * P.H * P.H * a[k];
+    if (lam < kLambdaBulk) {
+      double cn = 0.0;
+      for (int k = 0; k < d; ++k) cn += c[k] * c[k];
+      cn = std::sqrt(cn);
+      if (cn > 0.0) {
+        double n[3], sn = 0.0;
+        for (int k = 0; k < d; ++k) { n[k] = -c[k] / cn; sn += s[k] * n[k]; }
+        for (int k = 0; k < d; ++k) s[k] -= sn * n[k];
+      }
+    }
+    for (int k = 0; k < d; ++k) dx[(size_t)i * d + k] = s[k];
+  }
+}
+
+// One full step (Sec. 3.4): [summation density] -> walls -> rates -> kick-drift of the fluid
+// -> [particle shifting at the new positions].
 template <class T>
 void step(const OrcParams& P, State<T>& S) {
   Pairs pr = pairs_of(P, S);
@@ -588,6 +664,14 @@ void step(const OrcParams& P, State<T>& S) {
       S.x[(size_t)i * d + k] = S.x[(size_t)i * d + k] + T(P.dt) * S.v[(size_t)i * d + k];
     }
     if (P.density_mode == 0) S.rho[i] = S.rho[i] + T(P.dt) * drho[i];
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    if (P.shift > 0.0) {
+      Pairs pr2 = pairs_of(P, S);  // neighbours at the new positions
+      std::vector<double> dx;
+      shift_displacements(P, S, pr2, dx);
+      for (size_t k = 0; k < dx.size(); ++k) S.x[k] = S.x[k] + dx[k];
+    }
   }
 }
 
@@ -989,6 +1073,20 @@ int orc_renorm_gradient(const OrcParams* P, int nf, int nw, const float* x, cons
   return 0;
 }
 
+// Particle-shifting displacements (nf * dim) and lambda_i (nf) of the fluid at a float32 state as
+// given (the state the shift of a step sees: positions after the kick-drift, the fluid density
+// after the step, the walls' density of the step's wall pass).
+int orc_shift(const OrcParams* P, int nf, int nw, const float* x, const float* v, const float* rho, const float* m,
+              double* dx_out, double* lambda_out) {
+  State<double> S = load_state<double>(*P, nf, nw, x, v, rho, m);
+  Pairs pr = pairs_of(*P, S);
+  std::vector<double> dx, lam;
+  shift_displacements(*P, S, pr, dx, &lam);
+  std::copy(dx.begin(), dx.end(), dx_out);
+  if (lambda_out) std::copy(lam.begin(), lam.end(), lambda_out);
+  return 0;
+}
+
 // n_steps of the FP64 scheme from a float32 initial state; FP64 final state out.
 int orc_rollout(const OrcParams* P, int nf, int nw, const float* x, const float* v, const float* rho, const float* m,
                 int n_steps, double* x_out, double* v_out, double* rho_out) {
@@ -1020,7 +1118,7 @@ int orc_rollout64(const OrcParams* P, int nf, int nw, const double* x, const dou
 int orc_jvp(const OrcParams* P, int nf, int nw, const double* x, const double* v, const double* rho, const float* m,
             double nu, const double* dx0, const double* dv0, const double* drho0, double dnu, int n_steps,
             double* x_out, double* v_out, double* rho_out, double* dx_out, double* dv_out, double* drho_out) {
-  if (renormalised(*P)) return -4;  // no derivative of the renormalised gradient
+  if (renormalised(*P) || P->shift > 0.0) return -4;  // no derivative of these terms
   int N = nf + nw, d = P->dim;
   State<Dual> S;
   S.nf = nf; S.nw = nw; S.d = d;
@@ -1041,7 +1139,7 @@ int orc_adjoint(const OrcParams* P, int nf, int nw, const double* x, const doubl
                 const double* rb_T, double* xb_0, double* vb_0, double* rb_0, double* nub,
                 double* x_T, double* v_T, double* rho_T) {
   if (nw != 0 || P->density_mode != 0) return -1;
-  if (renormalised(*P)) return -4;  // no derivative of the renormalised gradient
+  if (renormalised(*P) || P->shift > 0.0) return -4;  // no derivative of these terms
   int N = nf, d = P->dim;
   State<double> S;
   S.nf = nf; S.nw = 0; S.d = d;

@@ -80,7 +80,7 @@ def _f32(v: float) -> float:
 
 def _params(dim, kernel, H, dt, c0, nu, delta, box_lo, box_hi, periodic_mask,
             g=(0.0, 0.0, 0.0), rho0=1.0, gamma=7.0, eps=0.01, density_mode=DENSITY_CONTINUITY,
-            rebuild_interval=1, skin=0.0, diffusion=DIFFUSION_MC):
+            rebuild_interval=1, skin=0.0, diffusion=DIFFUSION_MC, shift=0.0):
     return dict(
         dim=int(dim), kernel=int(kernel), density_mode=int(density_mode),
         periodic_mask=int(periodic_mask),
@@ -90,6 +90,7 @@ def _params(dim, kernel, H, dt, c0, nu, delta, box_lo, box_hi, periodic_mask,
         nu=_f32(nu), delta=_f32(delta), eps=_f32(eps),
         g=[_f32(x) for x in g] + [0.0] * (3 - len(g)),
         rebuild_interval=int(rebuild_interval), skin=_f32(skin), diffusion=int(diffusion),
+        shift=_f32(shift),
     )
 
 
@@ -114,7 +115,7 @@ def taylor_green_2d(n_side: int = 64, seed: int = 0, steps: int = 100, nu: float
                     c0: float = 10.0, delta: float = 0.1, jitter: float = 0.05,
                     density_mode: int = DENSITY_CONTINUITY, rebuild_interval: int = 1,
                     skin: float = 0.0, dt: float | None = None, pressure: bool = False,
-                    diffusion: int = 0) -> dict:
+                    diffusion: int = 0, shift: float = 0.0) -> dict:
     """Periodic 2D Taylor-Green vortex on the unit square (u = sin 2pi x cos 2pi y,
     v = -cos 2pi x sin 2pi y), lattice at (i+1/2)dx jittered by U[-jitter, jitter) dx,
     rho = rho0 = 1, m = rho0 dx^2, Wendland C4 with support H = 4 dx, dt = h / (4 c0) with the
@@ -128,7 +129,7 @@ def taylor_green_2d(n_side: int = 64, seed: int = 0, steps: int = 100, nu: float
     dt = 0.25 * (0.5 * _f32(H)) / c0 if dt is None else dt
     p = _params(2, KERNEL_WENDLAND4, H, dt, c0, nu, delta, (0.0, 0.0), (1.0, 1.0), 0b11,
                 density_mode=density_mode, rebuild_interval=rebuild_interval, skin=skin,
-                diffusion=diffusion)
+                diffusion=diffusion, shift=shift)
     rho = np.full(n, p["rho0"])
     if pressure:
         pr = 0.25 * (np.cos(4 * np.pi * xy[:, 0]) + np.cos(4 * np.pi * xy[:, 1]))
@@ -143,7 +144,7 @@ def taylor_green_2d(n_side: int = 64, seed: int = 0, steps: int = 100, nu: float
 def taylor_green_3d(n_side: int = 128, seed: int = 0, steps: int = 200, nu: float = 0.005,
                     c0: float = 10.0, delta: float = 0.1, jitter: float = 0.05,
                     support: float = 2.43, rebuild_interval: int = 1, skin: float = 0.0,
-                    pressure: bool = False, diffusion: int = 0) -> dict:
+                    pressure: bool = False, diffusion: int = 0, shift: float = 0.0) -> dict:
     """Periodic 3D Taylor-Green vortex in the unit cube (u = sin cos cos, v = -cos sin cos,
     w = 0), Wendland C2 with support 2.43 dx, lattice jittered by U[-jitter, jitter) dx.  With
     ``pressure`` the density carries the analytic pressure
@@ -159,7 +160,8 @@ def taylor_green_3d(n_side: int = 128, seed: int = 0, steps: int = 200, nu: floa
     v = np.stack([sx * cy * cz, -cx * sy * cz, np.zeros(n)], 1)
     H = support * dx
     p = _params(3, KERNEL_WENDLAND2, H, 0.25 * (0.5 * _f32(H)) / c0, c0, nu, delta, (0.0, 0.0, 0.0),
-                (1.0, 1.0, 1.0), 0b111, rebuild_interval=rebuild_interval, skin=skin, diffusion=diffusion)
+                (1.0, 1.0, 1.0), 0b111, rebuild_interval=rebuild_interval, skin=skin, diffusion=diffusion,
+                shift=shift)
     rho = np.full(n, p["rho0"])
     if pressure:
         pr = (1.0 / 16.0) * (np.cos(4 * np.pi * x[:, 0]) + np.cos(4 * np.pi * x[:, 1])) * \
@@ -173,7 +175,7 @@ def taylor_green_3d(n_side: int = 128, seed: int = 0, steps: int = 200, nu: floa
 
 
 def dam_break(res: int = 128, steps: int = 2000, alpha_visc: float = 0.02, delta: float = 0.1,
-              rebuild_interval: int = 1, skin: float = 0.0, diffusion: int = 0) -> dict:
+              rebuild_interval: int = 1, skin: float = 0.0, diffusion: int = 0, shift: float = 0.0) -> dict:
     """2D dam break: fluid column [0,1] x [0,2] at (i+1/2)dx in the tank [0,4] x [0,3],
     dx = 1/res, three layers of fixed wall particles at -(k+1/2)dx (left, bottom, corners
     filled) and 4+(k+1/2)dx (right), open top.  g = (0, -9.81), c0 = 10 sqrt(2 g 2.0),
@@ -213,7 +215,7 @@ def dam_break(res: int = 128, steps: int = 2000, alpha_visc: float = 0.02, delta
     rho = np.concatenate([rho_f, np.full(nw, rho0)])
     p = _params(2, KERNEL_WENDLAND4, H, 0.25 * dx / _f32(c0), c0, nu, delta,
                 (-4 * dx, -4 * dx), (4.0 + 4 * dx, 3.0), 0b00, g=(0.0, -g), rho0=rho0, gamma=gamma,
-                rebuild_interval=rebuild_interval, skin=skin, diffusion=diffusion)
+                rebuild_interval=rebuild_interval, skin=skin, diffusion=diffusion, shift=shift)
     return dict(
         name=f"dambreak_{res}", params=p, n_fluid=nf, n_wall=nw, steps=steps, seed=0, dx=dx,
         x=x.astype(np.float32), v=v.astype(np.float32), rho=rho.astype(np.float32),

@@ -1,0 +1,122 @@
+"""Oracle pins of the explicit particle shifting applied at the end of each step (the paper's
+post-processing step, citing the explicit scheme of Sun et al.):
+dx_i = -C H^2 sum_j V_j [1 + 0.2 (W_ij / W(dp))^4] grad_i W_ij in the bulk, tangential only in the
+free-surface band, none for isolated particles (lambda_i of the renormalisation matrix)."""
+import numpy as np
+import pytest
+
+import sph_inputs as si
+from tests.scenes import lattice, params, scene
+
+
+def _periodic(n=32, jitter=0.0, seed=0, shift=0.05, rho=None):
+    dx, x = lattice(n, 2)
+    rng = np.random.default_rng(seed)
+    x = (x + rng.uniform(-jitter, jitter, x.shape) * dx) % 1.0
+    p = params(H=4 * dx, periodic_mask=0b11, shift=shift)
+    return dx, scene(p, x, rho=rho, mass=np.full(len(x), dx * dx))
+
+
+def test_regular_lattice_does_not_move(orc):
+    dx, s = _periodic(32)
+    d, lam = orc.shift(s)
+    assert np.abs(d).max() < 1e-14 * dx
+    assert np.all(lam > 0.75)  # all bulk
+
+
+def test_no_net_drift_and_bulk_everywhere_in_a_periodic_box(orc):
+    """With equal masses the pair weight is symmetric and grad_i W_ij antisymmetric, so
+    sum_i V_i dx_i = 0 even for non-uniform densities; using V_i in place of V_j breaks it."""
+    rng = np.random.default_rng(2)
+    dx, s = _periodic(32, jitter=0.2, seed=1, rho=1.0 + 0.02 * rng.standard_normal(32 * 32))
+    d, lam = orc.shift(s)
+    V = s["mass"].astype(np.float64) / s["rho"].astype(np.float64)
+    assert np.all(lam > 0.75)
+    assert np.abs(d).max() > 1e-6 * dx
+    tot = (V[:, None] * d).sum(0)
+    assert np.all(np.abs(tot) < 1e-12 * (V[:, None] * np.abs(d)).sum(0))
+
+
+def test_shifting_regularises_a_disordered_lattice(orc):
+    """Repeated shifting lowers the spread of the kernel-sum density and raises the smallest
+    particle distance of a jittered periodic lattice (the purpose of shifting)."""
+    dx, s = _periodic(24, jitter=0.3, seed=4, shift=0.1)
+    x = s["x"].astype(np.float64)
+
+    def spread(x):
+        o = dict(s, x=x.astype(np.float32), params=dict(s["params"], shift=0.0, density_mode=1))
+        return np.std(orc.rates(o)["rho"])
+
+    def dmin(x):
+        r = x[:, None, :] - x[None, :, :]
+        r -= np.round(r)
+        d2 = (r ** 2).sum(-1) + np.eye(len(x))
+        return np.sqrt(d2.min())
+
+    sp0, dm0 = spread(x), dmin(x)
+    prev = sp0
+    for it in range(8):
+        d, _ = orc.shift(dict(s, x=x.astype(np.float32)))
+        x = (x + d) % 1.0
+        cur = spread(x)
+        assert cur < prev
+        prev = cur
+    assert prev < 0.5 * sp0
+    assert dmin(x) > dm0
+
+
+def test_translation_invariance_of_the_shift(orc):
+    dx, x = lattice(32, 2)
+    rng = np.random.default_rng(5)
+    x = (x + rng.integers(-500, 501, x.shape) * 2.0 ** -16) % 1.0  # dyadic, exact under the shift
+    s = scene(params(H=4 * dx, periodic_mask=0b11, shift=0.05), x, mass=np.full(len(x), dx * dx))
+    d0, _ = orc.shift(s)
+    t = np.array([0.3125, 0.5625])  # dyadic: the translated float32 positions are exact
+    x1 = (s["x"].astype(np.float64) + t) % 1.0
+    d1, _ = orc.shift(dict(s, x=x1.astype(np.float32)))
+    np.testing.assert_allclose(d1, d0, rtol=0, atol=1e-9 * np.abs(d0).max())
+
+
+def test_free_surface_band_moves_tangentially_and_isolated_particles_stay(orc):
+    """Open block (no walls) plus one far particle: the isolated particle (lambda = 0) does not
+    move; particles in the band along the top face keep almost no normal component, while bulk
+    particles move in every direction."""
+    dx, x = lattice(32, 2)
+    rng = np.random.default_rng(6)
+    x = x + rng.uniform(-0.15, 0.15, x.shape) * dx
+    x = np.vstack([x, [[0.5, 1.8]]])
+    p = params(H=4 * dx, periodic_mask=0, box_lo=(-1, -1), box_hi=(2, 3), shift=0.05)
+    s = scene(p, x, mass=np.full(len(x), dx * dx))
+    d, lam = orc.shift(s)
+    assert lam[-1] < 0.4 and np.all(d[-1] == 0.0)
+    top = (x[:-1, 1] > 1 - 1.5 * dx) & (np.abs(x[:-1, 0] - 0.5) < 0.3) & (lam[:-1] < 0.75) & (lam[:-1] >= 0.4)
+    bulk = lam[:-1] >= 0.75
+    assert top.sum() > 10 and bulk.sum() > 100
+    ny_top = np.abs(d[:-1][top][:, 1]).mean() / np.linalg.norm(d[:-1][top], axis=1).mean()
+    ny_bulk = np.abs(d[:-1][bulk][:, 1]).mean() / np.linalg.norm(d[:-1][bulk], axis=1).mean()
+    assert ny_top < 0.25 < ny_bulk
+
+
+def test_shift_moves_positions_only_at_the_end_of_the_step(orc):
+    """One step with shifting: v and rho equal the unshifted step's, and x differs by the shift
+    evaluated at the unshifted step's result."""
+    s = si.dam_break(res=16, shift=0.05)
+    s0 = dict(s, params=dict(s["params"], shift=0.0))
+    x1, v1, r1 = orc.rollout(s, 1)
+    x0, v0, r0 = orc.rollout(s0, 1)
+    assert np.array_equal(v1, v0) and np.array_equal(r1, r0)
+    nf = s["n_fluid"]
+    # the state the shift sees: post-step fluid, and the walls' density of the step's wall pass
+    mid = dict(s, x=x0.astype(np.float32), v=v0.astype(np.float32), rho=r0.astype(np.float32))
+    d, _ = orc.shift(mid)
+    np.testing.assert_allclose(x1[:nf] - x0[:nf], d, rtol=0, atol=1e-5 * np.abs(d).max())
+    assert np.array_equal(x1[nf:], x0[nf:])
+    assert np.abs(d).max() > 0
+
+
+def test_shifting_has_no_derivative_pass(orc):
+    s = si.taylor_green_2d(16, seed=0, shift=0.05)
+    n = s["n_fluid"]
+    z = np.zeros((n, 2))
+    with pytest.raises(ValueError):
+        orc.adjoint(s, 1, z, z, np.zeros(n))
