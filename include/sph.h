@@ -108,6 +108,18 @@ typedef struct sph_params {
   int32_t rebuild_interval; /* >= 1, used when skin > 0 */
   float skin;             /* Verlet skin (absolute length, >= 0) */
   int32_t diffusion;      /* SPH_DIFFUSION_* (continuity mode; no effect with summation density) */
+  float shift;            /* explicit particle shifting at the end of each step, coefficient C >= 0
+                           * (0: off).  The paper shifts in a post-processing step after each time
+                           * step, citing the explicit scheme of Sun et al. (not printed); here the
+                           * delta+-SPH form dx_i = -C H^2 sum_j V_j [1 + 0.2 (W_ij/W(dp))^4] grad_i W_ij,
+                           * dp = (m_i/rho0)^(1/d), over the neighbours at the swept positions, in
+                           * the bulk (lambda_i >= 0.75, lambda_i the smallest eigenvalue of the
+                           * renormalisation matrix), tangential to the outward normal
+                           * -sum_j V_j grad_i W_ij in the free-surface band (0.4 <= lambda_i < 0.75),
+                           * none for isolated particles.  Positions only; walls stay.  C is the
+                           * product CFL * Mach of Sun et al.  No adjoint (sph_rollout rejects it).
+                           * The shift needs cells valid for the swept positions: eager steps rebuild
+                           * twice per step, captured steps check the skin again before the shift. */
 } sph_params;
 
 typedef struct sph_scene sph_scene;
@@ -193,7 +205,8 @@ SPH_API int sph_debug_pairs(sph_scene* scene, int64_t* n_pairs, int32_t* pi, int
 /* Per-kernel device timing.  When enabled, the scene records CUDA events around its launches
  * on its stream; sph_timing returns the accumulated milliseconds and launch count of one
  * kernel class (0 = fused sweep, 1 = rebuild (keys+sort+ranges+permute), 2 = walls,
- * 3 = density, 4 = adjoint sweep, 5 = renormalised density gradient) and resets it.  Synchronises the stream. */
+ * 3 = density, 4 = adjoint sweep, 5 = renormalised density gradient, 6 = particle shifting)
+ * and resets it.  Synchronises the stream. */
 SPH_API int sph_profile(sph_scene* scene, int enable);
 SPH_API int sph_timing(sph_scene* scene, int kernel_class, double* ms, int64_t* launches);
 
@@ -228,8 +241,8 @@ SPH_API void sph_destroy(sph_scene* scene);
  * pass for the loss L = (1/N) sum_i |x_i^T - x~_i|^2 with target positions x~, Sec. 4.1) run on
  * the second stream concurrently.  A served result is bitwise the result of the scene alone.
  * Forward requests share the batch only with requests of the same dim, kernel, density mode,
- * diffusion form, skin and rebuild_interval; one of another kind waits, in arrival order, until
- * the running batch has drained.
+ * diffusion form, shifting on or off, skin and rebuild_interval; one of another kind waits, in
+ * arrival order, until the running batch has drained.
  * Results stay with the server until sph_wait returns them (once per ticket). */
 #define SPH_REQ_FORWARD 0
 #define SPH_REQ_ADJOINT 1

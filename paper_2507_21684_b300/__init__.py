@@ -26,7 +26,7 @@ SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EUNSTABLE, SPH_ETIMEOUT, SPH_EBUS
 _NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT", 6: "EBUSY", 7: "EINTERNAL"}
 
 # kernel classes of sph_timing
-TIMING_SWEEP, TIMING_REBUILD, TIMING_WALLS, TIMING_DENSITY, TIMING_ADJOINT, TIMING_GRADIENT = range(6)
+TIMING_SWEEP, TIMING_REBUILD, TIMING_WALLS, TIMING_DENSITY, TIMING_ADJOINT, TIMING_GRADIENT, TIMING_SHIFT = range(7)
 DIFFUSION_MC, DIFFUSION_RENORM = 0, 1
 
 
@@ -42,7 +42,7 @@ class Params(C.Structure):
         ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
         ("H", C.c_float), ("dt", C.c_float), ("rho0", C.c_float), ("c0", C.c_float), ("gamma", C.c_float),
         ("nu", C.c_float), ("delta", C.c_float), ("eps", C.c_float), ("g", C.c_float * 3),
-        ("rebuild_interval", C.c_int32), ("skin", C.c_float), ("diffusion", C.c_int32),
+        ("rebuild_interval", C.c_int32), ("skin", C.c_float), ("diffusion", C.c_int32), ("shift", C.c_float),
     ]
 
     @classmethod
@@ -53,6 +53,7 @@ class Params(C.Structure):
         for k in ("H", "dt", "rho0", "c0", "gamma", "nu", "delta", "eps", "skin"):
             setattr(o, k, float(p[k]))
         o.diffusion = int(p.get("diffusion", 0))
+        o.shift = float(p.get("shift", 0.0))
         for k in range(3):
             o.box_lo[k] = float(p["box_lo"][k])
             o.box_hi[k] = float(p["box_hi"][k])

@@ -43,7 +43,7 @@ struct DevSeg {
   float g[3];
   float band_lo, band_hi;  // FP32 r^2 guard band for the exact pair predicate
   double H2_d;
-  float nu, pad1;
+  float nu, shiftC;         // shiftC = C H^2 of the particle shifting (0: off)
   float cs[3];             // cell edge (FP32) of the folded frame
   float trimR2;            // squared reach used to skip neighbour cells (H + skin/2 + margins)
   float invcs[3];          // FP32 reciprocal cell edge (fast path of the cell key)

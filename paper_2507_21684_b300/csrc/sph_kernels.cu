@@ -323,16 +323,16 @@ void launch_copy_state(int N, const Arrays& src, const Arrays& dst, cudaStream_t
 // Rebuild decision of one step, taken on the device: rebuild when the cells have served
 // `interval` sweeps or when some particle has moved farther than half the skin since the last
 // build (maxr > 1, from the previous sweep).  Sets the graph's conditional and the counters.
-__global__ void k_rebuild_decide(RebuildCtl* ctl, int interval, cudaGraphConditionalHandle h) {
+__global__ void k_rebuild_decide(RebuildCtl* ctl, int interval, int count, cudaGraphConditionalHandle h) {
   const unsigned r = (ctl->since >= interval || __uint_as_float(ctl->maxr) > 1.f) ? 1u : 0u;
   cudaGraphSetConditional(h, r);
-  ctl->since = r ? 1 : ctl->since + 1;
+  ctl->since = r ? count : ctl->since + count;
   ctl->maxr = 0u;
   ctl->rebuilds += r;
   ctl->call_rebuilds += r;
 }
-void launch_rebuild_decide(RebuildCtl* ctl, int interval, cudaGraphConditionalHandle h, cudaStream_t st) {
-  k_rebuild_decide<<<1, 1, 0, st>>>(ctl, interval, h);
+void launch_rebuild_decide(RebuildCtl* ctl, int interval, int count, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_rebuild_decide<<<1, 1, 0, st>>>(ctl, interval, count, h);
 }
 template <int D>
 void launch_upload(const DevSeg* segs, int seg, int n, int nf, int p0, const float* x, const float* v, const float* rho,

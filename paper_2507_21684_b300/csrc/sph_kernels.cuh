@@ -53,7 +53,8 @@ void launch_permute(const DevSeg* segs, int N, const uint32_t* perm, const Array
                     const uint32_t* keys, int C, int* off, float4* xb, cudaStream_t st);
 template <int D>
 void launch_copy_state(int N, const Arrays& src, const Arrays& dst, cudaStream_t st);
-void launch_rebuild_decide(RebuildCtl* ctl, int interval, cudaGraphConditionalHandle h, cudaStream_t st);
+// count: 1 when a sweep follows and uses the cells (it counts towards rebuild_interval), else 0
+void launch_rebuild_decide(RebuildCtl* ctl, int interval, int count, cudaGraphConditionalHandle h, cudaStream_t st);
 template <int D>
 void launch_upload(const DevSeg* segs, int seg, int n, int nf, int p0, const float* x, const float* v,
                    const float* rho, const float* mass, const Arrays& a, cudaStream_t st);

@@ -5,6 +5,7 @@
 //   gradient        renormalised density gradient <grad rho>^L (kernel renormalisation, App. A)
 //   sweep           continuity + delta diffusion, Tait pressure, viscosity, gravity, and the
 //                   kick-drift epilogue (Sec. 2.3, Sec. 3.4); also the rate-only evaluation
+//   shift           explicit particle shifting at the end of a step (free-surface aware)
 //   pairs           exact pair export (FP64 predicate in a guard band)
 //   adjoint sweep   vector-Jacobian product of one step, gathered per particle (Sec. 2.2)
 #include <algorithm>
@@ -491,11 +492,20 @@ __device__ __forceinline__ void pinv_sym2(float a, float b, float c, float* L) {
   }
 }
 
-// pinv of a symmetric 3x3 by cyclic Jacobi rotations (Golub & Van Loan, Sec. 8.5), FP32.
-// m = (xx, xy, xz, yy, yz, zz) in and L (same packing) out.
-__device__ __forceinline__ void pinv_sym3(const float* m, float* L) {
-  float A[3][3] = {{m[0], m[1], m[2]}, {m[1], m[3], m[4]}, {m[2], m[4], m[5]}};
-  float Q[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+// Eigen-decomposition of a symmetric 3x3 by cyclic Jacobi rotations (Golub & Van Loan,
+// Sec. 8.5), FP32: A becomes diagonal (the eigenvalues), Q (if wanted) collects the eigenvectors
+// as columns.  m = (xx, xy, xz, yy, yz, zz).
+template <bool VECTORS>
+__device__ __forceinline__ void jacobi_sym3(const float* m, float A[3][3], float Q[3][3]) {
+  A[0][0] = m[0]; A[0][1] = m[1]; A[0][2] = m[2];
+  A[1][0] = m[1]; A[1][1] = m[3]; A[1][2] = m[4];
+  A[2][0] = m[2]; A[2][1] = m[4]; A[2][2] = m[5];
+  if (VECTORS) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Q[a][b] = a == b ? 1.f : 0.f;
+  }
 #pragma unroll 1
   for (int sweep = 0; sweep < 8; ++sweep) {
     const float off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
@@ -521,14 +531,22 @@ __device__ __forceinline__ void pinv_sym3(const float* m, float* L) {
         A[p][k] = c * apk - sn * aqk;
         A[q][k] = sn * apk + c * aqk;
       }
+      if (VECTORS) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float qkp = Q[k][p], qkq = Q[k][q];
-        Q[k][p] = c * qkp - sn * qkq;
-        Q[k][q] = sn * qkp + c * qkq;
+        for (int k = 0; k < 3; ++k) {
+          const float qkp = Q[k][p], qkq = Q[k][q];
+          Q[k][p] = c * qkp - sn * qkq;
+          Q[k][q] = sn * qkp + c * qkq;
+        }
       }
     }
   }
+}
+
+// pinv of a symmetric 3x3, m = (xx, xy, xz, yy, yz, zz) in and L (same packing) out.
+__device__ __forceinline__ void pinv_sym3(const float* m, float* L) {
+  float A[3][3], Q[3][3];
+  jacobi_sym3<true>(m, A, Q);
   const float lam[3] = {A[0][0], A[1][1], A[2][2]};
   const float cut = kPinvRtol * fmaxf(fabsf(lam[0]), fmaxf(fabsf(lam[1]), fabsf(lam[2])));
 #pragma unroll
@@ -771,6 +789,150 @@ struct SweepPass {
   }
 };
 
+// ================================================================== particle shifting
+// Explicit shifting at the end of a step (the paper's post-processing step; the delta+-SPH form
+// of Sun et al.), on the post-sweep state of every fluid particle:
+//   a_i = sum_j V_j [1 + R (W_ij / W(dp_i))^4] grad_i W_ij,  dx_i = -C H^2 a_i,  R = 0.2,
+//   dp_i = (m_i / rho0)^(1/d);
+// the smallest eigenvalue lambda_i of M_i = sum_j V_j (x_j - x_i) (x) grad_i W_ij selects bulk
+// (>= 0.75: dx_i), free-surface band (>= 0.4: the part of dx_i orthogonal to the outward normal
+// n_i = -c_i / |c_i|, c_i = sum_j V_j grad_i W_ij) or isolated (no shift).  The pass writes the
+// whole state into the other buffer (walls and velocities unchanged) and measures the
+// displacement since the last cell build, like the sweep.
+constexpr float kShiftR = 0.2f, kLambdaBulk = 0.75f, kLambdaSplash = 0.4f;
+
+template <int D, int KERN>
+struct ShiftPass {
+  static constexpr int NM = D * (D + 1) / 2;
+  struct Body {
+    const DevSeg* s;
+    float invW0;
+    float a[D], c[D], m[NM];
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4, float, int) {
+      float r[D];
+      const float r2 = diff<D>(xs, pj.x, r);
+      const float q = safe_q(r2, s->invH);
+      const float Vg = pj.V * (s->Kg * kern_gt<KERN>(q));
+      const float wr = s->Kw * kern_w<KERN>(q) * invW0;
+      const float w2 = wr * wr;
+      const float Vgf = Vg * fmaf(kShiftR, w2 * w2, 1.f);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        a[k] = fmaf(Vgf, r[k], a[k]);
+        c[k] = fmaf(Vg, r[k], c[k]);
+      }
+      int e = 0;
+#pragma unroll
+      for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q2 = p; q2 < D; ++q2, ++e) m[e] = fmaf(-Vg * r[p], r[q2], m[e]);
+    }
+    template <int L>
+    __device__ __forceinline__ void reduce() {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        a[k] = group_sum<L>(a[k]);
+        c[k] = group_sum<L>(c[k]);
+      }
+#pragma unroll
+      for (int e = 0; e < NM; ++e) m[e] = group_sum<L>(m[e]);
+    }
+  };
+  Arrays a, out;
+  Displace disp;
+  float dmax = 0.f;
+  // the rebuild decision of the next step, now from the shifted positions (the sweep has
+  // counted this step already)
+  __device__ __forceinline__ void last_cta() {
+    if (!disp.ctl) return;
+    RebuildCtl* c = disp.ctl;
+    const bool r = c->since >= disp.interval || __uint_as_float(*(volatile unsigned*)&c->maxr) > 1.f;
+    c->flag = r ? 1 : 0;
+    if (r) c->since = 0;
+    c->maxr = 0u;
+  }
+  __device__ __forceinline__ void flush() {
+    if (!disp.maxr) return;
+    const unsigned v = __reduce_max_sync(kFull, __float_as_uint(dmax));
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(disp.maxr, v);
+  }
+  __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) == 0; }
+  __device__ __forceinline__ void skip(int i, const TgtView& tv) {
+    store_pd<D>(out, i, load_pd_plain<D>(tv.a, tv.k));
+    store_cold<D>(out, i, load_cold<D>(tv.a, tv.k));
+    out.meta[i] = tv.a.meta[tv.k];
+  }
+  __device__ __forceinline__ const float4* tex0() const { return disp.xb; }
+  __device__ __forceinline__ const float4* tex1() const { return nullptr; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView& tv) {
+    b.s = &s;
+    const PD<D> me = load_pd_plain<D>(tv.a, tv.k);
+    const float vol = fabsf(me.m) / s.rho0;
+    const float dp = D == 2 ? sqrtf(vol) : cbrtf(vol);
+    b.invW0 = 1.f / (s.Kw * kern_w<KERN>(dp * s.invH));
+#pragma unroll
+    for (int k = 0; k < D; ++k) b.a[k] = b.c[k] = 0.f;
+#pragma unroll
+    for (int e = 0; e < NM; ++e) b.m[e] = 0.f;
+    return me.m > 0.f;  // fluid
+  }
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i, const TgtView& tv) {
+    PD<D> me = load_pd_plain<D>(tv.a, tv.k);
+    Cold c = load_cold<D>(tv.a, tv.k);
+    const uint2 m = tv.a.meta[tv.k];
+    if (me.m > 0.f && s.shiftC > 0.f) {
+      float lam;
+      if constexpr (D == 2) {
+        const float half = 0.5f * (b.m[0] - b.m[2]);
+        lam = 0.5f * (b.m[0] + b.m[2]) - sqrtf(fmaf(half, half, b.m[1] * b.m[1]));
+      } else {
+        float A[3][3], Q[3][3];
+        jacobi_sym3<false>(b.m, A, Q);
+        lam = fminf(A[0][0], fminf(A[1][1], A[2][2]));
+      }
+      float dx[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) dx[k] = lam >= kLambdaSplash ? -s.shiftC * b.a[k] : 0.f;
+      if (lam >= kLambdaSplash && lam < kLambdaBulk) {
+        float c2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) c2 = fmaf(b.c[k], b.c[k], c2);
+        if (c2 > 0.f) {
+          const float inv = rsqrtf(c2);
+          float n[D], sn = 0.f;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            n[k] = -b.c[k] * inv;
+            sn = fmaf(dx[k], n[k], sn);
+          }
+#pragma unroll
+          for (int k = 0; k < D; ++k) dx[k] = fmaf(-sn, n[k], dx[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        ds_add(c.hi[k], c.lo[k], dx[k]);
+        me.x[k] = __fadd_rn(__fsub_rn(c.hi[k], c.off[k]), c.lo[k]);
+      }
+    }
+    if (me.m > 0.f && disp.xb) {
+      const float4 xb = tv.e0[tv.k];
+      float d2;
+      if (D == 2) {
+        const float e0 = me.x[0] - xb.x, e1 = me.x[1] - xb.y;
+        d2 = fmaf(e0, e0, e1 * e1);
+      } else {
+        const float e0 = me.x[0] - xb.x, e1 = me.x[1] - xb.y, e2 = me.x[D - 1] - xb.z;
+        d2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+      }
+      dmax = fmaxf(dmax, d2 * disp.inv_r2);
+    }
+    store_pd<D>(out, i, me);
+    store_cold<D>(out, i, c);
+    out.meta[i] = m;
+  }
+};
+
 // ================================================================== pair export
 template <int D>
 struct PairPass {
@@ -988,6 +1150,15 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, (D == 3 && RENORM ? 768 :
   pass.grad = grad;
   run_tiles<D, RENORM ? 1 : 0, 0>(t, tiles, ntiles, RENORM ? grad : nullptr, nullptr, pass);
 }
+template <int D, int KERN>
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, (D == 3 ? 768 : 1024) / TileCfg<D>::THREADS) k_shift_t(TravArgs t, const Tile* tiles, const int* ntiles, Arrays out,
+                                                 Displace disp) {
+  ShiftPass<D, KERN> pass;
+  pass.a = t.a;
+  pass.out = out;
+  pass.disp = disp;
+  run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
+}
 template <int D>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_pairs_t(TravArgs t, const Tile* tiles, const int* ntiles, int32_t* pi,
                                                  int32_t* pj, unsigned long long* count, long long cap) {
@@ -1101,6 +1272,11 @@ void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int
   if (grad) launch_sweep_any<D, KERN, false, true>(t, tiles, ntiles, tiles_upper, Arrays{}, ro, Displace{}, grad, st);
   else launch_sweep_any<D, KERN, false, false>(t, tiles, ntiles, tiles_upper, Arrays{}, ro, Displace{}, nullptr, st);
 }
+template <int D, int KERN>
+void launch_shift_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
+                    const Displace& disp, cudaStream_t st) {
+  k_shift_t<D, KERN><<<pass_grid((const void*)k_shift_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, out, disp);
+}
 template <int D>
 void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
                     unsigned long long* count, long long cap, cudaStream_t st) {
@@ -1139,6 +1315,8 @@ cudaError_t configure_passes() {
   SPH_ATTR(3, (k_sweep_t<3, 0, true, true>), pass_smem<3>(1)) SPH_ATTR(3, (k_sweep_t<3, 1, true, true>), pass_smem<3>(1))
   SPH_ATTR(2, (k_sweep_t<2, 0, false, true>), pass_smem<2>(1)) SPH_ATTR(2, (k_sweep_t<2, 1, false, true>), pass_smem<2>(1))
   SPH_ATTR(3, (k_sweep_t<3, 0, false, true>), pass_smem<3>(1)) SPH_ATTR(3, (k_sweep_t<3, 1, false, true>), pass_smem<3>(1))
+  SPH_ATTR(2, (k_shift_t<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_shift_t<2, 1>), pass_smem<2>(0))
+  SPH_ATTR(3, (k_shift_t<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_shift_t<3, 1>), pass_smem<3>(0))
   SPH_ATTR(2, (k_grad_t<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_grad_t<2, 1>), pass_smem<2>(0))
   SPH_ATTR(3, (k_grad_t<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_grad_t<3, 1>), pass_smem<3>(0))
   SPH_ATTR(2, (k_pairs_t<2>), pass_smem<2>(0)) SPH_ATTR(3, (k_pairs_t<3>), pass_smem<3>(0))
@@ -1158,6 +1336,8 @@ SPH_INST_PD(3)
   template void launch_walls_t<D, K>(const TravArgs&, const Tile*, const int*, const int*, int, cudaStream_t); \
   template void launch_density_t<D, K>(const TravArgs&, const Tile*, const int*, int, cudaStream_t);        \
   template void launch_grad_t<D, K>(const TravArgs&, const Tile*, const int*, int, float4*, cudaStream_t);   \
+  template void launch_shift_t<D, K>(const TravArgs&, const Tile*, const int*, int, const Arrays&,          \
+                                     const Displace&, cudaStream_t);                                         \
   template void launch_sweep_t<D, K>(const TravArgs&, const Tile*, const int*, int, const Arrays&, const Displace&, \
                                      const float4*, cudaStream_t);                                           \
   template void launch_rates_t<D, K>(const TravArgs&, const Tile*, const int*, int, const RateOut&, const float4*, \

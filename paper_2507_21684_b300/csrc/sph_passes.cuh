@@ -26,6 +26,9 @@ void launch_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int
 template <int D, int KERN>
 void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const RateOut& ro,
                     const float4* grad, cudaStream_t st);
+template <int D, int KERN>
+void launch_shift_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
+                    const Displace& disp, cudaStream_t st);
 template <int D>
 void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
                     unsigned long long* count, long long cap, cudaStream_t st);

@@ -106,6 +106,7 @@ DevSeg make_seg(const sph_params& p, int n_fluid, int cell_base, int p0, int p1,
   if (p.kernel != 0 && p.kernel != 1) einval("kernel must be SPH_KERNEL_WENDLAND4 or SPH_KERNEL_WENDLAND2");
   if (p.density_mode != 0 && p.density_mode != 1) einval("density_mode must be 0 or 1");
   if (p.diffusion != 0 && p.diffusion != 1) einval("diffusion must be SPH_DIFFUSION_MC or SPH_DIFFUSION_RENORM");
+  if (!(p.shift >= 0.f) || !std::isfinite(p.shift)) einval("shift must be finite and >= 0");
   if (!(p.H > 0.f) || !(p.dt > 0.f) || !(p.rho0 > 0.f) || !(p.c0 > 0.f) || !(p.gamma > 0.f))
     einval("H, dt, rho0, c0 and gamma must be positive");
   if (!(p.nu >= 0.f) || !(p.eps > 0.f) || !(p.skin >= 0.f) || p.rebuild_interval < 1)
@@ -157,6 +158,7 @@ DevSeg make_seg(const sph_params& p, int n_fluid, int cell_base, int p0, int p1,
   s.gamma = p.gamma;
   s.B = (float)((double)p.rho0 * p.c0 * p.c0 / p.gamma);
   s.nu = p.nu;
+  s.shiftC = (float)((double)p.shift * (double)p.H * (double)p.H);
   s.dCv_dnu = (float)(2.0 * (d + 2) * p.rho0);
   s.Cv = (float)(2.0 * (d + 2) * p.rho0 * (double)p.nu);
   // h = H/2: the smoothing length of the delta-SPH diffusion and of the regulariser
@@ -277,6 +279,7 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
   kern = prms[0].kernel;
   summation = prms[0].density_mode == 1;
   renorm = !summation && prms[0].diffusion == 1;
+  shifting = prms[0].shift > 0.f;
   any_walls = false;
   skin = prms[0].skin;
   interval = prms[0].rebuild_interval;
@@ -289,6 +292,7 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
     if (p.dim != D || p.kernel != kern || (p.density_mode == 1) != summation)
       einval("all scenes of a batch must share dim, kernel and density mode");
     if (p.diffusion != prms[0].diffusion) einval("all scenes of a batch must share the diffusion form");
+    if ((p.shift > 0.f) != (prms[0].shift > 0.f)) einval("all scenes of a batch must agree on particle shifting");
     int n = nfs[s] + nws[s];
     if (nfs[s] < 0 || nws[s] < 0 || n < 1) einval("particle counts must be non-negative with at least one particle");
     if ((long long)N + n >= (1LL << 30)) einval("too many particles");
@@ -610,6 +614,26 @@ void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const in
   ++launches;
 }
 
+// Particle shifting at the end of the step: from buf[cur] (the sweep's result, on cells valid
+// for it) into the other buffer.
+void Scene::shift_pass() {
+  prof_begin(6);
+  const TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  const Displace dp = dev_policy ? Displace{xbuild, &d_ctl->maxr, inv_r2, use_coop ? d_ctl : nullptr, interval}
+                                 : Displace{nullptr, nullptr, 0.f, nullptr, 0};
+  if (D == 2) {
+    if (kern == 0) launch_shift_t<2, 0>(t, tiles, d_ntiles, tiles_upper, buf[1 - cur], dp, st);
+    else launch_shift_t<2, 1>(t, tiles, d_ntiles, tiles_upper, buf[1 - cur], dp, st);
+  } else {
+    if (kern == 0) launch_shift_t<3, 0>(t, tiles, d_ntiles, tiles_upper, buf[1 - cur], dp, st);
+    else launch_shift_t<3, 1>(t, tiles, d_ntiles, tiles_upper, buf[1 - cur], dp, st);
+  }
+  CKL();
+  prof_end();
+  ++launches;
+  cur = 1 - cur;
+}
+
 // Rebuild launched by the host (eager steps, cells needed by a query): permute into the other
 // buffer; the device-side policy counters restart from this build.
 void Scene::host_rebuild() {
@@ -642,6 +666,10 @@ void Scene::step_once() {
   sweep(t, buf[1 - cur]);
   cur = 1 - cur;
   ++steps_since_build;
+  if (shifting) {  // the shift needs the neighbours of the swept positions
+    host_rebuild();
+    shift_pass();
+  }
 }
 
 // A captured step whose rebuild is a conditional graph node: a one-thread kernel decides
@@ -649,6 +677,19 @@ void Scene::step_once() {
 // sorts and permutes into the other buffer and copies the result back, so the buffer parity of
 // the step does not depend on the decision.
 void Scene::step_conditional() {
+  cond_rebuild(1);
+  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  passes_before_sweep(t);
+  sweep(t, buf[1 - cur]);
+  cur = 1 - cur;
+  if (shifting) {
+    cond_rebuild(0);
+    shift_pass();
+  }
+}
+
+// The conditional rebuild node (count: whether a sweep follows and uses the cells).
+void Scene::cond_rebuild(int count) {
   prof_begin(1);
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
@@ -658,7 +699,7 @@ void Scene::step_conditional() {
   CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
   cudaGraphConditionalHandle h;
   CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-  launch_rebuild_decide(d_ctl, interval, h, st);
+  launch_rebuild_decide(d_ctl, interval, count, h, st);
   CKL();
   ++launches;
   CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
@@ -700,10 +741,6 @@ void Scene::step_conditional() {
   prof_end();
   keys_sorted = (passes % 2 == 0) ? kA : kB;
   perm = (passes % 2 == 0) ? vA : vB;
-  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
-  passes_before_sweep(t);
-  sweep(t, buf[1 - cur]);
-  cur = 1 - cur;
 }
 
 // A captured step whose rebuild is one cooperative launch that returns at once unless the
@@ -739,6 +776,18 @@ RebuildArgs Scene::coop_args(const Arrays& in, const Arrays& out, int* off, cons
 }
 
 void Scene::step_coop() {
+  coop_rebuild();
+  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  passes_before_sweep(t);
+  sweep(t, buf[1 - cur]);
+  cur = 1 - cur;
+  if (shifting) {  // the sweep's last CTA has decided whether the shift needs new cells
+    coop_rebuild();
+    shift_pass();
+  }
+}
+
+void Scene::coop_rebuild() {
   prof_begin(1);
   const RebuildArgs r = coop_args(buf[cur], buf[1 - cur], cell_off, &d_ctl->flag, 1);
   CK(D == 2 ? launch_rebuild_coop<2>(r, coop_grid, st) : launch_rebuild_coop<3>(r, coop_grid, st));
@@ -746,16 +795,16 @@ void Scene::step_coop() {
   prof_end();
   keys_sorted = (passes % 2 == 0) ? kA : kB;
   perm = (passes % 2 == 0) ? vA : vB;
-  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
-  passes_before_sweep(t);
-  sweep(t, buf[1 - cur]);
-  cur = 1 - cur;
 }
 
 // Host-side replay of the buffer schedule of one captured step (graph bookkeeping).
 void Scene::advance_schedule() {
   if (!dev_policy) cur = 1 - cur;  // the rebuild's permute
   cur = 1 - cur;                   // the sweep
+  if (shifting) {
+    if (!dev_policy) cur = 1 - cur;  // the rebuild before the shift
+    cur = 1 - cur;                   // the shift
+  }
   cells_valid = true;
   keys_sorted = (passes % 2 == 0) ? kA : kB;
   perm = (passes % 2 == 0) ? vA : vB;
@@ -863,6 +912,7 @@ void Scene::ensure_cells() {
 void Scene::rollout(int n, int k) {
   if (n < 1 || k < 1) einval("n_steps and ckpt_every must be >= 1");
   if (renorm) einval("the renormalised diffusion (SPH_DIFFUSION_RENORM) has no adjoint; use sph_step");
+  if (shifting) einval("particle shifting has no adjoint; use sph_step");
   tape_n = n;
   tape_k = k;
   int ncp = (n + k - 1) / k;

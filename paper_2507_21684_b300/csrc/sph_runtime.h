@@ -90,6 +90,7 @@ struct Scene {
   int S = 0, D = 2, kern = 0, N = 0, nf_total = 0, C_tot = 0, bits = 0, passes = 0;
   bool summation = false, any_walls = false;
   bool renorm = false;              // renormalised delta-SPH diffusion (continuity mode)
+  bool shifting = false;            // particle shifting at the end of each step
   float4* gradrho = nullptr;        // <grad rho>^L per particle, sorted order (renorm, or on request)
   float skin = 0.f;
   int interval = 1;
@@ -191,6 +192,9 @@ struct Scene {
   void step_once();
   void step_conditional();
   void step_coop();
+  void cond_rebuild(int count);
+  void coop_rebuild();
+  void shift_pass();
   RebuildArgs coop_args(const Arrays& in, const Arrays& out, int* off, const int* flag, int copy_back);
   void advance_schedule();
   void steps(int n);

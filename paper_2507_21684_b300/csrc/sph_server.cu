@@ -92,7 +92,8 @@ struct Server {
   // (the launches' template choices and the rebuild policy).
   static bool same_class(const sph_params& a, const sph_params& b) {
     return a.dim == b.dim && a.kernel == b.kernel && (a.density_mode == 1) == (b.density_mode == 1) &&
-           a.skin == b.skin && a.rebuild_interval == b.rebuild_interval && a.diffusion == b.diffusion;
+           a.skin == b.skin && a.rebuild_interval == b.rebuild_interval && a.diffusion == b.diffusion &&
+           (a.shift > 0.f) == (b.shift > 0.f);
   }
 
   void admit_locked() {
@@ -369,8 +370,8 @@ int sph_submit(sph_server* sv, const sph_request* rq, uint64_t* ticket) {
     return SPH_EINVAL;
   }
   if (rq->mode == SPH_REQ_ADJOINT && (r->nw != 0 || rq->params.density_mode != SPH_DENSITY_CONTINUITY ||
-                                      rq->params.diffusion != SPH_DIFFUSION_MC)) {
-    sph::set_err("sph_submit: adjoint requests need continuity mode, the MC diffusion and no wall particles");
+                                      rq->params.diffusion != SPH_DIFFUSION_MC || rq->params.shift > 0.f)) {
+    sph::set_err("sph_submit: adjoint requests need continuity mode, the MC diffusion, no shifting and no wall particles");
     return SPH_EINVAL;
   }
   const size_t nd = (size_t)r->n * r->d;
