@@ -179,6 +179,7 @@ def run_forward(sph, torch, spec, steps, warmup, flush_l2: bool, stream, prof_st
     sc.timing(sph.TIMING_REBUILD)
     sc.timing(sph.TIMING_WALLS)
     sc.timing(sph.TIMING_GRADIENT)
+    sc.timing(sph.TIMING_SHIFT)
     for k in range(prof_steps):
         if flush:
             flush()
@@ -188,11 +189,12 @@ def run_forward(sph, torch, spec, steps, warmup, flush_l2: bool, stream, prof_st
     reb_ms, reb_n = sc.timing(sph.TIMING_REBUILD)
     wall_ms, wall_n = sc.timing(sph.TIMING_WALLS)
     grad_ms, grad_n = sc.timing(sph.TIMING_GRADIENT)
+    shift_ms, shift_n = sc.timing(sph.TIMING_SHIFT)
     sc.close()
     return dict(ms=ms, pairs_per_step=pairs_per_step, launches=st1["launches"] - st0["launches"],
                 rebuilds=st1["rebuilds"] - st0["rebuilds"], sweep_ms=sweep_ms / max(sweep_n, 1), sweep_n=sweep_n,
                 rebuild_ms=reb_ms / max(reb_n, 1), walls_ms=wall_ms / max(wall_n, 1),
-                gradient_ms=grad_ms / max(grad_n, 1))
+                gradient_ms=grad_ms / max(grad_n, 1), shift_ms=shift_ms / max(shift_n, 1))
 
 
 def run_e2e(sph, torch, spec, n_steps, reps):
@@ -353,7 +355,8 @@ def main():
                     help="--profile-run: Verlet skin as a fraction of H (default: 0.02 dam break, 0 3D)")
     ap.add_argument("--diffusion", type=int, default=0, choices=[0, 1],
                     help="--profile-run: 0 Molteni-Colagrossi, 1 renormalised delta-SPH diffusion")
-    ap.add_argument("--stream-scenes", type=int, default=64, help="requests of the served mixed-size stream")
+    ap.add_argument("--shift", type=float, default=0.0, help="--profile-run: particle shifting coefficient")
+    ap.add_argument("--stream-scenes", type=int, default=512, help="requests of the served mixed-size stream")
     ap.add_argument("--stream-rates", type=float, nargs="*", default=[20.0, 80.0, 320.0])
     args = ap.parse_args()
     ws, rank = _dist()
@@ -369,10 +372,11 @@ def main():
         sp = (si.dam_break(res=128, diffusion=args.diffusion) if args.workload == "dambreak"
               else si.taylor_green_3d(128, seed=0, diffusion=args.diffusion))
         skin = args.skin if args.skin is not None else (0.02 if args.workload == "dambreak" else 0.0)
-        sp = dict(sp, params=tune.with_skin(sp, skin)["params"])
+        sp = dict(sp, params=dict(tune.with_skin(sp, skin)["params"], shift=args.shift))
         r = run_forward(sph, torch, sp, args.steps, args.warmup, args.workload == "dambreak", torch.cuda.Stream(),
                         prof_steps=0, eager=args.eager)
-        print(json.dumps({"profile_run": args.workload, "diffusion": args.diffusion, "skin_over_H": skin,
+        print(json.dumps({"profile_run": args.workload, "diffusion": args.diffusion, "shift": args.shift,
+                          "skin_over_H": skin,
                           "eager": args.eager,
                           "ms_per_step": sum(r["ms"]) / len(r["ms"]), "pairs_per_step": r["pairs_per_step"]}))
         return
@@ -455,6 +459,16 @@ def main():
             "pair_interactions_per_s": fr["pairs_per_step"] * args.steps / tr,
             "sweep_ms": fr["sweep_ms"], "gradient_ms": fr["gradient_ms"], "walls_ms": fr["walls_ms"],
             "l2": "flushed between timed steps"}
+        # ... and with both next-row features: renormalised diffusion and particle shifting
+        ss = dict(sr, params=dict(sr["params"], shift=float(np.float32(0.05))))
+        fs = run_forward(sph, torch, ss, args.steps, args.warmup, True, torch.cuda.Stream())
+        ts = sum(fs["ms"]) / 1e3
+        extras["dambreak_128_renorm_shift"] = {
+            "diffusion": "renormalised", "shift": "explicit, C = 0.05, free-surface band tangential",
+            "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * ts / args.steps,
+            "pair_interactions_per_s": fs["pairs_per_step"] * args.steps / ts,
+            "sweep_ms": fs["sweep_ms"], "gradient_ms": fs["gradient_ms"], "shift_ms": fs["shift_ms"],
+            "rebuilds_in_timed_region": fs["rebuilds"], "l2": "flushed between timed steps"}
         sa = si.adjoint_problem(128)
         ad = run_adjoint(sph, torch, sa, 200, 20)
         extras["adjoint_128"] = {

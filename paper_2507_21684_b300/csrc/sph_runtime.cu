@@ -618,7 +618,8 @@ void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const in
 // for it) into the other buffer.
 void Scene::shift_pass() {
   prof_begin(6);
-  const TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  t.pair_count = nullptr;  // pair counts are those of the sweep
   const Displace dp = dev_policy ? Displace{xbuild, &d_ctl->maxr, inv_r2, use_coop ? d_ctl : nullptr, interval}
                                  : Displace{nullptr, nullptr, 0.f, nullptr, 0};
   if (D == 2) {
