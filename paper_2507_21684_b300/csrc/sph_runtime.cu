@@ -576,8 +576,8 @@ void Scene::passes_before_sweep(const TravArgs& t_in, const Tile* tl, const int*
   }
   TravArgs t = t_in;
   t.pair_count = nullptr;  // pair counts are those of the sweep (fluid targets) only
-  if (any_walls) walls_pass(t, tl);
-  if (renorm) grad_pass(t, tl, ntl);
+  // the step's order (Sec. 3.4): summation density of the fluid, then the walls' pressure from
+  // the fluid's, then the gradients that need both
   if (summation) {
     prof_begin(3);
     if (D == 2) {
@@ -591,6 +591,8 @@ void Scene::passes_before_sweep(const TravArgs& t_in, const Tile* tl, const int*
     prof_end();
     ++launches;
   }
+  if (any_walls) walls_pass(t, tl);
+  if (renorm) grad_pass(t, tl, ntl);
 }
 
 void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const int* ntl) {

@@ -115,6 +115,10 @@ def _snapshot(orc, s, steps):
     return dict(s, x=xo.astype(np.float32), v=vo.astype(np.float32), rho=ro.astype(np.float32))
 
 
+def _summation(s):
+    return dict(s, params=dict(s["params"], density_mode=1))
+
+
 RATE_CASES = {
     "tgv2d_64_t0": lambda orc: si.taylor_green_2d(64, seed=0),
     "tgv2d_64_pressure_t0": lambda orc: si.taylor_green_2d(64, seed=6, pressure=True),
@@ -122,6 +126,7 @@ RATE_CASES = {
     "dambreak_64_t20": lambda orc: _snapshot(orc, si.dam_break(res=64), 20),
     "tgv3d_24_t10": lambda orc: _snapshot(orc, si.taylor_green_3d(24, seed=2), 10),
     "tgv2d_48_summation_t10": lambda orc: _snapshot(orc, si.taylor_green_2d(48, seed=1, density_mode=1), 10),
+    "dambreak_48_summation_t10": lambda orc: _snapshot(orc, _summation(si.dam_break(res=48)), 10),
 }
 
 
@@ -144,6 +149,7 @@ ROLL_CASES = {
     "dambreak_128_full": lambda: si.dam_break(res=128),
     "tgv3d_32": lambda: si.taylor_green_3d(32, seed=1),
     "tgv2d_32_summation": lambda: si.taylor_green_2d(32, seed=2, density_mode=1),
+    "dambreak_64_summation": lambda: _summation(si.dam_break(res=64)),
     "tgv2d_32_verlet": lambda: si.taylor_green_2d(32, seed=2, skin=0.02, rebuild_interval=5),
 }
 
