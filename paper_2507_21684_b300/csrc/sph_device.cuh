@@ -197,15 +197,16 @@ struct PD {
   float x[D], v[D], rho, p, V, m;
 };
 
-template <int D>
+// (COH: through L2 only, for records another CTA of the same launch may have rewritten)
+template <int D, bool COH = false>
 __device__ __forceinline__ PD<D> load_pd(const Arrays& a, int j) {
   PD<D> r;
-  float4 A = __ldg(a.A + j), B = __ldg(a.B + j);
+  float4 A = COH ? __ldcg(a.A + j) : __ldg(a.A + j), B = COH ? __ldcg(a.B + j) : __ldg(a.B + j);
   if (D == 2) {
     r.x[0] = A.x; r.x[1] = A.y; r.v[0] = A.z; r.v[1] = A.w;
     r.rho = B.x; r.p = B.y; r.V = B.z; r.m = B.w;
   } else {
-    float2 C = __ldg(a.C + j);
+    float2 C = COH ? __ldcg(a.C + j) : __ldg(a.C + j);
     r.x[0] = A.x; r.x[1] = A.y; r.x[2] = A.z; r.V = A.w;
     r.v[0] = B.x; r.v[1] = B.y; r.v[2] = B.z; r.p = B.w;
     r.rho = C.x; r.m = C.y;

@@ -1,6 +1,7 @@
 // Neighbour passes of the WCSPH step on the cell-block tiles (sph_tiles.cuh):
 //   tile table      (built after every rebuild from the cell offsets)
 //   walls           Shepard extrapolation of the fluid pressure onto wall particles
+//   walls + sweep   both in one launch (wall tiles first; sweep tiles near walls wait for them)
 //   density         summation density rho_i = sum_j m_j W_ij            (Sec. 2.3)
 //   gradient        renormalised density gradient <grad rho>^L (kernel renormalisation, App. A)
 //   sweep           continuity + delta diffusion, Tait pressure, viscosity, gravity, and the
@@ -15,6 +16,9 @@
 #include "sph_tilebuild.cuh"
 
 namespace sph {
+
+// Bounded wait of a sweep tile on the wall tasks of the fused kernel: ~0.1 s, then status bit 1.
+constexpr long long kGateSpins = 1LL << 22;
 
 // ================================================================== tile table
 // (builders in sph_tilebuild.cuh)
@@ -195,7 +199,7 @@ __device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s
 
 // Fallback for tiles whose staged region does not fit: the target's own 3^d cells straight from
 // global memory, one thread per target (the caller lets only lane 0 of the group do this).
-template <int D, int SELF, class Body>
+template <int D, int SELF, bool COH, class Body>
 __device__ int gather_global(const DevSeg& s, const Arrays& a, const uint32_t* __restrict__ keys,
                              const int* __restrict__ cell_off, const float4* __restrict__ extra0,
                              const float* __restrict__ extra1, int i, const float* xi, Body& body) {
@@ -218,7 +222,7 @@ __device__ int gather_global(const DevSeg& s, const Arrays& a, const uint32_t* _
         if (skip) continue;
         const int cell = s.cell_base + (cc[2] * s.n[1] + cc[1]) * s.n[0] + cc[0];
         for (int j = cell_off[cell]; j < cell_off[cell + 1]; ++j) {
-          const PD<D> pj = load_pd<D>(a, j);
+          const PD<D> pj = load_pd<D, COH>(a, j);
           float r[D];
           const float r2 = separation<D>(s, xi, pj.x, r);
           bool in;
@@ -259,74 +263,92 @@ __device__ __forceinline__ double group_sum(double v) {
   return v;
 }
 
-// Common skeleton of a tiled pass: for each tile, stage, gather per target, reduce, epilogue.
-// Body must provide: init(s, me, i), pair(...), reduce<LANES>(), finish(...) via the Pass.
-template <int D, int E, int SELF, class Pass>
-__device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restrict__ tiles, const int* __restrict__ ntiles,
-                                          const float4* __restrict__ extra0, const float* __restrict__ extra1,
-                                          Pass& pass, const int* __restrict__ tile_list = nullptr) {
+// One tile of a pass: stage, gather per target, reduce, epilogue (or skip).  Returns the pairs
+// evaluated by this thread.  gate (fused wall + sweep kernel): the tile may read records that the
+// launch's wall tasks rewrite; unless all gate_n wall tasks had finished when the tile started,
+// a tile whose staged region holds a wall particle (or that falls back to global memory) waits
+// for them (bounded) and stages again, through L2 (COH).  A tile without a target of the pass
+// does not wait: the fused sweep's skip touches nothing.
+template <int D, int E, int SELF, bool COH, class Pass>
+__device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileSmem<D, E>& sm,
+                                         const float4* __restrict__ extra0, const float* __restrict__ extra1,
+                                         Pass& pass, const unsigned* gate = nullptr, unsigned gate_n = 0) {
   using Cfg = TileCfg<D>;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  TileSmem<D, E>& sm = *reinterpret_cast<TileSmem<D, E>*>(smraw);
-  __shared__ int s_tile;
-  const int nt = *ntiles;
+  __shared__ int s_ready;
+  const DevSeg& s = t.segs[T.seg];
   const int tgt = threadIdx.x / Cfg::LANES;
   const int lane = threadIdx.x % Cfg::LANES;
-  long long pairs_cta = 0;
-  // tiles are handed out dynamically (one atomic per CTA and tile) after a first tile per CTA
-  // by block index: load balance whatever the occupancy and the tile sizes, and no atomic on the
-  // first tile's path
-  int ti = blockIdx.x;
-  while (ti < nt) {
-    const Tile T = tiles[tile_list ? tile_list[ti] : ti];  // a list selects a subset of the tiles
-    const DevSeg& s = t.segs[T.seg];
-    const int i = T.p0 + tgt;
-    const bool valid = i < T.p1;
-    // the targets' own records go to the cache while the neighbours are staged; the key and the
-    // meta word (for the skip decision) are requested now so that their loads overlap too
-    fill_target_cache<D>(sm.tc, t.a, pass.tex0(), pass.tex1(), T.p0, T.p1 - T.p0);
-    const int key = valid ? (int)t.keys[i] : 0;
-    // tiles without a target of this pass (walls only, fluid only) are skipped unstaged
-    const bool want = valid && lane == 0 && Pass::wants(t.a.meta[i].x);
-    const int stg = stage_tile<D, E>(sm, s, T, t.a, t.cell_off, extra0, extra1, want);
-    const TgtView tv{sm.tc.view(), sm.tc.E0, sm.tc.E1, tgt};
-    if (stg >= 0) {
-      const bool staged = stg > 0;
-      typename Pass::Body body;
-      bool active = false;
-      int ccol = 0;
-      float xi[3] = {0.f, 0.f, 0.f}, flo[3] = {0.f, 0.f, 0.f}, fhi[3] = {0.f, 0.f, 0.f};
-      if (valid) {
-        active = pass.init(body, s, i, tv);
-        const float4 A = tv.a.A[tgt];
-        xi[0] = A.x; xi[1] = A.y; xi[2] = A.z;
-        const int c[3] = {key - (s.cell_base + (T.cz * s.n[1] + T.cy) * s.n[0]), T.cy, T.cz};
-        ccol = c[0] - (staged ? sm.colbase : 0);
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-          flo[q] = s.lo[q] + s.cs[q] * (float)c[q];
-          fhi[q] = flo[q] + s.cs[q];
-        }
-      }
-      int np = 0;
-      if (active) {
-        if (staged)
-          np = gather_staged<D, E, SELF>(sm, s, t.a, i, ccol, xi, flo, fhi, body);
-        else if (lane == 0)
-          np = gather_global<D, SELF>(s, t.a, t.keys, t.cell_off, extra0, extra1, i, xi, body);
-      }
-      __syncwarp();
-      body.template reduce<Cfg::LANES>();
-      if (valid && lane == 0) pass.finish(body, s, i, tv);
-      pairs_cta += np;
-    } else if (valid && lane == 0) {
-      pass.skip(i, tv);
-    }
-    __syncthreads();  // shared memory is restaged for the next tile
-    if (threadIdx.x == 0) s_tile = gridDim.x + atomicAdd(t.tile_ctr, 1);
-    __syncthreads();
-    ti = s_tile;
+  const int i = T.p0 + tgt;
+  const bool valid = i < T.p1;
+  if (gate && threadIdx.x == 0) {
+    s_ready = *(volatile const unsigned*)gate >= gate_n;
+    __threadfence();
   }
+  // the targets' own records go to the cache while the neighbours are staged; the key and the
+  // meta word (for the skip decision) are requested now so that their loads overlap too
+  fill_target_cache<D, COH>(sm.tc, t.a, pass.tex0(), pass.tex1(), T.p0, T.p1 - T.p0);
+  const int key = valid ? (int)t.keys[i] : 0;
+  // tiles without a target of this pass (walls only, fluid only) are skipped unstaged
+  const bool want = valid && lane == 0 && Pass::wants(t.a.meta[i].x);
+  int seen = 1;
+  int stg = stage_tile<D, E, COH>(sm, s, T, t.a, t.cell_off, extra0, extra1, want, gate ? &seen : nullptr);
+  if (gate && !s_ready && (stg == 0 || (stg == 1 && seen))) {  // uniform over the CTA (barrier results)
+    if (threadIdx.x == 0) {
+      long long it = 0;
+      while (*(volatile const unsigned*)gate < gate_n) {
+        if (++it > kGateSpins) {
+          atomicOr(t.status, 2);
+          break;
+        }
+        __nanosleep(32);
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    fill_target_cache<D, COH>(sm.tc, t.a, pass.tex0(), pass.tex1(), T.p0, T.p1 - T.p0);
+    stg = stage_tile<D, E, COH>(sm, s, T, t.a, t.cell_off, extra0, extra1, want);
+  }
+  const TgtView tv{sm.tc.view(), sm.tc.E0, sm.tc.E1, tgt};
+  int np = 0;
+  if (stg >= 0) {
+    const bool staged = stg > 0;
+    typename Pass::Body body;
+    bool active = false;
+    int ccol = 0;
+    float xi[3] = {0.f, 0.f, 0.f}, flo[3] = {0.f, 0.f, 0.f}, fhi[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+      active = pass.init(body, s, i, tv);
+      const float4 A = tv.a.A[tgt];
+      xi[0] = A.x; xi[1] = A.y; xi[2] = A.z;
+      const int c[3] = {key - (s.cell_base + (T.cz * s.n[1] + T.cy) * s.n[0]), T.cy, T.cz};
+      ccol = c[0] - (staged ? sm.colbase : 0);
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        flo[q] = s.lo[q] + s.cs[q] * (float)c[q];
+        fhi[q] = flo[q] + s.cs[q];
+      }
+    }
+    if (active) {
+      if (staged)
+        np = gather_staged<D, E, SELF>(sm, s, t.a, i, ccol, xi, flo, fhi, body);
+      else if (lane == 0)
+        np = gather_global<D, SELF, COH>(s, t.a, t.keys, t.cell_off, extra0, extra1, i, xi, body);
+    }
+    __syncwarp();
+    body.template reduce<Cfg::LANES>();
+    if (valid && lane == 0) pass.finish(body, s, i, tv);
+  } else if (valid && lane == 0) {
+    pass.skip(i, tv);
+  }
+  return np;
+}
+
+// The end of a tiled launch: the pass's partial results, the pair count, and the last CTA to
+// finish zeroes the tile counters (ctr[0] task counter, ctr[1] finished CTAs, ctr[2] finished
+// wall tasks of the fused kernel) for the next launch: every CTA has taken its last task index,
+// and flushed its partial results, before it counts itself done.
+template <class Pass>
+__device__ __forceinline__ void end_tiles(const TravArgs& t, Pass& pass, long long pairs_cta) {
   pass.flush();
   if (t.pair_count) {
     long long v = pairs_cta;
@@ -334,9 +356,6 @@ __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restr
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(t.pair_count, (unsigned long long)v);
   }
-  // the last CTA to finish zeroes the tile counter (and its own) for the next tiled launch:
-  // every CTA has taken its last tile index, and flushed its partial results, before it counts
-  // itself done
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -344,9 +363,34 @@ __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restr
       __threadfence();
       t.tile_ctr[0] = 0;
       t.tile_ctr[1] = 0;
+      t.tile_ctr[2] = 0;
       pass.last_cta();
     }
   }
+}
+
+// Common skeleton of a tiled pass: tiles are handed out dynamically (one atomic per CTA and tile)
+// after a first tile per CTA by block index: load balance whatever the occupancy and the tile
+// sizes, and no atomic on the first tile's path.  A list selects a subset of the tiles.
+template <int D, int E, int SELF, class Pass>
+__device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restrict__ tiles, const int* __restrict__ ntiles,
+                                          const float4* __restrict__ extra0, const float* __restrict__ extra1,
+                                          Pass& pass, const int* __restrict__ tile_list = nullptr) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TileSmem<D, E>& sm = *reinterpret_cast<TileSmem<D, E>*>(smraw);
+  __shared__ int s_tile;
+  const int nt = *ntiles;
+  long long pairs_cta = 0;
+  int ti = blockIdx.x;
+  while (ti < nt) {
+    const Tile T = tiles[tile_list ? tile_list[ti] : ti];
+    pairs_cta += tile_task<D, E, SELF, false>(t, T, sm, extra0, extra1, pass);
+    __syncthreads();  // shared memory is restaged for the next tile
+    if (threadIdx.x == 0) s_tile = gridDim.x + atomicAdd(t.tile_ctr, 1);
+    __syncthreads();
+    ti = s_tile;
+  }
+  end_tiles(t, pass, pairs_cta);
 }
 
 // ================================================================== walls
@@ -376,6 +420,7 @@ struct WallPass {
     }
   };
   Arrays a;
+  Arrays out{};  // optional: the records are written here too
   // superset of the targets init() activates, from the meta word alone
   __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) != 0; }
   __device__ __forceinline__ void skip(int, const TgtView&) {}
@@ -393,7 +438,8 @@ struct WallPass {
     return (m.x & kWallBit) != 0;
   }
   __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i, const TgtView& tv) {
-    if (!(tv.a.meta[tv.k].x & kWallBit)) return;
+    const uint2 m = tv.a.meta[tv.k];
+    if (!(m.x & kWallBit)) return;
     const float pw = b.sW > 0.f ? (b.sp + b.sh) / b.sW : 0.f;
     const float rw = tait_rho(s, pw);
     PD<D> me = load_pd_plain<D>(tv.a, tv.k);
@@ -401,6 +447,11 @@ struct WallPass {
     me.p = pw;
     me.V = fabsf(me.m) / rw;
     store_pd<D>(a, i, me);
+    if (out.A) {  // the step's output buffer as well (the fused sweep does not copy walls)
+      store_pd<D>(out, i, me);
+      store_cold<D>(out, i, load_cold<D>(tv.a, tv.k));
+      out.meta[i] = m;
+    }
   }
 };
 
@@ -632,7 +683,9 @@ struct GradPass {
 //  Cv = 2(d+2) nu rho0, Cdel = delta h c0): the paper's terms regrouped per pair.
 // RENORM: the renormalised diffusion, rho_j - rho_i -> rho_j - rho_i + (g_i + g_j).r / 2 with
 // g = <grad rho>^L of both ends (g_j staged with the neighbour records, g_i in the target cache).
-template <int D, int KERN, bool INTEGRATE, bool RENORM>
+// FUSED: the wall tasks of the same launch write the wall records of the output, so the sweep
+// writes fluid targets only (and skips tiles without fluid without touching them).
+template <int D, int KERN, bool INTEGRATE, bool RENORM, bool FUSED = false>
 struct SweepPass {
   struct Body {
     const DevSeg* s;
@@ -698,7 +751,7 @@ struct SweepPass {
   // fluid targets only (walls carry m <= 0); a skipped wall keeps its state
   __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) == 0; }
   __device__ __forceinline__ void skip(int i, const TgtView& tv) {
-    if (!INTEGRATE) return;
+    if (!INTEGRATE || FUSED) return;
     store_pd<D>(out, i, load_pd_plain<D>(tv.a, tv.k));
     store_cold<D>(out, i, load_cold<D>(tv.a, tv.k));
     out.meta[i] = tv.a.meta[tv.k];
@@ -782,6 +835,8 @@ struct SweepPass {
 #pragma unroll
       for (int k = 0; k < D; ++k) bad |= !isfinite(c.hi[k]) || !isfinite(me.v[k]);
       if (bad) atomicOr(status, 1);
+    } else if (FUSED) {
+      return;  // a wall: written by its wall task
     }
     store_pd<D>(out, i, me);
     store_cold<D>(out, i, c);
@@ -1131,6 +1186,48 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREAD
   pass.a = t.a;
   run_tiles<D, 0, 1>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
+// Wall pass and sweep in one launch: the wall tiles are the first tasks of the shared task counter
+// (so every wall task is held by a running CTA before any sweep task waits on it), the sweep tiles
+// follow; a sweep tile whose staged region holds no wall particle runs at once, the others wait
+// for the wall tasks to finish (tile_task's gate).  Same results as the two launches.
+template <int D, int KERN>
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_walls_sweep_t(TravArgs t, const Tile* tiles, const int* ntiles,
+                                                 const int* wall_tiles, const int* n_wall_tiles, Arrays out, Displace disp) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TileSmem<D, 0>& sm = *reinterpret_cast<TileSmem<D, 0>*>(smraw);
+  __shared__ int s_task;
+  WallPass<D, KERN> wp;
+  wp.a = t.a;
+  wp.out = out;
+  SweepPass<D, KERN, true, false, true> sp;
+  sp.a = t.a;
+  sp.out = out;
+  sp.ro = RateOut{};
+  sp.status = t.status;
+  sp.disp = disp;
+  sp.grad = nullptr;
+  const int nw = *n_wall_tiles, nt = *ntiles;
+  unsigned* gate = reinterpret_cast<unsigned*>(t.tile_ctr + 2);
+  long long pairs_cta = 0;
+  while (true) {
+    if (threadIdx.x == 0) s_task = atomicAdd(t.tile_ctr, 1);
+    __syncthreads();
+    const int task = s_task;
+    if (task >= nw + nt) break;
+    if (task < nw) {
+      tile_task<D, 0, 0, false>(t, tiles[wall_tiles[task]], sm, nullptr, nullptr, wp);
+      __syncthreads();  // every wall record of the tile is written
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(gate, 1u);
+      }
+    } else {
+      pairs_cta += tile_task<D, 0, 0, true>(t, tiles[task - nw], sm, nullptr, nullptr, sp, gate, (unsigned)nw);
+      __syncthreads();
+    }
+  }
+  end_tiles(t, sp, pairs_cta);
+}
 template <int D, int KERN>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_grad_t(TravArgs t, const Tile* tiles, const int* ntiles, float4* grad) {
   GradPass<D, KERN> pass;
@@ -1250,6 +1347,13 @@ void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, i
   k_density_t<D, KERN><<<pass_grid((const void*)k_density_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles);
 }
 template <int D, int KERN>
+void launch_walls_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, const int* wall_tiles,
+                          const int* n_wall_tiles, int tiles_upper, const Arrays& out, const Displace& disp,
+                          cudaStream_t st) {
+  k_walls_sweep_t<D, KERN><<<pass_grid((const void*)k_walls_sweep_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(
+      t, tiles, ntiles, wall_tiles, n_wall_tiles, out, disp);
+}
+template <int D, int KERN>
 void launch_grad_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, float4* grad,
                    cudaStream_t st) {
   k_grad_t<D, KERN><<<pass_grid((const void*)k_grad_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, grad);
@@ -1315,6 +1419,8 @@ cudaError_t configure_passes() {
   SPH_ATTR(3, (k_sweep_t<3, 0, true, true>), pass_smem<3>(1)) SPH_ATTR(3, (k_sweep_t<3, 1, true, true>), pass_smem<3>(1))
   SPH_ATTR(2, (k_sweep_t<2, 0, false, true>), pass_smem<2>(1)) SPH_ATTR(2, (k_sweep_t<2, 1, false, true>), pass_smem<2>(1))
   SPH_ATTR(3, (k_sweep_t<3, 0, false, true>), pass_smem<3>(1)) SPH_ATTR(3, (k_sweep_t<3, 1, false, true>), pass_smem<3>(1))
+  SPH_ATTR(2, (k_walls_sweep_t<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_walls_sweep_t<2, 1>), pass_smem<2>(0))
+  SPH_ATTR(3, (k_walls_sweep_t<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_walls_sweep_t<3, 1>), pass_smem<3>(0))
   SPH_ATTR(2, (k_shift_t<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_shift_t<2, 1>), pass_smem<2>(0))
   SPH_ATTR(3, (k_shift_t<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_shift_t<3, 1>), pass_smem<3>(0))
   SPH_ATTR(2, (k_grad_t<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_grad_t<2, 1>), pass_smem<2>(0))
@@ -1336,6 +1442,8 @@ SPH_INST_PD(3)
   template void launch_walls_t<D, K>(const TravArgs&, const Tile*, const int*, const int*, int, cudaStream_t); \
   template void launch_density_t<D, K>(const TravArgs&, const Tile*, const int*, int, cudaStream_t);        \
   template void launch_grad_t<D, K>(const TravArgs&, const Tile*, const int*, int, float4*, cudaStream_t);   \
+  template void launch_walls_sweep_t<D, K>(const TravArgs&, const Tile*, const int*, const int*, const int*, int, \
+                                           const Arrays&, const Displace&, cudaStream_t);                    \
   template void launch_shift_t<D, K>(const TravArgs&, const Tile*, const int*, int, const Arrays&,          \
                                      const Displace&, cudaStream_t);                                         \
   template void launch_sweep_t<D, K>(const TravArgs&, const Tile*, const int*, int, const Arrays&, const Displace&, \

@@ -17,6 +17,10 @@ void launch_wall_tiles(const Tile* tiles, const int* ntiles, int tiles_upper, co
 template <int D, int KERN>
 void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st);
 template <int D, int KERN>
+void launch_walls_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, const int* wall_tiles,
+                          const int* n_wall_tiles, int tiles_upper, const Arrays& out, const Displace& disp,
+                          cudaStream_t st);
+template <int D, int KERN>
 void launch_grad_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, float4* grad,
                    cudaStream_t st);
 // grad != nullptr selects the renormalised diffusion (gradients from launch_grad_t)

@@ -569,7 +569,7 @@ void Scene::grad_pass(const TravArgs& t, const Tile* tl, const int* ntl) {
   ++launches;
 }
 
-void Scene::passes_before_sweep(const TravArgs& t_in, const Tile* tl, const int* ntl) {
+void Scene::passes_before_sweep(const TravArgs& t_in, const Tile* tl, const int* ntl, bool fused_walls) {
   if (!tl) {
     tl = tiles;
     ntl = d_ntiles;
@@ -591,11 +591,11 @@ void Scene::passes_before_sweep(const TravArgs& t_in, const Tile* tl, const int*
     prof_end();
     ++launches;
   }
-  if (any_walls) walls_pass(t, tl);
+  if (any_walls && !fused_walls) walls_pass(t, tl);
   if (renorm) grad_pass(t, tl, ntl);
 }
 
-void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const int* ntl) {
+void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const int* ntl, bool fused_walls) {
   if (!tl) {
     tl = tiles;
     ntl = d_ntiles;
@@ -604,7 +604,15 @@ void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const in
   const Displace dp = dev_policy ? Displace{xbuild, &d_ctl->maxr, inv_r2, use_coop ? d_ctl : nullptr, interval}
                                  : Displace{nullptr, nullptr, 0.f, nullptr, 0};
   const float4* g = renorm ? gradrho : nullptr;
-  if (D == 2) {
+  if (fused_walls) {
+    if (D == 2) {
+      if (kern == 0) launch_walls_sweep_t<2, 0>(t, tl, ntl, wall_tiles, d_nwall, tiles_upper, out, dp, st);
+      else launch_walls_sweep_t<2, 1>(t, tl, ntl, wall_tiles, d_nwall, tiles_upper, out, dp, st);
+    } else {
+      if (kern == 0) launch_walls_sweep_t<3, 0>(t, tl, ntl, wall_tiles, d_nwall, tiles_upper, out, dp, st);
+      else launch_walls_sweep_t<3, 1>(t, tl, ntl, wall_tiles, d_nwall, tiles_upper, out, dp, st);
+    }
+  } else if (D == 2) {
     if (kern == 0) launch_sweep_t<2, 0>(t, tl, ntl, tiles_upper, out, dp, g, st);
     else launch_sweep_t<2, 1>(t, tl, ntl, tiles_upper, out, dp, g, st);
   } else {
@@ -665,8 +673,8 @@ void Scene::step_once() {
   }
   host_rebuild();
   TravArgs t = trav(buf[cur], keys_sorted, cell_off);
-  passes_before_sweep(t);
-  sweep(t, buf[1 - cur]);
+  passes_before_sweep(t, nullptr, nullptr, walls_in_sweep());
+  sweep(t, buf[1 - cur], nullptr, nullptr, walls_in_sweep());
   cur = 1 - cur;
   ++steps_since_build;
   if (shifting) {  // the shift needs the neighbours of the swept positions
@@ -682,8 +690,8 @@ void Scene::step_once() {
 void Scene::step_conditional() {
   cond_rebuild(1);
   TravArgs t = trav(buf[cur], keys_sorted, cell_off);
-  passes_before_sweep(t);
-  sweep(t, buf[1 - cur]);
+  passes_before_sweep(t, nullptr, nullptr, walls_in_sweep());
+  sweep(t, buf[1 - cur], nullptr, nullptr, walls_in_sweep());
   cur = 1 - cur;
   if (shifting) {
     cond_rebuild(0);
@@ -781,8 +789,8 @@ RebuildArgs Scene::coop_args(const Arrays& in, const Arrays& out, int* off, cons
 void Scene::step_coop() {
   coop_rebuild();
   TravArgs t = trav(buf[cur], keys_sorted, cell_off);
-  passes_before_sweep(t);
-  sweep(t, buf[1 - cur]);
+  passes_before_sweep(t, nullptr, nullptr, walls_in_sweep());
+  sweep(t, buf[1 - cur], nullptr, nullptr, walls_in_sweep());
   cur = 1 - cur;
   if (shifting) {  // the sweep's last CTA has decided whether the shift needs new cells
     coop_rebuild();
@@ -1135,7 +1143,7 @@ void Scene::check_status() {
   CK(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (h & 2) {
-    set_err("a grid barrier of the cooperative rebuild gave up waiting");
+    set_err("a bounded device wait gave up (a grid barrier of the cooperative rebuild, or a sweep tile waiting for the wall tasks)");
     throw Fail{SPH_EINTERNAL};
   }
   if (h & 1) {

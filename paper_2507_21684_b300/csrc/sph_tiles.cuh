@@ -70,9 +70,17 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Record loads of the staging: through the read-only path, or (COH) through L2 only, for
+// records that another CTA of the same launch may have rewritten (the fused wall + sweep kernel).
+template <bool COH>
+__device__ __forceinline__ float4 ld_rec(const float4* p) { return COH ? __ldcg(p) : __ldg(p); }
+template <bool COH>
+__device__ __forceinline__ float2 ld_rec(const float2* p) { return COH ? __ldcg(p) : __ldg(p); }
+
 // Issue the copies of targets [p0, p0 + n) into the cache (all threads of the CTA; completion is
-// awaited by stage_tile before its first barrier).
-template <int D>
+// awaited by stage_tile before its first barrier).  The 16-byte copies bypass L1; with COH the
+// 8-byte records are read through L2 as well.
+template <int D, bool COH = false>
 __device__ __forceinline__ void fill_target_cache(TargetCache<D>& tc, const Arrays& a, const float4* e0,
                                                   const float4* e1, int p0, int n) {
   constexpr int NF = (D == 3) ? 5 : 4;  // float4 arrays A, B, X, O (, XL)
@@ -84,7 +92,10 @@ __device__ __forceinline__ void fill_target_cache(TargetCache<D>& tc, const Arra
   }
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     cp_async8(&tc.meta[k], a.meta + p0 + k);
-    if (D == 3) cp_async8(&tc.C[k], a.C + p0 + k);
+    if (D == 3) {
+      if (COH) tc.C[k] = __ldcg(a.C + p0 + k);
+      else cp_async8(&tc.C[k], a.C + p0 + k);
+    }
     if (e0) cp_async16(&tc.E0[k], e0 + p0 + k);
     if (e1) cp_async16(&tc.E1[k], e1 + p0 + k);
   }
@@ -165,10 +176,12 @@ __device__ __forceinline__ int staged_run(const TileSmem<D, EXTRA>& sm, int k) {
 // when the staged region exceeds the shared-memory capacity or the column table, -1 when no
 // thread passed want (no target of the pass in this tile: nothing is staged; the decision rides
 // on the first barrier, so it costs no extra round trip).  All threads of the CTA call it.
-template <int D, int EXTRA>
+// wall_seen (optional): set to whether any staged particle is a wall (mass <= 0).  COH: record
+// loads through L2 (see ld_rec).
+template <int D, int EXTRA, bool COH = false>
 __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T, const Arrays& a,
                           const int* __restrict__ cell_off, const float4* __restrict__ extra0,
-                          const float* __restrict__ extra1, bool want) {
+                          const float* __restrict__ extra1, bool want, int* wall_seen = nullptr) {
   constexpr int NL = TileCfg<D>::NL;
   constexpr int NCOL = TileSmem<D, EXTRA>::NCOL;
   constexpr int NRUN = TileSmem<D, EXTRA>::NRUN;
@@ -259,21 +272,31 @@ __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T
     if (sm.linecell[l] < 0) v = sm.run_s[3 * l + 0];
     sm.colstart[l * NCOL + c] = v;
   }
+  int walls = 0;
   for (int k = tid; k < total; k += blockDim.x) {
     const int r = staged_run(sm, k);
     const int j = sm.run_g[r] + (k - sm.run_s[r]);
     const int l = r / 3;
-    float4 A = __ldg(a.A + j), B = __ldg(a.B + j);
+    float4 A = ld_rec<COH>(a.A + j), B = ld_rec<COH>(a.B + j);
     A.x += sm.run_sx[r];
     A.y += sm.cshift[l][1];
     if (D == 3) A.z += sm.cshift[l][2];
     sm.A[k] = A;
     sm.B[k] = B;
-    if (D == 3) sm.C[k] = __ldg(a.C + j);
+    float m = B.w;
+    if (D == 3) {
+      const float2 C = ld_rec<COH>(a.C + j);
+      sm.C[k] = C;
+      m = C.y;
+    }
+    walls |= m <= 0.f;
     if (EXTRA > 0) sm.E[k] = __ldg(extra0 + j);
     if (EXTRA > 1) sm.E[CAP + k] = make_float4(__ldg(extra1 + j), 0.f, 0.f, 0.f);
   }
-  __syncthreads();
+  if (wall_seen)
+    *wall_seen = __syncthreads_or(walls);
+  else
+    __syncthreads();
   return 1;
 }
 
