@@ -509,11 +509,11 @@ def main():
             "pairs_per_step": fw["pairs_per_step"], "gpu_launches": fw["launches"],
             "rebuilds_in_timed_region": fw["rebuilds"],
             "clocks": clocks,
-            "roofline": {"bound": "alu", "kernel": "k_sweep (fused rates + kick-drift)",
+            "roofline": {"bound": "alu", "kernel": "k_walls_sweep_t (wall pass + fused rates + kick-drift, one launch)",
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS,
-                         "traffic": stored_traffic("k_sweep_t_dambreak_128.md"),
-                         "traffic_source": "profiles/k_sweep_t_dambreak_128.md (ncu, cold caches, one launch)",
+                         "traffic": stored_traffic("k_walls_sweep_t_dambreak_128.md"),
+                         "traffic_source": "profiles/k_walls_sweep_t_dambreak_128.md (ncu, cold caches, one launch)",
                          "flops_per_pair": FLOPS_PER_PAIR[2], "pairs_per_launch": fw["pairs_per_step"],
                          "sweep_ms_avg": fw["sweep_ms"], "sweep_launches": fw["sweep_n"],
                          "peak_source": "148 SM x 128 FP32 lanes x 2 x 2.032 GHz (unit counts and max clock)"},
