@@ -39,12 +39,19 @@ class OrcParams(C.Structure):
         ("H", C.c_double), ("dt", C.c_double), ("rho0", C.c_double), ("c0", C.c_double),
         ("gamma", C.c_double), ("nu", C.c_double), ("delta", C.c_double), ("eps", C.c_double),
         ("g", C.c_double * 3), ("rebuild_interval", C.c_int32), ("skin", C.c_double),
-        ("diffusion", C.c_int32), ("shift", C.c_double),
+        ("diffusion", C.c_int32), ("shift", C.c_double), ("boundary", C.c_int32), ("ghost", C.c_void_p),
     ]
 
 
-def params(p: dict) -> OrcParams:
+def params(p: dict, scene: dict | None = None) -> OrcParams:
+    """The oracle's parameters; with a scene, its mDBC ghost nodes (kept alive by the result)."""
     o = OrcParams()
+    o.boundary = int(p.get("boundary", 0))
+    o.ghost = None
+    if scene is not None and scene.get("ghost") is not None:
+        g = np.ascontiguousarray(scene["ghost"], np.float32)
+        o._ghost = g
+        o.ghost = g.ctypes.data
     for k in ("dim", "kernel", "density_mode", "periodic_mask", "rebuild_interval"):
         setattr(o, k, int(p[k]))
     for k in ("H", "dt", "rho0", "c0", "gamma", "nu", "delta", "eps", "skin"):
@@ -89,6 +96,8 @@ def lib():
         L.orc_sym_pinv.argtypes = [C.c_int, _d, _d]
         L.orc_renorm_gradient.argtypes = [_P(OrcParams), C.c_int, C.c_int, _f, _f, _f, _f, _d, _d]
         L.orc_shift.argtypes = [_P(OrcParams), C.c_int, C.c_int, _f, _f, _f, _f, _d, _d]
+        L.orc_gen_pinv.argtypes = [C.c_int, _d, _d]
+        L.orc_mdbc.argtypes = [_P(OrcParams), C.c_int, C.c_int, _f, _f, _f, _f, _d, _d]
         _lib = L
     return _lib
 
@@ -158,7 +167,7 @@ def pairs(p: dict, x: np.ndarray, brute: bool = False) -> np.ndarray:
 def rates(scene: dict, who: np.ndarray | None = None, x=None, v=None, rho=None):
     """a, drho (and the rho, p used) of fluid particles at a float32 state."""
     p = scene["params"]
-    P = params(p)
+    P = params(p, scene)
     x = np.ascontiguousarray(scene["x"] if x is None else x, np.float32)
     v = np.ascontiguousarray(scene["v"] if v is None else v, np.float32)
     rho = np.ascontiguousarray(scene["rho"] if rho is None else rho, np.float32)
@@ -194,7 +203,7 @@ def sym_pinv(M: np.ndarray) -> np.ndarray:
 def renorm_gradient(scene: dict, x=None, v=None, rho=None, with_M: bool = False):
     """<grad rho>^L of every particle (fluid rows, then wall rows) at a float32 state."""
     p = scene["params"]
-    P = params(p)
+    P = params(p, scene)
     x = np.ascontiguousarray(scene["x"] if x is None else x, np.float32)
     v = np.ascontiguousarray(scene["v"] if v is None else v, np.float32)
     rho = np.ascontiguousarray(scene["rho"] if rho is None else rho, np.float32)
@@ -213,7 +222,7 @@ def renorm_gradient(scene: dict, x=None, v=None, rho=None, with_M: bool = False)
 def shift(scene: dict, x=None, v=None, rho=None):
     """Particle-shifting displacements (n_fluid x dim) and lambda_i of the fluid at a float32 state."""
     p = scene["params"]
-    P = params(p)
+    P = params(p, scene)
     x = np.ascontiguousarray(scene["x"] if x is None else x, np.float32)
     v = np.ascontiguousarray(scene["v"] if v is None else v, np.float32)
     rho = np.ascontiguousarray(scene["rho"] if rho is None else rho, np.float32)
@@ -226,10 +235,41 @@ def shift(scene: dict, x=None, v=None, rho=None):
     return dx, lam
 
 
+def gen_pinv(A: np.ndarray) -> np.ndarray:
+    """Pseudo-inverse of an n x n matrix (n <= 4) as the mDBC solve takes it."""
+    A = np.asarray(A, np.float64)
+    n = A.shape[0]
+    a = np.zeros((4, 4))
+    a[:n, :n] = A
+    X = np.zeros((4, 4))
+    lib().orc_gen_pinv(n, _ptr(np.ascontiguousarray(a), C.c_double), _ptr(X, C.c_double))
+    return X[:n, :n].copy()
+
+
+def mdbc(scene: dict, x=None, v=None, rho=None, with_system: bool = False):
+    """mDBC densities of the wall particles at a float32 state (scene["ghost"]: ghost nodes)."""
+    p = scene["params"]
+    P = params(p, scene)
+    x = np.ascontiguousarray(scene["x"] if x is None else x, np.float32)
+    v = np.ascontiguousarray(scene["v"] if v is None else v, np.float32)
+    rho = np.ascontiguousarray(scene["rho"] if rho is None else rho, np.float32)
+    m = np.ascontiguousarray(scene["mass"], np.float32)
+    nf, nw = scene["n_fluid"], scene["n_wall"]
+    rw = np.zeros(max(nw, 1))
+    sys = np.zeros((max(nw, 1), 20)) if with_system else None
+    rc = lib().orc_mdbc(C.byref(P), nf, nw, _ptr(x, C.c_float), _ptr(v, C.c_float), _ptr(rho, C.c_float),
+                        _ptr(m, C.c_float), _ptr(rw, C.c_double), _ptr(sys, C.c_double))
+    if rc != 0:
+        raise ValueError("orc_mdbc: the scene has no ghost nodes")
+    if with_system:
+        return rw[:nw], sys[:nw]
+    return rw[:nw]
+
+
 def rollout(scene: dict, n_steps: int, x=None, v=None, rho=None):
     """FP64 rollout from the scene's float32 state (or the given float32 arrays)."""
     p = scene["params"]
-    P = params(p)
+    P = params(p, scene)
     x = np.ascontiguousarray(scene["x"] if x is None else x, np.float32)
     v = np.ascontiguousarray(scene["v"] if v is None else v, np.float32)
     rho = np.ascontiguousarray(scene["rho"] if rho is None else rho, np.float32)
@@ -245,7 +285,7 @@ def rollout(scene: dict, n_steps: int, x=None, v=None, rho=None):
 
 def rollout64(scene: dict, n_steps: int, x: np.ndarray, v: np.ndarray, rho: np.ndarray, nu: float | None = None):
     p = scene["params"]
-    P = params(p)
+    P = params(p, scene)
     nf, nw, d = scene["n_fluid"], scene["n_wall"], p["dim"]
     N = nf + nw
     x = np.ascontiguousarray(x, np.float64)
@@ -262,15 +302,15 @@ def rollout64(scene: dict, n_steps: int, x: np.ndarray, v: np.ndarray, rho: np.n
 
 def jvp(scene: dict, n_steps: int, x, v, rho, dx, dv, drho, dnu: float = 0.0, nu: float | None = None):
     p = scene["params"]
-    P = params(p)
+    P = params(p, scene)
     nf, nw, d = scene["n_fluid"], scene["n_wall"], p["dim"]
     N = nf + nw
     arrs = [np.ascontiguousarray(a, np.float64) for a in (x, v, rho, dx, dv, drho)]
     m = np.ascontiguousarray(scene["mass"], np.float32)
     nu = p["nu"] if nu is None else nu
     out = [np.zeros((N, d)), np.zeros((N, d)), np.zeros(N), np.zeros((N, d)), np.zeros((N, d)), np.zeros(N)]
-    if (P.diffusion == 1 and P.density_mode == 0) or P.shift > 0:
-        raise ValueError("orc_jvp: the renormalised diffusion and particle shifting have no tangent pass")
+    if (P.diffusion == 1 and P.density_mode == 0) or P.shift > 0 or (P.boundary == 1 and nw > 0):
+        raise ValueError("orc_jvp: the renormalised diffusion, particle shifting and mDBC have no tangent pass")
     lib().orc_jvp(C.byref(P), nf, nw, *[_ptr(a, C.c_double) for a in arrs[:3]], _ptr(m, C.c_float), float(nu),
                   *[_ptr(a, C.c_double) for a in arrs[3:]], float(dnu), int(n_steps),
                   *[_ptr(a, C.c_double) for a in out])
@@ -280,7 +320,7 @@ def jvp(scene: dict, n_steps: int, x, v, rho, dx, dv, drho, dnu: float = 0.0, nu
 def adjoint(scene: dict, n_steps: int, xb_T, vb_T, rb_T, x=None, v=None, rho=None, nu: float | None = None):
     """Reverse pass of an n-step rollout: adjoints of (x0, v0, rho0, nu) and the final state."""
     p = scene["params"]
-    P = params(p)
+    P = params(p, scene)
     nf, nw, d = scene["n_fluid"], scene["n_wall"], p["dim"]
     N = nf + nw
     x = np.ascontiguousarray(scene["x"] if x is None else x, np.float64)

@@ -48,6 +48,8 @@ struct OrcParams {
   double skin;
   int32_t diffusion;  // 0: Molteni-Colagrossi psi_ij, 1: renormalised (Antuono) psi_ij
   double shift;       // explicit particle shifting coefficient (0: off)
+  int32_t boundary;   // 0: Shepard pressure extrapolation onto the walls, 1: mDBC with ghost nodes
+  const float* ghost; // mDBC: ghost node of each wall particle (n_wall * dim, wall order)
 };
 }
 
@@ -492,6 +494,201 @@ void renorm_gradient(const OrcParams& P, const State<double>& S, const Pairs& pr
   }
 }
 
+// ---------------------------------------------------------------- mDBC wall treatment
+// Modified dynamic boundary conditions (the paper's boundary handling for weakly-compressible
+// flow, after English et al.): each wall particle b has a ghost node g inside the fluid, its mirror
+// image across the wall surface (given with the scene).  The fluid density around g is expanded
+// to first order, rho(x) ~ f + (x - x_g) . f', and the SPH interpolation of the expansion and of
+// its gradient at g gives the (d+1) x (d+1) system of the paper's boundary section
+//   [ <1>       <x_jg>^T        ] [ f  ]   [ <rho>      ]
+//   [ <grad 1>  <grad (x) x_jg> ] [ f' ] = [ <grad rho> ]
+// with <q> = sum_j V_j q_j W(x_g - x_j), <grad q> = sum_j V_j q_j grad_g W(x_g - x_j) and
+// x_jg = x_j - x_g over the fluid particles j within H of g (so f' is the density gradient).  It is
+// solved by a pseudo-inverse in units of H (the second block row and f' scaled by H, so that every
+// entry is dimensionless; singular values at or below kPinvRtol of the largest are dropped), and
+// rho_b = f + x_bg . f' with x_bg = x_b - x_g.  A ghost without fluid neighbours gives rho0.
+// The wall pressure follows from the Tait law.
+
+// Moore-Penrose pseudo-inverse of an n x n matrix (n <= 4) through the eigen-decomposition of
+// A^T A (cyclic Jacobi): pinv(A) = sum_k q_k q_k^T A^T / lambda_k over lambda_k > rtol^2 max lambda
+// (lambda_k = sigma_k^2).
+void gen_pinv(int n, const double A[4][4], double X[4][4]) {
+  double M[4][4] = {{0.0}}, Q[4][4];
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b)
+      for (int k = 0; k < n; ++k) M[a][b] += A[k][a] * A[k][b];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) Q[a][b] = a == b ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = 0.0, all = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = 0; q < n; ++q) {
+        all += M[p][q] * M[p][q];
+        if (p != q) off += M[p][q] * M[p][q];
+      }
+    if (off <= 1e-36 * all) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (M[p][q] == 0.0) continue;
+        double tau = (M[q][q] - M[p][p]) / (2.0 * M[p][q]);
+        double t = (tau >= 0.0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+        for (int k = 0; k < n; ++k) {
+          double kp = M[k][p], kq = M[k][q];
+          M[k][p] = c * kp - sn * kq;
+          M[k][q] = sn * kp + c * kq;
+        }
+        for (int k = 0; k < n; ++k) {
+          double pk = M[p][k], qk = M[q][k];
+          M[p][k] = c * pk - sn * qk;
+          M[q][k] = sn * pk + c * qk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double kp = Q[k][p], kq = Q[k][q];
+          Q[k][p] = c * kp - sn * kq;
+          Q[k][q] = sn * kp + c * kq;
+        }
+      }
+  }
+  double lmax = 0.0;
+  for (int k = 0; k < n; ++k) lmax = std::max(lmax, M[k][k]);
+  double P[4][4] = {{0.0}};  // pinv(A^T A)
+  for (int k = 0; k < n; ++k) {
+    if (!(M[k][k] > kPinvRtol * kPinvRtol * lmax)) continue;
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) P[a][b] += Q[a][k] * Q[b][k] / M[k][k];
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      X[a][b] = 0.0;
+      if (a < n && b < n)
+        for (int k = 0; k < n; ++k) X[a][b] += P[a][k] * A[b][k];
+    }
+}
+
+// Fluid particles within H of the point xq (cells of edge >= H over the fluid; periodic images).
+struct FluidCells {
+  CellGrid G;
+  std::vector<int64_t> start;
+  std::vector<int> items;
+};
+FluidCells fluid_cells(const OrcParams& P, const State<double>& S) {
+  FluidCells C;
+  C.G = make_grid(P, 0.0);
+  const int d = S.d;
+  int64_t ncell = (int64_t)C.G.n[0] * C.G.n[1] * C.G.n[2];
+  std::vector<int64_t> key(S.nf);
+  for (int i = 0; i < S.nf; ++i) key[i] = cell_key(P, C.G, &S.x[(size_t)i * d]);
+  C.start.assign(ncell + 1, 0);
+  for (int i = 0; i < S.nf; ++i) C.start[key[i] + 1]++;
+  for (int64_t c = 0; c < ncell; ++c) C.start[c + 1] += C.start[c];
+  C.items.resize(S.nf);
+  std::vector<int64_t> fill(C.start.begin(), C.start.end() - 1);
+  for (int i = 0; i < S.nf; ++i) C.items[fill[key[i]]++] = i;
+  return C;
+}
+void fluid_near(const OrcParams& P, const FluidCells& C, const State<double>& S, const double* xq,
+                std::vector<int>& out) {
+  const int d = S.d;
+  out.clear();
+  if (!C.G.ok) {
+    for (int j = 0; j < S.nf; ++j)
+      if (is_neighbour(P, xq, &S.x[(size_t)j * d])) out.push_back(j);
+    return;
+  }
+  int ci[3] = {0, 0, 0};
+  for (int k = 0; k < d; ++k) ci[k] = cell_coord(P, C.G, k, xq[k]);
+  for (int oz = (d == 3 ? -1 : 0); oz <= (d == 3 ? 1 : 0); ++oz)
+    for (int oy = -1; oy <= 1; ++oy)
+      for (int ox = -1; ox <= 1; ++ox) {
+        int c[3] = {ci[0] + ox, ci[1] + oy, ci[2] + oz};
+        bool skip = false;
+        for (int k = 0; k < d; ++k)
+          if (c[k] < 0 || c[k] >= C.G.n[k]) {
+            if (!periodic(P, k)) { skip = true; break; }
+            c[k] = (c[k] + C.G.n[k]) % C.G.n[k];
+          }
+        if (skip) continue;
+        int64_t cc = ((int64_t)c[2] * C.G.n[1] + c[1]) * C.G.n[0] + c[0];
+        for (int64_t t = C.start[cc]; t < C.start[cc + 1]; ++t) {
+          int j = C.items[t];
+          if (is_neighbour(P, xq, &S.x[(size_t)j * d])) out.push_back(j);
+        }
+      }
+  std::sort(out.begin(), out.end());
+  out.erase(std::unique(out.begin(), out.end()), out.end());
+}
+
+// mDBC densities of the wall particles (rho_out: n_wall) at the state S; optionally the system
+// (A and b per wall, scaled form) for tests.
+void mdbc_densities(const OrcParams& P, const State<double>& S, std::vector<double>& rho_out,
+                    double* sys_out = nullptr) {
+  const int d = S.d, n = d + 1;
+  FluidCells C = fluid_cells(P, S);
+  rho_out.assign(S.nw, P.rho0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int w = 0; w < S.nw; ++w) {
+    const int b = S.nf + w;
+    double xg[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < d; ++k) xg[k] = (double)P.ghost[(size_t)w * d + k];
+    std::vector<int> nb;
+    fluid_near(P, C, S, xg, nb);
+    double A[4][4] = {{0.0}}, rhs[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j : nb) {
+      double r[3] = {0.0, 0.0, 0.0}, r2 = 0.0, G[3];
+      for (int k = 0; k < d; ++k) {
+        r[k] = min_image(P, k, xg[k] - S.x[(size_t)j * d + k]);  // x_g - x_j
+        r2 += r[k] * r[k];
+      }
+      kernel_gradW<double>(P, r, G);  // grad_g W(x_g - x_j)
+      const double W = kernel_W<double>(P, std::sqrt(r2));
+      const double Vj = S.m[j] / S.rho[j];
+      // row 0: <1>, <x_jg>^T / H ; rows 1..d: H <grad 1>, <grad (x) x_jg>
+      A[0][0] += Vj * W;
+      for (int l = 0; l < d; ++l) A[0][1 + l] += Vj * (-r[l]) * W / P.H;
+      for (int k = 0; k < d; ++k) {
+        A[1 + k][0] += Vj * G[k] * P.H;
+        for (int l = 0; l < d; ++l) A[1 + k][1 + l] += Vj * G[k] * (-r[l]);
+      }
+      rhs[0] += Vj * S.rho[j] * W;
+      for (int k = 0; k < d; ++k) rhs[1 + k] += Vj * S.rho[j] * G[k] * P.H;
+    }
+    if (sys_out) {
+      for (int a = 0; a < n; ++a) {
+        for (int c = 0; c < n; ++c) sys_out[(size_t)w * 20 + a * 4 + c] = A[a][c];
+        sys_out[(size_t)w * 20 + 16 + a] = rhs[a];
+      }
+    }
+    if (nb.empty()) continue;  // rho0
+    double X[4][4];
+    gen_pinv(n, A, X);
+    double u[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < n; ++c) u[a] += X[a][c] * rhs[c];
+    // rho_b = f + x_bg . f', f' = u[1..d] / H, x_bg = x_b - x_g
+    double rb = u[0];
+    for (int k = 0; k < d; ++k) rb += (min_image(P, k, S.x[(size_t)b * d + k] - xg[k])) * u[1 + k] / P.H;
+    rho_out[w] = rb;
+  }
+}
+
+
+// The walls' density and pressure for this step: mDBC (boundary 1) or the Shepard extrapolation.
+template <class T>
+void walls_update(const OrcParams& P, State<T>& S, const Pairs& pr, std::vector<double>& p_wall) {
+  if (P.boundary != 1 || S.nw == 0) {
+    wall_extrapolation(P, S, pr, p_wall);
+    return;
+  }
+  std::vector<double> rw;
+  mdbc_densities(P, plain(S), rw);
+  p_wall.assign(S.nw, 0.0);
+  for (int w = 0; w < S.nw; ++w) {
+    S.rho[S.nf + w] = T(rw[w]);
+    p_wall[w] = val(tait<double>(P, rw[w]));
+  }
+}
+
 // Rates of the fluid particles (Sec. 2.3, delta-SPH):
 //   drho_i/dt = -rho_i sum_j V_j (v_j - v_i) . gradW_ij + delta h c0 sum_j V_j psi_ij . gradW_ij
 //   psi_ij    = 2 (rho_j - rho_i) (x_j - x_i) / (|x_ij|^2 + eps h^2)                (diffusion 0)
@@ -646,7 +843,7 @@ void step(const OrcParams& P, State<T>& S) {
   Pairs pr = pairs_of(P, S);
   if (P.density_mode == 1) density_summation(P, S, pr);
   std::vector<double> p_wall;
-  wall_extrapolation(P, S, pr, p_wall);
+  walls_update(P, S, pr, p_wall);
   std::vector<T> a, drho;
   if (renormalised(P)) {
     std::vector<double> grad;
@@ -1008,7 +1205,7 @@ int orc_rates(const OrcParams* P, int nf, int nw, const float* x, const float* v
   }
   Pairs pr = pairs_of(*P, S);
   if (P->density_mode == 1) density_summation(*P, S, pr);
-  wall_extrapolation(*P, S, pr, p_wall);
+  walls_update(*P, S, pr, p_wall);
   std::vector<double> grad;
   if (renormalised(*P)) {
     std::vector<int> all(S.N());
@@ -1065,7 +1262,7 @@ int orc_renorm_gradient(const OrcParams* P, int nf, int nw, const float* x, cons
   State<double> S = load_state<double>(*P, nf, nw, x, v, rho, m);
   Pairs pr = pairs_of(*P, S);
   std::vector<double> p_wall, grad;
-  wall_extrapolation(*P, S, pr, p_wall);
+  walls_update(*P, S, pr, p_wall);
   std::vector<int> all(S.N());
   std::iota(all.begin(), all.end(), 0);
   renorm_gradient(*P, S, pr, all, grad, M_out);
@@ -1084,6 +1281,28 @@ int orc_shift(const OrcParams* P, int nf, int nw, const float* x, const float* v
   shift_displacements(*P, S, pr, dx, &lam);
   std::copy(dx.begin(), dx.end(), dx_out);
   if (lambda_out) std::copy(lam.begin(), lam.end(), lambda_out);
+  return 0;
+}
+
+// Pseudo-inverse of an n x n matrix (n <= 4, row-major 4 x 4 storage) as the mDBC solve takes it.
+void orc_gen_pinv(int n, const double* A, double* X) {
+  double a[4][4], x[4][4];
+  for (int p = 0; p < 4; ++p)
+    for (int q = 0; q < 4; ++q) a[p][q] = A[p * 4 + q];
+  gen_pinv(n, a, x);
+  for (int p = 0; p < 4; ++p)
+    for (int q = 0; q < 4; ++q) X[p * 4 + q] = x[p][q];
+}
+
+// mDBC densities of the wall particles at a float32 state (P->ghost set); sys_out (optional,
+// n_wall * 20 doubles): the scaled system A (4 x 4) and right-hand side (4) of each wall.
+int orc_mdbc(const OrcParams* P, int nf, int nw, const float* x, const float* v, const float* rho, const float* m,
+             double* rho_out, double* sys_out) {
+  if (!P->ghost) return -1;
+  State<double> S = load_state<double>(*P, nf, nw, x, v, rho, m);
+  std::vector<double> rw;
+  mdbc_densities(*P, S, rw, sys_out);
+  std::copy(rw.begin(), rw.end(), rho_out);
   return 0;
 }
 
@@ -1118,7 +1337,7 @@ int orc_rollout64(const OrcParams* P, int nf, int nw, const double* x, const dou
 int orc_jvp(const OrcParams* P, int nf, int nw, const double* x, const double* v, const double* rho, const float* m,
             double nu, const double* dx0, const double* dv0, const double* drho0, double dnu, int n_steps,
             double* x_out, double* v_out, double* rho_out, double* dx_out, double* dv_out, double* drho_out) {
-  if (renormalised(*P) || P->shift > 0.0) return -4;  // no derivative of these terms
+  if (renormalised(*P) || P->shift > 0.0 || (P->boundary == 1 && nw > 0)) return -4;  // no derivative of these terms
   int N = nf + nw, d = P->dim;
   State<Dual> S;
   S.nf = nf; S.nw = nw; S.d = d;

@@ -29,7 +29,7 @@ __all__ = [
     "taylor_green_2d", "taylor_green_3d", "dam_break", "perturbed_velocity",
     "served_stream", "SceneSpec",
     "KERNEL_WENDLAND4", "KERNEL_WENDLAND2", "DENSITY_CONTINUITY", "DENSITY_SUMMATION",
-    "DIFFUSION_MC", "DIFFUSION_RENORM",
+    "DIFFUSION_MC", "DIFFUSION_RENORM", "BOUNDARY_SHEPARD", "BOUNDARY_MDBC",
 ]
 
 KERNEL_WENDLAND4 = 0
@@ -38,6 +38,8 @@ DENSITY_CONTINUITY = 0
 DENSITY_SUMMATION = 1
 DIFFUSION_MC = 0        # delta-SPH diffusion in the Molteni-Colagrossi form
 DIFFUSION_RENORM = 1    # with the renormalised density gradient (Antuono et al.)
+BOUNDARY_SHEPARD = 0    # wall pressure by Shepard extrapolation of the fluid's, hydrostatic term
+BOUNDARY_MDBC = 1       # mDBC: first-order extrapolation from ghost nodes mirrored into the fluid
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 
@@ -80,7 +82,7 @@ def _f32(v: float) -> float:
 
 def _params(dim, kernel, H, dt, c0, nu, delta, box_lo, box_hi, periodic_mask,
             g=(0.0, 0.0, 0.0), rho0=1.0, gamma=7.0, eps=0.01, density_mode=DENSITY_CONTINUITY,
-            rebuild_interval=1, skin=0.0, diffusion=DIFFUSION_MC, shift=0.0):
+            rebuild_interval=1, skin=0.0, diffusion=DIFFUSION_MC, shift=0.0, boundary=BOUNDARY_SHEPARD):
     return dict(
         dim=int(dim), kernel=int(kernel), density_mode=int(density_mode),
         periodic_mask=int(periodic_mask),
@@ -90,7 +92,7 @@ def _params(dim, kernel, H, dt, c0, nu, delta, box_lo, box_hi, periodic_mask,
         nu=_f32(nu), delta=_f32(delta), eps=_f32(eps),
         g=[_f32(x) for x in g] + [0.0] * (3 - len(g)),
         rebuild_interval=int(rebuild_interval), skin=_f32(skin), diffusion=int(diffusion),
-        shift=_f32(shift),
+        shift=_f32(shift), boundary=int(boundary),
     )
 
 
@@ -175,7 +177,8 @@ def taylor_green_3d(n_side: int = 128, seed: int = 0, steps: int = 200, nu: floa
 
 
 def dam_break(res: int = 128, steps: int = 2000, alpha_visc: float = 0.02, delta: float = 0.1,
-              rebuild_interval: int = 1, skin: float = 0.0, diffusion: int = 0, shift: float = 0.0) -> dict:
+              rebuild_interval: int = 1, skin: float = 0.0, diffusion: int = 0, shift: float = 0.0,
+              boundary: int = 0) -> dict:
     """2D dam break: fluid column [0,1] x [0,2] at (i+1/2)dx in the tank [0,4] x [0,3],
     dx = 1/res, three layers of fixed wall particles at -(k+1/2)dx (left, bottom, corners
     filled) and 4+(k+1/2)dx (right), open top.  g = (0, -9.81), c0 = 10 sqrt(2 g 2.0),
@@ -215,8 +218,14 @@ def dam_break(res: int = 128, steps: int = 2000, alpha_visc: float = 0.02, delta
     rho = np.concatenate([rho_f, np.full(nw, rho0)])
     p = _params(2, KERNEL_WENDLAND4, H, 0.25 * dx / _f32(c0), c0, nu, delta,
                 (-4 * dx, -4 * dx), (4.0 + 4 * dx, 3.0), 0b00, g=(0.0, -g), rho0=rho0, gamma=gamma,
-                rebuild_interval=rebuild_interval, skin=skin, diffusion=diffusion, shift=shift)
+                rebuild_interval=rebuild_interval, skin=skin, diffusion=diffusion, shift=shift,
+                boundary=boundary)
+    # mDBC ghost nodes: each wall particle mirrored across the tank's wall surfaces (x = 0, x = 4,
+    # y = 0; the corner particles across both)
+    gx = np.where(w[:, 0] < 0.0, -w[:, 0], np.where(w[:, 0] > 4.0, 8.0 - w[:, 0], w[:, 0]))
+    gy = np.where(w[:, 1] < 0.0, -w[:, 1], w[:, 1])
     return dict(
+        ghost=np.stack([gx, gy], 1).astype(np.float32),
         name=f"dambreak_{res}", params=p, n_fluid=nf, n_wall=nw, steps=steps, seed=0, dx=dx,
         x=x.astype(np.float32), v=v.astype(np.float32), rho=rho.astype(np.float32),
         mass=np.full(nf + nw, _f32(rho0 * dx * dx), np.float32),
