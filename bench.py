@@ -356,6 +356,8 @@ def main():
     ap.add_argument("--diffusion", type=int, default=0, choices=[0, 1],
                     help="--profile-run: 0 Molteni-Colagrossi, 1 renormalised delta-SPH diffusion")
     ap.add_argument("--shift", type=float, default=0.0, help="--profile-run: particle shifting coefficient")
+    ap.add_argument("--boundary", type=int, default=0, choices=[0, 1],
+                    help="--profile-run (dam break): 0 Shepard wall pressure, 1 mDBC")
     ap.add_argument("--stream-scenes", type=int, default=512, help="requests of the served mixed-size stream")
     ap.add_argument("--stream-rates", type=float, nargs="*", default=[20.0, 80.0, 320.0])
     args = ap.parse_args()
@@ -369,13 +371,14 @@ def main():
         import paper_2507_21684_b300 as sph
         sph.use_torch_allocator()
         from paper_2507_21684_b300 import tune
-        sp = (si.dam_break(res=128, diffusion=args.diffusion) if args.workload == "dambreak"
+        sp = (si.dam_break(res=128, diffusion=args.diffusion, boundary=args.boundary) if args.workload == "dambreak"
               else si.taylor_green_3d(128, seed=0, diffusion=args.diffusion))
         skin = args.skin if args.skin is not None else (0.02 if args.workload == "dambreak" else 0.0)
         sp = dict(sp, params=dict(tune.with_skin(sp, skin)["params"], shift=args.shift))
         r = run_forward(sph, torch, sp, args.steps, args.warmup, args.workload == "dambreak", torch.cuda.Stream(),
                         prof_steps=0, eager=args.eager)
         print(json.dumps({"profile_run": args.workload, "diffusion": args.diffusion, "shift": args.shift,
+                          "boundary": args.boundary,
                           "skin_over_H": skin,
                           "eager": args.eager,
                           "ms_per_step": sum(r["ms"]) / len(r["ms"]), "pairs_per_step": r["pairs_per_step"]}))
@@ -469,6 +472,15 @@ def main():
             "pair_interactions_per_s": fs["pairs_per_step"] * args.steps / ts,
             "sweep_ms": fs["sweep_ms"], "gradient_ms": fs["gradient_ms"], "shift_ms": fs["shift_ms"],
             "rebuilds_in_timed_region": fs["rebuilds"], "l2": "flushed between timed steps"}
+        # the dam break with mDBC walls (ghost nodes) in place of the Shepard wall pressure
+        sm = dict(si.dam_break(res=128, boundary=1), params=dict(spec["params"], boundary=1))
+        fm = run_forward(sph, torch, sm, args.steps, args.warmup, True, torch.cuda.Stream())
+        tm = sum(fm["ms"]) / 1e3
+        extras["dambreak_128_mdbc"] = {
+            "boundary": "mDBC: first-order system at mirrored ghost nodes, pseudo-inverse",
+            "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * tm / args.steps,
+            "pair_interactions_per_s": fm["pairs_per_step"] * args.steps / tm,
+            "sweep_ms": fm["sweep_ms"], "mdbc_walls_ms": fm["walls_ms"], "l2": "flushed between timed steps"}
         sa = si.adjoint_problem(128)
         ad = run_adjoint(sph, torch, sa, 200, 20)
         extras["adjoint_128"] = {

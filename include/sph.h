@@ -78,6 +78,18 @@ extern "C" {
  *           free surface.  One extra neighbour pass per step; no adjoint (sph_rollout rejects it). */
 #define SPH_DIFFUSION_MC 0
 #define SPH_DIFFUSION_RENORM 1
+/* Wall treatment (Sec. "Boundary Conditions"):
+ *   SHEPARD  p_w = (sum_f p_f W + g . sum_f rho_f r_wf W) / sum_f W over fluid neighbours f,
+ *            rho_w by the inverse Tait law (the default);
+ *   MDBC     each wall particle b has a ghost node g inside the fluid (its mirror image across the
+ *            wall surface, sph_set_ghosts); the SPH interpolation at g of a first-order expansion
+ *            of q = rho - rho0 in the fluid gives the (d+1) x (d+1) system
+ *              [<1> <x_jg>^T; <grad 1> <grad (x) x_jg>] [f; f'] = [<q>; <grad q>],
+ *            x_jg = x_j - x_g over fluid j within H of g, solved by a pseudo-inverse in units of H
+ *            (singular values <= 1e-3 of the largest dropped); rho_b = rho0 + f + (x_b - x_g) . f',
+ *            rho0 when no fluid is in range; p_b by the Tait law.  Walls keep v = 0.  No adjoint. */
+#define SPH_BOUNDARY_SHEPARD 0
+#define SPH_BOUNDARY_MDBC 1
 
 /* Global parameters sigma of one scene (Sec. 2.2; App. C "global state dictionary").
  * The support radius H is the kernel's cut-off (the paper stores the support and calls it h).
@@ -120,6 +132,7 @@ typedef struct sph_params {
                            * product CFL * Mach of Sun et al.  No adjoint (sph_rollout rejects it).
                            * The shift needs cells valid for the swept positions: eager steps rebuild
                            * twice per step, captured steps check the skin again before the shift. */
+  int32_t boundary;       /* SPH_BOUNDARY_* (shared by the scenes of a batch) */
 } sph_params;
 
 typedef struct sph_scene sph_scene;
@@ -167,6 +180,11 @@ SPH_API int sph_get_state(const sph_scene* scene, float* x, float* v, float* rho
  * summation mode).  Original order, fluid particles only.  Any output may be NULL. */
 SPH_API int sph_rates(sph_scene* scene, float* a, float* drho, float* rho_used, int ptr_is_device);
 
+/* Ghost nodes of the wall particles for SPH_BOUNDARY_MDBC: n_wall * dim floats per scene (the
+ * walls in their input order; a batch's scenes one after another).  Copied; required before the
+ * first step, rate evaluation or rollout of an mDBC scene with walls (SPH_EINVAL otherwise). */
+SPH_API int sph_set_ghosts(sph_scene* scene, const float* ghost, int ptr_is_device);
+
 /* Renormalised density gradient <grad rho>^L (see SPH_DIFFUSION_RENORM) at the current state,
  * after the wall extrapolation a step applies: (n_fluid + n_wall) * dim floats, original order
  * (fluid rows, then wall rows; per scene for a batch, n_rows of sph_batch_info plus the walls).
@@ -175,7 +193,8 @@ SPH_API int sph_density_gradient(sph_scene* scene, float* grad, int ptr_is_devic
 
 /* Forward rollout of n_steps that keeps what the adjoint needs: the state every ckpt_every
  * steps (gradient checkpointing, Sec. 3.3).  Replaces any previous tape of this scene.
- * SPH_EINVAL with SPH_DIFFUSION_RENORM in continuity mode (no reverse pass of that term). */
+ * SPH_EINVAL with SPH_DIFFUSION_RENORM in continuity mode or particle shifting (no reverse pass of
+ * those terms); sph_adjoint needs a scene without walls. */
 SPH_API int sph_rollout(sph_scene* scene, int n_steps, int ckpt_every);
 
 /* Reverse pass of the last sph_rollout (vector-Jacobian product, Sec. 2.2): given the adjoints
@@ -241,7 +260,7 @@ SPH_API void sph_destroy(sph_scene* scene);
  * pass for the loss L = (1/N) sum_i |x_i^T - x~_i|^2 with target positions x~, Sec. 4.1) run on
  * the second stream concurrently.  A served result is bitwise the result of the scene alone.
  * Forward requests share the batch only with requests of the same dim, kernel, density mode,
- * diffusion form, shifting on or off, skin and rebuild_interval; one of another kind waits, in
+ * diffusion form, shifting on or off, wall treatment, skin and rebuild_interval; one of another kind waits, in
  * arrival order, until the running batch has drained.
  * Results stay with the server until sph_wait returns them (once per ticket). */
 #define SPH_REQ_FORWARD 0
@@ -255,6 +274,7 @@ typedef struct sph_request {
   int mode;                         /* SPH_REQ_FORWARD or SPH_REQ_ADJOINT */
   int ckpt_every;                   /* adjoint: checkpoint interval (0: 20) */
   const float* x_target;            /* adjoint: target final positions (NULL: the initial positions) */
+  const float* ghost;               /* SPH_BOUNDARY_MDBC with walls: ghost nodes (n_wall * dim), copied */
 } sph_request;
 
 typedef struct sph_result {

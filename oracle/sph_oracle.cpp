@@ -497,17 +497,19 @@ void renorm_gradient(const OrcParams& P, const State<double>& S, const Pairs& pr
 // ---------------------------------------------------------------- mDBC wall treatment
 // Modified dynamic boundary conditions (the paper's boundary handling for weakly-compressible
 // flow, after English et al.): each wall particle b has a ghost node g inside the fluid, its mirror
-// image across the wall surface (given with the scene).  The fluid density around g is expanded
-// to first order, rho(x) ~ f + (x - x_g) . f', and the SPH interpolation of the expansion and of
-// its gradient at g gives the (d+1) x (d+1) system of the paper's boundary section
-//   [ <1>       <x_jg>^T        ] [ f  ]   [ <rho>      ]
-//   [ <grad 1>  <grad (x) x_jg> ] [ f' ] = [ <grad rho> ]
+// image across the wall surface (given with the scene).  The fluid quantity q = rho - rho0 around
+// g is expanded to first order, q(x) ~ f + (x - x_g) . f', and the SPH interpolation of the
+// expansion and of its gradient at g gives the (d+1) x (d+1) system of the paper's boundary section
+//   [ <1>       <x_jg>^T        ] [ f  ]   [ <q>      ]
+//   [ <grad 1>  <grad (x) x_jg> ] [ f' ] = [ <grad q> ]
 // with <q> = sum_j V_j q_j W(x_g - x_j), <grad q> = sum_j V_j q_j grad_g W(x_g - x_j) and
 // x_jg = x_j - x_g over the fluid particles j within H of g (so f' is the density gradient).  It is
 // solved by a pseudo-inverse in units of H (the second block row and f' scaled by H, so that every
 // entry is dimensionless; singular values at or below kPinvRtol of the largest are dropped), and
-// rho_b = f + x_bg . f' with x_bg = x_b - x_g.  A ghost without fluid neighbours gives rho0.
-// The wall pressure follows from the Tait law.
+// rho_b = rho0 + f + x_bg . f' with x_bg = x_b - x_g.  A ghost without fluid neighbours gives rho0.
+// The wall pressure follows from the Tait law.  (Expanding rho - rho0 rather than rho gives the
+// same result whenever the system has full rank; where the pseudo-inverse drops a direction, its
+// minimum-norm solution then falls back towards the rest state instead of towards zero density.)
 
 // Moore-Penrose pseudo-inverse of an n x n matrix (n <= 4) through the eigen-decomposition of
 // A^T A (cyclic Jacobi): pinv(A) = sum_k q_k q_k^T A^T / lambda_k over lambda_k > rtol^2 max lambda
@@ -650,8 +652,9 @@ void mdbc_densities(const OrcParams& P, const State<double>& S, std::vector<doub
         A[1 + k][0] += Vj * G[k] * P.H;
         for (int l = 0; l < d; ++l) A[1 + k][1 + l] += Vj * G[k] * (-r[l]);
       }
-      rhs[0] += Vj * S.rho[j] * W;
-      for (int k = 0; k < d; ++k) rhs[1 + k] += Vj * S.rho[j] * G[k] * P.H;
+      const double qj = S.rho[j] - P.rho0;
+      rhs[0] += Vj * qj * W;
+      for (int k = 0; k < d; ++k) rhs[1 + k] += Vj * qj * G[k] * P.H;
     }
     if (sys_out) {
       for (int a = 0; a < n; ++a) {
@@ -665,8 +668,8 @@ void mdbc_densities(const OrcParams& P, const State<double>& S, std::vector<doub
     double u[4] = {0.0, 0.0, 0.0, 0.0};
     for (int a = 0; a < n; ++a)
       for (int c = 0; c < n; ++c) u[a] += X[a][c] * rhs[c];
-    // rho_b = f + x_bg . f', f' = u[1..d] / H, x_bg = x_b - x_g
-    double rb = u[0];
+    // rho_b = rho0 + f + x_bg . f', f' = u[1..d] / H, x_bg = x_b - x_g
+    double rb = P.rho0 + u[0];
     for (int k = 0; k < d; ++k) rb += (min_image(P, k, S.x[(size_t)b * d + k] - xg[k])) * u[1 + k] / P.H;
     rho_out[w] = rb;
   }

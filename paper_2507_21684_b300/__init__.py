@@ -28,6 +28,7 @@ _NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT", 6
 # kernel classes of sph_timing
 TIMING_SWEEP, TIMING_REBUILD, TIMING_WALLS, TIMING_DENSITY, TIMING_ADJOINT, TIMING_GRADIENT, TIMING_SHIFT = range(7)
 DIFFUSION_MC, DIFFUSION_RENORM = 0, 1
+BOUNDARY_SHEPARD, BOUNDARY_MDBC = 0, 1
 
 
 class SphError(RuntimeError):
@@ -43,6 +44,7 @@ class Params(C.Structure):
         ("H", C.c_float), ("dt", C.c_float), ("rho0", C.c_float), ("c0", C.c_float), ("gamma", C.c_float),
         ("nu", C.c_float), ("delta", C.c_float), ("eps", C.c_float), ("g", C.c_float * 3),
         ("rebuild_interval", C.c_int32), ("skin", C.c_float), ("diffusion", C.c_int32), ("shift", C.c_float),
+        ("boundary", C.c_int32),
     ]
 
     @classmethod
@@ -54,6 +56,7 @@ class Params(C.Structure):
             setattr(o, k, float(p[k]))
         o.diffusion = int(p.get("diffusion", 0))
         o.shift = float(p.get("shift", 0.0))
+        o.boundary = int(p.get("boundary", 0))
         for k in range(3):
             o.box_lo[k] = float(p["box_lo"][k])
             o.box_hi[k] = float(p["box_hi"][k])
@@ -64,7 +67,8 @@ class Params(C.Structure):
 class Request(C.Structure):
     _fields_ = [("params", Params), ("n_fluid", C.c_int), ("n_wall", C.c_int),
                 ("x", C.c_void_p), ("v", C.c_void_p), ("rho", C.c_void_p), ("mass", C.c_void_p),
-                ("n_steps", C.c_int), ("mode", C.c_int), ("ckpt_every", C.c_int), ("x_target", C.c_void_p)]
+                ("n_steps", C.c_int), ("mode", C.c_int), ("ckpt_every", C.c_int), ("x_target", C.c_void_p),
+                ("ghost", C.c_void_p)]
 
 
 class Result(C.Structure):
@@ -112,6 +116,7 @@ def lib() -> C.CDLL:
     L.sph_get_state.argtypes = [vp, vp, vp, vp, C.c_int]
     L.sph_rates.argtypes = [vp, vp, vp, vp, C.c_int]
     L.sph_density_gradient.argtypes = [vp, vp, C.c_int]
+    L.sph_set_ghosts.argtypes = [vp, vp, C.c_int]
     L.sph_rollout.argtypes = [vp, C.c_int, C.c_int]
     L.sph_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
     L.sph_scene_info.argtypes = [vp, P(C.c_int32), P(C.c_int32)]
@@ -200,6 +205,8 @@ class Scene:
         self._init_batch([s["params"] for s in specs], [s["n_fluid"] for s in specs], [s["n_wall"] for s in specs],
                          [arr(s["x"]) for s in specs], [arr(s["v"]) for s in specs], [arr(s["rho"]) for s in specs],
                          [arr(s["mass"]) for s in specs], stream)
+        if any(int(s["params"].get("boundary", 0)) == BOUNDARY_MDBC and s["n_wall"] > 0 for s in specs):
+            self.set_ghosts(np.concatenate([np.asarray(s["ghost"], np.float32).reshape(-1) for s in specs]))
         return self
 
     def _init_batch(self, params, n_fluid, n_wall, xs, vs, rhos, masses, stream):
@@ -286,6 +293,14 @@ class Scene:
         ru = np.empty((nf,), np.float32)
         _check(lib().sph_rates(self._h, a.ctypes.data, dr.ctypes.data, ru.ctypes.data, 0))
         return dict(a=a, drho=dr, rho=ru)
+
+    def set_ghosts(self, ghost):
+        """mDBC ghost nodes of the wall particles (n_wall x dim, walls in input order; a batch's
+        scenes one after another)."""
+        g = np.ascontiguousarray(np.asarray(ghost, np.float32).reshape(-1))
+        if g.size != self.n_wall * self.dim:
+            raise ValueError("ghost nodes: one per wall particle")
+        _check(lib().sph_set_ghosts(self._h, g.ctypes.data, 0))
 
     def density_gradient(self):
         """Renormalised density gradient <grad rho>^L of every particle (n x dim, original order,
@@ -392,6 +407,10 @@ class Server:
         r.mode = REQ_ADJOINT if adjoint else REQ_FORWARD
         r.ckpt_every = int(ckpt_every)
         r.x_target = xt.ctypes.data if xt is not None else None
+        gh = None
+        if int(spec["params"].get("boundary", 0)) == BOUNDARY_MDBC and int(spec["n_wall"]) > 0:
+            gh = np.ascontiguousarray(spec["ghost"], np.float32)
+        r.ghost = gh.ctypes.data if gh is not None else None
         t = C.c_uint64()
         _check(lib().sph_submit(self._h, C.byref(r), C.byref(t)))
         n, d = spec["x"].shape
@@ -468,7 +487,10 @@ def scene_from(spec: dict, stream=None, device: bool = False) -> Scene:
     if device:
         torch = _torch()
         arrs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
-    return Scene(spec["params"], spec["n_fluid"], spec["n_wall"], *arrs, stream=stream)
+    sc = Scene(spec["params"], spec["n_fluid"], spec["n_wall"], *arrs, stream=stream)
+    if int(spec["params"].get("boundary", 0)) == BOUNDARY_MDBC and spec["n_wall"] > 0:
+        sc.set_ghosts(spec["ghost"])
+    return sc
 
 
 def rollout_fn():

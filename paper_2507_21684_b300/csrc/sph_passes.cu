@@ -2,6 +2,7 @@
 //   tile table      (built after every rebuild from the cell offsets)
 //   walls           Shepard extrapolation of the fluid pressure onto wall particles
 //   walls + sweep   both in one launch (wall tiles first; sweep tiles near walls wait for them)
+//   mDBC walls      first-order extrapolation from ghost nodes (a warp per wall particle)
 //   density         summation density rho_i = sum_j m_j W_ij            (Sec. 2.3)
 //   gradient        renormalised density gradient <grad rho>^L (kernel renormalisation, App. A)
 //   sweep           continuity + delta diffusion, Tait pressure, viscosity, gravity, and the
@@ -19,6 +20,9 @@ namespace sph {
 
 // Bounded wait of a sweep tile on the wall tasks of the fused kernel: ~0.1 s, then status bit 1.
 constexpr long long kGateSpins = 1LL << 22;
+// Relative cut-off of the pseudo-inverses (renormalisation, mDBC): eigen-directions with
+// |lambda| <= kPinvRtol max|lambda| (or singular values <= kPinvRtol max) are dropped.
+constexpr float kPinvRtol = 1e-3f;
 
 // ================================================================== tile table
 // (builders in sph_tilebuild.cuh)
@@ -393,6 +397,190 @@ __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restr
   end_tiles(t, pass, pairs_cta);
 }
 
+// ================================================================== mDBC walls
+// One warp per wall particle b of the wall tiles: the fluid particles within H of its ghost node g
+// (the 3^d cells around g's cell, read from global memory and split over the lanes) give the
+// first-order system of the paper's boundary section for q = rho - rho0, in units of H:
+//   [ <1>          <x_jg>^T / H    ] [ f    ]   [ <q>          ]
+//   [ H <grad 1>   <grad (x) x_jg> ] [ H f' ] = [ H <grad q>   ]
+// (<q> = sum_j V_j q_j W(x_g - x_j), grad = grad_g, x_jg = x_j - x_g), summed in FP32 and solved
+// by a pseudo-inverse (one-sided Jacobi SVD; singular values at or below kPinvRtol of the largest
+// dropped); rho_b = rho0 + f + x_bg . f' with x_bg = x_b - x_g, rho0 when no fluid is in
+// range.  The density deviation q (exact in FP32 for densities near rho0) keeps the right-hand
+// side small, so the FP32 sums lose nothing against the large rest density, and the pressure is
+// taken from the deviation directly.  The walls' records are rewritten in place (only their
+// density, pressure and volume change).
+// Minimum-norm least-squares solution u = pinv(A) b of the n x n system by one-sided Jacobi
+// (Hestenes): plane rotations A V make the columns orthogonal, so A = U S V^T with the column
+// norms as singular values; u = sum_k v_k (a_k . b) / s_k^2 over s_k > kPinvRtol max s (the same
+// cut-off as the oracle's).  FP32, registers only; the condition number enters once (no normal
+// equations).
+template <int N>
+__device__ __forceinline__ void mdbc_solve(const float (&A)[N][N], const float (&b)[N], float (&u)[N]) {
+  float a[N][N], v[N][N];
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      a[r][c] = A[r][c];
+      v[r][c] = r == c ? 1.f : 0.f;
+    }
+#pragma unroll 1
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    bool rotated = false;
+#pragma unroll
+    for (int p = 0; p < N; ++p)
+#pragma unroll
+      for (int q = p + 1; q < N; ++q) {
+        float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          al = fmaf(a[k][p], a[k][p], al);
+          be = fmaf(a[k][q], a[k][q], be);
+          ga = fmaf(a[k][p], a[k][q], ga);
+        }
+        if (!(fabsf(ga) > 1e-7f * sqrtf(al) * sqrtf(be))) continue;
+        rotated = true;
+        const float zeta = (be - al) / (2.f * ga);
+        const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+        const float c = rsqrtf(fmaf(t, t, 1.f)), sn = c * t;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const float ap = a[k][p], aq = a[k][q];
+          a[k][p] = c * ap - sn * aq;
+          a[k][q] = sn * ap + c * aq;
+          const float vp = v[k][p], vq = v[k][q];
+          v[k][p] = c * vp - sn * vq;
+          v[k][q] = sn * vp + c * vq;
+        }
+      }
+    if (!rotated) break;
+  }
+  float s2[N], s2max = 0.f;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    float n2 = 0.f;
+#pragma unroll
+    for (int r = 0; r < N; ++r) n2 = fmaf(a[r][k], a[r][k], n2);
+    s2[k] = n2;
+    s2max = fmaxf(s2max, n2);
+  }
+#pragma unroll
+  for (int r = 0; r < N; ++r) u[r] = 0.f;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    if (!(s2[k] > kPinvRtol * kPinvRtol * s2max)) continue;
+    float ab = 0.f;
+#pragma unroll
+    for (int r = 0; r < N; ++r) ab = fmaf(a[r][k], b[r], ab);
+    const float coef = ab / s2[k];
+#pragma unroll
+    for (int r = 0; r < N; ++r) u[r] = fmaf(coef, v[r][k], u[r]);
+  }
+}
+
+// Tasks: slices of 8 consecutive particles of the wall tiles, one warp per particle.
+template <int D, int KERN>
+__global__ void __launch_bounds__(256) k_mdbc(TravArgs t, const Tile* __restrict__ tiles,
+                                              const int* __restrict__ wall_tiles, const int* __restrict__ n_wall_tiles,
+                                              const float4* __restrict__ ghost, const int* __restrict__ orig_base) {
+  constexpr int N = D + 1, NS = N * N + N;  // the system and its right-hand side
+  constexpr int SLICES = TileCfg<D>::TP / 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntask = *n_wall_tiles * SLICES;
+  for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+    const Tile T = tiles[wall_tiles[task / SLICES]];
+    const DevSeg& s = t.segs[T.seg];
+    const int i = T.p0 + (task % SLICES) * 8 + warp;
+    if (i < T.p1) {
+      const uint2 m = t.a.meta[i];
+      if (!(m.x & kWallBit)) continue;  // warp-uniform (the whole warp has this particle)
+      const float4 G4 = __ldg(ghost + orig_base[m.y] + (int)(m.x & ~kWallBit));
+      float xg[3] = {G4.x, G4.y, G4.z};
+      int c[3] = {0, 0, 0};
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        if ((s.periodic_mask >> k) & 1) xg[k] -= s.L[k] * floorf((xg[k] - s.lo[k]) * s.invL[k]);
+        c[k] = min(max((int)floorf((xg[k] - s.lo[k]) * s.invcs[k]), 0), s.n[k] - 1);
+      }
+      float acc[NS];
+#pragma unroll
+      for (int e = 0; e < NS; ++e) acc[e] = 0.f;
+      const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
+      for (int oz = zlo; oz <= zhi; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+          for (int ox = -1; ox <= 1; ++ox) {
+            int cc[3] = {c[0] + ox, c[1] + oy, c[2] + oz};
+            bool skip = false;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              if (cc[k] < 0 || cc[k] >= s.n[k]) {
+                if (!((s.periodic_mask >> k) & 1)) skip = true;
+                cc[k] = (cc[k] + s.n[k]) % s.n[k];
+              }
+            }
+            if (skip) continue;
+            const int cell = s.cell_base + (cc[2] * s.n[1] + cc[1]) * s.n[0] + cc[0];
+            const int j1 = t.cell_off[cell + 1];
+            for (int j = t.cell_off[cell] + lane; j < j1; j += 32) {
+              const PD<D> pj = load_pd<D>(t.a, j);
+              if (!(pj.m > 0.f)) continue;  // fluid only
+              float r[D];
+              const float r2 = separation<D>(s, xg, pj.x, r);  // x_g - x_j
+              if (!(r2 < s.H2)) continue;
+              const float q = safe_q(r2, s.invH);
+              const float VW = pj.V * (s.Kw * kern_w<KERN>(q));
+              const float VgH = pj.V * (s.Kg * kern_gt<KERN>(q)) * s.H;  // V grad W / r, times H
+              acc[0] += VW;
+#pragma unroll
+              for (int l = 0; l < D; ++l) acc[1 + l] = fmaf(-VW * s.invH, r[l], acc[1 + l]);
+#pragma unroll
+              for (int k = 0; k < D; ++k) {
+                acc[(1 + k) * N] = fmaf(VgH, r[k], acc[(1 + k) * N]);
+#pragma unroll
+                for (int l = 0; l < D; ++l)
+                  acc[(1 + k) * N + 1 + l] = fmaf(-VgH * s.invH * r[k], r[l], acc[(1 + k) * N + 1 + l]);
+              }
+              const float qj = pj.rho - s.rho0;
+              acc[N * N] = fmaf(VW, qj, acc[N * N]);
+#pragma unroll
+              for (int k = 0; k < D; ++k) acc[N * N + 1 + k] = fmaf(VgH * qj, r[k], acc[N * N + 1 + k]);
+            }
+          }
+#pragma unroll
+      for (int e = 0; e < NS; ++e)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(kFull, acc[e], o);
+      if (lane == 0) {
+        PD<D> me = load_pd<D>(t.a, i);
+        double q = 0.0;  // rho_b - rho0
+        if (acc[0] > 0.f) {
+          float A[N][N], bb[N], u[N];
+#pragma unroll
+          for (int a = 0; a < N; ++a) {
+#pragma unroll
+            for (int cix = 0; cix < N; ++cix) A[a][cix] = acc[a * N + cix];
+            bb[a] = acc[N * N + a];
+          }
+          mdbc_solve<N>(A, bb, u);
+          float xb[D];
+          const float rbg2 = separation<D>(s, me.x, xg, xb);  // x_b - x_g
+          (void)rbg2;
+          q = (double)u[0];
+#pragma unroll
+          for (int k = 0; k < D; ++k) q += (double)xb[k] * (double)u[1 + k] / (double)s.H;
+        }
+        const float rb = (float)((double)s.rho0 + q);
+        me.rho = rb;
+        me.p = s.B * expm1f(s.gamma * log1pf((float)(q / (double)s.rho0)));
+        me.V = fabsf(me.m) / rb;
+        store_pd<D>(t.a, i, me);
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // ================================================================== walls
 template <int D, int KERN>
 struct WallPass {
@@ -506,7 +694,6 @@ struct DensityPass {
 //   s_i = sum_j V_j (rho_j - rho_i) grad_i W_ij,       <grad rho>_i^L = pinv(M_i) s_i
 // (L_i applies to every term of the sum, so it is taken out of it).  The pseudo-inverse keeps
 // the eigen-directions with |lambda| > kPinvRtol max|lambda|.
-constexpr float kPinvRtol = 1e-3f;
 
 // pinv of the symmetric 2x2 [a b; b c] in closed form: (Lxx, Lxy, Lyy)
 __device__ __forceinline__ void pinv_sym2(float a, float b, float c, float* L) {
@@ -1347,6 +1534,13 @@ void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, i
   k_density_t<D, KERN><<<pass_grid((const void*)k_density_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles);
 }
 template <int D, int KERN>
+void launch_mdbc(const TravArgs& t, const Tile* tiles, const int* wall_tiles, const int* n_wall_tiles, int tiles_upper,
+                 const float4* ghost, const int* orig_base, cudaStream_t st) {
+  const int grid = (int)std::max<long long>(1, std::min<long long>((long long)tiles_upper * (TileCfg<D>::TP / 8),
+                                                                   16LL * g_num_sms));
+  k_mdbc<D, KERN><<<grid, 256, 0, st>>>(t, tiles, wall_tiles, n_wall_tiles, ghost, orig_base);
+}
+template <int D, int KERN>
 void launch_walls_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, const int* wall_tiles,
                           const int* n_wall_tiles, int tiles_upper, const Arrays& out, const Displace& disp,
                           cudaStream_t st) {
@@ -1442,6 +1636,8 @@ SPH_INST_PD(3)
   template void launch_walls_t<D, K>(const TravArgs&, const Tile*, const int*, const int*, int, cudaStream_t); \
   template void launch_density_t<D, K>(const TravArgs&, const Tile*, const int*, int, cudaStream_t);        \
   template void launch_grad_t<D, K>(const TravArgs&, const Tile*, const int*, int, float4*, cudaStream_t);   \
+  template void launch_mdbc<D, K>(const TravArgs&, const Tile*, const int*, const int*, int, const float4*,  \
+                                  const int*, cudaStream_t);                                                 \
   template void launch_walls_sweep_t<D, K>(const TravArgs&, const Tile*, const int*, const int*, const int*, int, \
                                            const Arrays&, const Displace&, cudaStream_t);                    \
   template void launch_shift_t<D, K>(const TravArgs&, const Tile*, const int*, int, const Arrays&,          \

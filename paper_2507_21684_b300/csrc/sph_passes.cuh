@@ -17,6 +17,9 @@ void launch_wall_tiles(const Tile* tiles, const int* ntiles, int tiles_upper, co
 template <int D, int KERN>
 void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st);
 template <int D, int KERN>
+void launch_mdbc(const TravArgs& t, const Tile* tiles, const int* wall_tiles, const int* n_wall_tiles, int tiles_upper,
+                 const float4* ghost, const int* orig_base, cudaStream_t st);
+template <int D, int KERN>
 void launch_walls_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, const int* wall_tiles,
                           const int* n_wall_tiles, int tiles_upper, const Arrays& out, const Displace& disp,
                           cudaStream_t st);

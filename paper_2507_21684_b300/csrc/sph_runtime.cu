@@ -107,6 +107,7 @@ DevSeg make_seg(const sph_params& p, int n_fluid, int cell_base, int p0, int p1,
   if (p.density_mode != 0 && p.density_mode != 1) einval("density_mode must be 0 or 1");
   if (p.diffusion != 0 && p.diffusion != 1) einval("diffusion must be SPH_DIFFUSION_MC or SPH_DIFFUSION_RENORM");
   if (!(p.shift >= 0.f) || !std::isfinite(p.shift)) einval("shift must be finite and >= 0");
+  if (p.boundary != 0 && p.boundary != 1) einval("boundary must be SPH_BOUNDARY_SHEPARD or SPH_BOUNDARY_MDBC");
   if (!(p.H > 0.f) || !(p.dt > 0.f) || !(p.rho0 > 0.f) || !(p.c0 > 0.f) || !(p.gamma > 0.f))
     einval("H, dt, rho0, c0 and gamma must be positive");
   if (!(p.nu >= 0.f) || !(p.eps > 0.f) || !(p.skin >= 0.f) || p.rebuild_interval < 1)
@@ -280,6 +281,7 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
   summation = prms[0].density_mode == 1;
   renorm = !summation && prms[0].diffusion == 1;
   shifting = prms[0].shift > 0.f;
+  mdbc = false;
   any_walls = false;
   skin = prms[0].skin;
   interval = prms[0].rebuild_interval;
@@ -293,6 +295,7 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
       einval("all scenes of a batch must share dim, kernel and density mode");
     if (p.diffusion != prms[0].diffusion) einval("all scenes of a batch must share the diffusion form");
     if ((p.shift > 0.f) != (prms[0].shift > 0.f)) einval("all scenes of a batch must agree on particle shifting");
+    if (p.boundary != prms[0].boundary) einval("all scenes of a batch must share the wall treatment");
     int n = nfs[s] + nws[s];
     if (nfs[s] < 0 || nws[s] < 0 || n < 1) einval("particle counts must be non-negative with at least one particle");
     if ((long long)N + n >= (1LL << 30)) einval("too many particles");
@@ -304,6 +307,7 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
     N += n;
     C_tot += (int)c;
     if (nws[s] > 0) any_walls = true;
+    if (nws[s] > 0 && p.boundary == 1) mdbc = true;
     if (p.skin != skin || p.rebuild_interval != interval)
       einval("all scenes of a batch must share skin and rebuild_interval");
   }
@@ -374,6 +378,10 @@ void Scene::alloc_all() {
     d_nwall = (int*)mem.get(sizeof(int) * 2);
   }
   if (renorm) gradrho = (float4*)mem.get(sizeof(float4) * N);  // before any step is captured
+  if (mdbc) {
+    ghosts = (float4*)mem.get(sizeof(float4) * N);
+    CK(cudaMemsetAsync(ghosts, 0, sizeof(float4) * N, st));
+  }
   d_ntiles = (int*)mem.get(sizeof(int) * 2);
   d_tile_ctr = (int*)mem.get(sizeof(int) * 4);
   CK(cudaMemsetAsync(d_tile_ctr, 0, sizeof(int) * 4, st));  // tiled kernels leave it zeroed
@@ -539,7 +547,54 @@ void Scene::build_tiles(const int* off, const uint2* meta, Tile* tl, int* ntl) {
   }
 }
 
+// mDBC ghost nodes of the walls (n_wall rows per scene, in batch order) into the per-row table.
+void Scene::set_ghosts(const float* g, int is_dev) {
+  if (!mdbc) einval("sph_set_ghosts: the scene has no walls with boundary = SPH_BOUNDARY_MDBC");
+  std::vector<float> h;
+  size_t nw_total = 0;
+  for (int s = 0; s < S; ++s) nw_total += (size_t)(segs[s].p1 - segs[s].p0 - segs[s].nf);
+  const size_t n = nw_total * D;
+  if (is_dev) {
+    h.resize(n);
+    CK(cudaMemcpyAsync(h.data(), g, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    g = h.data();
+  }
+  std::vector<float4> rows((size_t)N, make_float4(0.f, 0.f, 0.f, 0.f));
+  size_t w = 0;
+  for (int s = 0; s < S; ++s) {
+    const int nw = segs[s].p1 - segs[s].p0 - segs[s].nf;
+    for (int k = 0; k < nw; ++k, ++w) {
+      float v[3] = {0.f, 0.f, 0.f};
+      for (int q = 0; q < D; ++q) v[q] = g[w * D + q];
+      if (!(std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]))) einval("sph_set_ghosts: non-finite ghost node");
+      rows[(size_t)orig_base[s] + segs[s].nf + k] = make_float4(v[0], v[1], v[2], 0.f);
+    }
+  }
+  CK(cudaMemcpyAsync(ghosts, rows.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  ghosts_set = true;
+}
+
+void Scene::need_ghosts() const {
+  if (mdbc && !ghosts_set) einval("boundary = SPH_BOUNDARY_MDBC needs the walls' ghost nodes (sph_set_ghosts)");
+}
+
 void Scene::walls_pass(const TravArgs& t, const Tile* tl) {
+  if (mdbc) {
+    prof_begin(2);
+    if (D == 2) {
+      if (kern == 0) launch_mdbc<2, 0>(t, tl, wall_tiles, d_nwall, tiles_upper, ghosts, d_orig_base, st);
+      else launch_mdbc<2, 1>(t, tl, wall_tiles, d_nwall, tiles_upper, ghosts, d_orig_base, st);
+    } else {
+      if (kern == 0) launch_mdbc<3, 0>(t, tl, wall_tiles, d_nwall, tiles_upper, ghosts, d_orig_base, st);
+      else launch_mdbc<3, 1>(t, tl, wall_tiles, d_nwall, tiles_upper, ghosts, d_orig_base, st);
+    }
+    CKL();
+    prof_end();
+    ++launches;
+    return;
+  }
   prof_begin(2);
   if (D == 2) {
     if (kern == 0) launch_walls_t<2, 0>(t, tl, wall_tiles, d_nwall, tiles_upper, st);
@@ -822,6 +877,7 @@ void Scene::advance_schedule() {
 }
 
 void Scene::steps(int n) {
+  need_ghosts();
   if (n <= 0) return;
   CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st));
   launches = 0;
@@ -921,6 +977,7 @@ void Scene::ensure_cells() {
 
 // ---------------------------------------------------------------- adjoint tape
 void Scene::rollout(int n, int k) {
+  need_ghosts();
   if (n < 1 || k < 1) einval("n_steps and ckpt_every must be >= 1");
   if (renorm) einval("the renormalised diffusion (SPH_DIFFUSION_RENORM) has no adjoint; use sph_step");
   if (shifting) einval("particle shifting has no adjoint; use sph_step");
@@ -1153,6 +1210,7 @@ void Scene::check_status() {
 }
 
 void Scene::rates(float* a, float* drho, float* rho, int is_dev) {
+  need_ghosts();
   // summation density / walls modify the records in place: work on a copy
   ensure_cells();
   if (!adj_alloc) alloc_tape(1);
@@ -1194,6 +1252,7 @@ void Scene::rates(float* a, float* drho, float* rho, int is_dev) {
 // <grad rho>^L at the current state in original order (all particles), on a copy of the records
 // (the wall pass writes the walls' density in place).
 void Scene::density_gradient(float* grad, int is_dev) {
+  need_ghosts();
   ensure_cells();
   if (!adj_alloc) alloc_tape(1);
   copy_arrays(scratch_arr, buf[cur]);
@@ -1454,6 +1513,18 @@ int sph_rates(sph_scene* sc, float* a, float* drho, float* rho_used, int ptr_is_
   API_BEGIN
   sc->s.enter();
   sc->s.rates(a, drho, rho_used, ptr_is_device);
+  sc->s.leave();
+  API_END
+}
+
+int sph_set_ghosts(sph_scene* sc, const float* ghost, int ptr_is_device) {
+  if (!sc || !ghost) {
+    sph::set_err("sph_set_ghosts: NULL scene or ghost array");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  sc->s.enter();
+  sc->s.set_ghosts(ghost, ptr_is_device);
   sc->s.leave();
   API_END
 }

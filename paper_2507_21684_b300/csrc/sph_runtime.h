@@ -91,6 +91,9 @@ struct Scene {
   bool summation = false, any_walls = false;
   bool renorm = false;              // renormalised delta-SPH diffusion (continuity mode)
   bool shifting = false;            // particle shifting at the end of each step
+  bool mdbc = false;                // mDBC wall treatment (ghost nodes) instead of Shepard's
+  float4* ghosts = nullptr;         // mDBC ghost node of each particle row (walls), original order
+  bool ghosts_set = false;
   float4* gradrho = nullptr;        // <grad rho>^L per particle, sorted order (renorm, or on request)
   float skin = 0.f;
   int interval = 1;
@@ -185,11 +188,13 @@ struct Scene {
                                           int* ntiles_out = nullptr);
   void build_tiles(const int* off, const uint2* meta, Tile* tl, int* ntl);
   bool fuse_walls = true;           // wall pass inside the sweep launch (continuity, MC diffusion)
-  bool walls_in_sweep() const { return fuse_walls && any_walls && !summation && !renorm; }
+  bool walls_in_sweep() const { return fuse_walls && any_walls && !summation && !renorm && !mdbc; }
   // fused_walls: the sweep launch does the wall pass (walls_in_sweep()), so it is left out here
   void passes_before_sweep(const TravArgs& t, const Tile* tl = nullptr, const int* ntl = nullptr,
                            bool fused_walls = false);
   void walls_pass(const TravArgs& t, const Tile* tl);
+  void set_ghosts(const float* g, int is_dev);
+  void need_ghosts() const;
   void grad_pass(const TravArgs& t, const Tile* tl, const int* ntl);
   void sweep(const TravArgs& t, const Arrays& out, const Tile* tl = nullptr, const int* ntl = nullptr,
              bool fused_walls = false);

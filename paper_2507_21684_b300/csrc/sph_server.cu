@@ -53,6 +53,7 @@ struct Request {
   sph_params p{};
   int nf = 0, nw = 0, n = 0, d = 2;
   std::vector<float> x, v, rho, mass, xtgt;
+  std::vector<float> ghost;  // mDBC ghost nodes of the walls (kept for every re-pack)
   int n_steps = 0, mode = 0, ckpt = 20;
   size_t bytes = 0;
   int phase = 0;  // 0 queued, 1 admitted, 2 done
@@ -93,7 +94,7 @@ struct Server {
   static bool same_class(const sph_params& a, const sph_params& b) {
     return a.dim == b.dim && a.kernel == b.kernel && (a.density_mode == 1) == (b.density_mode == 1) &&
            a.skin == b.skin && a.rebuild_interval == b.rebuild_interval && a.diffusion == b.diffusion &&
-           (a.shift > 0.f) == (b.shift > 0.f);
+           (a.shift > 0.f) == (b.shift > 0.f) && a.boundary == b.boundary;
   }
 
   void admit_locked() {
@@ -154,6 +155,11 @@ struct Server {
     nb->bind_stream(st_fwd);
     nb->alloc_all();
     nb->use_graphs = false;
+    if (nb->mdbc) {
+      std::vector<float> g;
+      for (auto& r : next) g.insert(g.end(), r->ghost.begin(), r->ghost.end());
+      nb->set_ghosts(g.data(), 0);
+    }
     for (size_t k = 0; k < next.size(); ++k) {
       auto& r = next[k];
       if (r->seg >= 0 && batch) {
@@ -371,6 +377,7 @@ int sph_submit(sph_server* sv, const sph_request* rq, uint64_t* ticket) {
   }
   if (rq->mode == SPH_REQ_ADJOINT && (r->nw != 0 || rq->params.density_mode != SPH_DENSITY_CONTINUITY ||
                                       rq->params.diffusion != SPH_DIFFUSION_MC || rq->params.shift > 0.f)) {
+    // (no walls, so the wall treatment does not matter)
     sph::set_err("sph_submit: adjoint requests need continuity mode, the MC diffusion, no shifting and no wall particles");
     return SPH_EINVAL;
   }
@@ -380,6 +387,13 @@ int sph_submit(sph_server* sv, const sph_request* rq, uint64_t* ticket) {
   r->rho.assign(rq->rho, rq->rho + r->n);
   r->mass.assign(rq->mass, rq->mass + r->n);
   if (rq->x_target) r->xtgt.assign(rq->x_target, rq->x_target + nd);
+  if (rq->params.boundary == SPH_BOUNDARY_MDBC && r->nw > 0) {
+    if (!rq->ghost) {
+      sph::set_err("sph_submit: an mDBC request with walls needs its ghost nodes");
+      return SPH_EINVAL;
+    }
+    r->ghost.assign(rq->ghost, rq->ghost + (size_t)r->nw * r->d);
+  }
   r->n_steps = rq->n_steps;
   r->mode = rq->mode;
   r->ckpt = rq->ckpt_every > 0 ? rq->ckpt_every : 20;

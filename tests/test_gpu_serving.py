@@ -58,8 +58,8 @@ def test_mixed_kinds_are_served_in_separate_batches(sph):
     then run in their own; every result is still the scene's result alone."""
     specs = [si.taylor_green_2d(24, seed=1), si.taylor_green_2d(20, seed=2, diffusion=1),
              si.taylor_green_3d(8, seed=3), si.taylor_green_2d(16, seed=4),
-             si.dam_break(res=16, diffusion=1)]
-    steps = [9, 12, 5, 7, 6]
+             si.dam_break(res=16, diffusion=1), si.dam_break(res=16, boundary=1), si.dam_break(res=20, boundary=1)]
+    steps = [9, 12, 5, 7, 6, 8, 4]
     with sph.Server(8 << 30, 64) as sv:
         tickets = [sv.submit(sp, st) for sp, st in zip(specs, steps)]
         got = [sv.wait(t) for t in tickets]
