@@ -43,6 +43,27 @@ class OrcParams(C.Structure):
     ]
 
 
+class OrcShiftLoss(C.Structure):
+    _fields_ = [
+        ("w_color", C.c_double), ("w_grad", C.c_double), ("w_density", C.c_double), ("w_reg", C.c_double),
+        ("reg_fraction", C.c_double), ("target_kind", C.c_int32),
+        ("t_base", C.c_double), ("t_amp", C.c_double), ("t_k", C.c_double * 3), ("t_phase", C.c_double),
+        ("t_lo", C.c_double), ("t_hi", C.c_double), ("t_n", C.c_double * 3), ("t_c", C.c_double),
+    ]
+
+
+def shift_loss(o: dict) -> OrcShiftLoss:
+    r = OrcShiftLoss()
+    for k in ("w_color", "w_grad", "w_density", "w_reg", "reg_fraction", "t_base", "t_amp", "t_phase",
+              "t_lo", "t_hi", "t_c"):
+        setattr(r, k, float(o.get(k, 0.0)))
+    r.target_kind = int(o.get("target_kind", 0))
+    for k in range(3):
+        r.t_k[k] = float(o.get("t_k", (0.0, 0.0, 0.0))[k])
+        r.t_n[k] = float(o.get("t_n", (0.0, 0.0, 0.0))[k])
+    return r
+
+
 def params(p: dict, scene: dict | None = None) -> OrcParams:
     """The oracle's parameters; with a scene, its mDBC ghost nodes (kept alive by the result)."""
     o = OrcParams()
@@ -97,6 +118,7 @@ def lib():
         L.orc_renorm_gradient.argtypes = [_P(OrcParams), C.c_int, C.c_int, _f, _f, _f, _f, _d, _d]
         L.orc_shift.argtypes = [_P(OrcParams), C.c_int, C.c_int, _f, _f, _f, _f, _d, _d]
         L.orc_gen_pinv.argtypes = [C.c_int, _d, _d]
+        L.orc_shift_objective.argtypes = [_P(OrcParams), C.c_int, C.c_int, _d, _f, _P(OrcShiftLoss), _d, _d, _d]
         L.orc_mdbc.argtypes = [_P(OrcParams), C.c_int, C.c_int, _f, _f, _f, _f, _d, _d]
         _lib = L
     return _lib
@@ -264,6 +286,37 @@ def mdbc(scene: dict, x=None, v=None, rho=None, with_system: bool = False):
     if with_system:
         return rw[:nw], sys[:nw]
     return rw[:nw]
+
+
+def shift_objective(scene: dict, loss: dict, x=None, direction=None):
+    """Shifting objective L at FP64 positions x (all particles; walls fixed) and, with a direction
+    (n_fluid x dim), its directional derivative (forward mode)."""
+    p = scene["params"]
+    P = params(p, scene)
+    o = shift_loss(loss)
+    x = np.ascontiguousarray(scene["x"] if x is None else x, np.float64)
+    m = np.ascontiguousarray(scene["mass"], np.float32)
+    nf, nw = scene["n_fluid"], scene["n_wall"]
+    dr = None if direction is None else np.ascontiguousarray(direction, np.float64)
+    L, dL = C.c_double(), C.c_double()
+    lib().orc_shift_objective(C.byref(P), nf, nw, _ptr(x, C.c_double), _ptr(m, C.c_float), C.byref(o),
+                              _ptr(dr, C.c_double), C.byref(L), C.byref(dL))
+    return (L.value, dL.value) if direction is not None else L.value
+
+
+def shift_gradient(scene: dict, loss: dict, x=None):
+    """dL/dx of the fluid particles (n_fluid x dim) by one forward-mode pass per coordinate."""
+    d = scene["params"]["dim"]
+    nf = scene["n_fluid"]
+    x = np.ascontiguousarray(scene["x"] if x is None else x, np.float64)
+    g = np.zeros((nf, d))
+    e = np.zeros((nf, d))
+    for i in range(nf):
+        for k in range(d):
+            e[i, k] = 1.0
+            g[i, k] = shift_objective(scene, loss, x, e)[1]
+            e[i, k] = 0.0
+    return g
 
 
 def rollout(scene: dict, n_steps: int, x=None, v=None, rho=None):

@@ -39,6 +39,13 @@
 #endif
 
 extern "C" {
+// Objective of the shifting-by-optimisation application (weights, regulariser, target density).
+struct OrcShiftLoss {
+  double w_color, w_grad, w_density, w_reg, reg_fraction;
+  int32_t target_kind;  // 0: t_base + t_amp sin(t_k . x + t_phase); 1: t_lo where t_n . x < t_c, else t_hi
+  double t_base, t_amp, t_k[3], t_phase;
+  double t_lo, t_hi, t_n[3], t_c;
+};
 struct OrcParams {
   int32_t dim, kernel, density_mode, periodic_mask;
   double box_lo[3], box_hi[3];
@@ -72,10 +79,12 @@ inline Dual operator/(Dual a, Dual b) { return {a.v / b.v, (a.d * b.v - a.v * b.
 inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
 inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
 inline Dual sqrt(Dual a) { double s = std::sqrt(a.v); return {s, a.d / (2.0 * s)}; }
+inline Dual sin(Dual a) { return {std::sin(a.v), std::cos(a.v) * a.d}; }
 inline Dual pow(Dual a, double e) { double p = std::pow(a.v, e); return {p, e * std::pow(a.v, e - 1.0) * a.d}; }
 inline double val(double a) { return a; }
 inline double val(const Dual& a) { return a.v; }
 using std::pow;
+using std::sin;
 using std::sqrt;
 
 // ---------------------------------------------------------------- kernels (App. A.1)
@@ -888,6 +897,82 @@ State<T> load_state(const OrcParams& P, int nf, int nw, const float* x, const fl
   return S;
 }
 
+// ---------------------------------------------------------------- shifting by optimisation
+// The paper's differentiable particle shifting and density-target sampling (Sec. "New
+// Applications: Differentiable Particle Shifting"): particle positions are optimised against
+//   L = (1/n) sum_i [ w_color (1 - c_i)^2 + w_grad |g_i|^2 + w_density (rho_i - rho^(x_i))^2
+//                     + w_reg sum_{j : |x_ij| < a dp_i} (a dp_i - |x_ij|)^2 ]
+// over the n fluid particles i, with the summation density rho_i = sum_j m_j W_ij (self included,
+// every particle), the colour field c_i = sum_j (m_j / rho_j) W_ij (self included), its gradient
+// g_i = sum_j (m_j / rho_j) grad_i W_ij, the target density rho^ (a sinusoid or a step, the paper's
+// profiles), and the pair penalty below a fraction a of the spacing dp_i = (m_i / rho0)^(1/d).
+// Walls take part as fixed neighbours.  The neighbour set is that of the evaluated positions and
+// is held fixed under differentiation.
+template <class T>
+T target_density(const OrcShiftLoss& o, int d, const T* x) {
+  if (o.target_kind == 0) {
+    T a = T(o.t_phase);
+    for (int k = 0; k < d; ++k) a += T(o.t_k[k]) * x[k];
+    return T(o.t_base) + T(o.t_amp) * sin(a);
+  }
+  double sgn = -o.t_c;
+  for (int k = 0; k < d; ++k) sgn += o.t_n[k] * val(x[k]);
+  return T(sgn < 0.0 ? o.t_lo : o.t_hi);
+}
+
+template <class T>
+T shift_objective(const OrcParams& P, const OrcShiftLoss& o, const State<T>& S, const Pairs& pr) {
+  const int N = S.N(), d = S.d;
+  std::vector<T> rho(N), V(N);
+  auto sep = [&](int i, int j, T* r) {
+    T r2 = T(0.0);
+    for (int k = 0; k < d; ++k) {
+      r[k] = min_image(P, k, S.x[(size_t)i * d + k] - S.x[(size_t)j * d + k]);
+      r2 += r[k] * r[k];
+    }
+    return r2;
+  };
+  for (int i = 0; i < N; ++i) {
+    T acc = T(S.m[i]) * kernel_W<T>(P, T(0.0));
+    for (int64_t t = pr.off[i]; t < pr.off[i + 1]; ++t) {
+      T r[3];
+      T r2 = sep(i, pr.nb[t], r);
+      acc += T(S.m[pr.nb[t]]) * kernel_W<T>(P, sqrt(r2));
+    }
+    rho[i] = acc;
+    V[i] = T(S.m[i]) / acc;
+  }
+  T L = T(0.0);
+  for (int i = 0; i < S.nf; ++i) {
+    T c = V[i] * kernel_W<T>(P, T(0.0));
+    T g[3] = {T(0.0), T(0.0), T(0.0)};
+    T reg = T(0.0);
+    const double delta = o.reg_fraction * std::pow(S.m[i] / P.rho0, 1.0 / d);
+    for (int64_t t = pr.off[i]; t < pr.off[i + 1]; ++t) {
+      const int j = pr.nb[t];
+      T r[3], G[3];
+      T r2 = sep(i, j, r);
+      T rl = sqrt(r2);
+      c += V[j] * kernel_W<T>(P, rl);
+      kernel_gradW<T>(P, r, G);
+      for (int k = 0; k < d; ++k) g[k] += V[j] * G[k];
+      if (val(rl) < delta) reg += (T(delta) - rl) * (T(delta) - rl);
+    }
+    T li = T(0.0);
+    if (o.w_color != 0.0) li += T(o.w_color) * (T(1.0) - c) * (T(1.0) - c);
+    if (o.w_grad != 0.0)
+      for (int k = 0; k < d; ++k) li += T(o.w_grad) * g[k] * g[k];
+    if (o.w_density != 0.0) {
+      T e = rho[i] - target_density<T>(o, d, &S.x[(size_t)i * d]);
+      li += T(o.w_density) * e * e;
+    }
+    if (o.w_reg != 0.0) li += T(o.w_reg) * reg;
+    L += li;
+  }
+  return L / T((double)S.nf);
+}
+
+
 // ---------------------------------------------------------------- reverse pass (Sec. 2.2)
 // Vector-Jacobian product of one continuity-mode step without walls.  Given the adjoints
 // (xb, vb, rb) of the state after the step, overwrite them with the adjoints of the state
@@ -1306,6 +1391,27 @@ int orc_mdbc(const OrcParams* P, int nf, int nw, const float* x, const float* v,
   std::vector<double> rw;
   mdbc_densities(*P, S, rw, sys_out);
   std::copy(rw.begin(), rw.end(), rho_out);
+  return 0;
+}
+
+// Shifting objective at FP64 positions (walls fixed) and its directional derivative along dir
+// (n_fluid * dim; forward mode).  Neighbours from the given positions.
+int orc_shift_objective(const OrcParams* P, int nf, int nw, const double* x, const float* m, const OrcShiftLoss* o,
+                        const double* dir, double* L, double* dL) {
+  const int N = nf + nw, d = P->dim;
+  State<Dual> S;
+  S.nf = nf; S.nw = nw; S.d = d;
+  S.x.resize((size_t)N * d); S.v.assign((size_t)N * d, Dual(0.0)); S.rho.assign(N, Dual(P->rho0)); S.m.resize(N);
+  for (int i = 0; i < N; ++i) {
+    S.m[i] = m[i];
+    for (int k = 0; k < d; ++k)
+      S.x[(size_t)i * d + k] = Dual(x[(size_t)i * d + k], (i < nf && dir) ? dir[(size_t)i * d + k] : 0.0);
+  }
+  S.nu.assign(1, Dual(P->nu));
+  Pairs pr = pairs_of(*P, S);
+  Dual r = shift_objective<Dual>(*P, *o, S, pr);
+  *L = r.v;
+  if (dL) *dL = r.d;
   return 0;
 }
 

@@ -29,7 +29,7 @@ __all__ = [
     "taylor_green_2d", "taylor_green_3d", "dam_break", "perturbed_velocity",
     "served_stream", "SceneSpec",
     "KERNEL_WENDLAND4", "KERNEL_WENDLAND2", "DENSITY_CONTINUITY", "DENSITY_SUMMATION",
-    "DIFFUSION_MC", "DIFFUSION_RENORM", "BOUNDARY_SHEPARD", "BOUNDARY_MDBC",
+    "DIFFUSION_MC", "DIFFUSION_RENORM", "BOUNDARY_SHEPARD", "BOUNDARY_MDBC", "shift_problem",
 ]
 
 KERNEL_WENDLAND4 = 0
@@ -286,3 +286,37 @@ def served_stream(n_scenes: int = 512, rate_hz: float = 80.0, seed: int = 0, n_m
     t = np.cumsum(gaps) - gaps[0]
     return [SceneSpec(int(i), int(n_side[i]), int(steps[i]), bool(adj[i]), float(t[i]), seed=int(i))
             for i in range(n_scenes)]
+
+
+def shift_problem(n_side: int = 32, seed: int = 0, dim: int = 2, walls: bool = False,
+                  support: float = 4.0) -> dict:
+    """The paper's differentiable-shifting setup: n_side^d particles of equal mass sampled uniformly
+    at random in [-1, 1]^d (rho0 = 1, m = 2^d / n), Wendland C4 (2D) or C2 (3D) with support
+    `support` x the mean spacing.  Periodic, or with three layers of fixed wall particles on a
+    regular lattice around the box (`walls`)."""
+    n = n_side ** dim
+    dx = 2.0 / n_side
+    ids = np.arange(n, dtype=np.int64)
+    u = np.stack([uniform24(seed, 7, ids, a).astype(np.float64) for a in range(dim)], 1)
+    xf = -1.0 + 2.0 * u
+    H = support * dx
+    if walls:
+        g = np.arange(-3, n_side + 3)
+        grids = np.meshgrid(*[g] * dim, indexing="ij")
+        pts = np.stack([a.ravel() for a in grids[::-1]], 1)
+        xw = -1.0 + (pts + 0.5) * dx
+        outside = np.any((xw < -1.0) | (xw > 1.0), axis=1)
+        xw = xw[outside]
+        lo, hi, mask = [-1.0 - 4 * dx] * dim, [1.0 + 4 * dx] * dim, 0
+    else:
+        xw = np.zeros((0, dim))
+        lo, hi, mask = [-1.0] * dim, [1.0] * dim, (1 << dim) - 1
+    x = np.concatenate([xf, xw], 0)
+    p = _params(dim, KERNEL_WENDLAND4 if dim == 2 else KERNEL_WENDLAND2, H, 1e-3, 10.0, 0.0, 0.0,
+                tuple(lo), tuple(hi), mask)
+    N = len(x)
+    return dict(
+        name=f"shift{dim}d_{n_side}{'_walls' if walls else ''}", params=p, n_fluid=n, n_wall=len(xw), steps=1,
+        seed=seed, dx=dx, x=x.astype(np.float32), v=np.zeros((N, dim), np.float32),
+        rho=np.ones(N, np.float32), mass=np.full(N, _f32(dx ** dim), np.float32),
+    )
