@@ -180,6 +180,33 @@ SPH_API int sph_get_state(const sph_scene* scene, float* x, float* v, float* rho
  * summation mode).  Original order, fluid particles only.  Any output may be NULL. */
 SPH_API int sph_rates(sph_scene* scene, float* a, float* drho, float* rho_used, int ptr_is_device);
 
+/* Shifting by optimisation (Sec. "New Applications: Differentiable Particle Shifting"): particle
+ * positions are optimised against
+ *   L = (1/n) sum_i [ w_color (1 - c_i)^2 + w_grad |g_i|^2 + w_density (rho_i - t(x_i))^2
+ *                     + w_reg sum_{j: |x_ij| < a dp_i} (a dp_i - |x_ij|)^2 ]
+ * over the n fluid particles of each scene (walls are fixed neighbours), with the summation density
+ * rho_i = sum_j m_j W_ij (self included, every particle), the colour field c_i = sum_j (m_j/rho_j) W_ij
+ * (self included), its gradient g_i = sum_j (m_j/rho_j) grad_i W_ij, the target density t (a
+ * sinusoid t_base + t_amp sin(t_k . x + t_phase), or a step: t_lo where t_n . x < t_c, else t_hi),
+ * and a pair penalty below a = reg_fraction times the spacing dp_i = (m_i/rho0)^(1/d).  The
+ * neighbour set is that of the current positions, held fixed under differentiation.  Only the
+ * positions are used (velocities and the state's densities are ignored). */
+typedef struct sph_shift_objective {
+  float w_color, w_grad, w_density, w_reg, reg_fraction;
+  int32_t target_kind;   /* 0 sinusoid, 1 step */
+  float t_base, t_amp, t_k[3], t_phase;
+  float t_lo, t_hi, t_n[3], t_c;
+} sph_shift_objective;
+
+/* L per scene (host doubles, may be NULL) and dL/dx of every particle row ((n_fluid + n_wall) * dim
+ * floats, original order, walls 0; may be NULL) at the current positions. */
+SPH_API int sph_shift_gradient(sph_scene* scene, const sph_shift_objective* objective, double* loss, float* grad,
+                               int ptr_is_device);
+/* n_iters steps of gradient descent x <- x - step dL/dx on the fluid positions (walls fixed);
+ * loss_hist (host, n_iters * n_scenes doubles, may be NULL) receives L before each step. */
+SPH_API int sph_shift_descend(sph_scene* scene, const sph_shift_objective* objective, int n_iters, float step,
+                              double* loss_hist);
+
 /* Ghost nodes of the wall particles for SPH_BOUNDARY_MDBC: n_wall * dim floats per scene (the
  * walls in their input order; a batch's scenes one after another).  Copied; required before the
  * first step, rate evaluation or rollout of an mDBC scene with walls (SPH_EINVAL otherwise). */
@@ -224,8 +251,8 @@ SPH_API int sph_debug_pairs(sph_scene* scene, int64_t* n_pairs, int32_t* pi, int
 /* Per-kernel device timing.  When enabled, the scene records CUDA events around its launches
  * on its stream; sph_timing returns the accumulated milliseconds and launch count of one
  * kernel class (0 = fused sweep, 1 = rebuild (keys+sort+ranges+permute), 2 = walls,
- * 3 = density, 4 = adjoint sweep, 5 = renormalised density gradient, 6 = particle shifting)
- * and resets it.  Synchronises the stream. */
+ * 3 = density, 4 = adjoint sweep, 5 = renormalised density gradient, 6 = particle shifting,
+ * 7 = shifting-by-optimisation objective, 8 = its gradient) and resets it.  Synchronises the stream. */
 SPH_API int sph_profile(sph_scene* scene, int enable);
 SPH_API int sph_timing(sph_scene* scene, int kernel_class, double* ms, int64_t* launches);
 

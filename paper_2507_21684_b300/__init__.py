@@ -26,7 +26,8 @@ SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EUNSTABLE, SPH_ETIMEOUT, SPH_EBUS
 _NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT", 6: "EBUSY", 7: "EINTERNAL"}
 
 # kernel classes of sph_timing
-TIMING_SWEEP, TIMING_REBUILD, TIMING_WALLS, TIMING_DENSITY, TIMING_ADJOINT, TIMING_GRADIENT, TIMING_SHIFT = range(7)
+TIMING_SWEEP, TIMING_REBUILD, TIMING_WALLS, TIMING_DENSITY, TIMING_ADJOINT, TIMING_GRADIENT, TIMING_SHIFT, \
+    TIMING_OPT_OBJECTIVE, TIMING_OPT_GRADIENT = range(9)
 DIFFUSION_MC, DIFFUSION_RENORM = 0, 1
 BOUNDARY_SHEPARD, BOUNDARY_MDBC = 0, 1
 
@@ -62,6 +63,25 @@ class Params(C.Structure):
             o.box_hi[k] = float(p["box_hi"][k])
             o.g[k] = float(p["g"][k])
         return o
+
+
+class ShiftObjective(C.Structure):
+    _fields_ = [("w_color", C.c_float), ("w_grad", C.c_float), ("w_density", C.c_float), ("w_reg", C.c_float),
+                ("reg_fraction", C.c_float), ("target_kind", C.c_int32),
+                ("t_base", C.c_float), ("t_amp", C.c_float), ("t_k", C.c_float * 3), ("t_phase", C.c_float),
+                ("t_lo", C.c_float), ("t_hi", C.c_float), ("t_n", C.c_float * 3), ("t_c", C.c_float)]
+
+    @classmethod
+    def from_dict(cls, o: dict) -> "ShiftObjective":
+        r = cls()
+        for k in ("w_color", "w_grad", "w_density", "w_reg", "reg_fraction", "t_base", "t_amp", "t_phase",
+                  "t_lo", "t_hi", "t_c"):
+            setattr(r, k, float(o.get(k, 0.0)))
+        r.target_kind = int(o.get("target_kind", 0))
+        for k in range(3):
+            r.t_k[k] = float(o.get("t_k", (0.0, 0.0, 0.0))[k])
+            r.t_n[k] = float(o.get("t_n", (0.0, 0.0, 0.0))[k])
+        return r
 
 
 class Request(C.Structure):
@@ -117,6 +137,8 @@ def lib() -> C.CDLL:
     L.sph_rates.argtypes = [vp, vp, vp, vp, C.c_int]
     L.sph_density_gradient.argtypes = [vp, vp, C.c_int]
     L.sph_set_ghosts.argtypes = [vp, vp, C.c_int]
+    L.sph_shift_gradient.argtypes = [vp, P(ShiftObjective), vp, vp, C.c_int]
+    L.sph_shift_descend.argtypes = [vp, P(ShiftObjective), C.c_int, C.c_float, vp]
     L.sph_rollout.argtypes = [vp, C.c_int, C.c_int]
     L.sph_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
     L.sph_scene_info.argtypes = [vp, P(C.c_int32), P(C.c_int32)]
@@ -293,6 +315,21 @@ class Scene:
         ru = np.empty((nf,), np.float32)
         _check(lib().sph_rates(self._h, a.ctypes.data, dr.ctypes.data, ru.ctypes.data, 0))
         return dict(a=a, drho=dr, rho=ru)
+
+    def shift_gradient(self, objective: dict):
+        """Shifting objective per scene and its gradient w.r.t. every particle row (n x dim, walls 0)."""
+        loss = (C.c_double * self.n_scenes)()
+        g = np.empty((self.n, self.dim), np.float32)
+        o = ShiftObjective.from_dict(objective)
+        _check(lib().sph_shift_gradient(self._h, C.byref(o), loss, g.ctypes.data, 0))
+        return np.array(loss[:]), g
+
+    def shift_descend(self, objective: dict, n_iters: int, step: float):
+        """Gradient descent on the fluid positions; the objective before each step (n_iters x scenes)."""
+        hist = np.empty((int(n_iters), self.n_scenes), np.float64)
+        o = ShiftObjective.from_dict(objective)
+        _check(lib().sph_shift_descend(self._h, C.byref(o), int(n_iters), float(step), hist.ctypes.data))
+        return hist
 
     def set_ghosts(self, ghost):
         """mDBC ghost nodes of the wall particles (n_wall x dim, walls in input order; a batch's

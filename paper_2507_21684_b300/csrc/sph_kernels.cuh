@@ -35,6 +35,14 @@ struct Displace {
   int interval;          // rebuild_interval
 };
 
+// Objective of the shifting-by-optimisation passes (weights, pair penalty, target density).
+struct ShiftObjective {
+  float w_color, w_grad, w_density, w_reg, reg_fraction;
+  int target_kind;  // 0: t_base + t_amp sin(t_k . x + t_phase); 1: t_lo where t_n . x < t_c, else t_hi
+  float t_base, t_amp, t_k[3], t_phase;
+  float t_lo, t_hi, t_n[3], t_c;
+};
+
 // Outputs of the rate evaluation (original order, fluid only).
 struct RateOut {
   float* a;

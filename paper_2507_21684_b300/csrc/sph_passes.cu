@@ -8,6 +8,7 @@
 //   sweep           continuity + delta diffusion, Tait pressure, viscosity, gravity, and the
 //                   kick-drift epilogue (Sec. 2.3, Sec. 3.4); also the rate-only evaluation
 //   shift           explicit particle shifting at the end of a step (free-surface aware)
+//   opt P1..P4      shifting by optimisation: objective, its gradient, a descent step
 //   pairs           exact pair export (FP64 predicate in a guard band)
 //   adjoint sweep   vector-Jacobian product of one step, gathered per particle (Sec. 2.2)
 #include <algorithm>
@@ -1350,6 +1351,351 @@ struct AdjPass {
   }
 };
 
+// ================================================================== shifting by optimisation
+// The paper's differentiable particle shifting / density-target sampling: the objective
+//   L = (1/n) sum_i [ w_c (1 - c_i)^2 + w_g |g_i|^2 + w_r (rho_i - t(x_i))^2 + w_p sum_{|x_ij| < a dp_i} (a dp_i - |x_ij|)^2 ]
+// over the fluid (walls are fixed neighbours), rho_i = sum_j m_j W_ij (self included, every
+// particle), c_i = sum_j V_j W_ij (self included), g_i = sum_j V_j grad_i W_ij, V_j = m_j / rho_j,
+// and its gradient with respect to the fluid positions, hand-derived and gathered per particle
+// in four passes (atomic-free):
+//   P1  rho_i, V_i                                             (every particle)
+//   P2  c_i, g_i, the penalty; loss l_i; seeds cb_i = -2 w_c (1 - c_i)/n, gb_i = 2 w_g g_i / n
+//   P3  Vb_i = cb_i W(0) + sum_j [cb_j W_ij - gK (gb_j . r_ij)],  rhob_i = 2 w_r e_i / n - Vb_i V_i / rho_i
+//       (every particle), and for the fluid xb_i = sum_j [(cb_i V_j + cb_j V_i) gK r_ij
+//       + Hess W_ij (V_j gb_i - V_i gb_j) + penalty terms] - 2 w_r e_i grad t(x_i) / n
+//   P4  xb_i += sum_j (rhob_i m_j + rhob_j m_i) gK r_ij; the gradient out, or a descent step
+// (r_ij = x_i - x_j, grad_i W_ij = gK r_ij, Hess W_ij = gK I + hK r r^T, e_i = rho_i - t(x_i)).
+template <int D>
+__device__ __forceinline__ float target_density(const ShiftObjective& o, const float* x, float* grad) {
+  if (o.target_kind == 0) {
+    float a = o.t_phase;
+#pragma unroll
+    for (int k = 0; k < D; ++k) a = fmaf(o.t_k[k], x[k], a);
+    float sn, cs;
+    sincosf(a, &sn, &cs);
+#pragma unroll
+    for (int k = 0; k < D; ++k) grad[k] = o.t_amp * cs * o.t_k[k];
+    return fmaf(o.t_amp, sn, o.t_base);
+  }
+  float sg = -o.t_c;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    sg = fmaf(o.t_n[k], x[k], sg);
+    grad[k] = 0.f;
+  }
+  return sg < 0.f ? o.t_lo : o.t_hi;
+}
+
+template <int D, int KERN>
+struct OptDensityPass {
+  struct Body {
+    const DevSeg* s;
+    float rho;
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4, float, int) {
+      float r[D];
+      const float r2 = diff<D>(xs, pj.x, r);
+      rho = fmaf(fabsf(pj.m), s->Kw * kern_w<KERN>(safe_q(r2, s->invH)), rho);
+    }
+    template <int L>
+    __device__ __forceinline__ void reduce() { rho = group_sum<L>(rho); }
+  };
+  float4* S1;  // (V, rho, 0, 0)
+  __device__ static __forceinline__ bool wants(uint32_t) { return true; }
+  __device__ __forceinline__ void skip(int, const TgtView&) {}
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ void last_cta() {}
+  __device__ __forceinline__ const float4* tex0() const { return nullptr; }
+  __device__ __forceinline__ const float4* tex1() const { return nullptr; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView&) {
+    b.s = &s;
+    b.rho = 0.f;
+    return true;
+  }
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i, const TgtView& tv) {
+    const float m = fabsf(load_pd_plain<D>(tv.a, tv.k).m);
+    const float rho = fmaf(m, s.Kw, b.rho);  // self term, w(0) = 1
+    S1[i] = make_float4(m / rho, rho, 0.f, 0.f);
+  }
+};
+
+template <int D, int KERN>
+struct OptColorPass {
+  struct Body {
+    const DevSeg* s;
+    float delta, c, reg, g[D];
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4 e, float, int) {
+      float r[D];
+      const float r2 = diff<D>(xs, pj.x, r);
+      const float q = safe_q(r2, s->invH);
+      const float Vj = e.x;
+      c = fmaf(Vj, s->Kw * kern_w<KERN>(q), c);
+      const float VgK = Vj * (s->Kg * kern_gt<KERN>(q));
+#pragma unroll
+      for (int k = 0; k < D; ++k) g[k] = fmaf(VgK, r[k], g[k]);
+      const float rl = sqrtf(r2);
+      if (rl < delta) reg = fmaf(delta - rl, delta - rl, reg);
+    }
+    template <int L>
+    __device__ __forceinline__ void reduce() {
+      c = group_sum<L>(c);
+      reg = group_sum<L>(reg);
+#pragma unroll
+      for (int k = 0; k < D; ++k) g[k] = group_sum<L>(g[k]);
+    }
+  };
+  const float4* S1;
+  float4* S2;  // (cb, gb)
+  float* Lp;   // loss contribution of each particle (0 for walls)
+  ShiftObjective o;
+  __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) == 0; }
+  __device__ __forceinline__ void skip(int i, const TgtView&) {
+    S2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    Lp[i] = 0.f;
+  }
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ void last_cta() {}
+  __device__ __forceinline__ const float4* tex0() const { return S1; }
+  __device__ __forceinline__ const float4* tex1() const { return nullptr; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView& tv) {
+    b.s = &s;
+    const float m = load_pd_plain<D>(tv.a, tv.k).m;
+    const float vol = fabsf(m) / s.rho0;
+    b.delta = o.reg_fraction * (D == 2 ? sqrtf(vol) : cbrtf(vol));
+    b.c = b.reg = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) b.g[k] = 0.f;
+    return m > 0.f;
+  }
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i, const TgtView& tv) {
+    const PD<D> me = load_pd_plain<D>(tv.a, tv.k);
+    if (!(me.m > 0.f)) {
+      skip(i, tv);
+      return;
+    }
+    const float4 s1 = tv.e0[tv.k];
+    const float inv_n = 1.f / (float)s.nf;
+    const float c = fmaf(s1.x, s.Kw, b.c);  // self term
+    float gt[3];
+    const float e = s1.y - target_density<D>(o, me.x, gt);
+    float g2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) g2 = fmaf(b.g[k], b.g[k], g2);
+    const float l = o.w_color * (1.f - c) * (1.f - c) + o.w_grad * g2 + o.w_density * e * e + o.w_reg * b.reg;
+    Lp[i] = l * inv_n;
+    const float gb = 2.f * o.w_grad * inv_n;
+    S2[i] = make_float4(-2.f * o.w_color * (1.f - c) * inv_n, gb * b.g[0], gb * b.g[1], D == 3 ? gb * b.g[D - 1] : 0.f);
+  }
+};
+
+template <int D, int KERN>
+struct OptAdjPass {
+  struct Body {
+    const DevSeg* s;
+    float cb, gb[D], V, delta, wr;  // the target's seeds, volume, penalty reach, 2 w_p / n
+    bool fluid;
+    float Vb, xb[D];
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4 e, float Vj, int) {
+      float r[D];
+      const float r2 = diff<D>(xs, pj.x, r);
+      const float q = safe_q(r2, s->invH);
+      const float W = s->Kw * kern_w<KERN>(q);
+      const float gK = s->Kg * kern_gt<KERN>(q);
+      const float gbj[3] = {e.y, e.z, e.w};
+      float gr = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) gr = fmaf(gbj[k], r[k], gr);
+      Vb = fmaf(e.x, W, fmaf(-gK, gr, Vb));
+      if (!fluid) return;
+      const float hK = s->Kh * kern_ht<KERN>(q);
+      const float coef = fmaf(cb, Vj, e.x * V) * gK;
+      float v[D], rv = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        v[k] = fmaf(Vj, gb[k], -V * gbj[k]);
+        rv = fmaf(r[k], v[k], rv);
+      }
+      float pen = 0.f;  // pair penalty: d/dx_i of (a dp - |r|)^2 from both ends' terms
+      const float rl = sqrtf(r2);
+      if (rl < delta) pen += delta - rl;
+      if (pj.m > 0.f) {
+        const float volj = pj.m / s->rho0;
+        const float dj = delta_frac * (D == 2 ? sqrtf(volj) : cbrtf(volj));
+        if (rl < dj) pen += dj - rl;
+      }
+      const float pc = rl > 0.f ? -wr * pen / rl : 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) xb[k] += fmaf(coef + hK * rv + pc, r[k], gK * v[k]);
+    }
+    float delta_frac;
+    template <int L>
+    __device__ __forceinline__ void reduce() {
+      Vb = group_sum<L>(Vb);
+#pragma unroll
+      for (int k = 0; k < D; ++k) xb[k] = group_sum<L>(xb[k]);
+    }
+  };
+  const float4* S1;
+  const float4* S2;
+  float4* XB;  // (xb partial, rhob)
+  ShiftObjective o;
+  __device__ static __forceinline__ bool wants(uint32_t) { return true; }
+  __device__ __forceinline__ void skip(int, const TgtView&) {}
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ void last_cta() {}
+  __device__ __forceinline__ const float4* tex0() const { return S2; }
+  __device__ __forceinline__ const float4* tex1() const { return S1; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView& tv) {
+    b.s = &s;
+    const float m = load_pd_plain<D>(tv.a, tv.k).m;
+    const float4 s2 = tv.e0[tv.k], s1 = tv.e1[tv.k];
+    const float inv_n = 1.f / (float)s.nf;
+    b.cb = s2.x;
+    b.gb[0] = s2.y;
+    b.gb[1] = s2.z;
+    if (D == 3) b.gb[D - 1] = s2.w;
+    b.V = s1.x;
+    b.fluid = m > 0.f;
+    const float vol = fabsf(m) / s.rho0;
+    b.delta_frac = o.reg_fraction;
+    b.delta = b.fluid ? o.reg_fraction * (D == 2 ? sqrtf(vol) : cbrtf(vol)) : 0.f;
+    b.wr = 2.f * o.w_reg * inv_n;
+    b.Vb = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) b.xb[k] = 0.f;
+    return true;
+  }
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i, const TgtView& tv) {
+    const PD<D> me = load_pd_plain<D>(tv.a, tv.k);
+    const float4 s1 = tv.e1[tv.k];
+    const float inv_n = 1.f / (float)s.nf;
+    const float Vb = fmaf(b.cb, s.Kw, b.Vb);  // self term of the colour field
+    float rhob = -Vb * s1.x / s1.y;
+    float xb[3] = {0.f, 0.f, 0.f};
+    if (b.fluid) {
+      float gt[3];
+      const float e = s1.y - target_density<D>(o, me.x, gt);
+      const float se = 2.f * o.w_density * e * inv_n;
+      rhob += se;
+#pragma unroll
+      for (int k = 0; k < D; ++k) xb[k] = fmaf(-se, gt[k], b.xb[k]);
+    }
+    XB[i] = make_float4(xb[0], xb[1], xb[2], rhob);
+  }
+};
+
+template <int D, int KERN, bool UPDATE>
+struct OptAdj2Pass {
+  struct Body {
+    const DevSeg* s;
+    float rb, m;
+    float xb[D];
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4 e, float, int) {
+      float r[D];
+      const float r2 = diff<D>(xs, pj.x, r);
+      const float gK = s->Kg * kern_gt<KERN>(safe_q(r2, s->invH));
+      const float coef = fmaf(rb, fabsf(pj.m), e.w * m) * gK;
+#pragma unroll
+      for (int k = 0; k < D; ++k) xb[k] = fmaf(coef, r[k], xb[k]);
+    }
+    template <int L>
+    __device__ __forceinline__ void reduce() {
+#pragma unroll
+      for (int k = 0; k < D; ++k) xb[k] = group_sum<L>(xb[k]);
+    }
+  };
+  const float4* XB;
+  float4* G;     // the gradient dL/dx (0 for walls)
+  Arrays out;    // UPDATE: the state after the descent step x <- x - step dL/dx
+  float step;
+  __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) == 0; }
+  __device__ __forceinline__ void skip(int i, const TgtView& tv) {
+    G[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (UPDATE) {
+      store_pd<D>(out, i, load_pd_plain<D>(tv.a, tv.k));
+      store_cold<D>(out, i, load_cold<D>(tv.a, tv.k));
+      out.meta[i] = tv.a.meta[tv.k];
+    }
+  }
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ void last_cta() {}
+  __device__ __forceinline__ const float4* tex0() const { return XB; }
+  __device__ __forceinline__ const float4* tex1() const { return nullptr; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView& tv) {
+    b.s = &s;
+    b.rb = tv.e0[tv.k].w;
+    b.m = load_pd_plain<D>(tv.a, tv.k).m;
+#pragma unroll
+    for (int k = 0; k < D; ++k) b.xb[k] = 0.f;
+    return b.m > 0.f;
+  }
+  __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i, const TgtView& tv) {
+    PD<D> me = load_pd_plain<D>(tv.a, tv.k);
+    if (!(me.m > 0.f)) {
+      skip(i, tv);
+      return;
+    }
+    const float4 p = tv.e0[tv.k];
+    const float ps[3] = {p.x, p.y, p.z};
+    float gx[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < D; ++k) gx[k] = ps[k] + b.xb[k];
+    G[i] = make_float4(gx[0], gx[1], gx[2], 0.f);
+    if (UPDATE) {
+      Cold c = load_cold<D>(tv.a, tv.k);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        ds_add(c.hi[k], c.lo[k], -step * gx[k]);
+        me.x[k] = __fadd_rn(__fsub_rn(c.hi[k], c.off[k]), c.lo[k]);
+      }
+      store_pd<D>(out, i, me);
+      store_cold<D>(out, i, c);
+      out.meta[i] = tv.a.meta[tv.k];
+    }
+  }
+};
+
+template <int D, int KERN>
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_opt_density(TravArgs t, const Tile* tiles, const int* ntiles, float4* S1) {
+  OptDensityPass<D, KERN> pass;
+  pass.S1 = S1;
+  run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
+}
+template <int D, int KERN>
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_opt_color(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S1, float4* S2,
+                                                 float* Lp, ShiftObjective o) {
+  OptColorPass<D, KERN> pass;
+  pass.S1 = S1;
+  pass.S2 = S2;
+  pass.Lp = Lp;
+  pass.o = o;
+  run_tiles<D, 1, 0>(t, tiles, ntiles, S1, nullptr, pass);
+}
+template <int D, int KERN>
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, 512 / TileCfg<D>::THREADS) k_opt_adj(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S1, const float4* S2,
+                                               const float* Vs, float4* XB, ShiftObjective o) {
+  OptAdjPass<D, KERN> pass;
+  pass.S1 = S1;
+  pass.S2 = S2;
+  pass.XB = XB;
+  pass.o = o;
+  run_tiles<D, 2, 0>(t, tiles, ntiles, S2, Vs, pass);
+}
+template <int D, int KERN, bool UPDATE>
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_opt_adj2(TravArgs t, const Tile* tiles, const int* ntiles, const float4* XB, float4* G,
+                                                Arrays out, float step) {
+  OptAdj2Pass<D, KERN, UPDATE> pass;
+  pass.XB = XB;
+  pass.G = G;
+  pass.out = out;
+  pass.step = step;
+  run_tiles<D, 1, 0>(t, tiles, ntiles, XB, nullptr, pass);
+}
+// the volumes of P1 as a plain float array (the second staged payload of P3)
+__global__ void k_opt_volumes(int N, const float4* __restrict__ S1, float* __restrict__ V) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) V[i] = S1[i].x;
+}
+
 // ================================================================== kernels
 // The wall pass visits only the tiles that hold a wall particle (listed at each rebuild).
 template <int D, int KERN>
@@ -1587,6 +1933,27 @@ void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int t
   k_adj_t<D, KERN><<<pass_grid((const void*)k_adj_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(D == 2 ? 1 : 2), st>>>(
       t, tiles, ntiles, S, Pp, XBin, VBin, XBout, VBout, nu_part);
 }
+// Shifting-by-optimisation passes: the objective (P1, P2) and its gradient (P3, P4; with `out`, the
+// descent step).  Buffers: S1, S2, XB, G (float4 x N), V, Lp (N).
+template <int D, int KERN>
+void launch_opt_forward(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper,
+                        const ShiftObjective& o, float4* S1, float4* S2, float* V, float* Lp, cudaStream_t st) {
+  const int TH = TileCfg<D>::THREADS;
+  k_opt_density<D, KERN><<<pass_grid((const void*)k_opt_density<D, KERN>, tiles_upper), TH, pass_smem<D>(0), st>>>(t, tiles, ntiles, S1);
+  k_opt_color<D, KERN><<<pass_grid((const void*)k_opt_color<D, KERN>, tiles_upper), TH, pass_smem<D>(1), st>>>(t, tiles, ntiles, S1, S2, Lp, o);
+  if (t.N > 0) k_opt_volumes<<<(t.N + 255) / 256, 256, 0, st>>>(t.N, S1, V);
+}
+template <int D, int KERN>
+void launch_opt_backward(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper,
+                         const ShiftObjective& o, const float4* S1, const float4* S2, const float* V, float4* XB,
+                         float4* G, const Arrays* out, float step, cudaStream_t st) {
+  const int TH = TileCfg<D>::THREADS;
+  k_opt_adj<D, KERN><<<pass_grid((const void*)k_opt_adj<D, KERN>, tiles_upper), TH, pass_smem<D>(2), st>>>(t, tiles, ntiles, S1, S2, V, XB, o);
+  if (out)
+    k_opt_adj2<D, KERN, true><<<pass_grid((const void*)k_opt_adj2<D, KERN, true>, tiles_upper), TH, pass_smem<D>(1), st>>>(t, tiles, ntiles, XB, G, *out, step);
+  else
+    k_opt_adj2<D, KERN, false><<<pass_grid((const void*)k_opt_adj2<D, KERN, false>, tiles_upper), TH, pass_smem<D>(1), st>>>(t, tiles, ntiles, XB, G, Arrays{}, 0.f);
+}
 void launch_sum_segments(const float* part, const DevSeg* segs, int S, double* acc, cudaStream_t st) {
   k_sum_segments<<<S, 1024, 0, st>>>(part, segs, acc);
 }
@@ -1613,6 +1980,16 @@ cudaError_t configure_passes() {
   SPH_ATTR(3, (k_sweep_t<3, 0, true, true>), pass_smem<3>(1)) SPH_ATTR(3, (k_sweep_t<3, 1, true, true>), pass_smem<3>(1))
   SPH_ATTR(2, (k_sweep_t<2, 0, false, true>), pass_smem<2>(1)) SPH_ATTR(2, (k_sweep_t<2, 1, false, true>), pass_smem<2>(1))
   SPH_ATTR(3, (k_sweep_t<3, 0, false, true>), pass_smem<3>(1)) SPH_ATTR(3, (k_sweep_t<3, 1, false, true>), pass_smem<3>(1))
+  SPH_ATTR(2, (k_opt_density<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_opt_density<2, 1>), pass_smem<2>(0))
+  SPH_ATTR(3, (k_opt_density<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_opt_density<3, 1>), pass_smem<3>(0))
+  SPH_ATTR(2, (k_opt_color<2, 0>), pass_smem<2>(1)) SPH_ATTR(2, (k_opt_color<2, 1>), pass_smem<2>(1))
+  SPH_ATTR(3, (k_opt_color<3, 0>), pass_smem<3>(1)) SPH_ATTR(3, (k_opt_color<3, 1>), pass_smem<3>(1))
+  SPH_ATTR(2, (k_opt_adj<2, 0>), pass_smem<2>(2)) SPH_ATTR(2, (k_opt_adj<2, 1>), pass_smem<2>(2))
+  SPH_ATTR(3, (k_opt_adj<3, 0>), pass_smem<3>(2)) SPH_ATTR(3, (k_opt_adj<3, 1>), pass_smem<3>(2))
+  SPH_ATTR(2, (k_opt_adj2<2, 0, true>), pass_smem<2>(1)) SPH_ATTR(2, (k_opt_adj2<2, 1, true>), pass_smem<2>(1))
+  SPH_ATTR(3, (k_opt_adj2<3, 0, true>), pass_smem<3>(1)) SPH_ATTR(3, (k_opt_adj2<3, 1, true>), pass_smem<3>(1))
+  SPH_ATTR(2, (k_opt_adj2<2, 0, false>), pass_smem<2>(1)) SPH_ATTR(2, (k_opt_adj2<2, 1, false>), pass_smem<2>(1))
+  SPH_ATTR(3, (k_opt_adj2<3, 0, false>), pass_smem<3>(1)) SPH_ATTR(3, (k_opt_adj2<3, 1, false>), pass_smem<3>(1))
   SPH_ATTR(2, (k_walls_sweep_t<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_walls_sweep_t<2, 1>), pass_smem<2>(0))
   SPH_ATTR(3, (k_walls_sweep_t<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_walls_sweep_t<3, 1>), pass_smem<3>(0))
   SPH_ATTR(2, (k_shift_t<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_shift_t<2, 1>), pass_smem<2>(0))
@@ -1636,6 +2013,11 @@ SPH_INST_PD(3)
   template void launch_walls_t<D, K>(const TravArgs&, const Tile*, const int*, const int*, int, cudaStream_t); \
   template void launch_density_t<D, K>(const TravArgs&, const Tile*, const int*, int, cudaStream_t);        \
   template void launch_grad_t<D, K>(const TravArgs&, const Tile*, const int*, int, float4*, cudaStream_t);   \
+  template void launch_opt_forward<D, K>(const TravArgs&, const Tile*, const int*, int, const ShiftObjective&, \
+                                         float4*, float4*, float*, float*, cudaStream_t);                     \
+  template void launch_opt_backward<D, K>(const TravArgs&, const Tile*, const int*, int, const ShiftObjective&, \
+                                          const float4*, const float4*, const float*, float4*, float4*,       \
+                                          const Arrays*, float, cudaStream_t);                                \
   template void launch_mdbc<D, K>(const TravArgs&, const Tile*, const int*, const int*, int, const float4*,  \
                                   const int*, cudaStream_t);                                                 \
   template void launch_walls_sweep_t<D, K>(const TravArgs&, const Tile*, const int*, const int*, const int*, int, \

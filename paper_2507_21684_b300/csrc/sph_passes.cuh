@@ -36,6 +36,13 @@ void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int
 template <int D, int KERN>
 void launch_shift_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
                     const Displace& disp, cudaStream_t st);
+template <int D, int KERN>
+void launch_opt_forward(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper,
+                        const ShiftObjective& o, float4* S1, float4* S2, float* V, float* Lp, cudaStream_t st);
+template <int D, int KERN>
+void launch_opt_backward(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper,
+                         const ShiftObjective& o, const float4* S1, const float4* S2, const float* V, float4* XB,
+                         float4* G, const Arrays* out, float step, cudaStream_t st);
 template <int D>
 void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
                     unsigned long long* count, long long cap, cudaStream_t st);

@@ -1272,6 +1272,105 @@ void Scene::density_gradient(float* grad, int is_dev) {
   CK(cudaStreamSynchronize(st));
 }
 
+// Shifting by optimisation: the objective's passes on fresh cells of the current positions, the
+// per-scene loss summed into loss_slot (S doubles, zeroed here), the gradient into opt_G, and with
+// `out` a descent step into that buffer.
+void Scene::opt_passes(const ShiftObjective& o, const Arrays* out, float step, double* loss_slot) {
+  if (!opt_S1) {
+    opt_S1 = (float4*)mem.get(sizeof(float4) * N);
+    opt_S2 = (float4*)mem.get(sizeof(float4) * N);
+    opt_XB = (float4*)mem.get(sizeof(float4) * N);
+    opt_G = (float4*)mem.get(sizeof(float4) * N);
+    opt_V = (float*)mem.get(sizeof(float) * N);
+    opt_L = (float*)mem.get(sizeof(float) * N);
+  }
+  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  t.pair_count = nullptr;
+  prof_begin(7);  // the objective
+  if (D == 2) {
+    if (kern == 0) launch_opt_forward<2, 0>(t, tiles, d_ntiles, tiles_upper, o, opt_S1, opt_S2, opt_V, opt_L, st);
+    else launch_opt_forward<2, 1>(t, tiles, d_ntiles, tiles_upper, o, opt_S1, opt_S2, opt_V, opt_L, st);
+  } else {
+    if (kern == 0) launch_opt_forward<3, 0>(t, tiles, d_ntiles, tiles_upper, o, opt_S1, opt_S2, opt_V, opt_L, st);
+    else launch_opt_forward<3, 1>(t, tiles, d_ntiles, tiles_upper, o, opt_S1, opt_S2, opt_V, opt_L, st);
+  }
+  CKL();
+  prof_end();
+  prof_begin(8);  // its gradient (and the descent step)
+  if (D == 2) {
+    if (kern == 0) launch_opt_backward<2, 0>(t, tiles, d_ntiles, tiles_upper, o, opt_S1, opt_S2, opt_V, opt_XB, opt_G, out, step, st);
+    else launch_opt_backward<2, 1>(t, tiles, d_ntiles, tiles_upper, o, opt_S1, opt_S2, opt_V, opt_XB, opt_G, out, step, st);
+  } else {
+    if (kern == 0) launch_opt_backward<3, 0>(t, tiles, d_ntiles, tiles_upper, o, opt_S1, opt_S2, opt_V, opt_XB, opt_G, out, step, st);
+    else launch_opt_backward<3, 1>(t, tiles, d_ntiles, tiles_upper, o, opt_S1, opt_S2, opt_V, opt_XB, opt_G, out, step, st);
+  }
+  CKL();
+  prof_end();
+  launches += 5;
+  CK(cudaMemsetAsync(loss_slot, 0, sizeof(double) * S, st));
+  launch_sum_segments(opt_L, dseg, S, loss_slot, st);
+  CKL();
+  ++launches;
+}
+
+static ShiftObjective check_objective(const sph_shift_objective& q) {
+  const float w[5] = {q.w_color, q.w_grad, q.w_density, q.w_reg, q.reg_fraction};
+  for (float v : w)
+    if (!(v >= 0.f) || !std::isfinite(v)) einval("objective weights and reg_fraction must be finite and >= 0");
+  if (q.target_kind != 0 && q.target_kind != 1) einval("target_kind must be 0 (sinusoid) or 1 (step)");
+  ShiftObjective o;
+  o.w_color = q.w_color; o.w_grad = q.w_grad; o.w_density = q.w_density; o.w_reg = q.w_reg;
+  o.reg_fraction = q.reg_fraction; o.target_kind = q.target_kind;
+  o.t_base = q.t_base; o.t_amp = q.t_amp; o.t_phase = q.t_phase; o.t_lo = q.t_lo; o.t_hi = q.t_hi; o.t_c = q.t_c;
+  for (int k = 0; k < 3; ++k) {
+    o.t_k[k] = q.t_k[k];
+    o.t_n[k] = q.t_n[k];
+  }
+  return o;
+}
+
+void Scene::shift_gradient(const ShiftObjective& o, double* loss, float* grad, int is_dev) {
+  for (int s = 0; s < S; ++s)
+    if (segs[s].nf < 1) einval("sph_shift_gradient: every scene needs fluid particles");
+  host_rebuild();  // cells of the current positions
+  if (opt_loss_cap < 1) {
+    opt_loss = (double*)mem.get(sizeof(double) * S);
+    opt_loss_cap = 1;
+  }
+  opt_passes(o, nullptr, 0.f, opt_loss);
+  if (loss) CK(cudaMemcpyAsync(loss, opt_loss, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
+  if (grad) {
+    const size_t nd = (size_t)N * D;
+    float* outp = is_dev ? grad : (float*)mem_tmp(sizeof(float) * (nd + 64));
+    // the adjoint's unpermuting store writes the xyz of a float4 array to original rows
+    if (D == 2)
+      launch_adj_store<2>(N, buf[cur].meta, d_orig_base, opt_G, opt_G, outp, nullptr, nullptr, st);
+    else
+      launch_adj_store<3>(N, buf[cur].meta, d_orig_base, opt_G, opt_G, outp, nullptr, nullptr, st);
+    CKL();
+    if (!is_dev) CK(cudaMemcpyAsync(grad, outp, 4 * nd, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+}
+
+void Scene::shift_descend(const ShiftObjective& o, int n_iters, float step, double* loss_hist) {
+  if (n_iters < 1 || !(step >= 0.f) || !std::isfinite(step)) einval("sph_shift_descend: n_iters >= 1 and a finite step >= 0");
+  for (int s = 0; s < S; ++s)
+    if (segs[s].nf < 1) einval("sph_shift_descend: every scene needs fluid particles");
+  if (opt_loss_cap < n_iters) {
+    opt_loss = (double*)mem.get(sizeof(double) * (size_t)S * n_iters);
+    opt_loss_cap = n_iters;
+  }
+  for (int it = 0; it < n_iters; ++it) {
+    host_rebuild();
+    opt_passes(o, &buf[1 - cur], step, opt_loss + (size_t)it * S);
+    cur = 1 - cur;
+  }
+  cells_valid = false;  // the positions moved after the last build
+  if (loss_hist) CK(cudaMemcpyAsync(loss_hist, opt_loss, sizeof(double) * S * n_iters, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+}
+
 // Launch and rebuild counters since the scene was created (device rebuilds read back).
 void Scene::stats(int64_t* steps, int64_t* rebuilds, int64_t* n_launches) {
   RebuildCtl c{};
@@ -1513,6 +1612,32 @@ int sph_rates(sph_scene* sc, float* a, float* drho, float* rho_used, int ptr_is_
   API_BEGIN
   sc->s.enter();
   sc->s.rates(a, drho, rho_used, ptr_is_device);
+  sc->s.leave();
+  API_END
+}
+
+int sph_shift_gradient(sph_scene* sc, const sph_shift_objective* obj, double* loss, float* grad, int ptr_is_device) {
+  if (!sc || !obj) {
+    sph::set_err("sph_shift_gradient: NULL scene or objective");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  const sph::ShiftObjective o = sph::check_objective(*obj);
+  sc->s.enter();
+  sc->s.shift_gradient(o, loss, grad, ptr_is_device);
+  sc->s.leave();
+  API_END
+}
+
+int sph_shift_descend(sph_scene* sc, const sph_shift_objective* obj, int n_iters, float step, double* loss_hist) {
+  if (!sc || !obj) {
+    sph::set_err("sph_shift_descend: NULL scene or objective");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  const sph::ShiftObjective o = sph::check_objective(*obj);
+  sc->s.enter();
+  sc->s.shift_descend(o, n_iters, step, loss_hist);
   sc->s.leave();
   API_END
 }

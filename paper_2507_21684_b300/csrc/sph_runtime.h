@@ -94,6 +94,11 @@ struct Scene {
   bool mdbc = false;                // mDBC wall treatment (ghost nodes) instead of Shepard's
   float4* ghosts = nullptr;         // mDBC ghost node of each particle row (walls), original order
   bool ghosts_set = false;
+  // shifting by optimisation (allocated on first use)
+  float4 *opt_S1 = nullptr, *opt_S2 = nullptr, *opt_XB = nullptr, *opt_G = nullptr;
+  float *opt_V = nullptr, *opt_L = nullptr;
+  double* opt_loss = nullptr;
+  int opt_loss_cap = 0;
   float4* gradrho = nullptr;        // <grad rho>^L per particle, sorted order (renorm, or on request)
   float skin = 0.f;
   int interval = 1;
@@ -218,6 +223,9 @@ struct Scene {
   void check_status();
   void rates(float* a, float* drho, float* rho, int is_dev);
   void density_gradient(float* grad, int is_dev);
+  void opt_passes(const ShiftObjective& o, const Arrays* out, float step, double* loss_slot);
+  void shift_gradient(const ShiftObjective& o, double* loss, float* grad, int is_dev);
+  void shift_descend(const ShiftObjective& o, int n_iters, float step, double* loss_hist);
   void debug_cells(int64_t* start, int32_t* ids);
   void debug_pairs(int64_t* n_pairs, int32_t* pi, int32_t* pj, int64_t cap);
   void timing(int cls, double* ms, int64_t* count);
