@@ -207,6 +207,22 @@ SPH_API int sph_shift_gradient(sph_scene* scene, const sph_shift_objective* obje
 SPH_API int sph_shift_descend(sph_scene* scene, const sph_shift_objective* objective, int n_iters, float step,
                               double* loss_hist);
 
+/* Variable support radius (the paper's symmetric neighbour search for per-particle radii): radii
+ * H_i of every particle row ((n_fluid + n_wall) floats, original order), 0 < H_i <= the scene's H
+ * (which sizes the cells).  Kept with the particles; the time step itself keeps the uniform H.
+ * With radii set, sph_debug_pairs returns the pairs with |x_ij| < max(H_i, H_j) (FP64 decision).
+ * Single scenes. */
+SPH_API int sph_set_support(sph_scene* scene, const float* H, int ptr_is_device);
+/* At the current positions, per particle row (any output may be NULL; radii H_i, or the scene's H
+ * where none were set):
+ *   search_radius  s_i = max(H_i, max{H_k : |x_ik| < H_k})   (the neighbour search's radius: every
+ *                  j with |x_ij| < max(H_i, H_j) lies within s_i; exact, FP64 decisions)
+ *   rho_super      sum_j m_j (W(|x_ij|, H_i) + W(|x_ij|, H_j)) / 2 over |x_ij| < max(H_i, H_j)
+ *   rho_gather     sum_j m_j W(|x_ij|, H_i) over |x_ij| < H_i
+ * (self terms included; W(r, h) = C_d / h^d w(r / h)). */
+SPH_API int sph_support_query(sph_scene* scene, float* search_radius, float* rho_super, float* rho_gather,
+                              int ptr_is_device);
+
 /* Ghost nodes of the wall particles for SPH_BOUNDARY_MDBC: n_wall * dim floats per scene (the
  * walls in their input order; a batch's scenes one after another).  Copied; required before the
  * first step, rate evaluation or rollout of an mDBC scene with walls (SPH_EINVAL otherwise). */

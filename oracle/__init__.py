@@ -119,6 +119,9 @@ def lib():
         L.orc_shift.argtypes = [_P(OrcParams), C.c_int, C.c_int, _f, _f, _f, _f, _d, _d]
         L.orc_gen_pinv.argtypes = [C.c_int, _d, _d]
         L.orc_shift_objective.argtypes = [_P(OrcParams), C.c_int, C.c_int, _d, _f, _P(OrcShiftLoss), _d, _d, _d]
+        L.orc_support.argtypes = [_P(OrcParams), C.c_int, _f, _f, _f, _d, _d, _d]
+        L.orc_pairs_var.argtypes = [_P(OrcParams), C.c_int, _f, _f, C.c_int64, _i32, _i32]
+        L.orc_pairs_var.restype = C.c_int64
         L.orc_mdbc.argtypes = [_P(OrcParams), C.c_int, C.c_int, _f, _f, _f, _f, _d, _d]
         _lib = L
     return _lib
@@ -317,6 +320,33 @@ def shift_gradient(scene: dict, loss: dict, x=None):
             g[i, k] = shift_objective(scene, loss, x, e)[1]
             e[i, k] = 0.0
     return g
+
+
+def support(scene: dict, h: np.ndarray):
+    """Search radius, super-symmetric and gather densities with per-particle radii h (all rows)."""
+    P = params(scene["params"])
+    x = np.ascontiguousarray(scene["x"], np.float32)
+    m = np.ascontiguousarray(np.abs(scene["mass"]), np.float32)
+    h = np.ascontiguousarray(h, np.float32)
+    N = x.shape[0]
+    out = [np.zeros(N) for _ in range(3)]
+    lib().orc_support(C.byref(P), N, _ptr(x, C.c_float), _ptr(m, C.c_float), _ptr(h, C.c_float),
+                      *[_ptr(o, C.c_double) for o in out])
+    return dict(search_radius=out[0], rho_super=out[1], rho_gather=out[2])
+
+
+def pairs_var(scene: dict, h: np.ndarray) -> np.ndarray:
+    """Ordered pairs with |x_ij| < max(h_i, h_j) (brute force), sorted by (i, j)."""
+    P = params(scene["params"])
+    x = np.ascontiguousarray(scene["x"], np.float32)
+    h = np.ascontiguousarray(h, np.float32)
+    N = x.shape[0]
+    n = lib().orc_pairs_var(C.byref(P), N, _ptr(x, C.c_float), _ptr(h, C.c_float), 0, None, None)
+    pi = np.zeros(n, np.int32)
+    pj = np.zeros(n, np.int32)
+    lib().orc_pairs_var(C.byref(P), N, _ptr(x, C.c_float), _ptr(h, C.c_float), n, _ptr(pi, C.c_int32),
+                        _ptr(pj, C.c_int32))
+    return np.stack([pi, pj], 1)
 
 
 def rollout(scene: dict, n_steps: int, x=None, v=None, rho=None):

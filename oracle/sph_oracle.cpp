@@ -1415,6 +1415,73 @@ int orc_shift_objective(const OrcParams* P, int nf, int nw, const double* x, con
   return 0;
 }
 
+// ---------------------------------------------------------------- variable support radius
+// Per-particle support radii h_i (the paper's "ensuring symmetric interactions" for varying
+// resolutions): a pair interacts when |x_ij| < max(h_i, h_j); the search radius of particle i is
+// s_i = max(h_i, max{h_k : |x_ik| < h_k}); the super-symmetric density averages the kernels of both
+// ends, the gather density uses h_i alone (self terms included).  Brute force over all pairs, FP64
+// on the float32 inputs.
+double kernel_W_h(const OrcParams& P, double r, double h) {
+  if (r >= h) return 0.0;
+  double w, w1, w2;
+  kernel_poly<double>(P.kernel, r / h, w, w1, w2);
+  return kernel_Cd(P.dim, P.kernel) / std::pow(h, P.dim) * w;
+}
+
+double sep2(const OrcParams& P, const double* xi, const double* xj) {
+  double d2 = 0.0;
+  for (int k = 0; k < P.dim; ++k) {
+    double dx = min_image(P, k, xi[k] - xj[k]);
+    d2 = d2 + dx * dx;
+  }
+  return d2;
+}
+
+int orc_support(const OrcParams* P, int N, const float* x, const float* m, const float* h, double* s_out,
+                double* rho_super, double* rho_gather) {
+  const int d = P->dim;
+  std::vector<double> xd((size_t)N * d), hd(N);
+  for (size_t k = 0; k < xd.size(); ++k) xd[k] = (double)x[k];
+  for (int i = 0; i < N; ++i) hd[i] = h[i] > 0.f ? (double)h[i] : P->H;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int i = 0; i < N; ++i) {
+    double s = hd[i], rs = m[i] * kernel_W_h(*P, 0.0, hd[i]), rg = rs;
+    for (int j = 0; j < N; ++j) {
+      if (j == i) continue;
+      const double d2 = sep2(*P, &xd[(size_t)i * d], &xd[(size_t)j * d]);
+      const bool inj = d2 < hd[j] * hd[j], ini = d2 < hd[i] * hd[i];
+      if (inj) s = std::max(s, hd[j]);
+      const double r = std::sqrt(d2);
+      if (ini || inj) rs += m[j] * 0.5 * (kernel_W_h(*P, r, hd[i]) + kernel_W_h(*P, r, hd[j]));
+      if (ini) rg += m[j] * kernel_W_h(*P, r, hd[i]);
+    }
+    s_out[i] = s;
+    rho_super[i] = rs;
+    rho_gather[i] = rg;
+  }
+  return 0;
+}
+
+// Ordered pairs (i, j), i != j, |x_ij| < max(h_i, h_j), sorted by (i, j).
+int64_t orc_pairs_var(const OrcParams* P, int N, const float* x, const float* h, int64_t cap, int32_t* pi,
+                      int32_t* pj) {
+  const int d = P->dim;
+  std::vector<double> xd((size_t)N * d), hd(N);
+  for (size_t k = 0; k < xd.size(); ++k) xd[k] = (double)x[k];
+  for (int i = 0; i < N; ++i) hd[i] = h[i] > 0.f ? (double)h[i] : P->H;
+  int64_t n = 0;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      if (i == j) continue;
+      const double hm = std::max(hd[i], hd[j]);
+      if (sep2(*P, &xd[(size_t)i * d], &xd[(size_t)j * d]) < hm * hm) {
+        if (n < cap) { pi[n] = i; pj[n] = j; }
+        ++n;
+      }
+    }
+  return n;
+}
+
 // n_steps of the FP64 scheme from a float32 initial state; FP64 final state out.
 int orc_rollout(const OrcParams* P, int nf, int nw, const float* x, const float* v, const float* rho, const float* m,
                 int n_steps, double* x_out, double* v_out, double* rho_out) {

@@ -137,6 +137,8 @@ def lib() -> C.CDLL:
     L.sph_rates.argtypes = [vp, vp, vp, vp, C.c_int]
     L.sph_density_gradient.argtypes = [vp, vp, C.c_int]
     L.sph_set_ghosts.argtypes = [vp, vp, C.c_int]
+    L.sph_set_support.argtypes = [vp, vp, C.c_int]
+    L.sph_support_query.argtypes = [vp, vp, vp, vp, C.c_int]
     L.sph_shift_gradient.argtypes = [vp, P(ShiftObjective), vp, vp, C.c_int]
     L.sph_shift_descend.argtypes = [vp, P(ShiftObjective), C.c_int, C.c_float, vp]
     L.sph_rollout.argtypes = [vp, C.c_int, C.c_int]
@@ -330,6 +332,19 @@ class Scene:
         o = ShiftObjective.from_dict(objective)
         _check(lib().sph_shift_descend(self._h, C.byref(o), int(n_iters), float(step), hist.ctypes.data))
         return hist
+
+    def set_support(self, H):
+        """Per-particle support radii (n rows, original order), 0 < H_i <= the scene's H."""
+        h = np.ascontiguousarray(np.asarray(H, np.float32).reshape(-1))
+        if h.size != self.n:
+            raise ValueError("one support radius per particle row")
+        _check(lib().sph_set_support(self._h, h.ctypes.data, 0))
+
+    def support_query(self):
+        """Search radius, super-symmetric and gather densities of every particle row."""
+        out = [np.empty(self.n, np.float32) for _ in range(3)]
+        _check(lib().sph_support_query(self._h, *[o.ctypes.data for o in out], 0))
+        return dict(search_radius=out[0], rho_super=out[1], rho_gather=out[2])
 
     def set_ghosts(self, ghost):
         """mDBC ghost nodes of the wall particles (n_wall x dim, walls in input order; a batch's

@@ -9,8 +9,9 @@
 //   cold records, read once per particle and step (the integrated state in double-single form,
 //   value = hi + lo with |lo| <= ulp(hi)/2, so rounding of the per-step increment does not
 //   accumulate over long rollouts):
-//     2D  X = (x_hi, y_hi, x_lo, y_lo)   O = (o_x, o_y, rho_lo, -)
-//     3D  X = (x_hi, y_hi, z_hi, rho_lo) XL = (x_lo, y_lo, z_lo, -)  O = (o_x, o_y, o_z, -)
+//     2D  X = (x_hi, y_hi, x_lo, y_lo)   O = (o_x, o_y, rho_lo, H_i)
+//     3D  X = (x_hi, y_hi, z_hi, rho_lo) XL = (x_lo, y_lo, z_lo, -)  O = (o_x, o_y, o_z, H_i)
+//     (H_i: per-particle support radius of the variable-support queries, 0 = the scene's H)
 //   meta = (original index | wall bit, scene index)
 // x_h = x - o is the position folded into the primary box at the last rebuild (o = L k for an
 // integer k per periodic axis), so a candidate range that crosses a periodic edge needs one
@@ -102,6 +103,7 @@ struct Arrays {
 struct Cold {
   float hi[3], lo[3], off[3];
   float rlo;
+  float aux;  // per-particle support radius of the variable-support queries (0: the scene's H)
 };
 
 template <int D>
@@ -109,6 +111,7 @@ __device__ __forceinline__ Cold load_cold(const Arrays& a, int i) {
   Cold c;
   float4 X = a.X[i], O = a.O[i];
   c.off[0] = O.x; c.off[1] = O.y; c.off[2] = O.z;
+  c.aux = O.w;
   if (D == 2) {
     c.hi[0] = X.x; c.hi[1] = X.y; c.hi[2] = 0.f;
     c.lo[0] = X.z; c.lo[1] = X.w; c.lo[2] = 0.f;
@@ -127,11 +130,11 @@ template <int D>
 __device__ __forceinline__ void store_cold(const Arrays& a, int i, const Cold& c) {
   if (D == 2) {
     a.X[i] = make_float4(c.hi[0], c.hi[1], c.lo[0], c.lo[1]);
-    a.O[i] = make_float4(c.off[0], c.off[1], c.rlo, 0.f);
+    a.O[i] = make_float4(c.off[0], c.off[1], c.rlo, c.aux);
   } else {
     a.X[i] = make_float4(c.hi[0], c.hi[1], c.hi[2], c.rlo);
     a.XL[i] = make_float4(c.lo[0], c.lo[1], c.lo[2], 0.f);
-    a.O[i] = make_float4(c.off[0], c.off[1], c.off[2], 0.f);
+    a.O[i] = make_float4(c.off[0], c.off[1], c.off[2], c.aux);
   }
 }
 
@@ -189,6 +192,25 @@ __device__ bool exact_pair(const DevSeg& s, const Arrays& arr, int i, int j) {
     d2 = __dadd_rn(d2, __dmul_rn(dx, dx));
   }
   return d2 < s.H2_d;
+}
+
+// The same FP64 squared distance, returned (for per-pair radii).
+template <int D>
+__device__ double exact_d2(const DevSeg& s, const Arrays& arr, int i, int j) {
+  Cold a = load_cold<D>(arr, i), b = load_cold<D>(arr, j);
+  double d2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    double xi = __dadd_rn((double)a.hi[k], (double)a.lo[k]);
+    double xj = __dadd_rn((double)b.hi[k], (double)b.lo[k]);
+    double dx = __dsub_rn(xi, xj);
+    if ((s.periodic_mask >> k) & 1) {
+      double n = rint(__ddiv_rn(dx, s.L_d[k]));
+      dx = __dsub_rn(dx, __dmul_rn(s.L_d[k], n));
+    }
+    d2 = __dadd_rn(d2, __dmul_rn(dx, dx));
+  }
+  return d2;
 }
 
 // ---------------------------------------------------------------- particle records

@@ -127,6 +127,7 @@ __global__ void k_upload(const DevSeg* __restrict__ segs, int seg, int n, int nf
     c.off[q] = 0.f;
   }
   c.rlo = 0.f;
+  c.aux = 0.f;
   for (int q = 0; q < D; ++q) {
     r.x[q] = c.hi[q];
     r.v[q] = wall ? 0.f : v[(size_t)k * D + q];

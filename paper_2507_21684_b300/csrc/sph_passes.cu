@@ -9,7 +9,8 @@
 //                   kick-drift epilogue (Sec. 2.3, Sec. 3.4); also the rate-only evaluation
 //   shift           explicit particle shifting at the end of a step (free-surface aware)
 //   opt P1..P4      shifting by optimisation: objective, its gradient, a descent step
-//   pairs           exact pair export (FP64 predicate in a guard band)
+//   pairs           exact pair export (FP64 predicate in a guard band; per-particle radii too)
+//   variable support   search radius and super-symmetric / gather densities with radii H_i
 //   adjoint sweep   vector-Jacobian product of one step, gathered per particle (Sec. 2.2)
 #include <algorithm>
 #include <map>
@@ -1177,7 +1178,9 @@ struct ShiftPass {
 };
 
 // ================================================================== pair export
-template <int D>
+// VAR: per-particle support radii (the records' H_i): a pair needs |x_ij| < max(H_i, H_j), decided
+// in FP64 like the scene's cut-off.
+template <int D, bool VAR = false>
 struct PairPass {
   struct Body {
     uint32_t id_i;
@@ -1185,7 +1188,16 @@ struct PairPass {
     int32_t *pi, *pj;
     unsigned long long* count;
     long long cap;
+    const DevSeg* s;
+    const Arrays* a;
+    int i;
+    float Hi;
     __device__ __forceinline__ void pair_at(const float*, const PD<D>&, float4, float, int j) {
+      if (VAR) {
+        const float hj = __ldg(&a->O[j].w);
+        const double Hm = (double)fmaxf(Hi, hj > 0.f ? hj : s->H);
+        if (!(exact_d2<D>(*s, *a, i, j) < Hm * Hm)) return;
+      }
       const unsigned long long k = atomicAdd(count, 1ull);
       if ((long long)k < cap) {
         pi[k] = (int32_t)id_i;
@@ -1205,9 +1217,14 @@ struct PairPass {
   __device__ __forceinline__ void last_cta() {}
   __device__ __forceinline__ const float4* tex0() const { return nullptr; }
   __device__ __forceinline__ const float4* tex1() const { return nullptr; }
-  __device__ __forceinline__ bool init(Body& b, const DevSeg&, int, const TgtView& tv) {
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i, const TgtView& tv) {
     b.id_i = tv.a.meta[tv.k].x & ~kWallBit;
     b.meta = a.meta;
+    b.s = &s;
+    b.a = &a;
+    b.i = i;
+    const float h = tv.a.O[tv.k].w;
+    b.Hi = h > 0.f ? h : s.H;
     b.pi = pi;
     b.pj = pj;
     b.count = count;
@@ -1696,6 +1713,121 @@ __global__ void k_opt_volumes(int N, const float4* __restrict__ S1, float* __res
   if (i < N) V[i] = S1[i].x;
 }
 
+// ================================================================== variable support radius
+// Per-particle support radii H_i <= H (the scene's H sizes the cells; H_i = 0 stands for H).  For
+// every particle (the paper's symmetric search radius and super-symmetric neighbourhood):
+//   s_i    = max(H_i, max{H_k : |x_ik| < H_k})                                the search radius
+//   rhoS_i = sum_j m_j (W(|x_ij|, H_i) + W(|x_ij|, H_j)) / 2 over |x_ij| < max(H_i, H_j)
+//   rhoG_i = sum_j m_j W(|x_ij|, H_i) over |x_ij| < H_i                       (gather)
+// self terms included, W(r, h) = C_d / h^d w(r / h).  The comparisons |x_ij|^2 < H_k^2 are taken
+// in FP64 from the double-single positions when the FP32 distance lies within a guard band of
+// H_k^2, so s_i (a maximum of given radii) is exact; the sum gathers what the paper computes with
+// an atomic maximum in scatter form.
+template <int D, int KERN>
+struct VarSupportPass {
+  struct Body {
+    const DevSeg* s;
+    const Arrays* a;
+    int i;
+    float Hi, band, smax, rs, rg;  // band: FP32 error bound of a squared distance (absolute)
+    __device__ __forceinline__ bool inside(float r2, float h, int j) const {
+      const float h2 = h * h;
+      if (fabsf(r2 - h2) > band) return r2 < h2;
+      return exact_d2<D>(*s, *a, i, j) < (double)h * (double)h;
+    }
+    __device__ __forceinline__ float Wh(float r2, float h) const {
+      const float sc = s->H / h;
+      float f = sc * sc;
+      if (D == 3) f *= sc;
+      const float q = sqrtf(r2) / h;
+      return q < 1.f ? s->Kw * f * kern_w<KERN>(q) : 0.f;
+    }
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4 e, float, int j) {
+      float r[D];
+      const float r2 = diff<D>(xs, pj.x, r);
+      const float Hj = e.x;
+      const bool inj = inside(r2, Hj, j), ini = inside(r2, Hi, j);
+      if (inj) smax = fmaxf(smax, Hj);
+      if (!(ini || inj)) return;
+      const float wi = ini ? Wh(r2, Hi) : 0.f, wj = inj ? Wh(r2, Hj) : 0.f;
+      const float m = fabsf(pj.m);
+      rs = fmaf(m, 0.5f * (wi + wj), rs);
+      rg = fmaf(m, wi, rg);
+    }
+    template <int L>
+    __device__ __forceinline__ void reduce() {
+#pragma unroll
+      for (int o = L / 2; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(kFull, smax, o));
+      rs = group_sum<L>(rs);
+      rg = group_sum<L>(rg);
+    }
+  };
+  Arrays a;
+  float4* out;  // (s, rhoS, rhoG, 0)
+  float band;
+  __device__ static __forceinline__ bool wants(uint32_t) { return true; }
+  __device__ __forceinline__ void skip(int, const TgtView&) {}
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ void last_cta() {}
+  __device__ __forceinline__ const float4* tex0() const { return nullptr; }
+  __device__ __forceinline__ const float4* tex1() const { return nullptr; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int i, const TgtView& tv) {
+    b.s = &s;
+    b.a = &a;
+    b.i = i;
+    const float h = tv.a.O[tv.k].w;
+    b.Hi = h > 0.f ? h : s.H;
+    b.band = band;
+    b.smax = b.Hi;
+    b.rs = b.rg = 0.f;
+    return true;
+  }
+  __device__ __forceinline__ void finish(Body& b, const DevSeg&, int i, const TgtView& tv) {
+    const float m = fabsf(load_pd_plain<D>(tv.a, tv.k).m);
+    const float w0 = b.Wh(0.f, b.Hi);
+    out[i] = make_float4(b.smax, fmaf(m, w0, b.rs), fmaf(m, w0, b.rg), 0.f);
+  }
+};
+
+template <int D, int KERN>
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_varsupport(TravArgs t, const Tile* tiles, const int* ntiles, const float4* Hs,
+                                                    float4* out, float band) {
+  VarSupportPass<D, KERN> pass;
+  pass.a = t.a;
+  pass.out = out;
+  pass.band = band;
+  run_tiles<D, 1, 2>(t, tiles, ntiles, Hs, nullptr, pass);
+}
+// the support radius of every particle as a staged payload (H_i, 0, 0, 0)
+__global__ void k_support_payload(int N, const float4* __restrict__ O, const DevSeg* __restrict__ segs,
+                                  const uint2* __restrict__ meta, float4* __restrict__ Hs) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const float h = O[k].w;
+  Hs[k] = make_float4(h > 0.f ? h : segs[meta[k].y].H, 0.f, 0.f, 0.f);
+}
+// per-particle support radii by original row into the records
+__global__ void k_set_support(int N, const uint2* __restrict__ meta, const int* __restrict__ orig_base,
+                              const float* __restrict__ H, float4* __restrict__ O) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const uint2 m = meta[k];
+  O[k].w = H[orig_base[m.y] + (int)(m.x & ~kWallBit)];
+}
+// a float4 array (x, y, z) in sorted order into three arrays by original row
+__global__ void k_unpermute3(int N, const uint2* __restrict__ meta, const int* __restrict__ orig_base,
+                             const float4* __restrict__ src, float* __restrict__ a, float* __restrict__ b,
+                             float* __restrict__ c) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const uint2 m = meta[k];
+  const int o = orig_base[m.y] + (int)(m.x & ~kWallBit);
+  const float4 v = src[k];
+  if (a) a[o] = v.x;
+  if (b) b[o] = v.y;
+  if (c) c[o] = v.z;
+}
+
 // ================================================================== kernels
 // The wall pass visits only the tiles that hold a wall particle (listed at each rebuild).
 template <int D, int KERN>
@@ -1789,10 +1921,10 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, (D == 3 ? 768 : 1024) / T
   pass.disp = disp;
   run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
-template <int D>
+template <int D, bool VAR>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_pairs_t(TravArgs t, const Tile* tiles, const int* ntiles, int32_t* pi,
                                                  int32_t* pj, unsigned long long* count, long long cap) {
-  PairPass<D> pass;
+  PairPass<D, VAR> pass;
   pass.a = t.a;
   pass.pi = pi;
   pass.pj = pj;
@@ -1923,8 +2055,11 @@ void launch_shift_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int
 }
 template <int D>
 void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
-                    unsigned long long* count, long long cap, cudaStream_t st) {
-  k_pairs_t<D><<<pass_grid((const void*)k_pairs_t<D>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, pi, pj, count, cap);
+                    unsigned long long* count, long long cap, bool var, cudaStream_t st) {
+  if (var)
+    k_pairs_t<D, true><<<pass_grid((const void*)k_pairs_t<D, true>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, pi, pj, count, cap);
+  else
+    k_pairs_t<D, false><<<pass_grid((const void*)k_pairs_t<D, false>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, pi, pj, count, cap);
 }
 template <int D, int KERN>
 void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* S,
@@ -1953,6 +2088,20 @@ void launch_opt_backward(const TravArgs& t, const Tile* tiles, const int* ntiles
     k_opt_adj2<D, KERN, true><<<pass_grid((const void*)k_opt_adj2<D, KERN, true>, tiles_upper), TH, pass_smem<D>(1), st>>>(t, tiles, ntiles, XB, G, *out, step);
   else
     k_opt_adj2<D, KERN, false><<<pass_grid((const void*)k_opt_adj2<D, KERN, false>, tiles_upper), TH, pass_smem<D>(1), st>>>(t, tiles, ntiles, XB, G, Arrays{}, 0.f);
+}
+template <int D, int KERN>
+void launch_varsupport(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, float4* Hs,
+                       float4* out, float band, cudaStream_t st) {
+  if (t.N > 0) k_support_payload<<<(t.N + 255) / 256, 256, 0, st>>>(t.N, t.a.O, t.segs, t.a.meta, Hs);
+  k_varsupport<D, KERN><<<pass_grid((const void*)k_varsupport<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(1), st>>>(
+      t, tiles, ntiles, Hs, out, band);
+}
+void launch_set_support(int N, const uint2* meta, const int* orig_base, const float* H, float4* O, cudaStream_t st) {
+  if (N > 0) k_set_support<<<(N + 255) / 256, 256, 0, st>>>(N, meta, orig_base, H, O);
+}
+void launch_unpermute3(int N, const uint2* meta, const int* orig_base, const float4* src, float* a, float* b, float* c,
+                       cudaStream_t st) {
+  if (N > 0) k_unpermute3<<<(N + 255) / 256, 256, 0, st>>>(N, meta, orig_base, src, a, b, c);
 }
 void launch_sum_segments(const float* part, const DevSeg* segs, int S, double* acc, cudaStream_t st) {
   k_sum_segments<<<S, 1024, 0, st>>>(part, segs, acc);
@@ -1996,7 +2145,10 @@ cudaError_t configure_passes() {
   SPH_ATTR(3, (k_shift_t<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_shift_t<3, 1>), pass_smem<3>(0))
   SPH_ATTR(2, (k_grad_t<2, 0>), pass_smem<2>(0)) SPH_ATTR(2, (k_grad_t<2, 1>), pass_smem<2>(0))
   SPH_ATTR(3, (k_grad_t<3, 0>), pass_smem<3>(0)) SPH_ATTR(3, (k_grad_t<3, 1>), pass_smem<3>(0))
-  SPH_ATTR(2, (k_pairs_t<2>), pass_smem<2>(0)) SPH_ATTR(3, (k_pairs_t<3>), pass_smem<3>(0))
+  SPH_ATTR(2, (k_pairs_t<2, false>), pass_smem<2>(0)) SPH_ATTR(3, (k_pairs_t<3, false>), pass_smem<3>(0))
+  SPH_ATTR(2, (k_pairs_t<2, true>), pass_smem<2>(0)) SPH_ATTR(3, (k_pairs_t<3, true>), pass_smem<3>(0))
+  SPH_ATTR(2, (k_varsupport<2, 0>), pass_smem<2>(1)) SPH_ATTR(2, (k_varsupport<2, 1>), pass_smem<2>(1))
+  SPH_ATTR(3, (k_varsupport<3, 0>), pass_smem<3>(1)) SPH_ATTR(3, (k_varsupport<3, 1>), pass_smem<3>(1))
   SPH_ATTR(2, (k_adj_t<2, 0>), pass_smem<2>(1)) SPH_ATTR(2, (k_adj_t<2, 1>), pass_smem<2>(1))
   SPH_ATTR(3, (k_adj_t<3, 0>), pass_smem<3>(2)) SPH_ATTR(3, (k_adj_t<3, 1>), pass_smem<3>(2))
 #undef SPH_ATTR
@@ -2006,13 +2158,15 @@ cudaError_t configure_passes() {
 #define SPH_INST_PD(D)                                                                                       \
   template void launch_tiles<D>(const DevSeg*, int, const int*, int, const int*, Tile*, int*, cudaStream_t);    \
   template void launch_pairs_t<D>(const TravArgs&, const Tile*, const int*, int, int32_t*, int32_t*,          \
-                                  unsigned long long*, long long, cudaStream_t);
+                                  unsigned long long*, long long, bool, cudaStream_t);
 SPH_INST_PD(2)
 SPH_INST_PD(3)
 #define SPH_INST_PDK(D, K)                                                                                   \
   template void launch_walls_t<D, K>(const TravArgs&, const Tile*, const int*, const int*, int, cudaStream_t); \
   template void launch_density_t<D, K>(const TravArgs&, const Tile*, const int*, int, cudaStream_t);        \
   template void launch_grad_t<D, K>(const TravArgs&, const Tile*, const int*, int, float4*, cudaStream_t);   \
+  template void launch_varsupport<D, K>(const TravArgs&, const Tile*, const int*, int, float4*, float4*, float, \
+                                        cudaStream_t);                                                       \
   template void launch_opt_forward<D, K>(const TravArgs&, const Tile*, const int*, int, const ShiftObjective&, \
                                          float4*, float4*, float*, float*, cudaStream_t);                     \
   template void launch_opt_backward<D, K>(const TravArgs&, const Tile*, const int*, int, const ShiftObjective&, \

@@ -45,7 +45,13 @@ void launch_opt_backward(const TravArgs& t, const Tile* tiles, const int* ntiles
                          float4* G, const Arrays* out, float step, cudaStream_t st);
 template <int D>
 void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,
-                    unsigned long long* count, long long cap, cudaStream_t st);
+                    unsigned long long* count, long long cap, bool var, cudaStream_t st);
+template <int D, int KERN>
+void launch_varsupport(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, float4* Hs,
+                       float4* out, float band, cudaStream_t st);
+void launch_set_support(int N, const uint2* meta, const int* orig_base, const float* H, float4* O, cudaStream_t st);
+void launch_unpermute3(int N, const uint2* meta, const int* orig_base, const float4* src, float* a, float* b, float* c,
+                       cudaStream_t st);
 template <int D, int KERN>
 void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* S,
                   const float* Pp, const float4* XBin, const float4* VBin, float4* XBout, float4* VBout,

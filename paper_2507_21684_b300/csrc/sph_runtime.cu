@@ -1397,28 +1397,83 @@ void Scene::debug_cells(int64_t* start, int32_t* ids) {
     for (int k = 0; k < N; ++k) ids[k] = (int32_t)(meta[k].x & ~kWallBit) + orig_base[meta[k].y];
 }
 
+// Widen the FP32 guard band of the exact pair predicate to the actual coordinate range (single
+// scene); returns the band as an absolute bound on the FP32 error of a squared distance below H^2.
+double Scene::pair_band() {
+  std::vector<float4> X(N);
+  CK(cudaMemcpyAsync(X.data(), buf[cur].X, sizeof(float4) * N, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double mx = 1.0;
+  for (int k = 0; k < N; ++k) {
+    float c[3] = {X[k].x, X[k].y, D == 3 ? X[k].z : 0.f};
+    for (int q = 0; q < D; ++q) mx = std::max(mx, (double)std::fabs(c[q]));
+  }
+  for (int q = 0; q < D; ++q) mx = std::max(mx, std::fabs(segs[0].lo_d[q]) + segs[0].L_d[q]);
+  DevSeg g = segs[0];
+  double H = g.H;
+  double band = std::max(1e-5, 4.0 * 8.0 * std::ldexp(mx, -23) / H);
+  g.band_lo = (float)(H * H * (1.0 - band));
+  g.band_hi = (float)(H * H * (1.0 + band));
+  CK(cudaMemcpyAsync(dseg, &g, sizeof(DevSeg), cudaMemcpyHostToDevice, st));
+  return band * H * H;
+}
+
+// Per-particle support radii (variable support queries): 0 < H_i <= the scene's H, by row.
+void Scene::set_support(const float* H, int is_dev) {
+  std::vector<float> h((size_t)N);
+  CK(cudaMemcpyAsync(h.data(), H, sizeof(float) * N, is_dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int s = 0; s < S; ++s)
+    for (int k = 0; k < segs[s].p1 - segs[s].p0; ++k) {
+      const float v = h[(size_t)orig_base[s] + k];
+      if (!(v > 0.f && v <= segs[s].H)) einval("sph_set_support: every H_i must satisfy 0 < H_i <= the scene's H");
+    }
+  float* d = (float*)mem_tmp(sizeof(float) * ((size_t)N + 64));
+  CK(cudaMemcpyAsync(d, h.data(), sizeof(float) * N, cudaMemcpyHostToDevice, st));
+  launch_set_support(N, buf[cur].meta, d_orig_base, d, buf[cur].O, st);
+  CKL();
+  CK(cudaStreamSynchronize(st));
+  var_support = true;
+}
+
+void Scene::support_query(float* sr, float* rs, float* rg, int is_dev) {
+  if (S > 1) einval("sph_support_query supports single scenes");
+  if (skin > 0.f) cells_valid = false;
+  ensure_cells();
+  const double band = pair_band();
+  float4* Hs = (float4*)mem_tmp(sizeof(float4) * (2 * (size_t)N + 16) + sizeof(float) * (3 * (size_t)N + 64));
+  float4* out = Hs + N;
+  float* h = (float*)(out + N + 16);
+  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  t.pair_count = nullptr;
+  if (D == 2) {
+    if (kern == 0) launch_varsupport<2, 0>(t, tiles, d_ntiles, tiles_upper, Hs, out, (float)band, st);
+    else launch_varsupport<2, 1>(t, tiles, d_ntiles, tiles_upper, Hs, out, (float)band, st);
+  } else {
+    if (kern == 0) launch_varsupport<3, 0>(t, tiles, d_ntiles, tiles_upper, Hs, out, (float)band, st);
+    else launch_varsupport<3, 1>(t, tiles, d_ntiles, tiles_upper, Hs, out, (float)band, st);
+  }
+  CKL();
+  float* a = is_dev ? sr : (sr ? h : nullptr);
+  float* b = is_dev ? rs : (rs ? h + N : nullptr);
+  float* c = is_dev ? rg : (rg ? h + 2 * (size_t)N : nullptr);
+  launch_unpermute3(N, buf[cur].meta, d_orig_base, out, a, b, c, st);
+  CKL();
+  if (!is_dev) {
+    if (sr) CK(cudaMemcpyAsync(sr, h, sizeof(float) * N, cudaMemcpyDeviceToHost, st));
+    if (rs) CK(cudaMemcpyAsync(rs, h + N, sizeof(float) * N, cudaMemcpyDeviceToHost, st));
+    if (rg) CK(cudaMemcpyAsync(rg, h + 2 * (size_t)N, sizeof(float) * N, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  // the debug band stays widened; restore the scene's own
+  CK(cudaMemcpyAsync(dseg, segs.data(), sizeof(DevSeg) * S, cudaMemcpyHostToDevice, st));
+}
+
 void Scene::debug_pairs(int64_t* n_pairs, int32_t* pi, int32_t* pj, int64_t cap) {
   if (S > 1) einval("sph_debug_pairs supports single scenes");
   if (skin > 0.f) cells_valid = false;
   ensure_cells();
-  // widen the FP32 guard band of the exact predicate to the actual coordinate range
-  {
-    std::vector<float4> X(N);
-    CK(cudaMemcpyAsync(X.data(), buf[cur].X, sizeof(float4) * N, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    double mx = 1.0;
-    for (int k = 0; k < N; ++k) {
-      float c[3] = {X[k].x, X[k].y, D == 3 ? X[k].z : 0.f};
-      for (int q = 0; q < D; ++q) mx = std::max(mx, (double)std::fabs(c[q]));
-    }
-    for (int q = 0; q < D; ++q) mx = std::max(mx, std::fabs(segs[0].lo_d[q]) + segs[0].L_d[q]);
-    DevSeg g = segs[0];
-    double H = g.H;
-    double band = std::max(1e-5, 4.0 * 8.0 * std::ldexp(mx, -23) / H);
-    g.band_lo = (float)(H * H * (1.0 - band));
-    g.band_hi = (float)(H * H * (1.0 + band));
-    CK(cudaMemcpyAsync(dseg, &g, sizeof(DevSeg), cudaMemcpyHostToDevice, st));
-  }
+  pair_band();
   int64_t c = std::max<int64_t>(cap, 0);
   int32_t* dpi = (int32_t*)mem_tmp(sizeof(int32_t) * (2 * (size_t)c + 64));
   int32_t* dpj = dpi + c;
@@ -1427,9 +1482,9 @@ void Scene::debug_pairs(int64_t* n_pairs, int32_t* pi, int32_t* pj, int64_t cap)
   TravArgs t = trav(buf[cur], keys_sorted, cell_off);
   t.pair_count = nullptr;
   if (D == 2)
-    launch_pairs_t<2>(t, tiles, d_ntiles, tiles_upper, dpi, dpj, cnt, (long long)c, st);
+    launch_pairs_t<2>(t, tiles, d_ntiles, tiles_upper, dpi, dpj, cnt, (long long)c, var_support, st);
   else
-    launch_pairs_t<3>(t, tiles, d_ntiles, tiles_upper, dpi, dpj, cnt, (long long)c, st);
+    launch_pairs_t<3>(t, tiles, d_ntiles, tiles_upper, dpi, dpj, cnt, (long long)c, var_support, st);
   CKL();
   unsigned long long h = 0;
   CK(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -1638,6 +1693,30 @@ int sph_shift_descend(sph_scene* sc, const sph_shift_objective* obj, int n_iters
   const sph::ShiftObjective o = sph::check_objective(*obj);
   sc->s.enter();
   sc->s.shift_descend(o, n_iters, step, loss_hist);
+  sc->s.leave();
+  API_END
+}
+
+int sph_set_support(sph_scene* sc, const float* H, int ptr_is_device) {
+  if (!sc || !H) {
+    sph::set_err("sph_set_support: NULL scene or radii");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  sc->s.enter();
+  sc->s.set_support(H, ptr_is_device);
+  sc->s.leave();
+  API_END
+}
+
+int sph_support_query(sph_scene* sc, float* search_radius, float* rho_super, float* rho_gather, int ptr_is_device) {
+  if (!sc) {
+    sph::set_err("sph_support_query: NULL scene");
+    return SPH_EINVAL;
+  }
+  API_BEGIN
+  sc->s.enter();
+  sc->s.support_query(search_radius, rho_super, rho_gather, ptr_is_device);
   sc->s.leave();
   API_END
 }

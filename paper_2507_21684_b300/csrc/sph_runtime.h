@@ -199,6 +199,10 @@ struct Scene {
                            bool fused_walls = false);
   void walls_pass(const TravArgs& t, const Tile* tl);
   void set_ghosts(const float* g, int is_dev);
+  bool var_support = false;         // per-particle support radii set (the records' H_i)
+  double pair_band();
+  void set_support(const float* H, int is_dev);
+  void support_query(float* sr, float* rs, float* rg, int is_dev);
   void need_ghosts() const;
   void grad_pass(const TravArgs& t, const Tile* tl, const int* ntl);
   void sweep(const TravArgs& t, const Arrays& out, const Tile* tl = nullptr, const int* ntl = nullptr,
