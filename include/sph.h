@@ -264,6 +264,12 @@ SPH_API int sph_debug_cells(sph_scene* scene, int64_t* cell_start, int32_t* sort
  * unordered).  *n_pairs receives the total; at most cap pairs are written. */
 SPH_API int sph_debug_pairs(sph_scene* scene, int64_t* n_pairs, int32_t* pi, int32_t* pj, int64_t cap);
 
+/* Test of the device-side bounded waits on the current device: a sweep tile's wait on a gate that
+ * no wall task opens, and a cooperative grid barrier that one CTA never reaches.  Each gives up
+ * after its poll limit (a fraction of a second) and reports status bit 1 (2) in *gate_status and
+ * *barrier_status; the context stays usable.  No fault is involved. */
+SPH_API int sph_debug_bounded_waits(int* gate_status, int* barrier_status);
+
 /* Per-kernel device timing.  When enabled, the scene records CUDA events around its launches
  * on its stream; sph_timing returns the accumulated milliseconds and launch count of one
  * kernel class (0 = fused sweep, 1 = rebuild (keys+sort+ranges+permute), 2 = walls,

@@ -138,6 +138,7 @@ def lib() -> C.CDLL:
     L.sph_density_gradient.argtypes = [vp, vp, C.c_int]
     L.sph_set_ghosts.argtypes = [vp, vp, C.c_int]
     L.sph_set_support.argtypes = [vp, vp, C.c_int]
+    L.sph_debug_bounded_waits.argtypes = [P(C.c_int), P(C.c_int)]
     L.sph_support_query.argtypes = [vp, vp, vp, vp, C.c_int]
     L.sph_shift_gradient.argtypes = [vp, P(ShiftObjective), vp, vp, C.c_int]
     L.sph_shift_descend.argtypes = [vp, P(ShiftObjective), C.c_int, C.c_float, vp]

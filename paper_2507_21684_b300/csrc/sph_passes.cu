@@ -22,6 +22,26 @@ namespace sph {
 
 // Bounded wait of a sweep tile on the wall tasks of the fused kernel: ~0.1 s, then status bit 1.
 constexpr long long kGateSpins = 1LL << 22;
+// One thread waits until *gate >= n (then a fence orders its later reads), or gives up after
+// kGateSpins polls, sets status bit 1 and returns false.
+__device__ __noinline__ bool gate_wait(const unsigned* gate, unsigned n, int* status) {
+  long long it = 0;
+  while (*(volatile const unsigned*)gate < n) {
+    if (++it > kGateSpins) {
+      atomicOr(status, 2);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  __threadfence();
+  return true;
+}
+
+// Test hook of the bounded waits: a gate that no task opens.
+__global__ void k_debug_gate(const unsigned* gate, int* status) {
+  if (threadIdx.x == 0) gate_wait(gate, 1u, status);
+}
+void launch_debug_gate(const unsigned* gate, int* status, cudaStream_t st) { k_debug_gate<<<1, 32, 0, st>>>(gate, status); }
 // Relative cut-off of the pseudo-inverses (renormalisation, mDBC): eigen-directions with
 // |lambda| <= kPinvRtol max|lambda| (or singular values <= kPinvRtol max) are dropped.
 constexpr float kPinvRtol = 1e-3f;
@@ -299,17 +319,7 @@ __device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileS
   int seen = 1;
   int stg = stage_tile<D, E, COH>(sm, s, T, t.a, t.cell_off, extra0, extra1, want, gate ? &seen : nullptr);
   if (gate && !s_ready && (stg == 0 || (stg == 1 && seen))) {  // uniform over the CTA (barrier results)
-    if (threadIdx.x == 0) {
-      long long it = 0;
-      while (*(volatile const unsigned*)gate < gate_n) {
-        if (++it > kGateSpins) {
-          atomicOr(t.status, 2);
-          break;
-        }
-        __nanosleep(32);
-      }
-      __threadfence();
-    }
+    if (threadIdx.x == 0) gate_wait(gate, gate_n, t.status);
     __syncthreads();
     fill_target_cache<D, COH>(sm.tc, t.a, pass.tex0(), pass.tex1(), T.p0, T.p1 - T.p0);
     stg = stage_tile<D, E, COH>(sm, s, T, t.a, t.cell_off, extra0, extra1, want);

@@ -6,6 +6,7 @@
 namespace sph {
 
 cudaError_t configure_passes();
+void launch_debug_gate(const unsigned* gate, int* status, cudaStream_t st);
 template <int D>
 void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, const int* cell_off, Tile* tiles,
                   int* ntiles, cudaStream_t st);

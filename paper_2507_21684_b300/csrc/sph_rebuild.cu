@@ -40,6 +40,24 @@ cudaError_t launch_rebuild_coop(const RebuildArgs& r, int grid, cudaStream_t st)
   return cudaLaunchKernelEx(&cfg, k_rebuild_coop<D>, r);
 }
 
+// Test hook of the bounded waits: a grid barrier that one CTA never reaches.
+__global__ void k_debug_barrier(unsigned* bar, int* status) {
+  if (blockIdx.x == 0) return;
+  grid_barrier(bar, status);
+}
+cudaError_t launch_debug_barrier(unsigned* bar, int* status, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(32);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_debug_barrier, bar, status);
+}
+
 template int rebuild_coop_grid<2>();
 template int rebuild_coop_grid<3>();
 template cudaError_t launch_rebuild_coop<2>(const RebuildArgs&, int, cudaStream_t);

@@ -31,5 +31,7 @@ template <int D>
 int rebuild_coop_grid();
 template <int D>
 cudaError_t launch_rebuild_coop(const RebuildArgs& r, int grid, cudaStream_t st);
+// test hook: a two-CTA cooperative launch whose grid barrier one CTA never reaches
+cudaError_t launch_debug_barrier(unsigned* bar, int* status, cudaStream_t st);
 
 }  // namespace sph

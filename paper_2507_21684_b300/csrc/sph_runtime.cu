@@ -1697,6 +1697,31 @@ int sph_shift_descend(sph_scene* sc, const sph_shift_objective* obj, int n_iters
   API_END
 }
 
+int sph_debug_bounded_waits(int* gate_status, int* barrier_status) {
+  API_BEGIN
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaStream_t st = nullptr;
+  CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  void* buf = nullptr;
+  CK(cudaMalloc(&buf, 64));
+  CK(cudaMemsetAsync(buf, 0, 64, st));
+  unsigned* words = (unsigned*)buf;   // [0] gate, [1..2] barrier
+  int* status = (int*)buf + 8;        // [8] gate status, [9] barrier status
+  sph::launch_debug_gate(words, status, st);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = sph::launch_debug_barrier(words + 1, status + 1, st);
+  int h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, status, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  cudaStreamDestroy(st);
+  CK(e);
+  if (gate_status) *gate_status = h[0];
+  if (barrier_status) *barrier_status = h[1];
+  API_END
+}
+
 int sph_set_support(sph_scene* sc, const float* H, int ptr_is_device) {
   if (!sc || !H) {
     sph::set_err("sph_set_support: NULL scene or radii");

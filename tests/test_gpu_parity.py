@@ -464,3 +464,23 @@ def test_batched_adjoint_bitwise_equal_alone(sph):
             ax, av, ar, anu = sc.adjoint(sd, None, None)
         assert np.array_equal(ax, gx[f:f + n]) and np.array_equal(av, gv[f:f + n])
         assert anu == nu_b
+
+
+def test_bounded_device_waits_give_up_and_the_context_survives(sph):
+    """The fused kernel's gate wait and the cooperative rebuild's grid barrier are bounded: made to
+    wait for something that never happens (no fault), each gives up, reports status bit 1, and
+    the next scene runs normally."""
+    import ctypes as C
+    import time
+    g, b = C.c_int(0), C.c_int(0)
+    t0 = time.perf_counter()
+    rc = sph.lib().sph_debug_bounded_waits(C.byref(g), C.byref(b))
+    dt = time.perf_counter() - t0
+    assert rc == sph.SPH_OK
+    assert g.value & 2 and b.value & 2
+    assert dt < 30.0
+    s = si.taylor_green_2d(16, seed=0)
+    with make(sph, s) as sc:
+        sc.step(3)
+        x, _, _ = sc.get_state()
+    assert np.all(np.isfinite(x))
