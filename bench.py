@@ -359,6 +359,8 @@ def main():
     ap.add_argument("--boundary", type=int, default=0, choices=[0, 1],
                     help="--profile-run (dam break): 0 Shepard wall pressure, 1 mDBC")
     ap.add_argument("--stream-scenes", type=int, default=512, help="requests of the served mixed-size stream")
+    ap.add_argument("--no-tile-tune", action="store_true", help="use the default tile shape (no variant timing)")
+    ap.add_argument("--variant", default="default", help="--profile-run: tile-shape variant of the library")
     ap.add_argument("--stream-rates", type=float, nargs="*", default=[20.0, 80.0, 320.0])
     args = ap.parse_args()
     ws, rank = _dist()
@@ -367,8 +369,9 @@ def main():
     if args.profile_run:
         import torch
         from paper_2507_21684_b300 import build as sbuild
-        sbuild.build()
+        sbuild.build(variant=args.variant)
         import paper_2507_21684_b300 as sph
+        sph.select_variant(args.variant)
         sph.use_torch_allocator()
         from paper_2507_21684_b300 import tune
         sp = (si.dam_break(res=128, diffusion=args.diffusion, boundary=args.boundary) if args.workload == "dambreak"
@@ -409,16 +412,25 @@ def main():
     from paper_2507_21684_b300 import build as sbuild
     sbuild.build()
     import paper_2507_21684_b300 as sph
+    from paper_2507_21684_b300 import tune
+
+    # tile shape (targets per tile, threads per target) chosen by the library's autotuner: each
+    # variant of the library times the headline scene in a child process; rank 0 decides
+    tiles = None
+    if rank == 0 and not args.no_tile_tune:
+        tiles = tune.tune_tiles(tune.with_skin(spec, 0.02), steps=100, warmup=50,
+                                device=int(os.environ.get("LOCAL_RANK", "0")))
+    variant = replica_choice(tiles["variant"] if tiles else "default")
+    sph.select_variant(variant)
     sph.use_torch_allocator()
     stream = torch.cuda.Stream()
 
     # neighbour-search setting of the headline scene chosen by the library's autotuner (a Verlet
     # skin; every candidate finds the same neighbours each step)
-    from paper_2507_21684_b300 import tune
     tuned = tune.tune_skin(spec, skins=(0.0, 0.02, 0.05, 0.1, 0.2), steps=100, warmup=100)
     best_skin = replica_choice(tuned["best"]["skin_over_H"])
     spec = dict(spec, params=tune.with_skin(spec, best_skin)["params"])
-    workload = dict(workload, verlet_skin_over_H=best_skin,
+    workload = dict(workload, verlet_skin_over_H=best_skin, library_variant=variant,
                     rebuild="on the device when a particle has moved skin/2 since the last build")
 
     clk = Clocks(torch.cuda.current_device())
@@ -556,6 +568,7 @@ def main():
                              "walls": fw["walls_ms"], "step_median": statistics.median(fw["ms"]),
                              "note": "kernel classes timed by event nodes on 50 extra profiled steps"},
             "autotune": tuned["table"],
+            "autotune_tiles": tiles["table"] if tiles else None,
             "e2e": e2e, "cpu_baseline": cb, "extras": extras,
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
         }

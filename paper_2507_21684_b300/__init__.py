@@ -20,6 +20,8 @@ __all__ = ["lib", "Params", "Scene", "Server", "SphError", "rollout_fn", "librar
 
 _HERE = Path(__file__).resolve().parent
 _LIBPATH = _HERE / "libsph_b300.so"
+if os.environ.get("SPH_B300_VARIANT", "default") != "default":
+    _LIBPATH = _HERE / f"libsph_b300_{os.environ['SPH_B300_VARIANT']}.so"
 _lib = None
 
 SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EUNSTABLE, SPH_ETIMEOUT, SPH_EBUSY, SPH_EINTERNAL = range(8)
@@ -113,6 +115,19 @@ _hooks = None
 
 def library_path() -> Path:
     return _LIBPATH
+
+
+def select_variant(name: str) -> None:
+    """Use a tile-shape variant of the library (build.VARIANTS; chosen by tune.tune_tiles).  Must be
+    called before the library is first used in this process."""
+    global _LIBPATH
+    from . import build as _b
+    if name not in _b.VARIANTS:
+        raise ValueError(f"unknown library variant {name!r}")
+    path = _b.lib_path(name)
+    if _lib is not None and path != _LIBPATH:
+        raise RuntimeError("the library is already loaded; select the variant first")
+    _LIBPATH = path
 
 
 def lib() -> C.CDLL:

@@ -12,6 +12,18 @@ INCLUDE = HERE.parent / "include"
 LIB = HERE / "libsph_b300.so"
 SOURCES = ["sph_kernels.cu", "sph_passes.cu", "sph_runtime.cu", "sph_server.cu", "sph_noalloc.cu", "sph_rebuild.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Tile-shape variants of the library (targets per tile, threads per target, hit-list length, for 2D
+# and 3D), timed against each other by tune.tune_tiles; "default" is libsph_b300.so.
+VARIANTS = {
+    "default": {},
+    "lanes8": {"SPH_TILE2_TP": 32, "SPH_TILE2_LANES": 8, "SPH_TILE2_LIST": 16,
+               "SPH_TILE3_TP": 16, "SPH_TILE3_LANES": 16, "SPH_TILE3_LIST": 12},
+    "lanes2": {"SPH_TILE2_TP": 128, "SPH_TILE2_LANES": 2, "SPH_TILE2_LIST": 40},
+}
+
+
+def lib_path(variant: str = "default") -> Path:
+    return LIB if variant == "default" else HERE / f"libsph_b300_{variant}.so"
 
 
 def nvcc() -> str:
@@ -21,23 +33,25 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def _stale() -> bool:
-    if not LIB.exists():
+def _stale(lib: Path = LIB) -> bool:
+    if not lib.exists():
         return True
-    t = LIB.stat().st_mtime
+    t = lib.stat().st_mtime
     deps = list(CSRC.glob("*")) + list(INCLUDE.glob("*.h")) + [Path(__file__)]
     return any(p.stat().st_mtime > t for p in deps if p.is_file())
 
 
-def build(force: bool = False, verbose: bool = False) -> Path:
-    """Compile every source into one shared library next to the package."""
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, variant: str = "default") -> Path:
+    """Compile every source into one shared library next to the package (one tile-shape variant)."""
+    lib = lib_path(variant)
+    if not force and not _stale(lib):
+        return lib
     objs = []
-    bdir = HERE / "_build"
-    bdir.mkdir(exist_ok=True)
+    bdir = HERE / "_build" / variant
+    bdir.mkdir(parents=True, exist_ok=True)
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
                     "--expt-relaxed-constexpr", "-I", str(INCLUDE)]
+    flags += [f"-D{k}={v}" for k, v in VARIANTS[variant].items()]
     if verbose:
         flags += ["-Xptxas", "-v"]
     for src in SOURCES:
@@ -47,12 +61,20 @@ def build(force: bool = False, verbose: bool = False) -> Path:
         o = bdir / (s.stem + ".o")
         subprocess.run([nvcc(), *flags, "-c", str(s), "-o", str(o)], check=True)
         objs.append(str(o))
-    tmp = str(LIB) + ".tmp"
+    tmp = str(lib) + ".tmp"
     subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False) -> list:
+    """Every tile-shape variant (the default first)."""
+    return [build(force=force, variant=v) for v in VARIANTS]
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    if "--all" in sys.argv:
+        for p in build_all(force="--force" in sys.argv):
+            print(p)
+    else:
+        print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
