@@ -254,8 +254,10 @@ def run_adjoint(sph, torch, spec, steps, ckpt):
     sc.adjoint(seed, None, None)
     torch.cuda.synchronize()
     adj_ms, adj_n = sc.timing(sph.TIMING_ADJOINT)
+    info = sc.adjoint_info()
     sc.close()
-    return dict(ms=total, pairs_per_step=pairs_per_step, adj_sweep_ms=adj_ms / max(adj_n, 1), adj_sweeps=adj_n)
+    return dict(ms=total, pairs_per_step=pairs_per_step, adj_sweep_ms=adj_ms / max(adj_n, 1), adj_sweeps=adj_n,
+                **info)
 
 
 def _stream_specs(n_scenes: int, rate: float, seed: int = 0):
@@ -517,14 +519,19 @@ def main():
             "loss_first_last": [float(hist[0, 0]), float(hist[-1, 0])],
             "note": "kernel classes timed by CUDA events on the scene's stream; the host time includes one cell rebuild per iteration"}
         sa = si.adjoint_problem(128)
-        ad = run_adjoint(sph, torch, sa, 200, 20)
-        extras["adjoint_128"] = {
-            "particles": sa["n_fluid"], "steps": 200, "ckpt_every": 20, "ms_total": ad["ms"],
-            "adjoint_pair_interactions_per_s": ad["pairs_per_step"] * 200 / (ad["ms"] / 1e3),
-            "adjoint_sweep_ms": ad["adj_sweep_ms"],
-            "adjoint_sweep_pairs_per_s": ad["pairs_per_step"] / (ad["adj_sweep_ms"] / 1e3),
-            "note": "time of sph_adjoint: 10 segment recomputes (forward replay) + 200 adjoint sweeps, "
-                    "one captured graph per segment"}
+        for name, skin in (("adjoint_128", 0.0), ("adjoint_128_skin", 0.1)):
+            spa = dict(sa, params=tune.with_skin(sa, skin)["params"])
+            ad = run_adjoint(sph, torch, spa, 200, 20)
+            extras[name] = {
+                "particles": sa["n_fluid"], "steps": 200, "ckpt_every": 20, "verlet_skin_over_H": skin,
+                "ms_total": ad["ms"],
+                "adjoint_pair_interactions_per_s": ad["pairs_per_step"] * 200 / (ad["ms"] / 1e3),
+                "adjoint_sweep_ms": ad["adj_sweep_ms"],
+                "adjoint_sweep_pairs_per_s": ad["pairs_per_step"] / (ad["adj_sweep_ms"] / 1e3),
+                "replay_rebuild_interval": ad["replay_interval"], "replay_fallbacks": ad["replay_fallbacks"],
+                "note": "time of sph_adjoint: 10 segment recomputes (forward replay) + 200 adjoint sweeps, "
+                        "captured graphs per segment part; with the skin the replay rebuilds every "
+                        "replay_rebuild_interval steps"}
         stream = {}
         for rate in args.stream_rates:
             reqs = _stream_specs(args.stream_scenes, rate)

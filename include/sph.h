@@ -250,6 +250,13 @@ SPH_API int sph_rollout(sph_scene* scene, int n_steps, int ckpt_every);
 SPH_API int sph_adjoint(sph_scene* scene, const float* xbar_T, const float* vbar_T, const float* rhobar_T,
                 float* xbar_0, float* vbar_0, float* rhobar_0, double* nubar, int ptr_is_device);
 
+/* The adjoint's forward replay of each segment rebuilds the cells at its first step and then
+ * every replay_interval steps when the scene has a Verlet skin (every step without one); a segment
+ * whose displacements outgrow the skin is replayed again with a rebuild every step, and the
+ * interval is halved for the segments that follow.  Reports the current interval and how many
+ * segments fell back (cumulative). */
+SPH_API int sph_adjoint_info(sph_scene* scene, int32_t* replay_interval, int64_t* replay_fallbacks);
+
 /* Scene geometry: cells per axis (3 ints), total particles. */
 SPH_API int sph_scene_info(const sph_scene* scene, int32_t* ncell3, int32_t* n_particles);
 

@@ -153,6 +153,7 @@ def lib() -> C.CDLL:
     L.sph_density_gradient.argtypes = [vp, vp, C.c_int]
     L.sph_set_ghosts.argtypes = [vp, vp, C.c_int]
     L.sph_set_support.argtypes = [vp, vp, C.c_int]
+    L.sph_adjoint_info.argtypes = [vp, P(C.c_int32), P(C.c_int64)]
     L.sph_debug_bounded_waits.argtypes = [P(C.c_int), P(C.c_int)]
     L.sph_support_query.argtypes = [vp, vp, vp, vp, C.c_int]
     L.sph_shift_gradient.argtypes = [vp, P(ShiftObjective), vp, vp, C.c_int]
@@ -348,6 +349,12 @@ class Scene:
         o = ShiftObjective.from_dict(objective)
         _check(lib().sph_shift_descend(self._h, C.byref(o), int(n_iters), float(step), hist.ctypes.data))
         return hist
+
+    def adjoint_info(self) -> dict:
+        """The adjoint replay's rebuild interval and the segments that fell back to every step."""
+        k, f = C.c_int32(), C.c_int64()
+        _check(lib().sph_adjoint_info(self._h, C.byref(k), C.byref(f)))
+        return {"replay_interval": k.value, "replay_fallbacks": f.value}
 
     def set_support(self, H):
         """Per-particle support radii (n rows, original order), 0 < H_i <= the scene's H."""

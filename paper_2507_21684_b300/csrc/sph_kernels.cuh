@@ -33,6 +33,8 @@ struct Displace {
   float inv_r2;          // 1 / (skin/2 - margin)^2
   RebuildCtl* ctl;       // set: the sweep's last CTA decides the next step's rebuild
   int interval;          // rebuild_interval
+  int* sticky;           // set (adjoint replay): the last CTA sets *sticky if the maximum exceeds 1,
+                         // then zeroes the maximum
 };
 
 // Objective of the shifting-by-optimisation passes (weights, pair penalty, target density).

@@ -933,7 +933,13 @@ struct SweepPass {
   // with the decision on the device: every CTA has folded its maximum in, so the last one
   // decides whether the next step rebuilds (interval reached or a displacement past skin/2)
   __device__ __forceinline__ void last_cta() {
-    if (!INTEGRATE || !disp.ctl) return;
+    if (!INTEGRATE) return;
+    if (disp.sticky) {  // a replayed step on a fixed rebuild schedule: record a violation
+      if (__uint_as_float(*(volatile unsigned*)disp.maxr) > 1.f) *disp.sticky = 1;
+      *disp.maxr = 0u;
+      return;
+    }
+    if (!disp.ctl) return;
     RebuildCtl* c = disp.ctl;
     const int since = c->since + 1;
     const bool r = since >= disp.interval || __uint_as_float(*(volatile unsigned*)&c->maxr) > 1.f;

@@ -343,6 +343,8 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
     const double half = 0.5 * (double)skin - 8.0 * std::ldexp(Lmax, -23);
     dev_policy = skin > 0.f && half > 0.0;
     inv_r2 = dev_policy ? (float)(1.0 / (half * half)) : 0.f;
+    // the adjoint's forward replay first tries a rebuild every 16 steps (every step without a skin)
+    replay_k = dev_policy ? 16 : 1;
   }
   // the decision is taken by the sweep and the rebuild is one cooperative launch when the
   // device supports it; otherwise a one-thread kernel decides and a conditional graph node rebuilds
@@ -650,13 +652,15 @@ void Scene::passes_before_sweep(const TravArgs& t_in, const Tile* tl, const int*
   if (renorm) grad_pass(t, tl, ntl);
 }
 
-void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const int* ntl, bool fused_walls) {
+void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const int* ntl, bool fused_walls,
+                  const Displace* disp) {
   if (!tl) {
     tl = tiles;
     ntl = d_ntiles;
   }
   prof_begin(0);
-  const Displace dp = dev_policy ? Displace{xbuild, &d_ctl->maxr, inv_r2, use_coop ? d_ctl : nullptr, interval}
+  const Displace dp = disp ? *disp
+                    : dev_policy ? Displace{xbuild, &d_ctl->maxr, inv_r2, use_coop ? d_ctl : nullptr, interval}
                                  : Displace{nullptr, nullptr, 0.f, nullptr, 0};
   const float4* g = renorm ? gradrho : nullptr;
   if (fused_walls) {
@@ -1023,6 +1027,11 @@ void Scene::alloc_tape(int k) {
     }
     Sd = (float4*)mem.get(sizeof(float4) * N);
     Pp = (float*)mem.get(sizeof(float) * N);
+    adj_rows = (float*)mem.get(sizeof(float) * (2 * (size_t)N * D + (size_t)N + 64));
+    d_replay_flag = (int*)mem.get(sizeof(int) * 4);
+    d_replay_maxr = (unsigned*)mem.get(sizeof(unsigned) * 2);
+    CK(cudaMemsetAsync(d_replay_flag, 0, sizeof(int) * 4, st));
+    CK(cudaMemsetAsync(d_replay_maxr, 0, sizeof(unsigned) * 2, st));
     nu_part = (float*)mem.get(sizeof(float) * (size_t)N);
     alloc_arrays(scratch_arr);
     alloc_arrays(ckpt_work);
@@ -1031,54 +1040,113 @@ void Scene::alloc_tape(int k) {
   tape_cap = k;
 }
 
-// Replay one segment forward from ckpt_work (keeping each step's sweep input, keys, permutation
-// and cell offsets in the tape), then run its adjoint steps backwards.  The adjoint state stays
-// in XB[0]/VB[0] at the segment's end (each backward step swaps the buffers twice).
-void Scene::adjoint_segment(int L) {
-  int q = 0;
-  // replay the segment forward, keeping the sweep input of every step; every replayed step
-  // rebuilds (the forward's displacement checks are not replayed)
+// Replay one segment of L steps forward from ckpt_work, keeping each step's sweep input in the
+// tape.  The cells are rebuilt at the segment's first step and every K steps (K = 1: every step);
+// a slot between rebuilds shares the cells of the last rebuild, and the sweep before it writes the
+// slot directly.  With K > 1 the sweeps measure the displacement since the last rebuild, and a
+// step whose successor does not rebuild sets d_replay_flag when it exceeds the skin's half: the
+// caller then replays the segment with K = 1.
+void Scene::adjoint_replay(int L, int K) {
   const Arrays* prev = &ckpt_work;
+  int r = 0;
   for (int s = 0; s < L; ++s) {
     TapeSlot& slot = tape[s];
-    rebuild(*prev, slot.a, slot.keys, slot.perm, slot.off, slot.tiles, slot.ntiles);  // kept in the slot
-    TravArgs t = trav(slot.a, slot.keys, slot.off);
-    passes_before_sweep(t, slot.tiles, slot.ntiles);
-    sweep(t, scratch_arr, slot.tiles, slot.ntiles);
+    if (s % K == 0) {
+      rebuild(*prev, slot.a, slot.keys, slot.perm, slot.off, slot.tiles, slot.ntiles);  // kept in the slot
+      r = s;
+    }
+    const TapeSlot& cells = tape[r];
+    TravArgs t = trav(slot.a, cells.keys, cells.off);
+    passes_before_sweep(t, cells.tiles, cells.ntiles);
+    const bool next_rebuilds = s + 1 == L || (s + 1) % K == 0;
+    const Arrays& out = next_rebuilds ? scratch_arr : tape[s + 1].a;
+    if (K > 1) {
+      const Displace dp{xbuild, d_replay_maxr, inv_r2, nullptr, interval, next_rebuilds ? d_replay_flag + 1 : d_replay_flag};
+      sweep(t, out, cells.tiles, cells.ntiles, false, &dp);
+    } else {
+      sweep(t, out, cells.tiles, cells.ntiles);
+    }
     prev = &scratch_arr;
   }
-  // backward through the segment
+}
+
+// The adjoint steps of a replayed segment backwards (rebuild every K steps, as replayed).  The
+// adjoint state enters and leaves in XB[0]/VB[0].
+void Scene::adjoint_backward(int L, int K) {
+  int q = 0;
   for (int s = L - 1; s >= 0; --s) {
     TapeSlot& slot = tape[s];
+    const TapeSlot& cells = tape[(s / K) * K];
     if (D == 2)
       launch_adj_seed<2>(dseg, N, slot.a, XB[q], VB[q], Sd, Pp, st);
     else
       launch_adj_seed<3>(dseg, N, slot.a, XB[q], VB[q], Sd, Pp, st);
     CKL();
-    TravArgs t = trav(slot.a, slot.keys, slot.off);
+    TravArgs t = trav(slot.a, cells.keys, cells.off);
     t.pair_count = nullptr;
     prof_begin(4);
     if (D == 2) {
       if (kern == 0)
-        launch_adj_t<2, 0>(t, slot.tiles, slot.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        launch_adj_t<2, 0>(t, cells.tiles, cells.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
       else
-        launch_adj_t<2, 1>(t, slot.tiles, slot.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        launch_adj_t<2, 1>(t, cells.tiles, cells.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
     } else {
       if (kern == 0)
-        launch_adj_t<3, 0>(t, slot.tiles, slot.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        launch_adj_t<3, 0>(t, cells.tiles, cells.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
       else
-        launch_adj_t<3, 1>(t, slot.tiles, slot.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        launch_adj_t<3, 1>(t, cells.tiles, cells.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
     }
     CKL();
     prof_end();
     launch_sum_segments(nu_part, dseg, S, d_nubar, st);
     CKL();
     q = 1 - q;
-    launch_adj_unpermute(N, slot.perm, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
-    CKL();
-    q = 1 - q;
-    launches += 4;  // seed, adjoint sweep, segment sums, un-permute
+    launches += 3;  // seed, adjoint sweep, segment sums
+    if (s % K == 0) {  // the step's rebuild permuted the state: back to the previous order
+      launch_adj_unpermute(N, slot.perm, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
+      CKL();
+      q = 1 - q;
+      ++launches;
+    }
   }
+  if (q != 0) {  // back into XB[0]/VB[0]
+    CK(cudaMemcpyAsync(XB[0], XB[1], sizeof(float4) * N, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(VB[0], VB[1], sizeof(float4) * N, cudaMemcpyDeviceToDevice, st));
+  }
+}
+
+// Runs (or captures and replays) one part of a segment: part 0 the forward replay, 1 the adjoint.
+void Scene::adjoint_part(int part, int L, int K) {
+  if (!use_graphs || profiling) {
+    if (part == 0) adjoint_replay(L, K);
+    else adjoint_backward(L, K);
+    return;
+  }
+  const long long key = ((long long)part << 40) | ((long long)K << 20) | (long long)L;
+  auto it = adj_graphs.find(key);
+  if (it == adj_graphs.end()) {
+    const long long l0 = launches;
+    cudaGraph_t g;
+    capturing = true;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+      if (part == 0) adjoint_replay(L, K);
+      else adjoint_backward(L, K);
+    } catch (...) {
+      cudaStreamEndCapture(st, &g);
+      capturing = false;
+      throw;
+    }
+    CK(cudaStreamEndCapture(st, &g));
+    capturing = false;
+    cudaGraphExec_t ge;
+    CK(cudaGraphInstantiate(&ge, g, 0));
+    cudaGraphDestroy(g);
+    it = adj_graphs.emplace(key, std::make_pair(ge, launches - l0)).first;
+  } else {
+    launches += it->second.second;
+  }
+  CK(cudaGraphLaunch(it->second.first, st));
 }
 
 void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb0, float* vb0, float* rb0, double* nub,
@@ -1098,11 +1166,11 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
     if (rb) { CK(cudaMemcpyAsync(p + 2 * nd, rb, 4 * (size_t)nf_total, cudaMemcpyHostToDevice, st)); drb = p + 2 * nd; }
   }
   int q = 0;
-  if (D == 2)
-    launch_adj_load<2>(N, buf[cur].meta, d_orig_base, dxb, dvb, drb, XB[q], VB[q], st);
-  else
-    launch_adj_load<3>(N, buf[cur].meta, d_orig_base, dxb, dvb, drb, XB[q], VB[q], st);
-  CKL();
+  // the adjoint state is carried in storage order; each segment's replay may store the particles
+  // in another order than the forward rollout did (its rebuild schedule differs), so the state
+  // enters each segment through the original order: the seeds after the last segment's replay,
+  // the running adjoint by a store / load through the rows at every later segment
+  float* rows = adj_rows;
   CK(cudaMemsetAsync(d_nubar, 0, sizeof(double) * S, st));
   const int ncp = (n + k - 1) / k;
   for (int sgi = ncp - 1; sgi >= 0; --sgi) {
@@ -1116,33 +1184,43 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
       launch_copy_state<3>(N, ckpts[sgi], ckpt_work, st);
     CKL();
     ++launches;
-    if (!use_graphs || profiling) {
-      adjoint_segment(L);
-      continue;
-    }
-    auto it = adj_graphs.find(L);
-    if (it == adj_graphs.end()) {
-      const long long l0 = launches;
-      cudaGraph_t g;
-      capturing = true;
-      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      try {
-        adjoint_segment(L);
-      } catch (...) {
-        cudaStreamEndCapture(st, &g);
-        capturing = false;
-        throw;
+    // the replay rebuilds every replay_k steps when the skin allows; a segment whose
+    // displacements outgrew the skin is replayed again with a rebuild every step (and later
+    // segments try half the interval)
+    int K = std::max(1, std::min(replay_k, L));
+    if (K > 1) CK(cudaMemsetAsync(d_replay_flag, 0, sizeof(int) * 2, st));
+    adjoint_part(0, L, K);
+    if (K > 1) {
+      int flag = 0;
+      CK(cudaMemcpyAsync(&flag, d_replay_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (flag) {
+        ++replay_fallbacks;
+        replay_k = std::max(1, replay_k / 2);
+        K = 1;
+        adjoint_part(0, L, K);
       }
-      CK(cudaStreamEndCapture(st, &g));
-      capturing = false;
-      cudaGraphExec_t ge;
-      CK(cudaGraphInstantiate(&ge, g, 0));
-      cudaGraphDestroy(g);
-      it = adj_graphs.emplace(L, std::make_pair(ge, launches - l0)).first;
-    } else {
-      launches += it->second.second;
     }
-    CK(cudaGraphLaunch(it->second.first, st));
+    // the adjoint of the segment's final state, in the order of the replay's last sweep output
+    const float *lx = dxb, *lv = dvb, *lr = drb;
+    if (sgi != ncp - 1) {  // the running adjoint, in the order of the checkpoint after this segment
+      if (D == 2)
+        launch_adj_store<2>(N, ckpts[sgi + 1].meta, d_orig_base, XB[0], VB[0], rows, rows + nd, rows + 2 * nd, st);
+      else
+        launch_adj_store<3>(N, ckpts[sgi + 1].meta, d_orig_base, XB[0], VB[0], rows, rows + nd, rows + 2 * nd, st);
+      CKL();
+      lx = rows;
+      lv = rows + nd;
+      lr = rows + 2 * nd;
+      ++launches;
+    }
+    if (D == 2)
+      launch_adj_load<2>(N, scratch_arr.meta, d_orig_base, lx, lv, lr, XB[0], VB[0], st);
+    else
+      launch_adj_load<3>(N, scratch_arr.meta, d_orig_base, lx, lv, lr, XB[0], VB[0], st);
+    CKL();
+    ++launches;
+    adjoint_part(1, L, K);
   }
   // XB[q] is in the storage order of checkpoint 0; deliver in original order
   float* oxb = xb0;
@@ -1720,6 +1798,16 @@ int sph_debug_bounded_waits(int* gate_status, int* barrier_status) {
   if (gate_status) *gate_status = h[0];
   if (barrier_status) *barrier_status = h[1];
   API_END
+}
+
+int sph_adjoint_info(sph_scene* sc, int32_t* replay_interval, int64_t* replay_fallbacks) {
+  if (!sc) {
+    sph::set_err("sph_adjoint_info: NULL scene");
+    return SPH_EINVAL;
+  }
+  if (replay_interval) *replay_interval = sc->s.replay_k;
+  if (replay_fallbacks) *replay_fallbacks = sc->s.replay_fallbacks;
+  return SPH_OK;
 }
 
 int sph_set_support(sph_scene* sc, const float* H, int ptr_is_device) {

@@ -172,7 +172,12 @@ struct Scene {
   float* nu_part = nullptr;
   Arrays scratch_arr{};
   Arrays ckpt_work{};               // the segment's checkpoint, copied (graphs do not depend on it)
-  std::map<int, std::pair<cudaGraphExec_t, long long>> adj_graphs;  // by segment length
+  std::map<long long, std::pair<cudaGraphExec_t, long long>> adj_graphs;  // by part, interval, length
+  int replay_k = 1;                 // rebuild interval of the adjoint's forward replay (skin > 0)
+  int* d_replay_flag = nullptr;     // [0] a replayed step outgrew the skin, [1] scratch
+  float* adj_rows = nullptr;        // the running adjoint by original row (segment boundaries)
+  unsigned* d_replay_maxr = nullptr;
+  long long replay_fallbacks = 0;
 
   ~Scene();
   void bind_stream(cudaStream_t user);
@@ -206,7 +211,7 @@ struct Scene {
   void need_ghosts() const;
   void grad_pass(const TravArgs& t, const Tile* tl, const int* ntl);
   void sweep(const TravArgs& t, const Arrays& out, const Tile* tl = nullptr, const int* ntl = nullptr,
-             bool fused_walls = false);
+             bool fused_walls = false, const Displace* disp = nullptr);
   void host_rebuild();
   void step_once();
   void step_conditional();
@@ -220,7 +225,9 @@ struct Scene {
   void ensure_cells();
   void rollout(int n, int k);
   void alloc_tape(int k);
-  void adjoint_segment(int L);
+  void adjoint_replay(int L, int K);
+  void adjoint_backward(int L, int K);
+  void adjoint_part(int part, int L, int K);
   void adjoint(const float* xb, const float* vb, const float* rb, float* xb0, float* vb0, float* rb0, double* nub,
                int is_dev);
   void get_state(float* x, float* v, float* rho, int is_dev);

@@ -297,6 +297,40 @@ def test_adjoint_matches_oracle_and_fd(sph, orc):
     assert abs(gnu - fd_nu) < 1e-3 * abs(fd_nu)
 
 
+def _adjoint_vs_oracle(sph, orc, s, steps=200):
+    vt = s["v_target"]
+    N = s["n_fluid"]
+    xt, _, _ = orc.rollout(s, steps, v=vt)
+    with make(sph, s) as sc:
+        sc.rollout(steps, 20)
+        xT, _, _ = sc.get_state()
+        seed = (2.0 * (xT.astype(np.float64) - xt) / N).astype(np.float32)
+        gx, gv, gr, gnu = sc.adjoint(seed, None, None)
+        info = sc.adjoint_info()
+    x0, v0, r0 = (s[k].astype(np.float64) for k in ("x", "v", "rho"))
+    xo, _, _ = orc.rollout64(s, steps, x0, v0, r0)
+    oseed = 2.0 * (xo - xt) / N
+    o = orc.adjoint(s, steps, oseed, np.zeros_like(oseed), np.zeros(N), x=x0, v=v0, rho=r0)
+    return gx, gv, gnu, o, info
+
+
+@pytest.mark.parametrize("skin_over_H,expect_fallback", [(0.1, False), (0.002, True)])
+def test_adjoint_replay_on_a_skin(sph, orc, skin_over_H, expect_fallback):
+    """With a Verlet skin the adjoint's forward replay rebuilds every 16 steps; a skin too thin
+    for that makes the replay fall back to a rebuild every step.  Either way the gradients are
+    the oracle's."""
+    s = si.adjoint_problem(16)
+    p = dict(s["params"], skin=float(np.float32(skin_over_H * s["params"]["H"])), rebuild_interval=1 << 20)
+    s = dict(s, params=p)
+    gx, gv, gnu, o, info = _adjoint_vs_oracle(sph, orc, s)
+    assert rel(gv, o["vb"]) < 1e-3
+    assert rel(gx, o["xb"]) < 1e-3
+    assert abs(gnu - o["nub"]) < 1e-3 * abs(o["nub"])
+    assert (info["replay_fallbacks"] > 0) == expect_fallback, info
+    if not expect_fallback:
+        assert info["replay_interval"] == 16
+
+
 def test_autograd_function_matches_adjoint(sph):
     """rollout_fn (torch.autograd.Function: forward sph_rollout, backward sph_adjoint) gives the
     gradients of the direct adjoint call, for a loss on the final positions."""
