@@ -519,7 +519,7 @@ def main():
             "loss_first_last": [float(hist[0, 0]), float(hist[-1, 0])],
             "note": "kernel classes timed by CUDA events on the scene's stream; the host time includes one cell rebuild per iteration"}
         sa = si.adjoint_problem(128)
-        for name, skin in (("adjoint_128", 0.0), ("adjoint_128_skin", 0.1)):
+        for name, skin in (("adjoint_128", 0.0), ("adjoint_128_skin", 0.3)):
             spa = dict(sa, params=tune.with_skin(sa, skin)["params"])
             ad = run_adjoint(sph, torch, spa, 200, 20)
             extras[name] = {

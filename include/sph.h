@@ -251,11 +251,15 @@ SPH_API int sph_adjoint(sph_scene* scene, const float* xbar_T, const float* vbar
                 float* xbar_0, float* vbar_0, float* rhobar_0, double* nubar, int ptr_is_device);
 
 /* The adjoint's forward replay of each segment rebuilds the cells at its first step and then
- * every replay_interval steps when the scene has a Verlet skin (every step without one); a segment
+ * every replay_interval steps when the scene has a Verlet skin (every step without one; the
+ * interval starts at three quarters of the rollout's mean rebuild interval, at most 16); a segment
  * whose displacements outgrow the skin is replayed again with a rebuild every step, and the
  * interval is halved for the segments that follow.  Reports the current interval and how many
  * segments fell back (cumulative). */
 SPH_API int sph_adjoint_info(sph_scene* scene, int32_t* replay_interval, int64_t* replay_fallbacks);
+/* Fix the replay's starting interval (taken at the next sph_rollout; 0 restores the automatic
+ * choice).  Results do not depend on it: an interval the skin cannot sustain falls back. */
+SPH_API int sph_set_adjoint_replay(sph_scene* scene, int replay_interval);
 
 /* Scene geometry: cells per axis (3 ints), total particles. */
 SPH_API int sph_scene_info(const sph_scene* scene, int32_t* ncell3, int32_t* n_particles);

@@ -154,6 +154,7 @@ def lib() -> C.CDLL:
     L.sph_set_ghosts.argtypes = [vp, vp, C.c_int]
     L.sph_set_support.argtypes = [vp, vp, C.c_int]
     L.sph_adjoint_info.argtypes = [vp, P(C.c_int32), P(C.c_int64)]
+    L.sph_set_adjoint_replay.argtypes = [vp, C.c_int]
     L.sph_debug_bounded_waits.argtypes = [P(C.c_int), P(C.c_int)]
     L.sph_support_query.argtypes = [vp, vp, vp, vp, C.c_int]
     L.sph_shift_gradient.argtypes = [vp, P(ShiftObjective), vp, vp, C.c_int]
@@ -355,6 +356,10 @@ class Scene:
         k, f = C.c_int32(), C.c_int64()
         _check(lib().sph_adjoint_info(self._h, C.byref(k), C.byref(f)))
         return {"replay_interval": k.value, "replay_fallbacks": f.value}
+
+    def set_adjoint_replay(self, interval: int = 0):
+        """Fix the adjoint replay's starting rebuild interval (0: from the rollout)."""
+        _check(lib().sph_set_adjoint_replay(self._h, int(interval)))
 
     def set_support(self, H):
         """Per-particle support radii (n rows, original order), 0 < H_i <= the scene's H."""

@@ -998,6 +998,8 @@ void Scene::rollout(int n, int k) {
   // segment by segment: checkpoint, then the segment's steps exactly as sph_step runs them
   // (graph chunks, the same rebuild schedule), starting from a fresh build like the replay
   long long seg_launches = 0;
+  int64_t r0 = 0, r1 = 0;
+  if (dev_policy) stats(nullptr, &r0, nullptr);
   for (int s0 = 0; s0 < n; s0 += k) {
     copy_arrays(ckpts[s0 / k], buf[cur]);
     cells_valid = false;
@@ -1006,6 +1008,14 @@ void Scene::rollout(int n, int k) {
   }
   launches = seg_launches;  // (pair counts: those of the last segment's steps)
   tape_valid = true;
+  if (dev_policy) {
+    // the adjoint's replay starts from three quarters of the rollout's mean rebuild interval
+    // (or the caller's choice)
+    stats(nullptr, &r1, nullptr);
+    const int64_t rb = std::max<int64_t>(1, r1 - r0);
+    replay_k = replay_k_user > 0 ? replay_k_user
+                                 : (int)std::max<int64_t>(1, std::min<int64_t>(16, (3 * (int64_t)n) / (4 * rb)));
+  }
 }
 
 void Scene::alloc_tape(int k) {
@@ -1798,6 +1808,15 @@ int sph_debug_bounded_waits(int* gate_status, int* barrier_status) {
   if (gate_status) *gate_status = h[0];
   if (barrier_status) *barrier_status = h[1];
   API_END
+}
+
+int sph_set_adjoint_replay(sph_scene* sc, int replay_interval) {
+  if (!sc || replay_interval < 0 || replay_interval > 4096) {
+    sph::set_err("sph_set_adjoint_replay: NULL scene or interval outside [0, 4096]");
+    return SPH_EINVAL;
+  }
+  sc->s.replay_k_user = replay_interval;
+  return SPH_OK;
 }
 
 int sph_adjoint_info(sph_scene* sc, int32_t* replay_interval, int64_t* replay_fallbacks) {

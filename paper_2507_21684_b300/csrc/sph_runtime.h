@@ -174,6 +174,7 @@ struct Scene {
   Arrays ckpt_work{};               // the segment's checkpoint, copied (graphs do not depend on it)
   std::map<long long, std::pair<cudaGraphExec_t, long long>> adj_graphs;  // by part, interval, length
   int replay_k = 1;                 // rebuild interval of the adjoint's forward replay (skin > 0)
+  int replay_k_user = 0;            // the caller's interval (0: from the rollout's rebuild rate)
   int* d_replay_flag = nullptr;     // [0] a replayed step outgrew the skin, [1] scratch
   float* adj_rows = nullptr;        // the running adjoint by original row (segment boundaries)
   unsigned* d_replay_maxr = nullptr;
