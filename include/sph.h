@@ -99,8 +99,9 @@ extern "C" {
  * The cell structure is rebuilt every step when skin == 0.  With skin > 0 (a Verlet list in the
  * sense of App. B) a captured step rebuilds only when rebuild_interval sweeps have used the
  * current cells or when some particle has moved farther than skin/2 since the last build (the
- * sweep measures the displacement; the decision is a conditional node of the step's CUDA graph,
- * taken on the device).  Steps run without graphs, and the adjoint's replay, rebuild every step. */
+ * sweep measures the displacement and its last CTA decides; the rebuild is a cooperative launch in
+ * the step's CUDA graph that returns at once unless a rebuild is due).  Steps run without graphs
+ * rebuild every step; the adjoint's replay rebuilds on its own schedule (sph_adjoint_info). */
 typedef struct sph_params {
   int32_t dim;            /* 2 or 3 */
   int32_t kernel;         /* SPH_KERNEL_* */
@@ -291,8 +292,8 @@ SPH_API int sph_timing(sph_scene* scene, int kernel_class, double* ms, int64_t* 
 
 /* How sph_step issues its work: use_graphs = 1 (default) captures chunks of graph_chunk steps
  * (default 8) into CUDA graphs and replays them; 0 launches every kernel from the host, one step
- * at a time, and then rebuilds the cell structure every step (the device-side skin check needs
- * the graphs' conditional nodes).  Results do not depend on the choice, except through the
+ * at a time, and then rebuilds the cell structure every step (the device-side skin check lives in
+ * the captured steps).  Results do not depend on the choice, except through the
  * summation order that the rebuild schedule sets.  SPH_EINVAL for graph_chunk outside [1, 4096]. */
 SPH_API int sph_set_execution(sph_scene* scene, int use_graphs, int graph_chunk);
 

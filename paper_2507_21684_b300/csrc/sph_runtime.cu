@@ -705,7 +705,7 @@ void Scene::shift_pass() {
 }
 
 // Rebuild launched by the host (eager steps, cells needed by a query): permute into the other
-// buffer; the device-side policy counters restart from this build.
+// buffer; the device-side policy counters restart from this rebuild.
 void Scene::host_rebuild() {
   auto kp = rebuild(buf[cur], buf[1 - cur], nullptr, nullptr, cell_off);
   keys_sorted = kp.first;
