@@ -891,10 +891,9 @@ struct SweepPass {
     float xi[D], vi[D], rho_i, p_i;
     float acc[D], c1, c2;
     float gi[D];              // RENORM: half the target's renormalised density gradient
-    float invH, Kg, Cv, eH2;  // 2D: the scene's constants kept in registers (3D reads them)
+    float invH, Kg, Cv, eH2;  // the scene's constants, kept in registers
     __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4 gj, float, int) {
-      const float cinvH = D == 2 ? invH : s->invH, cKg = D == 2 ? Kg : s->Kg;
-      const float cCv = D == 2 ? Cv : s->Cv, ceH2 = D == 2 ? eH2 : s->eH2;
+      const float cinvH = invH, cKg = Kg, cCv = Cv, ceH2 = eH2;
       float r[D];
       const float r2 = diff<D>(xs, pj.x, r);
       const float q = safe_q(r2, cinvH);
@@ -971,12 +970,10 @@ struct SweepPass {
 #pragma unroll
       for (int k = 0; k < D; ++k) b.gi[k] = 0.5f * gs[k];
     }
-    if (D == 2) {
-      b.invH = s.invH;
-      b.Kg = s.Kg;
-      b.Cv = s.Cv;
-      b.eH2 = s.eH2;
-    }
+    b.invH = s.invH;
+    b.Kg = s.Kg;
+    b.Cv = s.Cv;
+    b.eH2 = s.eH2;
     const PD<D> me = load_pd_plain<D>(tv.a, tv.k);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
