@@ -21,8 +21,8 @@ struct Tile {
   int cx0, cx1, cy, cz;
 };
 
-// Tile shape per dimension: targets per tile (TP), threads per target (LANES, TP x LANES = 256)
-// and hit-list entries per thread (LIST).  Set per build (SPH_TILE2_* / SPH_TILE3_*) so that the
+// Tile shape per dimension: targets per tile (TP), threads per target (LANES, TP x LANES = THREADS
+// per CTA), staged-particle capacity (CAP) and hit-list entries per thread (LIST).  Set per build (SPH_TILE2_* / SPH_TILE3_*) so that the
 // autotuner can time library variants against each other; the defaults are the shapes measured
 // best on the B300 for the dam break and the 3D Taylor-Green vortex.
 #ifndef SPH_TILE2_TP
@@ -30,23 +30,31 @@ struct Tile {
 #define SPH_TILE2_LANES 4
 #define SPH_TILE2_LIST 24
 #endif
+#ifndef SPH_TILE2_THREADS
+#define SPH_TILE2_THREADS 256
+#define SPH_TILE2_CAP 1024
+#endif
 #ifndef SPH_TILE3_TP
 #define SPH_TILE3_TP 32
 #define SPH_TILE3_LANES 8
 #define SPH_TILE3_LIST 18
+#endif
+#ifndef SPH_TILE3_THREADS
+#define SPH_TILE3_THREADS 256
+#define SPH_TILE3_CAP 1024
 #endif
 
 template <int D>
 struct TileCfg;
 template <>
 struct TileCfg<2> {
-  static constexpr int TP = SPH_TILE2_TP, LANES = SPH_TILE2_LANES, THREADS = 256, CAP = 1024, LIST = SPH_TILE2_LIST,
-                       NL = 3;
+  static constexpr int TP = SPH_TILE2_TP, LANES = SPH_TILE2_LANES, THREADS = SPH_TILE2_THREADS, CAP = SPH_TILE2_CAP,
+                       LIST = SPH_TILE2_LIST, NL = 3;
 };
 template <>
 struct TileCfg<3> {
-  static constexpr int TP = SPH_TILE3_TP, LANES = SPH_TILE3_LANES, THREADS = 256, CAP = 1024, LIST = SPH_TILE3_LIST,
-                       NL = 9;
+  static constexpr int TP = SPH_TILE3_TP, LANES = SPH_TILE3_LANES, THREADS = SPH_TILE3_THREADS, CAP = SPH_TILE3_CAP,
+                       LIST = SPH_TILE3_LIST, NL = 9;
 };
 
 // The records of a tile's own targets (a contiguous range of sorted particles), copied into
