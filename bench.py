@@ -65,6 +65,17 @@ def stored_traffic(profile: str):
     return int(tb.group(1))
 
 
+def hbm_view(alg_bytes: float, dram_bytes, ms: float, peak_gbs):
+    """A kernel's algorithmic and measured DRAM bandwidth against the measured HBM peak."""
+    if not ms or ms <= 0:
+        return None
+    alg = alg_bytes / (ms * 1e-3) / 1e9
+    dram = dram_bytes / (ms * 1e-3) / 1e9 if dram_bytes else None
+    return {"algorithmic_gbs": alg, "dram_gbs": dram, "peak_gbs": peak_gbs,
+            "algorithmic_frac": alg / peak_gbs if peak_gbs else None,
+            "dram_frac": dram / peak_gbs if (peak_gbs and dram) else None}
+
+
 def replica_reduce(t_local: float, units_local: float, device: str = "cpu"):
     """Whole-job figures of replicas: the slowest rank's time and the units of all ranks
     (identity for a single process)."""
@@ -578,6 +589,12 @@ def main():
             "autotune_tiles": tiles["table"] if tiles else None,
             "e2e": e2e, "cpu_baseline": cb, "extras": extras,
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
+            # the same kernel against the memory roofline (it is not memory bound): algorithmic
+            # bytes = the state read and written once (40 B per particle in 2D), and the DRAM
+            # bytes of the committed ncu capture, over the kernel's mean time
+            "hbm_view": hbm_view(40.0 * spec["n_fluid"] + 40.0 * spec["n_wall"],
+                                 stored_traffic("k_walls_sweep_t_dambreak_128.md"), fw["sweep_ms"],
+                                 peaks.get("hbm_gbs")),
         }
         print(json.dumps(line))
     if ws > 1:
