@@ -323,7 +323,8 @@ SPH_API void sph_destroy(sph_scene* scene);
  * Forward requests share the batch only with requests of the same dim, kernel, density mode,
  * diffusion form, shifting on or off, wall treatment, skin and rebuild_interval; one of another kind waits, in
  * arrival order, until the running batch has drained.
- * Results stay with the server until sph_wait returns them (once per ticket). */
+ * A scene of the batch that becomes unstable fails alone (SPH_EUNSTABLE from sph_wait); the others
+ * continue.  Results stay with the server until sph_wait returns them (once per ticket). */
 #define SPH_REQ_FORWARD 0
 #define SPH_REQ_ADJOINT 1
 

@@ -1036,7 +1036,10 @@ struct SweepPass {
       bool bad = !(me.rho > 0.5f * s.rho0 && me.rho < 2.f * s.rho0);
 #pragma unroll
       for (int k = 0; k < D; ++k) bad |= !isfinite(c.hi[k]) || !isfinite(me.v[k]);
-      if (bad) atomicOr(status, 1);
+      if (bad) {
+        atomicOr(status, 1);
+        atomicOr(status + 4 + (int)m.y, 1);  // which scene of the batch
+      }
     } else if (FUSED) {
       return;  // a wall: written by its wall task
     }

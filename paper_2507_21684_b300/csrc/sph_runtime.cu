@@ -387,7 +387,7 @@ void Scene::alloc_all() {
   d_ntiles = (int*)mem.get(sizeof(int) * 2);
   d_tile_ctr = (int*)mem.get(sizeof(int) * 4);
   CK(cudaMemsetAsync(d_tile_ctr, 0, sizeof(int) * 4, st));  // tiled kernels leave it zeroed
-  d_status = (int*)mem.get(sizeof(int) * 4);
+  d_status = (int*)mem.get(sizeof(int) * (4 + (size_t)S));  // [0] error bits, [4 + s] scene s unstable
   d_pairs = (unsigned long long*)mem.get(sizeof(unsigned long long) * 2);
   d_ctl = (RebuildCtl*)mem.get(sizeof(RebuildCtl));
   CK(cudaMemsetAsync(d_ctl, 0, sizeof(RebuildCtl), st));
@@ -395,7 +395,7 @@ void Scene::alloc_all() {
   CK(cudaMemsetAsync(d_bar, 0, sizeof(unsigned) * 2, st));
   xbuild = (float4*)mem.get(sizeof(float4) * (size_t)N);
   d_nubar = (double*)mem.get(sizeof(double) * (size_t)(S + 1));
-  CK(cudaMemsetAsync(d_status, 0, sizeof(int) * 4, st));
+  CK(cudaMemsetAsync(d_status, 0, sizeof(int) * (4 + (size_t)S), st));
   CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long) * 2, st));
   cells_valid = false;
   steps_since_build = 0;
@@ -1281,6 +1281,21 @@ void Scene::get_state(float* x, float* v, float* rho, int is_dev) {
     if (rho) CK(cudaMemcpyAsync(rho, orh, 4 * (size_t)N, cudaMemcpyDeviceToHost, st));
   }
   check_status();
+}
+
+// The status words (synchronises): [0] error bits, then one word per scene of the batch (bit 0: that
+// scene became unstable).
+std::vector<int> Scene::status_words() {
+  std::vector<int> h(4 + (size_t)S);
+  CK(cudaMemcpyAsync(h.data(), d_status, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return h;
+}
+
+// Clear the instability marks (the caller has taken the unstable scenes out).
+void Scene::clear_unstable() {
+  CK(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(d_status + 4, 0, sizeof(int) * (size_t)S, st));
 }
 
 void Scene::check_status() {

@@ -233,6 +233,8 @@ struct Scene {
                int is_dev);
   void get_state(float* x, float* v, float* rho, int is_dev);
   void check_status();
+  std::vector<int> status_words();
+  void clear_unstable();
   void rates(float* a, float* drho, float* rho, int is_dev);
   void density_gradient(float* grad, int is_dev);
   void opt_passes(const ShiftObjective& o, const Arrays* out, float step, double* loss_slot);

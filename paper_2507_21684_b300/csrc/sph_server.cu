@@ -224,7 +224,21 @@ struct Server {
           (r->steps_done >= r->n_steps ? done : keep).push_back(r);
         }
         if (!done.empty()) {
-          batch->check_status();
+          // scenes that became unstable fail alone; the others continue
+          const std::vector<int> sw = batch->status_words();
+          if (sw[0] & ~1) batch->check_status();  // an internal error fails the batch
+          if (sw[0] & 1) {
+            std::vector<std::shared_ptr<Request>> bad;
+            auto unstable = [&](const std::shared_ptr<Request>& r) { return (sw[4 + r->seg] & 1) != 0; };
+            for (auto& r : active)
+              if (unstable(r)) bad.push_back(r);
+            done.erase(std::remove_if(done.begin(), done.end(), unstable), done.end());
+            keep.erase(std::remove_if(keep.begin(), keep.end(), unstable), keep.end());
+            batch->clear_unstable();
+            std::lock_guard<std::mutex> lk(mu);
+            for (auto& r : bad)
+              finish_locked(r, SPH_EUNSTABLE, "unstable state: non-finite values or density outside [0.5, 2] rho0");
+          }
           for (auto& r : done) {
             const DevSeg& g = batch->segs[r->seg];
             float* dev = (float*)batch->mem_tmp(sizeof(float) * (size_t)r->n * (2 * r->d + 1));

@@ -69,6 +69,25 @@ def test_mixed_kinds_are_served_in_separate_batches(sph):
             assert np.array_equal(g[k], ref[k]), k
 
 
+def test_an_unstable_request_fails_alone(sph):
+    """A scene that goes unstable in the shared batch fails with SPH_EUNSTABLE; the scenes
+    batched with it finish with their results alone."""
+    good = [si.taylor_green_2d(24, seed=1), si.taylor_green_2d(20, seed=2)]
+    bad = si.taylor_green_2d(16, seed=0)
+    bad = dict(bad, v=(bad["v"] * 200.0).astype(np.float32))
+    with sph.Server(8 << 30, 64) as sv:
+        tg = [sv.submit(good[0], 30), sv.submit(bad, 40), sv.submit(good[1], 35)]
+        r0 = sv.wait(tg[0])
+        with pytest.raises(sph.SphError) as e:
+            sv.wait(tg[1])
+        assert e.value.code == sph.SPH_EUNSTABLE
+        r2 = sv.wait(tg[2])
+    for spec, st, g in ((good[0], 30, r0), (good[1], 35, r2)):
+        ref = _alone(sph, spec, st)
+        for k in ("x", "v", "rho"):
+            assert np.array_equal(g[k], ref[k]), k
+
+
 def test_admission_respects_budget_and_wait_is_bounded(sph):
     specs = [si.taylor_green_2d(48, seed=k) for k in range(4)]
     # budget for about one scene at a time: requests queue and run one after another
