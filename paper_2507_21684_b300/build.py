@@ -59,13 +59,19 @@ def build(force: bool = False, verbose: bool = False, variant: str = "default") 
     flags += [f"-D{k}={v}" for k, v in VARIANTS[variant].items()]
     if verbose:
         flags += ["-Xptxas", "-v"]
+    jobs = []
     for src in SOURCES:
         s = CSRC / src
         if not s.exists():
             continue
         o = bdir / (s.stem + ".o")
-        subprocess.run([nvcc(), *flags, "-c", str(s), "-o", str(o)], check=True)
+        jobs.append([nvcc(), *flags, "-c", str(s), "-o", str(o)])
         objs.append(str(o))
+    # one nvcc process per source, in parallel
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        for f in [ex.submit(subprocess.run, j, check=True) for j in jobs]:
+            f.result()
     tmp = str(lib) + ".tmp"
     subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], check=True)
     os.replace(tmp, lib)
@@ -73,8 +79,13 @@ def build(force: bool = False, verbose: bool = False, variant: str = "default") 
 
 
 def build_all(force: bool = False) -> list:
-    """Every tile-shape variant (the default first)."""
-    return [build(force=force, variant=v) for v in VARIANTS]
+    """Every tile-shape variant (the default first; the variants in parallel)."""
+    first = build(force=force)
+    from concurrent.futures import ThreadPoolExecutor
+    rest = [v for v in VARIANTS if v != "default"]
+    with ThreadPoolExecutor(max_workers=max(1, len(rest))) as ex:
+        libs = [f.result() for f in [ex.submit(build, force, False, v) for v in rest]]
+    return [first] + libs
 
 
 if __name__ == "__main__":
