@@ -162,7 +162,10 @@ SPH_API int sph_init(const sph_params* params, int n_fluid, int n_wall, const fl
  * The other calls then act on the whole batch: particle rows of get_state / rates / adjoint are
  * the scenes' rows concatenated in scene order (sph_batch_info gives each scene's first row and
  * row count), and sph_adjoint writes one viscosity adjoint per scene.  Each scene's results are
- * identical (bitwise) to running it alone. */
+ * identical (bitwise) to running it alone when the cells are rebuilt every step (no skin, or
+ * steps without graphs); with a Verlet skin the batch rebuilds all its scenes whenever one of them
+ * needs it, so a scene may be re-sorted at other steps than alone: the same neighbours, its sums
+ * taken in another order (float rounding). */
 SPH_API int sph_init_batch(int n_scenes, const sph_params* params, const int* n_fluid, const int* n_wall,
                            const float* const* x, const float* const* v, const float* const* rho,
                            const float* const* mass, int ptr_is_device, void* cuda_stream, sph_scene** out);
@@ -319,7 +322,8 @@ SPH_API void sph_destroy(sph_scene* scene);
  * launches; arrivals join and finished requests leave at step-chunk boundaries (the batch is
  * re-packed on the device).  Adjoint requests (forward rollout with checkpoints, then the reverse
  * pass for the loss L = (1/N) sum_i |x_i^T - x~_i|^2 with target positions x~, Sec. 4.1) run on
- * the second stream concurrently.  A served result is bitwise the result of the scene alone.
+ * the second stream concurrently.  The server steps without graphs (every step rebuilds), so a
+ * served result is bitwise the result of the scene alone with cells rebuilt every step.
  * Forward requests share the batch only with requests of the same dim, kernel, density mode,
  * diffusion form, shifting on or off, wall treatment, skin and rebuild_interval; one of another kind waits, in
  * arrival order, until the running batch has drained.

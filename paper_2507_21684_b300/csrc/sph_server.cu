@@ -8,8 +8,9 @@
 // while others run join at the next iteration boundary, finished ones leave, and the batch is
 // re-packed on the device (no round trip through the host).  Adjoint requests run on a second
 // stream and worker, so their work overlaps with the forward batch on the device.
-// Every scene's arithmetic is independent of the others in the batch, so a served result is
-// bitwise the result of running that scene alone.
+// Every scene's arithmetic is independent of the others in the batch and every step rebuilds the
+// cells, so a served result is bitwise the result of running that scene alone (with the cells
+// rebuilt every step).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
