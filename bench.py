@@ -36,8 +36,8 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 
 # Kernel sources whose change invalidates a stored ncu traffic figure.
-KERNEL_SOURCES = ("sph_device.cuh", "sph_tiles.cuh", "sph_passes.cuh", "sph_passes.cu", "sph_kernels.cuh",
-                  "sph_kernels.cu")
+KERNEL_SOURCES = ("sph_device.cuh", "sph_tiles.cuh", "sph_tilebuild.cuh", "sph_passes.cuh", "sph_passes.cu",
+                  "sph_kernels.cuh", "sph_kernels.cu")
 
 
 def kernel_fingerprint() -> str:
@@ -49,20 +49,21 @@ def kernel_fingerprint() -> str:
     return h.hexdigest()[:16]
 
 
-def stored_traffic(profile: str):
-    """DRAM bytes per launch from a committed ncu summary, or None when the kernel sources have
-    changed since that capture (the summary records their fingerprint)."""
+def stored_traffic(prefix: str, variant: str = "default"):
+    """DRAM bytes per launch from the committed ncu summary profiles/<prefix>*.md taken with the
+    same library variant (tile shape) and kernel sources (the summary records both), with the
+    summary's name; (None, None) when there is none."""
+    import glob
     import re
-    try:
-        with open(os.path.join(ROOT, "profiles", profile)) as fh:
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", prefix + "*.md"))):
+        with open(path) as fh:
             txt = fh.read()
-    except OSError:
-        return None
-    fp = re.search(r"fingerprint[^`]*`([0-9a-f]+)`", txt)
-    tb = re.search(r"DRAM bytes per launch \(read \+ write\): (\d+)", txt)
-    if not fp or not tb or fp.group(1) != kernel_fingerprint():
-        return None
-    return int(tb.group(1))
+        fp = re.search(r"fingerprint[^`]*`([0-9a-f]+)`", txt)
+        tb = re.search(r"DRAM bytes per launch \(read \+ write\): (\d+)", txt)
+        lv = re.search(r"Library variant[^`]*`(\w+)`", txt)
+        if fp and tb and fp.group(1) == kernel_fingerprint() and (lv.group(1) if lv else "default") == variant:
+            return int(tb.group(1)), "profiles/" + os.path.basename(path)
+    return None, None
 
 
 def hbm_view(alg_bytes: float, dram_bytes, ms: float, peak_gbs):
@@ -566,6 +567,7 @@ def main():
     if rank == 0 and ws == 1:
         cb = cpu_baseline(spec, budget_s=args.cpu_budget)
     if rank == 0:
+        traffic, traffic_src = stored_traffic("k_walls_sweep_t_dambreak_128", variant)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
@@ -577,8 +579,9 @@ def main():
             "roofline": {"bound": "alu", "kernel": "k_walls_sweep_t (wall pass + fused rates + kick-drift, one launch)",
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS,
-                         "traffic": stored_traffic("k_walls_sweep_t_dambreak_128.md"),
-                         "traffic_source": "profiles/k_walls_sweep_t_dambreak_128.md (ncu, cold caches, one launch)",
+                         "traffic": traffic,
+                         "traffic_source": (f"{traffic_src} (ncu, cold caches, one launch, library variant "
+                                            f"{variant})" if traffic_src else None),
                          "flops_per_pair": FLOPS_PER_PAIR[2], "pairs_per_launch": fw["pairs_per_step"],
                          "sweep_ms_avg": fw["sweep_ms"], "sweep_launches": fw["sweep_n"],
                          "peak_source": "148 SM x 128 FP32 lanes x 2 x 2.032 GHz (unit counts and max clock)"},
@@ -592,8 +595,7 @@ def main():
             # the same kernel against the memory roofline (it is not memory bound): algorithmic
             # bytes = the state read and written once (40 B per particle in 2D), and the DRAM
             # bytes of the committed ncu capture, over the kernel's mean time
-            "hbm_view": hbm_view(40.0 * spec["n_fluid"] + 40.0 * spec["n_wall"],
-                                 stored_traffic("k_walls_sweep_t_dambreak_128.md"), fw["sweep_ms"],
+            "hbm_view": hbm_view(40.0 * spec["n_fluid"] + 40.0 * spec["n_wall"], traffic, fw["sweep_ms"],
                                  peaks.get("hbm_gbs")),
         }
         print(json.dumps(line))

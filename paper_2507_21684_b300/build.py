@@ -13,17 +13,20 @@ LIB = HERE / "libsph_b300.so"
 SOURCES = ["sph_kernels.cu", "sph_passes.cu", "sph_runtime.cu", "sph_server.cu", "sph_noalloc.cu", "sph_rebuild.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Tile-shape variants of the library (targets per tile, threads per target, threads per CTA, staged
-# capacity, hit-list length, for 2D and 3D), timed against each other by tune.tune_tiles; "default"
-# is libsph_b300.so.
+# capacity, hit-list length, line cutting, for 2D and 3D), timed against each other by
+# tune.tune_tiles; "default" is libsph_b300.so.
 VARIANTS = {
     "default": {},
     "lanes8": {"SPH_TILE2_TP": 32, "SPH_TILE2_LANES": 8, "SPH_TILE2_LIST": 16,
                "SPH_TILE3_TP": 16, "SPH_TILE3_LANES": 16, "SPH_TILE3_LIST": 12},
     "lanes2": {"SPH_TILE2_TP": 128, "SPH_TILE2_LANES": 2, "SPH_TILE2_LIST": 40},
     "small": {"SPH_TILE2_TP": 32, "SPH_TILE2_LANES": 4, "SPH_TILE2_LIST": 24, "SPH_TILE2_THREADS": 128,
-              "SPH_TILE2_CAP": 512,
-              "SPH_TILE3_TP": 16, "SPH_TILE3_LANES": 8, "SPH_TILE3_LIST": 18, "SPH_TILE3_THREADS": 128,
-              "SPH_TILE3_CAP": 768},
+              "SPH_TILE2_CAP": 512},
+    "small3": {"SPH_TILE3_TP": 16, "SPH_TILE3_LANES": 8, "SPH_TILE3_LIST": 18, "SPH_TILE3_THREADS": 128,
+               "SPH_TILE3_CAP": 768},
+    # how lines are cut into tiles: whole cells in 2D, balanced tiles in 3D (the defaults swapped)
+    "cells2": {"SPH_TILE2_CUT": 0},
+    "balanced3": {"SPH_TILE3_CUT": 1},
 }
 
 

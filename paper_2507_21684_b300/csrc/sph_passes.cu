@@ -291,10 +291,12 @@ __device__ __forceinline__ double group_sum(double v) {
 
 // One tile of a pass: stage, gather per target, reduce, epilogue (or skip).  Returns the pairs
 // evaluated by this thread.  gate (fused wall + sweep kernel): the tile may read records that the
-// launch's wall tasks rewrite; unless all gate_n wall tasks had finished when the tile started,
-// a tile whose staged region holds a wall particle (or that falls back to global memory) waits
-// for them (bounded) and stages again, through L2 (COH).  A tile without a target of the pass
-// does not wait: the fused sweep's skip touches nothing.
+// launch's wall tasks rewrite; unless all gate_n wall tasks had finished when its records were
+// loaded, a tile whose staged region holds a wall particle waits for them (bounded) and loads its
+// wall particles again, through L2 (COH); one that falls back to global memory waits before it
+// reads any neighbour.  A tile without a target of the pass does not wait: the fused sweep's
+// skip touches nothing.  (Only wall records change: the fluid entries and the target cache, whose
+// wall targets the sweep does not use, stay valid.)
 template <int D, int E, int SELF, bool COH, class Pass>
 __device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileSmem<D, E>& sm,
                                          const float4* __restrict__ extra0, const float* __restrict__ extra1,
@@ -317,12 +319,12 @@ __device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileS
   // tiles without a target of this pass (walls only, fluid only) are skipped unstaged
   const bool want = valid && lane == 0 && Pass::wants(t.a.meta[i].x);
   int seen = 1;
-  int stg = stage_tile<D, E, COH>(sm, s, T, t.a, t.cell_off, extra0, extra1, want, gate ? &seen : nullptr);
+  const int stg = stage_tile<D, E, COH>(sm, s, T, t.a, t.cell_off, extra0, extra1, want, gate ? &seen : nullptr,
+                                        gate, gate_n, &s_ready);
   if (gate && !s_ready && (stg == 0 || (stg == 1 && seen))) {  // uniform over the CTA (barrier results)
     if (threadIdx.x == 0) gate_wait(gate, gate_n, t.status);
     __syncthreads();
-    fill_target_cache<D, COH>(sm.tc, t.a, pass.tex0(), pass.tex1(), T.p0, T.p1 - T.p0);
-    stg = stage_tile<D, E, COH>(sm, s, T, t.a, t.cell_off, extra0, extra1, want);
+    if (stg == 1) restage_walls<D, E>(sm, t.a, extra0, extra1);
   }
   const TgtView tv{sm.tc.view(), sm.tc.E0, sm.tc.E1, tgt};
   int np = 0;
@@ -1688,13 +1690,13 @@ struct OptAdj2Pass {
 };
 
 template <int D, int KERN>
-__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_opt_density(TravArgs t, const Tile* tiles, const int* ntiles, float4* S1) {
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_opt_density(TravArgs t, const Tile* tiles, const int* ntiles, float4* S1) {
   OptDensityPass<D, KERN> pass;
   pass.S1 = S1;
   run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
 template <int D, int KERN>
-__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_opt_color(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S1, float4* S2,
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_opt_color(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S1, float4* S2,
                                                  float* Lp, ShiftObjective o) {
   OptColorPass<D, KERN> pass;
   pass.S1 = S1;
@@ -1714,7 +1716,7 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, 512 / TileCfg<D>::THREADS
   run_tiles<D, 2, 0>(t, tiles, ntiles, S2, Vs, pass);
 }
 template <int D, int KERN, bool UPDATE>
-__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_opt_adj2(TravArgs t, const Tile* tiles, const int* ntiles, const float4* XB, float4* G,
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_opt_adj2(TravArgs t, const Tile* tiles, const int* ntiles, const float4* XB, float4* G,
                                                 Arrays out, float step) {
   OptAdj2Pass<D, KERN, UPDATE> pass;
   pass.XB = XB;
@@ -1806,7 +1808,7 @@ struct VarSupportPass {
 };
 
 template <int D, int KERN>
-__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_varsupport(TravArgs t, const Tile* tiles, const int* ntiles, const float4* Hs,
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_varsupport(TravArgs t, const Tile* tiles, const int* ntiles, const float4* Hs,
                                                     float4* out, float band) {
   VarSupportPass<D, KERN> pass;
   pass.a = t.a;
@@ -1847,7 +1849,7 @@ __global__ void k_unpermute3(int N, const uint2* __restrict__ meta, const int* _
 // ================================================================== kernels
 // The wall pass visits only the tiles that hold a wall particle (listed at each rebuild).
 template <int D, int KERN>
-__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_walls_t(TravArgs t, const Tile* tiles, const int* wall_tiles,
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_walls_t(TravArgs t, const Tile* tiles, const int* wall_tiles,
                                                  const int* n_wall_tiles) {
   WallPass<D, KERN> pass;
   pass.a = t.a;
@@ -1856,13 +1858,14 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREAD
 
 // List of the tiles holding at least one wall particle: one warp per tile.
 __global__ void k_wall_tiles(const Tile* __restrict__ tiles, const int* __restrict__ ntiles,
-                             const uint2* __restrict__ meta, int* __restrict__ list, int* __restrict__ count) {
+                             const uint2* __restrict__ meta, int* __restrict__ list, Tile* __restrict__ wall_t,
+                             Tile* __restrict__ fluid_t, int* __restrict__ count) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (w >= *ntiles) return;  // warp-uniform
-  if (tile_has_wall(tiles[w], lane, meta) && lane == 0) list[atomicAdd(count, 1)] = w;
+  list_tile(tiles[w], w, lane, meta, list, wall_t, fluid_t, count);
 }
 template <int D, int KERN>
-__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_density_t(TravArgs t, const Tile* tiles, const int* ntiles) {
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_density_t(TravArgs t, const Tile* tiles, const int* ntiles) {
   DensityPass<D, KERN> pass;
   pass.a = t.a;
   run_tiles<D, 0, 1>(t, tiles, ntiles, nullptr, nullptr, pass);
@@ -1872,8 +1875,8 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREAD
 // follow; a sweep tile whose staged region holds no wall particle runs at once, the others wait
 // for the wall tasks to finish (tile_task's gate).  Same results as the two launches.
 template <int D, int KERN>
-__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_walls_sweep_t(TravArgs t, const Tile* tiles, const int* ntiles,
-                                                 const int* wall_tiles, const int* n_wall_tiles, Arrays out, Displace disp) {
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_walls_sweep_t(TravArgs t, const Tile* wall_t,
+                                                 const Tile* fluid_t, const int* n_lists, Arrays out, Displace disp) {
   extern __shared__ __align__(16) unsigned char smraw[];
   TileSmem<D, 0>& sm = *reinterpret_cast<TileSmem<D, 0>*>(smraw);
   __shared__ int s_task;
@@ -1887,7 +1890,7 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREAD
   sp.status = t.status;
   sp.disp = disp;
   sp.grad = nullptr;
-  const int nw = *n_wall_tiles, nt = *ntiles;
+  const int nw = n_lists[0], nt = n_lists[1];
   unsigned* gate = reinterpret_cast<unsigned*>(t.tile_ctr + 2);
   long long pairs_cta = 0;
   while (true) {
@@ -1896,21 +1899,21 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREAD
     const int task = s_task;
     if (task >= nw + nt) break;
     if (task < nw) {
-      tile_task<D, 0, 0, false>(t, tiles[wall_tiles[task]], sm, nullptr, nullptr, wp);
+      tile_task<D, 0, 0, false>(t, wall_t[task], sm, nullptr, nullptr, wp);
       __syncthreads();  // every wall record of the tile is written
       if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(gate, 1u);
       }
     } else {
-      pairs_cta += tile_task<D, 0, 0, true>(t, tiles[task - nw], sm, nullptr, nullptr, sp, gate, (unsigned)nw);
+      pairs_cta += tile_task<D, 0, 0, true>(t, fluid_t[task - nw], sm, nullptr, nullptr, sp, gate, (unsigned)nw);
       __syncthreads();
     }
   }
   end_tiles(t, sp, pairs_cta);
 }
 template <int D, int KERN>
-__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_grad_t(TravArgs t, const Tile* tiles, const int* ntiles, float4* grad) {
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_grad_t(TravArgs t, const Tile* tiles, const int* ntiles, float4* grad) {
   GradPass<D, KERN> pass;
   pass.grad = grad;
   run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
@@ -1938,7 +1941,7 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, (D == 3 ? 768 : 1024) / T
   run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
 template <int D, bool VAR>
-__global__ void __launch_bounds__(TileCfg<D>::THREADS, 1024 / TileCfg<D>::THREADS) k_pairs_t(TravArgs t, const Tile* tiles, const int* ntiles, int32_t* pi,
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_pairs_t(TravArgs t, const Tile* tiles, const int* ntiles, int32_t* pi,
                                                  int32_t* pj, unsigned long long* count, long long cap) {
   PairPass<D, VAR> pass;
   pass.a = t.a;
@@ -2011,10 +2014,10 @@ void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, 
   cudaMemsetAsync(ntiles, 0, sizeof(int), st);
   if (n_lines > 0) k_tiles<D><<<(n_lines + 7) / 8, 256, 0, st>>>(segs, S, line_base, n_lines, cell_off, tiles, ntiles);
 }
-void launch_wall_tiles(const Tile* tiles, const int* ntiles, int tiles_upper, const uint2* meta, int* list, int* count,
-                       cudaStream_t st) {
-  cudaMemsetAsync(count, 0, sizeof(int), st);
-  k_wall_tiles<<<(tiles_upper + 7) / 8, 256, 0, st>>>(tiles, ntiles, meta, list, count);
+void launch_wall_tiles(const Tile* tiles, const int* ntiles, int tiles_upper, const uint2* meta, int* list,
+                       Tile* wall_t, Tile* fluid_t, int* count, cudaStream_t st) {
+  cudaMemsetAsync(count, 0, 2 * sizeof(int), st);
+  k_wall_tiles<<<(tiles_upper + 7) / 8, 256, 0, st>>>(tiles, ntiles, meta, list, wall_t, fluid_t, count);
 }
 
 template <int D, int KERN>
@@ -2035,11 +2038,10 @@ void launch_mdbc(const TravArgs& t, const Tile* tiles, const int* wall_tiles, co
   k_mdbc<D, KERN><<<grid, 256, 0, st>>>(t, tiles, wall_tiles, n_wall_tiles, ghost, orig_base);
 }
 template <int D, int KERN>
-void launch_walls_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, const int* wall_tiles,
-                          const int* n_wall_tiles, int tiles_upper, const Arrays& out, const Displace& disp,
-                          cudaStream_t st) {
+void launch_walls_sweep_t(const TravArgs& t, const Tile* wall_t, const Tile* fluid_t, const int* n_lists,
+                          int tiles_upper, const Arrays& out, const Displace& disp, cudaStream_t st) {
   k_walls_sweep_t<D, KERN><<<pass_grid((const void*)k_walls_sweep_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(
-      t, tiles, ntiles, wall_tiles, n_wall_tiles, out, disp);
+      t, wall_t, fluid_t, n_lists, out, disp);
 }
 template <int D, int KERN>
 void launch_grad_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, float4* grad,
@@ -2190,7 +2192,7 @@ SPH_INST_PD(3)
                                           const Arrays*, float, cudaStream_t);                                \
   template void launch_mdbc<D, K>(const TravArgs&, const Tile*, const int*, const int*, int, const float4*,  \
                                   const int*, cudaStream_t);                                                 \
-  template void launch_walls_sweep_t<D, K>(const TravArgs&, const Tile*, const int*, const int*, const int*, int, \
+  template void launch_walls_sweep_t<D, K>(const TravArgs&, const Tile*, const Tile*, const int*, int,           \
                                            const Arrays&, const Displace&, cudaStream_t);                    \
   template void launch_shift_t<D, K>(const TravArgs&, const Tile*, const int*, int, const Arrays&,          \
                                      const Displace&, cudaStream_t);                                         \

@@ -19,7 +19,9 @@ struct RebuildArgs {
   Tile* tiles;
   int* ntiles;
   int* wall_list;                  // tiles holding walls (or null)
-  int* nwall;
+  Tile* wall_tt;                   // copies of the tiles holding walls (with wall_list)
+  Tile* fluid_tt;                  // copies of the tiles holding fluid (with wall_list)
+  int* nwall;                      // the two lists' lengths
   const int* flag;                 // rebuild only when *flag != 0 (null: always)
   RebuildCtl* ctl;                 // rebuild counters (or null)
   unsigned* bar;                   // grid barrier words (two, zero at rest)

@@ -123,7 +123,7 @@ template <int D>
 __device__ bool rebuild_body(const RebuildArgs& r, RebuildSmem& sm) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *r.ntiles = 0;
-    if (r.nwall) *r.nwall = 0;
+    if (r.nwall) r.nwall[0] = r.nwall[1] = 0;
     if (r.ctl) {
       r.ctl->rebuilds += 1;
       r.ctl->call_rebuilds += 1;
@@ -168,7 +168,7 @@ __device__ bool rebuild_body(const RebuildArgs& r, RebuildSmem& sm) {
     if (!grid_barrier(r.bar, r.status)) return false;
     const int nt = *(volatile int*)r.ntiles;
     for (int w = warp; w < nt; w += nwarps)
-      if (tile_has_wall(r.tiles[w], lane, r.out.meta) && lane == 0) r.wall_list[atomicAdd(r.nwall, 1)] = w;
+      list_tile(r.tiles[w], w, lane, r.out.meta, r.wall_list, r.wall_tt, r.fluid_tt, r.nwall);
   }
   return true;
 }

@@ -324,8 +324,8 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
     line_base_h[s] = n_lines;
     n_lines += segs[s].n[1] * segs[s].n[2];
   }
-  // a tile is closed when it is full (TP particles), when its span would pass TP cells, or at
-  // an over-full cell: fewer than 3 N / TP + C_tot / TP + 2 n_lines tiles
+  // lines are cut into chunks of TP cells and each chunk into ceil(count / TP) tiles: at most
+  // N / TP + C_tot / TP + n_lines tiles (the bound below keeps a margin over that)
   {
     const int TP = D == 2 ? TileCfg<2>::TP : TileCfg<3>::TP;
     tiles_upper = 3 * ((N + TP - 1) / TP) + (C_tot + TP - 1) / TP + 2 * n_lines + 1;
@@ -377,6 +377,8 @@ void Scene::alloc_all() {
   tiles = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
   if (any_walls) {
     wall_tiles = (int*)mem.get(sizeof(int) * (size_t)tiles_upper);
+    wall_tt = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
+    fluid_tt = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
     d_nwall = (int*)mem.get(sizeof(int) * 2);
   }
   if (renorm) gradrho = (float4*)mem.get(sizeof(float4) * N);  // before any step is captured
@@ -543,7 +545,7 @@ void Scene::build_tiles(const int* off, const uint2* meta, Tile* tl, int* ntl) {
   CKL();
   ++launches;
   if (any_walls && meta) {
-    launch_wall_tiles(tl, ntl, tiles_upper, meta, wall_tiles, d_nwall, st);
+    launch_wall_tiles(tl, ntl, tiles_upper, meta, wall_tiles, wall_tt, fluid_tt, d_nwall, st);
     CKL();
     ++launches;
   }
@@ -665,11 +667,11 @@ void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const in
   const float4* g = renorm ? gradrho : nullptr;
   if (fused_walls) {
     if (D == 2) {
-      if (kern == 0) launch_walls_sweep_t<2, 0>(t, tl, ntl, wall_tiles, d_nwall, tiles_upper, out, dp, st);
-      else launch_walls_sweep_t<2, 1>(t, tl, ntl, wall_tiles, d_nwall, tiles_upper, out, dp, st);
+      if (kern == 0) launch_walls_sweep_t<2, 0>(t, wall_tt, fluid_tt, d_nwall, tiles_upper, out, dp, st);
+      else launch_walls_sweep_t<2, 1>(t, wall_tt, fluid_tt, d_nwall, tiles_upper, out, dp, st);
     } else {
-      if (kern == 0) launch_walls_sweep_t<3, 0>(t, tl, ntl, wall_tiles, d_nwall, tiles_upper, out, dp, st);
-      else launch_walls_sweep_t<3, 1>(t, tl, ntl, wall_tiles, d_nwall, tiles_upper, out, dp, st);
+      if (kern == 0) launch_walls_sweep_t<3, 0>(t, wall_tt, fluid_tt, d_nwall, tiles_upper, out, dp, st);
+      else launch_walls_sweep_t<3, 1>(t, wall_tt, fluid_tt, d_nwall, tiles_upper, out, dp, st);
     }
   } else if (D == 2) {
     if (kern == 0) launch_sweep_t<2, 0>(t, tl, ntl, tiles_upper, out, dp, g, st);
@@ -837,6 +839,8 @@ RebuildArgs Scene::coop_args(const Arrays& in, const Arrays& out, int* off, cons
   r.tiles = tiles;
   r.ntiles = d_ntiles;
   r.wall_list = any_walls ? wall_tiles : nullptr;
+  r.wall_tt = any_walls ? wall_tt : nullptr;
+  r.fluid_tt = any_walls ? fluid_tt : nullptr;
   r.nwall = any_walls ? d_nwall : nullptr;
   r.flag = flag;
   r.ctl = flag ? d_ctl : nullptr;

@@ -121,8 +121,10 @@ struct Scene {
   Tile* tiles = nullptr;
   int* d_ntiles = nullptr;
   int* d_tile_ctr = nullptr;   // dynamic tile counter (zeroed before each tiled launch)
-  int* wall_tiles = nullptr;   // tiles holding a wall particle (wall pass), and their count
-  int* d_nwall = nullptr;
+  int* wall_tiles = nullptr;   // tiles holding a wall particle (wall pass)
+  Tile* wall_tt = nullptr;     // copies of the tiles holding walls, and of those holding fluid: the
+  Tile* fluid_tt = nullptr;    // task lists of the fused wall + sweep launch
+  int* d_nwall = nullptr;      // the two lists' lengths
   int* d_status = nullptr;
   unsigned long long* d_pairs = nullptr;
   double* d_nubar = nullptr;

@@ -5,13 +5,21 @@
 
 namespace sph {
 
-// Tiles of one cell line are cut at cell boundaries, greedily from the left: a tile holds at
-// most TP particles and spans at most TP cells (so its column table fits); a cell with more
-// than TP particles is split into tiles of its own.  One warp per line: the lanes hold the
-// offsets of 32 consecutive cells, and each tile boundary is one ballot over them (the
-// conditions "count <= TP" and "span <= TP" are monotone along the line).  Finished tiles
-// wait in the registers of lane (k mod 32) and are written in batches of 32 at slots
-// reserved with one atomic; the order of the tiles in the table affects no result.
+// Tiles of one cell line, cut in one of two ways (TileCfg<D>::CUT):
+// - whole cells (0): greedily from the left, a tile holds at most TP particles and spans at most
+//   TP cells (so its column table fits); a cell with more than TP particles is split into tiles
+//   of its own.  One warp per line: the lanes hold the offsets of 32 consecutive cells, and each
+//   tile boundary is one ballot over them (the conditions "count <= TP" and "span <= TP" are
+//   monotone along the line).  Finished tiles wait in the registers of lane (k mod 32) and are
+//   written in batches of 32 at slots reserved with one atomic.
+// - balanced (1): the line is cut into chunks of TP cells, and the particles of each chunk into
+//   ceil(count / TP) tiles of equal size (+-1), cut between particles, not at cell boundaries:
+//   full tiles keep every thread of a CTA busy and a line needs ceil(count / TP) tiles, at the
+//   price of staging the cells around a cut twice.  One warp per line: lane j reads the bounds
+//   of chunk j (lines of up to 32 TP cells in one round trip), one atomic reserves the line's
+//   tiles, and each tile's first and last cell are found by binary search over its chunk.
+// Either way a tile's targets are one contiguous range of sorted particles whose cells lie in
+// [cx0, cx1], and the order of the tiles in the table affects no result.
 __device__ __forceinline__ int seg_of_line(const int* __restrict__ line_base, int S, int l) {
   int lo = 0, hi = S - 1;
   while (lo < hi) {
@@ -21,9 +29,63 @@ __device__ __forceinline__ int seg_of_line(const int* __restrict__ line_base, in
   return lo;
 }
 
-// Tiles of line l (one warp, all 32 lanes call it; lane = lane index).
+// Cell of particle p in cells [c0, c1) of a line (cell_off[first + c1] > p >= cell_off[first + c0]):
+// the largest c with cell_off[first + c] <= p.
+__device__ __forceinline__ int cell_of(const int* __restrict__ cell_off, int first, int c0, int c1, int p) {
+  int lo = c0, hi = c1 - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cell_off[first + mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Balanced tiles of line l (one warp, all 32 lanes call it; lane = lane index).
 template <int D>
-__device__ __forceinline__ void tiles_line(int l, int lane, const DevSeg* __restrict__ segs, int S,
+__device__ __forceinline__ void tiles_line_balanced(int l, int lane, const DevSeg* __restrict__ segs, int S,
+                                           const int* __restrict__ line_base, const int* __restrict__ cell_off,
+                                           Tile* __restrict__ tiles, int* __restrict__ ntiles) {
+  constexpr int TP = TileCfg<D>::TP;
+  const int sg = seg_of_line(line_base, S, l);
+  const DevSeg& s = segs[sg];
+  const int ll = l - line_base[sg];
+  const int nx = s.n[0];
+  const int first = s.cell_base + ll * nx;
+  const int cy = ll % s.n[1], cz = ll / s.n[1];
+  for (int w0 = 0; w0 < nx; w0 += 32 * TP) {  // windows of 32 chunks (warp-uniform)
+    const int c0 = min(w0 + lane * TP, nx), c1 = min(c0 + TP, nx);
+    int a = 0, cnt = 0;
+    if (c0 < nx) {
+      a = cell_off[first + c0];
+      cnt = cell_off[first + c1] - a;
+    }
+    const int n = (cnt + TP - 1) / TP;
+    int incl = n;  // tiles before this lane's chunk: exclusive scan over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) continue;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(ntiles, total);
+    base = __shfl_sync(kFull, base, 0) + incl - n;
+    for (int k = 0; k < n; ++k) {  // this lane's chunk (lanes with larger chunks run longer)
+      const int p0 = a + (int)((long long)cnt * k / n), p1 = a + (int)((long long)cnt * (k + 1) / n);
+      Tile T;
+      T.p0 = p0; T.p1 = p1; T.seg = sg; T.line = l;
+      T.cx0 = cell_of(cell_off, first, c0, c1, p0);
+      T.cx1 = cell_of(cell_off, first, c0, c1, p1 - 1);
+      T.cy = cy; T.cz = cz;
+      tiles[base + k] = T;
+    }
+  }
+}
+
+// Whole-cell tiles of line l (one warp, all 32 lanes call it; lane = lane index).
+template <int D>
+__device__ __forceinline__ void tiles_line_cells(int l, int lane, const DevSeg* __restrict__ segs, int S,
                                            const int* __restrict__ line_base, const int* __restrict__ cell_off,
                                            Tile* __restrict__ tiles, int* __restrict__ ntiles) {
   constexpr int TP = TileCfg<D>::TP;
@@ -116,11 +178,42 @@ __device__ __forceinline__ void tiles_line(int l, int lane, const DevSeg* __rest
 }
 
 
-// True (all lanes) when tile w holds a wall particle; one warp.
-__device__ __forceinline__ bool tile_has_wall(const Tile& T, int lane, const uint2* __restrict__ meta) {
-  bool wall = false;
-  for (int k = T.p0 + lane; k < T.p1; k += 32) wall |= (meta[k].x & kWallBit) != 0;
-  return __any_sync(kFull, wall);
+template <int D>
+__device__ __forceinline__ void tiles_line(int l, int lane, const DevSeg* __restrict__ segs, int S,
+                                           const int* __restrict__ line_base, const int* __restrict__ cell_off,
+                                           Tile* __restrict__ tiles, int* __restrict__ ntiles) {
+  if (TileCfg<D>::CUT)
+    tiles_line_balanced<D>(l, lane, segs, S, line_base, cell_off, tiles, ntiles);
+  else
+    tiles_line_cells<D>(l, lane, segs, S, line_base, cell_off, tiles, ntiles);
+}
+
+// What tile T holds (the same on all lanes; one warp): bit 0 a wall particle, bit 1 a fluid one.
+__device__ __forceinline__ unsigned tile_kinds(const Tile& T, int lane, const uint2* __restrict__ meta) {
+  bool wall = false, fluid = false;
+  for (int k = T.p0 + lane; k < T.p1; k += 32) {
+    const bool w = (meta[k].x & kWallBit) != 0;
+    wall |= w;
+    fluid |= !w;
+  }
+  return (__any_sync(kFull, wall) ? 1u : 0u) | (__any_sync(kFull, fluid) ? 2u : 0u);
+}
+// The task lists of a scene with walls (one warp per tile): tiles holding a wall particle
+// (list[0..count[0]) by index, for the wall pass, and wall_t[0..count[0]) as copies of the tiles)
+// and tiles holding a fluid particle (fluid_t[0..count[1]), copies), the two task lists of the
+// fused wall + sweep kernel: its sweep has nothing to do on tiles of walls alone, and a copy
+// saves the dependent load of the tile through its index.
+__device__ __forceinline__ void list_tile(const Tile& T, int w, int lane, const uint2* __restrict__ meta, int* list,
+                                          Tile* wall_t, Tile* fluid_t, int* count) {
+  const unsigned k = tile_kinds(T, lane, meta);
+  if (lane == 0) {
+    if (k & 1u) {
+      const int q = atomicAdd(count, 1);
+      list[q] = w;
+      wall_t[q] = T;
+    }
+    if (k & 2u) fluid_t[atomicAdd(count + 1, 1)] = T;
+  }
 }
 
 }  // namespace sph

@@ -44,17 +44,32 @@ struct Tile {
 #define SPH_TILE3_CAP 1024
 #endif
 
+// CUT: how cell lines are cut into tiles (0 whole cells, 1 balanced tiles cut between particles).
+#ifndef SPH_TILE2_CUT
+#define SPH_TILE2_CUT 1
+#endif
+#ifndef SPH_TILE3_CUT
+#define SPH_TILE3_CUT 0
+#endif
+// MINB: CTAs per SM the tiled kernels are compiled for (register budget 64K / (MINB x THREADS)).
+#ifndef SPH_TILE2_MINB
+#define SPH_TILE2_MINB (1024 / SPH_TILE2_THREADS)
+#endif
+#ifndef SPH_TILE3_MINB
+#define SPH_TILE3_MINB (1024 / SPH_TILE3_THREADS)
+#endif
+
 template <int D>
 struct TileCfg;
 template <>
 struct TileCfg<2> {
   static constexpr int TP = SPH_TILE2_TP, LANES = SPH_TILE2_LANES, THREADS = SPH_TILE2_THREADS, CAP = SPH_TILE2_CAP,
-                       LIST = SPH_TILE2_LIST, NL = 3;
+                       LIST = SPH_TILE2_LIST, NL = 3, MINB = SPH_TILE2_MINB, CUT = SPH_TILE2_CUT;
 };
 template <>
 struct TileCfg<3> {
   static constexpr int TP = SPH_TILE3_TP, LANES = SPH_TILE3_LANES, THREADS = SPH_TILE3_THREADS, CAP = SPH_TILE3_CAP,
-                       LIST = SPH_TILE3_LIST, NL = 9;
+                       LIST = SPH_TILE3_LIST, NL = 9, MINB = SPH_TILE3_MINB, CUT = SPH_TILE3_CUT;
 };
 
 // The records of a tile's own targets (a contiguous range of sorted particles), copied into
@@ -195,6 +210,32 @@ __device__ __forceinline__ int staged_run(const TileSmem<D, EXTRA>& sm, int k) {
   return r;
 }
 
+// Stage particle k of a tile whose run table is built: its records (with the run's periodic
+// shifts) and extras.  Returns whether it is a wall particle (mass <= 0).
+template <int D, int EXTRA, bool COH>
+__device__ __forceinline__ bool stage_record(TileSmem<D, EXTRA>& sm, const Arrays& a, int k,
+                                             const float4* __restrict__ extra0, const float* __restrict__ extra1) {
+  constexpr int CAP = TileCfg<D>::CAP;
+  const int r = staged_run(sm, k);
+  const int j = sm.run_g[r] + (k - sm.run_s[r]);
+  const int l = r / 3;
+  float4 A = ld_rec<COH>(a.A + j), B = ld_rec<COH>(a.B + j);
+  A.x += sm.run_sx[r];
+  A.y += sm.cshift[l][1];
+  if (D == 3) A.z += sm.cshift[l][2];
+  sm.A[k] = A;
+  sm.B[k] = B;
+  float m = B.w;
+  if (D == 3) {
+    const float2 C = ld_rec<COH>(a.C + j);
+    sm.C[k] = C;
+    m = C.y;
+  }
+  if (EXTRA > 0) sm.E[k] = __ldg(extra0 + j);
+  if (EXTRA > 1) sm.E[CAP + k] = make_float4(__ldg(extra1 + j), 0.f, 0.f, 0.f);
+  return m <= 0.f;
+}
+
 // Build the run table of a tile and stage its particles: two dependent global round trips (every
 // cell offset the tile needs, then the particle records).  The caller's cp.async copies into the
 // target cache are complete and visible after the first barrier.  Returns 1 when staged, 0 (fallback)
@@ -202,11 +243,14 @@ __device__ __forceinline__ int staged_run(const TileSmem<D, EXTRA>& sm, int k) {
 // thread passed want (no target of the pass in this tile: nothing is staged; the decision rides
 // on the first barrier, so it costs no extra round trip).  All threads of the CTA call it.
 // wall_seen (optional): set to whether any staged particle is a wall (mass <= 0).  COH: record
-// loads through L2 (see ld_rec).
+// loads through L2 (see ld_rec).  gate (optional): thread 0 reads *gate >= gate_n into *ready
+// (shared) just before the records are loaded, so that a set flag orders the loads after every
+// write that preceded the gate's last increment.
 template <int D, int EXTRA, bool COH = false>
 __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T, const Arrays& a,
                           const int* __restrict__ cell_off, const float4* __restrict__ extra0,
-                          const float* __restrict__ extra1, bool want, int* wall_seen = nullptr) {
+                          const float* __restrict__ extra1, bool want, int* wall_seen = nullptr,
+                          const unsigned* gate = nullptr, unsigned gate_n = 0, int* ready = nullptr) {
   constexpr int NL = TileCfg<D>::NL;
   constexpr int NCOL = TileSmem<D, EXTRA>::NCOL;
   constexpr int NRUN = TileSmem<D, EXTRA>::NRUN;
@@ -279,6 +323,10 @@ __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T
       sm.ncols = ncols;
       sm.colbase = colbase;
       sm.fallback = total > CAP;
+      if (gate && !*ready) {
+        *ready = *(volatile const unsigned*)gate >= gate_n;
+        __threadfence();
+      }
     }
   }
   __syncthreads();
@@ -298,31 +346,25 @@ __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T
     sm.colstart[l * NCOL + c] = v;
   }
   int walls = 0;
-  for (int k = tid; k < total; k += blockDim.x) {
-    const int r = staged_run(sm, k);
-    const int j = sm.run_g[r] + (k - sm.run_s[r]);
-    const int l = r / 3;
-    float4 A = ld_rec<COH>(a.A + j), B = ld_rec<COH>(a.B + j);
-    A.x += sm.run_sx[r];
-    A.y += sm.cshift[l][1];
-    if (D == 3) A.z += sm.cshift[l][2];
-    sm.A[k] = A;
-    sm.B[k] = B;
-    float m = B.w;
-    if (D == 3) {
-      const float2 C = ld_rec<COH>(a.C + j);
-      sm.C[k] = C;
-      m = C.y;
-    }
-    walls |= m <= 0.f;
-    if (EXTRA > 0) sm.E[k] = __ldg(extra0 + j);
-    if (EXTRA > 1) sm.E[CAP + k] = make_float4(__ldg(extra1 + j), 0.f, 0.f, 0.f);
-  }
+  for (int k = tid; k < total; k += blockDim.x) walls |= stage_record<D, EXTRA, COH>(sm, a, k, extra0, extra1);
   if (wall_seen)
     *wall_seen = __syncthreads_or(walls);
   else
     __syncthreads();
   return 1;
+}
+
+// Stage the wall particles of a staged tile again, through L2 (their records were rewritten
+// after the first staging); the fluid entries stay.  All threads of the CTA call it.
+template <int D, int EXTRA>
+__device__ void restage_walls(TileSmem<D, EXTRA>& sm, const Arrays& a, const float4* __restrict__ extra0,
+                              const float* __restrict__ extra1) {
+  const int total = sm.total;
+  for (int k = threadIdx.x; k < total; k += blockDim.x) {
+    const float m = D == 3 ? sm.C[k].y : sm.B[k].w;
+    if (m <= 0.f) stage_record<D, EXTRA, true>(sm, a, k, extra0, extra1);
+  }
+  __syncthreads();
 }
 
 // Global index of staged particle k (for predicates that exclude the target by index).

@@ -99,10 +99,17 @@ def time_variant(variant: str, spec: dict, steps: int = 100, warmup: int = 50, d
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def tune_tiles(spec: dict, variants=None, steps: int = 100, warmup: int = 50, device: int = 0) -> dict:
-    """Time every tile-shape variant on `spec`; the fastest one's name and the table."""
+def shape_variants(dim: int) -> list:
+    """The library variants whose tile shape differs for scenes of dimension `dim` (the default
+    first): a variant that only sets the other dimension's shape runs the default one."""
     from . import build
-    variants = list(build.VARIANTS) if variants is None else list(variants)
+    return [v for v, d in build.VARIANTS.items() if v == "default" or any(k.startswith(f"SPH_TILE{dim}_") for k in d)]
+
+
+def tune_tiles(spec: dict, variants=None, steps: int = 100, warmup: int = 50, device: int = 0) -> dict:
+    """Time every tile-shape variant for the scene's dimension on `spec`; the fastest one's name
+    and the table."""
+    variants = shape_variants(int(spec["params"]["dim"])) if variants is None else list(variants)
     table = []
     for v in variants:
         r = time_variant(v, spec, steps, warmup, device)

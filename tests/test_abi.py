@@ -55,3 +55,18 @@ def test_invalid_parameters_rejected_without_device(L):
     with pytest.raises(sph.SphError) as e:
         sph.Scene(p, s["n_fluid"], 0, s["x"], s["v"], s["rho"], s["mass"])
     assert e.value.code == sph.SPH_EINVAL
+
+
+def test_tile_tuner_candidates_per_dimension():
+    """The tuner times, for a scene, the default library and every variant that changes the tile
+    shape of the scene's dimension (a variant of the other dimension's shape would time the
+    default shape again)."""
+    from paper_2507_21684_b300 import build, tune
+    for dim in (2, 3):
+        c = tune.shape_variants(dim)
+        assert c[0] == "default" and len(set(c)) == len(c)
+        for v, d in build.VARIANTS.items():
+            if v != "default":
+                assert (v in c) == any(k.startswith(f"SPH_TILE{dim}_") for k in d)
+    assert "small" in tune.shape_variants(2) and "small" not in tune.shape_variants(3)
+    assert "small3" in tune.shape_variants(3) and "small3" not in tune.shape_variants(2)
