@@ -17,7 +17,8 @@ namespace sph {
 //   full tiles keep every thread of a CTA busy and a line needs ceil(count / TP) tiles, at the
 //   price of staging the cells around a cut twice.  One warp per line: lane j reads the bounds
 //   of chunk j (lines of up to 32 TP cells in one round trip), one atomic reserves the line's
-//   tiles, and each tile's first and last cell are found by binary search over its chunk.
+//   tiles, and the tiles are spread over the lanes, each finding its first and last cell by
+//   binary search over its chunk.
 // Either way a tile's targets are one contiguous range of sorted particles whose cells lie in
 // [cx0, cx1], and the order of the tiles in the table affects no result.
 __device__ __forceinline__ int seg_of_line(const int* __restrict__ line_base, int S, int l) {
@@ -70,15 +71,28 @@ __device__ __forceinline__ void tiles_line_balanced(int l, int lane, const DevSe
     if (total == 0) continue;
     int base = 0;
     if (lane == 0) base = atomicAdd(ntiles, total);
-    base = __shfl_sync(kFull, base, 0) + incl - n;
-    for (int k = 0; k < n; ++k) {  // this lane's chunk (lanes with larger chunks run longer)
-      const int p0 = a + (int)((long long)cnt * k / n), p1 = a + (int)((long long)cnt * (k + 1) / n);
-      Tile T;
-      T.p0 = p0; T.p1 = p1; T.seg = sg; T.line = l;
-      T.cx0 = cell_of(cell_off, first, c0, c1, p0);
-      T.cx1 = cell_of(cell_off, first, c0, c1, p1 - 1);
-      T.cy = cy; T.cz = cz;
-      tiles[base + k] = T;
+    base = __shfl_sync(kFull, base, 0);
+    // the window's tiles, 32 at a time over the lanes (one tile per lane and round): tile t lies
+    // in the chunk of the first lane whose inclusive count passes t
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int t = t0 + lane;
+      int j = 0;
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) j += __shfl_sync(kFull, incl, q) <= t;
+      j = min(j, 31);
+      const int ja = __shfl_sync(kFull, a, j), jcnt = __shfl_sync(kFull, cnt, j), jn = __shfl_sync(kFull, n, j);
+      const int jex = __shfl_sync(kFull, incl, j) - jn, jc0 = __shfl_sync(kFull, c0, j);
+      if (t < total) {
+        const int jc1 = min(jc0 + TP, nx);
+        const int k = t - jex;
+        const int p0 = ja + (int)((long long)jcnt * k / jn), p1 = ja + (int)((long long)jcnt * (k + 1) / jn);
+        Tile T;
+        T.p0 = p0; T.p1 = p1; T.seg = sg; T.line = l;
+        T.cx0 = cell_of(cell_off, first, jc0, jc1, p0);
+        T.cx1 = cell_of(cell_off, first, jc0, jc1, p1 - 1);
+        T.cy = cy; T.cz = cz;
+        tiles[base + t] = T;
+      }
     }
   }
 }
