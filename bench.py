@@ -66,15 +66,28 @@ def stored_traffic(prefix: str, variant: str = "default"):
     return None, None
 
 
-def hbm_view(alg_bytes: float, dram_bytes, ms: float, peak_gbs):
-    """A kernel's algorithmic and measured DRAM bandwidth against the measured HBM peak."""
+def stored_l2_bytes(source):
+    """L2 bytes per launch (32 B sectors, `lts__t_sectors.sum`) of the summary stored_traffic found."""
+    import re
+    if not source:
+        return None
+    with open(os.path.join(ROOT, source)) as fh:
+        m = re.search(r"`lts__t_sectors\.sum`\) \| ([0-9.]+)", fh.read())
+    return float(m.group(1)) * 32.0 if m else None
+
+
+def hbm_view(alg_bytes: float, dram_bytes, ms: float, peak_gbs, l2_bytes=None):
+    """A kernel's algorithmic, measured DRAM and measured L2 bandwidth (bytes of one ncu launch
+    over the kernel's mean time) against the measured HBM peak."""
     if not ms or ms <= 0:
         return None
     alg = alg_bytes / (ms * 1e-3) / 1e9
     dram = dram_bytes / (ms * 1e-3) / 1e9 if dram_bytes else None
-    return {"algorithmic_gbs": alg, "dram_gbs": dram, "peak_gbs": peak_gbs,
+    l2 = l2_bytes / (ms * 1e-3) / 1e9 if l2_bytes else None
+    return {"algorithmic_gbs": alg, "dram_gbs": dram, "l2_gbs": l2, "peak_gbs": peak_gbs,
             "algorithmic_frac": alg / peak_gbs if peak_gbs else None,
-            "dram_frac": dram / peak_gbs if (peak_gbs and dram) else None}
+            "dram_frac": dram / peak_gbs if (peak_gbs and dram) else None,
+            "l2_over_hbm_peak": l2 / peak_gbs if (peak_gbs and l2) else None}
 
 
 def replica_reduce(t_local: float, units_local: float, device: str = "cpu"):
@@ -478,6 +491,14 @@ def main():
             "sweep_ms": f3["sweep_ms"], "rebuild_ms": f3["rebuild_ms"],
             "sweep_fp32_tflops": FLOPS_PER_PAIR[3] * f3["pairs_per_step"] / (f3["sweep_ms"] / 1e3) / 1e12,
             "l2": "state 2M particles x 112 B > L2, no flush"}
+        # the 3D sweep against the memory roofline: 56 B per particle-step algorithmic, and the
+        # DRAM and L2 bytes of the committed capture taken with the same 3D tile shape
+        v3 = variant if variant in tune.shape_variants(3) else "default"
+        t3b, t3src = stored_traffic("k_sweep_t_tgv3d_128", v3)
+        extras["tgv3d_128"]["sweep_fp32_frac"] = extras["tgv3d_128"]["sweep_fp32_tflops"] / FP32_PEAK_TFLOPS
+        extras["tgv3d_128"]["hbm_view"] = hbm_view(56.0 * s3["n_fluid"], t3b, f3["sweep_ms"], peaks.get("hbm_gbs"),
+                                                   stored_l2_bytes(t3src))
+        extras["tgv3d_128"]["traffic_source"] = t3src
         # the same dam break with the renormalised delta-SPH diffusion (one more neighbour pass)
         sr = dict(si.dam_break(res=128, diffusion=1), params=dict(spec["params"], diffusion=1))
         fr = run_forward(sph, torch, sr, args.steps, args.warmup, True, torch.cuda.Stream())
@@ -596,7 +617,7 @@ def main():
             # bytes = the state read and written once (40 B per particle in 2D), and the DRAM
             # bytes of the committed ncu capture, over the kernel's mean time
             "hbm_view": hbm_view(40.0 * spec["n_fluid"] + 40.0 * spec["n_wall"], traffic, fw["sweep_ms"],
-                                 peaks.get("hbm_gbs")),
+                                 peaks.get("hbm_gbs"), stored_l2_bytes(traffic_src)),
         }
         print(json.dumps(line))
     if ws > 1:
