@@ -186,33 +186,50 @@ __device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s
       }
       for (int k0 = b + lane; k0 < en; k0 += 4 * Cfg::LANES) {
         if (cnt > Cfg::LIST - 4) drain();
+        if constexpr (D == 3 && SELF == 0) {
+          // branch-free in 3D (-1 % there, +1.5 % in 2D): every slot is tested (an index past the
+          // run is clamped to a valid one and rejected) and written at the list's end, which only
+          // a hit advances (cnt <= LIST - 4 here, so the four writes stay in the list); the list
+          // is the same as the branching form's
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int k = k0 + u * Cfg::LANES;
-          if (k < en) {
-            const float4 P = sm.A[k];
-            const float dx = tx - P.x, dy2 = ty - P.y;
-            float r2 = fmaf(dy2, dy2, dx * dx);
-            if (D == 3) {
-              const float dz2 = tz - P.z;
-              r2 = fmaf(dz2, dz2, r2);
-            }
-            bool in;
-            if (SELF == 2) {
-              in = r2 < s.band_hi;
-              if (in) {
-                const int gj = staged_gidx<D, E>(sm, k);
-                in = gj != i;
-                if (in && r2 >= s.band_lo) in = exact_pair<D>(s, a, i, gj);
+          for (int u = 0; u < 4; ++u) {
+            const int k = k0 + u * Cfg::LANES;
+            const int kc = min(k, en - 1);
+            const float4 P = sm.A[kc];
+            const float dx = tx - P.x, dy2 = ty - P.y, dz2 = tz - P.z;
+            const float r2 = fmaf(dz2, dz2, fmaf(dy2, dy2, dx * dx));
+            list[cnt * Cfg::THREADS] = (unsigned short)(kc | shift_bits);
+            cnt += (k < en && r2 < H2 && r2 > 0.f) ? 1 : 0;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int k = k0 + u * Cfg::LANES;
+            if (k < en) {
+              const float4 P = sm.A[k];
+              const float dx = tx - P.x, dy2 = ty - P.y;
+              float r2 = fmaf(dy2, dy2, dx * dx);
+              if (D == 3) {
+                const float dz2 = tz - P.z;
+                r2 = fmaf(dz2, dz2, r2);
               }
-            } else if (SELF == 1) {
-              in = r2 < H2 && (r2 > 0.f || staged_gidx<D, E>(sm, k) != i);
-            } else {
-              in = r2 < H2 && r2 > 0.f;
-            }
-            if (in) {
-              list[cnt * Cfg::THREADS] = (unsigned short)(k | shift_bits);
-              ++cnt;
+              bool in;
+              if (SELF == 2) {
+                in = r2 < s.band_hi;
+                if (in) {
+                  const int gj = staged_gidx<D, E>(sm, k);
+                  in = gj != i;
+                  if (in && r2 >= s.band_lo) in = exact_pair<D>(s, a, i, gj);
+                }
+              } else if (SELF == 1) {
+                in = r2 < H2 && (r2 > 0.f || staged_gidx<D, E>(sm, k) != i);
+              } else {
+                in = r2 < H2 && r2 > 0.f;
+              }
+              if (in) {
+                list[cnt * Cfg::THREADS] = (unsigned short)(k | shift_bits);
+                ++cnt;
+              }
             }
           }
         }
