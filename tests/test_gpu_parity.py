@@ -425,8 +425,9 @@ def test_device_inputs_match_host_inputs(sph):
 
 
 def _sparse_line_scene():
-    """Clusters of two particles every three cells along one cell line: a tile of 64 particles
-    spans more cells than the staged column table holds (global-memory fallback path)."""
+    """Clusters of two particles every three cells along one cell line: cut at whole cells, a tile
+    of 64 particles would span more cells than the staged column table holds (global-memory
+    fallback path); cut into balanced tiles, the chunks of TP cells bound the span."""
     H = 0.01
     p = params(H=H, dt=1e-4, box_lo=(0, 0), box_hi=(4, 0.1), periodic_mask=0b01, nu=0.01)
     xs = []
@@ -452,7 +453,26 @@ def _clump_scene():
     return scene(p, x, v=0.1 * rng.standard_normal(x.shape), rho=rho, mass=np.full(len(x), 1e-4))
 
 
-@pytest.mark.parametrize("maker", [_sparse_line_scene, _clump_scene])
+def _long_line_scene():
+    """Cell lines of 2500 cells (more than 32 chunks of TP cells: the balanced tiler's second
+    window), with a lattice strip, clusters straddling the chunk boundaries (multiples of 32 and
+    64 cells), an over-full cell of 150 particles and scattered particles."""
+    H = 0.01
+    p = params(H=H, dt=1e-4, box_lo=(0, 0), box_hi=(25, 0.05), periodic_mask=0b11, nu=0.01)
+    rng = np.random.default_rng(7)
+    parts = [np.stack([rng.uniform(0, 25, 1200), rng.uniform(0, 0.05, 1200)], 1)]
+    gx, gy = np.meshgrid(np.arange(0.0, 1.2, 0.25 * H), np.arange(0.0, 0.05, 0.25 * H))
+    parts.append(np.stack([gx.ravel() + 20.0, gy.ravel()], 1))
+    for c in (32, 64, 96, 128, 1024, 2048, 2080):
+        parts.append(np.stack([c * H + rng.uniform(-1.5 * H, 1.5 * H, 40), rng.uniform(0, 0.05, 40)], 1))
+    parts.append(np.stack([13.0 + rng.uniform(0, 0.9 * H, 150), 0.02 + rng.uniform(0, 0.9 * H, 150)], 1))
+    x = np.concatenate(parts)
+    v = rng.standard_normal(x.shape) * 0.1
+    rho = 1.0 + 0.01 * rng.standard_normal(len(x))
+    return scene(p, x, v=v, rho=rho, mass=np.full(len(x), H * H / 16))
+
+
+@pytest.mark.parametrize("maker", [_sparse_line_scene, _clump_scene, _long_line_scene])
 def test_fallback_tiles_match_oracle(sph, orc, maker):
     s = maker()
     with make(sph, s) as sc:
