@@ -360,8 +360,15 @@ def cpu_baseline(spec, budget_s: float = 15.0):
     t0 = time.perf_counter()
     oracle.rollout(spec, n)
     dt = time.perf_counter() - t0
+    # the same oracle on one core (a shorter sample: two steps)
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    oracle.rollout(spec, 2)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
     return dict(value=pairs_fluid * n / dt, unit=UNIT, cores=cores, kind="oracle",
-                sample=f"{spec['name']}: {n} FP64 steps from the initial state ({dt:.1f} s)")
+                sample=f"{spec['name']}: {n} FP64 steps from the initial state ({dt:.1f} s)",
+                value_1core=pairs_fluid * 2 / dt1, sample_1core=f"2 FP64 steps on one core ({dt1:.1f} s)")
 
 
 def main():
