@@ -353,22 +353,24 @@ def cpu_baseline(spec, budget_s: float = 15.0):
     nf = spec["n_fluid"]
     pairs = oracle.pairs(spec["params"], spec["x"])
     pairs_fluid = int((pairs[:, 0] < nf).sum())
+    oracle.rollout(spec, 2)  # first steps (thread start-up) untimed
     t0 = time.perf_counter()
-    oracle.rollout(spec, 2)
-    per = (time.perf_counter() - t0) / 2
-    n = max(2, min(2000, int(budget_s / max(per, 1e-6))))
+    oracle.rollout(spec, 8)
+    per = (time.perf_counter() - t0) / 8
+    n = max(2, min(4000, int(budget_s / max(per, 1e-6))))
     t0 = time.perf_counter()
     oracle.rollout(spec, n)
     dt = time.perf_counter() - t0
     # the same oracle on one core (a shorter sample: two steps)
     oracle.set_threads(1)
+    n1 = max(2, min(50, int(0.2 * budget_s / max(per * cores, 1e-6))))
     t1 = time.perf_counter()
-    oracle.rollout(spec, 2)
+    oracle.rollout(spec, n1)
     dt1 = time.perf_counter() - t1
     oracle.set_threads(cores)
     return dict(value=pairs_fluid * n / dt, unit=UNIT, cores=cores, kind="oracle",
                 sample=f"{spec['name']}: {n} FP64 steps from the initial state ({dt:.1f} s)",
-                value_1core=pairs_fluid * 2 / dt1, sample_1core=f"2 FP64 steps on one core ({dt1:.1f} s)")
+                value_1core=pairs_fluid * n1 / dt1, sample_1core=f"{n1} FP64 steps on one core ({dt1:.1f} s)")
 
 
 def main():

@@ -37,6 +37,29 @@ __device__ __noinline__ bool gate_wait(const unsigned* gate, unsigned n, int* st
   return true;
 }
 
+// Programmatic dependent launch: the step's first neighbour pass (density, gradient, sweep or
+// shift) is launched while the kernel before it (the cell rebuild launch, which allows it at its
+// start) still runs, and waits here, before its first memory access, until that kernel has
+// completed and its writes are visible.  Without the launch attribute it returns at once.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch configuration of a kernel that may start before the previous kernel in its stream has
+// finished (it calls wait_prior_grid first).
+struct PdlLaunch {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  PdlLaunch(int grid, int threads, size_t smem, cudaStream_t st) {
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+};
+
 // Test hook of the bounded waits: a gate that no task opens.
 __global__ void k_debug_gate(const unsigned* gate, int* status) {
   if (threadIdx.x == 0) gate_wait(gate, 1u, status);
@@ -1883,6 +1906,7 @@ __global__ void k_wall_tiles(const Tile* __restrict__ tiles, const int* __restri
 }
 template <int D, int KERN>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_density_t(TravArgs t, const Tile* tiles, const int* ntiles) {
+  wait_prior_grid();
   DensityPass<D, KERN> pass;
   pass.a = t.a;
   run_tiles<D, 0, 1>(t, tiles, ntiles, nullptr, nullptr, pass);
@@ -1894,6 +1918,7 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_densi
 template <int D, int KERN>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_walls_sweep_t(TravArgs t, const Tile* wall_t,
                                                  const Tile* fluid_t, const int* n_lists, Arrays out, Displace disp) {
+  wait_prior_grid();
   extern __shared__ __align__(16) unsigned char smraw[];
   TileSmem<D, 0>& sm = *reinterpret_cast<TileSmem<D, 0>*>(smraw);
   __shared__ int s_task;
@@ -1931,6 +1956,7 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_walls
 }
 template <int D, int KERN>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_grad_t(TravArgs t, const Tile* tiles, const int* ntiles, float4* grad) {
+  wait_prior_grid();
   GradPass<D, KERN> pass;
   pass.grad = grad;
   run_tiles<D, 0, 0>(t, tiles, ntiles, nullptr, nullptr, pass);
@@ -1939,6 +1965,7 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_grad_
 template <int D, int KERN, bool INTEGRATE, bool RENORM>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, (D == 3 && RENORM ? 768 : 1024) / TileCfg<D>::THREADS) k_sweep_t(TravArgs t, const Tile* tiles, const int* ntiles, Arrays out,
                                                  RateOut ro, Displace disp, const float4* grad) {
+  wait_prior_grid();
   SweepPass<D, KERN, INTEGRATE, RENORM> pass;
   pass.a = t.a;
   pass.out = out;
@@ -1951,6 +1978,7 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, (D == 3 && RENORM ? 768 :
 template <int D, int KERN>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, (D == 3 ? 768 : 1024) / TileCfg<D>::THREADS) k_shift_t(TravArgs t, const Tile* tiles, const int* ntiles, Arrays out,
                                                  Displace disp) {
+  wait_prior_grid();
   ShiftPass<D, KERN> pass;
   pass.a = t.a;
   pass.out = out;
@@ -2045,7 +2073,8 @@ void launch_walls_t(const TravArgs& t, const Tile* tiles, const int* wall_tiles,
 }
 template <int D, int KERN>
 void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st) {
-  k_density_t<D, KERN><<<pass_grid((const void*)k_density_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles);
+  PdlLaunch L(pass_grid((const void*)k_density_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st);
+  cudaLaunchKernelEx(&L.cfg, k_density_t<D, KERN>, t, tiles, ntiles);
 }
 template <int D, int KERN>
 void launch_mdbc(const TravArgs& t, const Tile* tiles, const int* wall_tiles, const int* n_wall_tiles, int tiles_upper,
@@ -2057,19 +2086,21 @@ void launch_mdbc(const TravArgs& t, const Tile* tiles, const int* wall_tiles, co
 template <int D, int KERN>
 void launch_walls_sweep_t(const TravArgs& t, const Tile* wall_t, const Tile* fluid_t, const int* n_lists,
                           int tiles_upper, const Arrays& out, const Displace& disp, cudaStream_t st) {
-  k_walls_sweep_t<D, KERN><<<pass_grid((const void*)k_walls_sweep_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(
-      t, wall_t, fluid_t, n_lists, out, disp);
+  PdlLaunch L(pass_grid((const void*)k_walls_sweep_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st);
+  cudaLaunchKernelEx(&L.cfg, k_walls_sweep_t<D, KERN>, t, wall_t, fluid_t, n_lists, out, disp);
 }
 template <int D, int KERN>
 void launch_grad_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, float4* grad,
                    cudaStream_t st) {
-  k_grad_t<D, KERN><<<pass_grid((const void*)k_grad_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, grad);
+  PdlLaunch L(pass_grid((const void*)k_grad_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st);
+  cudaLaunchKernelEx(&L.cfg, k_grad_t<D, KERN>, t, tiles, ntiles, grad);
 }
 template <int D, int KERN, bool INTEGRATE, bool RENORM>
 static void launch_sweep_any(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
                              const RateOut& ro, const Displace& disp, const float4* grad, cudaStream_t st) {
   auto fn = k_sweep_t<D, KERN, INTEGRATE, RENORM>;
-  fn<<<pass_grid((const void*)fn, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(RENORM ? 1 : 0), st>>>(t, tiles, ntiles, out, ro, disp, grad);
+  PdlLaunch L(pass_grid((const void*)fn, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(RENORM ? 1 : 0), st);
+  cudaLaunchKernelEx(&L.cfg, fn, t, tiles, ntiles, out, ro, disp, grad);
 }
 template <int D, int KERN>
 void launch_sweep_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
@@ -2086,7 +2117,8 @@ void launch_rates_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int
 template <int D, int KERN>
 void launch_shift_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
                     const Displace& disp, cudaStream_t st) {
-  k_shift_t<D, KERN><<<pass_grid((const void*)k_shift_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st>>>(t, tiles, ntiles, out, disp);
+  PdlLaunch L(pass_grid((const void*)k_shift_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st);
+  cudaLaunchKernelEx(&L.cfg, k_shift_t<D, KERN>, t, tiles, ntiles, out, disp);
 }
 template <int D>
 void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, int32_t* pi, int32_t* pj,

@@ -9,6 +9,9 @@ namespace {
 
 template <int D>
 __global__ void __launch_bounds__(kRbThreads) k_rebuild_coop(RebuildArgs r) {
+  // the next kernel (the sweep, launched as a programmatic dependent) may be scheduled at once:
+  // it waits for this grid's completion before its first memory access
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (r.flag && *(volatile const int*)r.flag == 0) return;  // no rebuild due: the whole grid leaves
   __shared__ RebuildSmem sm;
   rebuild_body<D>(r, sm);
