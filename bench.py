@@ -380,7 +380,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--profile-run", action="store_true",
                     help="forward steps of one workload only (for ncu): no extras, e2e or CPU leg")
     ap.add_argument("--workload", default="dambreak", choices=["dambreak", "tgv3d"])
