@@ -331,10 +331,10 @@ __device__ __forceinline__ double group_sum(double v) {
 
 // One tile of a pass: stage, gather per target, reduce, epilogue (or skip).  Returns the pairs
 // evaluated by this thread.  gate (fused wall + sweep kernel): the tile may read records that the
-// launch's wall tasks rewrite; unless all gate_n wall tasks had finished when its records were
-// loaded, a tile whose staged region holds a wall particle waits for them (bounded) and loads its
-// wall particles again, through L2 (COH); one that falls back to global memory waits before it
-// reads any neighbour.  A tile without a target of the pass does not wait: the fused sweep's
+// launch's wall tasks rewrite; unless all gate_n wall tasks had finished when the tile started
+// (an acquire load of the counter), a tile whose staged region holds a wall particle waits for
+// them (bounded) and loads its wall particles again, through L2 (COH); one that falls back to
+// global memory waits before it reads any neighbour.  A tile without a target of the pass does not wait: the fused sweep's
 // skip touches nothing.  (Only wall records change: the fluid entries and the target cache, whose
 // wall targets the sweep does not use, stay valid.)
 template <int D, int E, int SELF, bool COH, class Pass>
@@ -348,10 +348,7 @@ __device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileS
   const int lane = threadIdx.x % Cfg::LANES;
   const int i = T.p0 + tgt;
   const bool valid = i < T.p1;
-  if (gate && threadIdx.x == 0) {
-    s_ready = *(volatile const unsigned*)gate >= gate_n;
-    __threadfence();
-  }
+  if (gate && threadIdx.x == 0) s_ready = ld_acquire(gate) >= gate_n;
   // the targets' own records go to the cache while the neighbours are staged; the key and the
   // meta word (for the skip decision) are requested now so that their loads overlap too
   fill_target_cache<D, COH>(sm.tc, t.a, pass.tex0(), pass.tex1(), T.p0, T.p1 - T.p0);
@@ -359,8 +356,7 @@ __device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileS
   // tiles without a target of this pass (walls only, fluid only) are skipped unstaged
   const bool want = valid && lane == 0 && Pass::wants(t.a.meta[i].x);
   int seen = 1;
-  const int stg = stage_tile<D, E, COH>(sm, s, T, t.a, t.cell_off, extra0, extra1, want, gate ? &seen : nullptr,
-                                        gate, gate_n, &s_ready);
+  const int stg = stage_tile<D, E, COH>(sm, s, T, t.a, t.cell_off, extra0, extra1, want, gate ? &seen : nullptr);
   if (gate && !s_ready && (stg == 0 || (stg == 1 && seen))) {  // uniform over the CTA (barrier results)
     if (threadIdx.x == 0) gate_wait(gate, gate_n, t.status);
     __syncthreads();

@@ -110,6 +110,14 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Load with acquire semantics at GPU scope: the caller's later accesses (and, through a barrier,
+// its CTA's) see every write that preceded the release of the value read.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Record loads of the staging: through the read-only path, or (COH) through L2 only, for
 // records that another CTA of the same launch may have rewritten (the fused wall + sweep kernel).
 template <bool COH>
@@ -243,14 +251,11 @@ __device__ __forceinline__ bool stage_record(TileSmem<D, EXTRA>& sm, const Array
 // thread passed want (no target of the pass in this tile: nothing is staged; the decision rides
 // on the first barrier, so it costs no extra round trip).  All threads of the CTA call it.
 // wall_seen (optional): set to whether any staged particle is a wall (mass <= 0).  COH: record
-// loads through L2 (see ld_rec).  gate (optional): thread 0 reads *gate >= gate_n into *ready
-// (shared) just before the records are loaded, so that a set flag orders the loads after every
-// write that preceded the gate's last increment.
+// loads through L2 (see ld_rec).
 template <int D, int EXTRA, bool COH = false>
 __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T, const Arrays& a,
                           const int* __restrict__ cell_off, const float4* __restrict__ extra0,
-                          const float* __restrict__ extra1, bool want, int* wall_seen = nullptr,
-                          const unsigned* gate = nullptr, unsigned gate_n = 0, int* ready = nullptr) {
+                          const float* __restrict__ extra1, bool want, int* wall_seen = nullptr) {
   constexpr int NL = TileCfg<D>::NL;
   constexpr int NCOL = TileSmem<D, EXTRA>::NCOL;
   constexpr int NRUN = TileSmem<D, EXTRA>::NRUN;
@@ -323,10 +328,6 @@ __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T
       sm.ncols = ncols;
       sm.colbase = colbase;
       sm.fallback = total > CAP;
-      if (gate && !*ready) {
-        *ready = *(volatile const unsigned*)gate >= gate_n;
-        __threadfence();
-      }
     }
   }
   __syncthreads();
