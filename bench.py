@@ -383,7 +383,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--profile-run", action="store_true",
                     help="forward steps of one workload only (for ncu): no extras, e2e or CPU leg")
-    ap.add_argument("--workload", default="dambreak", choices=["dambreak", "tgv3d"])
+    ap.add_argument("--workload", default="dambreak", choices=["dambreak", "tgv3d", "adjoint"],
+                    help="--profile-run: dam break or 3D Taylor-Green forward steps, or the 128^2 adjoint "
+                         "(200-step rollout, checkpoints every 20, then the reverse pass; --steps reverse passes)")
     ap.add_argument("--eager", action="store_true",
                     help="--profile-run: launch kernels from the host (ncu cannot profile kernel nodes of graphs "
                          "with conditional nodes); the cells are then rebuilt every step")
@@ -410,6 +412,22 @@ def main():
         sph.select_variant(args.variant)
         sph.use_torch_allocator()
         from paper_2507_21684_b300 import tune
+        if args.workload == "adjoint":
+            sa = si.adjoint_problem(128)
+            sa = dict(sa, params=tune.with_skin(sa, args.skin or 0.0)["params"])
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                sc = sph.scene_from(sa, stream=stream.cuda_stream)
+            seed = np.full((sa["n_fluid"], 2), 1.0 / sa["n_fluid"], np.float32)
+            t0 = time.perf_counter()
+            for _ in range(max(1, args.steps)):
+                sc.rollout(200, 20)
+                sc.adjoint(seed, None, None)
+            torch.cuda.synchronize()
+            sc.close()
+            print(json.dumps({"profile_run": "adjoint", "skin_over_H": args.skin or 0.0, "passes": max(1, args.steps),
+                              "s_per_pass": (time.perf_counter() - t0) / max(1, args.steps)}))
+            return
         sp = (si.dam_break(res=128, diffusion=args.diffusion, boundary=args.boundary) if args.workload == "dambreak"
               else si.taylor_green_3d(128, seed=0, diffusion=args.diffusion))
         skin = args.skin if args.skin is not None else (0.02 if args.workload == "dambreak" else 0.0)
