@@ -41,11 +41,16 @@ KERNEL_SOURCES = ("sph_device.cuh", "sph_tiles.cuh", "sph_tilebuild.cuh", "sph_p
 
 
 def kernel_fingerprint() -> str:
+    """sha256 of the kernel sources with comments and blank lines removed (a comment edit leaves
+    the compiled kernels, and so a stored capture, as they were)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2507_21684_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2507_21684_b300", "csrc", f)) as fh:
+            txt = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in txt.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1907,10 +1907,11 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_densi
   pass.a = t.a;
   run_tiles<D, 0, 1>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
-// Wall pass and sweep in one launch: the wall tiles are the first tasks of the shared task counter
-// (so every wall task is held by a running CTA before any sweep task waits on it), the sweep tiles
-// follow; a sweep tile whose staged region holds no wall particle runs at once, the others wait
-// for the wall tasks to finish (tile_task's gate).  Same results as the two launches.
+// Wall pass and sweep in one launch: the tiles holding walls are the first tasks of the shared
+// task counter (so every wall task is held by a running CTA before any sweep task waits on it),
+// the tiles holding fluid follow (both lists hold copies of the tiles); a sweep tile whose staged
+// region holds no wall particle runs at once, the others wait for the wall tasks to finish
+// (tile_task's gate).  Same results as the two launches.
 template <int D, int KERN>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_walls_sweep_t(TravArgs t, const Tile* wall_t,
                                                  const Tile* fluid_t, const int* n_lists, Arrays out, Displace disp) {
