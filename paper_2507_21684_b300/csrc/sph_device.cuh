@@ -23,6 +23,31 @@
 
 namespace sph {
 
+// Programmatic dependent launch: a kernel launched with PdlLaunch may start while the kernel
+// before it in its stream still runs (the step's first neighbour pass after the cell rebuild
+// launch, which allows it at its start; the kernels of an adjoint step after one another); it
+// waits here, before its first memory access, until that kernel has completed and its writes are
+// visible.  Without the launch attribute it returns at once.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch configuration of a kernel that may start before the previous kernel in its stream has
+// finished (it calls wait_prior_grid first).
+struct PdlLaunch {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  PdlLaunch(int grid, int threads, size_t smem, cudaStream_t st) {
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+};
+
+
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint32_t kWallBit = 0x80000000u;
 

@@ -164,6 +164,8 @@ __global__ void k_download(int N, Arrays a, const int* __restrict__ orig_base, f
 template <int D>
 __global__ void k_adj_seed(const DevSeg* __restrict__ segs, int N, Arrays fw, const float4* __restrict__ XB,
                            const float4* __restrict__ VB, float4* __restrict__ S, float* __restrict__ Pp) {
+  wait_prior_grid();
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the next kernel of the adjoint step may launch
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const DevSeg& s = segs[fw.meta[k].y];
@@ -185,6 +187,8 @@ __global__ void k_adj_seed(const DevSeg* __restrict__ segs, int N, Arrays fw, co
 // Adjoint of the permutation of a rebuild: out[perm[k]] = in[k].
 __global__ void k_adj_unpermute(int N, const uint32_t* __restrict__ perm, const float4* __restrict__ XBin,
                                 const float4* __restrict__ VBin, float4* __restrict__ XBout, float4* __restrict__ VBout) {
+  wait_prior_grid();
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the next kernel of the adjoint step may launch
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   int d = (int)perm[k];
@@ -347,11 +351,17 @@ void launch_download(int N, const Arrays& a, const int* orig_base, float* x, flo
 template <int D>
 void launch_adj_seed(const DevSeg* segs, int N, const Arrays& fw, const float4* XB, const float4* VB, float4* S,
                      float* Pp, cudaStream_t st) {
-  if (N > 0) k_adj_seed<D><<<(N + 255) / 256, 256, 0, st>>>(segs, N, fw, XB, VB, S, Pp);
+  if (N > 0) {
+    PdlLaunch L((N + 255) / 256, 256, 0, st);
+    cudaLaunchKernelEx(&L.cfg, k_adj_seed<D>, segs, N, fw, XB, VB, S, Pp);
+  }
 }
 void launch_adj_unpermute(int N, const uint32_t* perm, const float4* XBin, const float4* VBin, float4* XBout,
                           float4* VBout, cudaStream_t st) {
-  if (N > 0) k_adj_unpermute<<<(N + 255) / 256, 256, 0, st>>>(N, perm, XBin, VBin, XBout, VBout);
+  if (N > 0) {
+    PdlLaunch L((N + 255) / 256, 256, 0, st);
+    cudaLaunchKernelEx(&L.cfg, k_adj_unpermute, N, perm, XBin, VBin, XBout, VBout);
+  }
 }
 template <int D>
 void launch_adj_load(int N, const uint2* meta, const int* orig_base, const float* xb, const float* vb, const float* rb,

@@ -37,29 +37,6 @@ __device__ __noinline__ bool gate_wait(const unsigned* gate, unsigned n, int* st
   return true;
 }
 
-// Programmatic dependent launch: the step's first neighbour pass (density, gradient, sweep or
-// shift) is launched while the kernel before it (the cell rebuild launch, which allows it at its
-// start) still runs, and waits here, before its first memory access, until that kernel has
-// completed and its writes are visible.  Without the launch attribute it returns at once.
-__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-// Launch configuration of a kernel that may start before the previous kernel in its stream has
-// finished (it calls wait_prior_grid first).
-struct PdlLaunch {
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  PdlLaunch(int grid, int threads, size_t smem, cudaStream_t st) {
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-  }
-};
-
 // Test hook of the bounded waits: a gate that no task opens.
 __global__ void k_debug_gate(const unsigned* gate, int* status) {
   if (threadIdx.x == 0) gate_wait(gate, 1u, status);
@@ -1997,6 +1974,8 @@ template <int D, int KERN>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, 512 / TileCfg<D>::THREADS) k_adj_t(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S,
                                                const float* Pp, const float4* XBin, const float4* VBin, float4* XBout,
                                                float4* VBout, float* nu_part) {
+  wait_prior_grid();
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the next kernel of the adjoint step may launch
   AdjPass<D, KERN> pass;
   pass.a = t.a;
   pass.S = S;
@@ -2011,6 +1990,8 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, 512 / TileCfg<D>::THREADS
 
 // Per-scene deterministic sums of per-particle float partials (block s sums scene s, fixed order).
 __global__ void k_sum_segments(const float* __restrict__ part, const DevSeg* __restrict__ segs, double* __restrict__ acc) {
+  wait_prior_grid();
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the next kernel of the adjoint step may launch
   __shared__ double sh[32];
   const DevSeg& s = segs[blockIdx.x];
   double v = 0.0;
@@ -2129,8 +2110,8 @@ template <int D, int KERN>
 void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* S,
                   const float* Pp, const float4* XBin, const float4* VBin, float4* XBout, float4* VBout,
                   float* nu_part, cudaStream_t st) {
-  k_adj_t<D, KERN><<<pass_grid((const void*)k_adj_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(D == 2 ? 1 : 2), st>>>(
-      t, tiles, ntiles, S, Pp, XBin, VBin, XBout, VBout, nu_part);
+  PdlLaunch L(pass_grid((const void*)k_adj_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(D == 2 ? 1 : 2), st);
+  cudaLaunchKernelEx(&L.cfg, k_adj_t<D, KERN>, t, tiles, ntiles, S, Pp, XBin, VBin, XBout, VBout, nu_part);
 }
 // Shifting-by-optimisation passes: the objective (P1, P2) and its gradient (P3, P4; with `out`, the
 // descent step).  Buffers: S1, S2, XB, G (float4 x N), V, Lp (N).
@@ -2168,7 +2149,8 @@ void launch_unpermute3(int N, const uint2* meta, const int* orig_base, const flo
   if (N > 0) k_unpermute3<<<(N + 255) / 256, 256, 0, st>>>(N, meta, orig_base, src, a, b, c);
 }
 void launch_sum_segments(const float* part, const DevSeg* segs, int S, double* acc, cudaStream_t st) {
-  k_sum_segments<<<S, 1024, 0, st>>>(part, segs, acc);
+  PdlLaunch L(S, 1024, 0, st);
+  cudaLaunchKernelEx(&L.cfg, k_sum_segments, part, segs, acc);
 }
 void launch_sum_float_partials(const float* part, int n, double* acc, cudaStream_t st) {
   k_sum_float_partials<<<1, 1024, 0, st>>>(part, n, acc);
