@@ -210,6 +210,7 @@ def run_forward(sph, torch, spec, steps, warmup, flush_l2: bool, stream, prof_st
     sc.timing(sph.TIMING_WALLS)
     sc.timing(sph.TIMING_GRADIENT)
     sc.timing(sph.TIMING_SHIFT)
+    sc.timing(sph.TIMING_DENSITY)
     for k in range(prof_steps):
         if flush:
             flush()
@@ -220,11 +221,13 @@ def run_forward(sph, torch, spec, steps, warmup, flush_l2: bool, stream, prof_st
     wall_ms, wall_n = sc.timing(sph.TIMING_WALLS)
     grad_ms, grad_n = sc.timing(sph.TIMING_GRADIENT)
     shift_ms, shift_n = sc.timing(sph.TIMING_SHIFT)
+    dens_ms, dens_n = sc.timing(sph.TIMING_DENSITY)
     sc.close()
     return dict(ms=ms, pairs_per_step=pairs_per_step, launches=st1["launches"] - st0["launches"],
                 rebuilds=st1["rebuilds"] - st0["rebuilds"], sweep_ms=sweep_ms / max(sweep_n, 1), sweep_n=sweep_n,
                 rebuild_ms=reb_ms / max(reb_n, 1), walls_ms=wall_ms / max(wall_n, 1),
-                gradient_ms=grad_ms / max(grad_n, 1), shift_ms=shift_ms / max(shift_n, 1))
+                gradient_ms=grad_ms / max(grad_n, 1), shift_ms=shift_ms / max(shift_n, 1),
+                density_ms=dens_ms / max(dens_n, 1))
 
 
 def run_e2e(sph, torch, spec, n_steps, reps):
@@ -560,6 +563,20 @@ def main():
             "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * tm / args.steps,
             "pair_interactions_per_s": fm["pairs_per_step"] * args.steps / tm,
             "sweep_ms": fm["sweep_ms"], "mdbc_walls_ms": fm["walls_ms"], "l2": "flushed between timed steps"}
+        # the dam break in summation mode: density sum of the fluid (a6), then the wall pass and
+        # the sweep
+        sd = dict(spec, params=dict(spec["params"], density_mode=1))
+        try:
+            fd = run_forward(sph, torch, sd, args.steps, args.warmup, True, torch.cuda.Stream())
+            td = sum(fd["ms"]) / 1e3
+            extras["dambreak_128_summation"] = {
+                "density": "summation (rho_i = sum_j m_j W_ij, compensated FP32 accumulation)",
+                "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * td / args.steps,
+                "pair_interactions_per_s": fd["pairs_per_step"] * args.steps / td,
+                "sweep_ms": fd["sweep_ms"], "density_ms": fd["density_ms"], "walls_ms": fd["walls_ms"],
+                "l2": "flushed between timed steps"}
+        except sph.SphError as e:  # the scene's own error (e.g. a density outside the stable band)
+            extras["dambreak_128_summation"] = {"error": str(e)}
         # shifting by optimisation at the paper's backward-cost size: 65,536 randomly sampled
         # particles, objective (2 passes) and its gradient (2 passes) per descent iteration
         so = si.shift_problem(256, seed=0)

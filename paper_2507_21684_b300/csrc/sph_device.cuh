@@ -163,6 +163,26 @@ __device__ __forceinline__ void store_cold(const Arrays& a, int i, const Cold& c
   }
 }
 
+// Compensated accumulation: hi + lo gathers the terms d with hi the rounded running sum and lo
+// the sum of the exact rounding errors (TwoSum; explicit roundings, never contracted).  For the
+// sums of non-negative kernel terms this is as accurate as an FP64 sum, in FP32 arithmetic.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float d) {
+  const float s = __fadd_rn(hi, d);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(d, bp));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+// (hi, lo) += (oh, ol): the same for a partial sum of another lane (exact error of the hi parts;
+// symmetric in its two operands, so a butterfly gives every lane the same result)
+__device__ __forceinline__ void two_sum_merge(float& hi, float& lo, float oh, float ol) {
+  const float s = __fadd_rn(hi, oh);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(oh, bp));
+  hi = s;
+  lo = __fadd_rn(__fadd_rn(lo, ol), e);
+}
+
 // hi + lo <- hi + lo + d  (TwoSum, then renormalise; explicit roundings, never contracted)
 __device__ __forceinline__ void ds_add(float& hi, float& lo, float d) {
   float s = __fadd_rn(hi, d);

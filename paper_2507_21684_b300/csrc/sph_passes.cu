@@ -676,14 +676,20 @@ struct DensityPass {
   struct Body {
     const DevSeg* s;
     float xi[D];
-    double rho;
+    float rh, rl;  // compensated FP32 sum (FP64 accuracy without FP64 arithmetic per pair)
     __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4, float, int) {
       float r[D];
       const float r2 = diff<D>(xs, pj.x, r);
-      rho += (double)(fabsf(pj.m) * (s->Kw * kern_w<KERN>(safe_q(r2, s->invH))));
+      two_sum_acc(rh, rl, fabsf(pj.m) * (s->Kw * kern_w<KERN>(safe_q(r2, s->invH))));
     }
     template <int L>
-    __device__ __forceinline__ void reduce() { rho = group_sum<L>(rho); }
+    __device__ __forceinline__ void reduce() {
+#pragma unroll
+      for (int o = L / 2; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(kFull, rh, o), ol = __shfl_xor_sync(kFull, rl, o);
+        two_sum_merge(rh, rl, oh, ol);
+      }
+    }
   };
   Arrays a;
   __device__ static __forceinline__ bool wants(uint32_t m) { return (m & kWallBit) == 0; }
@@ -694,7 +700,7 @@ struct DensityPass {
   __device__ __forceinline__ const float4* tex1() const { return nullptr; }
   __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView& tv) {
     b.s = &s;
-    b.rho = 0.0;
+    b.rh = b.rl = 0.f;
     const float4 A = tv.a.A[tv.k];
     b.xi[0] = A.x; b.xi[1] = A.y;
     if (D == 3) b.xi[2] = A.z;
@@ -703,7 +709,7 @@ struct DensityPass {
   __device__ __forceinline__ void finish(Body& b, const DevSeg& s, int i, const TgtView& tv) {
     if (tv.a.meta[tv.k].x & kWallBit) return;
     PD<D> me = load_pd_plain<D>(tv.a, tv.k);
-    const double rho = b.rho + (double)(me.m * s.Kw);  // self term, w(0) = 1
+    const double rho = ((double)b.rh + (double)b.rl) + (double)(me.m * s.Kw);  // self term, w(0) = 1
     const float e = (float)((rho - (double)s.rho0) / (double)s.rho0);
     me.rho = (float)rho;
     me.p = s.B * expm1f(s.gamma * log1pf(e));
