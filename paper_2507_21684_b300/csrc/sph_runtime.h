@@ -200,8 +200,9 @@ struct Scene {
                                           uint32_t* perm_out, int* off_out, Tile* tiles_out = nullptr,
                                           int* ntiles_out = nullptr);
   void build_tiles(const int* off, const uint2* meta, Tile* tl, int* ntl);
-  bool fuse_walls = true;           // wall pass inside the sweep launch (continuity, MC diffusion)
-  bool walls_in_sweep() const { return fuse_walls && any_walls && !summation && !renorm && !mdbc; }
+  bool fuse_walls = true;           // wall pass inside the sweep launch (Shepard walls, MC diffusion;
+                                    // in summation mode after the density launch)
+  bool walls_in_sweep() const { return fuse_walls && any_walls && !renorm && !mdbc; }
   // fused_walls: the sweep launch does the wall pass (walls_in_sweep()), so it is left out here
   void passes_before_sweep(const TravArgs& t, const Tile* tl = nullptr, const int* ntl = nullptr,
                            bool fused_walls = false);
