@@ -317,7 +317,8 @@ __device__ __forceinline__ double group_sum(double v) {
 template <int D, int E, int SELF, bool COH, class Pass>
 __device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileSmem<D, E>& sm,
                                          const float4* __restrict__ extra0, const float* __restrict__ extra1,
-                                         Pass& pass, const unsigned* gate = nullptr, unsigned gate_n = 0) {
+                                         Pass& pass, const unsigned* gate = nullptr, unsigned gate_n = 0,
+                                         uint4* plan = nullptr, int gate_ready = -1) {
   using Cfg = TileCfg<D>;
   __shared__ int s_ready;
   const DevSeg& s = t.segs[T.seg];
@@ -325,7 +326,9 @@ __device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileS
   const int lane = threadIdx.x % Cfg::LANES;
   const int i = T.p0 + tgt;
   const bool valid = i < T.p1;
-  if (gate && threadIdx.x == 0) s_ready = ld_acquire(gate) >= gate_n;
+  // (gate_ready: the caller's reading of the gate, taken before a barrier that precedes every load
+  // of this task; a plan's records are loaded without a barrier of their own before them)
+  if (gate && threadIdx.x == 0) s_ready = gate_ready >= 0 ? gate_ready : ld_acquire(gate) >= gate_n;
   // the targets' own records go to the cache while the neighbours are staged; the key and the
   // meta word (for the skip decision) are requested now so that their loads overlap too
   fill_target_cache<D, COH>(sm.tc, t.a, pass.tex0(), pass.tex1(), T.p0, T.p1 - T.p0);
@@ -333,7 +336,25 @@ __device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileS
   // tiles without a target of this pass (walls only, fluid only) are skipped unstaged
   const bool want = valid && lane == 0 && Pass::wants(t.a.meta[i].x);
   int seen = 1;
-  const int stg = stage_tile<D, E, COH>(sm, s, T, t.a, t.cell_off, extra0, extra1, want, gate ? &seen : nullptr);
+  int stg;
+  if (TilePlan<D>::CACHED && plan && sm.pvalid) {
+    // the staging table is the plan's (loaded with the tile): the records at once, then one
+    // barrier for the records, the target cache and the decisions
+    stg = 1;
+    if (sm.fallback) {
+      stg = 0;
+      cp_async_wait_all();
+    } else {
+      int walls = 0;
+      for (int k = threadIdx.x; k < sm.total; k += blockDim.x) walls |= stage_record<D, E, COH>(sm, t.a, k, extra0, extra1);
+      cp_async_wait_all();
+      seen = __syncthreads_or(walls);
+    }
+    if (!__syncthreads_or(want)) stg = -1;
+  } else {
+    stg = stage_tile<D, E, COH>(sm, s, T, t.a, t.cell_off, extra0, extra1, want, gate ? &seen : nullptr);
+    if (TilePlan<D>::CACHED && plan && stg == 1) store_plan(sm, plan);  // for the steps up to the next rebuild
+  }
   if (gate && !s_ready && (stg == 0 || (stg == 1 && seen))) {  // uniform over the CTA (barrier results)
     if (threadIdx.x == 0) gate_wait(gate, gate_n, t.status);
     __syncthreads();
@@ -1876,12 +1897,13 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_walls
 }
 
 // List of the tiles holding at least one wall particle: one warp per tile.
+template <int D>
 __global__ void k_wall_tiles(const Tile* __restrict__ tiles, const int* __restrict__ ntiles,
-                             const uint2* __restrict__ meta, int* __restrict__ list, Tile* __restrict__ wall_t,
-                             Tile* __restrict__ fluid_t, int* __restrict__ count) {
+                             const uint2* __restrict__ meta, int* __restrict__ list, uint4* __restrict__ wall_p,
+                             uint4* __restrict__ fluid_p, int* __restrict__ count) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (w >= *ntiles) return;  // warp-uniform
-  list_tile(tiles[w], w, lane, meta, list, wall_t, fluid_t, count);
+  list_tile<D>(tiles[w], w, lane, meta, list, wall_p, fluid_p, count);
 }
 template <int D, int KERN>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_density_t(TravArgs t, const Tile* tiles, const int* ntiles) {
@@ -1896,8 +1918,8 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_densi
 // region holds no wall particle runs at once, the others wait for the wall tasks to finish
 // (tile_task's gate).  Same results as the two launches.
 template <int D, int KERN>
-__global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_walls_sweep_t(TravArgs t, const Tile* wall_t,
-                                                 const Tile* fluid_t, const int* n_lists, Arrays out, Displace disp) {
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_walls_sweep_t(TravArgs t, uint4* wall_p,
+                                                 uint4* fluid_p, const int* n_lists, Arrays out, Displace disp) {
   wait_prior_grid();
   extern __shared__ __align__(16) unsigned char smraw[];
   TileSmem<D, 0>& sm = *reinterpret_cast<TileSmem<D, 0>*>(smraw);
@@ -1914,21 +1936,29 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_walls
   sp.grad = nullptr;
   const int nw = n_lists[0], nt = n_lists[1];
   unsigned* gate = reinterpret_cast<unsigned*>(t.tile_ctr + 2);
+  __shared__ int s_gate;
   long long pairs_cta = 0;
   while (true) {
-    if (threadIdx.x == 0) s_task = atomicAdd(t.tile_ctr, 1);
+    if (threadIdx.x == 0) {
+      s_task = atomicAdd(t.tile_ctr, 1);
+      s_gate = ld_acquire(gate) >= (unsigned)nw;  // before every load of the task (two barriers on)
+    }
     __syncthreads();
     const int task = s_task;
     if (task >= nw + nt) break;
+    uint4* plan = task < nw ? wall_p + (size_t)task * TilePlan<D>::U4 : fluid_p + (size_t)(task - nw) * TilePlan<D>::U4;
+    load_plan(sm, plan);
+    __syncthreads();
+    const Tile T = sm.ptile;
     if (task < nw) {
-      tile_task<D, 0, 0, false>(t, wall_t[task], sm, nullptr, nullptr, wp);
+      tile_task<D, 0, 0, false>(t, T, sm, nullptr, nullptr, wp, nullptr, 0, plan);
       __syncthreads();  // every wall record of the tile is written
       if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(gate, 1u);
       }
     } else {
-      pairs_cta += tile_task<D, 0, 0, true>(t, fluid_t[task - nw], sm, nullptr, nullptr, sp, gate, (unsigned)nw);
+      pairs_cta += tile_task<D, 0, 0, true>(t, T, sm, nullptr, nullptr, sp, gate, (unsigned)nw, plan, s_gate);
       __syncthreads();
     }
   }
@@ -2043,11 +2073,14 @@ void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, 
   cudaMemsetAsync(ntiles, 0, sizeof(int), st);
   if (n_lines > 0) k_tiles<D><<<(n_lines + 7) / 8, 256, 0, st>>>(segs, S, line_base, n_lines, cell_off, tiles, ntiles);
 }
+template <int D>
 void launch_wall_tiles(const Tile* tiles, const int* ntiles, int tiles_upper, const uint2* meta, int* list,
-                       Tile* wall_t, Tile* fluid_t, int* count, cudaStream_t st) {
+                       uint4* wall_p, uint4* fluid_p, int* count, cudaStream_t st) {
   cudaMemsetAsync(count, 0, 2 * sizeof(int), st);
-  k_wall_tiles<<<(tiles_upper + 7) / 8, 256, 0, st>>>(tiles, ntiles, meta, list, wall_t, fluid_t, count);
+  k_wall_tiles<D><<<(tiles_upper + 7) / 8, 256, 0, st>>>(tiles, ntiles, meta, list, wall_p, fluid_p, count);
 }
+template void launch_wall_tiles<2>(const Tile*, const int*, int, const uint2*, int*, uint4*, uint4*, int*, cudaStream_t);
+template void launch_wall_tiles<3>(const Tile*, const int*, int, const uint2*, int*, uint4*, uint4*, int*, cudaStream_t);
 
 template <int D, int KERN>
 void launch_walls_t(const TravArgs& t, const Tile* tiles, const int* wall_tiles, const int* n_wall_tiles,
@@ -2068,10 +2101,10 @@ void launch_mdbc(const TravArgs& t, const Tile* tiles, const int* wall_tiles, co
   k_mdbc<D, KERN><<<grid, 256, 0, st>>>(t, tiles, wall_tiles, n_wall_tiles, ghost, orig_base);
 }
 template <int D, int KERN>
-void launch_walls_sweep_t(const TravArgs& t, const Tile* wall_t, const Tile* fluid_t, const int* n_lists,
+void launch_walls_sweep_t(const TravArgs& t, uint4* wall_p, uint4* fluid_p, const int* n_lists,
                           int tiles_upper, const Arrays& out, const Displace& disp, cudaStream_t st) {
   PdlLaunch L(pass_grid((const void*)k_walls_sweep_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(0), st);
-  cudaLaunchKernelEx(&L.cfg, k_walls_sweep_t<D, KERN>, t, wall_t, fluid_t, n_lists, out, disp);
+  cudaLaunchKernelEx(&L.cfg, k_walls_sweep_t<D, KERN>, t, wall_p, fluid_p, n_lists, out, disp);
 }
 template <int D, int KERN>
 void launch_grad_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, float4* grad,
@@ -2226,7 +2259,7 @@ SPH_INST_PD(3)
                                           const Arrays*, float, cudaStream_t);                                \
   template void launch_mdbc<D, K>(const TravArgs&, const Tile*, const int*, const int*, int, const float4*,  \
                                   const int*, cudaStream_t);                                                 \
-  template void launch_walls_sweep_t<D, K>(const TravArgs&, const Tile*, const Tile*, const int*, int,           \
+  template void launch_walls_sweep_t<D, K>(const TravArgs&, uint4*, uint4*, const int*, int,                     \
                                            const Arrays&, const Displace&, cudaStream_t);                    \
   template void launch_shift_t<D, K>(const TravArgs&, const Tile*, const int*, int, const Arrays&,          \
                                      const Displace&, cudaStream_t);                                         \

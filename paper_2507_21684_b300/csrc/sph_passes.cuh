@@ -13,18 +13,20 @@ void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, 
 template <int D, int KERN>
 void launch_walls_t(const TravArgs& t, const Tile* tiles, const int* wall_tiles, const int* n_wall_tiles,
                     int tiles_upper, cudaStream_t st);
-// tiles holding walls into list (indices) and wall_t (copies), tiles holding fluid into fluid_t
-// (copies), the two counts into count[0..1]
+// tiles holding walls into list (indices) and wall_p (plans), tiles holding fluid into fluid_p
+// (plans), the two counts into count[0..1]
+template <int D>
 void launch_wall_tiles(const Tile* tiles, const int* ntiles, int tiles_upper, const uint2* meta, int* list,
-                       Tile* wall_t, Tile* fluid_t, int* count, cudaStream_t st);
+                       uint4* wall_p, uint4* fluid_p, int* count, cudaStream_t st);
 template <int D, int KERN>
 void launch_density_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, cudaStream_t st);
 template <int D, int KERN>
 void launch_mdbc(const TravArgs& t, const Tile* tiles, const int* wall_tiles, const int* n_wall_tiles, int tiles_upper,
                  const float4* ghost, const int* orig_base, cudaStream_t st);
-// wall tasks from wall_t, sweep tasks from fluid_t (tile copies; lengths n_lists[0], n_lists[1])
+// wall tasks from wall_p, sweep tasks from fluid_p (tile plans, TilePlan<D>::U4 words each;
+// lengths n_lists[0], n_lists[1]); the launch fills in the plans' staging tables
 template <int D, int KERN>
-void launch_walls_sweep_t(const TravArgs& t, const Tile* wall_t, const Tile* fluid_t, const int* n_lists,
+void launch_walls_sweep_t(const TravArgs& t, uint4* wall_p, uint4* fluid_p, const int* n_lists,
                           int tiles_upper, const Arrays& out, const Displace& disp, cudaStream_t st);
 template <int D, int KERN>
 void launch_grad_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, float4* grad,

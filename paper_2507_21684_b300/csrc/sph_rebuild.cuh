@@ -19,8 +19,8 @@ struct RebuildArgs {
   Tile* tiles;
   int* ntiles;
   int* wall_list;                  // tiles holding walls (or null)
-  Tile* wall_tt;                   // copies of the tiles holding walls (with wall_list)
-  Tile* fluid_tt;                  // copies of the tiles holding fluid (with wall_list)
+  uint4* wall_plans;               // plans of the tiles holding walls (with wall_list)
+  uint4* fluid_plans;              // plans of the tiles holding fluid (with wall_list)
   int* nwall;                      // the two lists' lengths
   const int* flag;                 // rebuild only when *flag != 0 (null: always)
   RebuildCtl* ctl;                 // rebuild counters (or null)

@@ -168,7 +168,7 @@ __device__ bool rebuild_body(const RebuildArgs& r, RebuildSmem& sm) {
     if (!grid_barrier(r.bar, r.status)) return false;
     const int nt = *(volatile int*)r.ntiles;
     for (int w = warp; w < nt; w += nwarps)
-      list_tile(r.tiles[w], w, lane, r.out.meta, r.wall_list, r.wall_tt, r.fluid_tt, r.nwall);
+      list_tile<D>(r.tiles[w], w, lane, r.out.meta, r.wall_list, r.wall_plans, r.fluid_plans, r.nwall);
   }
   return true;
 }

@@ -377,8 +377,15 @@ void Scene::alloc_all() {
   tiles = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
   if (any_walls) {
     wall_tiles = (int*)mem.get(sizeof(int) * (size_t)tiles_upper);
-    wall_tt = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
-    fluid_tt = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
+    // a plan per listed tile: the lists hold at most the tiles of the table, which balanced cuts
+    // bound by N / TP + cells / TP + lines
+    const int TPd = D == 2 ? TileCfg<2>::TP : TileCfg<3>::TP;
+    const bool balanced = D == 2 ? TileCfg<2>::CUT : TileCfg<3>::CUT;
+    const long long lu = balanced ? (long long)(N + TPd - 1) / TPd + (C_tot + TPd - 1) / TPd + n_lines + 1
+                                  : (long long)tiles_upper;
+    const size_t pw = (size_t)(D == 2 ? TilePlan<2>::U4 : TilePlan<3>::U4) * (size_t)std::min<long long>(lu, tiles_upper);
+    wall_plans = (uint4*)mem.get(sizeof(uint4) * pw);
+    fluid_plans = (uint4*)mem.get(sizeof(uint4) * pw);
     d_nwall = (int*)mem.get(sizeof(int) * 2);
   }
   if (renorm) gradrho = (float4*)mem.get(sizeof(float4) * N);  // before any step is captured
@@ -545,7 +552,10 @@ void Scene::build_tiles(const int* off, const uint2* meta, Tile* tl, int* ntl) {
   CKL();
   ++launches;
   if (any_walls && meta) {
-    launch_wall_tiles(tl, ntl, tiles_upper, meta, wall_tiles, wall_tt, fluid_tt, d_nwall, st);
+    if (D == 2)
+      launch_wall_tiles<2>(tl, ntl, tiles_upper, meta, wall_tiles, wall_plans, fluid_plans, d_nwall, st);
+    else
+      launch_wall_tiles<3>(tl, ntl, tiles_upper, meta, wall_tiles, wall_plans, fluid_plans, d_nwall, st);
     CKL();
     ++launches;
   }
@@ -667,11 +677,11 @@ void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const in
   const float4* g = renorm ? gradrho : nullptr;
   if (fused_walls) {
     if (D == 2) {
-      if (kern == 0) launch_walls_sweep_t<2, 0>(t, wall_tt, fluid_tt, d_nwall, tiles_upper, out, dp, st);
-      else launch_walls_sweep_t<2, 1>(t, wall_tt, fluid_tt, d_nwall, tiles_upper, out, dp, st);
+      if (kern == 0) launch_walls_sweep_t<2, 0>(t, wall_plans, fluid_plans, d_nwall, tiles_upper, out, dp, st);
+      else launch_walls_sweep_t<2, 1>(t, wall_plans, fluid_plans, d_nwall, tiles_upper, out, dp, st);
     } else {
-      if (kern == 0) launch_walls_sweep_t<3, 0>(t, wall_tt, fluid_tt, d_nwall, tiles_upper, out, dp, st);
-      else launch_walls_sweep_t<3, 1>(t, wall_tt, fluid_tt, d_nwall, tiles_upper, out, dp, st);
+      if (kern == 0) launch_walls_sweep_t<3, 0>(t, wall_plans, fluid_plans, d_nwall, tiles_upper, out, dp, st);
+      else launch_walls_sweep_t<3, 1>(t, wall_plans, fluid_plans, d_nwall, tiles_upper, out, dp, st);
     }
   } else if (D == 2) {
     if (kern == 0) launch_sweep_t<2, 0>(t, tl, ntl, tiles_upper, out, dp, g, st);
@@ -839,8 +849,8 @@ RebuildArgs Scene::coop_args(const Arrays& in, const Arrays& out, int* off, cons
   r.tiles = tiles;
   r.ntiles = d_ntiles;
   r.wall_list = any_walls ? wall_tiles : nullptr;
-  r.wall_tt = any_walls ? wall_tt : nullptr;
-  r.fluid_tt = any_walls ? fluid_tt : nullptr;
+  r.wall_plans = any_walls ? wall_plans : nullptr;
+  r.fluid_plans = any_walls ? fluid_plans : nullptr;
   r.nwall = any_walls ? d_nwall : nullptr;
   r.flag = flag;
   r.ctl = flag ? d_ctl : nullptr;

@@ -122,8 +122,8 @@ struct Scene {
   int* d_ntiles = nullptr;
   int* d_tile_ctr = nullptr;   // dynamic tile counter (zeroed before each tiled launch)
   int* wall_tiles = nullptr;   // tiles holding a wall particle (wall pass)
-  Tile* wall_tt = nullptr;     // copies of the tiles holding walls, and of those holding fluid: the
-  Tile* fluid_tt = nullptr;    // task lists of the fused wall + sweep launch
+  uint4* wall_plans = nullptr;  // plans of the tiles holding walls, and of those holding fluid: the
+  uint4* fluid_plans = nullptr; // task lists of the fused wall + sweep launch (TilePlan)
   int* d_nwall = nullptr;      // the two lists' lengths
   int* d_status = nullptr;
   unsigned long long* d_pairs = nullptr;

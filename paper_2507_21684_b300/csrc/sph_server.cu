@@ -37,9 +37,10 @@ static double now_s() {
 // state buffers, sort keys and values, cell offsets, tiles, staging and the build positions;
 // an adjoint adds its checkpoints, the tape slots (state, keys, permutation, offsets, tiles)
 // and the adjoint work arrays.
-static size_t request_bytes(const sph_params& p, int n, int steps, int mode, int ckpt) {
+static size_t request_bytes(const sph_params& p, int n, int nw, int steps, int mode, int ckpt) {
   const size_t per = p.dim == 2 ? 256 : 320;
   size_t b = (size_t)n * per + (1 << 20);
+  if (nw > 0) b += (size_t)n * (p.dim == 2 ? 80 : 8);  // the fused wall + sweep launch's tile plans
   if (p.diffusion == SPH_DIFFUSION_RENORM && p.density_mode == SPH_DENSITY_CONTINUITY) b += (size_t)n * 16;
   if (mode == SPH_REQ_ADJOINT) {
     const size_t rec = p.dim == 2 ? 72 : 96;  // one copy of the records
@@ -412,7 +413,7 @@ int sph_submit(sph_server* sv, const sph_request* rq, uint64_t* ticket) {
   r->n_steps = rq->n_steps;
   r->mode = rq->mode;
   r->ckpt = rq->ckpt_every > 0 ? rq->ckpt_every : 20;
-  r->bytes = sph::request_bytes(rq->params, r->n, r->n_steps, r->mode, r->ckpt);
+  r->bytes = sph::request_bytes(rq->params, r->n, r->nw, r->n_steps, r->mode, r->ckpt);
   if (r->bytes > s.budget) {
     sph::set_err("sph_submit: the request alone exceeds the HBM budget");
     return SPH_EINVAL;

@@ -213,20 +213,27 @@ __device__ __forceinline__ unsigned tile_kinds(const Tile& T, int lane, const ui
   return (__any_sync(kFull, wall) ? 1u : 0u) | (__any_sync(kFull, fluid) ? 2u : 0u);
 }
 // The task lists of a scene with walls (one warp per tile): tiles holding a wall particle
-// (list[0..count[0]) by index, for the wall pass, and wall_t[0..count[0]) as copies of the tiles)
-// and tiles holding a fluid particle (fluid_t[0..count[1]), copies), the two task lists of the
-// fused wall + sweep kernel: its sweep has nothing to do on tiles of walls alone, and a copy
-// saves the dependent load of the tile through its index.
+// (list[0..count[0]) by index, for the wall pass, and wall_p[0..count[0]) as plans) and tiles
+// holding a fluid particle (fluid_p[0..count[1]), plans): the two task lists of the fused wall +
+// sweep kernel, whose sweep has nothing to do on tiles of walls alone.  A plan starts as the tile
+// with its flag cleared; the fused kernel fills in the staging table the first time it stages it.
+template <int D>
 __device__ __forceinline__ void list_tile(const Tile& T, int w, int lane, const uint2* __restrict__ meta, int* list,
-                                          Tile* wall_t, Tile* fluid_t, int* count) {
+                                          uint4* wall_p, uint4* fluid_p, int* count) {
   const unsigned k = tile_kinds(T, lane, meta);
   if (lane == 0) {
     if (k & 1u) {
       const int q = atomicAdd(count, 1);
       list[q] = w;
-      wall_t[q] = T;
+      uint4* b = wall_p + (size_t)q * TilePlan<D>::U4;
+      *reinterpret_cast<Tile*>(b) = T;
+      reinterpret_cast<int*>(b + 2)[0] = 0;
     }
-    if (k & 2u) fluid_t[atomicAdd(count + 1, 1)] = T;
+    if (k & 2u) {
+      uint4* b = fluid_p + (size_t)atomicAdd(count + 1, 1) * TilePlan<D>::U4;
+      *reinterpret_cast<Tile*>(b) = T;
+      reinterpret_cast<int*>(b + 2)[0] = 0;
+    }
   }
 }
 

@@ -10,6 +10,8 @@
 // of the LANES threads are then combined with shuffles.  Tiles whose staged region would not fit
 // fall back to the warp traversal on global memory.
 #pragma once
+#include <cstddef>
+
 #include "sph_device.cuh"
 
 namespace sph {
@@ -171,8 +173,11 @@ struct TileSmem {
   float2 C[D == 3 ? CAP : 1];
   float4 E[EXTRA > 0 ? EXTRA * CAP : 1];
   TargetCache<D> tc;
-  int colstart[NL * NCOL + 1];      // staged index of each (line, column) cell start
   unsigned short list[TileCfg<D>::LIST * TileCfg<D>::THREADS];
+  // From here to img: a tile's staging plan (TilePlan), which depends on the cell structure only
+  alignas(16) Tile ptile;           // the tile
+  int pvalid, ppad[3];              // whether the rest of the plan (the staging table) is filled
+  int colstart[NL * NCOL + 1];      // staged index of each (line, column) cell start
   int run_g[NRUN];                  // global start of each run
   int run_n[NRUN];                  // length of each run
   int run_s[NRUN + 1];              // staged start of each run (exclusive scan)
@@ -186,6 +191,36 @@ struct TileSmem {
 
 template <int D, int EXTRA>
 constexpr size_t tile_smem_bytes() { return sizeof(TileSmem<D, EXTRA>); }
+
+// A tile's staging plan in global memory, as uint4 words laid out like TileSmem from ptile to img:
+// the tile, a flag, and the staging table (column starts as staged indices, the run table and the
+// periodic shifts).  The table depends only on the cell structure, so the fused wall + sweep
+// launch keeps it from the step after a rebuild to the next rebuild, and a tile then starts
+// with one load of its plan instead of its cell offsets and a run-table scan.  Kept in 2D (the
+// plans of 3D tiles would outweigh their particles' state); a 3D plan is the tile and the flag.
+template <int D>
+struct TilePlan {
+  using SM = TileSmem<D, 0>;
+  static constexpr bool CACHED = D == 2;
+  static constexpr size_t BEGIN = offsetof(SM, ptile);
+  static constexpr size_t END = offsetof(SM, img) + sizeof(int) * 4 * TileCfg<D>::NL;
+  static constexpr int U4 = CACHED ? (int)((END - BEGIN + 15) / 16) : 3;
+  static_assert(BEGIN % 16 == 0, "the plan is copied as uint4 words");
+};
+
+// Copy of a plan (U4 words from the tile on) into the CTA's shared memory (all threads).
+template <int D, int EXTRA>
+__device__ __forceinline__ void load_plan(TileSmem<D, EXTRA>& sm, const uint4* __restrict__ plan) {
+  uint4* dst = reinterpret_cast<uint4*>(&sm.ptile);
+  for (int e = threadIdx.x; e < TilePlan<D>::U4; e += blockDim.x) dst[e] = plan[e];
+}
+// The staging table of a staged tile into its plan, and the flag (all threads; read by later launches).
+template <int D, int EXTRA>
+__device__ __forceinline__ void store_plan(const TileSmem<D, EXTRA>& sm, uint4* __restrict__ plan) {
+  const uint4* src = reinterpret_cast<const uint4*>(&sm.ptile);
+  for (int e = 3 + threadIdx.x; e < TilePlan<D>::U4; e += blockDim.x) plan[e] = src[e];
+  if (threadIdx.x == 0) reinterpret_cast<int*>(plan + 2)[0] = 1;
+}
 
 // Geometry of staged line l of a tile: global cell id of its column 0 (-1 when the line lies
 // outside a closed box), the target shift (upper periodic image: +L) and the candidate shift
@@ -242,6 +277,20 @@ __device__ __forceinline__ bool stage_record(TileSmem<D, EXTRA>& sm, const Array
   if (EXTRA > 0) sm.E[k] = __ldg(extra0 + j);
   if (EXTRA > 1) sm.E[CAP + k] = make_float4(__ldg(extra1 + j), 0.f, 0.f, 0.f);
   return m <= 0.f;
+}
+
+// Stage the records of a tile whose staging table is in shared memory (all threads); returns 1.
+template <int D, int EXTRA, bool COH>
+__device__ __forceinline__ int stage_records(TileSmem<D, EXTRA>& sm, const Arrays& a, int total,
+                                             const float4* __restrict__ extra0, const float* __restrict__ extra1,
+                                             int* wall_seen) {
+  int walls = 0;
+  for (int k = threadIdx.x; k < total; k += blockDim.x) walls |= stage_record<D, EXTRA, COH>(sm, a, k, extra0, extra1);
+  if (wall_seen)
+    *wall_seen = __syncthreads_or(walls);
+  else
+    __syncthreads();
+  return 1;
 }
 
 // Build the run table of a tile and stage its particles: two dependent global round trips (every
@@ -346,13 +395,7 @@ __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T
     if (sm.linecell[l] < 0) v = sm.run_s[3 * l + 0];
     sm.colstart[l * NCOL + c] = v;
   }
-  int walls = 0;
-  for (int k = tid; k < total; k += blockDim.x) walls |= stage_record<D, EXTRA, COH>(sm, a, k, extra0, extra1);
-  if (wall_seen)
-    *wall_seen = __syncthreads_or(walls);
-  else
-    __syncthreads();
-  return 1;
+  return stage_records<D, EXTRA, COH>(sm, a, total, extra0, extra1, wall_seen);
 }
 
 // Stage the wall particles of a staged tile again, through L2 (their records were rewritten
