@@ -554,47 +554,70 @@ __global__ void __launch_bounds__(256) k_mdbc(TravArgs t, const Tile* __restrict
       float acc[NS];
 #pragma unroll
       for (int e = 0; e < NS; ++e) acc[e] = 0.f;
-      const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
-      for (int oz = zlo; oz <= zhi; ++oz)
-        for (int oy = -1; oy <= 1; ++oy)
-          for (int ox = -1; ox <= 1; ++ox) {
-            int cc[3] = {c[0] + ox, c[1] + oy, c[2] + oz};
-            bool skip = false;
+      // the 3^d cells around the ghost node in one round trip: lane k < NC holds cell k's first
+      // particle and count; the warp then walks their concatenation, 32 candidates per round
+      constexpr int NC = D == 3 ? 27 : 9;
+      int cfirst = 0, ccount = 0;
+      if (lane < NC) {
+        int cc[3] = {c[0] + lane % 3 - 1, c[1] + (lane / 3) % 3 - 1, c[2] + (D == 3 ? lane / 9 - 1 : 0)};
+        bool skip = false;
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-              if (cc[k] < 0 || cc[k] >= s.n[k]) {
-                if (!((s.periodic_mask >> k) & 1)) skip = true;
-                cc[k] = (cc[k] + s.n[k]) % s.n[k];
-              }
-            }
-            if (skip) continue;
-            const int cell = s.cell_base + (cc[2] * s.n[1] + cc[1]) * s.n[0] + cc[0];
-            const int j1 = t.cell_off[cell + 1];
-            for (int j = t.cell_off[cell] + lane; j < j1; j += 32) {
-              const PD<D> pj = load_pd<D>(t.a, j);
-              if (!(pj.m > 0.f)) continue;  // fluid only
-              float r[D];
-              const float r2 = separation<D>(s, xg, pj.x, r);  // x_g - x_j
-              if (!(r2 < s.H2)) continue;
-              const float q = safe_q(r2, s.invH);
-              const float VW = pj.V * (s.Kw * kern_w<KERN>(q));
-              const float VgH = pj.V * (s.Kg * kern_gt<KERN>(q)) * s.H;  // V grad W / r, times H
-              acc[0] += VW;
-#pragma unroll
-              for (int l = 0; l < D; ++l) acc[1 + l] = fmaf(-VW * s.invH, r[l], acc[1 + l]);
-#pragma unroll
-              for (int k = 0; k < D; ++k) {
-                acc[(1 + k) * N] = fmaf(VgH, r[k], acc[(1 + k) * N]);
-#pragma unroll
-                for (int l = 0; l < D; ++l)
-                  acc[(1 + k) * N + 1 + l] = fmaf(-VgH * s.invH * r[k], r[l], acc[(1 + k) * N + 1 + l]);
-              }
-              const float qj = pj.rho - s.rho0;
-              acc[N * N] = fmaf(VW, qj, acc[N * N]);
-#pragma unroll
-              for (int k = 0; k < D; ++k) acc[N * N + 1 + k] = fmaf(VgH * qj, r[k], acc[N * N + 1 + k]);
-            }
+        for (int k = 0; k < D; ++k) {
+          if (cc[k] < 0 || cc[k] >= s.n[k]) {
+            if (!((s.periodic_mask >> k) & 1)) skip = true;
+            cc[k] = (cc[k] + s.n[k]) % s.n[k];
           }
+        }
+        if (!skip) {
+          const int cell = s.cell_base + (cc[2] * s.n[1] + cc[1]) * s.n[0] + cc[0];
+          cfirst = t.cell_off[cell];
+          ccount = t.cell_off[cell + 1] - cfirst;
+        }
+      }
+      int incl = ccount;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      int ex[NC], fi[NC], nn[NC];  // every lane: each cell's offset in the walk, first particle, count
+#pragma unroll
+      for (int b = 0; b < NC; ++b) {
+        nn[b] = __shfl_sync(kFull, ccount, b);
+        ex[b] = __shfl_sync(kFull, incl, b) - nn[b];
+        fi[b] = __shfl_sync(kFull, cfirst, b);
+      }
+      for (int base = 0; base < total; base += 32) {
+        const int idx = base + lane;
+        int j = -1;
+#pragma unroll
+        for (int b = 0; b < NC; ++b)
+          if (idx >= ex[b] && idx < ex[b] + nn[b]) j = fi[b] + (idx - ex[b]);
+        if (j < 0) continue;
+        const PD<D> pj = load_pd<D>(t.a, j);
+        if (!(pj.m > 0.f)) continue;  // fluid only
+        float r[D];
+        const float r2 = separation<D>(s, xg, pj.x, r);  // x_g - x_j
+        if (!(r2 < s.H2)) continue;
+        const float q = safe_q(r2, s.invH);
+        const float VW = pj.V * (s.Kw * kern_w<KERN>(q));
+        const float VgH = pj.V * (s.Kg * kern_gt<KERN>(q)) * s.H;  // V grad W / r, times H
+        acc[0] += VW;
+#pragma unroll
+        for (int l = 0; l < D; ++l) acc[1 + l] = fmaf(-VW * s.invH, r[l], acc[1 + l]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          acc[(1 + k) * N] = fmaf(VgH, r[k], acc[(1 + k) * N]);
+#pragma unroll
+          for (int l = 0; l < D; ++l)
+            acc[(1 + k) * N + 1 + l] = fmaf(-VgH * s.invH * r[k], r[l], acc[(1 + k) * N + 1 + l]);
+        }
+        const float qj = pj.rho - s.rho0;
+        acc[N * N] = fmaf(VW, qj, acc[N * N]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[N * N + 1 + k] = fmaf(VgH * qj, r[k], acc[N * N + 1 + k]);
+      }
 #pragma unroll
       for (int e = 0; e < NS; ++e)
 #pragma unroll
