@@ -1,9 +1,9 @@
 /* sph_noalloc.h — cell binning that allocates nothing (libsph_b300.so).
  *
  * The paper has no counterpart to this call: it is a library service, not part of the method.
- * It does the neighbour-search set-up of one step (cell key of every particle, stable sort by
- * key, CSR cell ranges; Sec. 3.2 and App. B) for a caller that must not allocate device
- * memory, and returns the cell structure instead of advancing a scene.
+ * It bins particles into the cells a scene would use (cell key of every particle, stable sort
+ * by key, CSR cell ranges) for a caller that must not allocate device memory, and returns the
+ * cell structure instead of advancing a scene.
  *
  * Who cannot allocate, and why:
  *   - code that runs inside a device-memory allocator (for example an allocator callback
@@ -54,8 +54,10 @@ extern "C" {
  *   cell_start  device pointer, cell_start_len int32 entries; receives the CSR offsets
  *               cell_start[c] = first sorted position of cell c, for c = 0 .. n_cells
  *               (cell index (cz * ny + cy) * nx + cx).  SPH_EINVAL if cell_start_len < n_cells + 1.
- *   sorted_ids  device pointer, n int32; receives the original index of each particle in cell
- *               order, ties in ascending original index (a stable sort).
+ *   sorted_ids  device pointer to at least n int32 (the call cannot check its length: a shorter
+ *               buffer is written past its end); receives the original index of each particle
+ *               in cell order, ties in ascending original index (a stable sort).  The sort also
+ *               uses it as one of its two value buffers while it runs.
  *   n_cells     host pointer or NULL; receives the number of cells (also on SPH_EINVAL for a
  *               short cell_start, so that a caller can size the buffer and call again).
  *   stream      cudaStream_t of the caller (NULL = legacy default stream).  The call only

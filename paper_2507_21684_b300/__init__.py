@@ -543,18 +543,39 @@ NOALLOC_MAX_PARTICLES = 524288
 
 
 def cells_noalloc(params: dict, x, cell_start, sorted_ids, stream=None) -> int:
-    """Cell binning without allocation (sph_cells_noalloc): x is a CUDA float32 tensor (n, dim)
-    in original order; cell_start (n_cells + 1) and sorted_ids (n) are caller-owned CUDA int32
-    tensors that receive the CSR cell offsets and the stably sorted original indices.  Work is
-    enqueued on `stream` (a torch.cuda.Stream; None = the legacy default stream).  Returns
-    n_cells.  Passing cell_start=None only reports n_cells (SPH_EINVAL is swallowed)."""
-    n = int(x.shape[0]) if x is not None else 0
+    """Cell binning without allocation (sph_cells_noalloc): x is a contiguous CUDA float32 tensor
+    (n, dim) in original order; cell_start (>= n_cells + 1 entries) and sorted_ids (>= n entries)
+    are caller-owned contiguous CUDA int32 tensors that receive the CSR cell offsets and the stably
+    sorted original indices (sorted_ids also serves the sort as scratch).  Work is enqueued on
+    `stream` (a torch.cuda.Stream; None = the legacy default stream).  Returns n_cells.  Passing
+    cell_start=None only reports n_cells (SPH_EINVAL is swallowed).  Arguments of the wrong type,
+    shape or device raise ValueError before anything reaches the library."""
+    dim = int(params["dim"])
+    n = 0
+    if x is not None:
+        if not _is_torch(x) or not x.is_cuda or x.dtype != _torch().float32 or not x.is_contiguous():
+            raise ValueError("cells_noalloc: x must be a contiguous CUDA float32 tensor")
+        if x.dim() != 2 or int(x.shape[1]) != dim:
+            raise ValueError(f"cells_noalloc: x must have shape (n, {dim}), got {tuple(x.shape)}")
+        n = int(x.shape[0])
     nc = C.c_int32(0)
     st = None if stream is None else C.c_void_p(stream.cuda_stream)
     pp = Params.from_dict(params)
     if cell_start is None:
         lib().sph_cells_noalloc(C.byref(pp), None, 0, None, 0, None, C.byref(nc), st)
         return nc.value
+    torch = _torch()
+    for name, t in (("cell_start", cell_start), ("sorted_ids", sorted_ids)):
+        if t is None and name == "sorted_ids" and n == 0:
+            continue
+        if not _is_torch(t) or not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous():
+            raise ValueError(f"cells_noalloc: {name} must be a contiguous CUDA int32 tensor")
+    lib().sph_cells_noalloc(C.byref(pp), None, 0, None, 0, None, C.byref(nc), st)
+    if int(cell_start.numel()) < nc.value + 1:
+        raise ValueError(f"cells_noalloc: cell_start needs n_cells + 1 = {nc.value + 1} entries, "
+                         f"has {int(cell_start.numel())}")
+    if n and int(sorted_ids.numel()) < n:
+        raise ValueError(f"cells_noalloc: sorted_ids needs n = {n} entries, has {int(sorted_ids.numel())}")
     _check(lib().sph_cells_noalloc(C.byref(pp), x.data_ptr() if n else None, n, cell_start.data_ptr(),
                                    int(cell_start.numel()), sorted_ids.data_ptr() if n else None,
                                    C.byref(nc), st))
