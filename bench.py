@@ -1,13 +1,16 @@
 """Benchmark of the B300 WCSPH library (one JSON line on rank 0).
 
-Headline: forward pair interactions per second on the 2D dam break (32,768 fluid + 3,858 wall
-particles), one bench step = one full SPH step (cell keys, radix sort, cell ranges, permute,
-wall extrapolation, fused sweep with kick-drift), replayed as a CUDA graph, L2 flushed between
-timed steps.  Extra sections measure the 3D Taylor-Green forward step (2,097,152 particles),
-the adjoint rollout (128^2, 200 steps, checkpoints every 20) and the end-to-end call with host
-buffers.  ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
-workload.  Multi-GPU runs are independent replicas (the method has no data exchange between
-scenes): value = all ranks' pairs / the slowest rank's time.
+Headline: forward pair interactions per second on the 3D periodic Taylor-Green vortex at 128^3 =
+2,097,152 particles (Wendland C2, support 2.43 dx), one bench step = one full SPH step (cell keys,
+radix sort, cell ranges, permute, fused sweep with kick-drift) replayed as a CUDA graph; the
+state (235 MB) exceeds L2, so no flush is needed between steps.  Beside it on the same workload:
+the end-to-end call with host buffers, the FP64 oracle on the host cores (the CPU baseline) and
+the FP32-vs-FP64 error of every step of a 20-step rollout.  Extra sections measure the 2D dam
+break (and its renormalised, shifted, mDBC and summation variants), the adjoint rollout (128^2,
+200 steps, checkpoints every 20), shifting by optimisation and the served mixed-size stream.
+``--impl reference`` times the FP64 CPU oracle on the headline workload.  Multi-GPU runs are
+independent replicas (the method has no data exchange between scenes): value = all ranks' pairs /
+the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -29,8 +32,10 @@ if ROOT not in sys.path:
 METRIC = "pair interactions/s (fwd, adjoint); batched-vs-plain particle-steps/s, p99 latency"
 UNIT = "pair interactions/s"
 # Algorithmic FP32 flops of one in-radius ordered pair in the fused sweep (FMA = 2): the pair
-# terms of the continuity, delta-diffusion, pressure and viscous sums as written.
-FLOPS_PER_PAIR = {2: 42, 3: 50}
+# terms of the method as written, unfolded (minimum image, r^2, |r| and q, kernel gradient, Tait
+# pressure of the neighbour, volume, continuity, delta diffusion, pressure, viscosity, the
+# accumulations), about 80 in 2D and 3D; rejected candidates are not counted.
+FLOPS_PER_PAIR = {2: 80, 3: 80}
 # FP32 peak from unit counts and the maximum SM clock: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz.
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
@@ -381,6 +386,90 @@ def cpu_baseline(spec, budget_s: float = 15.0):
                 value_1core=pairs_fluid * n1 / dt1, sample_1core=f"{n1} FP64 steps on one core ({dt1:.1f} s)")
 
 
+def cpu_adjoint_baseline(spec, steps: int, ckpt: int):
+    """The FP64 oracle's reverse pass of the adjoint workload on the host cores: its forward
+    rollout and reverse pass of `steps` steps, timed together, in adjoint pair interactions/s
+    (pairs per step x steps / the reverse call's time)."""
+    import oracle
+    oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    n, d = spec["n_fluid"], spec["params"]["dim"]
+    pairs = oracle.pair_count(spec["params"], spec["x"])
+    xb = np.full((n, d), 1.0 / n)
+    t0 = time.perf_counter()
+    oracle.adjoint(spec, steps, xb, np.zeros((n, d)), np.zeros(n))
+    dt = time.perf_counter() - t0
+    return dict(value=pairs * steps / dt, unit="adjoint pair interactions/s", cores=cores, kind="oracle",
+                s=dt, sample=f"{spec['name']}: FP64 forward + reverse pass of {steps} steps at full size "
+                             f"({dt:.1f} s; the oracle keeps every step, no checkpoints)")
+
+
+def oracle_leg(sph, torch, spec, steps: int, budget_1core_s: float = 8.0):
+    """The FP64 oracle on the host cores beside the GPU on the same workload: `steps` oracle steps
+    from the initial state, each timed (the CPU baseline), and after every step the normwise error
+    of the GPU's FP32 state against the oracle's FP64 state (displacement x_n - x_0, v, rho - rho0,
+    ||gpu - oracle|| / ||oracle||, and the largest elementwise error over the field's largest
+    value).  One core: the oracle's rates of a sample of particles at full size."""
+    import oracle
+    oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    p = spec["params"]
+    d, n = p["dim"], spec["n_fluid"] + spec["n_wall"]
+    rho0 = float(p["rho0"])
+    pairs = oracle.pair_count(p, spec["x"])
+    x0 = spec["x"].astype(np.float64).reshape(n, d)
+    xo, vo, ro = x0.copy(), spec["v"].astype(np.float64).reshape(n, d), spec["rho"].astype(np.float64)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sc = sph.scene_from(spec, stream=stream.cuda_stream)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    def rmax(a, b):
+        return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+    per_step, t_cpu = [], 0.0
+    for k in range(steps):
+        t = time.perf_counter()
+        xo, vo, ro = oracle.rollout64(spec, 1, xo, vo, ro)
+        t_cpu += time.perf_counter() - t
+        sc.step(1)
+        xg, vg, rg = sc.get_state()
+        xg = xg.astype(np.float64).reshape(n, d)
+        vg = vg.astype(np.float64).reshape(n, d)
+        rg = rg.astype(np.float64)
+        # half an ulp of the float32 output at the oracle's values: the floor no FP32 result beats
+        qx = float(np.linalg.norm(np.spacing(np.abs(xo).astype(np.float32)).astype(np.float64) / 2)
+                   / max(np.linalg.norm(xo - x0), 1e-300))
+        per_step.append({"step": k + 1, "x_disp": rel(xg - x0, xo - x0), "v": rel(vg, vo),
+                         "rho_minus_rho0": rel(rg - rho0, ro - rho0), "x_disp_max": rmax(xg - x0, xo - x0),
+                         "v_max": rmax(vg, vo), "rho_minus_rho0_max": rmax(rg - rho0, ro - rho0),
+                         "x_disp_f32_floor": qx})
+    sc.close()
+    # one core: rates of a sample of the particles (neighbour lists of the sample included)
+    oracle.set_threads(1)
+    m = max(1, min(n, int(n / 64)))
+    who = np.linspace(0, spec["n_fluid"] - 1, m).astype(np.int32)
+    t = time.perf_counter()
+    oracle.rates(spec, who=who)
+    t1 = time.perf_counter() - t
+    oracle.set_threads(cores)
+    worst = {k: max(r[k] for r in per_step) for k in ("x_disp", "v", "rho_minus_rho0")}
+    cb = dict(value=pairs * steps / t_cpu, unit=UNIT, cores=cores, kind="oracle",
+              sample=f"{spec['name']}: {steps} FP64 steps at full size from the initial state "
+                     f"({t_cpu:.1f} s, {pairs} ordered pairs per step)",
+              value_1core=pairs * (m / n) / t1,
+              sample_1core=f"rates of {m} sampled particles (1/64) at full size on one core ({t1:.1f} s; "
+                           f"pairs scaled from the full step's count)")
+    err = {"steps": steps, "per_step": per_step, "worst": worst,
+           "norm": "||gpu - oracle|| / ||oracle|| per field over all particles (x as the displacement "
+                   "x_n - x_0); *_max: largest elementwise error / largest oracle value; "
+                   "x_disp_f32_floor: half an ulp of float32 x over the displacement norm",
+           "gpu": "FP32 (double-single x and rho)", "oracle": "FP64"}
+    return cb, err
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,7 +477,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
-    ap.add_argument("--cpu-budget", type=float, default=30.0)
+    ap.add_argument("--cpu-steps", type=int, default=20,
+                    help="FP64 oracle steps at full size beside the headline (CPU baseline, FP32-vs-FP64 error)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle leg of the headline")
     ap.add_argument("--profile-run", action="store_true",
                     help="forward steps of one workload only (for ncu): no extras, e2e or CPU leg")
     ap.add_argument("--workload", default="dambreak", choices=["dambreak", "tgv3d", "adjoint"],
@@ -449,21 +540,18 @@ def main():
                           "ms_per_step": sum(r["ms"]) / len(r["ms"]), "pairs_per_step": r["pairs_per_step"]}))
         return
 
-    spec = si.dam_break(res=128)
-    workload = {"workload": "2D WCSPH dam break, 32768 fluid + 3858 wall particles, dx=1/128, Wendland C4 "
-                            "support 4dx, delta-SPH, Tait gamma=7, c0=10 sqrt(2 g 2.0)",
-                "particles": spec["n_fluid"] + spec["n_wall"], "step": "one full SPH time step",
-                "l2": "flushed (320 MB write) between timed steps", "graph": "CUDA graph per step"}
+    spec = si.taylor_green_3d(128, seed=0)
+    workload = {"workload": "3D periodic Taylor-Green WCSPH, 128^3 = 2,097,152 particles in the unit cube, lattice "
+                            "jittered +-0.05 dx, Wendland C2 support 2.43 dx, Tait gamma=7, c0=10, nu=0.005, "
+                            "delta-SPH delta=0.1, FP32",
+                "particles": spec["n_fluid"], "step": "one full SPH time step (forward only)",
+                "l2": "not flushed: the state (2 x 112 MB record buffers) exceeds the 126 MB L2",
+                "graph": "CUDA graph per step"}
 
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = cpu_baseline(spec, budget_s=max(5.0, min(args.cpu_budget, 60.0)))
-        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
-                "data": "synthetic", "config": workload, "cpu_baseline": cb,
-                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        print(json.dumps(reference_arm(spec, workload, args)))
         return
 
     import torch
@@ -477,167 +565,70 @@ def main():
     from paper_2507_21684_b300 import tune
 
     # tile shape (targets per tile, threads per target) chosen by the library's autotuner: each
-    # variant of the library times the headline scene in a child process; rank 0 decides
-    tiles = None
+    # variant of the library times the headline scene (3D shapes) and the dam break (2D shapes) in
+    # a child process; the process then loads the library built with both choices; rank 0 decides
+    tiles = tiles2 = None
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
     if rank == 0 and not args.no_tile_tune:
-        tiles = tune.tune_tiles(tune.with_skin(spec, 0.02), steps=100, warmup=50,
-                                device=int(os.environ.get("LOCAL_RANK", "0")))
-    variant = replica_choice(tiles["variant"] if tiles else "default")
+        tiles = tune.tune_tiles(spec, steps=40, warmup=10, device=dev)
+        if not args.no_extras:
+            tiles2 = tune.tune_tiles(tune.with_skin(si.dam_break(res=128), 0.02), steps=100, warmup=50, device=dev)
+    v3 = tiles["variant"] if tiles else "default"
+    v2 = tiles2["variant"] if tiles2 else "default"
+    try:
+        variant = sbuild.canonical(f"{v3}+{v2}")
+    except ValueError:  # the two choices set the same shape: the headline's wins
+        variant = v3
+    variant = replica_choice(variant)
+    sbuild.build(variant=variant)
     sph.select_variant(variant)
     sph.use_torch_allocator()
     stream = torch.cuda.Stream()
 
     # neighbour-search setting of the headline scene chosen by the library's autotuner (a Verlet
     # skin; every candidate finds the same neighbours each step)
-    tuned = tune.tune_skin(spec, skins=(0.0, 0.02, 0.05, 0.1, 0.2), steps=100, warmup=100)
+    tuned = tune.tune_skin(spec, skins=(0.0, 0.02, 0.05), steps=40, warmup=10)
     best_skin = replica_choice(tuned["best"]["skin_over_H"])
     spec = dict(spec, params=tune.with_skin(spec, best_skin)["params"])
-    workload = dict(workload, verlet_skin_over_H=best_skin, library_variant=variant,
+    workload = dict(workload, verlet_skin_over_H=best_skin, library_variant=variant, tile_variant_3d=v3,
                     rebuild="on the device when a particle has moved skin/2 since the last build")
-
-    clk = Clocks(torch.cuda.current_device())
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clk.start()
-    fw = run_forward(sph, torch, spec, args.steps, args.warmup, True, stream)
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    t_total, pairs_total = replica_reduce(sum(fw["ms"]) / 1e3, float(fw["pairs_per_step"] * args.steps),
-                                          device="cuda")
-    value = pairs_total / t_total
-    sweep_flops = FLOPS_PER_PAIR[2] * fw["pairs_per_step"]
-    achieved = sweep_flops / (fw["sweep_ms"] / 1e3) / 1e12
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
 
-    extras = {}
-    if not args.no_extras and rank == 0:
-        s3 = si.taylor_green_3d(128, seed=0)
-        f3 = run_forward(sph, torch, s3, 20, 3, False, torch.cuda.Stream())
-        t3 = sum(f3["ms"]) / 1e3
-        extras["tgv3d_128"] = {
-            "particles": s3["n_fluid"], "steps": 20, "ms_per_step": 1e3 * t3 / 20,
-            "pair_interactions_per_s": f3["pairs_per_step"] * 20 / t3,
-            "particle_steps_per_s": s3["n_fluid"] * 20 / t3,
-            "sweep_ms": f3["sweep_ms"], "rebuild_ms": f3["rebuild_ms"],
-            "sweep_fp32_tflops": FLOPS_PER_PAIR[3] * f3["pairs_per_step"] / (f3["sweep_ms"] / 1e3) / 1e12,
-            "l2": "state 2M particles x 112 B > L2, no flush"}
-        # the 3D sweep against the memory roofline: 56 B per particle-step algorithmic, and the
-        # DRAM and L2 bytes of the committed capture taken with the same 3D tile shape
-        v3 = variant if variant in tune.shape_variants(3) else "default"
-        t3b, t3src = stored_traffic("k_sweep_t_tgv3d_128", v3)
-        extras["tgv3d_128"]["sweep_fp32_frac"] = extras["tgv3d_128"]["sweep_fp32_tflops"] / FP32_PEAK_TFLOPS
-        extras["tgv3d_128"]["hbm_view"] = hbm_view(56.0 * s3["n_fluid"], t3b, f3["sweep_ms"], peaks.get("hbm_gbs"),
-                                                   stored_l2_bytes(t3src))
-        extras["tgv3d_128"]["traffic_source"] = t3src
-        # the same dam break with the renormalised delta-SPH diffusion (one more neighbour pass)
-        sr = dict(si.dam_break(res=128, diffusion=1), params=dict(spec["params"], diffusion=1))
-        fr = run_forward(sph, torch, sr, args.steps, args.warmup, True, torch.cuda.Stream())
-        tr = sum(fr["ms"]) / 1e3
-        extras["dambreak_128_renorm"] = {
-            "diffusion": "renormalised delta-SPH (kernel renormalisation L_i, Antuono psi_ij)",
-            "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * tr / args.steps,
-            "pair_interactions_per_s": fr["pairs_per_step"] * args.steps / tr,
-            "sweep_ms": fr["sweep_ms"], "gradient_ms": fr["gradient_ms"], "walls_ms": fr["walls_ms"],
-            "l2": "flushed between timed steps"}
-        # ... and with both next-row features: renormalised diffusion and particle shifting
-        ss = dict(sr, params=dict(sr["params"], shift=float(np.float32(0.05))))
-        fs = run_forward(sph, torch, ss, args.steps, args.warmup, True, torch.cuda.Stream())
-        ts = sum(fs["ms"]) / 1e3
-        extras["dambreak_128_renorm_shift"] = {
-            "diffusion": "renormalised", "shift": "explicit, C = 0.05, free-surface band tangential",
-            "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * ts / args.steps,
-            "pair_interactions_per_s": fs["pairs_per_step"] * args.steps / ts,
-            "sweep_ms": fs["sweep_ms"], "gradient_ms": fs["gradient_ms"], "shift_ms": fs["shift_ms"],
-            "rebuilds_in_timed_region": fs["rebuilds"], "l2": "flushed between timed steps"}
-        # the dam break with mDBC walls (ghost nodes) in place of the Shepard wall pressure
-        sm = dict(si.dam_break(res=128, boundary=1), params=dict(spec["params"], boundary=1))
-        fm = run_forward(sph, torch, sm, args.steps, args.warmup, True, torch.cuda.Stream())
-        tm = sum(fm["ms"]) / 1e3
-        extras["dambreak_128_mdbc"] = {
-            "boundary": "mDBC: first-order system at mirrored ghost nodes, pseudo-inverse",
-            "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * tm / args.steps,
-            "pair_interactions_per_s": fm["pairs_per_step"] * args.steps / tm,
-            "sweep_ms": fm["sweep_ms"], "mdbc_walls_ms": fm["walls_ms"], "l2": "flushed between timed steps"}
-        # the dam break in summation mode: density sum of the fluid (a6), then the wall pass and
-        # the sweep
-        sd = dict(spec, params=dict(spec["params"], density_mode=1))
-        try:
-            fd = run_forward(sph, torch, sd, args.steps, args.warmup, True, torch.cuda.Stream())
-            td = sum(fd["ms"]) / 1e3
-            extras["dambreak_128_summation"] = {
-                "density": "summation (rho_i = sum_j m_j W_ij, compensated FP32 accumulation)",
-                "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * td / args.steps,
-                "pair_interactions_per_s": fd["pairs_per_step"] * args.steps / td,
-                "sweep_ms": fd["sweep_ms"], "density_ms": fd["density_ms"], "walls_ms": fd["walls_ms"],
-                "l2": "flushed between timed steps"}
-        except sph.SphError as e:  # the scene's own error (e.g. a density outside the stable band)
-            extras["dambreak_128_summation"] = {"error": str(e)}
-        # shifting by optimisation at the paper's backward-cost size: 65,536 randomly sampled
-        # particles, objective (2 passes) and its gradient (2 passes) per descent iteration
-        so = si.shift_problem(256, seed=0)
-        obj = dict(w_grad=1.0, w_reg=1.0, reg_fraction=0.5)
-        with sph.scene_from(so) as sc:
-            _, g0 = sc.shift_gradient(obj)
-            step = float(5e-3 * so["dx"] / max(float(np.abs(g0).max()), 1e-30))
-            sc.shift_descend(obj, 3, step)  # warm-up
-            sc.profile(True)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            hist = sc.shift_descend(obj, 50, step)
-            t_it = (time.perf_counter() - t0) / 50
-            f_ms, f_n = sc.timing(sph.TIMING_OPT_OBJECTIVE)
-            b_ms, b_n = sc.timing(sph.TIMING_OPT_GRADIENT)
-            r_ms, r_n = sc.timing(sph.TIMING_REBUILD)
-        extras["shift_opt_64k"] = {
-            "particles": so["n_fluid"], "objective": "|grad <1>|^2 + pair penalty below 0.5 dx (the paper's 2D shifting)",
-            "iterations": 50, "ms_per_iteration_host": 1e3 * t_it,
-            "objective_ms": f_ms / max(f_n, 1), "gradient_ms": b_ms / max(b_n, 1), "rebuild_ms": r_ms / max(r_n, 1),
-            "gradient_over_objective": (b_ms / max(b_n, 1)) / max(f_ms / max(f_n, 1), 1e-12),
-            "loss_first_last": [float(hist[0, 0]), float(hist[-1, 0])],
-            "note": "kernel classes timed by CUDA events on the scene's stream; the host time includes one cell rebuild per iteration"}
-        sa = si.adjoint_problem(128)
-        for name, skin in (("adjoint_128", 0.0), ("adjoint_128_skin", 0.3)):
-            spa = dict(sa, params=tune.with_skin(sa, skin)["params"])
-            ad = run_adjoint(sph, torch, spa, 200, 20)
-            extras[name] = {
-                "particles": sa["n_fluid"], "steps": 200, "ckpt_every": 20, "verlet_skin_over_H": skin,
-                "ms_total": ad["ms"],
-                "adjoint_pair_interactions_per_s": ad["pairs_per_step"] * 200 / (ad["ms"] / 1e3),
-                "adjoint_sweep_ms": ad["adj_sweep_ms"],
-                "adjoint_sweep_pairs_per_s": ad["pairs_per_step"] / (ad["adj_sweep_ms"] / 1e3),
-                "replay_rebuild_interval": ad["replay_interval"], "replay_fallbacks": ad["replay_fallbacks"],
-                "note": "time of sph_adjoint: 10 segment recomputes (forward replay) + 200 adjoint sweeps, "
-                        "captured graphs per segment part; with the skin the replay rebuilds every "
-                        "replay_rebuild_interval steps"}
-        stream = {}
-        for rate in args.stream_rates:
-            reqs = _stream_specs(args.stream_scenes, rate)
-            pl = run_plain(sph, reqs)
-            sv = run_served(sph, reqs)
-            stream[f"{rate:g}_req_s"] = {"plain": pl, "served": sv,
-                                         "served_over_plain_throughput": sv["particle_steps_per_s"] / pl["particle_steps_per_s"],
-                                         "served_over_plain_p99": sv["p99_s"] / pl["p99_s"]}
-        extras["served_stream"] = {
-            "scenes": args.stream_scenes, "sizes": "log-uniform in [1024, 262144] (square lattices)",
-            "steps": "uniform in [50, 500]", "adjoint_fraction": 0.2, "arrivals": "Poisson", "by_rate": stream,
-            "metric": "fluid particle-steps/s over the makespan; latency = completion - arrival"}
+    clk = Clocks(torch.cuda.current_device())
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    fw = run_forward(sph, torch, spec, args.steps, args.warmup, False, stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    t_total, pairs_total = replica_reduce(sum(fw["ms"]) / 1e3, float(fw["pairs_per_step"] * args.steps),
+                                          device="cuda")
+    value = pairs_total / t_total
+    achieved = FLOPS_PER_PAIR[3] * fw["pairs_per_step"] / (fw["sweep_ms"] / 1e3) / 1e12
+
     e2e = None
     if rank == 0:
-        ee = run_e2e(sph, torch, spec, 2000, 2)
-        e2e = {"value": ee["pairs_per_step"] * 2000 / ee["s"], "unit": UNIT,
-               "h2d_bytes_per_step": ee["h2d"] / 2000.0, "d2h_bytes_per_step": ee["d2h"] / 2000.0,
-               "call": "sph_init(host pinned) + sph_step(2000) + sph_get_state(host pinned), host wall clock",
+        n_e2e = 200
+        ee = run_e2e(sph, torch, spec, n_e2e, 2)
+        e2e = {"value": ee["pairs_per_step"] * n_e2e / ee["s"], "unit": UNIT,
+               "h2d_bytes_per_step": ee["h2d"] / n_e2e, "d2h_bytes_per_step": ee["d2h"] / n_e2e,
+               "call": f"sph_init(host pinned) + sph_step({n_e2e}) + sph_get_state(host pinned), host wall clock "
+                       f"(the workload's 200 steps)",
                "h2d_bytes_per_call": ee["h2d"], "d2h_bytes_per_call": ee["d2h"], "s_per_call": ee["s"]}
-    cb = None
-    if rank == 0 and ws == 1:
-        cb = cpu_baseline(spec, budget_s=args.cpu_budget)
+    cb, err = None, None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cb, err = oracle_leg(sph, torch, spec, args.cpu_steps)
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(sph, torch, tune, args, variant, peaks, tiles2)
     if rank == 0:
-        traffic, traffic_src = stored_traffic("k_walls_sweep_t_dambreak_128", variant)
+        traffic, traffic_src = stored_traffic("k_sweep_t_tgv3d_128", v3 if v3 in tune.shape_variants(3) else "default")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
@@ -645,33 +636,203 @@ def main():
             "config": dict(workload, parallelism=f"replicas x{ws}"),
             "pairs_per_step": fw["pairs_per_step"], "gpu_launches": fw["launches"],
             "rebuilds_in_timed_region": fw["rebuilds"],
+            "particle_steps_per_s": spec["n_fluid"] * args.steps * ws / t_total,
             "clocks": clocks,
-            "roofline": {"bound": "alu", "kernel": "k_walls_sweep_t (wall pass + fused rates + kick-drift, one launch)",
+            "roofline": {"bound": "alu", "kernel": "k_sweep_t<3> (fused rates + kick-drift)",
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS,
                          "traffic": traffic,
-                         "traffic_source": (f"{traffic_src} (ncu, cold caches, one launch, library variant "
-                                            f"{variant})" if traffic_src else None),
-                         "flops_per_pair": FLOPS_PER_PAIR[2], "pairs_per_launch": fw["pairs_per_step"],
+                         "traffic_source": (f"{traffic_src} (ncu, one launch, library variant {variant})"
+                                            if traffic_src else None),
+                         "flops_per_pair": FLOPS_PER_PAIR[3], "pairs_per_launch": fw["pairs_per_step"],
                          "sweep_ms_avg": fw["sweep_ms"], "sweep_launches": fw["sweep_n"],
-                         "peak_source": "148 SM x 128 FP32 lanes x 2 x 2.032 GHz (unit counts and max clock)"},
+                         "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz (unit counts and "
+                                        "maximum SM clock; MEASURED_PEAKS has no FP32 figure)"},
             "breakdown_ms": {"sweep": fw["sweep_ms"], "rebuild_decision_and_rebuilds": fw["rebuild_ms"],
-                             "walls": fw["walls_ms"], "step_median": statistics.median(fw["ms"]),
+                             "step_median": statistics.median(fw["ms"]),
                              "note": "kernel classes timed by event nodes on 50 extra profiled steps"},
             "autotune": tuned["table"],
             "autotune_tiles": tiles["table"] if tiles else None,
-            "e2e": e2e, "cpu_baseline": cb, "extras": extras,
+            "e2e": e2e, "cpu_baseline": cb, "fp32_vs_fp64": err, "extras": extras,
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
             # the same kernel against the memory roofline (it is not memory bound): algorithmic
-            # bytes = the state read and written once (40 B per particle in 2D), and the DRAM
+            # bytes = the state read and written once (56 B per particle in 3D), and the DRAM
             # bytes of the committed ncu capture, over the kernel's mean time
-            "hbm_view": hbm_view(40.0 * spec["n_fluid"] + 40.0 * spec["n_wall"], traffic, fw["sweep_ms"],
-                                 peaks.get("hbm_gbs"), stored_l2_bytes(traffic_src)),
+            "hbm_view": hbm_view(56.0 * spec["n_fluid"], traffic, fw["sweep_ms"], peaks.get("hbm_gbs"),
+                                 stored_l2_bytes(traffic_src)),
         }
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
 
+
+def reference_arm(spec, workload, args) -> dict:
+    """The FP64 oracle as it stands on the host cores, on the headline workload: W untimed steps,
+    then K timed full-size steps (fewer if they would not end within about two minutes)."""
+    import oracle
+    oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    p = spec["params"]
+    n, d = spec["n_fluid"], p["dim"]
+    pairs = oracle.pair_count(p, spec["x"])
+    x, v, r = (spec["x"].astype(np.float64).reshape(n, d), spec["v"].astype(np.float64).reshape(n, d),
+               spec["rho"].astype(np.float64))
+    t = time.perf_counter()
+    for _ in range(max(1, min(args.warmup, 2))):
+        x, v, r = oracle.rollout64(spec, 1, x, v, r)
+    per = (time.perf_counter() - t) / max(1, min(args.warmup, 2))
+    k = max(1, min(args.steps, int(120.0 / max(per, 1e-6))))
+    t = time.perf_counter()
+    for _ in range(k):
+        x, v, r = oracle.rollout64(spec, 1, x, v, r)
+    dt = time.perf_counter() - t
+    value = pairs * k / dt
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / k, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic", "config": workload,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{spec['name']}: {k} of the {args.steps} requested FP64 steps at full size "
+                                       f"after {max(1, min(args.warmup, 2))} untimed ({dt:.1f} s)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_extras(sph, torch, tune, args, variant, peaks, tiles2=None) -> dict:
+    """The other workloads: the dam break (and its variants), the adjoint rollout, shifting by
+    optimisation, the served stream, and the oracle beside the small configurations."""
+    extras = {}
+    import sph_inputs as si
+    # the 2D dam break (36,626 particles), L2 flushed between timed steps, with the 2D tile shape
+    # tuned for it (part of the loaded library variant) and its own skin
+    db = si.dam_break(res=128)
+    v2 = tiles2["variant"] if tiles2 else "default"
+    dtuned = tune.tune_skin(db, skins=(0.0, 0.02, 0.05, 0.1, 0.2), steps=100, warmup=100)
+    dskin = dtuned["best"]["skin_over_H"]
+    db = dict(db, params=tune.with_skin(db, dskin)["params"])
+    dfw = run_forward(sph, torch, db, args.steps, args.warmup, True, torch.cuda.Stream())
+    d = {"particles": db["n_fluid"] + db["n_wall"], "verlet_skin_over_H": dskin, "tile_variant_2d": v2,
+         "library_variant": variant, "autotune_tiles": tiles2["table"] if tiles2 else None,
+         "autotune_skin": dtuned["table"], "l2": "flushed (320 MB write) between timed steps"}
+    td = sum(dfw["ms"]) / 1e3
+    traffic, src = stored_traffic("k_walls_sweep_t_dambreak_128", v2)
+    ach = FLOPS_PER_PAIR[2] * dfw["pairs_per_step"] / (dfw["sweep_ms"] / 1e3) / 1e12
+    d.update({"steps": args.steps, "ms_per_step": 1e3 * td / args.steps,
+              "pair_interactions_per_s": dfw["pairs_per_step"] * args.steps / td,
+              "sweep_ms": dfw["sweep_ms"], "rebuild_ms": dfw["rebuild_ms"], "gpu_launches": dfw["launches"],
+              "roofline": {"bound": "alu", "kernel": "k_walls_sweep_t<2> (wall pass + fused rates + kick-drift)",
+                           "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic, "traffic_source": src,
+                           "flops_per_pair": FLOPS_PER_PAIR[2]},
+              "hbm_view": hbm_view(40.0 * (db["n_fluid"] + db["n_wall"]), traffic, dfw["sweep_ms"],
+                                   peaks.get("hbm_gbs"), stored_l2_bytes(src))})
+    ee = run_e2e(sph, torch, db, 2000, 2)
+    d["e2e"] = {"value": ee["pairs_per_step"] * 2000 / ee["s"], "unit": UNIT, "s_per_call": ee["s"],
+                "call": "sph_init(host pinned) + sph_step(2000) + sph_get_state(host pinned)"}
+    d["cpu_baseline"] = cpu_baseline(dict(db, name="dambreak_128"), budget_s=10.0)
+    extras["dambreak_128"] = d
+    spec = db
+    best_skin = dskin
+    # the same dam break with the renormalised delta-SPH diffusion (one more neighbour pass)
+    sr = dict(si.dam_break(res=128, diffusion=1), params=dict(spec["params"], diffusion=1))
+    fr = run_forward(sph, torch, sr, args.steps, args.warmup, True, torch.cuda.Stream())
+    tr = sum(fr["ms"]) / 1e3
+    extras["dambreak_128_renorm"] = {
+        "diffusion": "renormalised delta-SPH (kernel renormalisation L_i, Antuono psi_ij)",
+        "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * tr / args.steps,
+        "pair_interactions_per_s": fr["pairs_per_step"] * args.steps / tr,
+        "sweep_ms": fr["sweep_ms"], "gradient_ms": fr["gradient_ms"], "walls_ms": fr["walls_ms"],
+        "l2": "flushed between timed steps"}
+    # ... and with both next-row features: renormalised diffusion and particle shifting
+    ss = dict(sr, params=dict(sr["params"], shift=float(np.float32(0.05))))
+    fs = run_forward(sph, torch, ss, args.steps, args.warmup, True, torch.cuda.Stream())
+    ts = sum(fs["ms"]) / 1e3
+    extras["dambreak_128_renorm_shift"] = {
+        "diffusion": "renormalised", "shift": "explicit, C = 0.05, free-surface band tangential",
+        "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * ts / args.steps,
+        "pair_interactions_per_s": fs["pairs_per_step"] * args.steps / ts,
+        "sweep_ms": fs["sweep_ms"], "gradient_ms": fs["gradient_ms"], "shift_ms": fs["shift_ms"],
+        "rebuilds_in_timed_region": fs["rebuilds"], "l2": "flushed between timed steps"}
+    # the dam break with mDBC walls (ghost nodes) in place of the Shepard wall pressure
+    sm = dict(si.dam_break(res=128, boundary=1), params=dict(spec["params"], boundary=1))
+    fm = run_forward(sph, torch, sm, args.steps, args.warmup, True, torch.cuda.Stream())
+    tm = sum(fm["ms"]) / 1e3
+    extras["dambreak_128_mdbc"] = {
+        "boundary": "mDBC: first-order system at mirrored ghost nodes, pseudo-inverse",
+        "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * tm / args.steps,
+        "pair_interactions_per_s": fm["pairs_per_step"] * args.steps / tm,
+        "sweep_ms": fm["sweep_ms"], "mdbc_walls_ms": fm["walls_ms"], "l2": "flushed between timed steps"}
+    # the dam break in summation mode: density sum of the fluid (a6), then the wall pass and
+    # the sweep
+    sd = dict(spec, params=dict(spec["params"], density_mode=1))
+    try:
+        fd = run_forward(sph, torch, sd, args.steps, args.warmup, True, torch.cuda.Stream())
+        td = sum(fd["ms"]) / 1e3
+        extras["dambreak_128_summation"] = {
+            "density": "summation (rho_i = sum_j m_j W_ij, compensated FP32 accumulation)",
+            "verlet_skin_over_H": best_skin, "steps": args.steps, "ms_per_step": 1e3 * td / args.steps,
+            "pair_interactions_per_s": fd["pairs_per_step"] * args.steps / td,
+            "sweep_ms": fd["sweep_ms"], "density_ms": fd["density_ms"], "walls_ms": fd["walls_ms"],
+            "l2": "flushed between timed steps"}
+    except sph.SphError as e:  # the scene's own error (e.g. a density outside the stable band)
+        extras["dambreak_128_summation"] = {"error": str(e)}
+    # the 2D Taylor-Green at 64^2 (the small configuration), 100 steps, and the oracle beside it
+    s0 = si.taylor_green_2d(64, seed=0)
+    f0 = run_forward(sph, torch, s0, 100, args.warmup, False, torch.cuda.Stream(), prof_steps=0)
+    t0 = sum(f0["ms"]) / 1e3
+    extras["tgv2d_64"] = {"particles": s0["n_fluid"], "steps": 100, "ms_per_step": 1e3 * t0 / 100,
+                          "pair_interactions_per_s": f0["pairs_per_step"] * 100 / t0,
+                          "cpu_baseline": cpu_baseline(dict(s0, name="tgv2d_64"), budget_s=3.0),
+                          "l2": "resident (state 0.3 MB), no flush"}
+    # shifting by optimisation at the paper's backward-cost size: 65,536 randomly sampled
+    # particles, objective (2 passes) and its gradient (2 passes) per descent iteration
+    so = si.shift_problem(256, seed=0)
+    obj = dict(w_grad=1.0, w_reg=1.0, reg_fraction=0.5)
+    with sph.scene_from(so) as sc:
+        _, g0 = sc.shift_gradient(obj)
+        step = float(5e-3 * so["dx"] / max(float(np.abs(g0).max()), 1e-30))
+        sc.shift_descend(obj, 3, step)  # warm-up
+        sc.profile(True)
+        torch.cuda.synchronize()
+        tt = time.perf_counter()
+        hist = sc.shift_descend(obj, 50, step)
+        t_it = (time.perf_counter() - tt) / 50
+        f_ms, f_n = sc.timing(sph.TIMING_OPT_OBJECTIVE)
+        b_ms, b_n = sc.timing(sph.TIMING_OPT_GRADIENT)
+        r_ms, r_n = sc.timing(sph.TIMING_REBUILD)
+    extras["shift_opt_64k"] = {
+        "particles": so["n_fluid"], "objective": "|grad <1>|^2 + pair penalty below 0.5 dx (the paper's 2D shifting)",
+        "iterations": 50, "ms_per_iteration_host": 1e3 * t_it,
+        "objective_ms": f_ms / max(f_n, 1), "gradient_ms": b_ms / max(b_n, 1), "rebuild_ms": r_ms / max(r_n, 1),
+        "gradient_over_objective": (b_ms / max(b_n, 1)) / max(f_ms / max(f_n, 1), 1e-12),
+        "loss_first_last": [float(hist[0, 0]), float(hist[-1, 0])],
+        "note": "kernel classes timed by CUDA events on the scene's stream; the host time includes one cell rebuild per iteration"}
+    sa = si.adjoint_problem(128)
+    for name, skin in (("adjoint_128", 0.0), ("adjoint_128_skin", 0.3)):
+        spa = dict(sa, params=tune.with_skin(sa, skin)["params"])
+        ad = run_adjoint(sph, torch, spa, 200, 20)
+        extras[name] = {
+            "particles": sa["n_fluid"], "steps": 200, "ckpt_every": 20, "verlet_skin_over_H": skin,
+            "ms_total": ad["ms"],
+            "adjoint_pair_interactions_per_s": ad["pairs_per_step"] * 200 / (ad["ms"] / 1e3),
+            "adjoint_sweep_ms": ad["adj_sweep_ms"],
+            "adjoint_sweep_pairs_per_s": ad["pairs_per_step"] / (ad["adj_sweep_ms"] / 1e3),
+            "replay_rebuild_interval": ad["replay_interval"], "replay_fallbacks": ad["replay_fallbacks"],
+            "note": "time of sph_adjoint: 10 segment recomputes (forward replay) + 200 adjoint sweeps, "
+                    "captured graphs per segment part; with the skin the replay rebuilds every "
+                    "replay_rebuild_interval steps"}
+    extras["adjoint_128"]["cpu_baseline"] = cpu_adjoint_baseline(dict(sa, name="adjoint_128"), 200, 20)
+    stream = {}
+    for rate in args.stream_rates:
+        reqs = _stream_specs(args.stream_scenes, rate)
+        pl = run_plain(sph, reqs)
+        sv = run_served(sph, reqs)
+        stream[f"{rate:g}_req_s"] = {"plain": pl, "served": sv,
+                                     "served_over_plain_throughput": sv["particle_steps_per_s"] / pl["particle_steps_per_s"],
+                                     "served_over_plain_p99": sv["p99_s"] / pl["p99_s"]}
+    extras["served_stream"] = {
+        "scenes": args.stream_scenes, "sizes": "log-uniform in [1024, 262144] (square lattices)",
+        "steps": "uniform in [50, 500]", "adjoint_fraction": 0.2, "arrivals": "Poisson", "by_rate": stream,
+        "metric": "fluid particle-steps/s over the makespan; latency = completion - arrival"}
+    return extras
 
 if __name__ == "__main__":
     main()

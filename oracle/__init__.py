@@ -189,6 +189,14 @@ def pairs(p: dict, x: np.ndarray, brute: bool = False) -> np.ndarray:
     return np.stack([pi, pj], 1)
 
 
+def pair_count(p: dict, x: np.ndarray) -> int:
+    """Number of ordered neighbour pairs (i != j, |r| < H) at the float32 positions x (cell search;
+    the lists themselves are not returned)."""
+    P = params(p)
+    x = np.ascontiguousarray(x, np.float32)
+    return int(lib().orc_pairs_cells(C.byref(P), x.shape[0], _ptr(x, C.c_float), 0, None, None))
+
+
 def rates(scene: dict, who: np.ndarray | None = None, x=None, v=None, rho=None):
     """a, drho (and the rho, p used) of fluid particles at a float32 state."""
     p = scene["params"]

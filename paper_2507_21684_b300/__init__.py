@@ -19,9 +19,9 @@ import numpy as np
 __all__ = ["lib", "Params", "Scene", "Server", "SphError", "rollout_fn", "library_path"]
 
 _HERE = Path(__file__).resolve().parent
-_LIBPATH = _HERE / "libsph_b300.so"
-if os.environ.get("SPH_B300_VARIANT", "default") != "default":
-    _LIBPATH = _HERE / f"libsph_b300_{os.environ['SPH_B300_VARIANT']}.so"
+from . import build as _build  # noqa: E402  (paths of the library variants; no compilation here)
+
+_LIBPATH = _build.lib_path(os.environ.get("SPH_B300_VARIANT", "default"))
 _lib = None
 
 SPH_OK, SPH_EINVAL, SPH_ENOMEM, SPH_ECUDA, SPH_EUNSTABLE, SPH_ETIMEOUT, SPH_EBUSY, SPH_EINTERNAL = range(8)
@@ -122,8 +122,7 @@ def select_variant(name: str) -> None:
     called before the library is first used in this process."""
     global _LIBPATH
     from . import build as _b
-    if name not in _b.VARIANTS:
-        raise ValueError(f"unknown library variant {name!r}")
+    name = _b.canonical(name)  # raises ValueError for an unknown part
     path = _b.lib_path(name)
     if _lib is not None and path != _LIBPATH:
         raise RuntimeError("the library is already loaded; select the variant first")

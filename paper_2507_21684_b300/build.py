@@ -27,11 +27,37 @@ VARIANTS = {
     # how lines are cut into tiles: whole cells in 2D, balanced tiles in 3D (the defaults swapped)
     "cells2": {"SPH_TILE2_CUT": 0},
     "balanced3": {"SPH_TILE3_CUT": 1},
+    # the 3D sweep on the staged traversal instead of the warp-per-tile one
+    "staged3": {"SPH_W3": 0},
 }
 
 
+def variant_macros(variant: str) -> dict:
+    """Macros of a variant; "a+b" combines two variants that set different dimensions' shapes
+    (the autotuner's 3D choice with its 2D one)."""
+    parts = [p for p in variant.split("+") if p and p != "default"]
+    out: dict = {}
+    for p in parts:
+        if p not in VARIANTS:
+            raise ValueError(f"unknown library variant {p!r}")
+        for k, v in VARIANTS[p].items():
+            if k in out and out[k] != v:
+                raise ValueError(f"variants in {variant!r} disagree on {k}")
+            out[k] = v
+    return out
+
+
+def canonical(variant: str) -> str:
+    """One name per combination: the non-default parts in VARIANTS order, joined by "+"."""
+    parts = {p for p in variant.split("+") if p and p != "default"}
+    variant_macros(variant)  # validates
+    names = [v for v in VARIANTS if v in parts]
+    return "+".join(names) if names else "default"
+
+
 def lib_path(variant: str = "default") -> Path:
-    return LIB if variant == "default" else HERE / f"libsph_b300_{variant}.so"
+    variant = canonical(variant)
+    return LIB if variant == "default" else HERE / f"libsph_b300_{variant.replace('+', '_')}.so"
 
 
 def nvcc() -> str:
@@ -51,15 +77,16 @@ def _stale(lib: Path = LIB) -> bool:
 
 def build(force: bool = False, verbose: bool = False, variant: str = "default") -> Path:
     """Compile every source into one shared library next to the package (one tile-shape variant)."""
+    variant = canonical(variant)
     lib = lib_path(variant)
     if not force and not _stale(lib):
         return lib
     objs = []
-    bdir = HERE / "_build" / variant
+    bdir = HERE / "_build" / variant.replace("+", "_")
     bdir.mkdir(parents=True, exist_ok=True)
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
                     "--expt-relaxed-constexpr", "-I", str(INCLUDE)]
-    flags += [f"-D{k}={v}" for k, v in VARIANTS[variant].items()]
+    flags += [f"-D{k}={v}" for k, v in variant_macros(variant).items()]
     if verbose:
         flags += ["-Xptxas", "-v"]
     jobs = []
