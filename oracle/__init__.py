@@ -430,5 +430,5 @@ def adjoint(scene: dict, n_steps: int, xb_T, vb_T, rb_T, x=None, v=None, rho=Non
                            _ptr(xb0, C.c_double), _ptr(vb0, C.c_double), _ptr(rb0, C.c_double), C.byref(nub),
                            _ptr(xT, C.c_double), _ptr(vT, C.c_double), _ptr(rT, C.c_double))
     if rc != 0:
-        raise ValueError("orc_adjoint: continuity mode without walls only")
+        raise ValueError("orc_adjoint: scenes without walls only")
     return dict(xb=xb0, vb=vb0, rb=rb0, nub=nub.value, x_T=xT, v_T=vT, rho_T=rT)

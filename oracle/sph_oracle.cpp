@@ -974,14 +974,27 @@ T shift_objective(const OrcParams& P, const OrcShiftLoss& o, const State<T>& S, 
 
 
 // ---------------------------------------------------------------- reverse pass (Sec. 2.2)
-// Vector-Jacobian product of one continuity-mode step without walls.  Given the adjoints
-// (xb, vb, rb) of the state after the step, overwrite them with the adjoints of the state
-// before it and add the viscosity adjoint to nub.  Each pair contribution is back-propagated
-// through its own expression graph (reverse accumulation, scatter into i and j).
-void step_reverse(const OrcParams& P, const State<double>& S, std::vector<double>& xb, std::vector<double>& vb,
+// Vector-Jacobian product of one step without walls.  Given the adjoints (xb, vb, rb) of the
+// state after the step, overwrite them with the adjoints of the state before it and add the
+// viscosity adjoint to nub.  Each pair contribution is back-propagated through its own expression
+// graph (reverse accumulation, scatter into i and j).
+// Continuity mode: rho' = rho + dt drho, so rb reaches rho directly and through drho.
+// Summation mode: the step first replaces rho by rho^_i = sum_j m_j W_ij (self term included) of
+// the step's positions, the rates see rho^, and the stored density after the step is rho^ (drho is
+// not integrated).  So rb and the rates' density adjoints both land on rho^, which passes them on
+// to the positions: x_bar_i += sum_j grad_i W_ij (rho^_bar_i m_j + rho^_bar_j m_i); the density
+// before the step does not influence the step (its adjoint is zero).
+void step_reverse(const OrcParams& P, const State<double>& S0, std::vector<double>& xb, std::vector<double>& vb,
                   std::vector<double>& rb, double& nub) {
-  const int d = S.d, N = S.N();
-  Pairs pr = pairs_of(P, S);
+  const int d = S0.d, N = S0.N();
+  const bool summation = P.density_mode == 1;
+  Pairs pr = pairs_of(P, S0);
+  State<double> Ssum;
+  if (summation) {
+    Ssum = S0;
+    density_summation(P, Ssum, pr);
+  }
+  const State<double>& S = summation ? Ssum : S0;  // the state the rates see
   const double dt = P.dt, eH2 = P.eps * (0.5 * P.H) * (0.5 * P.H);  // h = H/2
   const double Cv = 2.0 * (d + 2) * P.rho0 * S.nu[0];
   const double dCv_dnu = 2.0 * (d + 2) * P.rho0;
@@ -993,7 +1006,7 @@ void step_reverse(const OrcParams& P, const State<double>& S, std::vector<double
       vt[(size_t)i * d + k] = vb[(size_t)i * d + k] + dt * xb[(size_t)i * d + k];
       abar[(size_t)i * d + k] = dt * vt[(size_t)i * d + k];
     }
-    bbar[i] = dt * rb[i];
+    bbar[i] = summation ? 0.0 : dt * rb[i];  // drho is integrated in continuity mode only
   }
   int nthreads = 1;
 #ifdef _OPENMP
@@ -1133,6 +1146,23 @@ void step_reverse(const OrcParams& P, const State<double>& S, std::vector<double
     rb[i] = rb[i] + sr;
   }
   for (int t = 0; t < nthreads; ++t) nub += Nub[t];
+  if (summation) {
+    // rb now holds the adjoint of rho^; its chain to the positions, gathered per particle
+    std::vector<double> cx((size_t)N * d, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < S.nf; ++i) {
+      for (int64_t t = pr.off[i]; t < pr.off[i + 1]; ++t) {
+        const int j = pr.nb[t];
+        double r[3], G[3];
+        for (int k = 0; k < d; ++k) r[k] = min_image(P, k, S.x[(size_t)i * d + k] - S.x[(size_t)j * d + k]);
+        kernel_gradW<double>(P, r, G);
+        const double c = rb[i] * S.m[j] + rb[j] * S.m[i];
+        for (int k = 0; k < d; ++k) cx[(size_t)i * d + k] += c * G[k];
+      }
+    }
+    for (size_t k = 0; k < cx.size(); ++k) xb[k] += cx[k];
+    std::fill(rb.begin(), rb.end(), 0.0);
+  }
 }
 
 template <class T>
@@ -1526,14 +1556,15 @@ int orc_jvp(const OrcParams* P, int nf, int nw, const double* x, const double* v
   return 0;
 }
 
-// Reverse pass of an n-step continuity-mode rollout without walls from a float64 state.
+// Reverse pass of an n-step rollout without walls (continuity or summation density) from a
+// float64 state.
 // All intermediate states are stored (no checkpointing: the oracle favours plainness).
 // Inputs: adjoints of the final state; outputs: adjoints of the initial state and of nu.
 int orc_adjoint(const OrcParams* P, int nf, int nw, const double* x, const double* v, const double* rho,
                 const float* m, double nu, int n_steps, const double* xb_T, const double* vb_T,
                 const double* rb_T, double* xb_0, double* vb_0, double* rb_0, double* nub,
                 double* x_T, double* v_T, double* rho_T) {
-  if (nw != 0 || P->density_mode != 0) return -1;
+  if (nw != 0) return -1;
   if (renormalised(*P) || P->shift > 0.0) return -4;  // no derivative of these terms
   int N = nf, d = P->dim;
   State<double> S;

@@ -6,8 +6,8 @@ import pytest
 import sph_inputs as si
 
 
-def _setup(n_side=16, seed=2):
-    s = si.taylor_green_2d(n_side, seed=seed)
+def _setup(n_side=16, seed=2, density_mode=0):
+    s = si.taylor_green_2d(n_side, seed=seed, density_mode=density_mode)
     N, d = s["n_fluid"], 2
     rng = np.random.default_rng(seed)
     x0 = s["x"].astype(np.float64)
@@ -18,9 +18,12 @@ def _setup(n_side=16, seed=2):
     return s, x0, v0, r0, yb, tan
 
 
+@pytest.mark.parametrize("density_mode", [0, 1])
 @pytest.mark.parametrize("steps", [1, 6])
-def test_vjp_matches_dual_number_jvp(orc, steps):
-    s, x0, v0, r0, yb, tan = _setup()
+def test_vjp_matches_dual_number_jvp(orc, steps, density_mode):
+    """Continuity and summation density (the latter: rho^ = sum_j m_j W_ij of the positions feeds
+    the rates and is the stored density, so the position adjoint gains its chain)."""
+    s, x0, v0, r0, yb, tan = _setup(density_mode=density_mode)
     dnu = 0.7
     adj = orc.adjoint(s, steps, *yb, x=x0, v=v0, rho=r0)
     out = orc.jvp(s, steps, x0, v0, r0, *tan, dnu=dnu)
@@ -33,8 +36,9 @@ def test_vjp_matches_dual_number_jvp(orc, steps):
     assert np.array_equal(adj["x_T"], xo)
 
 
-def test_vjp_matches_central_differences(orc):
-    s, x0, v0, r0, yb, tan = _setup(seed=5)
+@pytest.mark.parametrize("density_mode", [0, 1])
+def test_vjp_matches_central_differences(orc, density_mode):
+    s, x0, v0, r0, yb, tan = _setup(seed=5, density_mode=density_mode)
     steps = 4
     adj = orc.adjoint(s, steps, *yb, x=x0, v=v0, rho=r0)
     nu = s["params"]["nu"]
@@ -70,3 +74,28 @@ def test_loss_seed_position_mse(orc):
         return ((xx - xt) ** 2).sum() / N
     fd = (loss(v0 + h * dv) - loss(v0 - h * dv)) / (2 * h)
     assert abs(fd - (adj["vb"] * dv).sum()) < 1e-6 * abs(fd)
+
+
+def test_summation_adjoint_ignores_the_input_density_and_has_the_density_chain(orc):
+    """Summation mode: the density before the first step does not influence the rollout (its
+    adjoint is exactly zero), and dropping the rho^ -> x chain changes the position adjoint (the
+    chain is not negligible), which central differences in x alone confirm."""
+    s, x0, v0, r0, yb, tan = _setup(seed=7, density_mode=1)
+    steps = 3
+    adj = orc.adjoint(s, steps, *yb, x=x0, v=v0, rho=r0)
+    assert np.all(adj["rb"] == 0.0)
+    a1 = orc.rollout64(s, steps, x0, v0, r0)
+    a2 = orc.rollout64(s, steps, x0, v0, r0 * 1.01)
+    assert all(np.array_equal(p, q) for p, q in zip(a1, a2))
+
+    def L(eps):
+        xo, vo, ro = orc.rollout64(s, steps, x0 + eps * tan[0], v0, r0)
+        return (yb[0] * xo).sum() + (yb[1] * vo).sum() + (yb[2] * ro).sum()
+    h = 1e-6
+    fd = (L(h) - L(-h)) / (2 * h)
+    an = (adj["xb"] * tan[0]).sum()
+    assert abs(fd - an) < 1e-6 * abs(an)
+    # the same rollout in continuity mode has a different position adjoint
+    sc = dict(s, params=dict(s["params"], density_mode=0))
+    adj_c = orc.adjoint(sc, steps, *yb, x=x0, v=v0, rho=r0)
+    assert np.linalg.norm(adj_c["xb"] - adj["xb"]) > 1e-3 * np.linalg.norm(adj["xb"])
