@@ -298,12 +298,17 @@ def run_adjoint(sph, torch, spec, steps, ckpt):
                 **info)
 
 
-def _stream_specs(n_scenes: int, rate: float, seed: int = 0):
+def _stream_specs(n_scenes: int, rate: float, seed: int = 0, skin_over_H: float = 0.0):
+    """The served stream's requests; both the plain path and the server get the same scenes (with
+    the same Verlet skin, a neighbour-search setting that leaves the neighbours unchanged)."""
     import sph_inputs as si
+    from paper_2507_21684_b300 import tune
     reqs = si.served_stream(n_scenes=n_scenes, rate_hz=rate, seed=seed)
     out = []
     for r in reqs:
         sp = si.taylor_green_2d(r.n_side, seed=r.seed)
+        if skin_over_H > 0:
+            sp = tune.with_skin(sp, skin_over_H)
         out.append((r, sp))
     return out
 
@@ -499,9 +504,30 @@ def main():
     ap.add_argument("--no-tile-tune", action="store_true", help="use the default tile shape (no variant timing)")
     ap.add_argument("--variant", default="default", help="--profile-run: tile-shape variant of the library")
     ap.add_argument("--stream-rates", type=float, nargs="*", default=[20.0, 80.0, 320.0])
+    ap.add_argument("--stream-skin", type=float, default=0.1,
+                    help="Verlet skin (fraction of H) of every request of the served stream, plain and served alike")
+    ap.add_argument("--stream-only", action="store_true", help="only the served stream (plain vs served)")
     args = ap.parse_args()
     ws, rank = _dist()
     import sph_inputs as si
+
+    if args.stream_only:  # the served mixed-size stream alone (plain vs served)
+        import torch  # noqa: F401  (device memory for the library's allocator hook)
+        from paper_2507_21684_b300 import build as sbuild
+        sbuild.build(variant=args.variant)
+        import paper_2507_21684_b300 as sph
+        sph.select_variant(args.variant)
+        sph.use_torch_allocator()
+        out = {}
+        for rate in args.stream_rates:
+            reqs = _stream_specs(args.stream_scenes, rate, skin_over_H=args.stream_skin)
+            pl = run_plain(sph, reqs)
+            sv = run_served(sph, reqs)
+            out[f"{rate:g}_req_s"] = {"plain": pl, "served": sv,
+                                      "served_over_plain_throughput": sv["particle_steps_per_s"] / pl["particle_steps_per_s"],
+                                      "served_over_plain_p99": sv["p99_s"] / pl["p99_s"]}
+        print(json.dumps({"stream_only": True, "skin_over_H": args.stream_skin, "by_rate": out}))
+        return
 
     if args.profile_run:
         import torch
@@ -822,7 +848,7 @@ def run_extras(sph, torch, tune, args, variant, peaks, tiles2=None) -> dict:
     extras["adjoint_128"]["cpu_baseline"] = cpu_adjoint_baseline(dict(sa, name="adjoint_128"), 200, 20)
     stream = {}
     for rate in args.stream_rates:
-        reqs = _stream_specs(args.stream_scenes, rate)
+        reqs = _stream_specs(args.stream_scenes, rate, skin_over_H=args.stream_skin)
         pl = run_plain(sph, reqs)
         sv = run_served(sph, reqs)
         stream[f"{rate:g}_req_s"] = {"plain": pl, "served": sv,
@@ -831,6 +857,7 @@ def run_extras(sph, torch, tune, args, variant, peaks, tiles2=None) -> dict:
     extras["served_stream"] = {
         "scenes": args.stream_scenes, "sizes": "log-uniform in [1024, 262144] (square lattices)",
         "steps": "uniform in [50, 500]", "adjoint_fraction": 0.2, "arrivals": "Poisson", "by_rate": stream,
+        "verlet_skin_over_H": args.stream_skin,
         "metric": "fluid particle-steps/s over the makespan; latency = completion - arrival"}
     return extras
 

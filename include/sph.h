@@ -248,8 +248,11 @@ SPH_API int sph_rollout(sph_scene* scene, int n_steps, int ckpt_every);
  * of the final state (xbar_T, vbar_T, rhobar_T; NULL = zero) return those of the initial state
  * (xbar_0, vbar_0, rhobar_0; NULL = skip) and of the viscosity (nubar: host doubles, one per
  * scene of a batch; may be NULL).
- * Segments between checkpoints are recomputed forward and replayed backwards.  Continuity
- * mode without wall particles only (SPH_EINVAL otherwise, or without a preceding rollout).
+ * Segments between checkpoints are recomputed forward and replayed backwards.  Continuity or
+ * summation density (Sec. 2.3); in summation mode each step's density sum_j m_j W_ij of the
+ * step's positions is differentiated too (its adjoint passes to the positions, and rhobar_0 is
+ * zero: the step overwrites the density it is given).  Scenes without wall particles only
+ * (SPH_EINVAL otherwise, or without a preceding rollout).
  * The scene's state is left at the end of the rollout. */
 SPH_API int sph_adjoint(sph_scene* scene, const float* xbar_T, const float* vbar_T, const float* rhobar_T,
                 float* xbar_0, float* vbar_0, float* rhobar_0, double* nubar, int ptr_is_device);

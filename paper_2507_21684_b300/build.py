@@ -24,11 +24,17 @@ VARIANTS = {
               "SPH_TILE2_CAP": 512},
     "small3": {"SPH_TILE3_TP": 16, "SPH_TILE3_LANES": 8, "SPH_TILE3_LIST": 18, "SPH_TILE3_THREADS": 128,
                "SPH_TILE3_CAP": 768},
-    # how lines are cut into tiles: whole cells in 2D, balanced tiles in 3D (the defaults swapped)
+    # how lines are cut into tiles: whole cells in 2D, whole cells in 3D (the defaults swapped)
     "cells2": {"SPH_TILE2_CUT": 0},
-    "balanced3": {"SPH_TILE3_CUT": 1},
-    # the 3D sweep on the staged traversal instead of the warp-per-tile one
-    "staged3": {"SPH_W3": 0},
+    "cells3": {"SPH_TILE3_CUT": 0},
+    # the 3D sweep on the staged traversal instead of the warp-per-tile one (with its whole-cell cut)
+    "staged3": {"SPH_W3": 0, "SPH_TILE3_CUT": 0},
+    # the warp-per-tile 3D sweep: register budget (CTAs per SM), hit-list length, when the lists
+    # are evaluated
+    "w3occ5": {"SPH_W_MINB": 5},
+    "w3l48": {"SPH_W_LIST": 48, "SPH_W_MINB": 5},
+    "w3line": {"SPH_W_LINE_DRAIN": 1, "SPH_W_LIST": 24},
+    "w3line5": {"SPH_W_LINE_DRAIN": 1, "SPH_W_LIST": 24, "SPH_W_MINB": 5},
 }
 
 

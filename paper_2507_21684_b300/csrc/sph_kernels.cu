@@ -173,7 +173,7 @@ __global__ void k_adj_seed(const DevSeg* __restrict__ segs, int N, Arrays fw, co
   float4 xb = XB[k], vb = VB[k];
   float xbs[3] = {xb.x, xb.y, xb.z}, vbs[3] = {vb.x, vb.y, vb.z}, ab[3];
   for (int q = 0; q < 3; ++q) ab[q] = (q < D) ? s.dt * fmaf(s.dt, xbs[q], vbs[q]) : 0.f;
-  float bb = s.dt * xb.w;
+  float bb = s.density_mode == 0 ? s.dt * xb.w : 0.f;  // drho is integrated in continuity mode only
   float pp = tait_slope(s, r.rho, r.p);
   if (D == 2) {
     S[k] = make_float4(ab[0], ab[1], bb, pp);

@@ -17,6 +17,7 @@
 
 #include "sph_passes.cuh"
 #include "sph_tilebuild.cuh"
+#include "sph_warptiles.cuh"
 
 namespace sph {
 
@@ -1449,6 +1450,60 @@ struct AdjPass {
   }
 };
 
+// Summation mode: the step's density rho^_i = sum_j m_j W_ij (self term included) feeds the rates
+// and is the stored density after the step (it is not integrated), so its adjoint, which the
+// adjoint sweep leaves in XB.w (the seed's rhobar' plus the rates' density terms), passes on to
+// the positions,
+//   x_bar_i += sum_j grad_i W_ij (rhobar_i m_j + rhobar_j m_i),
+// and the density before the step, which the step overwrites, gets a zero adjoint.  A second
+// gathered pass after the adjoint sweep (it needs the neighbours' complete rhobar_j).
+template <int D, int KERN>
+struct AdjDensityPass {
+  struct Body {
+    const DevSeg* s;
+    float xi[D], rb_i, m_i;
+    float gx[D];
+    __device__ __forceinline__ void pair_at(const float* xs, const PD<D>& pj, float4 XBj, float, int) {
+      float r[D];
+      const float r2 = diff<D>(xs, pj.x, r);
+      const float gK = s->Kg * kern_gt<KERN>(safe_q(r2, s->invH));
+      const float c = gK * fmaf(rb_i, fabsf(pj.m), XBj.w * m_i);
+#pragma unroll
+      for (int k = 0; k < D; ++k) gx[k] = fmaf(c, r[k], gx[k]);
+    }
+    template <int L>
+    __device__ __forceinline__ void reduce() {
+#pragma unroll
+      for (int k = 0; k < D; ++k) gx[k] = group_sum<L>(gx[k]);
+    }
+  };
+  const float4 *XBin, *VBin;
+  float4 *XBout, *VBout;
+  __device__ static __forceinline__ bool wants(uint32_t) { return true; }
+  __device__ __forceinline__ void skip(int, const TgtView&) {}
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ void last_cta() {}
+  __device__ __forceinline__ const float4* tex0() const { return XBin; }
+  __device__ __forceinline__ const float4* tex1() const { return VBin; }
+  __device__ __forceinline__ bool init(Body& b, const DevSeg& s, int, const TgtView& tv) {
+    b.s = &s;
+    const float4 A = tv.a.A[tv.k];
+    b.xi[0] = A.x; b.xi[1] = A.y;
+    if (D == 3) b.xi[2] = A.z;
+    b.rb_i = tv.e0[tv.k].w;
+    b.m_i = fabsf(D == 3 ? tv.a.C[tv.k].y : tv.a.B[tv.k].w);
+#pragma unroll
+    for (int k = 0; k < D; ++k) b.gx[k] = 0.f;
+    return true;
+  }
+  __device__ __forceinline__ void finish(Body& b, const DevSeg&, int i, const TgtView& tv) {
+    const float4 xb = tv.e0[tv.k];
+    const float gz = D == 3 ? b.gx[D - 1] : 0.f;
+    XBout[i] = make_float4(xb.x + b.gx[0], xb.y + b.gx[1], D == 3 ? xb.z + gz : xb.z, 0.f);
+    VBout[i] = tv.e1[tv.k];
+  }
+};
+
 // ================================================================== shifting by optimisation
 // The paper's differentiable particle shifting / density-target sampling: the objective
 //   L = (1/n) sum_i [ w_c (1 - c_i)^2 + w_g |g_i|^2 + w_r (rho_i - t(x_i))^2 + w_p sum_{|x_ij| < a dp_i} (a dp_i - |x_ij|)^2 ]
@@ -2008,6 +2063,23 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, (D == 3 && RENORM ? 768 :
   pass.grad = grad;
   run_tiles<D, RENORM ? 1 : 0, 0>(t, tiles, ntiles, RENORM ? grad : nullptr, nullptr, pass);
 }
+// The same sweep on the warp-per-tile traversal (one thread per target).
+template <int D, int KERN, bool INTEGRATE, bool RENORM>
+__global__ void __launch_bounds__(WCfg::THREADS, SPH_W_MINB) k_sweep_w(TravArgs t, const Tile* tiles,
+                                                                            const int* ntiles, Arrays out,
+                                                                            RateOut ro, Displace disp,
+                                                                            const float4* grad) {
+  wait_prior_grid();
+  SweepPass<D, KERN, INTEGRATE, RENORM> pass;
+  pass.a = t.a;
+  pass.out = out;
+  pass.ro = ro;
+  pass.status = t.status;
+  pass.disp = disp;
+  pass.grad = grad;
+  run_warp_tiles<D, true, RENORM, false>(t, tiles, ntiles, RENORM ? grad : nullptr, nullptr, pass,
+                                         [&](long long pairs) { end_tiles(t, pass, pairs); });
+}
 template <int D, int KERN>
 __global__ void __launch_bounds__(TileCfg<D>::THREADS, (D == 3 ? 768 : 1024) / TileCfg<D>::THREADS) k_shift_t(TravArgs t, const Tile* tiles, const int* ntiles, Arrays out,
                                                  Displace disp) {
@@ -2045,6 +2117,20 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, 512 / TileCfg<D>::THREADS
   pass.VBout = VBout;
   pass.nu_part = nu_part;
   run_tiles<D, (D == 2 ? 1 : 2), 0>(t, tiles, ntiles, S, D == 2 ? nullptr : Pp, pass);
+}
+
+template <int D, int KERN>
+__global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_adj_dens_t(TravArgs t, const Tile* tiles, const int* ntiles,
+                                                                     const float4* XBin, const float4* VBin,
+                                                                     float4* XBout, float4* VBout) {
+  wait_prior_grid();
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the next kernel of the adjoint step may launch
+  AdjDensityPass<D, KERN> pass;
+  pass.XBin = XBin;
+  pass.VBin = VBin;
+  pass.XBout = XBout;
+  pass.VBout = VBout;
+  run_tiles<D, 1, 0>(t, tiles, ntiles, XBin, nullptr, pass);
 }
 
 // Per-scene deterministic sums of per-particle float partials (block s sums scene s, fixed order).
@@ -2138,6 +2224,15 @@ void launch_grad_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int 
 template <int D, int KERN, bool INTEGRATE, bool RENORM>
 static void launch_sweep_any(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
                              const RateOut& ro, const Displace& disp, const float4* grad, cudaStream_t st) {
+  if constexpr (D == 3 && SPH_W3) {
+    if (t.N <= kWMaxParticles) {
+      auto fw = k_sweep_w<D, KERN, INTEGRATE, RENORM>;
+      PdlLaunch L(pass_grid((const void*)fw, (tiles_upper + WCfg::WARPS - 1) / WCfg::WARPS), WCfg::THREADS,
+                  warp_tiles_smem(), st);
+      cudaLaunchKernelEx(&L.cfg, fw, t, tiles, ntiles, out, ro, disp, grad);
+      return;
+    }
+  }
   auto fn = k_sweep_t<D, KERN, INTEGRATE, RENORM>;
   PdlLaunch L(pass_grid((const void*)fn, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(RENORM ? 1 : 0), st);
   cudaLaunchKernelEx(&L.cfg, fn, t, tiles, ntiles, out, ro, disp, grad);
@@ -2174,6 +2269,12 @@ void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int t
                   float* nu_part, cudaStream_t st) {
   PdlLaunch L(pass_grid((const void*)k_adj_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(D == 2 ? 1 : 2), st);
   cudaLaunchKernelEx(&L.cfg, k_adj_t<D, KERN>, t, tiles, ntiles, S, Pp, XBin, VBin, XBout, VBout, nu_part);
+}
+template <int D, int KERN>
+void launch_adj_dens_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* XBin,
+                       const float4* VBin, float4* XBout, float4* VBout, cudaStream_t st) {
+  PdlLaunch L(pass_grid((const void*)k_adj_dens_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(1), st);
+  cudaLaunchKernelEx(&L.cfg, k_adj_dens_t<D, KERN>, t, tiles, ntiles, XBin, VBin, XBout, VBout);
 }
 // Shifting-by-optimisation passes: the objective (P1, P2) and its gradient (P3, P4; with `out`, the
 // descent step).  Buffers: S1, S2, XB, G (float4 x N), V, Lp (N).
@@ -2259,6 +2360,19 @@ cudaError_t configure_passes() {
   SPH_ATTR(3, (k_varsupport<3, 0>), pass_smem<3>(1)) SPH_ATTR(3, (k_varsupport<3, 1>), pass_smem<3>(1))
   SPH_ATTR(2, (k_adj_t<2, 0>), pass_smem<2>(1)) SPH_ATTR(2, (k_adj_t<2, 1>), pass_smem<2>(1))
   SPH_ATTR(3, (k_adj_t<3, 0>), pass_smem<3>(2)) SPH_ATTR(3, (k_adj_t<3, 1>), pass_smem<3>(2))
+  SPH_ATTR(2, (k_adj_dens_t<2, 0>), pass_smem<2>(1)) SPH_ATTR(2, (k_adj_dens_t<2, 1>), pass_smem<2>(1))
+  SPH_ATTR(3, (k_adj_dens_t<3, 0>), pass_smem<3>(1)) SPH_ATTR(3, (k_adj_dens_t<3, 1>), pass_smem<3>(1))
+#define SPH_WATTR(fn)                                                                                            \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                                 (int)warp_tiles_smem());                                           \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributePreferredSharedMemoryCarveout,   \
+                                                 warp_tiles_carveout());                                            \
+  if (e == cudaSuccess) set_occ((const void*)fn, warp_tiles_smem(), WCfg::THREADS);
+  SPH_WATTR((k_sweep_w<3, 0, true, false>)) SPH_WATTR((k_sweep_w<3, 1, true, false>))
+  SPH_WATTR((k_sweep_w<3, 0, false, false>)) SPH_WATTR((k_sweep_w<3, 1, false, false>))
+  SPH_WATTR((k_sweep_w<3, 0, true, true>)) SPH_WATTR((k_sweep_w<3, 1, true, true>))
+  SPH_WATTR((k_sweep_w<3, 0, false, true>)) SPH_WATTR((k_sweep_w<3, 1, false, true>))
+#undef SPH_WATTR
 #undef SPH_ATTR
   return e;
 }
@@ -2291,7 +2405,9 @@ SPH_INST_PD(3)
   template void launch_rates_t<D, K>(const TravArgs&, const Tile*, const int*, int, const RateOut&, const float4*, \
                                      cudaStream_t);                                                          \
   template void launch_adj_t<D, K>(const TravArgs&, const Tile*, const int*, int, const float4*, const float*,  \
-                                   const float4*, const float4*, float4*, float4*, float*, cudaStream_t);
+                                   const float4*, const float4*, float4*, float4*, float*, cudaStream_t);      \
+  template void launch_adj_dens_t<D, K>(const TravArgs&, const Tile*, const int*, int, const float4*,          \
+                                        const float4*, float4*, float4*, cudaStream_t);
 SPH_INST_PDK(2, 0)
 SPH_INST_PDK(2, 1)
 SPH_INST_PDK(3, 0)

@@ -1126,6 +1126,18 @@ void Scene::adjoint_backward(int L, int K) {
     CKL();
     q = 1 - q;
     launches += 3;  // seed, adjoint sweep, segment sums
+    if (summation) {  // the density adjoint left in XB.w passes to the positions
+      if (D == 2) {
+        if (kern == 0) launch_adj_dens_t<2, 0>(t, cells.tiles, cells.ntiles, tiles_upper, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
+        else launch_adj_dens_t<2, 1>(t, cells.tiles, cells.ntiles, tiles_upper, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
+      } else {
+        if (kern == 0) launch_adj_dens_t<3, 0>(t, cells.tiles, cells.ntiles, tiles_upper, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
+        else launch_adj_dens_t<3, 1>(t, cells.tiles, cells.ntiles, tiles_upper, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
+      }
+      CKL();
+      q = 1 - q;
+      ++launches;
+    }
     if (s % K == 0) {  // the step's rebuild permuted the state: back to the previous order
       launch_adj_unpermute(N, slot.perm, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
       CKL();
@@ -1176,7 +1188,7 @@ void Scene::adjoint_part(int part, int L, int K) {
 void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb0, float* vb0, float* rb0, double* nub,
                     int is_dev) {
   if (!tape_valid) einval("sph_adjoint needs a preceding sph_rollout on this scene");
-  if (any_walls || summation) einval("the adjoint supports continuity mode without wall particles");
+  if (any_walls) einval("the adjoint supports scenes without wall particles");
   const int n = tape_n, k = tape_k;
   alloc_tape(k);
   launches = 0;

@@ -6,8 +6,9 @@
 // forward requests keep their particle state resident in one packed batch (segments): every
 // iteration advances all of them with the same launches (one per stage); requests that arrive
 // while others run join at the next iteration boundary, finished ones leave, and the batch is
-// re-packed on the device (no round trip through the host).  Adjoint requests run on a second
-// stream and worker, so their work overlaps with the forward batch on the device.
+// re-packed on the device (no round trip through the host).  Adjoint requests run on a pool of
+// workers with a stream each, so they overlap with one another and with the forward batch on the
+// device (one adjoint scene of the served sizes fills a fraction of the GPU).
 // Every scene's arithmetic is independent of the others in the batch and every step rebuilds the
 // cells, so a served result is bitwise the result of running that scene alone (with the cells
 // rebuilt every step).
@@ -68,12 +69,14 @@ struct Request {
   double nubar = 0, loss = 0;
 };
 
+constexpr int kAdjWorkers = 3;  // adjoint requests in flight at once
+
 struct Server {
   size_t budget = 0;
   int max_active = 0;
   int device = 0;
-  cudaStream_t st_fwd = nullptr, st_adj = nullptr;
-  std::thread th_fwd, th_adj;
+  cudaStream_t st_fwd = nullptr, st_adj[kAdjWorkers] = {};
+  std::thread th_fwd, th_adj[kAdjWorkers];
   std::mutex mu;
   std::condition_variable cv_work, cv_adj, cv_done;
   bool stop = false;
@@ -283,7 +286,7 @@ struct Server {
     }
   }
 
-  void adjoint_loop() {
+  void adjoint_loop(int w) {
     cudaSetDevice(device);
     while (true) {
       std::shared_ptr<Request> r;
@@ -303,7 +306,7 @@ struct Server {
         double m = 16.0;
         for (float c : r->x) m = std::max(m, (double)std::fabs(c));
         sc.setup_checked({r->p}, {r->nf}, {r->nw}, {m});
-        sc.bind_stream(st_adj);
+        sc.bind_stream(st_adj[w]);
         sc.use_graphs = false;  // a one-off scene: capturing graphs would cost more than it saves
         sc.alloc_all();
         sc.upload(0, r->x.data(), r->v.data(), r->rho.data(), r->mass.data(), 0);
@@ -364,9 +367,9 @@ int sph_server_create(size_t hbm_budget_bytes, int max_active, sph_server** out)
     s.max_active = max_active;
     CK(cudaGetDevice(&s.device));
     CK(cudaStreamCreateWithFlags(&s.st_fwd, cudaStreamNonBlocking));
-    CK(cudaStreamCreateWithFlags(&s.st_adj, cudaStreamNonBlocking));
+    for (int w = 0; w < sph::kAdjWorkers; ++w) CK(cudaStreamCreateWithFlags(&s.st_adj[w], cudaStreamNonBlocking));
     s.th_fwd = std::thread([&s] { s.forward_loop(); });
-    s.th_adj = std::thread([&s] { s.adjoint_loop(); });
+    for (int w = 0; w < sph::kAdjWorkers; ++w) s.th_adj[w] = std::thread([&s, w] { s.adjoint_loop(w); });
     *out = sv;
   } catch (const Fail& f) {
     return f.code;
@@ -391,10 +394,11 @@ int sph_submit(sph_server* sv, const sph_request* rq, uint64_t* ticket) {
     sph::set_err("sph_submit: bad particle counts or dimension");
     return SPH_EINVAL;
   }
-  if (rq->mode == SPH_REQ_ADJOINT && (r->nw != 0 || rq->params.density_mode != SPH_DENSITY_CONTINUITY ||
-                                      rq->params.diffusion != SPH_DIFFUSION_MC || rq->params.shift > 0.f)) {
+  if (rq->mode == SPH_REQ_ADJOINT &&
+      (r->nw != 0 || (rq->params.density_mode == SPH_DENSITY_CONTINUITY && rq->params.diffusion != SPH_DIFFUSION_MC) ||
+       rq->params.shift > 0.f)) {
     // (no walls, so the wall treatment does not matter)
-    sph::set_err("sph_submit: adjoint requests need continuity mode, the MC diffusion, no shifting and no wall particles");
+    sph::set_err("sph_submit: adjoint requests need no wall particles, no shifting and, in continuity mode, the MC diffusion");
     return SPH_EINVAL;
   }
   const size_t nd = (size_t)r->n * r->d;
@@ -507,12 +511,16 @@ void sph_server_destroy(sph_server* sv) {
   s.cv_work.notify_all();
   s.cv_adj.notify_all();
   if (s.th_fwd.joinable()) s.th_fwd.join();
-  if (s.th_adj.joinable()) s.th_adj.join();
+  for (auto& th : s.th_adj)
+    if (th.joinable()) th.join();
   s.batch.reset();
   cudaStreamSynchronize(s.st_fwd);
-  cudaStreamSynchronize(s.st_adj);
   cudaStreamDestroy(s.st_fwd);
-  cudaStreamDestroy(s.st_adj);
+  for (auto& st : s.st_adj) {
+    if (!st) continue;
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
   delete sv;
 }
 

@@ -46,12 +46,20 @@ struct Tile {
 #define SPH_TILE3_CAP 1024
 #endif
 
+// SPH_W3: the 3D sweep (and rate evaluation) on the warp-per-tile traversal (sph_warptiles.cuh);
+// 0 keeps them on the staged traversal (a library variant, timed against it by the autotuner).
+#ifndef SPH_W3
+#define SPH_W3 1
+#endif
 // CUT: how cell lines are cut into tiles (0 whole cells, 1 balanced tiles cut between particles).
+// 3D: balanced tiles fill the warps of the warp-per-tile sweep (a warp of a whole-cell tile of
+// two cells of about 15 particles leaves a fifth of its lanes idle); whole cells with the staged
+// sweep.
 #ifndef SPH_TILE2_CUT
 #define SPH_TILE2_CUT 1
 #endif
 #ifndef SPH_TILE3_CUT
-#define SPH_TILE3_CUT 0
+#define SPH_TILE3_CUT (SPH_W3 ? 1 : 0)
 #endif
 // MINB: CTAs per SM the tiled kernels are compiled for (register budget 64K / (MINB x THREADS)).
 #ifndef SPH_TILE2_MINB

@@ -103,7 +103,9 @@ def shape_variants(dim: int) -> list:
     """The library variants whose tile shape differs for scenes of dimension `dim` (the default
     first): a variant that only sets the other dimension's shape runs the default one."""
     from . import build
-    return [v for v, d in build.VARIANTS.items() if v == "default" or any(k.startswith(f"SPH_TILE{dim}_") for k in d)]
+    return [v for v, d in build.VARIANTS.items()
+            if v == "default" or any(k.startswith(f"SPH_TILE{dim}_") or k == f"SPH_W{dim}" or
+                                     (dim == 3 and k.startswith("SPH_W_")) for k in d)]
 
 
 def tune_tiles(spec: dict, variants=None, steps: int = 100, warmup: int = 50, device: int = 0) -> dict:

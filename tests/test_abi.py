@@ -67,6 +67,23 @@ def test_tile_tuner_candidates_per_dimension():
         assert c[0] == "default" and len(set(c)) == len(c)
         for v, d in build.VARIANTS.items():
             if v != "default":
-                assert (v in c) == any(k.startswith(f"SPH_TILE{dim}_") for k in d)
+                assert (v in c) == any(k.startswith(f"SPH_TILE{dim}_") or k == f"SPH_W{dim}" or
+                                       (dim == 3 and k.startswith("SPH_W_")) for k in d)
     assert "small" in tune.shape_variants(2) and "small" not in tune.shape_variants(3)
     assert "small3" in tune.shape_variants(3) and "small3" not in tune.shape_variants(2)
+    # the staged 3D traversal is a candidate against the warp-per-tile one in 3D only
+    assert "staged3" in tune.shape_variants(3) and "staged3" not in tune.shape_variants(2)
+
+
+def test_combined_variant_names():
+    """A 3D and a 2D choice combine into one library; conflicting choices are refused."""
+    from paper_2507_21684_b300 import build
+    assert build.canonical("small+default") == "small"
+    assert build.canonical("small+small3") == build.canonical("small3+small") == "small+small3"
+    assert build.lib_path("small3+small").name == "libsph_b300_small_small3.so"
+    m = build.variant_macros("small+staged3")
+    assert m["SPH_W3"] == 0 and m["SPH_TILE2_TP"] == 32
+    with pytest.raises(ValueError):
+        build.variant_macros("lanes8+small")  # both set the 2D shape
+    with pytest.raises(ValueError):
+        build.canonical("nosuch")

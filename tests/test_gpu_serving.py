@@ -53,6 +53,40 @@ def test_served_results_equal_alone(sph):
             assert g["nubar"] == ref["nubar"]
 
 
+def test_served_with_a_skin_and_summation_adjoints_match_alone(sph):
+    """Requests with a Verlet skin (a batch rebuilds all its scenes when one needs it, so a scene
+    may be re-sorted on other steps than alone: the same neighbours summed in another order) equal
+    their results alone to rounding; adjoint requests in summation mode, on the adjoint workers,
+    equal theirs bitwise."""
+    def skinned(sp):
+        p = dict(sp["params"], skin=float(np.float32(0.1 * sp["params"]["H"])), rebuild_interval=1 << 20)
+        return dict(sp, params=p)
+    specs = [skinned(si.taylor_green_2d(n, seed=k)) for k, n in enumerate([16, 40, 24, 32])]
+    steps = [40, 61, 27, 50]
+    adj_specs = [si.taylor_green_2d(n, seed=10 + k, density_mode=1) for k, n in enumerate([16, 20, 24])]
+    with sph.Server(8 << 30, 64) as sv:
+        tickets = []
+        for sp, st in zip(specs, steps):
+            tickets.append(sv.submit(sp, st))
+            time.sleep(0.002)
+        at = [sv.submit(sp, 30, adjoint=True, ckpt_every=10) for sp in adj_specs]
+        got = [sv.wait(t) for t in tickets]
+        agot = [sv.wait(t) for t in at]
+    for sp, st, g in zip(specs, steps, got):
+        ref = _alone(sph, sp, st)
+        x0 = sp["x"].astype(np.float64)
+        dref = ref["x"].astype(np.float64) - x0
+        assert np.linalg.norm(g["x"].astype(np.float64) - x0 - dref) <= 1e-4 * np.linalg.norm(dref)
+        for k in ("v", "rho"):
+            a, b = g[k].astype(np.float64), ref[k].astype(np.float64)
+            assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b), k
+    for sp, g in zip(adj_specs, agot):
+        ref = _alone(sph, sp, 30, adjoint=True, ckpt=10)
+        for k in ("x", "v", "rho", "xbar0", "vbar0", "rhobar0"):
+            assert np.array_equal(g[k], ref[k]), k
+        assert g["nubar"] == ref["nubar"]
+
+
 def test_mixed_kinds_are_served_in_separate_batches(sph):
     """Requests of another dimension or diffusion form wait for the running batch to drain and
     then run in their own; every result is still the scene's result alone."""

@@ -26,7 +26,7 @@ np.savez(sys.argv[2], x=x, v=v, rho=r)
 """
 
 
-@pytest.mark.parametrize("variant", ["lanes8", "lanes2", "small", "small3", "cells2", "balanced3"])
+@pytest.mark.parametrize("variant", ["lanes8", "lanes2", "small", "small3", "cells2", "cells3", "staged3"])
 @pytest.mark.parametrize("case", ["dambreak_64", "tgv3d_24"])
 def test_variant_rollouts_match_oracle(orc, tmp_path, variant, case):
     from paper_2507_21684_b300 import build, tune
