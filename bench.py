@@ -41,8 +41,8 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 
 # Kernel sources whose change invalidates a stored ncu traffic figure.
-KERNEL_SOURCES = ("sph_device.cuh", "sph_tiles.cuh", "sph_tilebuild.cuh", "sph_passes.cuh", "sph_passes.cu",
-                  "sph_kernels.cuh", "sph_kernels.cu")
+KERNEL_SOURCES = ("sph_device.cuh", "sph_tiles.cuh", "sph_tilebuild.cuh", "sph_warptiles.cuh", "sph_passes.cuh",
+                  "sph_passes.cu", "sph_kernels.cuh", "sph_kernels.cu")
 
 
 def kernel_fingerprint() -> str:
@@ -545,13 +545,18 @@ def main():
                 sc = sph.scene_from(sa, stream=stream.cuda_stream)
             seed = np.full((sa["n_fluid"], 2), 1.0 / sa["n_fluid"], np.float32)
             t0 = time.perf_counter()
+            t_adj = []
             for _ in range(max(1, args.steps)):
                 sc.rollout(200, 20)
+                torch.cuda.synchronize()
+                ta = time.perf_counter()
                 sc.adjoint(seed, None, None)
-            torch.cuda.synchronize()
+                torch.cuda.synchronize()
+                t_adj.append(time.perf_counter() - ta)
             sc.close()
             print(json.dumps({"profile_run": "adjoint", "skin_over_H": args.skin or 0.0, "passes": max(1, args.steps),
-                              "s_per_pass": (time.perf_counter() - t0) / max(1, args.steps)}))
+                              "s_per_pass": (time.perf_counter() - t0) / max(1, args.steps),
+                              "adjoint_ms_min": 1e3 * min(t_adj), "adjoint_ms_median": 1e3 * statistics.median(t_adj)}))
             return
         sp = (si.dam_break(res=128, diffusion=args.diffusion, boundary=args.boundary) if args.workload == "dambreak"
               else si.taylor_green_3d(128, seed=0, diffusion=args.diffusion))
@@ -654,7 +659,9 @@ def main():
     if not args.no_extras and rank == 0:
         extras = run_extras(sph, torch, tune, args, variant, peaks, tiles2)
     if rank == 0:
-        traffic, traffic_src = stored_traffic("k_sweep_t_tgv3d_128", v3 if v3 in tune.shape_variants(3) else "default")
+        staged3 = "SPH_W3" in sbuild.variant_macros(variant) and not sbuild.variant_macros(variant)["SPH_W3"]
+        sweep_kernel = "k_sweep_t" if staged3 else "k_sweep_w"
+        traffic, traffic_src = stored_traffic(f"{sweep_kernel}_tgv3d_128", v3 if v3 in tune.shape_variants(3) else "default")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
@@ -664,7 +671,7 @@ def main():
             "rebuilds_in_timed_region": fw["rebuilds"],
             "particle_steps_per_s": spec["n_fluid"] * args.steps * ws / t_total,
             "clocks": clocks,
-            "roofline": {"bound": "alu", "kernel": "k_sweep_t<3> (fused rates + kick-drift)",
+            "roofline": {"bound": "alu", "kernel": f"{sweep_kernel}<3> (fused rates + kick-drift)",
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS,
                          "traffic": traffic,

@@ -157,8 +157,9 @@ SPH_API int sph_init(const sph_params* params, int n_fluid, int n_wall, const fl
 
 /* Batched scenes: n_scenes independent problems packed into one scene object (segments), advanced
  * by the same launches (one launch per stage for all of them; the paper's batched merging of
- * scenes, Sec. 4.1 "Computational Scaling").  All scenes must share dim, kernel, density mode,
- * skin and rebuild_interval; every other parameter is per scene.  Arrays are given per scene.
+ * scenes, Sec. 4.1 "Computational Scaling").  All scenes must share dim, kernel, density mode and
+ * rebuild_interval, and either all or none have a Verlet skin (the skins may differ); every other
+ * parameter is per scene.  Arrays are given per scene.
  * The other calls then act on the whole batch: particle rows of get_state / rates / adjoint are
  * the scenes' rows concatenated in scene order (sph_batch_info gives each scene's first row and
  * row count), and sph_adjoint writes one viscosity adjoint per scene.  Each scene's results are
@@ -318,18 +319,23 @@ SPH_API void sph_destroy(sph_scene* scene);
  * Serving: continuous batching of rollout requests on one GPU (no counterpart in the paper;
  * it serves many independent scenes the way the paper batches them, Sec. 4.1).
  *
- * A server owns two streams and two host threads.  sph_submit copies the request and queues it;
+ * A server owns a stream and a host thread for the forward batch and one of each per adjoint
+ * worker (three).  sph_submit copies the request and queues it;
  * requests are admitted in arrival order while the estimated device bytes of all admitted
  * requests stay within hbm_budget_bytes and at most max_active run at once.  Admitted forward
  * rollouts keep their particle state resident in one packed batch that is advanced with shared
  * launches; arrivals join and finished requests leave at step-chunk boundaries (the batch is
  * re-packed on the device).  Adjoint requests (forward rollout with checkpoints, then the reverse
  * pass for the loss L = (1/N) sum_i |x_i^T - x~_i|^2 with target positions x~, Sec. 4.1) run on
- * the second stream concurrently.  The server steps without graphs (every step rebuilds), so a
- * served result is bitwise the result of the scene alone with cells rebuilt every step.
+ * a pool of adjoint workers (one stream each) concurrently.  The server launches the batch's steps
+ * without graphs; without a Verlet skin every step rebuilds the cells, so a served result is
+ * bitwise the result of the scene alone; with a skin the batch rebuilds all its scenes when the
+ * device finds that one of them needs it, so a served scene may be re-sorted at other steps than
+ * alone (the same neighbours, its sums in another order: float rounding).
  * Forward requests share the batch only with requests of the same dim, kernel, density mode,
- * diffusion form, shifting on or off, wall treatment, skin and rebuild_interval; one of another kind waits, in
- * arrival order, until the running batch has drained.
+ * diffusion form, shifting on or off, wall treatment, rebuild_interval and with a skin or without
+ * (the skins may differ); one of another kind waits, in arrival order, until the running batch has
+ * drained.
  * A scene of the batch that becomes unstable fails alone (SPH_EUNSTABLE from sph_wait); the others
  * continue.  Results stay with the server until sph_wait returns them (once per ticket). */
 #define SPH_REQ_FORWARD 0

@@ -29,12 +29,16 @@ VARIANTS = {
     "cells3": {"SPH_TILE3_CUT": 0},
     # the 3D sweep on the staged traversal instead of the warp-per-tile one (with its whole-cell cut)
     "staged3": {"SPH_W3": 0, "SPH_TILE3_CUT": 0},
-    # the warp-per-tile 3D sweep: register budget (CTAs per SM), hit-list length, when the lists
-    # are evaluated
-    "w3occ5": {"SPH_W_MINB": 5},
-    "w3l48": {"SPH_W_LIST": 48, "SPH_W_MINB": 5},
-    "w3line": {"SPH_W_LINE_DRAIN": 1, "SPH_W_LIST": 24},
-    "w3line5": {"SPH_W_LINE_DRAIN": 1, "SPH_W_LIST": 24, "SPH_W_MINB": 5},
+    # the warp-per-tile 3D sweep with hit rings of 32 entries, or 8 candidate loads in flight per
+    # step of the test loop
+    "w3r32": {"SPH_W_LIST": 32},
+    "w3u8": {"SPH_W_UNROLL": 8},
+    # the adjoint sweep with twice the tile shape's threads per target (registers for the default
+    # CTAs per SM, or for 4 CTAs per SM)
+    "adjx2": {"SPH_ADJ_LANES_X": 2},
+    "adjx2r": {"SPH_ADJ_LANES_X": 2, "SPH_ADJ_MINB": 4},
+    # the cooperative rebuild on one CTA per SM (a cheaper launch on the steps that rebuild nothing)
+    "rb1": {"SPH_RB_CTAS_PER_SM": 1},
 }
 
 

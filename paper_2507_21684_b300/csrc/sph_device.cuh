@@ -73,6 +73,7 @@ struct DevSeg {
   float cs[3];             // cell edge (FP32) of the folded frame
   float trimR2;            // squared reach used to skip neighbour cells (H + skin/2 + margins)
   float invcs[3];          // FP32 reciprocal cell edge (fast path of the cell key)
+  float inv_half2;         // 1 / (skin/2 - margin)^2: displacement scale of the rebuild check (0: no skin)
 };
 
 // ---------------------------------------------------------------- Wendland kernels

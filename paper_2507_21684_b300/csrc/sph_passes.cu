@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(256) k_tiles(const DevSeg* __restrict__ segs, 
 }
 
 // ================================================================== staged particle data
-template <int D, int E>
-__device__ __forceinline__ PD<D> smem_pd(const TileSmem<D, E>& sm, int k) {
+template <int D, int E, int LN>
+__device__ __forceinline__ PD<D> smem_pd(const TileSmem<D, E, LN>& sm, int k) {
   PD<D> r;
   const float4 A = sm.A[k], B = sm.B[k];
   if (D == 2) {
@@ -83,22 +83,23 @@ __device__ __forceinline__ PD<D> smem_pd(const TileSmem<D, E>& sm, int k) {
 // axes take the box length off the target (periodic images on the upper side).
 // SELF: 0 = exclude r^2 == 0 (gradient terms vanish there anyway), 1 = exclude by index,
 // 2 = exact FP64 predicate in the guard band (pair export).
-template <int D, int E, int SELF, class Body>
-__device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s, const Arrays& a, int i, int ccol,
+template <int D, int E, int SELF, class Body, int LN>
+__device__ __forceinline__ int gather_staged(TileSmem<D, E, LN>& sm, const DevSeg& s, const Arrays& a, int i, int ccol,
                                              const float* xt0, const float* face_lo, const float* face_hi,
                                              Body& body) {
   using Cfg = TileCfg<D>;
   constexpr int CAP = Cfg::CAP;
-  const int lane = threadIdx.x % Cfg::LANES;
+  constexpr int THREADS = TileSmem<D, E, LN>::THREADS;
+  const int lane = threadIdx.x % LN;
   unsigned short* list = sm.list + threadIdx.x;
   int cnt = 0, npair = 0;
   const float H2 = s.H2;
   const float R2 = s.trimR2;
   auto drain = [&]() {
     for (int e = 0; e < cnt; ++e) {
-      const unsigned code = list[e * Cfg::THREADS];
+      const unsigned code = list[e * THREADS];
       const int k = (int)(code & 0x1fffu);  // bits 0..12: staged index (CAP <= 8192)
-      PD<D> pj = smem_pd<D, E>(sm, k);
+      PD<D> pj = smem_pd(sm, k);
       // periodic image of the entry: the target takes off the box length on the flagged axes
       // (an exact shift: the target lies in the upper half of the box on those axes)
       float xs[D];
@@ -118,7 +119,7 @@ __device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s
       float pp = 0.f;
       if (E > 0) ex = sm.E[k];
       if (E > 1) pp = sm.E[CAP + k].x;
-      body.pair_at(xs, pj, ex, pp, SELF == 2 ? staged_gidx<D, E>(sm, k) : 0);
+      body.pair_at(xs, pj, ex, pp, SELF == 2 ? staged_gidx(sm, k) : 0);
     }
     npair += cnt;
     cnt = 0;
@@ -136,7 +137,7 @@ __device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s
   // j, j + LANES, ...): [lo, hi) in staged order, mid = start of the right periodic image (the
   // target takes off L in x from there on), and the line's y/z image bits.  The loop over lines
   // then fetches each line's run with two shuffles instead of every lane redoing the setup.
-  constexpr int NL = Cfg::NL, LANES = Cfg::LANES;
+  constexpr int NL = Cfg::NL, LANES = LN;
   constexpr int NSLOT = (NL + LANES - 1) / LANES;
   static_assert(NSLOT <= 2, "a lane sets up at most two lines");
   const unsigned gmask = (LANES == 32 ? 0xffffffffu : ((1u << LANES) - 1u)) << ((threadIdx.x & 31) & ~(LANES - 1));
@@ -151,7 +152,7 @@ __device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s
       const float dyz = (dy < 0 ? fl[1] : dy > 0 ? fh[1] : 0.f) + (dz < 0 ? fl[2] : dz > 0 ? fh[2] : 0.f);
       if (dyz < R2) {
         const bool need_left = fl[0] + dyz < R2, need_right = fh[0] + dyz < R2;
-        constexpr int NCOL = TileSmem<D, E>::NCOL;
+        constexpr int NCOL = TileSmem<D, E, LN>::NCOL;
         const int lo = sm.colstart[l * NCOL + (need_left ? ccol - 1 : ccol)];
         const int hi = sm.colstart[l * NCOL + (need_right ? ccol + 2 : ccol + 1)];
         const bool wrap_right = need_right && (sm.colbase + ccol + 1 >= s.n[0]);
@@ -185,7 +186,7 @@ __device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s
         tx -= s.L[0];
         shift_bits |= 1u << 13;
       }
-      for (int k0 = b + lane; k0 < en; k0 += 4 * Cfg::LANES) {
+      for (int k0 = b + lane; k0 < en; k0 += 4 * LN) {
         if (cnt > Cfg::LIST - 4) drain();
         if constexpr (D == 3 && SELF == 0) {
           // branch-free in 3D (-1 % there, +1.5 % in 2D): every slot is tested (an index past the
@@ -194,18 +195,18 @@ __device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s
           // is the same as the branching form's
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int k = k0 + u * Cfg::LANES;
+            const int k = k0 + u * LN;
             const int kc = min(k, en - 1);
             const float4 P = sm.A[kc];
             const float dx = tx - P.x, dy2 = ty - P.y, dz2 = tz - P.z;
             const float r2 = fmaf(dz2, dz2, fmaf(dy2, dy2, dx * dx));
-            list[cnt * Cfg::THREADS] = (unsigned short)(kc | shift_bits);
+            list[cnt * THREADS] = (unsigned short)(kc | shift_bits);
             cnt += (k < en && r2 < H2 && r2 > 0.f) ? 1 : 0;
           }
         } else {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int k = k0 + u * Cfg::LANES;
+            const int k = k0 + u * LN;
             if (k < en) {
               const float4 P = sm.A[k];
               const float dx = tx - P.x, dy2 = ty - P.y;
@@ -218,17 +219,17 @@ __device__ __forceinline__ int gather_staged(TileSmem<D, E>& sm, const DevSeg& s
               if (SELF == 2) {
                 in = r2 < s.band_hi;
                 if (in) {
-                  const int gj = staged_gidx<D, E>(sm, k);
+                  const int gj = staged_gidx(sm, k);
                   in = gj != i;
                   if (in && r2 >= s.band_lo) in = exact_pair<D>(s, a, i, gj);
                 }
               } else if (SELF == 1) {
-                in = r2 < H2 && (r2 > 0.f || staged_gidx<D, E>(sm, k) != i);
+                in = r2 < H2 && (r2 > 0.f || staged_gidx(sm, k) != i);
               } else {
                 in = r2 < H2 && r2 > 0.f;
               }
               if (in) {
-                list[cnt * Cfg::THREADS] = (unsigned short)(k | shift_bits);
+                list[cnt * THREADS] = (unsigned short)(k | shift_bits);
                 ++cnt;
               }
             }
@@ -315,16 +316,16 @@ __device__ __forceinline__ double group_sum(double v) {
 // global memory waits before it reads any neighbour.  A tile without a target of the pass does not wait: the fused sweep's
 // skip touches nothing.  (Only wall records change: the fluid entries and the target cache, whose
 // wall targets the sweep does not use, stay valid.)
-template <int D, int E, int SELF, bool COH, class Pass>
-__device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileSmem<D, E>& sm,
+template <int D, int E, int SELF, bool COH, class Pass, int LN>
+__device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileSmem<D, E, LN>& sm,
                                          const float4* __restrict__ extra0, const float* __restrict__ extra1,
                                          Pass& pass, const unsigned* gate = nullptr, unsigned gate_n = 0,
                                          uint4* plan = nullptr, int gate_ready = -1) {
   using Cfg = TileCfg<D>;
   __shared__ int s_ready;
   const DevSeg& s = t.segs[T.seg];
-  const int tgt = threadIdx.x / Cfg::LANES;
-  const int lane = threadIdx.x % Cfg::LANES;
+  const int tgt = threadIdx.x / LN;
+  const int lane = threadIdx.x % LN;
   const int i = T.p0 + tgt;
   const bool valid = i < T.p1;
   // (gate_ready: the caller's reading of the gate, taken before a barrier that precedes every load
@@ -359,7 +360,7 @@ __device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileS
   if (gate && !s_ready && (stg == 0 || (stg == 1 && seen))) {  // uniform over the CTA (barrier results)
     if (threadIdx.x == 0) gate_wait(gate, gate_n, t.status);
     __syncthreads();
-    if (stg == 1) restage_walls<D, E>(sm, t.a, extra0, extra1);
+    if (stg == 1) restage_walls(sm, t.a, extra0, extra1);
   }
   const TgtView tv{sm.tc.view(), sm.tc.E0, sm.tc.E1, tgt};
   int np = 0;
@@ -388,7 +389,7 @@ __device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileS
         np = gather_global<D, SELF, COH>(s, t.a, t.keys, t.cell_off, extra0, extra1, i, xi, body);
     }
     __syncwarp();
-    body.template reduce<Cfg::LANES>();
+    body.template reduce<LN>();
     if (valid && lane == 0) pass.finish(body, s, i, tv);
   } else if (valid && lane == 0) {
     pass.skip(i, tv);
@@ -425,12 +426,12 @@ __device__ __forceinline__ void end_tiles(const TravArgs& t, Pass& pass, long lo
 // Common skeleton of a tiled pass: tiles are handed out dynamically (one atomic per CTA and tile)
 // after a first tile per CTA by block index: load balance whatever the occupancy and the tile
 // sizes, and no atomic on the first tile's path.  A list selects a subset of the tiles.
-template <int D, int E, int SELF, class Pass>
+template <int D, int E, int SELF, class Pass, int LN = TileCfg<D>::LANES>
 __device__ __forceinline__ void run_tiles(const TravArgs& t, const Tile* __restrict__ tiles, const int* __restrict__ ntiles,
                                           const float4* __restrict__ extra0, const float* __restrict__ extra1,
                                           Pass& pass, const int* __restrict__ tile_list = nullptr) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  TileSmem<D, E>& sm = *reinterpret_cast<TileSmem<D, E>*>(smraw);
+  TileSmem<D, E, LN>& sm = *reinterpret_cast<TileSmem<D, E, LN>*>(smraw);
   __shared__ int s_tile;
   const int nt = *ntiles;
   long long pairs_cta = 0;
@@ -1097,7 +1098,7 @@ struct SweepPass {
           const float e0 = me.x[0] - xb.x, e1 = me.x[1] - xb.y, e2 = me.x[D - 1] - xb.z;
           d2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
         }
-        dmax = fmaxf(dmax, d2 * disp.inv_r2);
+        dmax = fmaxf(dmax, d2 * s.inv_half2);
       }
       bool bad = !(me.rho > 0.5f * s.rho0 && me.rho < 2.f * s.rho0);
 #pragma unroll
@@ -1251,7 +1252,7 @@ struct ShiftPass {
         const float e0 = me.x[0] - xb.x, e1 = me.x[1] - xb.y, e2 = me.x[D - 1] - xb.z;
         d2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
       }
-      dmax = fmaxf(dmax, d2 * disp.inv_r2);
+      dmax = fmaxf(dmax, d2 * s.inv_half2);
     }
     store_pd<D>(out, i, me);
     store_cold<D>(out, i, c);
@@ -1317,6 +1318,25 @@ struct PairPass {
 };
 
 // ================================================================== adjoint sweep (Sec. 2.2)
+// Threads per target of the adjoint sweep: SPH_ADJ_LANES_X times the tile shape's (the same tiles
+// as the forward passes; more lanes split a target's candidates further, for the small scenes of
+// adjoint workloads where the launch has few targets per SM), and the CTAs per SM its registers
+// are budgeted for.
+#ifndef SPH_ADJ_LANES_X
+#define SPH_ADJ_LANES_X 1
+#endif
+template <int D>
+constexpr int adj_lanes() {
+  constexpr int l = TileCfg<D>::LANES * SPH_ADJ_LANES_X;
+  return (l > 32 || TileCfg<D>::TP * l > 1024) ? TileCfg<D>::LANES : l;
+}
+template <int D>
+constexpr int adj_threads() { return TileCfg<D>::TP * adj_lanes<D>(); }
+#ifndef SPH_ADJ_MINB
+#define SPH_ADJ_MINB 0
+#endif
+template <int D>
+constexpr int adj_minb() { return SPH_ADJ_MINB > 0 ? SPH_ADJ_MINB : (512 / adj_threads<D>() > 0 ? 512 / adj_threads<D>() : 1); }
 // For pair (i, j) the step's pair terms add alpha_ab r_ab to a_a and beta_ab to drho_a
 // (a = self, b = other).  With seeds abar = dt vtilde, bbar = dt rhobar' of the self particle,
 // Phi_ab = alpha_ab (abar_a . r_ab) + bbar_a beta_ab; the gather at i adds the derivatives of
@@ -2102,7 +2122,7 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_pairs
   run_tiles<D, 0, 2>(t, tiles, ntiles, nullptr, nullptr, pass);
 }
 template <int D, int KERN>
-__global__ void __launch_bounds__(TileCfg<D>::THREADS, 512 / TileCfg<D>::THREADS) k_adj_t(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S,
+__global__ void __launch_bounds__(adj_threads<D>(), adj_minb<D>()) k_adj_t(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S,
                                                const float* Pp, const float4* XBin, const float4* VBin, float4* XBout,
                                                float4* VBout, float* nu_part) {
   wait_prior_grid();
@@ -2116,7 +2136,7 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, 512 / TileCfg<D>::THREADS
   pass.XBout = XBout;
   pass.VBout = VBout;
   pass.nu_part = nu_part;
-  run_tiles<D, (D == 2 ? 1 : 2), 0>(t, tiles, ntiles, S, D == 2 ? nullptr : Pp, pass);
+  run_tiles<D, (D == 2 ? 1 : 2), 0, AdjPass<D, KERN>, adj_lanes<D>()>(t, tiles, ntiles, S, D == 2 ? nullptr : Pp, pass);
 }
 
 template <int D, int KERN>
@@ -2134,14 +2154,31 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_adj_d
 }
 
 // Per-scene deterministic sums of per-particle float partials (block s sums scene s, fixed order).
+// The scene's partials are read as float4 (an unaligned head and tail element-wise), each thread
+// keeping four independent FP64 sums so that its loads are all in flight at once (a single chain
+// of dependent loads and FP64 adds made this launch as long as the adjoint sweep's half).
 __global__ void k_sum_segments(const float* __restrict__ part, const DevSeg* __restrict__ segs, double* __restrict__ acc) {
   wait_prior_grid();
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the next kernel of the adjoint step may launch
   __shared__ double sh[32];
   const DevSeg& s = segs[blockIdx.x];
-  double v = 0.0;
-  for (int k = s.p0 + threadIdx.x; k < s.p1; k += blockDim.x) v += (double)part[k];
-  double tot = block_sum(v, sh);
+  const int p0 = s.p0, p1 = s.p1;
+  const int a0 = min(p1, (p0 + 3) & ~3);  // first element on a 16-byte boundary (part is 256-byte aligned)
+  const int n4 = (p1 - a0) >> 2;
+  const int t0 = a0 + 4 * n4;             // the tail after the last whole float4
+  const float4* __restrict__ q = reinterpret_cast<const float4*>(part + a0);
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+#pragma unroll 4
+  for (int k = threadIdx.x; k < n4; k += blockDim.x) {
+    const float4 x = __ldg(q + k);
+    v0 += (double)x.x;
+    v1 += (double)x.y;
+    v2 += (double)x.z;
+    v3 += (double)x.w;
+  }
+  if ((int)threadIdx.x < a0 - p0) v0 += (double)part[p0 + threadIdx.x];
+  if ((int)threadIdx.x < p1 - t0) v1 += (double)part[t0 + threadIdx.x];
+  double tot = block_sum((v0 + v1) + (v2 + v3), sh);
   if (threadIdx.x == 0) acc[blockIdx.x] += tot;
 }
 
@@ -2267,7 +2304,8 @@ template <int D, int KERN>
 void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* S,
                   const float* Pp, const float4* XBin, const float4* VBin, float4* XBout, float4* VBout,
                   float* nu_part, cudaStream_t st) {
-  PdlLaunch L(pass_grid((const void*)k_adj_t<D, KERN>, tiles_upper), TileCfg<D>::THREADS, pass_smem<D>(D == 2 ? 1 : 2), st);
+  PdlLaunch L(pass_grid((const void*)k_adj_t<D, KERN>, tiles_upper), adj_threads<D>(),
+              tile_smem_bytes<D, (D == 2 ? 1 : 2), adj_lanes<D>()>(), st);
   cudaLaunchKernelEx(&L.cfg, k_adj_t<D, KERN>, t, tiles, ntiles, S, Pp, XBin, VBin, XBout, VBout, nu_part);
 }
 template <int D, int KERN>
@@ -2358,8 +2396,14 @@ cudaError_t configure_passes() {
   SPH_ATTR(2, (k_pairs_t<2, true>), pass_smem<2>(0)) SPH_ATTR(3, (k_pairs_t<3, true>), pass_smem<3>(0))
   SPH_ATTR(2, (k_varsupport<2, 0>), pass_smem<2>(1)) SPH_ATTR(2, (k_varsupport<2, 1>), pass_smem<2>(1))
   SPH_ATTR(3, (k_varsupport<3, 0>), pass_smem<3>(1)) SPH_ATTR(3, (k_varsupport<3, 1>), pass_smem<3>(1))
-  SPH_ATTR(2, (k_adj_t<2, 0>), pass_smem<2>(1)) SPH_ATTR(2, (k_adj_t<2, 1>), pass_smem<2>(1))
-  SPH_ATTR(3, (k_adj_t<3, 0>), pass_smem<3>(2)) SPH_ATTR(3, (k_adj_t<3, 1>), pass_smem<3>(2))
+#define SPH_AATTR(DIM, fn, bytes)                                                                                 \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
+  if (e == cudaSuccess) set_occ((const void*)fn, (bytes), adj_threads<DIM>());
+  SPH_AATTR(2, (k_adj_t<2, 0>), (tile_smem_bytes<2, 1, adj_lanes<2>()>()))
+  SPH_AATTR(2, (k_adj_t<2, 1>), (tile_smem_bytes<2, 1, adj_lanes<2>()>()))
+  SPH_AATTR(3, (k_adj_t<3, 0>), (tile_smem_bytes<3, 2, adj_lanes<3>()>()))
+  SPH_AATTR(3, (k_adj_t<3, 1>), (tile_smem_bytes<3, 2, adj_lanes<3>()>()))
+#undef SPH_AATTR
   SPH_ATTR(2, (k_adj_dens_t<2, 0>), pass_smem<2>(1)) SPH_ATTR(2, (k_adj_dens_t<2, 1>), pass_smem<2>(1))
   SPH_ATTR(3, (k_adj_dens_t<3, 0>), pass_smem<3>(1)) SPH_ATTR(3, (k_adj_dens_t<3, 1>), pass_smem<3>(1))
 #define SPH_WATTR(fn)                                                                                            \

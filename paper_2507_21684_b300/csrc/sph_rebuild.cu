@@ -19,13 +19,19 @@ __global__ void __launch_bounds__(kRbThreads) k_rebuild_coop(RebuildArgs r) {
 
 }  // namespace
 
+// CTAs per SM of the cooperative rebuild: more make a rebuild faster, fewer make the usual launch
+// that finds no rebuild due (every step between rebuilds) cheaper.
+#ifndef SPH_RB_CTAS_PER_SM
+#define SPH_RB_CTAS_PER_SM 2
+#endif
+
 template <int D>
 int rebuild_coop_grid() {
   int dev = 0, sms = 0, occ = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rebuild_coop<D>, kRbThreads, 0) != cudaSuccess) return 0;
-  return sms * std::min(occ, 2);
+  return sms * std::min(occ, SPH_RB_CTAS_PER_SM);
 }
 
 template <int D>

@@ -283,7 +283,7 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
   shifting = prms[0].shift > 0.f;
   mdbc = false;
   any_walls = false;
-  skin = prms[0].skin;
+  skin = 0.f;  // the largest of the scenes' skins
   interval = prms[0].rebuild_interval;
   N = 0;
   C_tot = 0;
@@ -308,8 +308,9 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
     C_tot += (int)c;
     if (nws[s] > 0) any_walls = true;
     if (nws[s] > 0 && p.boundary == 1) mdbc = true;
-    if (p.skin != skin || p.rebuild_interval != interval)
-      einval("all scenes of a batch must share skin and rebuild_interval");
+    if ((p.skin > 0.f) != (prms[0].skin > 0.f) || p.rebuild_interval != interval)
+      einval("all scenes of a batch must share rebuild_interval, and either all or none have a Verlet skin");
+    skin = std::max(skin, p.skin);
   }
   if (S >= 4096) einval("at most 4095 scenes per batch");
   static std::once_flag cfg_once;
@@ -340,9 +341,19 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
     for (int s = 0; s < S; ++s)
       for (int k = 0; k < D; ++k)
         Lmax = std::max(Lmax, std::max(std::fabs(segs[s].lo_d[k]), std::fabs(segs[s].lo_d[k] + segs[s].L_d[k])));
-    const double half = 0.5 * (double)skin - 8.0 * std::ldexp(Lmax, -23);
-    dev_policy = skin > 0.f && half > 0.0;
-    inv_r2 = dev_policy ? (float)(1.0 / (half * half)) : 0.f;
+    // per scene: its own skin sets its displacement scale (a batch rebuilds all its scenes when
+    // one of them has moved too far)
+    dev_policy = skin > 0.f;
+    inv_r2 = 0.f;
+    for (int s = 0; s < S; ++s) {
+      const double half = 0.5 * (double)prms[s].skin - 8.0 * std::ldexp(Lmax, -23);
+      if (!(half > 0.0)) dev_policy = false;
+    }
+    for (int s = 0; s < S; ++s) {
+      const double half = 0.5 * (double)prms[s].skin - 8.0 * std::ldexp(Lmax, -23);
+      segs[s].inv_half2 = dev_policy ? (float)(1.0 / (half * half)) : 0.f;
+      inv_r2 = std::max(inv_r2, segs[s].inv_half2);
+    }
     // the adjoint's forward replay first tries a rebuild every 16 steps (every step without a skin)
     replay_k = dev_policy ? 16 : 1;
   }
@@ -733,9 +744,11 @@ void Scene::host_rebuild() {
 }
 
 // One forward step on the scene's own buffers.  Eager steps rebuild every time (the host does
-// not see the displacements); captured steps of a scene with a Verlet skin decide on the device.
+// not see the displacements) unless eager_dev is set, where the device decides as in captured
+// steps (the cooperative rebuild launch needs no host decision); captured steps of a scene with
+// a Verlet skin decide on the device.
 void Scene::step_once() {
-  if (dev_policy && capturing && cells_valid) {
+  if (dev_policy && cells_valid && (capturing || (eager_dev && use_coop))) {
     if (use_coop)
       step_coop();
     else

@@ -139,6 +139,7 @@ struct Scene {
   float4* xbuild = nullptr;         // folded positions at the last build
   cudaStream_t st_body = nullptr;   // captures the rebuild body of a conditional node
   bool use_coop = false;            // decide in the sweep, rebuild in one cooperative launch
+  bool eager_dev = false;           // eager steps also take the device's rebuild decision (the server's batches)
   int coop_grid = 0;
   unsigned* d_bar = nullptr;        // grid barrier of the cooperative rebuild
   bool in_body = false;

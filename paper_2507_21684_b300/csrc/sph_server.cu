@@ -98,7 +98,7 @@ struct Server {
   // (the launches' template choices and the rebuild policy).
   static bool same_class(const sph_params& a, const sph_params& b) {
     return a.dim == b.dim && a.kernel == b.kernel && (a.density_mode == 1) == (b.density_mode == 1) &&
-           a.skin == b.skin && a.rebuild_interval == b.rebuild_interval && a.diffusion == b.diffusion &&
+           (a.skin > 0.f) == (b.skin > 0.f) && a.rebuild_interval == b.rebuild_interval && a.diffusion == b.diffusion &&
            (a.shift > 0.f) == (b.shift > 0.f) && a.boundary == b.boundary;
   }
 
@@ -160,6 +160,7 @@ struct Server {
     nb->bind_stream(st_fwd);
     nb->alloc_all();
     nb->use_graphs = false;
+    nb->eager_dev = true;  // with a Verlet skin the batch rebuilds when the device decides, not every step
     if (nb->mdbc) {
       std::vector<float> g;
       for (auto& r : next) g.insert(g.end(), r->ghost.begin(), r->ghost.end());

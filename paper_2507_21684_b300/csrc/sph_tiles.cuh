@@ -165,13 +165,16 @@ template <int D>
 constexpr int tile_cols() { return TileCfg<D>::TP + 2; }
 
 // Shared-memory layout of a staged tile.  EXTRA: number of additional float4 payloads per
-// staged particle (adjoint seeds).  Each staged line holds up to three runs in stencil order:
-// the left periodic image cell, the in-box columns (one contiguous range of sorted particles),
-// the right periodic image cell.
-template <int D, int EXTRA>
+// staged particle (adjoint seeds).  LN: threads per target of the pass (the tile shape's LANES,
+// or more for a pass that wants more parallelism on the same tiles).  Each staged line holds up
+// to three runs in stencil order: the left periodic image cell, the in-box columns (one contiguous
+// range of sorted particles), the right periodic image cell.
+template <int D, int EXTRA, int LN = TileCfg<D>::LANES>
 struct TileSmem {
   static constexpr int CAP = TileCfg<D>::CAP;
+  static constexpr int THREADS = TileCfg<D>::TP * LN;  // the pass's CTA
   static_assert(CAP <= 8192, "hit-list entries hold the staged index in 13 bits");
+  static_assert(LN >= 1 && LN <= 32 && (LN & (LN - 1)) == 0 && THREADS <= 1024, "one group of LN lanes per target");
   static_assert(TileCfg<D>::TP * TileCfg<D>::LANES == TileCfg<D>::THREADS, "one group of LANES per target");
   static constexpr int NCOL = tile_cols<D>() + 1;
   static constexpr int NL = TileCfg<D>::NL;
@@ -181,7 +184,7 @@ struct TileSmem {
   float2 C[D == 3 ? CAP : 1];
   float4 E[EXTRA > 0 ? EXTRA * CAP : 1];
   TargetCache<D> tc;
-  unsigned short list[TileCfg<D>::LIST * TileCfg<D>::THREADS];
+  unsigned short list[TileCfg<D>::LIST * THREADS];
   // From here to img: a tile's staging plan (TilePlan), which depends on the cell structure only
   alignas(16) Tile ptile;           // the tile
   int pvalid, ppad[3];              // whether the rest of the plan (the staging table) is filled
@@ -197,8 +200,8 @@ struct TileSmem {
   int img[NL][4];                   // offsets bounding the left and right periodic image cells
 };
 
-template <int D, int EXTRA>
-constexpr size_t tile_smem_bytes() { return sizeof(TileSmem<D, EXTRA>); }
+template <int D, int EXTRA, int LN = TileCfg<D>::LANES>
+constexpr size_t tile_smem_bytes() { return sizeof(TileSmem<D, EXTRA, LN>); }
 
 // A tile's staging plan in global memory, as uint4 words laid out like TileSmem from ptile to img:
 // the tile, a flag, and the staging table (column starts as staged indices, the run table and the
@@ -217,14 +220,14 @@ struct TilePlan {
 };
 
 // Copy of a plan (U4 words from the tile on) into the CTA's shared memory (all threads).
-template <int D, int EXTRA>
-__device__ __forceinline__ void load_plan(TileSmem<D, EXTRA>& sm, const uint4* __restrict__ plan) {
+template <int D, int EXTRA, int LN>
+__device__ __forceinline__ void load_plan(TileSmem<D, EXTRA, LN>& sm, const uint4* __restrict__ plan) {
   uint4* dst = reinterpret_cast<uint4*>(&sm.ptile);
   for (int e = threadIdx.x; e < TilePlan<D>::U4; e += blockDim.x) dst[e] = plan[e];
 }
 // The staging table of a staged tile into its plan, and the flag (all threads; read by later launches).
-template <int D, int EXTRA>
-__device__ __forceinline__ void store_plan(const TileSmem<D, EXTRA>& sm, uint4* __restrict__ plan) {
+template <int D, int EXTRA, int LN>
+__device__ __forceinline__ void store_plan(const TileSmem<D, EXTRA, LN>& sm, uint4* __restrict__ plan) {
   const uint4* src = reinterpret_cast<const uint4*>(&sm.ptile);
   for (int e = 3 + threadIdx.x; e < TilePlan<D>::U4; e += blockDim.x) plan[e] = src[e];
   if (threadIdx.x == 0) reinterpret_cast<int*>(plan + 2)[0] = 1;
@@ -251,9 +254,9 @@ __device__ __forceinline__ int tile_line(const DevSeg& s, const Tile& T, int l, 
 
 // Run containing staged index k: the largest r with run_s[r] <= k (run_s is non-decreasing and
 // k < total, so that run is not empty).
-template <int D, int EXTRA>
-__device__ __forceinline__ int staged_run(const TileSmem<D, EXTRA>& sm, int k) {
-  constexpr int NRUN = TileSmem<D, EXTRA>::NRUN;
+template <int D, int EXTRA, int LN>
+__device__ __forceinline__ int staged_run(const TileSmem<D, EXTRA, LN>& sm, int k) {
+  constexpr int NRUN = TileSmem<D, EXTRA, LN>::NRUN;
   int r = 0;
 #pragma unroll
   for (int step = 16; step > 0; step >>= 1)
@@ -263,8 +266,8 @@ __device__ __forceinline__ int staged_run(const TileSmem<D, EXTRA>& sm, int k) {
 
 // Stage particle k of a tile whose run table is built: its records (with the run's periodic
 // shifts) and extras.  Returns whether it is a wall particle (mass <= 0).
-template <int D, int EXTRA, bool COH>
-__device__ __forceinline__ bool stage_record(TileSmem<D, EXTRA>& sm, const Arrays& a, int k,
+template <int D, int EXTRA, bool COH, int LN>
+__device__ __forceinline__ bool stage_record(TileSmem<D, EXTRA, LN>& sm, const Arrays& a, int k,
                                              const float4* __restrict__ extra0, const float* __restrict__ extra1) {
   constexpr int CAP = TileCfg<D>::CAP;
   const int r = staged_run(sm, k);
@@ -288,8 +291,8 @@ __device__ __forceinline__ bool stage_record(TileSmem<D, EXTRA>& sm, const Array
 }
 
 // Stage the records of a tile whose staging table is in shared memory (all threads); returns 1.
-template <int D, int EXTRA, bool COH>
-__device__ __forceinline__ int stage_records(TileSmem<D, EXTRA>& sm, const Arrays& a, int total,
+template <int D, int EXTRA, bool COH, int LN>
+__device__ __forceinline__ int stage_records(TileSmem<D, EXTRA, LN>& sm, const Arrays& a, int total,
                                              const float4* __restrict__ extra0, const float* __restrict__ extra1,
                                              int* wall_seen) {
   int walls = 0;
@@ -309,13 +312,13 @@ __device__ __forceinline__ int stage_records(TileSmem<D, EXTRA>& sm, const Array
 // on the first barrier, so it costs no extra round trip).  All threads of the CTA call it.
 // wall_seen (optional): set to whether any staged particle is a wall (mass <= 0).  COH: record
 // loads through L2 (see ld_rec).
-template <int D, int EXTRA, bool COH = false>
-__device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T, const Arrays& a,
+template <int D, int EXTRA, bool COH = false, int LN = TileCfg<D>::LANES>
+__device__ int stage_tile(TileSmem<D, EXTRA, LN>& sm, const DevSeg& s, const Tile& T, const Arrays& a,
                           const int* __restrict__ cell_off, const float4* __restrict__ extra0,
                           const float* __restrict__ extra1, bool want, int* wall_seen = nullptr) {
   constexpr int NL = TileCfg<D>::NL;
-  constexpr int NCOL = TileSmem<D, EXTRA>::NCOL;
-  constexpr int NRUN = TileSmem<D, EXTRA>::NRUN;
+  constexpr int NCOL = TileSmem<D, EXTRA, LN>::NCOL;
+  constexpr int NRUN = TileSmem<D, EXTRA, LN>::NRUN;
   constexpr int CAP = TileCfg<D>::CAP;
   const int tid = threadIdx.x;
   const int nx = s.n[0];
@@ -408,8 +411,8 @@ __device__ int stage_tile(TileSmem<D, EXTRA>& sm, const DevSeg& s, const Tile& T
 
 // Stage the wall particles of a staged tile again, through L2 (their records were rewritten
 // after the first staging); the fluid entries stay.  All threads of the CTA call it.
-template <int D, int EXTRA>
-__device__ void restage_walls(TileSmem<D, EXTRA>& sm, const Arrays& a, const float4* __restrict__ extra0,
+template <int D, int EXTRA, int LN>
+__device__ void restage_walls(TileSmem<D, EXTRA, LN>& sm, const Arrays& a, const float4* __restrict__ extra0,
                               const float* __restrict__ extra1) {
   const int total = sm.total;
   for (int k = threadIdx.x; k < total; k += blockDim.x) {
@@ -420,8 +423,8 @@ __device__ void restage_walls(TileSmem<D, EXTRA>& sm, const Arrays& a, const flo
 }
 
 // Global index of staged particle k (for predicates that exclude the target by index).
-template <int D, int EXTRA>
-__device__ __forceinline__ int staged_gidx(const TileSmem<D, EXTRA>& sm, int k) {
+template <int D, int EXTRA, int LN>
+__device__ __forceinline__ int staged_gidx(const TileSmem<D, EXTRA, LN>& sm, int k) {
   const int r = staged_run(sm, k);
   return sm.run_g[r] + (k - sm.run_s[r]);
 }

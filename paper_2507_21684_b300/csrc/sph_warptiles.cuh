@@ -29,25 +29,30 @@ namespace sph {
 #define SPH_W_WARPS 4
 #endif
 #ifndef SPH_W_LIST
-#define SPH_W_LIST 32
+#define SPH_W_LIST 64
 #endif
-// SPH_W_LINE_DRAIN: evaluate the lists after every neighbour line (the records the evaluation reads
-// are then those of one line's runs, which stay in L1) instead of only when a list is full
-#ifndef SPH_W_LINE_DRAIN
-#define SPH_W_LINE_DRAIN 0
+// entries of every lane's ring evaluated at a time when one may overflow
+#ifndef SPH_W_EVAL
+#define SPH_W_EVAL (SPH_W_LIST / 2)
+#endif
+// candidates per step of the test loop (loads in flight per lane)
+#ifndef SPH_W_UNROLL
+#define SPH_W_UNROLL 4
 #endif
 // CTAs per SM the warp-traversal kernels are compiled for (register budget 64K / (MINB x THREADS))
 #ifndef SPH_W_MINB
-#define SPH_W_MINB 6
+#define SPH_W_MINB 5
 #endif
 
 struct WCfg {
   static constexpr int WARPS = SPH_W_WARPS;    // warps per CTA
   static constexpr int THREADS = 32 * WARPS;
-  static constexpr int LIST = SPH_W_LIST;      // hit-list entries per thread
-  static constexpr int UNROLL = 4;             // candidates per step of the test loop
+  static constexpr int LIST = SPH_W_LIST;      // hit-ring entries per thread
+  static constexpr int EVAL = SPH_W_EVAL;      // entries per lane evaluated at a time
+  static constexpr int UNROLL = SPH_W_UNROLL;  // candidates per step of the test loop
 };
 static_assert(WCfg::LIST > WCfg::UNROLL, "a step of the test loop must fit into a list with room");
+static_assert(WCfg::EVAL >= WCfg::UNROLL && WCfg::EVAL <= WCfg::LIST, "an evaluation frees a step's room");
 static_assert(TileCfg<3>::TP <= 32, "a warp holds one tile's targets");
 
 // Hit-list entry: neighbour index in the packed arrays (26 bits) and the shifts of the pair:
@@ -63,19 +68,30 @@ constexpr int warp_tiles_carveout() {
   return (int)((100 * (size_t)SPH_W_MINB * (warp_tiles_smem() + 1024) + 228 * 1024 - 1) / (228 * 1024));
 }
 
-// Evaluation of a lane's list: the warp iterates up to the longest list (lanes with shorter ones
-// idle), each lane loads its neighbour's records and calls body.pair_at with both ends in the
-// pair's periodic image.  Returns the entries evaluated by this lane.  EX0 / EX1: the pass stages
-// a float4 / float payload with the neighbours.
+// A lane's hit list is a ring of LIST entries (free-running counters head and tail): the tests
+// append at head, the evaluation takes entries from tail.  When some lane's ring may overflow, the
+// warp evaluates up to EVAL entries of every lane (the oldest ones) and goes on testing: the lanes
+// keep about half a ring each, so an evaluation keeps most lanes busy (evaluating every list to
+// the end whenever the fullest one is full leaves the others idle for the difference; a ring of
+// 64 with 32 per evaluation needs a third fewer evaluation steps than emptying lists of 48 on the
+// 128^3 vortex, counted on its cell lists).
+static_assert((WCfg::LIST & (WCfg::LIST - 1)) == 0, "the hit ring's length is a power of two");
+
+// Evaluation of up to `most` entries of every lane's ring: the warp iterates up to the longest
+// batch (lanes with fewer entries idle), each lane loads its neighbour's records and calls
+// body.pair_at with both ends in the pair's periodic image.  Returns the entries evaluated by this
+// lane.  EX0 / EX1: the pass stages a float4 / float payload with the neighbours.
 template <int D, bool EX0, bool EX1, class Body>
 __device__ __forceinline__ int warp_drain(const float* L, const Arrays& a, const float4* __restrict__ extra0,
-                                          const float* __restrict__ extra1, const uint32_t* list, int cnt,
-                                          const float* xt, Body& body) {
+                                          const float* __restrict__ extra1, const uint32_t* list, unsigned head,
+                                          unsigned& tail, int most, const float* xt, Body& body) {
+  constexpr unsigned MASK = WCfg::LIST - 1;
   const int lane = threadIdx.x & 31;
-  const int m = (int)__reduce_max_sync(kFull, (unsigned)cnt);
+  const int mine = min((int)(head - tail), most);
+  const int m = (int)__reduce_max_sync(kFull, (unsigned)mine);
   for (int e = 0; e < m; ++e) {
-    if (e < cnt) {
-      const uint32_t code = list[e * 32 + lane];
+    if (e < mine) {
+      const uint32_t code = list[((tail + (unsigned)e) & MASK) * 32u + lane];
       const int j = (int)(code & kWIdxMask);
       PD<D> pj = load_pd<D>(a, j);
       float xs[D];
@@ -93,28 +109,29 @@ __device__ __forceinline__ int warp_drain(const float* L, const Arrays& a, const
       body.pair_at(xs, pj, ex, pp, j);
     }
   }
-  return cnt;
+  tail += (unsigned)mine;
+  return mine;
 }
 
 // Test the candidates [g0, g1) of one run (per lane: the run of the lane's group) against this
 // lane's target (t: the target's coordinates in the run's image; sh: the shift taken off the
-// candidates' coordinates, zero unless SHIFTED), appending hits with the entry tag.  The loop is
-// warp-uniform (up to the longest run of the warp); a lane whose run is shorter tests clamped
-// indices and keeps none of them.  ZERO_OK: a pair at zero distance (the target itself) is
-// harmless to the pass (its terms vanish), so only r^2 < H^2 is tested; the caller discounts the
-// target from the pair count.  Otherwise r^2 > 0 is required as well.
+// candidates' coordinates, zero unless SHIFTED), appending hits to the lane's ring with the entry
+// tag.  The loop is warp-uniform (up to the longest run of the warp); a lane whose run is shorter
+// tests clamped indices and keeps none of them.  ZERO_OK: a pair at zero distance (the target
+// itself) is harmless to the pass (its terms vanish), so only r^2 < H^2 is tested; the caller
+// discounts the target from the pair count.  Otherwise r^2 > 0 is required as well.
 template <int D, bool SHIFTED, bool ZERO_OK, class Drain>
 __device__ __forceinline__ void warp_scan_run(const float4* __restrict__ A, int g0, int g1, const float* t,
-                                              const float* sh, uint32_t tag, float H2, uint32_t* list, int& cnt,
-                                              Drain& drain) {
+                                              const float* sh, uint32_t tag, float H2, uint32_t* list,
+                                              unsigned& head, const unsigned& tail, Drain& drain) {
   constexpr int U = WCfg::UNROLL;
+  constexpr unsigned MASK = WCfg::LIST - 1;
   const int lane = threadIdx.x & 31;
   const int len = max(g1 - g0, 0);
   const int mlen = (int)__reduce_max_sync(kFull, (unsigned)len);
   const int klast = max(g1 - 1, 0);  // a valid index for the clamped tests of a short run
-  auto test = [&](int it) {
+  auto test_p = [&](int it, float4 P) {
     const int k = g0 + it;
-    const float4 P = __ldg(A + min(k, klast));
     float px = P.x, py = P.y, pz = P.z;
     if (SHIFTED) {
       px -= sh[0];
@@ -127,17 +144,22 @@ __device__ __forceinline__ void warp_scan_run(const float4* __restrict__ A, int 
       const float dz = t[2] - pz;
       r2 = fmaf(dz, dz, r2);
     }
-    list[cnt * 32 + lane] = (uint32_t)k | tag;
-    cnt += (it < len && r2 < H2 && (ZERO_OK || r2 > 0.f)) ? 1 : 0;
+    list[(head & MASK) * 32u + lane] = (uint32_t)k | tag;
+    head += (it < len && r2 < H2 && (ZERO_OK || r2 > 0.f)) ? 1u : 0u;
   };
+  auto load = [&](int it) { return __ldg(A + min(g0 + it, klast)); };
+  auto test = [&](int it) { test_p(it, load(it)); };
   int it = 0;
   for (; it + U <= mlen; it += U) {
-    if (__any_sync(kFull, cnt > WCfg::LIST - U)) drain();
+    if (__any_sync(kFull, (int)(head - tail) > WCfg::LIST - U)) drain();
+    float4 P[U];  // all of the step's loads first, then the tests
 #pragma unroll
-    for (int u = 0; u < U; ++u) test(it + u);
+    for (int u = 0; u < U; ++u) P[u] = load(it + u);
+#pragma unroll
+    for (int u = 0; u < U; ++u) test_p(it + u, P[u]);
   }
   if (it < mlen) {
-    if (__any_sync(kFull, cnt > WCfg::LIST - U)) drain();
+    if (__any_sync(kFull, (int)(head - tail) > WCfg::LIST - U)) drain();
     for (; it < mlen; ++it) test(it);
   }
 }
@@ -188,11 +210,9 @@ __device__ __forceinline__ int warp_tile_task(const TravArgs& t, const Tile& T, 
   const float H2 = s.H2, R2 = s.trimR2;
   const int nx = s.n[0];
   const bool px = s.periodic_mask & 1;
-  int cnt = 0, np = 0;
-  auto drain = [&]() {
-    np += warp_drain<D, EX0, EX1>(L, t.a, extra0, extra1, list, cnt, xt, body);
-    cnt = 0;
-  };
+  unsigned head = 0u, tail = 0u;
+  int np = 0;
+  auto drain = [&]() { np += warp_drain<D, EX0, EX1>(L, t.a, extra0, extra1, list, head, tail, WCfg::EVAL, xt, body); };
   for (int l = 0; l < NL; ++l) {
     float tsh[2], csh[2];
     const int lc = tile_line<D>(s, T, l, tsh, csh);  // uniform over the warp
@@ -236,15 +256,15 @@ __device__ __forceinline__ int warp_tile_task(const TravArgs& t, const Tile& T, 
       int g0 = 0, g1 = 0;
       if (active && clo < 0) { g0 = t.cell_off[lc + nx - 1]; g1 = t.cell_off[lc + nx]; }
       const float shl[3] = {L[0], sh[1], sh[2]};
-      warp_scan_run<D, true, ZERO_OK>(t.a.A, g0, g1, tl, shl, tag | (1u << 26), H2, list, cnt, drain);
+      warp_scan_run<D, true, ZERO_OK>(t.a.A, g0, g1, tl, shl, tag | (1u << 26), H2, list, head, tail, drain);
     }
     // in-box columns
     {
       const int c0 = max(clo, 0), c1 = min(chi, nx);
       int g0 = 0, g1 = 0;
       if (active && c0 < c1) { g0 = t.cell_off[lc + c0]; g1 = t.cell_off[lc + c1]; }
-      if (shifted_yz) warp_scan_run<D, true, ZERO_OK>(t.a.A, g0, g1, tl, sh, tag, H2, list, cnt, drain);
-      else warp_scan_run<D, false, ZERO_OK>(t.a.A, g0, g1, tl, sh, tag, H2, list, cnt, drain);
+      if (shifted_yz) warp_scan_run<D, true, ZERO_OK>(t.a.A, g0, g1, tl, sh, tag, H2, list, head, tail, drain);
+      else warp_scan_run<D, false, ZERO_OK>(t.a.A, g0, g1, tl, sh, tag, H2, list, head, tail, drain);
     }
     // right periodic image (groups whose union ends right of the last column): the first column
     // of the line; the target takes off L
@@ -252,12 +272,11 @@ __device__ __forceinline__ int warp_tile_task(const TravArgs& t, const Tile& T, 
       int g0 = 0, g1 = 0;
       if (active && chi > nx) { g0 = t.cell_off[lc]; g1 = t.cell_off[lc + 1]; }
       const float tr[3] = {xt[0] - L[0], tl[1], tl[2]};
-      if (shifted_yz) warp_scan_run<D, true, ZERO_OK>(t.a.A, g0, g1, tr, sh, tag | (1u << 29), H2, list, cnt, drain);
-      else warp_scan_run<D, false, ZERO_OK>(t.a.A, g0, g1, tr, sh, tag | (1u << 29), H2, list, cnt, drain);
+      if (shifted_yz) warp_scan_run<D, true, ZERO_OK>(t.a.A, g0, g1, tr, sh, tag | (1u << 29), H2, list, head, tail, drain);
+      else warp_scan_run<D, false, ZERO_OK>(t.a.A, g0, g1, tr, sh, tag | (1u << 29), H2, list, head, tail, drain);
     }
-    if (SPH_W_LINE_DRAIN) drain();
   }
-  drain();
+  while (__any_sync(kFull, head != tail)) drain();
   if (ZERO_OK && active) --np;  // the target found itself
   body.template reduce<1>();
   if (valid) pass.finish(body, s, i, tv);
