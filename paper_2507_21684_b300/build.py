@@ -33,10 +33,6 @@ VARIANTS = {
     # step of the test loop
     "w3r32": {"SPH_W_LIST": 32},
     "w3u8": {"SPH_W_UNROLL": 8},
-    # the adjoint sweep with twice the tile shape's threads per target (registers for the default
-    # CTAs per SM, or for 4 CTAs per SM)
-    "adjx2": {"SPH_ADJ_LANES_X": 2},
-    "adjx2r": {"SPH_ADJ_LANES_X": 2, "SPH_ADJ_MINB": 4},
     # the cooperative rebuild on one CTA per SM (a cheaper launch on the steps that rebuild nothing)
     "rb1": {"SPH_RB_CTAS_PER_SM": 1},
 }

@@ -583,20 +583,22 @@ __global__ void __launch_bounds__(256) k_mdbc(TravArgs t, const Tile* __restrict
         if (lane >= o) incl += v;
       }
       const int total = __shfl_sync(kFull, incl, 31);
-      int ex[NC], fi[NC], nn[NC];  // every lane: each cell's offset in the walk, first particle, count
-#pragma unroll
-      for (int b = 0; b < NC; ++b) {
-        nn[b] = __shfl_sync(kFull, ccount, b);
-        ex[b] = __shfl_sync(kFull, incl, b) - nn[b];
-        fi[b] = __shfl_sync(kFull, cfirst, b);
-      }
+      const int excl = incl - ccount;
       for (int base = 0; base < total; base += 32) {
         const int idx = base + lane;
-        int j = -1;
+        // the cell holding walk position idx: the smallest b with incl_b > idx (incl is
+        // non-decreasing over the lanes, and only a non-empty cell raises it), by a binary
+        // search over the lanes' prefix sums; then that cell's first particle and offset
+        int lo = 0, hi = NC - 1;
 #pragma unroll
-        for (int b = 0; b < NC; ++b)
-          if (idx >= ex[b] && idx < ex[b] + nn[b]) j = fi[b] + (idx - ex[b]);
-        if (j < 0) continue;
+        for (int step = 0; step < 5; ++step) {  // NC <= 32
+          const int mid = (lo + hi) >> 1;
+          if (__shfl_sync(kFull, incl, mid) > idx) hi = mid;
+          else lo = mid + 1;
+        }
+        const int fb = __shfl_sync(kFull, cfirst, hi), eb = __shfl_sync(kFull, excl, hi);
+        if (idx >= total) continue;
+        const int j = fb + (idx - eb);
         const PD<D> pj = load_pd<D>(t.a, j);
         if (!(pj.m > 0.f)) continue;  // fluid only
         float r[D];

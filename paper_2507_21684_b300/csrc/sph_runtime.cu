@@ -193,6 +193,20 @@ DevSeg make_seg(const sph_params& p, int n_fluid, int cell_base, int p0, int p1,
   return s;
 }
 
+// Device bytes of the fused wall + sweep launch's task lists for one scene with walls, as
+// Scene::alloc_all sizes them (the wall-tile index list and the two plan lists), for admission.
+size_t wall_plan_bytes(const sph_params& p, int n_fluid, int n) {
+  const DevSeg g = make_seg(p, n_fluid, 0, 0, n, 16.0);
+  const long long C = (long long)g.n[0] * g.n[1] * g.n[2];
+  const long long lines = (long long)g.n[1] * g.n[2];
+  const int TP = p.dim == 2 ? TileCfg<2>::TP : TileCfg<3>::TP;
+  const bool balanced = p.dim == 2 ? TileCfg<2>::CUT : TileCfg<3>::CUT;
+  const long long upper = 3 * (((long long)n + TP - 1) / TP) + (C + TP - 1) / TP + 2 * lines + 1;
+  const long long lu = balanced ? ((long long)n + TP - 1) / TP + (C + TP - 1) / TP + lines + 1 : upper;
+  const long long u4 = p.dim == 2 ? TilePlan<2>::U4 : TilePlan<3>::U4;
+  return (size_t)(2 * 16 * u4 * std::min(lu, upper) + 4 * upper + 8);
+}
+
 static int key_bits(long long C) {
   int b = 0;
   while ((1LL << b) < C) ++b;

@@ -250,4 +250,7 @@ struct Scene {
   void stats(int64_t* steps, int64_t* rebuilds, int64_t* launches);
 };
 
+// device bytes of a scene's wall-task lists (fused wall + sweep launch), as alloc_all sizes them
+size_t wall_plan_bytes(const sph_params& p, int n_fluid, int n);
+
 }  // namespace sph

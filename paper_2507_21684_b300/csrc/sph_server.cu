@@ -41,7 +41,7 @@ static double now_s() {
 static size_t request_bytes(const sph_params& p, int n, int nw, int steps, int mode, int ckpt) {
   const size_t per = p.dim == 2 ? 256 : 320;
   size_t b = (size_t)n * per + (1 << 20);
-  if (nw > 0) b += (size_t)n * (p.dim == 2 ? 80 : 8);  // the fused wall + sweep launch's tile plans
+  if (nw > 0) b += wall_plan_bytes(p, n - nw, n);  // the fused wall + sweep launch's tile plans
   if (p.diffusion == SPH_DIFFUSION_RENORM && p.density_mode == SPH_DENSITY_CONTINUITY) b += (size_t)n * 16;
   if (mode == SPH_REQ_ADJOINT) {
     const size_t rec = p.dim == 2 ? 72 : 96;  // one copy of the records
@@ -418,7 +418,14 @@ int sph_submit(sph_server* sv, const sph_request* rq, uint64_t* ticket) {
   r->n_steps = rq->n_steps;
   r->mode = rq->mode;
   r->ckpt = rq->ckpt_every > 0 ? rq->ckpt_every : 20;
-  r->bytes = sph::request_bytes(rq->params, r->n, r->nw, r->n_steps, r->mode, r->ckpt);
+  try {  // (validates the parameters: make_seg rejects an invalid scene with SPH_EINVAL)
+    r->bytes = sph::request_bytes(rq->params, r->n, r->nw, r->n_steps, r->mode, r->ckpt);
+  } catch (const Fail& f) {
+    return f.code;
+  } catch (...) {
+    sph::set_err("sph_submit: unexpected internal exception");
+    return SPH_EINTERNAL;
+  }
   if (r->bytes > s.budget) {
     sph::set_err("sph_submit: the request alone exceeds the HBM budget");
     return SPH_EINVAL;
