@@ -29,10 +29,11 @@ VARIANTS = {
     "cells3": {"SPH_TILE3_CUT": 0},
     # the 3D sweep on the staged traversal instead of the warp-per-tile one (with its whole-cell cut)
     "staged3": {"SPH_W3": 0, "SPH_TILE3_CUT": 0},
-    # the warp-per-tile 3D sweep with hit rings of 32 entries, or 8 candidate loads in flight per
-    # step of the test loop
+    # the warp-per-tile 3D sweep with hit rings of 32 entries, or 4 / 16 candidates (2 / 8 paired
+    # loads) per step of the test loop
     "w3r32": {"SPH_W_LIST": 32},
-    "w3u8": {"SPH_W_UNROLL": 8},
+    "w3u4": {"SPH_W_UNROLL": 4},
+    "w3u16": {"SPH_W_UNROLL": 16},
     # the cooperative rebuild on one CTA per SM (a cheaper launch on the steps that rebuild nothing)
     "rb1": {"SPH_RB_CTAS_PER_SM": 1},
 }

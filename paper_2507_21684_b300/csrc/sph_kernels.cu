@@ -14,9 +14,10 @@ namespace sph {
 template <int D, bool KEYS_FROM_STATE>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, int N, int shift,
                                                             uint32_t* __restrict__ hist, int nblocks,
-                                                            const DevSeg* __restrict__ segs, Arrays a) {
+                                                            const DevSeg* __restrict__ segs, Arrays a,
+                                                            uint32_t* __restrict__ kcache) {
   __shared__ uint32_t h[256];
-  sort_hist_tile<D, KEYS_FROM_STATE>(blockIdx.x, keys, N, shift, hist, nblocks, segs, a, h);
+  sort_hist_tile<D, KEYS_FROM_STATE>(blockIdx.x, keys, N, shift, hist, nblocks, segs, a, h, kcache);
 }
 
 // Exclusive scan of n uint32 in place, 2048 per block; block totals to sums.
@@ -97,9 +98,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
                                                                const uint32_t* __restrict__ vin,
                                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                                int N, int shift, const uint32_t* __restrict__ hist,
-                                                               int nblocks, const DevSeg* __restrict__ segs, Arrays a) {
+                                                               int nblocks, const DevSeg* __restrict__ segs, Arrays a,
+                                                               const uint32_t* __restrict__ kcache) {
   __shared__ ScatterSmem sm;
-  sort_scatter_tile<D, KEYS_FROM_STATE>(blockIdx.x, kin, vin, kout, vout, N, shift, hist, nblocks, segs, a, sm);
+  sort_scatter_tile<D, KEYS_FROM_STATE>(blockIdx.x, kin, vin, kout, vout, N, shift, hist, nblocks, segs, a, sm, kcache);
 }
 
 template <int D>
@@ -293,13 +295,16 @@ void launch_sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, 
   if (N <= 0) return;
   int nb = (N + kSortTile - 1) / kSortTile;
   if (segs) {
-    k_sort_hist<D, true><<<nb, kSortThreads, 0, st>>>(kin, N, shift, hist, nb, segs, a);
+    // the first pass computes the keys from the state once: the histogram launch stores them in
+    // kin (which the first pass does not read otherwise) and the scatter launch reads them there
+    uint32_t* kc = const_cast<uint32_t*>(kin);
+    k_sort_hist<D, true><<<nb, kSortThreads, 0, st>>>(kin, N, shift, hist, nb, segs, a, kc);
     launch_exclusive_scan(hist, 256 * nb, sums, st);
-    k_sort_scatter<D, true><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, shift, hist, nb, segs, a);
+    k_sort_scatter<D, true><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, shift, hist, nb, segs, a, kc);
   } else {
-    k_sort_hist<D, false><<<nb, kSortThreads, 0, st>>>(kin, N, shift, hist, nb, segs, a);
+    k_sort_hist<D, false><<<nb, kSortThreads, 0, st>>>(kin, N, shift, hist, nb, segs, a, nullptr);
     launch_exclusive_scan(hist, 256 * nb, sums, st);
-    k_sort_scatter<D, false><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, shift, hist, nb, segs, a);
+    k_sort_scatter<D, false><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, shift, hist, nb, segs, a, nullptr);
   }
 }
 

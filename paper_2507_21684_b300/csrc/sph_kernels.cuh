@@ -14,6 +14,7 @@ struct TravArgs {
   int* status;               // device error word (bit 0: unstable state)
   unsigned long long* pair_count;  // optional: in-radius pairs of fluid particles
   int* tile_ctr;             // [0] dynamic tile counter, [1] finished CTAs (both zero between launches)
+  float* packed;             // 3D: scratch of the positions as pairs for the warp-per-tile sweep (or null)
 };
 
 // Device-side rebuild policy state of a scene (Verlet skin).

@@ -2085,6 +2085,19 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, (D == 3 && RENORM ? 768 :
   pass.grad = grad;
   run_tiles<D, RENORM ? 1 : 0, 0>(t, tiles, ntiles, RENORM ? grad : nullptr, nullptr, pass);
 }
+// The positions of the sweep's input as pairs (x_2p, x_2p+1, y_2p, y_2p+1) and (z_2p, z_2p+1) for
+// the warp-per-tile sweep's paired tests; a missing last partner lies far away.
+__global__ void k_pack_pairs3(int N, const float4* __restrict__ A, float4* __restrict__ PXY, float2* __restrict__ PZ) {
+  wait_prior_grid();
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the sweep may launch
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (N + 1) / 2) return;
+  const float4 a = __ldg(A + 2 * p);
+  const float4 b = 2 * p + 1 < N ? __ldg(A + 2 * p + 1) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+  PXY[p] = make_float4(a.x, b.x, a.y, b.y);
+  PZ[p] = make_float2(a.z, b.z);
+}
+
 // The same sweep on the warp-per-tile traversal (one thread per target).
 template <int D, int KERN, bool INTEGRATE, bool RENORM>
 __global__ void __launch_bounds__(WCfg::THREADS, SPH_W_MINB) k_sweep_w(TravArgs t, const Tile* tiles,
@@ -2264,7 +2277,11 @@ template <int D, int KERN, bool INTEGRATE, bool RENORM>
 static void launch_sweep_any(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const Arrays& out,
                              const RateOut& ro, const Displace& disp, const float4* grad, cudaStream_t st) {
   if constexpr (D == 3 && SPH_W3) {
-    if (t.N <= kWMaxParticles) {
+    if (t.N <= kWMaxParticles && t.packed) {
+      const int npairs = (t.N + 1) / 2;
+      PdlLaunch P((npairs + 255) / 256, 256, 0, st);
+      cudaLaunchKernelEx(&P.cfg, k_pack_pairs3, t.N, (const float4*)t.a.A, reinterpret_cast<float4*>(t.packed),
+                         reinterpret_cast<float2*>(t.packed + 4 * (size_t)npairs));
       auto fw = k_sweep_w<D, KERN, INTEGRATE, RENORM>;
       PdlLaunch L(pass_grid((const void*)fw, (tiles_upper + WCfg::WARPS - 1) / WCfg::WARPS), WCfg::THREADS,
                   warp_tiles_smem(), st);
@@ -2357,6 +2374,10 @@ void launch_sum_segments(const float* part, const DevSeg* segs, int S, double* a
 }
 void launch_sum_float_partials(const float* part, int n, double* acc, cudaStream_t st) {
   k_sum_float_partials<<<1, 1024, 0, st>>>(part, n, acc);
+}
+
+int sweep_kernels(int dim, long long N, const float* packed) {
+  return (dim == 3 && SPH_W3 && packed && N <= kWMaxParticles) ? 2 : 1;
 }
 
 cudaError_t configure_passes() {

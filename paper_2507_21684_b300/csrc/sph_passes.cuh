@@ -6,6 +6,8 @@
 namespace sph {
 
 cudaError_t configure_passes();
+// kernels one sweep launch call issues (the 3D warp-per-tile sweep packs the positions first)
+int sweep_kernels(int dim, long long N, const float* packed);
 void launch_debug_gate(const unsigned* gate, int* status, cudaStream_t st);
 template <int D>
 void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, const int* cell_off, Tile* tiles,

@@ -428,6 +428,7 @@ void Scene::alloc_all() {
   d_bar = (unsigned*)mem.get(sizeof(unsigned) * 2);
   CK(cudaMemsetAsync(d_bar, 0, sizeof(unsigned) * 2, st));
   xbuild = (float4*)mem.get(sizeof(float4) * (size_t)N);
+  if (D == 3) pairs_pos = (float*)mem.get(sizeof(float) * 6 * ((size_t)N + 1) / 2 + 16);
   d_nubar = (double*)mem.get(sizeof(double) * (size_t)(S + 1));
   CK(cudaMemsetAsync(d_status, 0, sizeof(int) * (4 + (size_t)S), st));
   CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long) * 2, st));
@@ -487,6 +488,7 @@ TravArgs Scene::trav(const Arrays& a, const uint32_t* keys, const int* off) cons
   t.status = d_status;
   t.pair_count = d_pairs;
   t.tile_ctr = d_tile_ctr;
+  t.packed = pairs_pos;
   return t;
 }
 
@@ -717,7 +719,7 @@ void Scene::sweep(const TravArgs& t, const Arrays& out, const Tile* tl, const in
   }
   CKL();
   prof_end();
-  ++launches;
+  launches += fused_walls ? 1 : sweep_kernels(D, N, t.packed);
 }
 
 // Particle shifting at the end of the step: from buf[cur] (the sweep's result, on cells valid

@@ -137,6 +137,7 @@ struct Scene {
   float inv_r2 = 0.f;               // 1 / (skin/2 - margin)^2
   RebuildCtl* d_ctl = nullptr;
   float4* xbuild = nullptr;         // folded positions at the last build
+  float* pairs_pos = nullptr;       // 3D: the sweep input's positions as pairs (warp-per-tile sweep)
   cudaStream_t st_body = nullptr;   // captures the rebuild body of a conditional node
   bool use_coop = false;            // decide in the sweep, rebuild in one cooperative launch
   bool eager_dev = false;           // eager steps also take the device's rebuild decision (the server's batches)

@@ -54,11 +54,13 @@ constexpr int kSortTile = kSortThreads * kSortIPT;
 
 // Histogram of one digit over sort tile `tile` (2048 keys), 256 threads; h: 256 words of shared
 // memory.  KEYS_FROM_STATE: the keys are the cell keys of the current storage order, computed
-// here (first pass of a rebuild) instead of read.
+// here (first pass of a rebuild) instead of read; with kcache they are also stored there, for the
+// pass's scatter in a later launch.
 template <int D, bool KEYS_FROM_STATE>
 __device__ __forceinline__ void sort_hist_tile(int tile, const uint32_t* __restrict__ keys, int N, int shift,
                                                uint32_t* __restrict__ hist, int nblocks,
-                                               const DevSeg* __restrict__ segs, const Arrays& a, uint32_t* h) {
+                                               const DevSeg* __restrict__ segs, const Arrays& a, uint32_t* h,
+                                               uint32_t* kcache = nullptr) {
   h[threadIdx.x] = 0;
   __syncthreads();
   const int base = tile * kSortTile;
@@ -67,6 +69,7 @@ __device__ __forceinline__ void sort_hist_tile(int tile, const uint32_t* __restr
     int i = base + k * kSortThreads + threadIdx.x;
     if (i < N) {
       const uint32_t key = KEYS_FROM_STATE ? cell_key_of<D>(segs, a, i) : keys[i];
+      if (KEYS_FROM_STATE && kcache) kcache[i] = key;
       atomicAdd(&h[(key >> shift) & 255u], 1u);
     }
   }
@@ -83,12 +86,15 @@ struct ScatterSmem {
 // Scatter of sort tile `tile` with stable ranks: warp w owns the contiguous sub-tile
 // [w*256, w*256+256) and walks it in 8 rounds of 32; within a round, equal digits are ranked by
 // lane via match_any.  hist holds the exclusive offsets of (digit, tile).  256 threads.
+// KEYS_FROM_STATE: the first pass; the keys come from kcache (stored by the histogram launch) or,
+// without it, are computed again from the state.
 template <int D, bool KEYS_FROM_STATE>
 __device__ __forceinline__ void sort_scatter_tile(int tile, const uint32_t* __restrict__ kin,
                                                   const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
                                                   uint32_t* __restrict__ vout, int N, int shift,
                                                   const uint32_t* __restrict__ hist, int nblocks,
-                                                  const DevSeg* __restrict__ segs, const Arrays& a, ScatterSmem& sm) {
+                                                  const DevSeg* __restrict__ segs, const Arrays& a, ScatterSmem& sm,
+                                                  const uint32_t* __restrict__ kcache = nullptr) {
   constexpr int W = kSortThreads / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int k = threadIdx.x; k < W * 257; k += kSortThreads) (&sm.cnt[0][0])[k] = 0;
@@ -101,7 +107,7 @@ __device__ __forceinline__ void sort_scatter_tile(int tile, const uint32_t* __re
     int i = base + r * 32 + lane;
     bool ok = i < N;
     if (KEYS_FROM_STATE) {
-      kk[r] = ok ? cell_key_of<D>(segs, a, i) : 0u;
+      kk[r] = ok ? (kcache ? kcache[i] : cell_key_of<D>(segs, a, i)) : 0u;
       vv[r] = (uint32_t)i;
     } else {
       kk[r] = ok ? kin[i] : 0u;

@@ -35,9 +35,9 @@ namespace sph {
 #ifndef SPH_W_EVAL
 #define SPH_W_EVAL (SPH_W_LIST / 2)
 #endif
-// candidates per step of the test loop (loads in flight per lane)
+// candidates per step of the test loop (two per paired load; loads in flight per lane)
 #ifndef SPH_W_UNROLL
-#define SPH_W_UNROLL 4
+#define SPH_W_UNROLL 8
 #endif
 // CTAs per SM the warp-traversal kernels are compiled for (register budget 64K / (MINB x THREADS))
 #ifndef SPH_W_MINB
@@ -114,53 +114,59 @@ __device__ __forceinline__ int warp_drain(const float* L, const Arrays& a, const
 }
 
 // Test the candidates [g0, g1) of one run (per lane: the run of the lane's group) against this
-// lane's target (t: the target's coordinates in the run's image; sh: the shift taken off the
-// candidates' coordinates, zero unless SHIFTED), appending hits to the lane's ring with the entry
-// tag.  The loop is warp-uniform (up to the longest run of the warp); a lane whose run is shorter
-// tests clamped indices and keeps none of them.  ZERO_OK: a pair at zero distance (the target
-// itself) is harmless to the pass (its terms vanish), so only r^2 < H^2 is tested; the caller
-// discounts the target from the pair count.  Otherwise r^2 > 0 is required as well.
-template <int D, bool SHIFTED, bool ZERO_OK, class Drain>
-__device__ __forceinline__ void warp_scan_run(const float4* __restrict__ A, int g0, int g1, const float* t,
-                                              const float* sh, uint32_t tag, float H2, uint32_t* list,
-                                              unsigned& head, const unsigned& tail, Drain& drain) {
-  constexpr int U = WCfg::UNROLL;
+// lane's target, two at a time: the positions come as pairs (PXY[p] = (x_2p, x_2p+1, y_2p, y_2p+1),
+// PZ[p] = (z_2p, z_2p+1), packed before the launch) and the squared distances of a pair are formed
+// with the paired FP32 instructions.  nt: minus the target's coordinates in the run's image plus
+// the shift taken off the candidates (the test's rounding near |r| = H does not matter: W and
+// grad W vanish there; the evaluation forms the pair's separation from exactly shifted operands).
+// Hits are appended to the lane's ring with the entry tag.  The loop is warp-uniform (up to the
+// longest run of the warp); a lane whose run is shorter tests clamped pairs and keeps none.
+// ZERO_OK: a pair at zero distance (the target itself) is harmless to the pass, so only
+// r^2 < H^2 is tested; the caller discounts the target from the pair count.
+template <int D, bool ZERO_OK, class Drain>
+__device__ __forceinline__ void warp_scan_run(const float4* __restrict__ PXY, const float2* __restrict__ PZ, int g0,
+                                              int g1, float2 ntx, float2 nty, float2 ntz, uint32_t tag, float H2,
+                                              uint32_t* list, unsigned& head, const unsigned& tail, Drain& drain) {
+  constexpr int U = WCfg::UNROLL / 2;  // pairs per step
   constexpr unsigned MASK = WCfg::LIST - 1;
   const int lane = threadIdx.x & 31;
-  const int len = max(g1 - g0, 0);
-  const int mlen = (int)__reduce_max_sync(kFull, (unsigned)len);
-  const int klast = max(g1 - 1, 0);  // a valid index for the clamped tests of a short run
-  auto test_p = [&](int it, float4 P) {
-    const int k = g0 + it;
-    float px = P.x, py = P.y, pz = P.z;
-    if (SHIFTED) {
-      px -= sh[0];
-      py -= sh[1];
-      if (D == 3) pz -= sh[2];
-    }
-    const float dx = t[0] - px, dy = t[1] - py;
-    float r2 = fmaf(dy, dy, dx * dx);
+  const int pa = g0 >> 1;
+  const int np = g1 > g0 ? ((g1 + 1) >> 1) - pa : 0;
+  const int mlen = (int)__reduce_max_sync(kFull, (unsigned)np);
+  const int plast = max(pa + np - 1, 0);  // a valid pair for the clamped tests of a short run
+  auto test = [&](int it, float4 Q, float2 Z) {
+    const int k0 = 2 * (pa + it);
+    const float2 dx = __fadd2_rn(make_float2(Q.x, Q.y), ntx);
+    const float2 dy = __fadd2_rn(make_float2(Q.z, Q.w), nty);
+    float2 r2 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
     if (D == 3) {
-      const float dz = t[2] - pz;
-      r2 = fmaf(dz, dz, r2);
+      const float2 dz = __fadd2_rn(Z, ntz);
+      r2 = __ffma2_rn(dz, dz, r2);
     }
-    list[(head & MASK) * 32u + lane] = (uint32_t)k | tag;
-    head += (it < len && r2 < H2 && (ZERO_OK || r2 > 0.f)) ? 1u : 0u;
+    const bool in = it < np;
+    list[(head & MASK) * 32u + lane] = (uint32_t)k0 | tag;
+    head += (in && k0 >= g0 && r2.x < H2 && (ZERO_OK || r2.x > 0.f)) ? 1u : 0u;
+    list[(head & MASK) * 32u + lane] = (uint32_t)(k0 + 1) | tag;
+    head += (in && k0 + 1 < g1 && r2.y < H2 && (ZERO_OK || r2.y > 0.f)) ? 1u : 0u;
   };
-  auto load = [&](int it) { return __ldg(A + min(g0 + it, klast)); };
-  auto test = [&](int it) { test_p(it, load(it)); };
+  auto ldq = [&](int it) { return __ldg(PXY + min(pa + it, plast)); };
+  auto ldz = [&](int it) { return D == 3 ? __ldg(PZ + min(pa + it, plast)) : make_float2(0.f, 0.f); };
   int it = 0;
   for (; it + U <= mlen; it += U) {
-    if (__any_sync(kFull, (int)(head - tail) > WCfg::LIST - U)) drain();
-    float4 P[U];  // all of the step's loads first, then the tests
+    if (__any_sync(kFull, (int)(head - tail) > WCfg::LIST - 2 * U)) drain();
+    float4 Q[U];
+    float2 Z[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) P[u] = load(it + u);
+    for (int u = 0; u < U; ++u) {
+      Q[u] = ldq(it + u);
+      Z[u] = ldz(it + u);
+    }
 #pragma unroll
-    for (int u = 0; u < U; ++u) test_p(it + u, P[u]);
+    for (int u = 0; u < U; ++u) test(it + u, Q[u], Z[u]);
   }
   if (it < mlen) {
-    if (__any_sync(kFull, (int)(head - tail) > WCfg::LIST - U)) drain();
-    for (; it < mlen; ++it) test(it);
+    if (__any_sync(kFull, (int)(head - tail) > WCfg::LIST - 2 * U)) drain();
+    for (; it < mlen; ++it) test(it, ldq(it), ldz(it));
   }
 }
 
@@ -249,31 +255,37 @@ __device__ __forceinline__ int warp_tile_task(const TravArgs& t, const Tile& T, 
     const float sh[3] = {0.f, -csh[0], D == 3 ? -csh[1] : 0.f};
     const uint32_t tag = (tsh[0] != 0.f ? 1u << 30 : 0u) | (D == 3 && tsh[1] != 0.f ? 1u << 31 : 0u) |
                          (csh[0] != 0.f ? 1u << 27 : 0u) | (D == 3 && csh[1] != 0.f ? 1u << 28 : 0u);
-    const bool shifted_yz = csh[0] != 0.f || (D == 3 && csh[1] != 0.f);  // uniform (a line property)
+    const float4* PXY = reinterpret_cast<const float4*>(t.packed);
+    const float2* PZ = reinterpret_cast<const float2*>(t.packed + 4 * (size_t)((t.N + 1) / 2));
     // left periodic image (groups whose union starts left of column 0): the last column of the
     // line, shifted down by L
     if (__any_sync(kFull, active && clo < 0)) {
       int g0 = 0, g1 = 0;
       if (active && clo < 0) { g0 = t.cell_off[lc + nx - 1]; g1 = t.cell_off[lc + nx]; }
-      const float shl[3] = {L[0], sh[1], sh[2]};
-      warp_scan_run<D, true, ZERO_OK>(t.a.A, g0, g1, tl, shl, tag | (1u << 26), H2, list, head, tail, drain);
+      warp_scan_run<D, ZERO_OK>(PXY, PZ, g0, g1, make_float2(-(tl[0] + L[0]), -(tl[0] + L[0])),
+                                make_float2(-(tl[1] + sh[1]), -(tl[1] + sh[1])),
+                                make_float2(-(tl[2] + sh[2]), -(tl[2] + sh[2])), tag | (1u << 26), H2, list, head,
+                                tail, drain);
     }
     // in-box columns
     {
       const int c0 = max(clo, 0), c1 = min(chi, nx);
       int g0 = 0, g1 = 0;
       if (active && c0 < c1) { g0 = t.cell_off[lc + c0]; g1 = t.cell_off[lc + c1]; }
-      if (shifted_yz) warp_scan_run<D, true, ZERO_OK>(t.a.A, g0, g1, tl, sh, tag, H2, list, head, tail, drain);
-      else warp_scan_run<D, false, ZERO_OK>(t.a.A, g0, g1, tl, sh, tag, H2, list, head, tail, drain);
+      warp_scan_run<D, ZERO_OK>(PXY, PZ, g0, g1, make_float2(-tl[0], -tl[0]),
+                                make_float2(-(tl[1] + sh[1]), -(tl[1] + sh[1])),
+                                make_float2(-(tl[2] + sh[2]), -(tl[2] + sh[2])), tag, H2, list, head, tail, drain);
     }
     // right periodic image (groups whose union ends right of the last column): the first column
     // of the line; the target takes off L
     if (__any_sync(kFull, active && chi > nx)) {
       int g0 = 0, g1 = 0;
       if (active && chi > nx) { g0 = t.cell_off[lc]; g1 = t.cell_off[lc + 1]; }
-      const float tr[3] = {xt[0] - L[0], tl[1], tl[2]};
-      if (shifted_yz) warp_scan_run<D, true, ZERO_OK>(t.a.A, g0, g1, tr, sh, tag | (1u << 29), H2, list, head, tail, drain);
-      else warp_scan_run<D, false, ZERO_OK>(t.a.A, g0, g1, tr, sh, tag | (1u << 29), H2, list, head, tail, drain);
+      const float txr = xt[0] - L[0];
+      warp_scan_run<D, ZERO_OK>(PXY, PZ, g0, g1, make_float2(-txr, -txr),
+                                make_float2(-(tl[1] + sh[1]), -(tl[1] + sh[1])),
+                                make_float2(-(tl[2] + sh[2]), -(tl[2] + sh[2])), tag | (1u << 29), H2, list, head,
+                                tail, drain);
     }
   }
   while (__any_sync(kFull, head != tail)) drain();

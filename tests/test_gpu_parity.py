@@ -548,6 +548,26 @@ def test_batched_scenes_bitwise_equal_alone(sph):
         assert np.array_equal(x, xb[f:f + n]) and np.array_equal(v, vb[f:f + n]) and np.array_equal(r, rb[f:f + n])
 
 
+def test_batched_3d_scenes_bitwise_equal_alone(sph, orc):
+    """3D scenes of different sizes and parameters in one batch, swept by the warp-per-tile
+    traversal (tiles of several scenes in one launch): every scene's result is the bits it gets
+    alone, and the first matches the oracle's 5-step rollout."""
+    specs = [si.taylor_green_3d(10, seed=1), si.taylor_green_3d(14, seed=2, nu=0.01),
+             si.taylor_green_3d(12, seed=3, pressure=True)]
+    with sph.Scene.batch(specs) as bt:
+        bt.step(5)
+        xb, vb, rb = bt.get_state()
+        rows = list(zip(bt.first_row, bt.rows))
+    for spec, (f, n) in zip(specs, rows):
+        with make(sph, spec) as sc:
+            sc.step(5)
+            x, v, r = sc.get_state()
+        assert np.array_equal(x, xb[f:f + n]) and np.array_equal(v, vb[f:f + n]) and np.array_equal(r, rb[f:f + n])
+    xo, vo, ro = orc.rollout(specs[0], 5)
+    f, n = rows[0]
+    check_rollout(specs[0], 5, xb[f:f + n], vb[f:f + n], rb[f:f + n], xo, vo, ro)
+
+
 def test_batched_adjoint_bitwise_equal_alone(sph):
     specs = _batch_specs()
     rng = np.random.default_rng(3)
