@@ -249,7 +249,9 @@ SPH_API int sph_rollout(sph_scene* scene, int n_steps, int ckpt_every);
  * of the final state (xbar_T, vbar_T, rhobar_T; NULL = zero) return those of the initial state
  * (xbar_0, vbar_0, rhobar_0; NULL = skip) and of the viscosity (nubar: host doubles, one per
  * scene of a batch; may be NULL).
- * Segments between checkpoints are recomputed forward and replayed backwards.  Continuity or
+ * Segments between checkpoints are recomputed forward and replayed backwards; the forward replay
+ * of the next segment runs on a second stream of the library's beside the reverse pass of the
+ * current one (two tapes of ckpt_every + 1 steps are kept).  Continuity or
  * summation density (Sec. 2.3); in summation mode each step's density sum_j m_j W_ij of the
  * step's positions is differentiated too (its adjoint passes to the positions, and rhobar_0 is
  * zero: the step overwrites the density it is given).  Scenes without wall particles only

@@ -35,8 +35,8 @@ __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol
 struct PdlLaunch {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
-  PdlLaunch(int grid, int threads, size_t smem, cudaStream_t st) {
-    cfg.gridDim = dim3(grid);
+  PdlLaunch(dim3 grid, int threads, size_t smem, cudaStream_t st) {
+    cfg.gridDim = grid;
     cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -368,6 +368,23 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   }
   __syncthreads();
   return t;
+}
+
+// Sub-bins of a cell along x (3D warp-per-tile sweep): the cell keys of such scenes carry the
+// particle's sub-bin in their low kXShift bits (cell * kXBins + bin), so the sort orders every
+// cell by sub-bin and the sweep can walk x windows of a line instead of whole cells.
+#ifndef SPH_W_XSHIFT
+#define SPH_W_XSHIFT 2
+#endif
+constexpr int kXShift = SPH_W_XSHIFT;
+constexpr int kXBins = 1 << kXShift;
+
+// Sub-bin of a folded x coordinate along its cell line: floor((x - lo_box) / cell edge * B), the
+// function the cell keys (sph_sort.cuh) and the warp-per-tile sweep's x windows share (monotone
+// in x).
+template <int B>
+__device__ __forceinline__ int line_xbin(const DevSeg& s, float x) {
+  return (int)floorf((x - s.lo[0]) * s.invcs[0] * (float)B);
 }
 
 // True when the FP32 estimate (hi - lo) / L of periodic axis q lies farther than a safety

@@ -11,7 +11,7 @@ namespace sph {
 
 // ================================================================== neighbour search
 // ---- stable LSD radix sort, 8-bit digits, 2048-key tiles (device parts in sph_sort.cuh) ----
-template <int D, bool KEYS_FROM_STATE>
+template <int D, int KEYS_FROM_STATE>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, int N, int shift,
                                                             uint32_t* __restrict__ hist, int nblocks,
                                                             const DevSeg* __restrict__ segs, Arrays a,
@@ -93,7 +93,7 @@ __global__ void k_scan_add(uint32_t* __restrict__ a, int n, const uint32_t* __re
   if (i < n) a[i] += sums[i / 2048];
 }
 
-template <int D, bool KEYS_FROM_STATE>
+template <int D, int KEYS_FROM_STATE>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
                                                                const uint32_t* __restrict__ vin,
                                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -107,9 +107,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 template <int D>
 __global__ void k_permute(const DevSeg* __restrict__ segs, int N, const uint32_t* __restrict__ perm, Arrays in,
                           Arrays out, const uint32_t* __restrict__ keys, int C, int* __restrict__ off,
-                          float4* __restrict__ xb) {
+                          float4* __restrict__ xb, int* __restrict__ boff) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k <= N) permute_one<D>(k, segs, N, perm, in, out, keys, C, off, xb);
+  if (k <= N) permute_one<D>(k, segs, N, perm, in, out, keys, C, off, xb, boff);
 }
 
 // ================================================================== state in/out
@@ -291,20 +291,27 @@ void launch_exclusive_scan(uint32_t* a, int n, uint32_t* sums, cudaStream_t st) 
 // (first pass) and the values are the storage indices.
 template <int D>
 void launch_sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, int N, int shift,
-                      uint32_t* hist, uint32_t* sums, const DevSeg* segs, const Arrays& a, cudaStream_t st) {
+                      uint32_t* hist, uint32_t* sums, const DevSeg* segs, const Arrays& a, cudaStream_t st,
+                      bool xbins) {
   if (N <= 0) return;
   int nb = (N + kSortTile - 1) / kSortTile;
   if (segs) {
     // the first pass computes the keys from the state once: the histogram launch stores them in
     // kin (which the first pass does not read otherwise) and the scatter launch reads them there
     uint32_t* kc = const_cast<uint32_t*>(kin);
-    k_sort_hist<D, true><<<nb, kSortThreads, 0, st>>>(kin, N, shift, hist, nb, segs, a, kc);
+    if (xbins && D == 3)
+      k_sort_hist<D, 2><<<nb, kSortThreads, 0, st>>>(kin, N, shift, hist, nb, segs, a, kc);
+    else
+      k_sort_hist<D, 1><<<nb, kSortThreads, 0, st>>>(kin, N, shift, hist, nb, segs, a, kc);
     launch_exclusive_scan(hist, 256 * nb, sums, st);
-    k_sort_scatter<D, true><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, shift, hist, nb, segs, a, kc);
+    if (xbins && D == 3)
+      k_sort_scatter<D, 2><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, shift, hist, nb, segs, a, kc);
+    else
+      k_sort_scatter<D, 1><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, shift, hist, nb, segs, a, kc);
   } else {
-    k_sort_hist<D, false><<<nb, kSortThreads, 0, st>>>(kin, N, shift, hist, nb, segs, a, nullptr);
+    k_sort_hist<D, 0><<<nb, kSortThreads, 0, st>>>(kin, N, shift, hist, nb, segs, a, nullptr);
     launch_exclusive_scan(hist, 256 * nb, sums, st);
-    k_sort_scatter<D, false><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, shift, hist, nb, segs, a, nullptr);
+    k_sort_scatter<D, 0><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, shift, hist, nb, segs, a, nullptr);
   }
 }
 
@@ -315,8 +322,8 @@ int sort_scratch_words(int N) {
 
 template <int D>
 void launch_permute(const DevSeg* segs, int N, const uint32_t* perm, const Arrays& in, const Arrays& out,
-                    const uint32_t* keys, int C, int* off, float4* xb, cudaStream_t st) {
-  k_permute<D><<<(N + 1 + 255) / 256, 256, 0, st>>>(segs, N, perm, in, out, keys, C, off, xb);
+                    const uint32_t* keys, int C, int* off, float4* xb, cudaStream_t st, int* boff) {
+  k_permute<D><<<(N + 1 + 255) / 256, 256, 0, st>>>(segs, N, perm, in, out, keys, C, off, xb, boff);
 }
 
 // Whole-state copy (every array of the records) in one launch.
@@ -392,10 +399,10 @@ void launch_download_range(const Arrays& a, int p0, int n, float* x, float* v, f
   template void launch_copy_range<D>(const Arrays&, int, const Arrays&, int, int, int, cudaStream_t);          \
   template void launch_download_range<D>(const Arrays&, int, int, float*, float*, float*, cudaStream_t);       \
   template void launch_permute<D>(const DevSeg*, int, const uint32_t*, const Arrays&, const Arrays&, const uint32_t*, \
-                                  int, int*, float4*, cudaStream_t);                                            \
+                                  int, int*, float4*, cudaStream_t, int*);                                      \
   template void launch_copy_state<D>(int, const Arrays&, const Arrays&, cudaStream_t);                        \
   template void launch_sort_pass<D>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int, int, uint32_t*,   \
-                                    uint32_t*, const DevSeg*, const Arrays&, cudaStream_t);                     \
+                                    uint32_t*, const DevSeg*, const Arrays&, cudaStream_t, bool);               \
   template void launch_upload<D>(const DevSeg*, int, int, int, int, const float*, const float*, const float*,   \
                                  const float*, const Arrays&, cudaStream_t);                                   \
   template void launch_download<D>(int, const Arrays&, const int*, float*, float*, float*, cudaStream_t);       \

@@ -15,6 +15,8 @@ struct TravArgs {
   unsigned long long* pair_count;  // optional: in-radius pairs of fluid particles
   int* tile_ctr;             // [0] dynamic tile counter, [1] finished CTAs (both zero between launches)
   float* packed;             // 3D: scratch of the positions as pairs for the warp-per-tile sweep (or null)
+  const int* bin_off;        // 3D: CSR offsets over cell * kXBins + x sub-bin (keys with sub-bins), or null
+  int kshift;                // keys >> kshift is the cell key (kXShift when the keys carry x sub-bins)
 };
 
 // Device-side rebuild policy state of a scene (Verlet skin).
@@ -56,14 +58,20 @@ struct RateOut {
 
 int sort_scratch_words(int N);
 void launch_exclusive_scan(uint32_t* a, int n, uint32_t* sums, cudaStream_t st);
+// One pass of the radix sort; segs set: the first pass, whose keys come from the state (cell keys,
+// with xbins the keys with x sub-bins, cell * kXBins + bin).
 template <int D>
 void launch_sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, int N, int shift,
-                      uint32_t* hist, uint32_t* sums, const DevSeg* segs, const Arrays& a, cudaStream_t st);
+                      uint32_t* hist, uint32_t* sums, const DevSeg* segs, const Arrays& a, cudaStream_t st,
+                      bool xbins = false);
+// boff set: the keys carry x sub-bins; off gets the cells' offsets (keys >> kXShift) and boff the
+// offsets over cell * kXBins + bin (C * kXBins + 1 entries).
 template <int D>
 void launch_permute(const DevSeg* segs, int N, const uint32_t* perm, const Arrays& in, const Arrays& out,
-                    const uint32_t* keys, int C, int* off, float4* xb, cudaStream_t st);
+                    const uint32_t* keys, int C, int* off, float4* xb, cudaStream_t st, int* boff = nullptr);
 template <int D>
 void launch_copy_state(int N, const Arrays& src, const Arrays& dst, cudaStream_t st);
+
 // count: 1 when a sweep follows and uses the cells (it counts towards rebuild_interval), else 0
 void launch_rebuild_decide(RebuildCtl* ctl, int interval, int count, cudaGraphConditionalHandle h, cudaStream_t st);
 template <int D>

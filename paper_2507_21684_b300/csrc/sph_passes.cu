@@ -245,11 +245,11 @@ __device__ __forceinline__ int gather_staged(TileSmem<D, E, LN>& sm, const DevSe
 // Fallback for tiles whose staged region does not fit: the target's own 3^d cells straight from
 // global memory, one thread per target (the caller lets only lane 0 of the group do this).
 template <int D, int SELF, bool COH, class Body>
-__device__ int gather_global(const DevSeg& s, const Arrays& a, const uint32_t* __restrict__ keys,
+__device__ int gather_global(const DevSeg& s, const Arrays& a, const uint32_t* __restrict__ keys, int kshift,
                              const int* __restrict__ cell_off, const float4* __restrict__ extra0,
                              const float* __restrict__ extra1, int i, const float* xi, Body& body) {
   int c[3];
-  key_coords(s, keys[i], c);
+  key_coords(s, keys[i] >> kshift, c);
   int npair = 0;
   const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
   for (int oz = zlo; oz <= zhi; ++oz)
@@ -334,7 +334,7 @@ __device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileS
   // the targets' own records go to the cache while the neighbours are staged; the key and the
   // meta word (for the skip decision) are requested now so that their loads overlap too
   fill_target_cache<D, COH>(sm.tc, t.a, pass.tex0(), pass.tex1(), T.p0, T.p1 - T.p0);
-  const int key = valid ? (int)t.keys[i] : 0;
+  const int key = valid ? (int)(t.keys[i] >> t.kshift) : 0;
   // tiles without a target of this pass (walls only, fluid only) are skipped unstaged
   const bool want = valid && lane == 0 && Pass::wants(t.a.meta[i].x);
   int seen = 1;
@@ -386,7 +386,7 @@ __device__ __forceinline__ int tile_task(const TravArgs& t, const Tile& T, TileS
       if (staged)
         np = gather_staged<D, E, SELF>(sm, s, t.a, i, ccol, xi, flo, fhi, body);
       else if (lane == 0)
-        np = gather_global<D, SELF, COH>(s, t.a, t.keys, t.cell_off, extra0, extra1, i, xi, body);
+        np = gather_global<D, SELF, COH>(s, t.a, t.keys, t.kshift, t.cell_off, extra0, extra1, i, xi, body);
     }
     __syncwarp();
     body.template reduce<LN>();
@@ -2086,14 +2086,17 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, (D == 3 && RENORM ? 768 :
   run_tiles<D, RENORM ? 1 : 0, 0>(t, tiles, ntiles, RENORM ? grad : nullptr, nullptr, pass);
 }
 // The positions of the sweep's input as pairs (x_2p, x_2p+1, y_2p, y_2p+1) and (z_2p, z_2p+1) for
-// the warp-per-tile sweep's paired tests; a missing last partner lies far away.
-__global__ void k_pack_pairs3(int N, const float4* __restrict__ A, float4* __restrict__ PXY, float2* __restrict__ PZ) {
+// the warp-per-tile sweep's paired tests; a missing last partner and the padding pairs lie far
+// away.  One thread per pair of the padded arrays (warp_pairs_stride(N) pairs each).
+__global__ void k_pack_pairs3(int N, int stride, const float4* __restrict__ A, float4* __restrict__ PXY,
+                              float2* __restrict__ PZ) {
   wait_prior_grid();
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the sweep may launch
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= (N + 1) / 2) return;
-  const float4 a = __ldg(A + 2 * p);
-  const float4 b = 2 * p + 1 < N ? __ldg(A + 2 * p + 1) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+  if (p >= stride) return;
+  const float4 far = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+  const float4 a = 2 * p < N ? __ldg(A + 2 * p) : far;
+  const float4 b = 2 * p + 1 < N ? __ldg(A + 2 * p + 1) : far;
   PXY[p] = make_float4(a.x, b.x, a.y, b.y);
   PZ[p] = make_float2(a.z, b.z);
 }
@@ -2168,33 +2171,39 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_adj_d
   run_tiles<D, 1, 0>(t, tiles, ntiles, XBin, nullptr, pass);
 }
 
-// Per-scene deterministic sums of per-particle float partials (block s sums scene s, fixed order).
-// The scene's partials are read as float4 (an unaligned head and tail element-wise), each thread
-// keeping four independent FP64 sums so that its loads are all in flight at once (a single chain
-// of dependent loads and FP64 adds made this launch as long as the adjoint sweep's half).
-__global__ void k_sum_segments(const float* __restrict__ part, const DevSeg* __restrict__ segs, double* __restrict__ acc) {
+// Per-scene sums of per-particle float partials into FP64 accumulators (acc[s] += sum over the
+// scene's particles), in a fixed order: CTA (c, s) sums chunk c (kSumChunk particles) of scene s,
+// and the CTA that finishes a scene's last chunk adds the chunk sums in chunk order.  B300's FP64
+// rate is low per SM, so the chunks spread the FP64 additions over many SMs (one CTA summing a
+// 16K-particle scene took about as long as half an adjoint sweep).  chunk: S x gridDim.x doubles;
+// ctr: S counters, zero between launches (the last CTA resets its scene's).
+constexpr int kSumChunk = 2048;
+__global__ void k_sum_segments(const float* __restrict__ part, const DevSeg* __restrict__ segs, double* __restrict__ chunk,
+                               int* __restrict__ ctr, double* __restrict__ acc) {
   wait_prior_grid();
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the next kernel of the adjoint step may launch
   __shared__ double sh[32];
-  const DevSeg& s = segs[blockIdx.x];
-  const int p0 = s.p0, p1 = s.p1;
-  const int a0 = min(p1, (p0 + 3) & ~3);  // first element on a 16-byte boundary (part is 256-byte aligned)
-  const int n4 = (p1 - a0) >> 2;
-  const int t0 = a0 + 4 * n4;             // the tail after the last whole float4
-  const float4* __restrict__ q = reinterpret_cast<const float4*>(part + a0);
-  double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-#pragma unroll 4
-  for (int k = threadIdx.x; k < n4; k += blockDim.x) {
-    const float4 x = __ldg(q + k);
-    v0 += (double)x.x;
-    v1 += (double)x.y;
-    v2 += (double)x.z;
-    v3 += (double)x.w;
+  __shared__ int last;
+  const int sg = blockIdx.y, nc = gridDim.x;
+  const DevSeg& s = segs[sg];
+  const int b = s.p0 + blockIdx.x * kSumChunk, e = min(s.p1, b + kSumChunk);
+  double v = 0.0;
+  for (int k = b + (int)threadIdx.x; k < e; k += blockDim.x) v += (double)__ldg(part + k);
+  const double tot = block_sum(v, sh);
+  if (threadIdx.x == 0) {
+    chunk[(size_t)sg * nc + blockIdx.x] = tot;
+    __threadfence();
+    last = atomicAdd(ctr + sg, 1) == nc - 1;
   }
-  if ((int)threadIdx.x < a0 - p0) v0 += (double)part[p0 + threadIdx.x];
-  if ((int)threadIdx.x < p1 - t0) v1 += (double)part[t0 + threadIdx.x];
-  double tot = block_sum((v0 + v1) + (v2 + v3), sh);
-  if (threadIdx.x == 0) acc[blockIdx.x] += tot;
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const volatile double* cv = chunk + (size_t)sg * nc;
+    double sum = 0.0;
+    for (int c = 0; c < nc; ++c) sum += cv[c];
+    acc[sg] += sum;
+    ctr[sg] = 0;
+  }
 }
 
 // Deterministic sum of per-particle float partials into an FP64 accumulator (fixed order).
@@ -2278,10 +2287,10 @@ static void launch_sweep_any(const TravArgs& t, const Tile* tiles, const int* nt
                              const RateOut& ro, const Displace& disp, const float4* grad, cudaStream_t st) {
   if constexpr (D == 3 && SPH_W3) {
     if (t.N <= kWMaxParticles && t.packed) {
-      const int npairs = (t.N + 1) / 2;
-      PdlLaunch P((npairs + 255) / 256, 256, 0, st);
-      cudaLaunchKernelEx(&P.cfg, k_pack_pairs3, t.N, (const float4*)t.a.A, reinterpret_cast<float4*>(t.packed),
-                         reinterpret_cast<float2*>(t.packed + 4 * (size_t)npairs));
+      const int stride = (int)warp_pairs_stride(t.N);
+      PdlLaunch P((stride + 255) / 256, 256, 0, st);
+      cudaLaunchKernelEx(&P.cfg, k_pack_pairs3, t.N, stride, (const float4*)t.a.A, reinterpret_cast<float4*>(t.packed),
+                         reinterpret_cast<float2*>(t.packed + 4 * (size_t)stride));
       auto fw = k_sweep_w<D, KERN, INTEGRATE, RENORM>;
       PdlLaunch L(pass_grid((const void*)fw, (tiles_upper + WCfg::WARPS - 1) / WCfg::WARPS), WCfg::THREADS,
                   warp_tiles_smem(), st);
@@ -2368,14 +2377,18 @@ void launch_unpermute3(int N, const uint2* meta, const int* orig_base, const flo
                        cudaStream_t st) {
   if (N > 0) k_unpermute3<<<(N + 255) / 256, 256, 0, st>>>(N, meta, orig_base, src, a, b, c);
 }
-void launch_sum_segments(const float* part, const DevSeg* segs, int S, double* acc, cudaStream_t st) {
-  PdlLaunch L(S, 1024, 0, st);
-  cudaLaunchKernelEx(&L.cfg, k_sum_segments, part, segs, acc);
+int sum_segments_chunks(long long max_seg_n) { return (int)std::max(1LL, (max_seg_n + kSumChunk - 1) / kSumChunk); }
+void launch_sum_segments(const float* part, const DevSeg* segs, int S, int nchunks, double* chunk, int* ctr,
+                         double* acc, cudaStream_t st) {
+  PdlLaunch L(dim3(nchunks, S), 256, 0, st);
+  cudaLaunchKernelEx(&L.cfg, k_sum_segments, part, segs, chunk, ctr, acc);
 }
 void launch_sum_float_partials(const float* part, int n, double* acc, cudaStream_t st) {
   k_sum_float_partials<<<1, 1024, 0, st>>>(part, n, acc);
 }
 
+size_t packed_pairs_floats(long long N) { return 6 * warp_pairs_stride(N); }
+bool warp_sweep(int dim, long long N) { return dim == 3 && SPH_W3 && N <= kWMaxParticles; }
 int sweep_kernels(int dim, long long N, const float* packed) {
   return (dim == 3 && SPH_W3 && packed && N <= kWMaxParticles) ? 2 : 1;
 }

@@ -8,6 +8,10 @@ namespace sph {
 cudaError_t configure_passes();
 // kernels one sweep launch call issues (the 3D warp-per-tile sweep packs the positions first)
 int sweep_kernels(int dim, long long N, const float* packed);
+// Floats of the 3D sweep's scratch of positions as pairs (TravArgs::packed) for N particles.
+size_t packed_pairs_floats(long long N);
+// Whether the sweep of a scene of this dimension and size runs on the warp-per-tile traversal.
+bool warp_sweep(int dim, long long N);
 void launch_debug_gate(const unsigned* gate, int* status, cudaStream_t st);
 template <int D>
 void launch_tiles(const DevSeg* segs, int S, const int* line_base, int n_lines, const int* cell_off, Tile* tiles,
@@ -68,6 +72,10 @@ template <int D, int KERN>
 void launch_adj_dens_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* XBin,
                        const float4* VBin, float4* XBout, float4* VBout, cudaStream_t st);
 void launch_sum_float_partials(const float* part, int n, double* acc, cudaStream_t st);
-void launch_sum_segments(const float* part, const DevSeg* segs, int S, double* acc, cudaStream_t st);
+// Per-scene FP64 sums of per-particle partials; chunk: S x nchunks doubles, ctr: S ints (zeroed
+// once, left zeroed), nchunks = sum_segments_chunks(largest scene's particle count).
+int sum_segments_chunks(long long max_seg_n);
+void launch_sum_segments(const float* part, const DevSeg* segs, int S, int nchunks, double* chunk, int* ctr,
+                         double* acc, cudaStream_t st);
 
 }  // namespace sph

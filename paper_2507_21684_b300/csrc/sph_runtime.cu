@@ -258,6 +258,11 @@ Scene::~Scene() {
     cudaStreamDestroy(st);
   }
   if (st_body) cudaStreamDestroy(st_body);
+  if (st_rep) cudaStreamDestroy(st_rep);
+  for (int b = 0; b < 2; ++b) {
+    if (ev_rep[b]) cudaEventDestroy(ev_rep[b]);
+    if (ev_free[b]) cudaEventDestroy(ev_free[b]);
+  }
 }
 
 void Scene::alloc_arrays(Arrays& a) {
@@ -378,6 +383,13 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, dev));
   use_coop = dev_policy && coop_grid > 0 && coop_attr != 0;
+  // keys with x sub-bins for the warp-per-tile sweep (not in the cooperative rebuild, so scenes
+  // that use it keep whole cells); they need kXShift more key bits
+  xorder = D == 3 && !use_coop && warp_sweep(D, N) && (long long)C_tot * kXBins < (1LL << 31);
+  if (xorder) {
+    bits = key_bits((long long)C_tot * kXBins);
+    passes = std::max(1, (bits + 7) / 8);
+  }
   if (N > 16384 * 2048) einval("too many particles for the radix sort scratch (max 33554432)");
 }
 
@@ -396,6 +408,7 @@ void Scene::alloc_all() {
   keys_sorted = kA;
   perm = vA;
   cell_off = (int*)mem.get(sizeof(int) * ((size_t)C_tot + 1));
+  if (xorder) bin_off = (int*)mem.get(sizeof(int) * ((size_t)C_tot * kXBins + 1));
   scratch = (uint32_t*)mem.get(4 * (size_t)sort_scratch_words(N));
   line_base = (int*)mem.get(sizeof(int) * S);
   CK(cudaMemcpyAsync(line_base, line_base_h.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
@@ -428,8 +441,16 @@ void Scene::alloc_all() {
   d_bar = (unsigned*)mem.get(sizeof(unsigned) * 2);
   CK(cudaMemsetAsync(d_bar, 0, sizeof(unsigned) * 2, st));
   xbuild = (float4*)mem.get(sizeof(float4) * (size_t)N);
-  if (D == 3) pairs_pos = (float*)mem.get(sizeof(float) * 6 * ((size_t)N + 1) / 2 + 16);
+  if (D == 3) pairs_pos = (float*)mem.get(sizeof(float) * packed_pairs_floats(N));
   d_nubar = (double*)mem.get(sizeof(double) * (size_t)(S + 1));
+  {
+    long long mx = 1;
+    for (const DevSeg& g : segs) mx = std::max(mx, (long long)(g.p1 - g.p0));
+    sum_nch = sum_segments_chunks(mx);
+    sum_chunk = (double*)mem.get(sizeof(double) * (size_t)S * sum_nch);
+    sum_ctr = (int*)mem.get(sizeof(int) * (size_t)S);
+    CK(cudaMemsetAsync(sum_ctr, 0, sizeof(int) * (size_t)S, st));  // left zeroed by the sums
+  }
   CK(cudaMemsetAsync(d_status, 0, sizeof(int) * (4 + (size_t)S), st));
   CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long) * 2, st));
   cells_valid = false;
@@ -478,8 +499,10 @@ void* Scene::mem_tmp(size_t bytes) {
   return tmp;
 }
 
-TravArgs Scene::trav(const Arrays& a, const uint32_t* keys, const int* off) const {
-  TravArgs t;
+TravArgs Scene::trav(const Arrays& a, const uint32_t* keys, const int* off, const int* boff) const {
+  TravArgs t{};
+  t.bin_off = boff;
+  t.kshift = xorder ? kXShift : 0;  // every rebuild of such a scene writes keys with x sub-bins
   t.segs = dseg;
   t.N = N;
   t.a = a;
@@ -533,16 +556,19 @@ void Scene::prof_end() {
 // sorted keys and the permutation (in kA/kB, vA/vB unless copied to the given tape buffers).
 std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& out, uint32_t* keys_out,
                                                uint32_t* perm_out, int* off_out, Tile* tiles_out,
-                                               int* ntiles_out) {
+                                               int* ntiles_out, int* boff_out) {
   prof_begin(1);
   uint32_t *ki = kA, *vi = vA, *ko = kB, *vo = vB;
   uint32_t* hist = scratch;
   uint32_t* sums = scratch + (sort_scratch_words(N) - 2048 - 64);
+  // boff_out (3D warp-per-tile sweep): keys with x sub-bins, so every cell comes out ordered by
+  // sub-bin, and the sub-bins' offsets beside the cells'
+  const bool xb = boff_out && D == 3;
   for (int p = 0; p < passes; ++p) {
     if (D == 2)
       launch_sort_pass<2>(ki, vi, ko, vo, N, 8 * p, hist, sums, p == 0 ? dseg : nullptr, in, st);
     else
-      launch_sort_pass<3>(ki, vi, ko, vo, N, 8 * p, hist, sums, p == 0 ? dseg : nullptr, in, st);
+      launch_sort_pass<3>(ki, vi, ko, vo, N, 8 * p, hist, sums, p == 0 ? dseg : nullptr, in, st, xb);
     CKL();
     std::swap(ki, ko);
     std::swap(vi, vo);
@@ -560,7 +586,7 @@ std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& o
   if (D == 2)
     launch_permute<2>(dseg, N, pm, in, out, ks, C_tot, off_out, xbuild, st);
   else
-    launch_permute<3>(dseg, N, pm, in, out, ks, C_tot, off_out, xbuild, st);
+    launch_permute<3>(dseg, N, pm, in, out, ks, C_tot, off_out, xbuild, st, xb ? boff_out : nullptr);
   CKL();
   build_tiles(off_out, out.meta, tiles_out ? tiles_out : tiles, ntiles_out ? ntiles_out : d_ntiles);
   prof_end();
@@ -746,7 +772,7 @@ void Scene::shift_pass() {
 // Rebuild launched by the host (eager steps, cells needed by a query): permute into the other
 // buffer; the device-side policy counters restart from this rebuild.
 void Scene::host_rebuild() {
-  auto kp = rebuild(buf[cur], buf[1 - cur], nullptr, nullptr, cell_off);
+  auto kp = rebuild(buf[cur], buf[1 - cur], nullptr, nullptr, cell_off, nullptr, nullptr, xorder ? bin_off : nullptr);
   keys_sorted = kp.first;
   perm = kp.second;
   cur = 1 - cur;
@@ -772,7 +798,7 @@ void Scene::step_once() {
     return;
   }
   host_rebuild();
-  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  TravArgs t = trav(buf[cur], keys_sorted, cell_off, xorder ? bin_off : nullptr);
   passes_before_sweep(t, nullptr, nullptr, walls_in_sweep());
   sweep(t, buf[1 - cur], nullptr, nullptr, walls_in_sweep());
   cur = 1 - cur;
@@ -789,7 +815,7 @@ void Scene::step_once() {
 // the step does not depend on the decision.
 void Scene::step_conditional() {
   cond_rebuild(1);
-  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  TravArgs t = trav(buf[cur], keys_sorted, cell_off, xorder ? bin_off : nullptr);
   passes_before_sweep(t, nullptr, nullptr, walls_in_sweep());
   sweep(t, buf[1 - cur], nullptr, nullptr, walls_in_sweep());
   cur = 1 - cur;
@@ -828,7 +854,7 @@ void Scene::cond_rebuild(int count) {
   std::swap(st, st_body);
   in_body = true;
   try {
-    rebuild(buf[cur], buf[1 - cur], nullptr, nullptr, cell_off);
+    rebuild(buf[cur], buf[1 - cur], nullptr, nullptr, cell_off, nullptr, nullptr, xorder ? bin_off : nullptr);
     if (D == 2)
       launch_copy_state<2>(N, buf[1 - cur], buf[cur], st);
     else
@@ -1063,15 +1089,18 @@ void Scene::rollout(int n, int k) {
 
 void Scene::alloc_tape(int k) {
   if (tape_cap >= k) return;
-  while ((int)tape.size() < k + 1) {
-    TapeSlot t;
-    alloc_arrays(t.a);
-    t.keys = (uint32_t*)mem.get(4 * (size_t)N);
-    t.perm = (uint32_t*)mem.get(4 * (size_t)N);
-    t.off = (int*)mem.get(sizeof(int) * ((size_t)C_tot + 1));
-    t.tiles = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
-    t.ntiles = (int*)mem.get(sizeof(int) * 2);
-    tape.push_back(t);
+  for (int b = 0; b < 2; ++b) {
+    while ((int)tapes[b].size() < k + 1) {
+      TapeSlot t;
+      alloc_arrays(t.a);
+      t.keys = (uint32_t*)mem.get(4 * (size_t)N);
+      t.perm = (uint32_t*)mem.get(4 * (size_t)N);
+      t.off = (int*)mem.get(sizeof(int) * ((size_t)C_tot + 1));
+      t.tiles = (Tile*)mem.get(sizeof(Tile) * (size_t)tiles_upper);
+      t.ntiles = (int*)mem.get(sizeof(int) * 2);
+      t.boff = xorder ? (int*)mem.get(sizeof(int) * ((size_t)C_tot * kXBins + 1)) : nullptr;
+      tapes[b].push_back(t);
+    }
   }
   if (!adj_alloc) {
     for (int q = 0; q < 2; ++q) {
@@ -1087,7 +1116,11 @@ void Scene::alloc_tape(int k) {
     CK(cudaMemsetAsync(d_replay_maxr, 0, sizeof(unsigned) * 2, st));
     nu_part = (float*)mem.get(sizeof(float) * (size_t)N);
     alloc_arrays(scratch_arr);
+    rep_out[0] = scratch_arr;
+    alloc_arrays(rep_out[1]);
     alloc_arrays(ckpt_work);
+    d_tile_ctr_b = (int*)mem.get(sizeof(int) * 4);
+    CK(cudaMemsetAsync(d_tile_ctr_b, 0, sizeof(int) * 4, st));  // tiled kernels leave it zeroed
     adj_alloc = true;
   }
   tape_cap = k;
@@ -1099,33 +1132,35 @@ void Scene::alloc_tape(int k) {
 // slot directly.  With K > 1 the sweeps measure the displacement since the last rebuild, and a
 // step whose successor does not rebuild sets d_replay_flag when it exceeds the skin's half: the
 // caller then replays the segment with K = 1.
-void Scene::adjoint_replay(int L, int K) {
+void Scene::adjoint_replay(int L, int K, int b) {
+  std::vector<TapeSlot>& tape = tapes[b];
   const Arrays* prev = &ckpt_work;
   int r = 0;
   for (int s = 0; s < L; ++s) {
     TapeSlot& slot = tape[s];
     if (s % K == 0) {
-      rebuild(*prev, slot.a, slot.keys, slot.perm, slot.off, slot.tiles, slot.ntiles);  // kept in the slot
+      rebuild(*prev, slot.a, slot.keys, slot.perm, slot.off, slot.tiles, slot.ntiles, slot.boff);  // kept in the slot
       r = s;
     }
     const TapeSlot& cells = tape[r];
-    TravArgs t = trav(slot.a, cells.keys, cells.off);
+    TravArgs t = trav(slot.a, cells.keys, cells.off, cells.boff);
     passes_before_sweep(t, cells.tiles, cells.ntiles);
     const bool next_rebuilds = s + 1 == L || (s + 1) % K == 0;
-    const Arrays& out = next_rebuilds ? scratch_arr : tape[s + 1].a;
+    const Arrays& out = next_rebuilds ? rep_out[b] : tape[s + 1].a;
     if (K > 1) {
       const Displace dp{xbuild, d_replay_maxr, inv_r2, nullptr, interval, next_rebuilds ? d_replay_flag + 1 : d_replay_flag};
       sweep(t, out, cells.tiles, cells.ntiles, false, &dp);
     } else {
       sweep(t, out, cells.tiles, cells.ntiles);
     }
-    prev = &scratch_arr;
+    prev = &rep_out[b];
   }
 }
 
 // The adjoint steps of a replayed segment backwards (rebuild every K steps, as replayed).  The
 // adjoint state enters and leaves in XB[0]/VB[0].
-void Scene::adjoint_backward(int L, int K) {
+void Scene::adjoint_backward(int L, int K, int b) {
+  std::vector<TapeSlot>& tape = tapes[b];
   int q = 0;
   for (int s = L - 1; s >= 0; --s) {
     TapeSlot& slot = tape[s];
@@ -1137,6 +1172,7 @@ void Scene::adjoint_backward(int L, int K) {
     CKL();
     TravArgs t = trav(slot.a, cells.keys, cells.off);
     t.pair_count = nullptr;
+    t.tile_ctr = d_tile_ctr_b;  // the next segment's replay may be running on st_rep
     prof_begin(4);
     if (D == 2) {
       if (kern == 0)
@@ -1151,7 +1187,7 @@ void Scene::adjoint_backward(int L, int K) {
     }
     CKL();
     prof_end();
-    launch_sum_segments(nu_part, dseg, S, d_nubar, st);
+    launch_sum_segments(nu_part, dseg, S, sum_nch, sum_chunk, sum_ctr, d_nubar, st);
     CKL();
     q = 1 - q;
     launches += 3;  // seed, adjoint sweep, segment sums
@@ -1181,13 +1217,13 @@ void Scene::adjoint_backward(int L, int K) {
 }
 
 // Runs (or captures and replays) one part of a segment: part 0 the forward replay, 1 the adjoint.
-void Scene::adjoint_part(int part, int L, int K) {
+void Scene::adjoint_part(int part, int L, int K, int b) {
   if (!use_graphs || profiling) {
-    if (part == 0) adjoint_replay(L, K);
-    else adjoint_backward(L, K);
+    if (part == 0) adjoint_replay(L, K, b);
+    else adjoint_backward(L, K, b);
     return;
   }
-  const long long key = ((long long)part << 40) | ((long long)K << 20) | (long long)L;
+  const long long key = ((long long)part << 41) | ((long long)b << 40) | ((long long)K << 20) | (long long)L;
   auto it = adj_graphs.find(key);
   if (it == adj_graphs.end()) {
     const long long l0 = launches;
@@ -1195,8 +1231,8 @@ void Scene::adjoint_part(int part, int L, int K) {
     capturing = true;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     try {
-      if (part == 0) adjoint_replay(L, K);
-      else adjoint_backward(L, K);
+      if (part == 0) adjoint_replay(L, K, b);
+      else adjoint_backward(L, K, b);
     } catch (...) {
       cudaStreamEndCapture(st, &g);
       capturing = false;
@@ -1212,6 +1248,37 @@ void Scene::adjoint_part(int part, int L, int K) {
     launches += it->second.second;
   }
   CK(cudaGraphLaunch(it->second.first, st));
+}
+
+// The forward replay of segment sgi into tape b, on the scene's current stream: from a working
+// copy of the segment's checkpoint (so that one captured graph per segment length serves every
+// segment), rebuilding every replay_k steps when the skin allows; a segment whose displacements
+// outgrew the skin is replayed again with a rebuild every step (and later segments try half the
+// interval).  Returns the rebuild interval the tape was recorded with.
+int Scene::adjoint_replay_segment(int sgi, int b) {
+  const int t0 = sgi * tape_k, t1 = std::min(tape_n, t0 + tape_k);
+  const int L = t1 - t0;
+  if (D == 2)
+    launch_copy_state<2>(N, ckpts[sgi], ckpt_work, st);
+  else
+    launch_copy_state<3>(N, ckpts[sgi], ckpt_work, st);
+  CKL();
+  ++launches;
+  int K = std::max(1, std::min(replay_k, L));
+  if (K > 1) CK(cudaMemsetAsync(d_replay_flag, 0, sizeof(int) * 2, st));
+  adjoint_part(0, L, K, b);
+  if (K > 1) {
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, d_replay_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (flag) {
+      ++replay_fallbacks;
+      replay_k = std::max(1, replay_k / 2);
+      K = 1;
+      adjoint_part(0, L, K, b);
+    }
+  }
+  return K;
 }
 
 void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb0, float* vb0, float* rb0, double* nub,
@@ -1238,34 +1305,40 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
   float* rows = adj_rows;
   CK(cudaMemsetAsync(d_nubar, 0, sizeof(double) * S, st));
   const int ncp = (n + k - 1) / k;
-  for (int sgi = ncp - 1; sgi >= 0; --sgi) {
-    const int t0 = sgi * k, t1 = std::min(n, t0 + k);
-    const int L = t1 - t0;
-    // the segment starts from a working copy of its checkpoint, so that one captured graph per
-    // segment length serves every segment
-    if (D == 2)
-      launch_copy_state<2>(N, ckpts[sgi], ckpt_work, st);
-    else
-      launch_copy_state<3>(N, ckpts[sgi], ckpt_work, st);
-    CKL();
-    ++launches;
-    // the replay rebuilds every replay_k steps when the skin allows; a segment whose
-    // displacements outgrew the skin is replayed again with a rebuild every step (and later
-    // segments try half the interval)
-    int K = std::max(1, std::min(replay_k, L));
-    if (K > 1) CK(cudaMemsetAsync(d_replay_flag, 0, sizeof(int) * 2, st));
-    adjoint_part(0, L, K);
-    if (K > 1) {
-      int flag = 0;
-      CK(cudaMemcpyAsync(&flag, d_replay_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      if (flag) {
-        ++replay_fallbacks;
-        replay_k = std::max(1, replay_k / 2);
-        K = 1;
-        adjoint_part(0, L, K);
-      }
+  // The segments' replays run on st_rep, one segment ahead of the reverse pass on st: while the
+  // reverse pass of segment sgi reads tape sgi % 2, the replay of segment sgi - 1 fills the other
+  // tape (each pass alone leaves most of the GPU idle at the sizes the adjoint is used at).  A
+  // replay waits for the reverse pass that last read its tape; a reverse pass waits for its replay.
+  if (!st_rep) {  // with the priority of the scene's stream
+    int prio = 0;
+    CK(cudaStreamGetPriority(st, &prio));
+    CK(cudaStreamCreateWithPriority(&st_rep, cudaStreamNonBlocking, prio));
+  }
+  for (int b = 0; b < 2; ++b) {
+    if (!ev_rep[b]) CK(cudaEventCreateWithFlags(&ev_rep[b], cudaEventDisableTiming));
+    if (!ev_free[b]) CK(cudaEventCreateWithFlags(&ev_free[b], cudaEventDisableTiming));
+    CK(cudaEventRecord(ev_free[b], st));  // the replays start after the work queued on st so far
+  }
+  auto replay_beside = [&](int sgi) {
+    const int b = sgi & 1;
+    CK(cudaStreamWaitEvent(st_rep, ev_free[b], 0));
+    std::swap(st, st_rep);
+    int K = 1;
+    try {
+      K = adjoint_replay_segment(sgi, b);
+    } catch (...) {
+      std::swap(st, st_rep);
+      throw;
     }
+    std::swap(st, st_rep);
+    CK(cudaEventRecord(ev_rep[b], st_rep));
+    return K;
+  };
+  int K = replay_beside(ncp - 1);
+  for (int sgi = ncp - 1; sgi >= 0; --sgi) {
+    const int b = sgi & 1;
+    const int L = std::min(n, sgi * k + k) - sgi * k;
+    CK(cudaStreamWaitEvent(st, ev_rep[b], 0));
     // the adjoint of the segment's final state, in the order of the replay's last sweep output
     const float *lx = dxb, *lv = dvb, *lr = drb;
     if (sgi != ncp - 1) {  // the running adjoint, in the order of the checkpoint after this segment
@@ -1280,12 +1353,14 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
       ++launches;
     }
     if (D == 2)
-      launch_adj_load<2>(N, scratch_arr.meta, d_orig_base, lx, lv, lr, XB[0], VB[0], st);
+      launch_adj_load<2>(N, rep_out[b].meta, d_orig_base, lx, lv, lr, XB[0], VB[0], st);
     else
-      launch_adj_load<3>(N, scratch_arr.meta, d_orig_base, lx, lv, lr, XB[0], VB[0], st);
+      launch_adj_load<3>(N, rep_out[b].meta, d_orig_base, lx, lv, lr, XB[0], VB[0], st);
     CKL();
     ++launches;
-    adjoint_part(1, L, K);
+    adjoint_part(1, L, K, b);
+    CK(cudaEventRecord(ev_free[b], st));
+    if (sgi > 0) K = replay_beside(sgi - 1);
   }
   // XB[q] is in the storage order of checkpoint 0; deliver in original order
   float* oxb = xb0;
@@ -1466,7 +1541,7 @@ void Scene::opt_passes(const ShiftObjective& o, const Arrays* out, float step, d
   prof_end();
   launches += 5;
   CK(cudaMemsetAsync(loss_slot, 0, sizeof(double) * S, st));
-  launch_sum_segments(opt_L, dseg, S, loss_slot, st);
+  launch_sum_segments(opt_L, dseg, S, sum_nch, sum_chunk, sum_ctr, loss_slot, st);
   CKL();
   ++launches;
 }
@@ -1542,8 +1617,19 @@ void Scene::stats(int64_t* steps, int64_t* rebuilds, int64_t* n_launches) {
 }
 
 void Scene::debug_cells(int64_t* start, int32_t* ids) {
-  if (skin > 0.f) cells_valid = false;  // report the cells of the current positions
-  ensure_cells();
+  // the cells of the current positions in the stable order by cell (plain cell keys: the x
+  // sub-bins of the 3D sweep's keys are left out, and restored by a rebuild at the next step)
+  const bool xo = xorder;
+  xorder = false;
+  cells_valid = false;
+  try {
+    ensure_cells();
+  } catch (...) {
+    xorder = xo;
+    throw;
+  }
+  xorder = xo;
+  if (xo) cells_valid = false;
   std::vector<int> off((size_t)C_tot + 1);
   std::vector<uint2> meta(N);
   CK(cudaMemcpyAsync(off.data(), cell_off, sizeof(int) * ((size_t)C_tot + 1), cudaMemcpyDeviceToHost, st));

@@ -65,6 +65,7 @@ struct TapeSlot {
   int* off;            // cell offsets in effect
   Tile* tiles;         // tile table of that cell structure, and its count
   int* ntiles;
+  int* boff;           // sub-bin offsets of the cells ordered by x (3D warp-per-tile sweep), or null
 };
 
 struct GraphKey {
@@ -113,6 +114,11 @@ struct Scene {
   uint32_t* keys_sorted = nullptr;
   uint32_t* perm = nullptr;
   int* cell_off = nullptr;
+  // 3D warp-per-tile sweep: the cell keys carry x sub-bins (cell * kXBins + bin), so the sort
+  // orders every cell by sub-bin, and the permute writes the sub-bins' offsets (bin_off) beside
+  // the cells'; host-launched rebuilds only (scenes with the cooperative rebuild keep plain keys)
+  bool xorder = false;
+  int* bin_off = nullptr;
   uint32_t* scratch = nullptr;
   // cell-block tiles of the current cell structure
   std::vector<int> line_base_h;
@@ -128,6 +134,9 @@ struct Scene {
   int* d_status = nullptr;
   unsigned long long* d_pairs = nullptr;
   double* d_nubar = nullptr;
+  double* sum_chunk = nullptr;      // scratch of the per-scene sums (launch_sum_segments)
+  int* sum_ctr = nullptr;
+  int sum_nch = 1;
   void* tmp = nullptr;
   size_t tmp_bytes = 0;
   bool cells_valid = false;
@@ -167,7 +176,9 @@ struct Scene {
   bool tape_valid = false;
   int tape_n = 0, tape_k = 0, tape_cap = 0;
   std::vector<Arrays> ckpts;
-  std::vector<TapeSlot> tape;
+  // two tapes: the replay of a segment fills one while the reverse pass of the segment after it
+  // reads the other (the replay runs on st_rep, the reverse pass on st)
+  std::vector<TapeSlot> tapes[2];
   bool adj_alloc = false;
   float4* XB[2] = {nullptr, nullptr};
   float4* VB[2] = {nullptr, nullptr};
@@ -175,8 +186,13 @@ struct Scene {
   float* Pp = nullptr;
   float* nu_part = nullptr;
   Arrays scratch_arr{};
+  Arrays rep_out[2]{};               // a replay's sweep output before a rebuild, per tape ([0] is scratch_arr)
+  int* d_tile_ctr_b = nullptr;      // tile counter of the reverse pass's launches (beside the replay's)
+  cudaStream_t st_rep = nullptr;    // the adjoint's forward replays
+  cudaEvent_t ev_rep[2] = {nullptr, nullptr};   // a tape's replay finished
+  cudaEvent_t ev_free[2] = {nullptr, nullptr};  // a tape's reverse pass finished (the tape is free)
   Arrays ckpt_work{};               // the segment's checkpoint, copied (graphs do not depend on it)
-  std::map<long long, std::pair<cudaGraphExec_t, long long>> adj_graphs;  // by part, interval, length
+  std::map<long long, std::pair<cudaGraphExec_t, long long>> adj_graphs;  // by part, tape, interval, length
   int replay_k = 1;                 // rebuild interval of the adjoint's forward replay (skin > 0)
   int replay_k_user = 0;            // the caller's interval (0: from the rollout's rebuild rate)
   int* d_replay_flag = nullptr;     // [0] a replayed step outgrew the skin, [1] scratch
@@ -195,12 +211,12 @@ struct Scene {
   void copy_arrays(const Arrays& dst, const Arrays& src);
   void upload(int s, const float* x, const float* v, const float* rho, const float* mass, int is_dev);
   void* mem_tmp(size_t bytes);
-  TravArgs trav(const Arrays& a, const uint32_t* keys, const int* off) const;
+  TravArgs trav(const Arrays& a, const uint32_t* keys, const int* off, const int* boff = nullptr) const;
   void prof_begin(int cls);
   void prof_end();
   std::pair<uint32_t*, uint32_t*> rebuild(const Arrays& in, const Arrays& out, uint32_t* keys_out,
                                           uint32_t* perm_out, int* off_out, Tile* tiles_out = nullptr,
-                                          int* ntiles_out = nullptr);
+                                          int* ntiles_out = nullptr, int* boff_out = nullptr);
   void build_tiles(const int* off, const uint2* meta, Tile* tl, int* ntl);
   bool fuse_walls = true;           // wall pass inside the sweep launch (Shepard walls, MC diffusion;
                                     // in summation mode after the density launch)
@@ -231,9 +247,10 @@ struct Scene {
   void ensure_cells();
   void rollout(int n, int k);
   void alloc_tape(int k);
-  void adjoint_replay(int L, int K);
-  void adjoint_backward(int L, int K);
-  void adjoint_part(int part, int L, int K);
+  void adjoint_replay(int L, int K, int b);
+  void adjoint_backward(int L, int K, int b);
+  void adjoint_part(int part, int L, int K, int b);
+  int adjoint_replay_segment(int sgi, int b);
   void adjoint(const float* xb, const float* vb, const float* rb, float* xb0, float* vb0, float* rb0, double* nub,
                int is_dev);
   void get_state(float* x, float* v, float* rho, int is_dev);

@@ -46,7 +46,9 @@ static size_t request_bytes(const sph_params& p, int n, int nw, int steps, int m
   if (mode == SPH_REQ_ADJOINT) {
     const size_t rec = p.dim == 2 ? 72 : 96;  // one copy of the records
     const int k = std::max(ckpt, 1);
-    b += (size_t)((steps + k - 1) / k) * n * rec + (size_t)(k + 1) * n * (rec + 16) + (size_t)n * (2 * rec + 64);
+    // checkpoints, two tapes of k + 1 slots (records, keys, permutation), the adjoint state and
+    // the replay's working copies
+    b += (size_t)((steps + k - 1) / k) * n * rec + 2 * (size_t)(k + 1) * n * (rec + 16) + (size_t)n * (3 * rec + 64);
   }
   return b;
 }
@@ -367,8 +369,13 @@ int sph_server_create(size_t hbm_budget_bytes, int max_active, sph_server** out)
     s.budget = hbm_budget_bytes;
     s.max_active = max_active;
     CK(cudaGetDevice(&s.device));
-    CK(cudaStreamCreateWithFlags(&s.st_fwd, cudaStreamNonBlocking));
-    for (int w = 0; w < sph::kAdjWorkers; ++w) CK(cudaStreamCreateWithFlags(&s.st_adj[w], cudaStreamNonBlocking));
+    // the adjoint workers' streams take the highest priority: an adjoint request is several times
+    // as long as a forward one of its size and sets the tail of the latencies when it shares the
+    // GPU with the forward batch
+    int prio_lo = 0, prio_hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    CK(cudaStreamCreateWithPriority(&s.st_fwd, cudaStreamNonBlocking, prio_lo));
+    for (int w = 0; w < sph::kAdjWorkers; ++w) CK(cudaStreamCreateWithPriority(&s.st_adj[w], cudaStreamNonBlocking, prio_hi));
     s.th_fwd = std::thread([&s] { s.forward_loop(); });
     for (int w = 0; w < sph::kAdjWorkers; ++w) s.th_adj[w] = std::thread([&s, w] { s.adjoint_loop(w); });
     *out = sv;

@@ -6,13 +6,29 @@
 
 namespace sph {
 
+// Coordinate q of x = hi + lo folded into the primary box, rounded to FP32, and the fold offset
+// o = L floor((x - lo_box) / L) (decided in FP64; in_primary_box() settles the common case 0
+// without the FP64 division and gives the same result).
+__device__ __forceinline__ float fold_coord(const DevSeg& s, int q, float hi, float lo, double* o_out) {
+  const double x = __dadd_rn((double)hi, (double)lo);
+  double f = 0.0;
+  if (((s.periodic_mask >> q) & 1) && !in_primary_box(s, q, hi))
+    f = floor(__ddiv_rn(__dsub_rn(x, s.lo_d[q]), s.L_d[q]));
+  const double o = __dmul_rn(s.L_d[q], f);
+  *o_out = o;
+  return (float)__dsub_rn(x, o);
+}
+
 // Cell key of particle i, decided in FP64 from x = hi + lo exactly as floor(((x wrapped) - lo) /
 // cell edge), clamped to the grid.  Fast path: an FP32 estimate from hi alone decides the floor
 // whenever it lies farther than a margin from an integer; the margin, 2^-18 (|x| + |lo|) /
 // cell edge + 2^-18, exceeds the estimate's error (five FP32 roundings, and |lo part| <= 2^-24
 // |hi|) by more than ten times, so the FP64 decision is only taken near a cell face (and for
 // NaN or huge coordinates).  Both paths give the same key.
-template <int D>
+// XB: the key with the particle's x sub-bin, cell * kXBins + bin, the bin taken from the position
+// folded into the box exactly as the permute folds it (fold_coord), so the sorted cells are
+// ordered by sub-bin as the sweep's x windows see them.
+template <int D, bool XB = false>
 __device__ __forceinline__ uint32_t cell_key_of(const DevSeg* __restrict__ segs, const Arrays& a, int i) {
   const DevSeg& s = segs[a.meta[i].y];
   Cold c = load_cold<D>(a, i);
@@ -44,7 +60,12 @@ __device__ __forceinline__ uint32_t cell_key_of(const DevSeg* __restrict__ segs,
       cc3[k] = (int)cc;
     }
   }
-  return (uint32_t)(s.cell_base + (cc3[2] * s.n[1] + cc3[1]) * s.n[0] + cc3[0]);
+  const uint32_t key = (uint32_t)(s.cell_base + (cc3[2] * s.n[1] + cc3[1]) * s.n[0] + cc3[0]);
+  if (!XB) return key;
+  double o;
+  const float xh = fold_coord(s, 0, c.hi[0], c.lo[0], &o);
+  const int b = min(max(line_xbin<kXBins>(s, xh) - cc3[0] * kXBins, 0), kXBins - 1);
+  return key * kXBins + (uint32_t)b;
 }
 
 // ---- stable LSD radix sort, 8-bit digits, 2048-key tiles ---------------------------------
@@ -53,10 +74,10 @@ constexpr int kSortIPT = 8;
 constexpr int kSortTile = kSortThreads * kSortIPT;
 
 // Histogram of one digit over sort tile `tile` (2048 keys), 256 threads; h: 256 words of shared
-// memory.  KEYS_FROM_STATE: the keys are the cell keys of the current storage order, computed
-// here (first pass of a rebuild) instead of read; with kcache they are also stored there, for the
-// pass's scatter in a later launch.
-template <int D, bool KEYS_FROM_STATE>
+// memory.  KEYS_FROM_STATE: the keys are the cell keys of the current storage order (2: with x
+// sub-bins), computed here (first pass of a rebuild) instead of read; with kcache they are also
+// stored there, for the pass's scatter in a later launch.
+template <int D, int KEYS_FROM_STATE>
 __device__ __forceinline__ void sort_hist_tile(int tile, const uint32_t* __restrict__ keys, int N, int shift,
                                                uint32_t* __restrict__ hist, int nblocks,
                                                const DevSeg* __restrict__ segs, const Arrays& a, uint32_t* h,
@@ -68,7 +89,7 @@ __device__ __forceinline__ void sort_hist_tile(int tile, const uint32_t* __restr
   for (int k = 0; k < kSortIPT; ++k) {
     int i = base + k * kSortThreads + threadIdx.x;
     if (i < N) {
-      const uint32_t key = KEYS_FROM_STATE ? cell_key_of<D>(segs, a, i) : keys[i];
+      const uint32_t key = KEYS_FROM_STATE ? cell_key_of<D, KEYS_FROM_STATE == 2>(segs, a, i) : keys[i];
       if (KEYS_FROM_STATE && kcache) kcache[i] = key;
       atomicAdd(&h[(key >> shift) & 255u], 1u);
     }
@@ -88,7 +109,7 @@ struct ScatterSmem {
 // lane via match_any.  hist holds the exclusive offsets of (digit, tile).  256 threads.
 // KEYS_FROM_STATE: the first pass; the keys come from kcache (stored by the histogram launch) or,
 // without it, are computed again from the state.
-template <int D, bool KEYS_FROM_STATE>
+template <int D, int KEYS_FROM_STATE>
 __device__ __forceinline__ void sort_scatter_tile(int tile, const uint32_t* __restrict__ kin,
                                                   const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
                                                   uint32_t* __restrict__ vout, int N, int shift,
@@ -107,7 +128,7 @@ __device__ __forceinline__ void sort_scatter_tile(int tile, const uint32_t* __re
     int i = base + r * 32 + lane;
     bool ok = i < N;
     if (KEYS_FROM_STATE) {
-      kk[r] = ok ? (kcache ? kcache[i] : cell_key_of<D>(segs, a, i)) : 0u;
+      kk[r] = ok ? (kcache ? kcache[i] : cell_key_of<D, KEYS_FROM_STATE == 2>(segs, a, i)) : 0u;
       vv[r] = (uint32_t)i;
     } else {
       kk[r] = ok ? kin[i] : 0u;
@@ -144,20 +165,31 @@ __device__ __forceinline__ void sort_scatter_tile(int tile, const uint32_t* __re
   }
 }
 
+// Element k (0 <= k <= N) of the sorted keys writes the CSR offsets of the cells in
+// (key[k-1], key[k]] (off[c] = first index with key >= c).
+__device__ __forceinline__ void cell_offsets_one(int k, int N, const uint32_t* __restrict__ keys, int C,
+                                                 int* __restrict__ off) {
+  const int lo = (k == 0) ? 0 : (int)keys[k - 1] + 1;
+  const int hi = (k < N) ? (int)keys[k] : C;
+  for (int c = lo; c <= hi; ++c) off[c] = k;
+}
+
 // Gather element k of the sorted state and re-fold its position into the primary box; element k
-// (0 <= k <= N) also writes the CSR offsets of the cells in (key[k-1], key[k]] (off[c] = first
-// index with key >= c) and, when xb is set, the folded position (the reference of the
-// displacement check).  The fold floor((x - lo) / L) is decided in FP64; in_primary_box()
-// settles the common case (0) without the FP64 division and gives the same result.
+// (0 <= k <= N) also writes the cells' CSR offsets (cell_offsets_one) and, when xb is set, the
+// folded position (the reference of the displacement check).  boff set: the keys carry x
+// sub-bins; off gets the offsets of the cells (keys >> kXShift), boff those of the sub-bins.
 template <int D>
 __device__ __forceinline__ void permute_one(int k, const DevSeg* __restrict__ segs, int N,
                                             const uint32_t* __restrict__ perm, const Arrays& in, const Arrays& out,
                                             const uint32_t* __restrict__ keys, int C, int* __restrict__ off,
-                                            float4* __restrict__ xb) {
-  {
-    const int lo = (k == 0) ? 0 : (int)keys[k - 1] + 1;
-    const int hi = (k < N) ? (int)keys[k] : C;
+                                            float4* __restrict__ xb, int* __restrict__ boff = nullptr) {
+  if (boff) {
+    cell_offsets_one(k, N, keys, C * kXBins, boff);
+    const int lo = (k == 0) ? 0 : (int)(keys[k - 1] >> kXShift) + 1;
+    const int hi = (k < N) ? (int)(keys[k] >> kXShift) : C;
     for (int c = lo; c <= hi; ++c) off[c] = k;
+  } else {
+    cell_offsets_one(k, N, keys, C, off);
   }
   if (k >= N) return;
   int src = (int)perm[k];
@@ -168,13 +200,9 @@ __device__ __forceinline__ void permute_one(int k, const DevSeg* __restrict__ se
   float xh[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int q = 0; q < D; ++q) {
-    double x = __dadd_rn((double)c.hi[q], (double)c.lo[q]);
-    double f = 0.0;
-    if (((s.periodic_mask >> q) & 1) && !in_primary_box(s, q, c.hi[q]))
-      f = floor(__ddiv_rn(__dsub_rn(x, s.lo_d[q]), s.L_d[q]));
-    double o = __dmul_rn(s.L_d[q], f);
+    double o;
+    xh[q] = fold_coord(s, q, c.hi[q], c.lo[q], &o);
     c.off[q] = (float)o;
-    xh[q] = (float)__dsub_rn(x, o);
   }
   if (D == 2) {
     out.A[k] = make_float4(xh[0], xh[1], a.z, a.w);

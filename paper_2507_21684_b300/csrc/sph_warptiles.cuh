@@ -1,20 +1,21 @@
 // Warp-per-tile traversal of the tiled neighbour passes (one thread per target).
 //
-// A warp owns one tile (at most 32 consecutive sorted particles of one cell line) at a time and
-// walks, in lockstep, the union of its targets' stencil runs: for each of the 3^(d-1) neighbour
-// lines, the columns that some target of the tile can reach (the same reach test as the staged
-// traversal, reduced over the warp with redux.sync), split into the in-box range and the two
-// periodic image cells.  Every candidate record is therefore read once per warp at one address
-// (a broadcast through L1), tested by every lane against its own target and, on a hit, appended
-// to the lane's list in shared memory; the lists are evaluated (Body::pair_at) from the neighbour
-// records in global memory when a lane's list may overflow and at the end of the tile.
+// A warp owns one tile (at most 32 consecutive sorted particles of one cell line) at a time.  Each
+// lane walks its own target's stencil: for each of the 3^(d-1) neighbour lines, the columns its
+// target can reach (the same face-distance test as the staged traversal), split into the in-box
+// range and the two periodic image cells.  The walks run in lockstep over the warp (up to the
+// longest run of the warp; shorter runs are masked), so their loop control is warp-uniform, and
+// lanes of one cell, whose runs mostly coincide, read the same candidate records (a broadcast
+// through L1).  The candidates' positions come packed as pairs and are tested two at a time with
+// paired FP32 instructions; each step of the test loop records the step's hits as one entry of a
+// per-lane ring in shared memory (the step's first pair and a bit mask of its hits), so that a
+// candidate costs a bit, not a list append.  The rings are evaluated (Body::pair_at) from the
+// neighbour records in global memory when one may overflow and at the end of the tile.
 //
 // Against the staged traversal (sph_tiles.cuh: a CTA stages the 3^(d-1) lines into shared memory
 // and LANES threads split one target's candidates) this needs no staging, no CTA barrier per tile,
-// no reduction over lanes and no tile-size fallback, and its loop control is warp-uniform; it
-// tests more candidates per target (the union of 32 targets' stencils instead of each target's
-// own) but each test is a broadcast load and six FP32 operations.  Each warp takes its own tiles
-// from the launch's tile counter.
+// no reduction over lanes and no tile-size fallback.  Each warp takes its own tiles from the
+// launch's tile counter.
 //
 // Periodic images follow the staged traversal's convention, so that every coordinate difference
 // is formed from exactly shifted operands: a lower image (the line or column wraps below the box)
@@ -28,16 +29,21 @@ namespace sph {
 #ifndef SPH_W_WARPS
 #define SPH_W_WARPS 4
 #endif
+// hit-ring entries per lane (one entry per step of the test loop that found a hit)
 #ifndef SPH_W_LIST
-#define SPH_W_LIST 64
+#define SPH_W_LIST 32
 #endif
-// entries of every lane's ring evaluated at a time when one may overflow
+// hits of every lane evaluated at a time when some lane's ring is full
 #ifndef SPH_W_EVAL
-#define SPH_W_EVAL (SPH_W_LIST / 2)
+#define SPH_W_EVAL 32
 #endif
 // candidates per step of the test loop (two per paired load; loads in flight per lane)
 #ifndef SPH_W_UNROLL
 #define SPH_W_UNROLL 8
+#endif
+// evaluate two hits per iteration of the evaluation loop (their loads in flight together)
+#ifndef SPH_W_DRAIN2
+#define SPH_W_DRAIN2 1
 #endif
 // CTAs per SM the warp-traversal kernels are compiled for (register budget 64K / (MINB x THREADS))
 #ifndef SPH_W_MINB
@@ -48,135 +54,189 @@ struct WCfg {
   static constexpr int WARPS = SPH_W_WARPS;    // warps per CTA
   static constexpr int THREADS = 32 * WARPS;
   static constexpr int LIST = SPH_W_LIST;      // hit-ring entries per thread
-  static constexpr int EVAL = SPH_W_EVAL;      // entries per lane evaluated at a time
+  static constexpr int EVAL = SPH_W_EVAL;      // hits per lane evaluated at a time
   static constexpr int UNROLL = SPH_W_UNROLL;  // candidates per step of the test loop
 };
-static_assert(WCfg::LIST > WCfg::UNROLL, "a step of the test loop must fit into a list with room");
-static_assert(WCfg::EVAL >= WCfg::UNROLL && WCfg::EVAL <= WCfg::LIST, "an evaluation frees a step's room");
+static_assert(WCfg::UNROLL % 2 == 0 && WCfg::UNROLL <= 16, "a step's hit mask holds up to 16 candidates");
+// an evaluation of EVAL hits finishes the entry in registers (up to UNROLL hits) and frees a slot
+static_assert(WCfg::EVAL > WCfg::UNROLL, "an evaluation frees a ring slot");
+static_assert((WCfg::LIST & (WCfg::LIST - 1)) == 0, "the hit ring's length is a power of two");
 static_assert(TileCfg<3>::TP <= 32, "a warp holds one tile's targets");
 
-// Hit-list entry: neighbour index in the packed arrays (26 bits) and the shifts of the pair:
-// bit 26 + q: the neighbour's coordinate q takes off L_q; bit 29 + q: the target's does.
-constexpr int kWIdxBits = 26;
-constexpr uint32_t kWIdxMask = (1u << kWIdxBits) - 1u;
-constexpr long long kWMaxParticles = 1LL << kWIdxBits;
+// Hit-ring entry: x = index of the first candidate pair of the step, y = the step's hit mask (bit
+// k: candidate 2x + k) in bits 0-15 and the shifts of the run's periodic image in bits 16-21
+// (bit 16 + q: the neighbour's coordinate q takes off L_q; bit 19 + q: the target's does).
+constexpr uint32_t kWHitBits = 0xffffu;
+constexpr int kWShift = 16;
+constexpr long long kWMaxParticles = 1LL << 30;
+// The packed pair arrays are padded by this many pairs: the last step of a run reads up to
+// UNROLL/2 - 1 pairs past the run's end (masked out of the hits).
+constexpr int kWPadPairs = 16;
+static_assert(WCfg::UNROLL / 2 <= kWPadPairs, "the pair arrays' padding covers a step");
+// Pairs per packed array (positions as pairs (x_2p, x_2p+1, y_2p, y_2p+1) and (z_2p, z_2p+1));
+// the z array starts 4 x this many floats into the buffer, which holds 6 x this many floats.
+__host__ __device__ inline size_t warp_pairs_stride(long long N) { return (size_t)((N + 1) / 2) + kWPadPairs; }
 
-__host__ __device__ constexpr size_t warp_tiles_smem() { return sizeof(uint32_t) * WCfg::LIST * WCfg::THREADS; }
-// Shared-memory carveout (percent of the SM's maximum) that holds MINB CTAs' lists and no more:
+__host__ __device__ constexpr size_t warp_tiles_smem() { return sizeof(uint2) * WCfg::LIST * WCfg::THREADS; }
+// Shared-memory carveout (percent of the SM's maximum) that holds MINB CTAs' rings and no more:
 // the rest of the unified L1 caches the neighbour records the traversal reads from global memory.
 constexpr int warp_tiles_carveout() {
   return (int)((100 * (size_t)SPH_W_MINB * (warp_tiles_smem() + 1024) + 228 * 1024 - 1) / (228 * 1024));
 }
 
-// A lane's hit list is a ring of LIST entries (free-running counters head and tail): the tests
-// append at head, the evaluation takes entries from tail.  When some lane's ring may overflow, the
-// warp evaluates up to EVAL entries of every lane (the oldest ones) and goes on testing: the lanes
-// keep about half a ring each, so an evaluation keeps most lanes busy (evaluating every list to
-// the end whenever the fullest one is full leaves the others idle for the difference; a ring of
-// 64 with 32 per evaluation needs a third fewer evaluation steps than emptying lists of 48 on the
-// 128^3 vortex, counted on its cell lists).
-static_assert((WCfg::LIST & (WCfg::LIST - 1)) == 0, "the hit ring's length is a power of two");
+// A lane's hits: the ring (free-running counters head and tail, in entries), the entry being
+// evaluated (its first pair and its remaining mask and shifts) and the hits not yet evaluated.
+// When some lane's ring is full, the warp evaluates up to EVAL hits of every lane (the oldest
+// ones) and goes on testing, so the lanes keep part of their rings and an evaluation keeps most
+// lanes busy.
+struct WHits {
+  unsigned head = 0u, tail = 0u;
+  uint32_t base = 0u, bits = 0u;
+  int pend = 0;
+};
 
-// Evaluation of up to `most` entries of every lane's ring: the warp iterates up to the longest
-// batch (lanes with fewer entries idle), each lane loads its neighbour's records and calls
-// body.pair_at with both ends in the pair's periodic image.  Returns the entries evaluated by this
-// lane.  EX0 / EX1: the pass stages a float4 / float payload with the neighbours.
+// One hit's evaluation: body.pair_at with both ends in the pair's periodic image.  EX0 / EX1: the
+// pass reads a float4 / float payload of the neighbours.
 template <int D, bool EX0, bool EX1, class Body>
-__device__ __forceinline__ int warp_drain(const float* L, const Arrays& a, const float4* __restrict__ extra0,
-                                          const float* __restrict__ extra1, const uint32_t* list, unsigned head,
-                                          unsigned& tail, int most, const float* xt, Body& body) {
-  constexpr unsigned MASK = WCfg::LIST - 1;
-  const int lane = threadIdx.x & 31;
-  const int mine = min((int)(head - tail), most);
-  const int m = (int)__reduce_max_sync(kFull, (unsigned)mine);
-  for (int e = 0; e < m; ++e) {
-    if (e < mine) {
-      const uint32_t code = list[((tail + (unsigned)e) & MASK) * 32u + lane];
-      const int j = (int)(code & kWIdxMask);
-      PD<D> pj = load_pd<D>(a, j);
-      float xs[D];
+__device__ __forceinline__ void warp_eval_hit(const float* L, const Arrays& a, const float4* __restrict__ extra0,
+                                              const float* __restrict__ extra1, int j, uint32_t sh, PD<D> pj,
+                                              const float* xt, Body& body) {
+  float xs[D];
 #pragma unroll
-      for (int q = 0; q < D; ++q) xs[q] = xt[q];
-      if (code >> kWIdxBits) {  // a periodic image (particles near the box faces only)
+  for (int q = 0; q < D; ++q) xs[q] = xt[q];
+  if (sh) {  // a periodic image (particles near the box faces only)
 #pragma unroll
-        for (int q = 0; q < D; ++q) {
-          if ((code >> (29 + q)) & 1u) xs[q] -= L[q];
-          if ((code >> (26 + q)) & 1u) pj.x[q] -= L[q];
-        }
-      }
-      const float4 ex = EX0 ? __ldg(extra0 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float pp = EX1 ? __ldg(extra1 + j) : 0.f;
-      body.pair_at(xs, pj, ex, pp, j);
+    for (int q = 0; q < D; ++q) {
+      if ((sh >> (3 + q)) & 1u) xs[q] -= L[q];
+      if ((sh >> q) & 1u) pj.x[q] -= L[q];
     }
   }
-  tail += (unsigned)mine;
+  const float4 ex = EX0 ? __ldg(extra0 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float pp = EX1 ? __ldg(extra1 + j) : 0.f;
+  body.pair_at(xs, pj, ex, pp, j);
+}
+
+// The next hit of a lane: the lowest bit of its current entry, or of the next entry of its ring
+// when that one is spent.  j: the neighbour's index; sh: the pair's shifts.
+__device__ __forceinline__ void warp_pop_hit(const uint2* ring, WHits& h, int& j, uint32_t& sh) {
+  constexpr unsigned MASK = WCfg::LIST - 1;
+  if ((h.bits & kWHitBits) == 0u) {
+    const uint2 en = ring[(h.tail & MASK) * 32u + (threadIdx.x & 31)];
+    ++h.tail;
+    h.base = en.x;
+    h.bits = en.y;
+  }
+  const int b = __ffs(h.bits) - 1;  // the lowest set bit lies in the (non-empty) mask
+  h.bits &= h.bits - 1u;
+  j = 2 * (int)h.base + b;
+  sh = h.bits >> kWShift;
+}
+
+// Evaluation of up to `most` hits of every lane: the warp iterates up to the largest count (lanes
+// with fewer idle), each lane takes its next hit (the lowest bit of its current entry, the next
+// entry of its ring when that one is spent), loads the neighbour's records and calls
+// body.pair_at with both ends in the pair's periodic image.  Returns the hits this lane
+// evaluated.
+template <int D, bool EX0, bool EX1, class Body>
+__device__ __forceinline__ int warp_drain(const float* L, const Arrays& a, const float4* __restrict__ extra0,
+                                          const float* __restrict__ extra1, const uint2* ring, WHits& h, int most,
+                                          const float* xt, Body& body) {
+  const int mine = min(h.pend, most);
+  const int m = (int)__reduce_max_sync(kFull, (unsigned)mine);
+#if SPH_W_DRAIN2
+  // two hits per iteration: both neighbours' records are requested before either is evaluated
+  for (int e = 0; e < m; e += 2) {
+    const bool oa = e < mine, ob = e + 1 < mine;
+    int ja = 0, jb = 0;
+    uint32_t sa = 0u, sb = 0u;
+    if (oa) warp_pop_hit(ring, h, ja, sa);
+    if (ob) warp_pop_hit(ring, h, jb, sb);
+    const PD<D> pa = load_pd<D>(a, ja), pb = load_pd<D>(a, jb);  // index 0 for a lane without the hit
+    if (oa) warp_eval_hit<D, EX0, EX1>(L, a, extra0, extra1, ja, sa, pa, xt, body);
+    if (ob) warp_eval_hit<D, EX0, EX1>(L, a, extra0, extra1, jb, sb, pb, xt, body);
+  }
+#else
+  for (int e = 0; e < m; ++e) {
+    if (e < mine) {
+      int j;
+      uint32_t sh;
+      warp_pop_hit(ring, h, j, sh);
+      warp_eval_hit<D, EX0, EX1>(L, a, extra0, extra1, j, sh, load_pd<D>(a, j), xt, body);
+    }
+  }
+#endif
+  h.pend -= mine;
   return mine;
 }
 
-// Test the candidates [g0, g1) of one run (per lane: the run of the lane's group) against this
-// lane's target, two at a time: the positions come as pairs (PXY[p] = (x_2p, x_2p+1, y_2p, y_2p+1),
-// PZ[p] = (z_2p, z_2p+1), packed before the launch) and the squared distances of a pair are formed
-// with the paired FP32 instructions.  nt: minus the target's coordinates in the run's image plus
-// the shift taken off the candidates (the test's rounding near |r| = H does not matter: W and
-// grad W vanish there; the evaluation forms the pair's separation from exactly shifted operands).
-// Hits are appended to the lane's ring with the entry tag.  The loop is warp-uniform (up to the
-// longest run of the warp); a lane whose run is shorter tests clamped pairs and keeps none.
-// ZERO_OK: a pair at zero distance (the target itself) is harmless to the pass, so only
-// r^2 < H^2 is tested; the caller discounts the target from the pair count.
+// Test the candidates [g0, g1) of one run (per lane: its own run) against this lane's target,
+// UNROLL at a time: the positions come as pairs (PXY[p] = (x_2p, x_2p+1, y_2p, y_2p+1), PZ[p] =
+// (z_2p, z_2p+1), packed before the launch) and the squared distances of a pair are formed with
+// the paired FP32 instructions.  nt: minus the target's coordinates in the run's image plus the
+// shift taken off the candidates (the test's rounding near |r| = H does not matter: W and grad W
+// vanish there; the evaluation forms the pair's separation from exactly shifted operands).  A
+// step with hits appends one ring entry (its first pair, its hit mask and the run's shifts
+// `tag`).  The loop is warp-uniform (up to the longest run of the warp); the candidates of a
+// step that lie outside the lane's run (the one before g0 when g0 is odd, those past g1, and
+// every one of a lane past its run, which re-reads its last pairs) are masked out.  ZERO_OK: a
+// pair at zero distance (the target itself) is harmless to the pass, so only r^2 < H^2 is
+// tested; the caller discounts the target from the pair count.
 template <int D, bool ZERO_OK, class Drain>
 __device__ __forceinline__ void warp_scan_run(const float4* __restrict__ PXY, const float2* __restrict__ PZ, int g0,
                                               int g1, float2 ntx, float2 nty, float2 ntz, uint32_t tag, float H2,
-                                              uint32_t* list, unsigned& head, const unsigned& tail, Drain& drain) {
+                                              uint2* ring, WHits& h, Drain& drain) {
   constexpr int U = WCfg::UNROLL / 2;  // pairs per step
+  constexpr unsigned FULLM = (1u << (2 * U)) - 1u;
   constexpr unsigned MASK = WCfg::LIST - 1;
   const int lane = threadIdx.x & 31;
+  const int len = max(g1 - g0, 0);
   const int pa = g0 >> 1;
-  const int np = g1 > g0 ? ((g1 + 1) >> 1) - pa : 0;
+  const int odd = g0 & 1;
+  const int np = len > 0 ? ((g1 + 1) >> 1) - pa : 0;
   const int mlen = (int)__reduce_max_sync(kFull, (unsigned)np);
-  const int plast = max(pa + np - 1, 0);  // a valid pair for the clamped tests of a short run
-  auto test = [&](int it, float4 Q, float2 Z) {
-    const int k0 = 2 * (pa + it);
-    const float2 dx = __fadd2_rn(make_float2(Q.x, Q.y), ntx);
-    const float2 dy = __fadd2_rn(make_float2(Q.z, Q.w), nty);
-    float2 r2 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
-    if (D == 3) {
-      const float2 dz = __fadd2_rn(Z, ntz);
-      r2 = __ffma2_rn(dz, dz, r2);
-    }
-    const bool in = it < np;
-    list[(head & MASK) * 32u + lane] = (uint32_t)k0 | tag;
-    head += (in && k0 >= g0 && r2.x < H2 && (ZERO_OK || r2.x > 0.f)) ? 1u : 0u;
-    list[(head & MASK) * 32u + lane] = (uint32_t)(k0 + 1) | tag;
-    head += (in && k0 + 1 < g1 && r2.y < H2 && (ZERO_OK || r2.y > 0.f)) ? 1u : 0u;
-  };
-  auto ldq = [&](int it) { return __ldg(PXY + min(pa + it, plast)); };
-  auto ldz = [&](int it) { return D == 3 ? __ldg(PZ + min(pa + it, plast)) : make_float2(0.f, 0.f); };
-  int it = 0;
-  for (; it + U <= mlen; it += U) {
-    if (__any_sync(kFull, (int)(head - tail) > WCfg::LIST - 2 * U)) drain();
+  const int last = max(np - 1, 0);
+  unsigned fm = odd ? FULLM - 1u : FULLM;  // the first step's candidate 2 pa = g0 - 1 is not in the run
+  for (int it = 0; it < mlen; it += U) {
+    if (__any_sync(kFull, h.head - h.tail >= (unsigned)WCfg::LIST)) drain();
+    const int q0 = pa + min(it, last);
     float4 Q[U];
     float2 Z[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      Q[u] = ldq(it + u);
-      Z[u] = ldz(it + u);
+      Q[u] = __ldg(PXY + q0 + u);
+      Z[u] = D == 3 ? __ldg(PZ + q0 + u) : make_float2(0.f, 0.f);
     }
+    unsigned hm = 0u;
 #pragma unroll
-    for (int u = 0; u < U; ++u) test(it + u, Q[u], Z[u]);
-  }
-  if (it < mlen) {
-    if (__any_sync(kFull, (int)(head - tail) > WCfg::LIST - 2 * U)) drain();
-    for (; it < mlen; ++it) test(it, ldq(it), ldz(it));
+    for (int u = 0; u < U; ++u) {
+      const float2 dx = __fadd2_rn(make_float2(Q[u].x, Q[u].y), ntx);
+      const float2 dy = __fadd2_rn(make_float2(Q[u].z, Q[u].w), nty);
+      float2 r2 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
+      if (D == 3) {
+        const float2 dz = __fadd2_rn(Z[u], ntz);
+        r2 = __ffma2_rn(dz, dz, r2);
+      }
+      hm |= ((r2.x < H2 && (ZERO_OK || r2.x > 0.f)) ? 1u : 0u) << (2 * u);
+      hm |= ((r2.y < H2 && (ZERO_OK || r2.y > 0.f)) ? 1u : 0u) << (2 * u + 1);
+    }
+    // candidates of the step still in the run: 2 (pa + it) + k < g1
+    const int rem = len + odd - 2 * it;
+    const unsigned vm = rem >= 2 * U ? FULLM : (rem > 0 ? (1u << rem) - 1u : 0u);
+    const unsigned msk = hm & vm & fm;
+    fm = FULLM;
+    if (msk) {
+      ring[(h.head & MASK) * 32u + lane] = make_uint2((uint32_t)(pa + it), msk | tag);
+      ++h.head;
+      h.pend += __popc(msk);
+    }
   }
 }
 
-// One tile on one warp: per-lane target set-up, the union runs of every neighbour line, the
-// tests, the evaluation of the lists and the pass's epilogue.  The lanes are grouped by their
-// target's cell (match_any): each group walks the union of its own targets' reach, so a tile
-// whose targets span two or three cells does not test every target against all of them.
-// Returns the pairs this lane evaluated (the target itself not counted).
+// One tile on one warp: per-lane target set-up, the runs of every neighbour line, the tests, the
+// evaluation of the rings and the pass's epilogue.  Returns the pairs this lane evaluated (the
+// target itself not counted).
 template <int D, bool ZERO_OK, bool EX0, bool EX1, class Pass>
-__device__ __forceinline__ int warp_tile_task(const TravArgs& t, const Tile& T, uint32_t* list,
+__device__ __forceinline__ int warp_tile_task(const TravArgs& t, const Tile& T, uint2* ring,
                                               const float4* __restrict__ extra0, const float* __restrict__ extra1,
                                               Pass& pass) {
   constexpr int NL = TileCfg<D>::NL;
@@ -193,12 +253,12 @@ __device__ __forceinline__ int warp_tile_task(const TravArgs& t, const Tile& T, 
   typename Pass::Body body;
   bool active = false;
   float xt[3] = {0.f, 0.f, 0.f}, fl[3] = {0.f, 0.f, 0.f}, fh[3] = {0.f, 0.f, 0.f};
-  int cx = -1;  // invalid lanes form a group of their own and walk nothing
+  int cx = 0;
   if (valid) {
     active = pass.init(body, s, i, tv);
     const float4 A = __ldg(t.a.A + i);
     xt[0] = A.x; xt[1] = A.y; xt[2] = D == 3 ? A.z : 0.f;
-    const int c[3] = {(int)t.keys[i] - (s.cell_base + (T.cz * s.n[1] + T.cy) * s.n[0]), T.cy, T.cz};
+    const int c[3] = {(int)(t.keys[i] >> t.kshift) - (s.cell_base + (T.cz * s.n[1] + T.cy) * s.n[0]), T.cy, T.cz};
     cx = c[0];
 #pragma unroll
     for (int q = 0; q < D; ++q) {  // squared distances to the own cell's faces (0 past a face)
@@ -208,112 +268,105 @@ __device__ __forceinline__ int warp_tile_task(const TravArgs& t, const Tile& T, 
       fh[q] = a1 * a1;
     }
   }
-  // the lanes of one cell form a group (contiguous lanes: the targets are in cell order); the
-  // groups' lowest lanes
-  const unsigned gmask = __match_any_sync(kFull, cx);
-  const unsigned leaders = __ballot_sync(kFull, (gmask & ((1u << lane) - 1u)) == 0u);
   const float L[3] = {s.L[0], s.L[1], D == 3 ? s.L[2] : 0.f};
   const float H2 = s.H2, R2 = s.trimR2;
   const int nx = s.n[0];
   const bool px = s.periodic_mask & 1;
-  unsigned head = 0u, tail = 0u;
+  const float4* PXY = reinterpret_cast<const float4*>(t.packed);
+  const float2* PZ = reinterpret_cast<const float2*>(t.packed + 4 * warp_pairs_stride(t.N));
+  WHits h;
   int np = 0;
-  auto drain = [&]() { np += warp_drain<D, EX0, EX1>(L, t.a, extra0, extra1, list, head, tail, WCfg::EVAL, xt, body); };
+  auto drain = [&]() { np += warp_drain<D, EX0, EX1>(L, t.a, extra0, extra1, ring, h, WCfg::EVAL, xt, body); };
   for (int l = 0; l < NL; ++l) {
     float tsh[2], csh[2];
     const int lc = tile_line<D>(s, T, l, tsh, csh);  // uniform over the warp
     if (lc < 0) continue;
     const int dy = (D == 2) ? l - 1 : l % 3 - 1;
     const int dz = (D == 2) ? 0 : l / 3 - 1;
-    int clo = 0x7fffffff, chi = -0x7fffffff;
-    if (active) {
-      const float dyz = (dy < 0 ? fl[1] : dy > 0 ? fh[1] : 0.f) + (dz < 0 ? fl[2] : dz > 0 ? fh[2] : 0.f);
-      if (dyz < R2) {
-        clo = cx - (fl[0] + dyz < R2 ? 1 : 0);
-        chi = cx + 1 + (fh[0] + dyz < R2 ? 1 : 0);
+    // the lane's runs of this line: the left image (the line's upper end, shifted down by L), the
+    // in-box range and the right image (the line's lower end; the target takes off L)
+    int lg0 = 0, lg1 = 0, mg0 = 0, mg1 = 0, rg0 = 0, rg1 = 0;
+    const float dyz = (dy < 0 ? fl[1] : dy > 0 ? fh[1] : 0.f) + (dz < 0 ? fl[2] : dz > 0 ? fh[2] : 0.f);
+    if (active && dyz < R2) {
+      if (t.bin_off) {
+        // cells ordered by x sub-bin: the window of the reach's chord, [x - c, x + c] with c^2 =
+        // R^2 - dyz, in sub-bins of the line (the same monotone function the keys used)
+        constexpr int B = kXBins;
+        const int nb = nx * B;
+        const float c = sqrtf(R2 - dyz);
+        int bl = line_xbin<B>(s, xt[0] - c), bh = line_xbin<B>(s, xt[0] + c);
+        bl = px ? max(bl, -nb) : max(bl, 0);
+        bh = px ? min(bh, 2 * nb - 1) : min(bh, nb - 1);
+        const int* bo = t.bin_off + (size_t)lc * B;
+        if (bl < 0) { lg0 = bo[bl + nb]; lg1 = bo[nb]; }
+        const int b0 = max(bl, 0), b1 = min(bh, nb - 1);
+        if (b0 <= b1) { mg0 = bo[b0]; mg1 = bo[b1 + 1]; }
+        if (bh >= nb) { rg0 = bo[0]; rg1 = bo[bh - nb + 1]; }
+      } else {
+        // whole cells: the columns [clo, chi) the face-distance test keeps
+        int clo = cx - (fl[0] + dyz < R2 ? 1 : 0);
+        int chi = cx + 1 + (fh[0] + dyz < R2 ? 1 : 0);
+        if (!px) {
+          clo = max(clo, 0);
+          chi = min(chi, nx);
+        }
+        if (clo < 0) { lg0 = t.cell_off[lc + nx - 1]; lg1 = t.cell_off[lc + nx]; }
+        const int c0 = max(clo, 0), c1 = min(chi, nx);
+        if (c0 < c1) { mg0 = t.cell_off[lc + c0]; mg1 = t.cell_off[lc + c1]; }
+        if (chi > nx) { rg0 = t.cell_off[lc]; rg1 = t.cell_off[lc + 1]; }
       }
     }
-    {  // the union over the lane's group: full-warp reductions, one group at a time
-      int glo = clo, ghi = chi;
-      for (unsigned m = leaders; m; m &= m - 1u) {
-        const unsigned gm = __shfl_sync(kFull, gmask, __ffs(m) - 1);
-        const bool in = (gm >> lane) & 1u;
-        const int a = __reduce_min_sync(kFull, in ? clo : 0x7fffffff);
-        const int b = __reduce_max_sync(kFull, in ? chi : -0x7fffffff);
-        if (in) { glo = a; ghi = b; }
-      }
-      clo = glo;
-      chi = ghi;
-    }
-    if (!px) {
-      clo = max(clo, 0);
-      chi = min(chi, nx);
-    }
-    if (!__any_sync(kFull, active && clo < chi)) continue;  // (lanes of wall targets walk nothing)
+    const bool lft = __any_sync(kFull, lg0 < lg1), mid = __any_sync(kFull, mg0 < mg1),
+               rgt = __any_sync(kFull, rg0 < rg1);
+    if (!(lft || mid || rgt)) continue;  // (lanes of wall targets walk nothing)
     // the line's image on y and z: the target takes off L (upper) or the records do (lower)
     const float tl[3] = {xt[0], tsh[0] != 0.f ? xt[1] - L[1] : xt[1], (D == 3 && tsh[1] != 0.f) ? xt[2] - L[2] : xt[2]};
     const float sh[3] = {0.f, -csh[0], D == 3 ? -csh[1] : 0.f};
-    const uint32_t tag = (tsh[0] != 0.f ? 1u << 30 : 0u) | (D == 3 && tsh[1] != 0.f ? 1u << 31 : 0u) |
-                         (csh[0] != 0.f ? 1u << 27 : 0u) | (D == 3 && csh[1] != 0.f ? 1u << 28 : 0u);
-    const float4* PXY = reinterpret_cast<const float4*>(t.packed);
-    const float2* PZ = reinterpret_cast<const float2*>(t.packed + 4 * (size_t)((t.N + 1) / 2));
-    // left periodic image (groups whose union starts left of column 0): the last column of the
-    // line, shifted down by L
-    if (__any_sync(kFull, active && clo < 0)) {
-      int g0 = 0, g1 = 0;
-      if (active && clo < 0) { g0 = t.cell_off[lc + nx - 1]; g1 = t.cell_off[lc + nx]; }
-      warp_scan_run<D, ZERO_OK>(PXY, PZ, g0, g1, make_float2(-(tl[0] + L[0]), -(tl[0] + L[0])),
-                                make_float2(-(tl[1] + sh[1]), -(tl[1] + sh[1])),
-                                make_float2(-(tl[2] + sh[2]), -(tl[2] + sh[2])), tag | (1u << 26), H2, list, head,
-                                tail, drain);
+    const uint32_t tag = (tsh[0] != 0.f ? 1u << (kWShift + 4) : 0u) | (D == 3 && tsh[1] != 0.f ? 1u << (kWShift + 5) : 0u) |
+                         (csh[0] != 0.f ? 1u << (kWShift + 1) : 0u) | (D == 3 && csh[1] != 0.f ? 1u << (kWShift + 2) : 0u);
+    const float2 nty = make_float2(-(tl[1] + sh[1]), -(tl[1] + sh[1]));
+    const float2 ntz = make_float2(-(tl[2] + sh[2]), -(tl[2] + sh[2]));
+    if (lft) {
+      const float nx0 = -(tl[0] + L[0]);
+      warp_scan_run<D, ZERO_OK>(PXY, PZ, lg0, lg1, make_float2(nx0, nx0), nty, ntz, tag | (1u << kWShift), H2, ring,
+                                h, drain);
     }
-    // in-box columns
-    {
-      const int c0 = max(clo, 0), c1 = min(chi, nx);
-      int g0 = 0, g1 = 0;
-      if (active && c0 < c1) { g0 = t.cell_off[lc + c0]; g1 = t.cell_off[lc + c1]; }
-      warp_scan_run<D, ZERO_OK>(PXY, PZ, g0, g1, make_float2(-tl[0], -tl[0]),
-                                make_float2(-(tl[1] + sh[1]), -(tl[1] + sh[1])),
-                                make_float2(-(tl[2] + sh[2]), -(tl[2] + sh[2])), tag, H2, list, head, tail, drain);
-    }
-    // right periodic image (groups whose union ends right of the last column): the first column
-    // of the line; the target takes off L
-    if (__any_sync(kFull, active && chi > nx)) {
-      int g0 = 0, g1 = 0;
-      if (active && chi > nx) { g0 = t.cell_off[lc]; g1 = t.cell_off[lc + 1]; }
-      const float txr = xt[0] - L[0];
-      warp_scan_run<D, ZERO_OK>(PXY, PZ, g0, g1, make_float2(-txr, -txr),
-                                make_float2(-(tl[1] + sh[1]), -(tl[1] + sh[1])),
-                                make_float2(-(tl[2] + sh[2]), -(tl[2] + sh[2])), tag | (1u << 29), H2, list, head,
-                                tail, drain);
+    if (mid) warp_scan_run<D, ZERO_OK>(PXY, PZ, mg0, mg1, make_float2(-tl[0], -tl[0]), nty, ntz, tag, H2, ring, h, drain);
+    if (rgt) {
+      const float txr = -(xt[0] - L[0]);
+      warp_scan_run<D, ZERO_OK>(PXY, PZ, rg0, rg1, make_float2(txr, txr), nty, ntz, tag | (1u << (kWShift + 3)), H2,
+                                ring, h, drain);
     }
   }
-  while (__any_sync(kFull, head != tail)) drain();
+  while (__any_sync(kFull, h.pend > 0)) drain();
   if (ZERO_OK && active) --np;  // the target found itself
   body.template reduce<1>();
   if (valid) pass.finish(body, s, i, tv);
   return np;
 }
 
-// Skeleton of a warp-traversal launch: each warp takes its first tile by its index in the grid,
-// then further ones from the launch's tile counter; the CTA ends as the staged launches do
-// (end_tiles in sph_passes.cu: partial results, pair count, counters reset by the last CTA).
+// Skeleton of a warp-traversal launch: the warps take tiles one at a time from the launch's tile
+// counter, so the warps in flight walk a narrow front of consecutive tiles (a few planes of cell
+// lines), whose neighbour lines stay in L2 (splitting the tiles into one contiguous chunk per CTA,
+// which spreads the warps over the whole domain, made the 128^3 sweep 5 % slower).  The CTA ends
+// as the staged launches do (end_tiles in sph_passes.cu: partial results, pair count, counters
+// reset by the last CTA).
 template <int D, bool ZERO_OK, bool EX0, bool EX1, class Pass, class End>
 __device__ __forceinline__ void run_warp_tiles(const TravArgs& t, const Tile* __restrict__ tiles,
                                                const int* __restrict__ ntiles, const float4* __restrict__ extra0,
                                                const float* __restrict__ extra1, Pass& pass, End end) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5;
-  uint32_t* list = reinterpret_cast<uint32_t*>(smraw) + (size_t)warp * WCfg::LIST * 32;
+  uint2* ring = reinterpret_cast<uint2*>(smraw) + (size_t)warp * WCfg::LIST * 32;
   const int nt = *ntiles;
   long long pairs = 0;
-  int ti = blockIdx.x * WCfg::WARPS + warp;
-  while (ti < nt) {
-    const Tile T = tiles[ti];
-    pairs += warp_tile_task<D, ZERO_OK, EX0, EX1>(t, T, list, extra0, extra1, pass);
+  for (;;) {
     int nxt = 0;
-    if ((threadIdx.x & 31) == 0) nxt = (int)gridDim.x * WCfg::WARPS + atomicAdd(t.tile_ctr, 1);
-    ti = __shfl_sync(kFull, nxt, 0);
+    if ((threadIdx.x & 31) == 0) nxt = atomicAdd(t.tile_ctr, 1);
+    const int ti = __shfl_sync(kFull, nxt, 0);
+    if (ti >= nt) break;
+    const Tile T = tiles[ti];
+    pairs += warp_tile_task<D, ZERO_OK, EX0, EX1>(t, T, ring, extra0, extra1, pass);
   }
   end(pairs);
 }

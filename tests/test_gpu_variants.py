@@ -14,6 +14,8 @@ from tests.test_gpu_parity import check_rollout
 pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+from paper_2507_21684_b300.build import VARIANTS as _VARIANTS  # noqa: E402  (no compilation at import)
 SCRIPT = r"""
 import sys, numpy as np
 import paper_2507_21684_b300 as sph
@@ -26,7 +28,7 @@ np.savez(sys.argv[2], x=x, v=v, rho=r)
 """
 
 
-@pytest.mark.parametrize("variant", ["lanes8", "lanes2", "small", "small3", "cells2", "cells3", "staged3"])
+@pytest.mark.parametrize("variant", sorted(v for v in _VARIANTS if v != "default"))
 @pytest.mark.parametrize("case", ["dambreak_64", "tgv3d_24"])
 def test_variant_rollouts_match_oracle(orc, tmp_path, variant, case):
     from paper_2507_21684_b300 import build, tune
