@@ -29,12 +29,13 @@ VARIANTS = {
     "cells3": {"SPH_TILE3_CUT": 0},
     # the 3D sweep on the staged traversal instead of the warp-per-tile one (with its whole-cell cut)
     "staged3": {"SPH_W3": 0, "SPH_TILE3_CUT": 0},
-    # the warp-per-tile 3D sweep with 16 candidates (8 paired loads) per step of the test loop
-    "w3u16": {"SPH_W_UNROLL": 16},
+    # the warp-per-tile 3D sweep with 8 candidates (4 paired loads) per step of the test loop
+    # (default 16)
+    "w3u8": {"SPH_W_UNROLL": 8},
     # the 3D sweep's evaluation one hit per iteration (default two)
     "w3d1": {"SPH_W_DRAIN2": 0},
-    # 8 x sub-bins per cell in the 3D sweep's keys (default 4)
-    "w3b8": {"SPH_W_XSHIFT": 3},
+    # 4 x sub-bins per cell in the 3D sweep's keys (default 8)
+    "w3b4": {"SPH_W_XSHIFT": 2},
     # the cooperative rebuild on one CTA per SM (a cheaper launch on the steps that rebuild nothing)
     "rb1": {"SPH_RB_CTAS_PER_SM": 1},
 }

@@ -371,10 +371,10 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Sub-bins of a cell along x (3D warp-per-tile sweep): the cell keys of such scenes carry the
-// particle's sub-bin in their low kXShift bits (cell * kXBins + bin), so the sort orders every
+// particle's sub-bin in their low kXShift bits (cell * kXBins + bin; 8 sub-bins), so the sort orders every
 // cell by sub-bin and the sweep can walk x windows of a line instead of whole cells.
 #ifndef SPH_W_XSHIFT
-#define SPH_W_XSHIFT 2
+#define SPH_W_XSHIFT 3
 #endif
 constexpr int kXShift = SPH_W_XSHIFT;
 constexpr int kXBins = 1 << kXShift;

@@ -563,12 +563,14 @@ std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& o
   uint32_t* sums = scratch + (sort_scratch_words(N) - 2048 - 64);
   // boff_out (3D warp-per-tile sweep): keys with x sub-bins, so every cell comes out ordered by
   // sub-bin, and the sub-bins' offsets beside the cells'
-  const bool xb = boff_out && D == 3;
+  const bool bins = boff_out && D == 3;
+  // the folded positions as the displacement check's reference: with a Verlet skin only
+  float4* xref = dev_policy ? xbuild : nullptr;
   for (int p = 0; p < passes; ++p) {
     if (D == 2)
       launch_sort_pass<2>(ki, vi, ko, vo, N, 8 * p, hist, sums, p == 0 ? dseg : nullptr, in, st);
     else
-      launch_sort_pass<3>(ki, vi, ko, vo, N, 8 * p, hist, sums, p == 0 ? dseg : nullptr, in, st, xb);
+      launch_sort_pass<3>(ki, vi, ko, vo, N, 8 * p, hist, sums, p == 0 ? dseg : nullptr, in, st, bins);
     CKL();
     std::swap(ki, ko);
     std::swap(vi, vo);
@@ -584,9 +586,9 @@ std::pair<uint32_t*, uint32_t*> Scene::rebuild(const Arrays& in, const Arrays& o
     pm = perm_out;
   }
   if (D == 2)
-    launch_permute<2>(dseg, N, pm, in, out, ks, C_tot, off_out, xbuild, st);
+    launch_permute<2>(dseg, N, pm, in, out, ks, C_tot, off_out, xref, st);
   else
-    launch_permute<3>(dseg, N, pm, in, out, ks, C_tot, off_out, xbuild, st, xb ? boff_out : nullptr);
+    launch_permute<3>(dseg, N, pm, in, out, ks, C_tot, off_out, xref, st, bins ? boff_out : nullptr);
   CKL();
   build_tiles(off_out, out.meta, tiles_out ? tiles_out : tiles, ntiles_out ? ntiles_out : d_ntiles);
   prof_end();

@@ -8,12 +8,16 @@ namespace sph {
 
 // Coordinate q of x = hi + lo folded into the primary box, rounded to FP32, and the fold offset
 // o = L floor((x - lo_box) / L) (decided in FP64; in_primary_box() settles the common case 0
-// without the FP64 division and gives the same result).
+// without the FP64 division and gives the same result).  With o = 0 the result is hi + lo rounded
+// once to FP32, which one FP32 addition gives exactly (IEEE addition rounds the exact sum; B300's
+// FP64 rate is low, and this runs for every particle of every rebuild).
 __device__ __forceinline__ float fold_coord(const DevSeg& s, int q, float hi, float lo, double* o_out) {
+  if (!((s.periodic_mask >> q) & 1) || in_primary_box(s, q, hi)) {
+    *o_out = 0.0;
+    return __fadd_rn(hi, lo);
+  }
   const double x = __dadd_rn((double)hi, (double)lo);
-  double f = 0.0;
-  if (((s.periodic_mask >> q) & 1) && !in_primary_box(s, q, hi))
-    f = floor(__ddiv_rn(__dsub_rn(x, s.lo_d[q]), s.L_d[q]));
+  const double f = floor(__ddiv_rn(__dsub_rn(x, s.lo_d[q]), s.L_d[q]));
   const double o = __dmul_rn(s.L_d[q], f);
   *o_out = o;
   return (float)__dsub_rn(x, o);

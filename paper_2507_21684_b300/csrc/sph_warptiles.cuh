@@ -39,7 +39,7 @@ namespace sph {
 #endif
 // candidates per step of the test loop (two per paired load; loads in flight per lane)
 #ifndef SPH_W_UNROLL
-#define SPH_W_UNROLL 8
+#define SPH_W_UNROLL 16
 #endif
 // evaluate two hits per iteration of the evaluation loop (their loads in flight together)
 #ifndef SPH_W_DRAIN2
