@@ -338,9 +338,10 @@ def run_plain(sph, reqs):
                 p99_s=float(np.percentile(lat, 99)), makespan_s=span)
 
 
-def run_served(sph, reqs, budget=120 << 30):
-    """Requests submitted at their arrival times to the continuous-batching server."""
-    with sph.Server(budget, 1024) as sv:
+def run_served(sph, reqs, budget=120 << 30, max_active=1024):
+    """Requests submitted at their arrival times to the continuous-batching server (at most
+    max_active requests admitted at once)."""
+    with sph.Server(budget, max_active) as sv:
         t0 = time.perf_counter()
         tickets = []
         for r, sp in reqs:
@@ -504,6 +505,8 @@ def main():
     ap.add_argument("--no-tile-tune", action="store_true", help="use the default tile shape (no variant timing)")
     ap.add_argument("--variant", default="default", help="--profile-run: tile-shape variant of the library")
     ap.add_argument("--stream-rates", type=float, nargs="*", default=[20.0, 80.0, 320.0])
+    ap.add_argument("--stream-max-active", type=int, default=1024,
+                    help="served stream: most requests the server admits at once")
     ap.add_argument("--stream-skin", type=float, default=0.1,
                     help="Verlet skin (fraction of H) of every request of the served stream, plain and served alike")
     ap.add_argument("--stream-only", action="store_true", help="only the served stream (plain vs served)")
@@ -522,7 +525,7 @@ def main():
         for rate in args.stream_rates:
             reqs = _stream_specs(args.stream_scenes, rate, skin_over_H=args.stream_skin)
             pl = run_plain(sph, reqs)
-            sv = run_served(sph, reqs)
+            sv = run_served(sph, reqs, max_active=args.stream_max_active)
             out[f"{rate:g}_req_s"] = {"plain": pl, "served": sv,
                                       "served_over_plain_throughput": sv["particle_steps_per_s"] / pl["particle_steps_per_s"],
                                       "served_over_plain_p99": sv["p99_s"] / pl["p99_s"]}
@@ -857,7 +860,7 @@ def run_extras(sph, torch, tune, args, variant, peaks, tiles2=None) -> dict:
     for rate in args.stream_rates:
         reqs = _stream_specs(args.stream_scenes, rate, skin_over_H=args.stream_skin)
         pl = run_plain(sph, reqs)
-        sv = run_served(sph, reqs)
+        sv = run_served(sph, reqs, max_active=args.stream_max_active)
         stream[f"{rate:g}_req_s"] = {"plain": pl, "served": sv,
                                      "served_over_plain_throughput": sv["particle_steps_per_s"] / pl["particle_steps_per_s"],
                                      "served_over_plain_p99": sv["p99_s"] / pl["p99_s"]}

@@ -38,6 +38,12 @@ VARIANTS = {
     "w3b4": {"SPH_W_XSHIFT": 2},
     # the cooperative rebuild on one CTA per SM (a cheaper launch on the steps that rebuild nothing)
     "rb1": {"SPH_RB_CTAS_PER_SM": 1},
+    # the 3D sweep's earlier schedule: CTAs of 4 warps at 5 per SM, every warp claiming its own tiles
+    # from the launch's counter, 32-entry hit rings (default: one CTA of 24 warps per SM taking
+    # chunks of 8 tiles, 16-entry rings)
+    "w3w4": {"SPH_W_WARPS": 4, "SPH_W_MINB": 5, "SPH_W_CHUNK": 0, "SPH_W_LIST": 32},
+    # chunks of 12 tiles
+    "w3c12": {"SPH_W_CHUNK": 12},
 }
 
 

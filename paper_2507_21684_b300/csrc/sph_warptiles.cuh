@@ -14,8 +14,9 @@
 //
 // Against the staged traversal (sph_tiles.cuh: a CTA stages the 3^(d-1) lines into shared memory
 // and LANES threads split one target's candidates) this needs no staging, no CTA barrier per tile,
-// no reduction over lanes and no tile-size fallback.  Each warp takes its own tiles from the
-// launch's tile counter.
+// no reduction over lanes and no tile-size fallback.  A CTA (one per SM) claims chunks of
+// consecutive tiles from the launch's tile counter and its warps take the chunk's tiles as they
+// free up.
 //
 // Periodic images follow the staged traversal's convention, so that every coordinate difference
 // is formed from exactly shifted operands: a lower image (the line or column wraps below the box)
@@ -26,12 +27,15 @@
 
 namespace sph {
 
+// warps per CTA: one CTA of 24 warps per SM (80 registers a thread), so that every warp of an SM
+// takes its tiles from the same chunks and shares the SM's L1
 #ifndef SPH_W_WARPS
-#define SPH_W_WARPS 4
+#define SPH_W_WARPS 24
 #endif
-// hit-ring entries per lane (one entry per step of the test loop that found a hit)
+// hit-ring entries per lane (one entry per step of the test loop that found a hit); 16 entries
+// (96 KB of rings per CTA) leave the rest of the SM's unified memory to L1
 #ifndef SPH_W_LIST
-#define SPH_W_LIST 32
+#define SPH_W_LIST 16
 #endif
 // hits of every lane evaluated at a time when some lane's ring is full
 #ifndef SPH_W_EVAL
@@ -47,7 +51,12 @@ namespace sph {
 #endif
 // CTAs per SM the warp-traversal kernels are compiled for (register budget 64K / (MINB x THREADS))
 #ifndef SPH_W_MINB
-#define SPH_W_MINB 5
+#define SPH_W_MINB 1
+#endif
+// consecutive tiles a CTA claims from the launch's counter at a time, shared out to its warps as
+// they free up (0: every warp claims its own tiles)
+#ifndef SPH_W_CHUNK
+#define SPH_W_CHUNK 8
 #endif
 
 struct WCfg {
@@ -345,12 +354,21 @@ __device__ __forceinline__ int warp_tile_task(const TravArgs& t, const Tile& T, 
   return np;
 }
 
-// Skeleton of a warp-traversal launch: the warps take tiles one at a time from the launch's tile
+// Skeleton of a warp-traversal launch: tiles are handed out in launch order from the launch's tile
 // counter, so the warps in flight walk a narrow front of consecutive tiles (a few planes of cell
-// lines), whose neighbour lines stay in L2 (splitting the tiles into one contiguous chunk per CTA,
+// lines), whose neighbour lines stay in L2 (splitting the tiles into one contiguous range per CTA,
 // which spreads the warps over the whole domain, made the 128^3 sweep 5 % slower).  The CTA ends
 // as the staged launches do (end_tiles in sph_passes.cu: partial results, pair count, counters
 // reset by the last CTA).
+//
+// With SPH_W_CHUNK > 0 (the default) the counter hands out chunks of CHUNK consecutive tiles to a
+// CTA, and the CTA's warps take the chunk's tiles one at a time as they free up, so the warps that
+// share an SM's L1 work on neighbouring tiles of one cell line, whose neighbour lines largely
+// coincide (with one warp per claim the warps of an SM held tiles about 148 apart).  A warp that
+// takes the first tile of a chunk claims the chunk and publishes its index in a small ring of
+// slots in shared memory; one that takes a later tile waits (bounded) for that slot.
+constexpr long long kChunkSpins = 1LL << 20;
+
 template <int D, bool ZERO_OK, bool EX0, bool EX1, class Pass, class End>
 __device__ __forceinline__ void run_warp_tiles(const TravArgs& t, const Tile* __restrict__ tiles,
                                                const int* __restrict__ ntiles, const float4* __restrict__ extra0,
@@ -360,9 +378,43 @@ __device__ __forceinline__ void run_warp_tiles(const TravArgs& t, const Tile* __
   uint2* ring = reinterpret_cast<uint2*>(smraw) + (size_t)warp * WCfg::LIST * 32;
   const int nt = *ntiles;
   long long pairs = 0;
+#if SPH_W_CHUNK > 0
+  constexpr int CH = SPH_W_CHUNK, SLOTS = 8;
+  __shared__ int s_claim;         // tiles this CTA has taken so far
+  __shared__ int s_chunk[SLOTS];  // the launch's index of the CTA's c-th chunk, in slot c % SLOTS
+  __shared__ int s_ready[SLOTS];  // c + 1 once slot c % SLOTS holds the c-th chunk
+  if (threadIdx.x == 0) s_claim = 0;
+  if (threadIdx.x < SLOTS) s_ready[threadIdx.x] = 0;
+  __syncthreads();
+#endif
   for (;;) {
     int nxt = 0;
-    if ((threadIdx.x & 31) == 0) nxt = atomicAdd(t.tile_ctr, 1);
+    if ((threadIdx.x & 31) == 0) {
+#if SPH_W_CHUNK > 0
+      const int k = atomicAdd(&s_claim, 1);
+      const int c = k / CH, pos = k - c * CH, slot = c % SLOTS;
+      int g;
+      if (pos == 0) {
+        g = atomicAdd(t.tile_ctr, 1);
+        s_chunk[slot] = g;
+        __threadfence_block();
+        atomicExch(&s_ready[slot], c + 1);
+      } else {
+        long long it = 0;
+        while (*(volatile int*)&s_ready[slot] != c + 1 && ++it <= kChunkSpins) __nanosleep(16);
+        __threadfence_block();
+        if (it > kChunkSpins) {
+          atomicOr(t.status, 2);
+          g = nt;  // gives up: no further tile for this warp
+        } else {
+          g = *(volatile int*)&s_chunk[slot];
+        }
+      }
+      nxt = g >= nt ? nt : g * CH + pos;
+#else
+      nxt = atomicAdd(t.tile_ctr, 1);
+#endif
+    }
     const int ti = __shfl_sync(kFull, nxt, 0);
     if (ti >= nt) break;
     const Tile T = tiles[ti];
