@@ -335,7 +335,7 @@ def run_plain(sph, reqs):
         ps += sp["n_fluid"] * r.steps
     span = time.perf_counter() - t0
     return dict(particle_steps_per_s=ps / span, p50_s=float(np.percentile(lat, 50)),
-                p99_s=float(np.percentile(lat, 99)), makespan_s=span)
+                p99_s=float(np.percentile(lat, 99)), makespan_s=span, _lat=lat)
 
 
 def run_served(sph, reqs, budget=120 << 30, max_active=1024):
@@ -349,18 +349,40 @@ def run_served(sph, reqs, budget=120 << 30, max_active=1024):
             if now < r.arrival_s:
                 time.sleep(r.arrival_s - now)
             tickets.append((sv.submit(sp, r.steps, adjoint=r.adjoint, ckpt_every=20), r, sp))
-        lat, ps = [], 0.0
+        lat, wait, ps = [], [], 0.0
         t_end = 0.0
         for t, r, sp in tickets:
             res = sv.wait(t)
             lat.append(res["t_done"] - res["t_submit"])
+            wait.append(res["t_admit"] - res["t_submit"])
             t_end = max(t_end, res["t_done"])
             ps += sp["n_fluid"] * r.steps
         span = time.perf_counter() - t0
         info = sv.stats()
     return dict(particle_steps_per_s=ps / span, p50_s=float(np.percentile(lat, 50)),
                 p99_s=float(np.percentile(lat, 99)), makespan_s=span, max_batch=info["max_batch"],
-                repacks=info["repacks"])
+                repacks=info["repacks"], _lat=lat, _wait=wait)
+
+
+def latency_diag(reqs, pl, sv, top: int = 6):
+    """Where the latencies differ: mean latency per request class (forward / adjoint, particle
+    count below or above the median) on both paths, and the requests with the largest served
+    latencies (class, size, steps, plain and served latency, the served admission wait)."""
+    lp, ls, ws = pl.pop("_lat"), sv.pop("_lat"), sv.pop("_wait")
+    ns = np.array([sp["n_fluid"] for _, sp in reqs])
+    med = float(np.median(ns))
+    cls = {}
+    for k, (r, sp) in enumerate(reqs):
+        key = ("adj" if r.adjoint else "fwd") + ("_large" if sp["n_fluid"] > med else "_small")
+        c = cls.setdefault(key, [0, 0.0, 0.0])
+        c[0] += 1
+        c[1] += lp[k]
+        c[2] += ls[k]
+    by_class = {k: {"n": c[0], "plain_mean_s": c[1] / c[0], "served_mean_s": c[2] / c[0]} for k, c in cls.items()}
+    order = np.argsort(ls)[::-1][:top]
+    worst = [{"adjoint": bool(reqs[k][0].adjoint), "particles": int(ns[k]), "steps": int(reqs[k][0].steps),
+              "plain_s": float(lp[k]), "served_s": float(ls[k]), "served_wait_s": float(ws[k])} for k in order]
+    return {"by_class": by_class, "largest_served": worst}
 
 
 def cpu_baseline(spec, budget_s: float = 15.0):
@@ -526,9 +548,10 @@ def main():
             reqs = _stream_specs(args.stream_scenes, rate, skin_over_H=args.stream_skin)
             pl = run_plain(sph, reqs)
             sv = run_served(sph, reqs, max_active=args.stream_max_active)
+            diag = latency_diag(reqs, pl, sv)
             out[f"{rate:g}_req_s"] = {"plain": pl, "served": sv,
                                       "served_over_plain_throughput": sv["particle_steps_per_s"] / pl["particle_steps_per_s"],
-                                      "served_over_plain_p99": sv["p99_s"] / pl["p99_s"]}
+                                      "served_over_plain_p99": sv["p99_s"] / pl["p99_s"], "latency_diag": diag}
         print(json.dumps({"stream_only": True, "skin_over_H": args.stream_skin, "by_rate": out}))
         return
 
@@ -621,7 +644,7 @@ def main():
 
     # neighbour-search setting of the headline scene chosen by the library's autotuner (a Verlet
     # skin; every candidate finds the same neighbours each step)
-    tuned = tune.tune_skin(spec, skins=(0.0, 0.02, 0.05), steps=40, warmup=10)
+    tuned = tune.tune_skin(spec, skins=(0.0, 0.05, 0.1, 0.15), steps=40, warmup=10)
     best_skin = replica_choice(tuned["best"]["skin_over_H"])
     spec = dict(spec, params=tune.with_skin(spec, best_skin)["params"])
     workload = dict(workload, verlet_skin_over_H=best_skin, library_variant=variant, tile_variant_3d=v3,
@@ -861,9 +884,10 @@ def run_extras(sph, torch, tune, args, variant, peaks, tiles2=None) -> dict:
         reqs = _stream_specs(args.stream_scenes, rate, skin_over_H=args.stream_skin)
         pl = run_plain(sph, reqs)
         sv = run_served(sph, reqs, max_active=args.stream_max_active)
+        diag = latency_diag(reqs, pl, sv)
         stream[f"{rate:g}_req_s"] = {"plain": pl, "served": sv,
                                      "served_over_plain_throughput": sv["particle_steps_per_s"] / pl["particle_steps_per_s"],
-                                     "served_over_plain_p99": sv["p99_s"] / pl["p99_s"]}
+                                     "served_over_plain_p99": sv["p99_s"] / pl["p99_s"], "latency_diag": diag}
     extras["served_stream"] = {
         "scenes": args.stream_scenes, "sizes": "log-uniform in [1024, 262144] (square lattices)",
         "steps": "uniform in [50, 500]", "adjoint_fraction": 0.2, "arrivals": "Poisson", "by_rate": stream,

@@ -30,8 +30,9 @@
  *   - Results are always returned in the caller's original particle order.
  *   - A scene is bound to one CUDA stream (0 = legacy default stream).  Calls on one scene
  *     are not thread-safe; different scenes may be used from different threads.
- *   - Device memory comes from the allocator set with sph_set_allocator (default: the device's
- *     stream-ordered pool, cudaMallocAsync).
+ *   - Device memory of scenes comes from the allocator set with sph_set_allocator (default: the
+ *     device's stream-ordered pool, cudaMallocAsync).  The serving loop's scenes always use the
+ *     stream-ordered pool (see sph_server_create).
  *   - A scene bound to stream 0 runs on a private non-blocking stream that is ordered after the
  *     legacy default stream at every call and before it when device outputs are returned.
  */
@@ -371,6 +372,11 @@ typedef struct sph_server_info {
 } sph_server_info;
 
 typedef struct sph_server sph_server;
+/* The server's threads create and destroy scenes at a high rate (every re-pack of the batch,
+ * every adjoint request); they allocate from the CUDA stream-ordered pool of the server's streams
+ * (cudaMallocAsync / cudaFreeAsync), never through the sph_set_allocator hooks, which may call
+ * back into an interpreter whose lock those threads would contend for.  hbm_budget_bytes bounds
+ * what the admitted requests may hold; max_active the number of requests admitted at once. */
 SPH_API int sph_server_create(size_t hbm_budget_bytes, int max_active, sph_server** out);
 /* SPH_EINVAL for malformed requests or one that alone exceeds the budget. */
 SPH_API int sph_submit(sph_server* server, const sph_request* request, uint64_t* ticket);

@@ -44,6 +44,9 @@ VARIANTS = {
     "w3w4": {"SPH_W_WARPS": 4, "SPH_W_MINB": 5, "SPH_W_CHUNK": 0, "SPH_W_LIST": 32},
     # chunks of 12 tiles
     "w3c12": {"SPH_W_CHUNK": 12},
+    # captured 3D steps with a skin rebuild in one cooperative launch instead of a conditional
+    # graph node (the same kernels; ncu can profile these graphs)
+    "coop3": {"SPH_COOP3": 1},
 }
 
 

@@ -13,6 +13,7 @@ struct RebuildArgs {
   uint32_t *kA, *vA, *kB, *vB;     // sort ping-pong buffers (result in kA/vA after an even count)
   uint32_t *hist, *sums;           // 256 x nb digit counts, scan block totals (>= grid words)
   int* off;                        // CSR cell offsets (C + 1)
+  int* boff;                       // 3D: keys with x sub-bins; their CSR offsets (C * kXBins + 1), or null
   float4* xb;                      // folded positions at the build (or null)
   const int* line_base;
   int n_lines;

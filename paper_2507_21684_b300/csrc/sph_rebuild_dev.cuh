@@ -133,8 +133,10 @@ __device__ bool rebuild_body(const RebuildArgs& r, RebuildSmem& sm) {
   const int M = 256 * r.nb;
   for (int p = 0; p < r.passes; ++p) {
     for (int tile = blockIdx.x; tile < r.nb; tile += gridDim.x) {
-      if (p == 0)
-        sort_hist_tile<D, true>(tile, ki, r.N, 0, r.hist, r.nb, r.segs, r.in, sm.hist);
+      if (p == 0 && D == 3 && r.boff)
+        sort_hist_tile<D, 2>(tile, ki, r.N, 0, r.hist, r.nb, r.segs, r.in, sm.hist);
+      else if (p == 0)
+        sort_hist_tile<D, 1>(tile, ki, r.N, 0, r.hist, r.nb, r.segs, r.in, sm.hist);
       else
         sort_hist_tile<D, false>(tile, ki, r.N, 8 * p, r.hist, r.nb, r.segs, r.in, sm.hist);
       __syncthreads();
@@ -142,8 +144,10 @@ __device__ bool rebuild_body(const RebuildArgs& r, RebuildSmem& sm) {
     if (!grid_barrier(r.bar, r.status)) return false;
     if (!grid_scan(r.hist, M, r.sums, sm.wsum, r.bar, r.status)) return false;
     for (int tile = blockIdx.x; tile < r.nb; tile += gridDim.x) {
-      if (p == 0)
-        sort_scatter_tile<D, true>(tile, ki, vi, ko, vo, r.N, 0, r.hist, r.nb, r.segs, r.in, sm.scatter);
+      if (p == 0 && D == 3 && r.boff)
+        sort_scatter_tile<D, 2>(tile, ki, vi, ko, vo, r.N, 0, r.hist, r.nb, r.segs, r.in, sm.scatter);
+      else if (p == 0)
+        sort_scatter_tile<D, 1>(tile, ki, vi, ko, vo, r.N, 0, r.hist, r.nb, r.segs, r.in, sm.scatter);
       else
         sort_scatter_tile<D, false>(tile, ki, vi, ko, vo, r.N, 8 * p, r.hist, r.nb, r.segs, r.in, sm.scatter);
       __syncthreads();
@@ -154,7 +158,7 @@ __device__ bool rebuild_body(const RebuildArgs& r, RebuildSmem& sm) {
   }
   // permute into `out` with the cell ranges and the displacement reference
   for (int k = blockIdx.x * kRbThreads + threadIdx.x; k <= r.N; k += gridDim.x * kRbThreads)
-    permute_one<D>(k, r.segs, r.N, vi, r.in, r.out, ki, r.C, r.off, r.xb);
+    permute_one<D>(k, r.segs, r.N, vi, r.in, r.out, ki, r.C, r.off, r.xb, D == 3 ? r.boff : nullptr);
   if (!grid_barrier(r.bar, r.status)) return false;
   // back into `in` (the buffer parity of the step does not depend on the rebuild), and the tiles
   if (r.copy_back)

@@ -15,6 +15,17 @@
 #include "sph_runtime.h"
 #include "sph_rebuild.cuh"
 
+// Captured steps of 3D scenes with a Verlet skin rebuild in a conditional graph node whose body is
+// the stand-alone rebuild (0) or in one cooperative launch (1).  On the 128^3 vortex with a 0.1 H
+// skin: 1.185 against 1.213 ms per step (the cooperative rebuild of 2.1 M particles, with two CTAs
+// per SM, takes 0.35 ms against 0.22 ms for the stand-alone kernels; a step's node costs about
+// 10 us against 5 us for a cooperative launch that finds no rebuild due).  ncu profiles no kernel
+// node of a graph with conditional nodes, so captures of 3D steps with a skin use the variant with
+// the cooperative launch (the same kernels).
+#ifndef SPH_COOP3
+#define SPH_COOP3 0
+#endif
+
 namespace sph {
 
 // ---------------------------------------------------------------- errors
@@ -377,15 +388,15 @@ void Scene::setup_checked(const std::vector<sph_params>& prms, const std::vector
     replay_k = dev_policy ? 16 : 1;
   }
   // the decision is taken by the sweep and the rebuild is one cooperative launch when the
-  // device supports it; otherwise a one-thread kernel decides and a conditional graph node rebuilds
+  // device supports it (2D; 3D with SPH_COOP3); otherwise a one-thread kernel decides and a
+  // conditional graph node rebuilds
   coop_grid = D == 2 ? rebuild_coop_grid<2>() : rebuild_coop_grid<3>();
   int coop_attr = 0, dev = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, dev));
-  use_coop = dev_policy && coop_grid > 0 && coop_attr != 0;
-  // keys with x sub-bins for the warp-per-tile sweep (not in the cooperative rebuild, so scenes
-  // that use it keep whole cells); they need kXShift more key bits
-  xorder = D == 3 && !use_coop && warp_sweep(D, N) && (long long)C_tot * kXBins < (1LL << 31);
+  use_coop = dev_policy && coop_grid > 0 && coop_attr != 0 && (D == 2 || SPH_COOP3);
+  // keys with x sub-bins for the warp-per-tile sweep; they need kXShift more key bits
+  xorder = D == 3 && warp_sweep(D, N) && (long long)C_tot * kXBins < (1LL << 31);
   if (xorder) {
     bits = key_bits((long long)C_tot * kXBins);
     passes = std::max(1, (bits + 7) / 8);
@@ -900,6 +911,7 @@ RebuildArgs Scene::coop_args(const Arrays& in, const Arrays& out, int* off, cons
   r.hist = scratch;
   r.sums = scratch + (sort_scratch_words(N) - 2048 - 64);
   r.off = off;
+  r.boff = xorder ? bin_off : nullptr;
   r.xb = xbuild;
   r.line_base = line_base;
   r.n_lines = n_lines;
@@ -918,7 +930,7 @@ RebuildArgs Scene::coop_args(const Arrays& in, const Arrays& out, int* off, cons
 
 void Scene::step_coop() {
   coop_rebuild();
-  TravArgs t = trav(buf[cur], keys_sorted, cell_off);
+  TravArgs t = trav(buf[cur], keys_sorted, cell_off, xorder ? bin_off : nullptr);
   passes_before_sweep(t, nullptr, nullptr, walls_in_sweep());
   sweep(t, buf[1 - cur], nullptr, nullptr, walls_in_sweep());
   cur = 1 - cur;

@@ -12,6 +12,14 @@
 // Every scene's arithmetic is independent of the others in the batch and every step rebuilds the
 // cells, so a served result is bitwise the result of running that scene alone (with the cells
 // rebuilt every step).
+//
+// Device memory: the server's scenes allocate from the CUDA stream-ordered pool of the server's
+// streams, not through the allocator hook of sph_set_allocator.  The hook may call back into an
+// interpreter (the PyTorch binding's caching allocator runs in Python), and the server's threads
+// would then contend for that interpreter's lock on every allocation of every re-pack and adjoint
+// scene: measured on the 20 requests/s stream, served adjoint requests took twice as long as the
+// same requests run alone through the hook's caller.  The HBM budget of the admission covers
+// these allocations as before.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -157,7 +165,7 @@ struct Server {
       mx.push_back(std::max(m, 16.0));
     }
     auto nb = std::make_unique<Scene>();
-    init_mem(nb->mem);
+    // (no init_mem: the server's scenes allocate from the CUDA stream-ordered pool, see above)
     nb->setup_checked(prm, nfs, nws, mx);
     nb->bind_stream(st_fwd);
     nb->alloc_all();
@@ -305,12 +313,14 @@ struct Server {
       std::string err;
       try {
         Scene sc;
-        init_mem(sc.mem);
         double m = 16.0;
         for (float c : r->x) m = std::max(m, (double)std::fabs(c));
         sc.setup_checked({r->p}, {r->nf}, {r->nw}, {m});
         sc.bind_stream(st_adj[w]);
-        sc.use_graphs = false;  // a one-off scene: capturing graphs would cost more than it saves
+        // a one-off scene: eager steps (capturing graphs costs more than it saves here) that take
+        // the device's rebuild decision, so a Verlet skin pays off as in graph-launched steps
+        sc.use_graphs = false;
+        sc.eager_dev = true;
         sc.alloc_all();
         sc.upload(0, r->x.data(), r->v.data(), r->rho.data(), r->mass.data(), 0);
         sc.rollout(r->n_steps, r->ckpt);

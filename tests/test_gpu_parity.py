@@ -216,12 +216,14 @@ def _verlet(s, skin_over_H, interval=1 << 20):
     return dict(s, params=p)
 
 
-@pytest.mark.parametrize("case,skin,n", [("tgv2d_64", 0.1, 40), ("dambreak_128", 0.02, 300)])
+@pytest.mark.parametrize("case,skin,n", [("tgv2d_64", 0.1, 40), ("dambreak_128", 0.02, 300), ("tgv3d_24", 0.1, 40)])
 def test_verlet_skin_rebuilds_on_displacement(sph, orc, case, skin, n):
     """Skin and no interval limit: the device-side displacement check alone decides when the cells
     are rebuilt (fewer rebuilds than steps, more than the initial one), and the rollout still
-    matches the oracle, which searches neighbours every step."""
-    base = si.taylor_green_2d(64, seed=0) if case == "tgv2d_64" else si.dam_break(res=128)
+    matches the oracle, which searches neighbours every step.  In 3D the rebuilds order the cells
+    by x sub-bin for the warp-per-tile sweep."""
+    base = {"tgv2d_64": lambda: si.taylor_green_2d(64, seed=0), "dambreak_128": lambda: si.dam_break(res=128),
+            "tgv3d_24": lambda: si.taylor_green_3d(24, seed=3)}[case]()
     s = _verlet(base, skin)
     with make(sph, s) as sc:
         sc.step(n)
