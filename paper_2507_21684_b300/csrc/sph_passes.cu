@@ -984,6 +984,46 @@ struct SweepPass {
       }
       c2 = fmaf(VgK * drho_ji, r2 * sd, c2);
     }
+#if SPH_W_PAIR2
+    // Two hits at once (a in .x, b in .y) with the paired FP32 operations (one instruction for
+    // both hits wherever the scalar form in pair_at has one; the square roots and reciprocals stay
+    // scalar); vb = false drops b.  The sums take a, then b, as two pair_at calls would.
+    static constexpr bool kPaired = !RENORM;
+    __device__ __forceinline__ static float2 sub2(float2 a, float2 b) {  // a - b, rounded once
+      return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+    }
+    __device__ __forceinline__ void pair_at2(const float* xsa, const PD<D>& pa, const float* xsb, const PD<D>& pb,
+                                             bool vb) {
+      float2 r[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) r[k] = sub2(make_float2(xsa[k], xsb[k]), make_float2(pa.x[k], pb.x[k]));
+      float2 r2 = __fmul2_rn(r[0], r[0]);
+#pragma unroll
+      for (int k = 1; k < D; ++k) r2 = __ffma2_rn(r[k], r[k], r2);
+      const float2 q = make_float2(safe_q(r2.x, invH), safe_q(r2.y, invH));
+      const float2 om = __ffma2_rn(q, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));
+      const float2 om2 = __fmul2_rn(om, om);
+      float2 g = __fmul2_rn(om2, om);
+      if (KERN == 0) g = __fmul2_rn(__fmul2_rn(__fmul2_rn(om2, om2), om), __ffma2_rn(make_float2(5.f, 5.f), q, make_float2(1.f, 1.f)));
+      const float2 gK = __fmul2_rn(make_float2(Kg, Kg), g);
+      float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < D; ++k) w = __ffma2_rn(sub2(make_float2(vi[k], vi[k]), make_float2(pa.v[k], pb.v[k])), r[k], w);
+      const float2 r2e = __fadd2_rn(r2, make_float2(eH2, eH2));
+      const float2 sd = make_float2(__fdividef(1.f, r2e.x), __fdividef(1.f, r2e.y));
+      const float2 VgK = __fmul2_rn(make_float2(pa.V, vb ? pb.V : 0.f), gK);
+      const float2 npp = __ffma2_rn(make_float2(pa.p, pb.p), make_float2(-1.f, -1.f), make_float2(-p_i, -p_i));
+      const float2 tt = __fmul2_rn(VgK, __ffma2_rn(__fmul2_rn(make_float2(Cv, Cv), w), sd, npp));
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc[k] = fmaf(tt.y, r[k].y, fmaf(tt.x, r[k].x, acc[k]));
+      c1 = fmaf(VgK.y, w.y, fmaf(VgK.x, w.x, c1));
+      const float2 drho = sub2(make_float2(pa.rho, pb.rho), make_float2(rho_i, rho_i));
+      const float2 t2 = __fmul2_rn(VgK, drho), u2 = __fmul2_rn(r2, sd);
+      c2 = fmaf(t2.y, u2.y, fmaf(t2.x, u2.x, c2));
+    }
+#else
+    static constexpr bool kPaired = false;
+#endif
     template <int L>
     __device__ __forceinline__ void reduce() {
 #pragma unroll

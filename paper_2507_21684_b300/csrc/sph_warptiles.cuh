@@ -49,6 +49,11 @@ namespace sph {
 #ifndef SPH_W_DRAIN2
 #define SPH_W_DRAIN2 1
 #endif
+// the two hits of an iteration evaluated together with the paired FP32 operations (passes whose
+// body provides pair_at2; the 128^3 vortex 1.195 -> 1.170 ms per step)
+#ifndef SPH_W_PAIR2
+#define SPH_W_PAIR2 1
+#endif
 // CTAs per SM the warp-traversal kernels are compiled for (register budget 64K / (MINB x THREADS))
 #ifndef SPH_W_MINB
 #define SPH_W_MINB 1
@@ -161,6 +166,27 @@ __device__ __forceinline__ int warp_drain(const float* L, const Arrays& a, const
     if (oa) warp_pop_hit(ring, h, ja, sa);
     if (ob) warp_pop_hit(ring, h, jb, sb);
     const PD<D> pa = load_pd<D>(a, ja), pb = load_pd<D>(a, jb);  // index 0 for a lane without the hit
+#if SPH_W_PAIR2
+    if constexpr (Body::kPaired) {
+      if (oa) {  // b rides along (dropped when this lane has no second hit)
+        float xa[D], xb[D];
+        PD<D> qa = pa, qb = pb;
+#pragma unroll
+        for (int q = 0; q < D; ++q) xa[q] = xb[q] = xt[q];
+        if (sa | sb) {  // periodic images (particles near the box faces only)
+#pragma unroll
+          for (int q = 0; q < D; ++q) {
+            if ((sa >> (3 + q)) & 1u) xa[q] -= L[q];
+            if ((sa >> q) & 1u) qa.x[q] -= L[q];
+            if ((sb >> (3 + q)) & 1u) xb[q] -= L[q];
+            if ((sb >> q) & 1u) qb.x[q] -= L[q];
+          }
+        }
+        body.pair_at2(xa, qa, xb, qb, ob);
+      }
+      continue;
+    }
+#endif
     if (oa) warp_eval_hit<D, EX0, EX1>(L, a, extra0, extra1, ja, sa, pa, xt, body);
     if (ob) warp_eval_hit<D, EX0, EX1>(L, a, extra0, extra1, jb, sb, pb, xt, body);
   }
