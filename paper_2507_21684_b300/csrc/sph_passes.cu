@@ -1468,7 +1468,7 @@ struct AdjPass {
   const float4 *S, *XBin, *VBin;
   const float* Pp;
   float4 *XBout, *VBout;
-  float* nu_part;  // per particle viscosity partials (summed deterministically afterwards)
+  double* nu_acc;  // per storage slot: the viscosity adjoint of every step so far (summed at the end)
   __device__ static __forceinline__ bool wants(uint32_t) { return true; }
   __device__ __forceinline__ void skip(int, const TgtView&) {}
   __device__ __forceinline__ void flush() {}
@@ -1508,7 +1508,7 @@ struct AdjPass {
     }
     XBout[i] = make_float4(ox[0], ox[1], ox[2], xb.w + b.grho);
     VBout[i] = make_float4(ov[0], ov[1], ov[2], 0.f);
-    nu_part[i] = b.gnu;
+    nu_acc[i] += (double)b.gnu;  // the slot's own running sum: no atomics, a fixed order
   }
 };
 
@@ -2182,7 +2182,7 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_pairs
 template <int D, int KERN>
 __global__ void __launch_bounds__(adj_threads<D>(), adj_minb<D>()) k_adj_t(TravArgs t, const Tile* tiles, const int* ntiles, const float4* S,
                                                const float* Pp, const float4* XBin, const float4* VBin, float4* XBout,
-                                               float4* VBout, float* nu_part) {
+                                               float4* VBout, double* nu_acc) {
   wait_prior_grid();
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the next kernel of the adjoint step may launch
   AdjPass<D, KERN> pass;
@@ -2193,7 +2193,7 @@ __global__ void __launch_bounds__(adj_threads<D>(), adj_minb<D>()) k_adj_t(TravA
   pass.VBin = VBin;
   pass.XBout = XBout;
   pass.VBout = VBout;
-  pass.nu_part = nu_part;
+  pass.nu_acc = nu_acc;
   run_tiles<D, (D == 2 ? 1 : 2), 0, AdjPass<D, KERN>, adj_lanes<D>()>(t, tiles, ntiles, S, D == 2 ? nullptr : Pp, pass);
 }
 
@@ -2218,7 +2218,8 @@ __global__ void __launch_bounds__(TileCfg<D>::THREADS, TileCfg<D>::MINB) k_adj_d
 // 16K-particle scene took about as long as half an adjoint sweep).  chunk: S x gridDim.x doubles;
 // ctr: S counters, zero between launches (the last CTA resets its scene's).
 constexpr int kSumChunk = 2048;
-__global__ void k_sum_segments(const float* __restrict__ part, const DevSeg* __restrict__ segs, double* __restrict__ chunk,
+template <class T>
+__global__ void k_sum_segments(const T* __restrict__ part, const DevSeg* __restrict__ segs, double* __restrict__ chunk,
                                int* __restrict__ ctr, double* __restrict__ acc) {
   wait_prior_grid();
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the next kernel of the adjoint step may launch
@@ -2371,10 +2372,10 @@ void launch_pairs_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int
 template <int D, int KERN>
 void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* S,
                   const float* Pp, const float4* XBin, const float4* VBin, float4* XBout, float4* VBout,
-                  float* nu_part, cudaStream_t st) {
+                  double* nu_acc, cudaStream_t st) {
   PdlLaunch L(pass_grid((const void*)k_adj_t<D, KERN>, tiles_upper), adj_threads<D>(),
               tile_smem_bytes<D, (D == 2 ? 1 : 2), adj_lanes<D>()>(), st);
-  cudaLaunchKernelEx(&L.cfg, k_adj_t<D, KERN>, t, tiles, ntiles, S, Pp, XBin, VBin, XBout, VBout, nu_part);
+  cudaLaunchKernelEx(&L.cfg, k_adj_t<D, KERN>, t, tiles, ntiles, S, Pp, XBin, VBin, XBout, VBout, nu_acc);
 }
 template <int D, int KERN>
 void launch_adj_dens_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* XBin,
@@ -2421,7 +2422,12 @@ int sum_segments_chunks(long long max_seg_n) { return (int)std::max(1LL, (max_se
 void launch_sum_segments(const float* part, const DevSeg* segs, int S, int nchunks, double* chunk, int* ctr,
                          double* acc, cudaStream_t st) {
   PdlLaunch L(dim3(nchunks, S), 256, 0, st);
-  cudaLaunchKernelEx(&L.cfg, k_sum_segments, part, segs, chunk, ctr, acc);
+  cudaLaunchKernelEx(&L.cfg, k_sum_segments<float>, part, segs, chunk, ctr, acc);
+}
+void launch_sum_segments(const double* part, const DevSeg* segs, int S, int nchunks, double* chunk, int* ctr,
+                         double* acc, cudaStream_t st) {
+  PdlLaunch L(dim3(nchunks, S), 256, 0, st);
+  cudaLaunchKernelEx(&L.cfg, k_sum_segments<double>, part, segs, chunk, ctr, acc);
 }
 void launch_sum_float_partials(const float* part, int n, double* acc, cudaStream_t st) {
   k_sum_float_partials<<<1, 1024, 0, st>>>(part, n, acc);
@@ -2525,7 +2531,7 @@ SPH_INST_PD(3)
   template void launch_rates_t<D, K>(const TravArgs&, const Tile*, const int*, int, const RateOut&, const float4*, \
                                      cudaStream_t);                                                          \
   template void launch_adj_t<D, K>(const TravArgs&, const Tile*, const int*, int, const float4*, const float*,  \
-                                   const float4*, const float4*, float4*, float4*, float*, cudaStream_t);      \
+                                   const float4*, const float4*, float4*, float4*, double*, cudaStream_t);     \
   template void launch_adj_dens_t<D, K>(const TravArgs&, const Tile*, const int*, int, const float4*,          \
                                         const float4*, float4*, float4*, cudaStream_t);
 SPH_INST_PDK(2, 0)

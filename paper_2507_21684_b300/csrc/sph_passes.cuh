@@ -66,7 +66,7 @@ void launch_unpermute3(int N, const uint2* meta, const int* orig_base, const flo
 template <int D, int KERN>
 void launch_adj_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* S,
                   const float* Pp, const float4* XBin, const float4* VBin, float4* XBout, float4* VBout,
-                  float* nu_part, cudaStream_t st);
+                  double* nu_acc, cudaStream_t st);
 // summation mode: the adjoint of rho^ = sum_j m_j W_ij (left in XBin.w) passed to the positions
 template <int D, int KERN>
 void launch_adj_dens_t(const TravArgs& t, const Tile* tiles, const int* ntiles, int tiles_upper, const float4* XBin,
@@ -76,6 +76,8 @@ void launch_sum_float_partials(const float* part, int n, double* acc, cudaStream
 // once, left zeroed), nchunks = sum_segments_chunks(largest scene's particle count).
 int sum_segments_chunks(long long max_seg_n);
 void launch_sum_segments(const float* part, const DevSeg* segs, int S, int nchunks, double* chunk, int* ctr,
+                         double* acc, cudaStream_t st);
+void launch_sum_segments(const double* part, const DevSeg* segs, int S, int nchunks, double* chunk, int* ctr,
                          double* acc, cudaStream_t st);
 
 }  // namespace sph

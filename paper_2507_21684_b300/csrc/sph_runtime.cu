@@ -1128,7 +1128,7 @@ void Scene::alloc_tape(int k) {
     d_replay_maxr = (unsigned*)mem.get(sizeof(unsigned) * 2);
     CK(cudaMemsetAsync(d_replay_flag, 0, sizeof(int) * 4, st));
     CK(cudaMemsetAsync(d_replay_maxr, 0, sizeof(unsigned) * 2, st));
-    nu_part = (float*)mem.get(sizeof(float) * (size_t)N);
+    nu_acc = (double*)mem.get(sizeof(double) * (size_t)N);
     alloc_arrays(scratch_arr);
     rep_out[0] = scratch_arr;
     alloc_arrays(rep_out[1]);
@@ -1190,21 +1190,19 @@ void Scene::adjoint_backward(int L, int K, int b) {
     prof_begin(4);
     if (D == 2) {
       if (kern == 0)
-        launch_adj_t<2, 0>(t, cells.tiles, cells.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        launch_adj_t<2, 0>(t, cells.tiles, cells.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_acc, st);
       else
-        launch_adj_t<2, 1>(t, cells.tiles, cells.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        launch_adj_t<2, 1>(t, cells.tiles, cells.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_acc, st);
     } else {
       if (kern == 0)
-        launch_adj_t<3, 0>(t, cells.tiles, cells.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        launch_adj_t<3, 0>(t, cells.tiles, cells.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_acc, st);
       else
-        launch_adj_t<3, 1>(t, cells.tiles, cells.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_part, st);
+        launch_adj_t<3, 1>(t, cells.tiles, cells.ntiles, tiles_upper, Sd, Pp, XB[q], VB[q], XB[1 - q], VB[1 - q], nu_acc, st);
     }
     CKL();
     prof_end();
-    launch_sum_segments(nu_part, dseg, S, sum_nch, sum_chunk, sum_ctr, d_nubar, st);
-    CKL();
     q = 1 - q;
-    launches += 3;  // seed, adjoint sweep, segment sums
+    launches += 2;  // seed, adjoint sweep
     if (summation) {  // the density adjoint left in XB.w passes to the positions
       if (D == 2) {
         if (kern == 0) launch_adj_dens_t<2, 0>(t, cells.tiles, cells.ntiles, tiles_upper, XB[q], VB[q], XB[1 - q], VB[1 - q], st);
@@ -1317,7 +1315,11 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
   // enters each segment through the original order: the seeds after the last segment's replay,
   // the running adjoint by a store / load through the rows at every later segment
   float* rows = adj_rows;
+  // dL/dnu: each adjoint sweep adds its particles' terms into their storage slots (nu_acc), and
+  // one deterministic per-scene sum over the slots after the last segment gives the total (the
+  // slots' order changes at rebuilds, which only regroups the same terms)
   CK(cudaMemsetAsync(d_nubar, 0, sizeof(double) * S, st));
+  CK(cudaMemsetAsync(nu_acc, 0, sizeof(double) * (size_t)N, st));
   const int ncp = (n + k - 1) / k;
   // The segments' replays run on st_rep, one segment ahead of the reverse pass on st: while the
   // reverse pass of segment sgi reads tape sgi % 2, the replay of segment sgi - 1 fills the other
@@ -1392,6 +1394,9 @@ void Scene::adjoint(const float* xb, const float* vb, const float* rb, float* xb
   else
     launch_adj_store<3>(N, ckpts[0].meta, d_orig_base, XB[q], VB[q], oxb, ovb, orb, st);
   CKL();
+  launch_sum_segments(nu_acc, dseg, S, sum_nch, sum_chunk, sum_ctr, d_nubar, st);
+  CKL();
+  launches += 2;
   // the replay reused the sort buffers: the live state must rebuild before its next step
   cells_valid = false;
   launches_total += launches;

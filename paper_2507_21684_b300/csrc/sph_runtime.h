@@ -184,7 +184,7 @@ struct Scene {
   float4* VB[2] = {nullptr, nullptr};
   float4* Sd = nullptr;
   float* Pp = nullptr;
-  float* nu_part = nullptr;
+  double* nu_acc = nullptr;         // adjoint: per storage slot, the viscosity adjoint summed over the steps
   Arrays scratch_arr{};
   Arrays rep_out[2]{};               // a replay's sweep output before a rebuild, per tape ([0] is scratch_arr)
   int* d_tile_ctr_b = nullptr;      // tile counter of the reverse pass's launches (beside the replay's)

@@ -146,3 +146,44 @@ def test_request_over_budget_is_rejected(sph):
         with pytest.raises(sph.SphError) as e:
             sv.submit(sp, 10)
         assert e.value.code == sph.SPH_EINVAL
+
+
+def test_server_scenes_bypass_the_allocator_hook(sph):
+    """The serving loop's scenes allocate from the CUDA stream-ordered pool, never through the
+    sph_set_allocator hook (a hook may call back into an interpreter whose lock the server's
+    threads would contend for): with a counting hook installed, a scene of the scene API
+    allocates through it, forward and adjoint requests of the server do not."""
+    import torch
+    calls = [0]
+
+    def alloc(nbytes, stream, ctx):
+        calls[0] += 1
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    hooks = (sph._ALLOC_FN(alloc), sph._FREE_FN(free))
+    lib = sph.lib()
+    prev = sph._hooks
+    assert lib.sph_set_allocator(hooks[0], hooks[1], None) == 0
+    try:
+        spec = si.taylor_green_2d(16, seed=0)
+        with sph.scene_from(spec) as sc:  # control: the scene API allocates through the hook
+            sc.step(2)
+        n_scene = calls[0]
+        assert n_scene > 0
+        with sph.Server(1 << 30, 8) as sv:
+            tf = sv.submit(spec, 6)
+            ta = sv.submit(spec, 6, adjoint=True, ckpt_every=3)
+            rf, ra = sv.wait(tf), sv.wait(ta)
+        assert np.isfinite(rf["x"]).all() and np.isfinite(ra["vbar0"]).all()
+        assert calls[0] == n_scene, f"served requests made {calls[0] - n_scene} allocations through the hook"
+    finally:
+        if prev is not None:
+            lib.sph_set_allocator(prev[0], prev[1], None)
+        else:
+            lib.sph_set_allocator(sph._ALLOC_FN(), sph._FREE_FN(), None)
