@@ -1452,7 +1452,7 @@ void Scene::check_status() {
   CK(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (h & 2) {
-    set_err("a bounded device wait gave up (a grid barrier of the cooperative rebuild, or a sweep tile waiting for the wall tasks)");
+    set_err("a bounded device wait gave up (a grid barrier of the cooperative rebuild, a sweep tile waiting for the wall tasks, or a warp waiting for its CTA's tile chunk)");
     throw Fail{SPH_EINTERNAL};
   }
   if (h & 1) {
