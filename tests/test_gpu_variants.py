@@ -50,3 +50,24 @@ def test_tile_tuner_times_every_variant():
     r = tune.tune_tiles(si.dam_break(res=32), steps=20, warmup=5)
     assert {t["variant"] for t in r["table"]} == set(tune.shape_variants(2))
     assert r["variant"] in build.VARIANTS and all(t["ms_per_step"] > 0 for t in r["table"])
+
+
+def test_cooperative_3d_rebuild_with_a_skin_matches_oracle(orc, tmp_path):
+    """The library variant whose captured 3D steps rebuild in one cooperative launch (keys with x
+    sub-bins computed in its first sort pass, the sub-bins' offsets written by its permute) gives
+    the oracle's 3D rollout under a Verlet skin, rebuilding fewer times than it steps."""
+    from paper_2507_21684_b300 import build, tune
+    build.build(variant="coop3")
+    s = si.taylor_green_3d(24, seed=3)
+    p = dict(s["params"], skin=float(np.float32(0.1 * s["params"]["H"])), rebuild_interval=1 << 20)
+    s = dict(s, params=p)
+    spec, out = str(tmp_path / "s.npz"), str(tmp_path / "o.npz")
+    tune.save_spec(s, spec)
+    script = SCRIPT.replace("sc.step(10)", "sc.step(40)\n    st = sc.stats()").replace(
+        "np.savez(sys.argv[2], x=x, v=v, rho=r)", "np.savez(sys.argv[2], x=x, v=v, rho=r, rebuilds=st['rebuilds'])")
+    subprocess.run([sys.executable, "-c", script, spec, out], cwd=ROOT, check=True,
+                   env=dict(os.environ, SPH_B300_VARIANT="coop3"))
+    z = np.load(out)
+    assert 1 < int(z["rebuilds"]) < 40
+    xo, vo, ro = orc.rollout(s, 40)
+    check_rollout(s, 40, z["x"], z["v"], z["rho"], xo, vo, ro)
