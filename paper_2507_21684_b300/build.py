@@ -22,6 +22,10 @@ VARIANTS = {
     "lanes2": {"SPH_TILE2_TP": 128, "SPH_TILE2_LANES": 2, "SPH_TILE2_LIST": 40},
     "small": {"SPH_TILE2_TP": 32, "SPH_TILE2_LANES": 4, "SPH_TILE2_LIST": 24, "SPH_TILE2_THREADS": 128,
               "SPH_TILE2_CAP": 512},
+    # the same 2D tiles with the cooperative rebuild on one CTA per SM (a cheaper launch on the
+    # steps that rebuild nothing, a slower rebuild when one is due)
+    "small1": {"SPH_TILE2_TP": 32, "SPH_TILE2_LANES": 4, "SPH_TILE2_LIST": 24, "SPH_TILE2_THREADS": 128,
+               "SPH_TILE2_CAP": 512, "SPH_RB_CTAS_PER_SM": 1},
     "small3": {"SPH_TILE3_TP": 16, "SPH_TILE3_LANES": 8, "SPH_TILE3_LIST": 18, "SPH_TILE3_THREADS": 128,
                "SPH_TILE3_CAP": 768},
     # how lines are cut into tiles: whole cells in 2D, whole cells in 3D (the defaults swapped)
