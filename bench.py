@@ -59,10 +59,22 @@ def kernel_fingerprint() -> str:
     return h.hexdigest()[:16]
 
 
+def _shape_macros(variant: str) -> dict:
+    """The macros of a library variant that shape the neighbour-pass kernels (tile shape and the
+    3D warp traversal); variants that differ only elsewhere (the rebuild launch) run the same
+    sweep kernels."""
+    from paper_2507_21684_b300 import build as sbuild
+    try:
+        m = sbuild.variant_macros(variant)
+    except ValueError:
+        return {"?": variant}
+    return {k: v for k, v in m.items() if k.startswith("SPH_TILE") or k.startswith("SPH_W")}
+
+
 def stored_traffic(prefix: str, variant: str = "default"):
     """DRAM bytes per launch from the committed ncu summary profiles/<prefix>*.md taken with the
-    same library variant (tile shape) and kernel sources (the summary records both), with the
-    summary's name; (None, None) when there is none."""
+    same kernel sources and a library variant of the same tile shape (the summary records both),
+    with the summary's name; (None, None) when there is none."""
     import glob
     import re
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", prefix + "*.md"))):
@@ -71,7 +83,8 @@ def stored_traffic(prefix: str, variant: str = "default"):
         fp = re.search(r"fingerprint[^`]*`([0-9a-f]+)`", txt)
         tb = re.search(r"DRAM bytes per launch \(read \+ write\): (\d+)", txt)
         lv = re.search(r"Library variant[^`]*`(\w+)`", txt)
-        if fp and tb and fp.group(1) == kernel_fingerprint() and (lv.group(1) if lv else "default") == variant:
+        if (fp and tb and fp.group(1) == kernel_fingerprint()
+                and _shape_macros(lv.group(1) if lv else "default") == _shape_macros(variant)):
             return int(tb.group(1)), "profiles/" + os.path.basename(path)
     return None, None
 
@@ -701,8 +714,8 @@ def main():
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS,
                          "traffic": traffic,
-                         "traffic_source": (f"{traffic_src} (ncu, one launch, library variant {variant})"
-                                            if traffic_src else None),
+                         "traffic_source": (f"{traffic_src} (ncu, one launch of the same sweep kernel and tile "
+                                            f"shape; this run's library variant {variant})" if traffic_src else None),
                          "flops_per_pair": FLOPS_PER_PAIR[3], "pairs_per_launch": fw["pairs_per_step"],
                          "sweep_ms_avg": fw["sweep_ms"], "sweep_launches": fw["sweep_n"],
                          "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz (unit counts and "
