@@ -392,7 +392,10 @@ __device__ __forceinline__ int warp_tile_task(const TravArgs& t, const Tile& T, 
 // share an SM's L1 work on neighbouring tiles of one cell line, whose neighbour lines largely
 // coincide (with one warp per claim the warps of an SM held tiles about 148 apart).  A warp that
 // takes the first tile of a chunk claims the chunk and publishes its index in a small ring of
-// slots in shared memory; one that takes a later tile waits (bounded) for that slot.
+// slots in shared memory; one that takes a later tile waits (bounded) for that slot.  A slot is
+// reused by the chunk SLOTS chunks later, which needs SLOTS x CHUNK further claims by the other
+// warps of the CTA, each after a whole tile, while the waiting warp polls a flag that the
+// claimant sets right after one global atomic; a wait that runs out sets status bit 1.
 constexpr long long kChunkSpins = 1LL << 20;
 
 template <int D, bool ZERO_OK, bool EX0, bool EX1, class Pass, class End>
