@@ -417,6 +417,22 @@ def test_full_size_3d_rates_sampled(sph, orc):
     assert rel(g["drho"][idx], o["drho"]) < 1e-5
 
 
+def test_full_size_3d_headline_steps(sph, orc):
+    """The benchmark's launch configuration: 2,097,152-particle 3D Taylor-Green with the tuned
+    Verlet skin of 0.05 H, graph-launched steps (the warp-per-tile sweep in CTAs of 24 warps, x
+    sub-bins, device-decided rebuilds in conditional graph nodes); five steps against the FP64
+    oracle's rollout over every particle."""
+    s = _verlet(si.taylor_green_3d(128, seed=0), 0.05)
+    n = 5
+    with make(sph, s) as sc:
+        sc.step(n)
+        st = sc.stats()
+        x, v, rho = sc.get_state()
+    assert 1 <= st["rebuilds"] <= n, st
+    xo, vo, ro = orc.rollout(s, n)
+    check_rollout(s, n, x, v, rho, xo, vo, ro)
+
+
 def test_instability_is_reported(sph):
     s = si.taylor_green_2d(16, seed=0)
     s = dict(s, v=(s["v"] * 200.0).astype(np.float32))
