@@ -433,6 +433,25 @@ def test_full_size_3d_headline_steps(sph, orc):
     check_rollout(s, n, x, v, rho, xo, vo, ro)
 
 
+def test_3d_closed_box_with_walls_rollout(sph, orc):
+    """3D scene in a closed box (no periodic axis) with three layers of wall particles around the
+    fluid: the warp-per-tile sweep's clamped windows at the box faces, the 3D wall pass (Shepard
+    extrapolation with gravity) and the fluid's rollout against the oracle."""
+    s = si.shift_problem(12, seed=5, dim=3, walls=True)
+    n, nf = len(s["x"]), s["n_fluid"]
+    rng = np.random.default_rng(3)
+    v = np.zeros((n, 3), np.float32)
+    v[:nf] = (0.3 * rng.standard_normal((nf, 3))).astype(np.float32)
+    p = dict(s["params"], nu=0.01, delta=0.1, g=[0.0, 0.0, -1.0])
+    s = dict(s, v=v, params=p)
+    nsteps = 10
+    with make(sph, s) as sc:
+        sc.step(nsteps)
+        x, v1, rho = sc.get_state()
+    xo, vo, ro = orc.rollout(s, nsteps)
+    check_rollout(dict(s, x=s["x"][:nf]), nsteps, x[:nf], v1[:nf], rho[:nf], xo[:nf], vo[:nf], ro[:nf])
+
+
 def test_instability_is_reported(sph):
     s = si.taylor_green_2d(16, seed=0)
     s = dict(s, v=(s["v"] * 200.0).astype(np.float32))
