@@ -100,9 +100,10 @@ extern "C" {
  * The cell structure is rebuilt every step when skin == 0.  With skin > 0 (a Verlet list in the
  * sense of App. B) a captured step rebuilds only when rebuild_interval sweeps have used the
  * current cells or when some particle has moved farther than skin/2 since the last build (the
- * sweep measures the displacement and its last CTA decides; the rebuild is a cooperative launch in
- * the step's CUDA graph that returns at once unless a rebuild is due).  Steps run without graphs
- * rebuild every step; the adjoint's replay rebuilds on its own schedule (sph_adjoint_info). */
+ * sweep measures the displacement; in 2D its last CTA decides and the rebuild is a cooperative
+ * launch in the step's CUDA graph that returns at once unless a rebuild is due; in 3D a one-thread
+ * kernel decides and a conditional node of the graph runs the rebuild kernels).  Steps run without
+ * graphs rebuild every step; the adjoint's replay rebuilds on its own schedule (sph_adjoint_info). */
 typedef struct sph_params {
   int32_t dim;            /* 2 or 3 */
   int32_t kernel;         /* SPH_KERNEL_* */
