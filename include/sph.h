@@ -324,7 +324,8 @@ SPH_API void sph_destroy(sph_scene* scene);
  * it serves many independent scenes the way the paper batches them, Sec. 4.1).
  *
  * A server owns a stream and a host thread for the forward batch and one of each per adjoint
- * worker (three).  sph_submit copies the request and queues it;
+ * worker (three), so it takes no caller stream: requests arrive from host memory and sph_wait
+ * returns results to host memory.  sph_submit copies the request and queues it;
  * requests are admitted in arrival order while the estimated device bytes of all admitted
  * requests stay within hbm_budget_bytes and at most max_active run at once.  Admitted forward
  * rollouts keep their particle state resident in one packed batch that is advanced with shared
