@@ -163,6 +163,9 @@ ROLL_CASES = {
     "tgv3d_32": lambda: si.taylor_green_3d(32, seed=1),
     "tgv2d_32_summation": lambda: si.taylor_green_2d(32, seed=2, density_mode=1),
     "dambreak_64_summation": lambda: _summation(si.dam_break(res=64)),
+    # 3D in summation mode with a Verlet skin: the density pass and the warp-per-tile sweep on cells
+    # rebuilt in conditional graph nodes, with x sub-bins
+    "tgv3d_20_summation_skin": lambda: _verlet(_summation(si.taylor_green_3d(20, seed=6)), 0.1),
     "tgv2d_32_verlet": lambda: si.taylor_green_2d(32, seed=2, skin=0.02, rebuild_interval=5),
 }
 
