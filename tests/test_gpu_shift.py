@@ -67,6 +67,11 @@ ROLL = {
     "dambreak_64_skin": (lambda: si.dam_break(res=64, shift=0.05, skin=float(np.float32(0.02 * 4 / 64)),
                                               rebuild_interval=1 << 20), True),
     "tgv3d_24": (lambda: si.taylor_green_3d(24, seed=1, jitter=0.2, shift=0.1), True),
+    # 3D with a Verlet skin: the sweep's and the shift's rebuilds in conditional graph nodes, with
+    # x sub-bins, and the renormalised diffusion's gradient pass
+    "tgv3d_24_renorm_skin": (lambda: si.taylor_green_3d(24, seed=1, jitter=0.2, shift=0.1, diffusion=1,
+                                                        skin=float(np.float32(0.1 * 2.43 / 24)),
+                                                        rebuild_interval=1 << 20), True),
 }
 
 
