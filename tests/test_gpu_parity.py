@@ -608,6 +608,32 @@ def test_batched_3d_scenes_bitwise_equal_alone(sph, orc):
     check_rollout(specs[0], 5, xb[f:f + n], vb[f:f + n], rb[f:f + n], xo, vo, ro)
 
 
+def test_batched_3d_scenes_with_a_skin_match_alone_and_oracle(sph, orc):
+    """3D scenes with Verlet skins in one batch (cells rebuilt in conditional graph nodes with x
+    sub-bins, the whole batch whenever one scene needs it): each scene equals its result alone to
+    float rounding (its sums may run in another order), and the first matches the oracle."""
+    raw = [si.taylor_green_3d(12, seed=1), si.taylor_green_3d(16, seed=2, nu=0.01), si.taylor_green_3d(10, seed=4)]
+    specs = [_verlet(s, 0.1) for s in raw]
+    n = 12
+    with sph.Scene.batch(specs) as bt:
+        bt.step(n)
+        st = bt.stats()
+        xb, vb, rb = bt.get_state()
+        rows = list(zip(bt.first_row, bt.rows))
+    assert 1 <= st["rebuilds"] < n, st
+    for spec, (f, m) in zip(specs, rows):
+        with make(sph, spec) as sc:
+            sc.step(n)
+            x, v, r = sc.get_state()
+        x0 = spec["x"].astype(np.float64)
+        assert rel(xb[f:f + m] - x0, x - x0) < 1e-4
+        assert rel(vb[f:f + m], v) < 1e-4
+        assert rel(rb[f:f + m] - 1.0, r - 1.0) < 1e-4
+    xo, vo, ro = orc.rollout(specs[0], n)
+    f, m = rows[0]
+    check_rollout(specs[0], n, xb[f:f + m], vb[f:f + m], rb[f:f + m], xo, vo, ro)
+
+
 def test_batched_adjoint_bitwise_equal_alone(sph):
     specs = _batch_specs()
     rng = np.random.default_rng(3)
